@@ -1,0 +1,365 @@
+"""Benchmark of the GB300 Burton-Miller BEM path: BEM solves per second.
+
+Workload (the interior-point-source case): a perturbed ellipsoid (radii 1, 0.8, 0.6, l <= 6
+radial harmonics of std 0.05) meshed with 10240 triangles, Neumann data of a monopole at the
+origin, 64 wavenumbers log-uniform in ka in [0.5, 20], 1024 field points at radius 4. One step
+is the whole path for all 64 wavenumbers: per wavenumber, assemble L and R on the device,
+solve L p = R g by GMRES to a relative residual of 1e-6, and evaluate the field at the 1024
+points. A "solve" is one (mesh, k, Neumann data) through all three stages.
+
+Prints one JSON line. `value` is solves/s with inputs resident in HBM; `e2e` is the same
+metric through the public API with host (numpy) buffers, host-device copies included.
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+
+Multi-GPU: independent solves shard with no exchange (replicas only): each rank runs the
+workload on its own GPU and `value` is the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+METRIC = "BEM solves/s at <=1e-4 rel err vs FP64 oracle (plain FP32 and mixed), p50/p99 ms"
+UNIT = "solves/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n_k: int):
+    return S.interior_source(n_k=n_k)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank: int, world: int):
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        nb_build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    prob = workload(args.n_k)
+    n = prob.F.shape[0]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    Vd = torch.from_numpy(prob.V).to(dev)
+    Fd = torch.from_numpy(prob.F).to(dev)
+    Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
+    Pd = torch.from_numpy(prob.points).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    results = {}
+
+    def one_solve(i, k, record=None):
+        op = nb.Operator.assemble(Vd, Fd, float(k), opts)
+        p, info, st = op.solve(Gd[i], check=True)
+        fld = op.evaluate(Pd, p, Gd[i])
+        op.close()
+        if record is not None:
+            record.append((i, p, fld, info.iterations, info.rel_residual, st))
+        return p, fld
+
+    def step(lat_events=None, record=None):
+        for i, k in enumerate(prob.ks):
+            if lat_events is not None:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            one_solve(i, k, record)
+            if lat_events is not None:
+                e1 = torch.cuda.Event(enable_timing=True)
+                e1.record(stream)
+                lat_events.append((e0, e1))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    nb.nat_bem_trace_reset()
+    nb.nat_bem_trace_enable(True)
+    lat = []
+    record = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(lat, record if not record else None)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    nb.nat_bem_trace_enable(False)
+    ms_total = t0.elapsed_time(t1)
+    launches = nb.nat_bem_trace_launches()
+    kern = {}
+    for name in ("assemble_regular", "assemble_near", "geometry", "gemv_rhs", "gemv_resid",
+                 "gmres_dots", "gmres_update_dots", "gmres_update_norm", "gmres_normalize",
+                 "eval_reduce"):
+        kern[name] = nb.nat_bem_trace_kernel(name)
+    kern["gemv"] = tuple(a - b - c for a, b, c in zip(nb.nat_bem_trace_kernel("gemv"), kern["gemv_rhs"], kern["gemv_resid"]))
+    ev = nb.nat_bem_trace_kernel("eval")
+    kern["eval"] = (ev[0] - kern["eval_reduce"][0], ev[1] - kern["eval_reduce"][1])
+    nb.nat_bem_trace_reset()
+    lats = sorted(a.elapsed_time(b) for a, b in lat)
+    iters = [r[3] for r in record]
+    # GPU solution for the first wavenumber (compared with the oracle below)
+    first = record[0]
+    results.update(
+        ms_total=ms_total, launches=launches, kern=kern, lat=lats, iters=iters,
+        p0=first[1].cpu().numpy(), f0=first[2].cpu().numpy(), clocks=clk.summary(), n=n,
+        max_rel_res=max(r[4] for r in record))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e:
+        Vh, Fh, Ph = prob.V, prob.F, prob.points
+        Gh = [np.ascontiguousarray(g[:, 0]).astype(np.complex64) for g in prob.neumann]
+        torch.cuda.synchronize()
+        ta = time.perf_counter()
+        for i, k in enumerate(prob.ks):
+            op = nb.Operator.assemble(Vh, Fh, float(k), opts)
+            p, info, st = op.solve(Gh[i])
+            fld = op.evaluate(Ph, p, Gh[i])
+            op.close()
+        torch.cuda.synchronize()
+        tb = time.perf_counter()
+        nk = len(prob.ks)
+        h2d = Vh.nbytes + Fh.nbytes + Gh[0].nbytes * 2 + Ph.nbytes + p.nbytes
+        d2h = p.nbytes + fld.nbytes
+        e2e = {"value": nk / (tb - ta), "unit": UNIT, "h2d_bytes_per_step": int(h2d * nk),
+               "d2h_bytes_per_step": int(d2h * nk), "solves_per_step": nk}
+    results["e2e"] = e2e
+    results["prob"] = prob
+    return results
+
+
+def roofline(res, peaks, peak_kind):
+    """Dominant kernel's achieved rate against its ceiling."""
+    n = res["n"]
+    ld = (n + 31) // 32 * 32
+    kern = res["kern"]
+    table = {}
+    # gemv: 8 n ld bytes of operator + 8 ld of x + 16 n of y per launch (one RHS)
+    t, c = kern["gemv"]
+    if c:
+        bytes_per = 8.0 * n * ld + 8.0 * ld + 16.0 * n
+        gbs = bytes_per / (t / c * 1e-3) / 1e9
+        table["gemv"] = {"bound": "hbm", "launches": c, "avg_ms": t / c, "achieved": gbs,
+                         "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                         "algorithmic_bytes_per_launch": bytes_per}
+    # regular assembly: FP32 flops per element pair (7 quadrature points), counted from the
+    # kernel's arithmetic (an FMA counts 2)
+    t, c = kern["assemble_regular"]
+    if c:
+        pairs = float(n) * n
+        flops = pairs * FLOPS_PER_PAIR
+        tf = flops / (t / c * 1e-3) / 1e12
+        fp32_peak = FP32_LANES_PER_SM * SMS * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        table["assemble_regular"] = {"bound": "alu", "launches": c, "avg_ms": t / c, "achieved": tf,
+                                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
+                                     "algorithmic_flops_per_launch": flops}
+    dom = max(table, key=lambda k: kern[k][0]) if table else None
+    return dom, table
+
+
+# FP32 operations of k_assemble_regular per (i, j) pair: per quadrature point 29 FMA + 19
+# other FP32 operations (2 x 29 + 19 = 77 flops) plus 3 MUFU operations (rsqrt, sin, cos) not
+# counted; per pair 6 + 15 operations for the centroid difference and the three dot products.
+FLOPS_PER_PAIR = 7 * 77 + 21
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def cpu_baseline(prob, nthreads: int):
+    import oracle
+    k = float(prob.ks[0])
+    g = prob.neumann[0][:, 0]
+    t = time.perf_counter()
+    p, fld, info = oracle.bem_solve(prob.V, prob.F, k, g, prob.points, tol=1e-6, maxit=200,
+                                    nthreads=nthreads)
+    dt = time.perf_counter() - t
+    return p, fld, dt, info
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="natbem", choices=["natbem", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "tf32"])
+    ap.add_argument("--n-k", type=int, default=64)
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    peaks, peak_kind = _peaks()
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        prob = workload(args.n_k)
+        nth = oracle.hardware_threads()
+        for w in range(args.warmup):
+            cpu_baseline(prob, nth)
+        t = time.perf_counter()
+        for s in range(args.steps):
+            cpu_baseline(prob, nth)
+        dt = time.perf_counter() - t
+        v = args.steps / dt
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "interior_source_10240tri_64k", "n_tri": int(prob.F.shape[0]),
+                           "step": "one solve (first wavenumber) of the workload"},
+                "cpu_baseline": {"value": v, "unit": UNIT, "cores": nth, "kind": "oracle",
+                                 "sample": "one wavenumber of the 64 per step"},
+                "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res = run_gpu(args, rank, world)
+    prob = res.pop("prob")
+    n_solves = args.steps * len(prob.ks)
+    ms = res["ms_total"]
+    my_rate_time = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        my_rate_time = float(t.item())
+    value = n_solves * world / (my_rate_time * 1e-3)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+    dom, table = roofline(res, peaks, peak_kind)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": my_rate_time / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (+f64 near pairs and Krylov)",
+        "data": "synthetic",
+        "config": {"workload": "interior_source_10240tri_64k", "n_tri": res["n"],
+                   "n_wavenumbers": len(prob.ks), "ka_range": [0.5, 20.0], "field_points": 1024,
+                   "precision": args.prec, "tol": 1e-6, "max_iter": 200,
+                   "l2": "inputs larger than L2: each wavenumber's operators are 2 x 839 MB"},
+        "latency_ms": {"p50": float(np.percentile(res["lat"], 50)), "p99": float(np.percentile(res["lat"], 99)),
+                       "per": "one solve: assemble + GMRES + field"},
+        "gmres_iterations": {"min": min(res["iters"]), "median": float(np.median(res["iters"])),
+                             "max": max(res["iters"])},
+        "max_rel_residual": res["max_rel_res"],
+        "gpu_launches": int(res["launches"]),
+        "clocks": res["clocks"],
+    }
+    if dom:
+        d = table[dom]
+        line["roofline"] = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                            "unit": d["unit"], "frac": d["frac"], "traffic": None,
+                            "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else 'derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock'})"}
+    line["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in res["kern"].items()}
+    line["rooflines"] = table
+    if res["e2e"]:
+        line["e2e"] = res["e2e"]
+    if args.cpu:
+        import oracle
+        oracle.build()
+        nth = oracle.hardware_threads()
+        p_ref, f_ref, dt, info = cpu_baseline(prob, nth)
+        ep = float(np.linalg.norm(res["p0"] - p_ref) / np.linalg.norm(p_ref))
+        ef = float(np.linalg.norm(res["f0"] - f_ref) / np.linalg.norm(f_ref))
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+                                "sample": f"one solve (k={prob.ks[0]:.4f}) of the 64; stage seconds "
+                                          f"{[round(x, 2) for x in info['times']]}"}
+        line["rel_err_vs_oracle"] = {"surface": ep, "field": ef, "k": float(prob.ks[0])}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

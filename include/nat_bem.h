@@ -1,0 +1,168 @@
+/*
+ * nat_bem.h -- C ABI of the GB300 (sm_103a) exterior Helmholtz Burton-Miller BEM solver.
+ *
+ * The problem (paper Sec. 3.4): given a closed triangle mesh, a wavenumber k and Neumann data
+ * (normal derivative of the pressure, constant per triangle), solve for the surface Dirichlet
+ * data (pressure) and then evaluate the radiated pressure at field points. The boundary
+ * integral equation is the Burton-Miller combination of Sec. 4, Eq. 6, with the free-space
+ * Green's function G(x,y) = e^{ikr}/(4 pi r) of Sec. 4.2 and coupling beta = i/k. It is
+ * discretised with piecewise-constant elements collocated at the centroids:
+ *
+ *   L p = R g,   L_ij = 1/2 d_ij - int_j [dG/dn_y + beta d2G/dn_x dn_y] dS_y,
+ *                R_ij = -int_j [G + beta dG/dn_x] dS_y - (beta/2) d_ij,
+ *
+ * which is the directly assembled two-matrix system "A g = B p" of Sec. 4.1. The linear solve
+ * is GMRES stopped at a relative residual of 1e-6 within 200 iterations (the paper's solver
+ * settings, Sec. 6.1). The field follows from the exterior representation
+ * p(x) = int [p dG/dn_y - G g] dS_y (Sec. 3.4: pressure anywhere from the Neumann and
+ * Dirichlet data).
+ *
+ * Conventions for every call:
+ *   - Triangles wind counter-clockwise seen from outside (outward normals).
+ *   - Complex arrays are single-precision complex (float re, float im) interleaved. A block of
+ *     nrhs right-hand sides is column-major: column s holds nt (or m) consecutive values.
+ *   - Array arguments may be host or device pointers; the library detects which. With host
+ *     pointers the call copies through the given stream and returns once the copy is done.
+ *   - `cuda_stream` is a cudaStream_t (NULL = the legacy default stream). All device work of
+ *     a call is ordered on it.
+ *   - The caller owns every array it passes. The library owns nat_bem_op (the device-resident
+ *     operator, geometry and Krylov workspace) until nat_bem_destroy.
+ *   - Calls on one op are not thread-safe; different ops are independent.
+ *   - No function throws or aborts across the ABI. On any status other than NAT_BEM_OK,
+ *     nat_bem_last_error() returns a message (thread-local) and outputs are untouched, except
+ *     NAT_BEM_ENOCONV, which still writes the best iterate and fills the info struct.
+ */
+#ifndef NAT_BEM_H
+#define NAT_BEM_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define NAT_BEM_API __attribute__((visibility("default")))
+#else
+#define NAT_BEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NAT_BEM_OK = 0,
+  NAT_BEM_EINVAL = 1,   /* bad argument or invalid mesh (see nat_bem_assemble)            */
+  NAT_BEM_ENOMEM = 2,   /* device allocation failed or the op would exceed a memory budget */
+  NAT_BEM_ENOCONV = 3,  /* GMRES did not reach tol within max_iter (best iterate returned)  */
+  NAT_BEM_ECUDA = 4,    /* a CUDA call failed; the message holds the CUDA error string      */
+  NAT_BEM_ETIMEOUT = 5, /* a bounded wait gave up                                           */
+  NAT_BEM_EBUSY = 6     /* the resource is in use (serving)                                 */
+} nat_bem_status;
+
+typedef enum {
+  NAT_BEM_PREC_FP32 = 0,       /* FP32 operator and matvec, FP64 Gram-Schmidt / least squares */
+  NAT_BEM_PREC_MIXED_TF32 = 1, /* inner GMRES products in TF32, FP64-refined FP32 residual    */
+  NAT_BEM_PREC_MIXED_BF16 = 2  /* inner GMRES on a BF16 operator copy, FP64-refined residual   */
+} nat_bem_precision;
+
+typedef struct {
+  int32_t adj_subdiv_levels; /* vertex-sharing pairs: 7-point rule on 4^levels sub-triangles (2) */
+  int32_t self_theta_pts;    /* self pair: Gauss-Legendre points per edge in the angle (16)      */
+  double tol;                /* relative residual ||b - L p|| / ||b|| to stop at (1e-6)         */
+  int32_t max_iter;          /* GMRES iterations (plain) or total inner iterations (mixed) (200) */
+  nat_bem_precision prec;    /* arithmetic of the solve (NAT_BEM_PREC_FP32)                      */
+  int32_t inner_max_iter;    /* mixed: iterations per inner solve (60)                            */
+  double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-3)              */
+  int32_t max_refinements;   /* mixed: outer refinement sweeps (10)                               */
+} nat_bem_opts;
+
+typedef struct nat_bem_op nat_bem_op; /* opaque */
+
+typedef struct {
+  int32_t iterations;   /* GMRES iterations (mixed: summed over inner solves), max over RHS   */
+  int32_t refinements;  /* mixed: outer sweeps done; plain: 0                                   */
+  double rel_residual;  /* largest ||b - L p|| / ||b|| over the RHS (FP64 accumulation)        */
+} nat_bem_solve_info;
+
+/* Fills *opts with the defaults listed above. */
+NAT_BEM_API void nat_bem_opts_default(nat_bem_opts* opts);
+
+/*
+ * Assembles L and R (Sec. 4, Eq. 6; Sec. 4.1) for mesh (verts, tris) at wavenumber k.
+ *   verts: nv x 3 float64, row-major.  tris: nt x 3 int32 vertex indices, row-major.
+ *   k: wavenumber (> 0, finite).  opts: NULL for defaults.  *out: receives the new op.
+ * Work: geometry on the device, FP32 regular element pairs, FP64 self and vertex-sharing
+ * pairs. The op keeps L and R (8 nt^2 bytes each, complex64, leading dimension nt rounded up
+ * to 32) plus a BF16 copy of L for NAT_BEM_PREC_MIXED_BF16 (4 nt^2 bytes). Returns when the
+ * work is enqueued (the mesh checks run on the host before).
+ * NAT_BEM_EINVAL: nv or nt <= 0, an index out of range, a non-finite coordinate, a zero-area
+ * triangle, a mesh that is not closed with every edge used once in each direction, negative
+ * enclosed volume (inward winding), k <= 0 or not finite, opts out of range.
+ * NAT_BEM_ENOMEM: the device allocations failed.
+ */
+NAT_BEM_API nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                                double k, const nat_bem_opts* opts, void* cuda_stream,
+                                nat_bem_op** out);
+
+/*
+ * Solves L p = R g for nrhs right-hand sides (GMRES from p = 0, Sec. 6.1 settings by default).
+ *   neumann: nt x nrhs complex64, column-major.  p_out: same layout, receives p.
+ *   info: may be NULL.  Blocks until the solve is done.
+ * NAT_BEM_EINVAL: op NULL, nrhs < 1, NULL arrays.
+ * NAT_BEM_ENOCONV: the tolerance was not met within the iteration limit; p_out holds the
+ * best iterate and info is filled.
+ */
+NAT_BEM_API nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, int32_t nrhs, float* p_out,
+                             nat_bem_solve_info* info, void* cuda_stream);
+
+/*
+ * Field pressure at m points: field[q, s] = sum_j int_j [p_js dG/dn_y - g_js G](x_q, y) dS_y
+ * with the 7-point rule on every element (points should lie off the surface by at least an
+ * element size). pts: m x 3 float64.  p, neumann: nt x nrhs complex64 column-major.
+ * field_out: m x nrhs complex64 column-major. m = 0 is allowed and does nothing.
+ * Returns when the work is enqueued (device outputs) or copied back (host outputs).
+ * NAT_BEM_EINVAL: op NULL, m < 0, nrhs < 1, NULL arrays.
+ */
+NAT_BEM_API nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts, int64_t m, const float* p,
+                            const float* neumann, int32_t nrhs, float* field_out,
+                            void* cuda_stream);
+
+/*
+ * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
+ * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
+ * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.
+ */
+NAT_BEM_API nat_bem_status nat_bem_op_rows(const nat_bem_op* op, int32_t which, int64_t row0, int64_t nrows,
+                               float* out, void* cuda_stream);
+
+/* Number of triangles of the op (0 for NULL). */
+NAT_BEM_API int64_t nat_bem_op_size(const nat_bem_op* op);
+
+/* Device bytes an op of nt triangles with nrhs right-hand sides holds under opts (NULL =
+ * defaults): the operators plus the solver workspace. Used for admission control. */
+NAT_BEM_API int64_t nat_bem_required_bytes(int64_t nt, int32_t nrhs, const nat_bem_opts* opts);
+
+/* Frees the op and its device memory (stream-ordered on the stream it was built on). NULL ok. */
+NAT_BEM_API void nat_bem_destroy(nat_bem_op* op);
+
+/*
+ * Tracing for benchmarks and profiling (no counterpart in the paper). Every kernel launch of
+ * the library is counted. With tracing enabled, each launch is also bracketed by two CUDA
+ * events recorded on its stream; nat_bem_trace_kernel waits for the recorded events and
+ * returns the summed device time and the number of launches of the kernels whose name contains
+ * `name` ("" = all). Names: "assemble_regular", "assemble_near", "geometry", "gemv",
+ * "gmres_dots", "gmres_update_dots", "gmres_update_norm", "gmres_normalize", "eval", ...
+ * The counters are process-wide and not thread-safe against concurrent resets.
+ */
+NAT_BEM_API void nat_bem_trace_enable(int32_t enable);
+NAT_BEM_API void nat_bem_trace_reset(void);
+NAT_BEM_API int64_t nat_bem_trace_launches(void);
+NAT_BEM_API nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms,
+                                                int64_t* launches);
+
+/* Message of the last failed call on this thread ("" if none). */
+NAT_BEM_API const char* nat_bem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NAT_BEM_H */

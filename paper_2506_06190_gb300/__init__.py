@@ -1,0 +1,289 @@
+"""Python binding of libnatbem.so, the GB300 Burton-Miller BEM library (include/nat_bem.h).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels. The
+functions keep the C names (nat_bem_assemble, nat_bem_solve, nat_bem_eval, ...). Arrays may be
+numpy arrays (host memory) or torch tensors (host or CUDA); CUDA tensors are passed by device
+pointer together with torch's current stream, so no copy is made.
+
+Layouts: vertices float64 (nv, 3); triangles int32 (nt, 3); complex data complex64 with one
+right-hand side per column of an (nt, nrhs) Fortran-ordered numpy array, or one per row of a
+(nrhs, nt) C-contiguous torch tensor (the same bytes); points float64 (m, 3).
+
+The library must have been built (python -m paper_2506_06190_gb300.build); there is no CPU
+fallback, and importing functions that need it raises if libnatbem.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnatbem.so")
+
+NAT_BEM_OK, NAT_BEM_EINVAL, NAT_BEM_ENOMEM, NAT_BEM_ENOCONV = 0, 1, 2, 3
+NAT_BEM_ECUDA, NAT_BEM_ETIMEOUT, NAT_BEM_EBUSY = 4, 5, 6
+PREC_FP32, PREC_MIXED_TF32, PREC_MIXED_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ECUDA", 5: "ETIMEOUT", 6: "EBUSY"}
+
+# every symbol include/nat_bem.h declares
+EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_solve", "nat_bem_eval",
+            "nat_bem_op_rows", "nat_bem_op_size", "nat_bem_required_bytes", "nat_bem_destroy",
+            "nat_bem_last_error", "nat_bem_trace_enable", "nat_bem_trace_reset",
+            "nat_bem_trace_launches", "nat_bem_trace_kernel"]
+
+
+class NatBemError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("adj_subdiv_levels", ctypes.c_int32), ("self_theta_pts", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("inner_max_iter", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("max_refinements", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libnatbem.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -m paper_2506_06190_gb300.build` (needs nvcc)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+        L.nat_bem_opts_default.argtypes = [ctypes.POINTER(Opts)]
+        L.nat_bem_opts_default.restype = None
+        L.nat_bem_assemble.argtypes = [vp, i64, vp, i64, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+        L.nat_bem_assemble.restype = ctypes.c_int
+        L.nat_bem_solve.argtypes = [vp, vp, i32, vp, ctypes.POINTER(SolveInfo), vp]
+        L.nat_bem_solve.restype = ctypes.c_int
+        L.nat_bem_eval.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
+        L.nat_bem_eval.restype = ctypes.c_int
+        L.nat_bem_op_rows.argtypes = [vp, i32, i64, i64, vp, vp]
+        L.nat_bem_op_rows.restype = ctypes.c_int
+        L.nat_bem_op_size.argtypes = [vp]
+        L.nat_bem_op_size.restype = i64
+        L.nat_bem_required_bytes.argtypes = [i64, i32, ctypes.POINTER(Opts)]
+        L.nat_bem_required_bytes.restype = i64
+        L.nat_bem_destroy.argtypes = [vp]
+        L.nat_bem_destroy.restype = None
+        L.nat_bem_last_error.argtypes = []
+        L.nat_bem_last_error.restype = ctypes.c_char_p
+        L.nat_bem_trace_enable.argtypes = [i32]
+        L.nat_bem_trace_enable.restype = None
+        L.nat_bem_trace_reset.argtypes = []
+        L.nat_bem_trace_reset.restype = None
+        L.nat_bem_trace_launches.argtypes = []
+        L.nat_bem_trace_launches.restype = i64
+        L.nat_bem_trace_kernel.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(i64)]
+        L.nat_bem_trace_kernel.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != NAT_BEM_OK:
+        raise NatBemError(status, lib().nat_bem_last_error().decode())
+
+
+def nat_bem_opts_default(**overrides) -> Opts:
+    o = Opts()
+    lib().nat_bem_opts_default(ctypes.byref(o))
+    for k, v in overrides.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ------------------------------------------------------------------ array marshalling
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _stream_of(x, stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    if _is_torch(x) and x.is_cuda:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def _ptr(x, dtype, shape_check=None):
+    """(pointer, keep-alive) for a numpy array or torch tensor of the given dtype."""
+    if _is_torch(x):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32, np.complex64: torch.complex64}[dtype]
+        if x.dtype != want or not x.is_contiguous():
+            raise TypeError(f"expected a contiguous torch tensor of {want}")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.asarray(x)
+    if dtype is np.complex64:
+        a = np.asfortranarray(a.astype(np.complex64, copy=False))
+    else:
+        a = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _nrhs_of(x, n):
+    shape = tuple(x.shape)
+    if _is_torch(x):
+        if len(shape) == 1:
+            return 1
+        if shape[1] != n:
+            raise ValueError(f"torch complex data must be (nrhs, {n})")
+        return shape[0]
+    if len(shape) == 1:
+        return 1
+    if shape[0] != n:
+        raise ValueError(f"numpy complex data must be ({n}, nrhs)")
+    return shape[1]
+
+
+# ------------------------------------------------------------------------ operations
+def nat_bem_assemble(V, F, k: float, opts: Opts | None = None, stream=None) -> ctypes.c_void_p:
+    """Assemble L and R on the device; returns the opaque op handle."""
+    pv, kv = _ptr(V, np.float64)
+    pt, kt = _ptr(F, np.int32)
+    nv, nt = int(V.shape[0]), int(F.shape[0])
+    op = ctypes.c_void_p()
+    st = lib().nat_bem_assemble(pv, nv, pt, nt, float(k), ctypes.byref(opts) if opts else None,
+                                _stream_of(V, stream), ctypes.byref(op))
+    del kv, kt
+    _check(st)
+    return op
+
+
+def nat_bem_solve(op, neumann, out=None, stream=None, check=True):
+    """Solve L p = R g. Returns (p, SolveInfo, status)."""
+    n = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(neumann, n)
+    pg, kg = _ptr(neumann, np.complex64)
+    if out is None:
+        if _is_torch(neumann):
+            import torch
+            out = torch.empty(tuple(neumann.shape), dtype=torch.complex64, device=neumann.device)
+        else:
+            out = np.zeros((n, nrhs) if np.ndim(neumann) == 2 else (n,), dtype=np.complex64, order="F")
+    po, ko = _ptr(out, np.complex64)
+    info = SolveInfo()
+    st = lib().nat_bem_solve(op, pg, nrhs, po, ctypes.byref(info), _stream_of(neumann, stream))
+    if check and st not in (NAT_BEM_OK, NAT_BEM_ENOCONV):
+        _check(st)
+    if not _is_torch(out) and ko is not out:
+        out[...] = ko
+    return out, info, st
+
+
+def nat_bem_eval(op, points, p, neumann, out=None, stream=None):
+    """Field at points (m, 3) for the surface data p and neumann."""
+    n = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(p, n)
+    m = int(points.shape[0])
+    pp, kp = _ptr(points, np.float64)
+    pd, kd = _ptr(p, np.complex64)
+    pg, kg = _ptr(neumann, np.complex64)
+    if out is None:
+        if _is_torch(p):
+            import torch
+            out = torch.empty((nrhs, m) if p.dim() == 2 else (m,), dtype=torch.complex64, device=p.device)
+        else:
+            out = np.zeros((m, nrhs) if np.ndim(p) == 2 else (m,), dtype=np.complex64, order="F")
+    po, ko = _ptr(out, np.complex64)
+    _check(lib().nat_bem_eval(op, pp, m, pd, pg, nrhs, po, _stream_of(p, stream)))
+    if not _is_torch(out) and ko is not out:
+        out[...] = ko
+    return out
+
+
+def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:
+    n = int(lib().nat_bem_op_size(op))
+    out = np.zeros((nrows, n), dtype=np.complex64)
+    _check(lib().nat_bem_op_rows(op, int(which), int(row0), int(nrows),
+                                 ctypes.c_void_p(out.ctypes.data), _stream_of(None, stream)))
+    return out
+
+
+def nat_bem_required_bytes(nt: int, nrhs: int, opts: Opts | None = None) -> int:
+    return int(lib().nat_bem_required_bytes(int(nt), int(nrhs), ctypes.byref(opts) if opts else None))
+
+
+def nat_bem_destroy(op):
+    if op:
+        lib().nat_bem_destroy(op)
+
+
+def nat_bem_last_error() -> str:
+    return lib().nat_bem_last_error().decode()
+
+
+def nat_bem_trace_enable(enable: bool = True):
+    lib().nat_bem_trace_enable(1 if enable else 0)
+
+
+def nat_bem_trace_reset():
+    lib().nat_bem_trace_reset()
+
+
+def nat_bem_trace_launches() -> int:
+    return int(lib().nat_bem_trace_launches())
+
+
+def nat_bem_trace_kernel(name: str = ""):
+    """(total device ms, launches) of the traced kernels whose name contains `name`."""
+    t, c = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(lib().nat_bem_trace_kernel(name.encode(), ctypes.byref(t), ctypes.byref(c)))
+    return t.value, c.value
+
+
+@dataclass
+class Operator:
+    """Owning wrapper of a nat_bem_op handle."""
+    handle: ctypes.c_void_p
+    n: int
+    k: float
+
+    @classmethod
+    def assemble(cls, V, F, k, opts=None, stream=None):
+        return cls(nat_bem_assemble(V, F, k, opts, stream), int(F.shape[0]), float(k))
+
+    def solve(self, neumann, out=None, stream=None, check=True):
+        return nat_bem_solve(self.handle, neumann, out, stream, check)
+
+    def evaluate(self, points, p, neumann, out=None, stream=None):
+        return nat_bem_eval(self.handle, points, p, neumann, out, stream)
+
+    def rows(self, which, row0, nrows):
+        return nat_bem_op_rows(self.handle, which, row0, nrows)
+
+    def close(self):
+        if self.handle:
+            nat_bem_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,387 @@
+// C ABI entry points (include/nat_bem.h): argument checks, host/device staging, memory pool,
+// and the order of the device stages. No function lets a C++ exception or abort cross the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace natbem {
+
+namespace {
+thread_local std::string g_last_error;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64] = {};
+bool g_rules_ready[64] = {};
+int g_rules_levels[64] = {};
+int g_rules_self[64] = {};
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+
+static cudaMemPool_t pool_for_current_device() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = p;
+  }
+  return g_pools[dev];
+}
+
+nat_bem_status dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaMemPool_t pool = pool_for_current_device();
+  if (!pool) {
+    set_error("could not create the device memory pool");
+    return NAT_BEM_ECUDA;
+  }
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " +
+              cudaGetErrorString(e));
+    *p = nullptr;
+    return NAT_BEM_ENOMEM;
+  }
+  return NAT_BEM_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static nat_bem_status ensure_rules(int levels, int self_pts) {
+  int dev = 0;
+  NB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return NAT_BEM_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_rules_ready[dev] && g_rules_levels[dev] == levels && g_rules_self[dev] == self_pts)
+    return NAT_BEM_OK;
+  NB_TRY(upload_rules(levels, self_pts));
+  g_rules_ready[dev] = true;
+  g_rules_levels[dev] = levels;
+  g_rules_self[dev] = self_pts;
+  return NAT_BEM_OK;
+}
+
+static nat_bem_status check_opts(const nat_bem_opts& o) {
+  if (o.adj_subdiv_levels < 0 || o.adj_subdiv_levels > 3) {
+    set_error("opts.adj_subdiv_levels must be in [0, 3]");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.self_theta_pts < 1 || o.self_theta_pts > 64) {
+    set_error("opts.self_theta_pts must be in [1, 64]");
+    return NAT_BEM_EINVAL;
+  }
+  if (!(o.tol > 0.0) || !std::isfinite(o.tol)) {
+    set_error("opts.tol must be positive and finite");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.max_iter < 1 || o.max_iter > 255) {
+    set_error("opts.max_iter must be in [1, 255]");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.prec != NAT_BEM_PREC_FP32 && o.prec != NAT_BEM_PREC_MIXED_TF32 &&
+      o.prec != NAT_BEM_PREC_MIXED_BF16) {
+    set_error("opts.prec is not a nat_bem_precision value");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.inner_max_iter < 1 || o.inner_max_iter > 255 || !(o.inner_tol > 0.0) ||
+      o.max_refinements < 1) {
+    set_error("opts: inner_max_iter in [1, 255], inner_tol > 0, max_refinements >= 1");
+    return NAT_BEM_EINVAL;
+  }
+  return NAT_BEM_OK;
+}
+
+// A device copy of `count` elements of p (which may be a host pointer). Sets *tmp when it
+// allocated one; the caller frees it on the same stream.
+template <class T>
+static nat_bem_status to_device(const T* p, size_t count, cudaStream_t s, const T** dp, T** tmp) {
+  *tmp = nullptr;
+  if (is_device_pointer(p)) {
+    *dp = p;
+    return NAT_BEM_OK;
+  }
+  NB_TRY(dev_alloc_n(tmp, count, s));
+  NB_TRY_CUDA(cudaMemcpyAsync(*tmp, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  *dp = *tmp;
+  return NAT_BEM_OK;
+}
+
+}  // namespace natbem
+
+using namespace natbem;
+
+extern "C" {
+
+void nat_bem_opts_default(nat_bem_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->adj_subdiv_levels = 2;
+  o->self_theta_pts = 16;
+  o->tol = 1e-6;
+  o->max_iter = 200;
+  o->prec = NAT_BEM_PREC_FP32;
+  o->inner_max_iter = 60;
+  o->inner_tol = 1e-3;
+  o->max_refinements = 10;
+}
+
+const char* nat_bem_last_error(void) { return g_last_error.c_str(); }
+
+int64_t nat_bem_op_size(const nat_bem_op* op) { return op ? op->n : 0; }
+
+int64_t nat_bem_required_bytes(int64_t nt, int32_t nrhs, const nat_bem_opts* opts) {
+  nat_bem_opts o;
+  nat_bem_opts_default(&o);
+  if (opts) o = *opts;
+  if (nt <= 0 || nrhs < 1) return 0;
+  const int64_t ld = round_up(nt, 32);
+  int64_t b = 2 * 8 * nt * ld;                                     // L and R
+  if (o.prec == NAT_BEM_PREC_MIXED_BF16) b += 4 * nt * ld;         // BF16 copy of L
+  b += nt * (7 * 16 + 5 * 16 + 9 * 8 + 7 * 8 + 8 * 14);             // geometry + near pairs
+  b += workspace_bytes(nt, nrhs, o);
+  return b;
+}
+
+nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                                double k, const nat_bem_opts* opts, void* cuda_stream,
+                                nat_bem_op** out) {
+  try {
+    clear_error();
+    if (!out) {
+      set_error("out is NULL");
+      return NAT_BEM_EINVAL;
+    }
+    *out = nullptr;
+    if (!verts || !tris) {
+      set_error("verts and tris must not be NULL");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) {
+      set_error("k must be positive and finite");
+      return NAT_BEM_EINVAL;
+    }
+    if (nv <= 0 || nt <= 0) {
+      set_error("mesh: need nv > 0 and nt > 0");
+      return NAT_BEM_EINVAL;
+    }
+    nat_bem_opts o;
+    nat_bem_opts_default(&o);
+    if (opts) o = *opts;
+    NB_TRY(check_opts(o));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // host copies for the mesh checks and the near-pair list
+    const bool vdev = is_device_pointer(verts), tdev = is_device_pointer(tris);
+    std::vector<double> hV;
+    std::vector<int32_t> hT;
+    const double* V = verts;
+    const int32_t* T = tris;
+    if (vdev) {
+      hV.resize(3 * nv);
+      NB_TRY_CUDA(cudaMemcpyAsync(hV.data(), verts, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaStreamSynchronize(s));
+      V = hV.data();
+    }
+    if (tdev) {
+      hT.resize(3 * nt);
+      NB_TRY_CUDA(cudaMemcpyAsync(hT.data(), tris, 3 * nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaStreamSynchronize(s));
+      T = hT.data();
+    }
+    NB_TRY(validate_mesh_host(V, nv, T, nt));
+    std::vector<int2> near;
+    build_near_pairs(T, nv, nt, near);
+    NB_TRY(ensure_rules(o.adj_subdiv_levels, o.self_theta_pts));
+
+    nat_bem_op* op = new (std::nothrow) nat_bem_op();
+    if (!op) {
+      set_error("host allocation failed");
+      return NAT_BEM_ENOMEM;
+    }
+    op->n = nt;
+    op->k = k;
+    op->opts = o;
+    op->stream = s;
+    cudaGetDevice(&op->device);
+    op->geo.n = nt;
+    op->geo.ld = round_up(nt, 32);
+    auto fail = [&](nat_bem_status st) {
+      nat_bem_destroy(op);
+      return st;
+    };
+    const double* dV = nullptr;
+    const int32_t* dT = nullptr;
+    double* tV = nullptr;
+    int32_t* tT = nullptr;
+    nat_bem_status st = to_device(verts, (size_t)(3 * nv), s, &dV, &tV);
+    if (st != NAT_BEM_OK) return fail(st);
+    st = to_device(tris, (size_t)(3 * nt), s, &dT, &tT);
+    if (st != NAT_BEM_OK) return fail(st);
+    st = geometry_build(op, dV, dT, nv, near, s);
+    dev_free(tV, s);
+    dev_free(tT, s);
+    if (st != NAT_BEM_OK) return fail(st);
+    const size_t mat = (size_t)nt * (size_t)op->geo.ld;
+    if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
+    if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
+    if ((st = assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
+    *out = op;
+    return NAT_BEM_OK;
+  } catch (...) {
+    set_error("internal error in nat_bem_assemble");
+    return NAT_BEM_ECUDA;
+  }
+}
+
+nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, int32_t nrhs, float* p_out,
+                             nat_bem_solve_info* info, void* cuda_stream) {
+  try {
+    clear_error();
+    if (!op || !neumann || !p_out || nrhs < 1) {
+      set_error("nat_bem_solve: op, neumann and p_out must be non-NULL and nrhs >= 1");
+      return NAT_BEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t cnt = (size_t)op->n * nrhs;
+    const float2* dg = nullptr;
+    float2* tg = nullptr;
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    const bool pdev = is_device_pointer(p_out);
+    float2* dp = reinterpret_cast<float2*>(p_out);
+    float2* tp = nullptr;
+    if (!pdev) {
+      NB_TRY(dev_alloc_n(&tp, cnt, s));
+      dp = tp;
+    }
+    nat_bem_status st = solve_impl(op, dg, nrhs, dp, info, s);
+    if ((st == NAT_BEM_OK || st == NAT_BEM_ENOCONV) && !pdev) {
+      cudaError_t e = cudaMemcpyAsync(p_out, tp, cnt * sizeof(float2), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copy of p to the host failed: ") + cudaGetErrorString(e));
+        st = NAT_BEM_ECUDA;
+      }
+    }
+    dev_free(tg, s);
+    dev_free(tp, s);
+    return st;
+  } catch (...) {
+    set_error("internal error in nat_bem_solve");
+    return NAT_BEM_ECUDA;
+  }
+}
+
+nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts, int64_t m, const float* p,
+                            const float* neumann, int32_t nrhs, float* field_out,
+                            void* cuda_stream) {
+  try {
+    clear_error();
+    if (!op || m < 0 || nrhs < 1 || (m > 0 && (!pts || !p || !neumann || !field_out))) {
+      set_error("nat_bem_eval: bad arguments (op NULL, m < 0, nrhs < 1 or NULL arrays)");
+      return NAT_BEM_EINVAL;
+    }
+    if (m == 0) return NAT_BEM_OK;
+    if (m > ((int64_t)1 << 31) - 1) {
+      set_error("nat_bem_eval: too many points");
+      return NAT_BEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t cnt = (size_t)op->n * nrhs;
+    const double* dpts = nullptr;
+    double* tpts = nullptr;
+    const float2 *dp = nullptr, *dg = nullptr;
+    float2 *tp = nullptr, *tg = nullptr;
+    NB_TRY(to_device(pts, (size_t)(3 * m), s, &dpts, &tpts));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    const bool odev = is_device_pointer(field_out);
+    float2* dout = reinterpret_cast<float2*>(field_out);
+    float2* tout = nullptr;
+    if (!odev) {
+      NB_TRY(dev_alloc_n(&tout, (size_t)m * nrhs, s));
+      dout = tout;
+    }
+    nat_bem_status st = eval_impl(op, dpts, m, dp, dg, nrhs, dout, s);
+    if (st == NAT_BEM_OK && !odev) {
+      cudaError_t e = cudaMemcpyAsync(field_out, tout, (size_t)m * nrhs * sizeof(float2),
+                                      cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copy of the field to the host failed: ") + cudaGetErrorString(e));
+        st = NAT_BEM_ECUDA;
+      }
+    }
+    dev_free(tpts, s);
+    dev_free(tp, s);
+    dev_free(tg, s);
+    dev_free(tout, s);
+    return st;
+  } catch (...) {
+    set_error("internal error in nat_bem_eval");
+    return NAT_BEM_ECUDA;
+  }
+}
+
+nat_bem_status nat_bem_op_rows(const nat_bem_op* op, int32_t which, int64_t row0, int64_t nrows,
+                               float* out, void* cuda_stream) {
+  clear_error();
+  if (!op || !out || which < 0 || which > 1 || row0 < 0 || nrows < 0 || row0 + nrows > op->n) {
+    set_error("nat_bem_op_rows: bad arguments");
+    return NAT_BEM_EINVAL;
+  }
+  const float2* M = which == 0 ? op->L : op->R;
+  if (!M) {
+    set_error("nat_bem_op_rows: matrix not stored");
+    return NAT_BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int64_t n = op->n, ld = op->geo.ld;
+  NB_TRY_CUDA(cudaMemcpy2DAsync(out, n * sizeof(float2), M + row0 * ld, ld * sizeof(float2),
+                                n * sizeof(float2), nrows, cudaMemcpyDefault, s));
+  NB_TRY_CUDA(cudaStreamSynchronize(s));
+  return NAT_BEM_OK;
+}
+
+void nat_bem_destroy(nat_bem_op* op) {
+  if (!op) return;
+  cudaStream_t s = op->stream;
+  Geometry& g = op->geo;
+  void* ptrs[] = {g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, g.tri, g.cen, g.nrm64, g.area,
+                  g.near_pairs, op->L, op->R, op->Lb};
+  for (void* p : ptrs) dev_free(p, s);
+  workspace_free(op->ws, s);
+  delete op;
+}
+
+}  // extern "C"

@@ -1,0 +1,471 @@
+// Assembly of the Burton-Miller collocation operators L and R (paper Sec. 4, Eq. 6; the two
+// combined matrices are built directly in one pass, Sec. 4.1).
+//
+//   L_ij = 1/2 d_ij - int_j [dG/dn_y + beta d2G/dn_x dn_y] dS_y
+//   R_ij = -int_j [G + beta dG/dn_x] dS_y - (beta/2) d_ij,     G = e^{ikr}/(4 pi r), beta = i/k
+//
+// Three kernels:
+//   k_geometry          per element: centroid (as a float hi/lo pair), normal, area, the 7
+//                       quadrature points as offsets from the centroid with their weights, and
+//                       the FP64 copies used by the near-pair kernel.
+//   k_assemble_regular  every pair (i, j) that shares no vertex, in FP32: one thread per source
+//                       column j holding that element's rule in registers, collocation rows
+//                       staged through shared memory and read as broadcasts, coalesced row
+//                       stores of L and R. Pairs that share a vertex are skipped.
+//   k_assemble_near     the self pair and vertex-sharing pairs in FP64, one warp per pair with
+//                       the lanes over quadrature points and a shuffle reduction.
+//
+// With d = x - y, r = |d|, rho = k r, q = (d.n_x)(d.n_y)/r^2 the integrands reduce to
+//   dG/dn_y + beta H = G/r^2 [ (d.n_y - b/k) + i (a/k - rho d.n_y) ],
+//       a = (rho^2 - 3) q + n_x.n_y,   b = rho (3 q - n_x.n_y),
+//   G + beta dG/dn_x = G [ 1 - d.n_x / r - i d.n_x / (k r^2) ].
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace natbem {
+
+// ------------------------------------------------------------------------ rule tables
+// 7-point degree-5 triangle rule (Radon 1948): centroid weight 9/40, then the orbits of
+// (a, a, 1-2a) with a = (6 -+ sqrt 15)/21 and weights (155 -+ sqrt 15)/1200.
+__constant__ double c_rule7[7][4];          // barycentric l0, l1, l2 and weight (sum 1)
+constexpr int kMaxAdjPts = 7 * 64;          // 4^3 sub-triangles
+constexpr int kMaxSelfPts = 64;
+__device__ double4 g_adj_rule[kMaxAdjPts];  // parent barycentrics and weight (sum 1)
+__device__ double2 g_gl[kMaxSelfPts];       // Gauss-Legendre nodes / weights on [-1, 1]
+__constant__ int c_adj_npts;
+__constant__ int c_self_pts;
+
+namespace {
+
+void rule7_host(double out[7][4]) {
+  const double s = std::sqrt(15.0);
+  const double a = (6.0 - s) / 21.0, wa = (155.0 - s) / 1200.0;
+  const double b = (6.0 + s) / 21.0, wb = (155.0 + s) / 1200.0;
+  const double t[7][4] = {{1.0 / 3, 1.0 / 3, 1.0 / 3, 9.0 / 40},
+                          {a, a, 1 - 2 * a, wa},
+                          {a, 1 - 2 * a, a, wa},
+                          {1 - 2 * a, a, a, wa},
+                          {b, b, 1 - 2 * b, wb},
+                          {b, 1 - 2 * b, b, wb},
+                          {1 - 2 * b, b, b, wb}};
+  for (int i = 0; i < 7; ++i)
+    for (int c = 0; c < 4; ++c) out[i][c] = t[i][c];
+}
+
+// The 4^levels congruent sub-triangles of the reference triangle, as barycentric corners.
+void split(const double tri[3][3], int levels, std::vector<std::array<double, 9>>& out) {
+  if (levels == 0) {
+    std::array<double, 9> t;
+    for (int v = 0; v < 3; ++v)
+      for (int c = 0; c < 3; ++c) t[3 * v + c] = tri[v][c];
+    out.push_back(t);
+    return;
+  }
+  double m[3][3];  // midpoints of edges (0,1), (1,2), (2,0)
+  for (int c = 0; c < 3; ++c) {
+    m[0][c] = 0.5 * (tri[0][c] + tri[1][c]);
+    m[1][c] = 0.5 * (tri[1][c] + tri[2][c]);
+    m[2][c] = 0.5 * (tri[2][c] + tri[0][c]);
+  }
+  const double* corner[4][3] = {{tri[0], m[0], m[2]}, {m[0], tri[1], m[1]},
+                                {m[2], m[1], tri[2]}, {m[0], m[1], m[2]}};
+  for (int s = 0; s < 4; ++s) {
+    double sub[3][3];
+    for (int v = 0; v < 3; ++v)
+      for (int c = 0; c < 3; ++c) sub[v][c] = corner[s][v][c];
+    split(sub, levels - 1, out);
+  }
+}
+
+void gauss_legendre_host(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(pi * (i + 0.75) / (n + 0.5)), d = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int m = 2; m <= n; ++m) {
+        double p2 = ((2 * m - 1) * z * p1 - (m - 1) * p0) / m;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) p0 = 1.0;
+      d = n * (z * p1 - p0) / (z * z - 1.0);
+      double step = p1 / d;
+      z -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * d * d);
+  }
+}
+
+}  // namespace
+
+nat_bem_status upload_rules(int adj_levels, int self_pts) {
+  double r7[7][4];
+  rule7_host(r7);
+  NB_TRY_CUDA(cudaMemcpyToSymbol(c_rule7, r7, sizeof(r7)));
+  // vertex-sharing pairs: the 7-point rule on each of the 4^levels sub-triangles
+  const double ref[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  std::vector<std::array<double, 9>> subs;
+  split(ref, adj_levels, subs);
+  std::vector<double4> pts;
+  const double wsub = 1.0 / (double)subs.size();
+  for (const auto& t : subs)
+    for (int q = 0; q < 7; ++q) {
+      double l[3];
+      for (int c = 0; c < 3; ++c) l[c] = r7[q][0] * t[c] + r7[q][1] * t[3 + c] + r7[q][2] * t[6 + c];
+      pts.push_back(make_double4(l[0], l[1], l[2], r7[q][3] * wsub));
+    }
+  int np = (int)pts.size();
+  NB_TRY_CUDA(cudaMemcpyToSymbol(g_adj_rule, pts.data(), np * sizeof(double4)));
+  NB_TRY_CUDA(cudaMemcpyToSymbol(c_adj_npts, &np, sizeof(int)));
+  std::vector<double> gx, gw;
+  gauss_legendre_host(self_pts, gx, gw);
+  std::vector<double2> gl(self_pts);
+  for (int i = 0; i < self_pts; ++i) gl[i] = make_double2(gx[i], gw[i]);
+  NB_TRY_CUDA(cudaMemcpyToSymbol(g_gl, gl.data(), self_pts * sizeof(double2)));
+  NB_TRY_CUDA(cudaMemcpyToSymbol(c_self_pts, &self_pts, sizeof(int)));
+  return NAT_BEM_OK;
+}
+
+// ------------------------------------------------------------------------- geometry
+__global__ void k_geometry(const double* __restrict__ V, const int32_t* __restrict__ T, int n,
+                           float4* c_hi, float4* c_lo, float4* nrm, float4* qp, int4* vid,
+                           double* tri, double* cen, double* nrm64, double* area) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int ia = T[3 * t], ib = T[3 * t + 1], ic = T[3 * t + 2];
+  double a[3], b[3], c[3];
+  for (int d = 0; d < 3; ++d) {
+    a[d] = V[3 * ia + d];
+    b[d] = V[3 * ib + d];
+    c[d] = V[3 * ic + d];
+  }
+  double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+  double cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                  e1[0] * e2[1] - e1[1] * e2[0]};
+  double len = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+  double A = 0.5 * len;
+  double nn[3] = {cr[0] / len, cr[1] / len, cr[2] / len};
+  double cc[3];
+  for (int d = 0; d < 3; ++d) cc[d] = (a[d] + b[d] + c[d]) / 3.0;
+  float hi[3], lo[3];
+  for (int d = 0; d < 3; ++d) {
+    hi[d] = (float)cc[d];
+    lo[d] = (float)(cc[d] - (double)hi[d]);
+  }
+  c_hi[t] = make_float4(hi[0], hi[1], hi[2], (float)A);
+  c_lo[t] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  nrm[t] = make_float4((float)nn[0], (float)nn[1], (float)nn[2], 0.f);
+  vid[t] = make_int4(ia, ib, ic, 0);
+  const double inv4pi = 0.25 / 3.14159265358979323846;
+  for (int q = 0; q < 7; ++q) {
+    double y[3];
+    for (int d = 0; d < 3; ++d)
+      y[d] = c_rule7[q][0] * a[d] + c_rule7[q][1] * b[d] + c_rule7[q][2] * c[d] - cc[d];
+    qp[7 * t + q] = make_float4((float)y[0], (float)y[1], (float)y[2],
+                                (float)(c_rule7[q][3] * A * inv4pi));
+  }
+  for (int d = 0; d < 3; ++d) {
+    tri[9 * t + d] = a[d];
+    tri[9 * t + 3 + d] = b[d];
+    tri[9 * t + 6 + d] = c[d];
+    cen[3 * t + d] = cc[d];
+    nrm64[3 * t + d] = nn[d];
+  }
+  area[t] = A;
+}
+
+// -------------------------------------------------------------- regular pairs (FP32)
+namespace {
+
+// 2 pi split for Cody-Waite reduction (Cody & Waite 1980): hi = 2 pi rounded to float,
+// lo = float(2 pi - hi); rho - n hi - n lo with n = rint(rho / 2 pi) keeps |t| <= pi.
+constexpr float kTwoPiHi = 6.28318548202514648f;
+constexpr float kTwoPiLo = -1.7484555314695172e-7f;
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+__device__ __forceinline__ bool shares_vertex(int4 a, int4 b) {
+  return a.x == b.x || a.x == b.y || a.x == b.z || a.y == b.x || a.y == b.y || a.y == b.z ||
+         a.z == b.x || a.z == b.y || a.z == b.z;
+}
+
+constexpr int kRegThreads = 256;  // source columns per block
+constexpr int kRowStage = 64;     // collocation rows staged in shared memory at a time
+
+}  // namespace
+
+__global__ void __launch_bounds__(kRegThreads)
+k_assemble_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
+                   const float4* __restrict__ nrm, const float4* __restrict__ qp,
+                   const int4* __restrict__ vid, int n, int ld, int rows_per_block, float k,
+                   float2* __restrict__ L, float2* __restrict__ R) {
+  __shared__ float4 s_hi[kRowStage], s_lo[kRowStage], s_n[kRowStage];
+  __shared__ int4 s_v[kRowStage];
+  const int j = blockIdx.x * kRegThreads + threadIdx.x;
+  const bool col_ok = j < n, col_pad = j >= n && j < ld;
+  // the source element's rule stays in registers for the whole row range
+  float3 chi = make_float3(0.f, 0.f, 0.f), clo = chi, nj = chi;
+  float4 q[7];
+  int4 vj = make_int4(-1, -1, -1, 0);
+  if (col_ok) {
+    float4 t = c_hi[j];
+    chi = make_float3(t.x, t.y, t.z);
+    t = c_lo[j];
+    clo = make_float3(t.x, t.y, t.z);
+    t = nrm[j];
+    nj = make_float3(t.x, t.y, t.z);
+#pragma unroll
+    for (int p = 0; p < 7; ++p) q[p] = qp[7 * j + p];
+    vj = vid[j];
+  } else {
+#pragma unroll
+    for (int p = 0; p < 7; ++p) q[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float kinv = 1.0f / k;
+  const int i_begin = blockIdx.y * rows_per_block;
+  const int i_end = min(n, i_begin + rows_per_block);
+  for (int ib = i_begin; ib < i_end; ib += kRowStage) {
+    const int cnt = min(kRowStage, i_end - ib);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      int i = ib + threadIdx.x;
+      s_hi[threadIdx.x] = c_hi[i];
+      s_lo[threadIdx.x] = c_lo[i];
+      s_n[threadIdx.x] = nrm[i];
+      s_v[threadIdx.x] = vid[i];
+    }
+    __syncthreads();
+    for (int t = 0; t < cnt; ++t) {
+      const int i = ib + t;
+      const size_t off = (size_t)i * ld + j;
+      if (col_pad) {
+        L[off] = make_float2(0.f, 0.f);
+        R[off] = make_float2(0.f, 0.f);
+        continue;
+      }
+      if (!col_ok) continue;
+      const int4 vi = s_v[t];
+      if (shares_vertex(vi, vj)) continue;  // self and vertex-sharing pairs: FP64 kernel
+      const float4 xh = s_hi[t], xl = s_lo[t], ni4 = s_n[t];
+      // centroid difference from the hi/lo pairs: exact-ish even for close elements
+      const float Dx = (xh.x - chi.x) + (xl.x - clo.x);
+      const float Dy = (xh.y - chi.y) + (xl.y - clo.y);
+      const float Dz = (xh.z - chi.z) + (xl.z - clo.z);
+      const float dny = Dx * nj.x + Dy * nj.y + Dz * nj.z;  // quadrature offsets lie in the plane
+      const float Dni = Dx * ni4.x + Dy * ni4.y + Dz * ni4.z;
+      const float nxny = ni4.x * nj.x + ni4.y * nj.y + ni4.z * nj.z;
+      float Lr = 0.f, Li = 0.f, Rr = 0.f, Ri = 0.f;
+#pragma unroll
+      for (int p = 0; p < 7; ++p) {
+        const float dx = Dx - q[p].x, dy = Dy - q[p].y, dz = Dz - q[p].z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float dnx = Dni - fmaf(q[p].x, ni4.x, fmaf(q[p].y, ni4.y, q[p].z * ni4.z));
+        const float rho = k * r;
+        const float nq = rintf(rho * kInvTwoPi);
+        float th = fmaf(-nq, kTwoPiHi, rho);
+        th = fmaf(-nq, kTwoPiLo, th);
+        float sn, cs;
+        __sincosf(th, &sn, &cs);
+        const float gw = rinv * q[p].w;  // w A / (4 pi r)
+        const float Gr = cs * gw, Gi = sn * gw;
+        const float rinv2 = rinv * rinv;
+        const float qq = dnx * dny * rinv2;
+        const float a = fmaf(fmaf(rho, rho, -3.0f), qq, nxny);
+        const float b = rho * fmaf(3.0f, qq, -nxny);
+        const float lr = fmaf(-b, kinv, dny);
+        const float li = fmaf(a, kinv, -rho * dny);
+        const float Hr = Gr * rinv2, Hi = Gi * rinv2;
+        Lr = fmaf(Hr, lr, fmaf(-Hi, li, Lr));
+        Li = fmaf(Hr, li, fmaf(Hi, lr, Li));
+        const float t1 = fmaf(-dnx, rinv, 1.0f);
+        const float t2 = -dnx * rinv2 * kinv;
+        Rr = fmaf(Gr, t1, fmaf(-Gi, t2, Rr));
+        Ri = fmaf(Gr, t2, fmaf(Gi, t1, Ri));
+      }
+      __stcs(L + off, make_float2(-Lr, -Li));
+      __stcs(R + off, make_float2(-Rr, -Ri));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ near pairs (FP64)
+namespace {
+
+struct dc {
+  double re, im;
+};
+__device__ __forceinline__ dc dmul(dc a, dc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// One warp per (i, j) pair from the near list: j == i (analytic radial integration in polar
+// coordinates about the centroid, Hadamard finite part of the hypersingular term) or j
+// sharing a vertex with i (7-point rule on the 4^levels sub-triangles of element j).
+__global__ void __launch_bounds__(256)
+k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
+                const double* __restrict__ cen, const double* __restrict__ nrm64,
+                const double* __restrict__ area, int ld, double k, float2* __restrict__ L,
+                float2* __restrict__ R) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n_pairs) return;
+  const int2 pr = pairs[w];
+  const int i = pr.x, j = pr.y;
+  const double kinv = 1.0 / k;
+  const double inv4pi = 0.25 / 3.14159265358979323846;
+  const double x0 = cen[3 * i], x1 = cen[3 * i + 1], x2 = cen[3 * i + 2];
+  const double n0 = nrm64[3 * i], n1 = nrm64[3 * i + 1], n2 = nrm64[3 * i + 2];
+  double Lre = 0, Lim = 0, Rre = 0, Rim = 0;
+  if (i != j) {
+    const double* t = tri + 9 * j;
+    const double m0 = nrm64[3 * j], m1 = nrm64[3 * j + 1], m2 = nrm64[3 * j + 2];
+    const double A = area[j];
+    const double nxny = n0 * m0 + n1 * m1 + n2 * m2;
+    const int np = c_adj_npts;
+    for (int p = lane; p < np; p += 32) {
+      const double4 rl = g_adj_rule[p];
+      const double y0 = rl.x * t[0] + rl.y * t[3] + rl.z * t[6];
+      const double y1 = rl.x * t[1] + rl.y * t[4] + rl.z * t[7];
+      const double y2 = rl.x * t[2] + rl.y * t[5] + rl.z * t[8];
+      const double d0 = x0 - y0, d1 = x1 - y1, d2 = x2 - y2;
+      const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+      const double rinv = rsqrt(r2);
+      const double r = r2 * rinv;
+      const double dny = d0 * m0 + d1 * m1 + d2 * m2;
+      const double dnx = d0 * n0 + d1 * n1 + d2 * n2;
+      const double rho = k * r;
+      double sn, cs;
+      sincos(rho, &sn, &cs);
+      const double gw = rl.w * A * inv4pi * rinv;
+      const double Gr = cs * gw, Gi = sn * gw;
+      const double rinv2 = rinv * rinv;
+      const double qq = dnx * dny * rinv2;
+      const double a = (rho * rho - 3.0) * qq + nxny;
+      const double b = rho * (3.0 * qq - nxny);
+      const dc lint = {dny - b * kinv, a * kinv - rho * dny};
+      const dc Lc = dmul({Gr * rinv2, Gi * rinv2}, lint);
+      const dc Rc = dmul({Gr, Gi}, {1.0 - dnx * rinv, -dnx * rinv2 * kinv});
+      Lre += Lc.re;
+      Lim += Lc.im;
+      Rre += Rc.re;
+      Rim += Rc.im;
+    }
+    Lre = -warp_sum(Lre);
+    Lim = -warp_sum(Lim);
+    Rre = -warp_sum(Rre);
+    Rim = -warp_sum(Rim);
+  } else {
+    // S = (1/4pi) sum_e int (e^{ikR} - 1)/(ik) dpsi,  FP = (1/4pi) sum_e int (ik - e^{ikR}/R) dpsi
+    // with R = d_e / cos(psi) the distance from the centroid to edge e along the ray.
+    const double* t = tri + 9 * i;
+    const int ns = c_self_pts;
+    double Sre = 0, Sim = 0, Fre = 0, Fim = 0;
+    for (int p = lane; p < 3 * ns; p += 32) {
+      const int e = p / ns, g = p - e * ns;
+      const double* P = t + 3 * e;
+      const double* Q = t + 3 * ((e + 1) % 3);
+      double u0 = Q[0] - P[0], u1 = Q[1] - P[1], u2 = Q[2] - P[2];
+      const double ul = rsqrt(u0 * u0 + u1 * u1 + u2 * u2);
+      u0 *= ul;
+      u1 *= ul;
+      u2 *= ul;
+      // positions of P and Q along the edge line, relative to the foot of the perpendicular
+      const double sP = (P[0] - x0) * u0 + (P[1] - x1) * u1 + (P[2] - x2) * u2;
+      const double sQ = (Q[0] - x0) * u0 + (Q[1] - x1) * u1 + (Q[2] - x2) * u2;
+      const double f0 = P[0] - x0 - sP * u0, f1 = P[1] - x1 - sP * u1, f2 = P[2] - x2 - sP * u2;
+      const double de = sqrt(f0 * f0 + f1 * f1 + f2 * f2);
+      const double psiP = atan2(sP, de), psiQ = atan2(sQ, de);
+      const double half = 0.5 * (psiQ - psiP), mid = 0.5 * (psiQ + psiP);
+      const double2 gl = g_gl[g];
+      const double psi = mid + half * gl.x;
+      const double Rr = de / cos(psi);
+      const double wq = half * gl.y;
+      double sn, cs;
+      sincos(k * Rr, &sn, &cs);
+      // (e^{ikR} - 1)/(ik) = sin(kR)/k + i (1 - cos(kR))/k
+      Sre += wq * sn * kinv;
+      Sim += wq * (1.0 - cs) * kinv;
+      Fre += -wq * cs / Rr;
+      Fim += wq * (k - sn / Rr);
+    }
+    Sre = warp_sum(Sre) * inv4pi;
+    Sim = warp_sum(Sim) * inv4pi;
+    Fre = warp_sum(Fre) * inv4pi;
+    Fim = warp_sum(Fim) * inv4pi;
+    // L_ii = 1/2 - beta FP, R_ii = -S - beta/2, beta = i/k
+    Lre = 0.5 + Fim * kinv;
+    Lim = -Fre * kinv;
+    Rre = -Sre;
+    Rim = -Sim - 0.5 * kinv;
+  }
+  if (lane == 0) {
+    L[(size_t)i * ld + j] = make_float2((float)Lre, (float)Lim);
+    R[(size_t)i * ld + j] = make_float2((float)Rre, (float)Rim);
+  }
+}
+
+// ----------------------------------------------------------------------- drivers
+nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
+                              const std::vector<int2>& near_pairs, cudaStream_t s) {
+  Geometry& g = op->geo;
+  const int64_t n = op->n;
+  (void)nv;
+  NB_TRY(dev_alloc_n(&g.c_hi, n, s));
+  NB_TRY(dev_alloc_n(&g.c_lo, n, s));
+  NB_TRY(dev_alloc_n(&g.nrm, n, s));
+  NB_TRY(dev_alloc_n(&g.qp, 7 * n, s));
+  NB_TRY(dev_alloc_n(&g.vid, n, s));
+  NB_TRY(dev_alloc_n(&g.tri, 9 * n, s));
+  NB_TRY(dev_alloc_n(&g.cen, 3 * n, s));
+  NB_TRY(dev_alloc_n(&g.nrm64, 3 * n, s));
+  NB_TRY(dev_alloc_n(&g.area, n, s));
+  g.n_near = (int64_t)near_pairs.size();
+  NB_TRY(dev_alloc_n(&g.near_pairs, g.n_near, s));
+  NB_TRY_CUDA(cudaMemcpyAsync(g.near_pairs, near_pairs.data(), g.n_near * sizeof(int2),
+                              cudaMemcpyHostToDevice, s));
+  const int threads = 128;
+  NB_LAUNCH("geometry", s, k_geometry<<<(unsigned)((n + threads - 1) / threads), threads, 0, s>>>(
+      dV, dT, (int)n, g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, g.tri, g.cen, g.nrm64, g.area));
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
+  const Geometry& g = op->geo;
+  const int n = (int)op->n, ld = (int)g.ld;
+  // regular pairs: columns in blocks of 256, rows split so the grid holds a few waves
+  const int col_blocks = (ld + kRegThreads - 1) / kRegThreads;
+  const int rows_per_block = 64;
+  const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
+  dim3 grid(col_blocks, row_blocks);
+  NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld,
+                                                  rows_per_block, (float)op->k, op->L, op->R));
+  NB_CHECK_LAUNCH();
+  // near pairs overwrite the entries the regular kernel skipped
+  const int64_t threads = 256, warps_per_block = threads / 32;
+  const int64_t blocks = (g.n_near + warps_per_block - 1) / warps_per_block;
+  NB_LAUNCH("assemble_near", s, k_assemble_near<<<(unsigned)blocks, (unsigned)threads, 0, s>>>(
+      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R));
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+}  // namespace natbem

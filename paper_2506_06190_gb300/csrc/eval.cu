@@ -1,0 +1,159 @@
+// Field evaluation: the exterior representation p(x) = int [p dG/dn_y - G g] dS_y with the
+// piecewise-constant surface data (pressure anywhere from the Neumann and Dirichlet data,
+// paper Sec. 3.4; its surface limit is the first line of Sec. 4, Eq. 6). The 7-point rule
+// is applied on every element:
+//
+//   field(x_q) = sum_j [ p_j sum_p w_p A_j dG/dn_y(x_q, y_jp) - g_j sum_p w_p A_j G(x_q, y_jp) ]
+//
+// FP32 kernel generation, one thread per field point, elements split over blocks and staged in
+// shared memory (broadcast reads); per-split FP64 partial sums are reduced in a fixed order.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace natbem {
+
+namespace {
+constexpr float kTwoPiHi = 6.28318548202514648f;
+constexpr float kTwoPiLo = -1.7484555314695172e-7f;
+constexpr float kInvTwoPi = 0.159154943091895336f;
+constexpr int kEvalThreads = 128;  // field points per block
+constexpr int kElemStage = 32;     // elements staged per shared-memory round
+constexpr int kMaxRhsPass = 4;     // right-hand sides accumulated per pass
+}  // namespace
+
+template <int NR>
+__global__ void __launch_bounds__(kEvalThreads)
+k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
+       const float4* __restrict__ nrm, const float4* __restrict__ qp, int n,
+       const double* __restrict__ pts, int m, float k, const float2* __restrict__ p,
+       const float2* __restrict__ g, int rhs0, int elems_per_split, double2* __restrict__ part) {
+  __shared__ float4 s_hi[kElemStage], s_lo[kElemStage], s_n[kElemStage];
+  __shared__ float4 s_q[kElemStage * 7];
+  __shared__ float2 s_p[kElemStage * NR], s_g[kElemStage * NR];
+  const int qi = blockIdx.x * kEvalThreads + threadIdx.x;
+  const bool ok = qi < m;
+  float xh[3] = {0.f, 0.f, 0.f}, xl[3] = {0.f, 0.f, 0.f};
+  if (ok)
+    for (int d = 0; d < 3; ++d) {
+      const double v = pts[3 * (size_t)qi + d];
+      xh[d] = (float)v;
+      xl[d] = (float)(v - (double)xh[d]);
+    }
+  const int j_begin = blockIdx.y * elems_per_split;
+  const int j_end = min(n, j_begin + elems_per_split);
+  float accr[NR], acci[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) accr[s] = acci[s] = 0.f;
+  for (int jb = j_begin; jb < j_end; jb += kElemStage) {
+    const int cnt = min(kElemStage, j_end - jb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt * 7; t += kEvalThreads) s_q[t] = qp[7 * (size_t)jb + t];
+    if (threadIdx.x < cnt) {
+      const int j = jb + threadIdx.x;
+      s_hi[threadIdx.x] = c_hi[j];
+      s_lo[threadIdx.x] = c_lo[j];
+      s_n[threadIdx.x] = nrm[j];
+#pragma unroll
+      for (int s = 0; s < NR; ++s) {
+        s_p[threadIdx.x * NR + s] = p[(size_t)(rhs0 + s) * n + j];
+        s_g[threadIdx.x * NR + s] = g[(size_t)(rhs0 + s) * n + j];
+      }
+    }
+    __syncthreads();
+    if (!ok) continue;
+    for (int t = 0; t < cnt; ++t) {
+      const float4 ch = s_hi[t], cl = s_lo[t], nj = s_n[t];
+      const float Dx = (xh[0] - ch.x) + (xl[0] - cl.x);
+      const float Dy = (xh[1] - ch.y) + (xl[1] - cl.y);
+      const float Dz = (xh[2] - ch.z) + (xl[2] - cl.z);
+      const float dny = Dx * nj.x + Dy * nj.y + Dz * nj.z;
+      float Gr = 0.f, Gi = 0.f, Dr = 0.f, Di = 0.f;  // sums of w A G and w A dG/dn_y
+#pragma unroll
+      for (int q = 0; q < 7; ++q) {
+        const float4 o = s_q[7 * t + q];
+        const float dx = Dx - o.x, dy = Dy - o.y, dz = Dz - o.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float rinv = rsqrtf(r2);
+        const float rho = k * (r2 * rinv);
+        const float nq = rintf(rho * kInvTwoPi);
+        float th = fmaf(-nq, kTwoPiHi, rho);
+        th = fmaf(-nq, kTwoPiLo, th);
+        float sn, cs;
+        __sincosf(th, &sn, &cs);
+        const float gw = rinv * o.w;
+        const float er = cs * gw, ei = sn * gw;  // w A G
+        Gr += er;
+        Gi += ei;
+        // dG/dn_y = G (1 - i rho) (d.n_y) / r^2
+        const float f = dny * rinv * rinv;
+        Dr = fmaf(f, fmaf(rho, ei, er), Dr);
+        Di = fmaf(f, fmaf(-rho, er, ei), Di);
+      }
+#pragma unroll
+      for (int s = 0; s < NR; ++s) {
+        const float2 pj = s_p[t * NR + s], gj = s_g[t * NR + s];
+        accr[s] += pj.x * Dr - pj.y * Di - (gj.x * Gr - gj.y * Gi);
+        acci[s] += pj.x * Di + pj.y * Dr - (gj.x * Gi + gj.y * Gr);
+      }
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < NR; ++s)
+      part[((size_t)blockIdx.y * m + qi) * kMaxRhsPass + s] = make_double2(accr[s], acci[s]);
+  }
+}
+
+// out[q, rhs0 + s] = sum over splits of the partials, complex64, column-major (m x nrhs)
+__global__ void k_eval_reduce(const double2* __restrict__ part, int m, int splits, int nr,
+                              int rhs0, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)m * nr) return;
+  const int qi = (int)(i / nr), s = (int)(i % nr);
+  double re = 0.0, im = 0.0;
+  for (int t = 0; t < splits; ++t) {
+    const double2 v = part[((size_t)t * m + qi) * kMaxRhsPass + s];
+    re += v.x;
+    im += v.y;
+  }
+  out[(size_t)(rhs0 + s) * m + qi] = make_float2((float)re, (float)im);
+}
+
+nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
+                         const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                         cudaStream_t s) {
+  if (m == 0) return NAT_BEM_OK;
+  const Geometry& g = op->geo;
+  const int n = (int)op->n;
+  const int pblocks = (int)((m + kEvalThreads - 1) / kEvalThreads);
+  // split the elements so that the grid holds about four blocks per SM
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int splits = (4 * sms + pblocks - 1) / pblocks;
+  splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
+  int per = (n + splits - 1) / splits;
+  per = (per + kElemStage - 1) / kElemStage * kElemStage;
+  splits = (n + per - 1) / per;
+  double2* part = nullptr;
+  NB_TRY(dev_alloc_n(&part, (size_t)splits * m * kMaxRhsPass, s));
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
+    const int nr = min(kMaxRhsPass, nrhs - r0);
+    dim3 grid(pblocks, splits);
+    switch (nr) {
+      case 1: NB_LAUNCH("eval", s, k_eval<1><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
+      case 2: NB_LAUNCH("eval", s, k_eval<2><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
+      case 3: NB_LAUNCH("eval", s, k_eval<3><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
+      default: NB_LAUNCH("eval", s, k_eval<4><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
+    }
+    NB_CHECK_LAUNCH();
+    const int64_t tot = m * nr;
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out));
+    NB_CHECK_LAUNCH();
+  }
+  dev_free(part, s);
+  return NAT_BEM_OK;
+}
+
+}  // namespace natbem

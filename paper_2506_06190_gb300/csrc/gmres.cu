@@ -1,0 +1,660 @@
+// Dense complex GMRES for L p = R g (paper Sec. 6.1 settings: relative residual 1e-6, at most
+// 200 iterations), run entirely on the device.
+//
+// Precision split: the operator and its matvec are FP32 (complex64 entries, FP32 products,
+// partial sums flushed into FP64 accumulators); the Krylov basis, classical Gram-Schmidt with
+// one re-orthogonalisation pass (CGS2), the Hessenberg matrix, the complex Givens rotations
+// and the small least-squares solve are FP64.
+//
+// One iteration (all right-hand sides in lockstep, each with its own Krylov space) is five
+// kernels: normalise v_j = w / h_{j,j-1}; w = L v_j; h = V^H w; w -= V h and h' = V^H w;
+// w -= V h' with ||w||, Givens update and convergence test. The iteration index, the per-RHS
+// convergence flags and the "all done" flag live in device memory, so the launch sequence is
+// the same every iteration and finished iterations cost only empty launches. Reductions are
+// deterministic: per-chunk partial sums, summed in a fixed order by the last block to finish
+// (counted with an atomic ticket).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace natbem {
+
+constexpr int kChunk = 256;       // rows per block in the vector kernels
+constexpr int kColGroup = 8;      // Krylov vectors per block in the first dot kernel
+constexpr int kCounters = 8;      // per-RHS tickets
+
+struct Workspace {
+  int64_t n = 0, ld = 0;
+  int nrhs = 0, cap = 0, m = 0, nchunk = 0;
+  double2 *b = nullptr, *V = nullptr, *w = nullptr, *x = nullptr;
+  double2 *H = nullptr, *hcol = nullptr, *htmp = nullptr, *sn = nullptr, *gv = nullptr;
+  double2 *y = nullptr, *part = nullptr;
+  double *cs = nullptr, *partn = nullptr, *bnorm = nullptr, *res = nullptr, *hnorm = nullptr;
+  double* res_true = nullptr;
+  float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
+  int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
+  unsigned* cnt = nullptr;
+  int* host_scal = nullptr;  // pinned mirror of scal[0..1]
+};
+
+struct GArgs {
+  int n, ld, nrhs, m, nchunk;
+  const float2* L;
+  double2 *b, *V, *w, *x, *H, *hcol, *htmp, *sn, *gv, *y, *part;
+  double *cs, *partn, *bnorm, *res, *hnorm, *res_true;
+  float2* xf;
+  int *done, *iters, *scal;
+  unsigned* cnt;
+  double tol;
+};
+
+namespace {
+
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of a double (blockDim.x a multiple of 32, <= 1024); result in all threads.
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < nw; ++i) t += sh[i];  // fixed order
+  return t;
+}
+
+// Ticket: returns true in every thread of the last block (among `total`) to arrive.
+__device__ bool last_block(unsigned* counter, unsigned total) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    last = (t == total - 1);
+    if (last) *counter = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ size_t vidx(const GArgs& a, int c, int s) {
+  return ((size_t)c * a.nrhs + s) * (size_t)a.n;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------ matvec
+// y_s = A x_s for the RHS s = blockIdx.y: A is n x ld complex64 (row-major, ld even, pad
+// columns zero), x_s complex64 with ld entries, y_s complex128. kRows rows per block; the
+// block's threads stride over the row in 16-byte (two-complex) steps; FP32 products summed
+// in FP32 over kUnroll steps, then into FP64.
+template <int kRows, int kUnroll>
+__global__ void __launch_bounds__(256)
+k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x, int64_t xstride,
+       double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+       const int* __restrict__ scal) {
+  __shared__ double sh[2 * kRows][8];
+  if (scal && scal[1]) return;
+  const int s = blockIdx.y;
+  if (done && done[s]) return;
+  const int row0 = blockIdx.x * kRows;
+  const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
+  const float4* a[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+    a[r] = reinterpret_cast<const float4*>(A + (size_t)min(row0 + r, n - 1) * ld);
+  const int n4 = ld >> 1;
+  double accr[kRows], acci[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) accr[r] = acci[r] = 0.0;
+  for (int base = threadIdx.x; base < n4; base += 256 * kUnroll) {
+    float pr[kRows], pi[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) pr[r] = pi[r] = 0.f;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int idx = base + u * 256;
+      if (idx < n4) {
+        const float4 xx = __ldg(xv + idx);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const float4 aa = __ldcs(a[r] + idx);
+          pr[r] = fmaf(aa.x, xx.x, fmaf(-aa.y, xx.y, fmaf(aa.z, xx.z, fmaf(-aa.w, xx.w, pr[r]))));
+          pi[r] = fmaf(aa.x, xx.y, fmaf(aa.y, xx.x, fmaf(aa.z, xx.w, fmaf(aa.w, xx.z, pi[r]))));
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      accr[r] += pr[r];
+      acci[r] += pi[r];
+    }
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    accr[r] = warp_sum(accr[r]);
+    acci[r] = warp_sum(acci[r]);
+    if (lane == 0) {
+      sh[2 * r][wid] = accr[r];
+      sh[2 * r + 1][wid] = acci[r];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
+    const int r = threadIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      sr += sh[2 * r][q];
+      si += sh[2 * r + 1][q];
+    }
+    y[(size_t)s * ystride + row0 + r] = make_double2(sr, si);
+  }
+}
+
+// ------------------------------------------------------------------------ GMRES steps
+// ||b_s|| (partials + last block per RHS); w_s = b_s; h_{0,-1} := ||b_s||, g_s[0] = ||b_s||.
+__global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int r = chunk * kChunk + threadIdx.x;
+  double v = 0.0;
+  if (r < a.n) {
+    const double2 bb = a.b[(size_t)s * a.n + r];
+    a.w[(size_t)s * a.n + r] = bb;
+    v = cabs2(bb);
+  }
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) a.partn[(size_t)chunk * a.nrhs + s] = v;
+  if (!last_block(a.cnt + s * kCounters + 0, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) t += a.partn[(size_t)c * a.nrhs + s];
+    const double bn = sqrt(t);
+    a.bnorm[s] = bn;
+    a.hnorm[s] = bn;
+    a.gv[(size_t)s * (a.m + 1)] = make_double2(bn, 0.0);
+    a.res[s] = bn;
+    a.iters[s] = 0;
+    a.done[s] = (bn == 0.0);
+    __threadfence();
+    const unsigned t2 = atomicAdd((unsigned*)&a.scal[2], 1u);
+    if (t2 == (unsigned)a.nrhs - 1) {
+      a.scal[2] = 0;
+      int all = 1;
+      for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
+      a.scal[0] = 0;
+      a.scal[1] = all || a.m == 0;
+    }
+  }
+}
+
+// v_j = w / h_{j,j-1} into V[j] (FP64) and the FP32 copy used by the matvec.
+__global__ void __launch_bounds__(kChunk) k_normalize(GArgs a) {
+  if (a.scal[1]) return;
+  const int s = blockIdx.y;
+  if (a.done[s]) return;
+  const int j = a.scal[0];
+  const int r = blockIdx.x * kChunk + threadIdx.x;
+  if (r >= a.n) return;
+  const double inv = 1.0 / a.hnorm[s];
+  const double2 ww = a.w[(size_t)s * a.n + r];
+  const double2 v = make_double2(ww.x * inv, ww.y * inv);
+  a.V[vidx(a, j, s) + r] = v;
+  a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+}
+
+// h_c = V[c]^H w for c <= j: block (chunk, column group, s); warp per column, lanes over
+// the chunk's rows. Last block per RHS sums the chunk partials into hcol.
+__global__ void __launch_bounds__(kChunk) k_dots(GArgs a) {
+  if (a.scal[1]) return;
+  const int s = blockIdx.z;
+  const int j = a.scal[0];
+  const int chunk = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.y * kColGroup + wid;
+  const bool active = !a.done[s];
+  if (active && c <= j) {
+    const double2* v = a.V + vidx(a, c, s);
+    const double2* w = a.w + (size_t)s * a.n;
+    double re = 0.0, im = 0.0;
+    const int r0 = chunk * kChunk;
+    const int r1 = min(a.n, r0 + kChunk);
+    for (int r = r0 + lane; r < r1; r += 32) {
+      const double2 p = cmulc(v[r], w[r]);
+      re += p.x;
+      im += p.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) a.part[((size_t)chunk * a.nrhs + s) * (a.m + 1) + c] = make_double2(re, im);
+  }
+  if (!last_block(a.cnt + s * kCounters + 1, gridDim.x * gridDim.y)) return;
+  if (!active) return;
+  for (int cc = threadIdx.x; cc <= j; cc += blockDim.x) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int q = 0; q < a.nchunk; ++q) t = cadd(t, a.part[((size_t)q * a.nrhs + s) * (a.m + 1) + cc]);
+    a.hcol[(size_t)s * (a.m + 1) + cc] = t;
+  }
+}
+
+// w -= V h (first pass, h = hcol), then h' = V^H w over the block's rows; the last block per
+// RHS sums h' into htmp and accumulates hcol += h'.
+__global__ void __launch_bounds__(kChunk) k_update_dots(GArgs a) {
+  __shared__ double2 s_h[256];
+  __shared__ double2 s_w[kChunk];
+  if (a.scal[1]) return;
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int j = a.scal[0];
+  const bool active = !a.done[s];
+  const int r = chunk * kChunk + threadIdx.x;
+  if (active) {
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = a.hcol[(size_t)s * (a.m + 1) + c];
+    __syncthreads();
+    double2 w = make_double2(0.0, 0.0);
+    if (r < a.n) {
+      w = a.w[(size_t)s * a.n + r];
+      double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+      int c = 0;
+      for (; c + 1 <= j; c += 2) {
+        acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+        acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 1, s) + r], s_h[c + 1]));
+      }
+      if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+      w = csub(w, cadd(acc0, acc1));
+      a.w[(size_t)s * a.n + r] = w;
+    }
+    s_w[threadIdx.x] = w;
+    __syncthreads();
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r0 = chunk * kChunk;
+    const int cnt = min(kChunk, a.n - r0);
+    for (int c = wid; c <= j; c += kChunk / 32) {
+      const double2* v = a.V + vidx(a, c, s) + r0;
+      double re = 0.0, im = 0.0;
+      for (int q = lane; q < cnt; q += 32) {
+        const double2 p = cmulc(v[q], s_w[q]);
+        re += p.x;
+        im += p.y;
+      }
+      re = warp_sum(re);
+      im = warp_sum(im);
+      if (lane == 0) a.part[((size_t)chunk * a.nrhs + s) * (a.m + 1) + c] = make_double2(re, im);
+    }
+  }
+  if (!last_block(a.cnt + s * kCounters + 2, gridDim.x)) return;
+  if (!active) return;
+  for (int cc = threadIdx.x; cc <= j; cc += blockDim.x) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int q = 0; q < a.nchunk; ++q) t = cadd(t, a.part[((size_t)q * a.nrhs + s) * (a.m + 1) + cc]);
+    a.htmp[(size_t)s * (a.m + 1) + cc] = t;
+    a.hcol[(size_t)s * (a.m + 1) + cc] = cadd(a.hcol[(size_t)s * (a.m + 1) + cc], t);
+  }
+}
+
+// w -= V h' (second pass) and ||w||; the last block per RHS applies the Givens rotations to
+// the new Hessenberg column, updates the residual estimate and the convergence flags; the
+// last RHS to finish advances j and sets the "all done" flag.
+__global__ void __launch_bounds__(kChunk) k_update_norm(GArgs a) {
+  __shared__ double2 s_h[256];
+  __shared__ double sh[32];
+  if (a.scal[1]) return;
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int j = a.scal[0];
+  const bool active = !a.done[s];
+  const int r = chunk * kChunk + threadIdx.x;
+  double nv = 0.0;
+  if (active) {
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = a.htmp[(size_t)s * (a.m + 1) + c];
+    __syncthreads();
+    if (r < a.n) {
+      double2 w = a.w[(size_t)s * a.n + r];
+      double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+      int c = 0;
+      for (; c + 1 <= j; c += 2) {
+        acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+        acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 1, s) + r], s_h[c + 1]));
+      }
+      if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+      w = csub(w, cadd(acc0, acc1));
+      a.w[(size_t)s * a.n + r] = w;
+      nv = cabs2(w);
+    }
+  }
+  nv = block_sum(nv, sh);
+  if (threadIdx.x == 0) a.partn[(size_t)chunk * a.nrhs + s] = nv;
+  if (!last_block(a.cnt + s * kCounters + 3, gridDim.x)) return;
+  if (threadIdx.x != 0) return;
+  if (active) {
+    double t = 0.0;
+    for (int q = 0; q < a.nchunk; ++q) t += a.partn[(size_t)q * a.nrhs + s];
+    const double hn = sqrt(t);
+    a.hnorm[s] = hn;
+    const size_t ho = (size_t)s * (a.m + 1);
+    double2* hc = a.hcol + ho;
+    double* cs = a.cs + (size_t)s * a.m;
+    double2* sn = a.sn + (size_t)s * a.m;
+    double2* gv = a.gv + ho;
+    // earlier rotations on the new column
+    for (int i = 0; i < j; ++i) {
+      const double2 h0 = hc[i], h1 = hc[i + 1];
+      // [t0; t1] = [c s; -conj(s) c] [h0; h1]
+      const double2 t0 = cadd(make_double2(cs[i] * h0.x, cs[i] * h0.y), cmul(sn[i], h1));
+      const double2 t1 = cadd(cmul(make_double2(-sn[i].x, sn[i].y), h0),
+                              make_double2(cs[i] * h1.x, cs[i] * h1.y));
+      hc[i] = t0;
+      hc[i + 1] = t1;
+    }
+    // new rotation zeroing h_{j+1,j} = hn
+    const double2 h0 = hc[j];
+    const double a0 = sqrt(cabs2(h0));
+    const double rho = sqrt(a0 * a0 + hn * hn);
+    double c;
+    double2 sv, top;
+    if (a0 == 0.0) {
+      c = 0.0;
+      sv = make_double2(1.0, 0.0);
+      top = make_double2(hn, 0.0);
+    } else {
+      c = a0 / rho;
+      const double2 ph = make_double2(h0.x / a0, h0.y / a0);
+      sv = make_double2(ph.x * hn / rho, ph.y * hn / rho);  // (h0/|h0|) conj(hn) / rho, hn real
+      top = make_double2(ph.x * rho, ph.y * rho);
+    }
+    cs[j] = c;
+    sn[j] = sv;
+    hc[j] = top;
+    const double2 gj = gv[j];
+    gv[j + 1] = cmul(make_double2(-sv.x, sv.y), gj);  // -conj(s) g_j
+    gv[j] = make_double2(c * gj.x, c * gj.y);
+    double2* Hcol = a.H + ((size_t)s * a.m + j) * (a.m + 1);
+    for (int i = 0; i <= j; ++i) Hcol[i] = hc[i];
+    const double res = sqrt(cabs2(gv[j + 1]));
+    a.res[s] = res;
+    a.iters[s] = j + 1;
+    if (res <= a.tol * a.bnorm[s] || hn == 0.0) a.done[s] = 1;
+  }
+  __threadfence();
+  const unsigned t2 = atomicAdd((unsigned*)&a.scal[2], 1u);
+  if (t2 == (unsigned)a.nrhs - 1) {
+    a.scal[2] = 0;
+    int all = 1;
+    for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
+    const int jn = j + 1;
+    a.scal[0] = jn;
+    a.scal[1] = all || jn >= a.m;
+  }
+}
+
+// Back substitution R y = g on the rotated Hessenberg matrix, one warp per RHS.
+__global__ void k_lsq(GArgs a) {
+  const int s = blockIdx.x, lane = threadIdx.x;
+  const int kdim = a.iters[s];
+  const size_t ho = (size_t)s * (a.m + 1);
+  double2* y = a.y + (size_t)s * a.m;
+  for (int i = kdim - 1; i >= 0; --i) {
+    double re = 0.0, im = 0.0;
+    for (int c = i + 1 + lane; c < kdim; c += 32) {
+      const double2 p = cmul(a.H[((size_t)s * a.m + c) * (a.m + 1) + i], y[c]);
+      re += p.x;
+      im += p.y;
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      const double2 num = csub(a.gv[ho + i], make_double2(re, im));
+      const double2 d = a.H[((size_t)s * a.m + i) * (a.m + 1) + i];
+      const double dd = cabs2(d);
+      y[i] = make_double2((num.x * d.x + num.y * d.y) / dd, (num.y * d.x - num.x * d.y) / dd);
+    }
+    __syncwarp();
+  }
+}
+
+// x = V y (FP64) and the complex64 output; also the FP32 copy of x for the residual matvec.
+__global__ void __launch_bounds__(kChunk) k_xupdate(GArgs a, float2* __restrict__ pout) {
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * kChunk + threadIdx.x;
+  if (r >= a.n) return;
+  const int kdim = a.iters[s];
+  const double2* y = a.y + (size_t)s * a.m;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int c = 0; c < kdim; ++c) acc = cadd(acc, cmul(a.V[vidx(a, c, s) + r], y[c]));
+  a.x[(size_t)s * a.n + r] = acc;
+  pout[(size_t)s * a.n + r] = make_float2((float)acc.x, (float)acc.y);
+  a.xf[(size_t)s * a.ld + r] = make_float2((float)acc.x, (float)acc.y);
+}
+
+// ||b - w|| / ||b|| with w = L x (true residual of the FP32 operator).
+__global__ void __launch_bounds__(kChunk) k_resid(GArgs a) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int r = chunk * kChunk + threadIdx.x;
+  double v = 0.0;
+  if (r < a.n) v = cabs2(csub(a.b[(size_t)s * a.n + r], a.w[(size_t)s * a.n + r]));
+  v = block_sum(v, sh);
+  if (threadIdx.x == 0) a.partn[(size_t)chunk * a.nrhs + s] = v;
+  if (!last_block(a.cnt + s * kCounters + 4, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) t += a.partn[(size_t)c * a.nrhs + s];
+    a.res_true[s] = a.bnorm[s] > 0.0 ? sqrt(t) / a.bnorm[s] : 0.0;
+  }
+}
+
+// complex64 (n) -> padded complex64 (ld), zero pad
+__global__ void k_pad_copy(const float2* __restrict__ src, int n, int ld, int nrhs,
+                           float2* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)ld * nrhs) return;
+  const int s = (int)(i / ld), r = (int)(i % ld);
+  dst[i] = r < n ? src[(size_t)s * n + r] : make_float2(0.f, 0.f);
+}
+
+// ---------------------------------------------------------------------------- host side
+int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
+  const int64_t m = std::max(1, o.max_iter);
+  const int64_t ld = round_up(n, 32);
+  const int64_t nchunk = (n + kChunk - 1) / kChunk;
+  int64_t b = 0;
+  b += 16 * n * nrhs * 3;                 // b, w, x
+  b += 16 * n * nrhs * (m + 1);           // V
+  b += 8 * ld * nrhs * 3;                 // xf, gin, pout
+  b += 16 * nrhs * (m + 1) * (m + 4);     // H, hcol, htmp, gv, sn, y
+  b += 16 * nchunk * nrhs * (m + 1);      // partial dots
+  return b;
+}
+
+void workspace_free(Workspace* ws, cudaStream_t s) {
+  if (!ws) return;
+  void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
+                  ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
+                  ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt};
+  for (void* p : ptrs)
+    if (p) dev_free(p, s);
+  if (ws->host_scal) cudaFreeHost(ws->host_scal);
+  delete ws;
+}
+
+static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s) {
+  const int m = std::max(1, op->opts.max_iter);
+  Workspace* ws = op->ws;
+  if (ws && ws->cap >= nrhs && ws->m == m) {
+    ws->nrhs = nrhs;  // reuse: every array is sized for `cap` right-hand sides
+    return NAT_BEM_OK;
+  }
+  if (ws) workspace_free(ws, s);
+  op->ws = ws = new Workspace();
+  const int64_t n = op->n, ld = op->geo.ld;
+  ws->n = n;
+  ws->ld = ld;
+  ws->nrhs = nrhs;
+  ws->cap = nrhs;
+  ws->m = m;
+  ws->nchunk = (int)((n + kChunk - 1) / kChunk);
+  const size_t nr = (size_t)nrhs, mm = (size_t)m;
+  NB_TRY(dev_alloc_n(&ws->b, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->w, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->x, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->V, n * nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->H, nr * mm * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->hcol, nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->htmp, nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->sn, nr * mm, s));
+  NB_TRY(dev_alloc_n(&ws->gv, nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->y, nr * mm, s));
+  NB_TRY(dev_alloc_n(&ws->part, (size_t)ws->nchunk * nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->cs, nr * mm, s));
+  NB_TRY(dev_alloc_n(&ws->partn, (size_t)ws->nchunk * nr, s));
+  NB_TRY(dev_alloc_n(&ws->bnorm, nr, s));
+  NB_TRY(dev_alloc_n(&ws->res, nr, s));
+  NB_TRY(dev_alloc_n(&ws->hnorm, nr, s));
+  NB_TRY(dev_alloc_n(&ws->res_true, nr, s));
+  NB_TRY(dev_alloc_n(&ws->xf, ld * nr, s));
+  NB_TRY(dev_alloc_n(&ws->gin, ld * nr, s));
+  NB_TRY(dev_alloc_n(&ws->pout, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->done, nr, s));
+  NB_TRY(dev_alloc_n(&ws->iters, nr, s));
+  NB_TRY(dev_alloc_n(&ws->scal, 4, s));
+  NB_TRY(dev_alloc_n(&ws->cnt, nr * kCounters, s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->cnt, 0, nr * kCounters * sizeof(unsigned), s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->scal, 0, 4 * sizeof(int), s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->xf, 0, ld * nr * sizeof(float2), s));
+  NB_TRY_CUDA(cudaMallocHost(&ws->host_scal, 4 * sizeof(int)));
+  return NAT_BEM_OK;
+}
+
+static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
+  GArgs a;
+  a.n = (int)ws->n;
+  a.ld = (int)ws->ld;
+  a.nrhs = ws->nrhs;
+  a.m = ws->m;
+  a.nchunk = ws->nchunk;
+  a.L = Lop;
+  a.b = ws->b;
+  a.V = ws->V;
+  a.w = ws->w;
+  a.x = ws->x;
+  a.H = ws->H;
+  a.hcol = ws->hcol;
+  a.htmp = ws->htmp;
+  a.sn = ws->sn;
+  a.gv = ws->gv;
+  a.y = ws->y;
+  a.part = ws->part;
+  a.cs = ws->cs;
+  a.partn = ws->partn;
+  a.bnorm = ws->bnorm;
+  a.res = ws->res;
+  a.hnorm = ws->hnorm;
+  a.res_true = ws->res_true;
+  a.xf = ws->xf;
+  a.done = ws->done;
+  a.iters = ws->iters;
+  a.scal = ws->scal;
+  a.cnt = ws->cnt;
+  a.tol = op->opts.tol;
+  return a;
+}
+
+// y_s = A x_s for all RHS (x padded to ld), skipping RHS flagged done when `done` is given.
+static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, const float2* x,
+                           double2* y, int nrhs, const int* done, const int* scal, cudaStream_t s) {
+  constexpr int kRows = 2;
+  dim3 grid((n + kRows - 1) / kRows, nrhs);
+  NB_LAUNCH(name, s, k_gemv<kRows, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
+                          nat_bem_solve_info* info, cudaStream_t s) {
+  NB_TRY(workspace_ensure(op, nrhs, s));
+  Workspace* ws = op->ws;
+  const int n = (int)op->n, ld = (int)op->geo.ld;
+  GArgs a = make_args(op, ws, op->L);
+  const dim3 vec_grid(ws->nchunk, nrhs);
+  // b = R g
+  {
+    const int64_t tot = (int64_t)ld * nrhs;
+    NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, n, ld, nrhs, ws->gin));
+    NB_CHECK_LAUNCH();
+    NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s));
+  }
+  NB_LAUNCH("gmres_init", s, k_init<<<vec_grid, kChunk, 0, s>>>(a));
+  NB_CHECK_LAUNCH();
+  const int m = ws->m;
+  const dim3 dots_grid(ws->nchunk, (m + 1 + kColGroup - 1) / kColGroup, nrhs);
+  int it = 0;
+  int chunk = 16;
+  while (it < m) {
+    const int c = std::min(chunk, m - it);
+    for (int q = 0; q < c; ++q) {
+      NB_LAUNCH("gmres_normalize", s, k_normalize<<<vec_grid, kChunk, 0, s>>>(a));
+      NB_TRY(gemv("gemv", op->L, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
+      NB_LAUNCH("gmres_dots", s, k_dots<<<dots_grid, kChunk, 0, s>>>(a));
+      NB_LAUNCH("gmres_update_dots", s, k_update_dots<<<vec_grid, kChunk, 0, s>>>(a));
+      NB_LAUNCH("gmres_update_norm", s, k_update_norm<<<vec_grid, kChunk, 0, s>>>(a));
+    }
+    NB_CHECK_LAUNCH();
+    it += c;
+    NB_TRY_CUDA(cudaMemcpyAsync(ws->host_scal, ws->scal, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    if (ws->host_scal[1]) break;
+    chunk = 8;
+  }
+  NB_LAUNCH("gmres_lsq", s, k_lsq<<<nrhs, 32, 0, s>>>(a));
+  NB_LAUNCH("gmres_xupdate", s, k_xupdate<<<vec_grid, kChunk, 0, s>>>(a, d_p));
+  NB_CHECK_LAUNCH();
+  // true residual ||R g - L p|| / ||R g|| with the FP32 operator
+  NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
+  NB_LAUNCH("gmres_resid", s, k_resid<<<vec_grid, kChunk, 0, s>>>(a));
+  NB_CHECK_LAUNCH();
+  std::vector<int> iters(nrhs), done(nrhs);
+  std::vector<double> rt(nrhs);
+  NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  NB_TRY_CUDA(cudaMemcpyAsync(done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+  NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+  NB_TRY_CUDA(cudaStreamSynchronize(s));
+  int maxit = 0, all_done = 1;
+  double maxres = 0.0;
+  for (int q = 0; q < nrhs; ++q) {
+    maxit = std::max(maxit, iters[q]);
+    all_done &= done[q];
+    maxres = std::max(maxres, rt[q]);
+  }
+  if (info) {
+    info->iterations = maxit;
+    info->refinements = 0;
+    info->rel_residual = maxres;
+  }
+  if (!all_done) {
+    set_error("GMRES did not reach the tolerance within max_iter");
+    return NAT_BEM_ENOCONV;
+  }
+  return NAT_BEM_OK;
+}
+
+}  // namespace natbem

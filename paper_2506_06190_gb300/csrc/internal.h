@@ -1,0 +1,143 @@
+// Internal declarations of the natbem library (CUDA path). Nothing here is shared with the
+// FP64 oracle; this header is only included by the library's own translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nat_bem.h"
+
+namespace natbem {
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+void clear_error();
+
+#define NB_TRY_CUDA(call)                                                                   \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      ::natbem::set_error(std::string(#call) + " failed: " + cudaGetErrorString(e_));       \
+      return (e_ == cudaErrorMemoryAllocation) ? NAT_BEM_ENOMEM : NAT_BEM_ECUDA;            \
+    }                                                                                       \
+  } while (0)
+
+#define NB_CHECK_LAUNCH() NB_TRY_CUDA(cudaGetLastError())
+
+#define NB_TRY(expr)                                                                        \
+  do {                                                                                      \
+    nat_bem_status s_ = (expr);                                                             \
+    if (s_ != NAT_BEM_OK) return s_;                                                        \
+  } while (0)
+
+// ---------------------------------------------------------------------------- tracing
+// Counts one kernel launch and, when tracing is on, brackets it with CUDA events on its
+// stream. Construct it immediately before the launch, in the same scope:
+//   { TraceScope t("gemv", s); k_gemv<<<g, b, 0, s>>>(...); }
+class TraceScope {
+ public:
+  TraceScope(const char* name, cudaStream_t s);
+  ~TraceScope();
+  TraceScope(const TraceScope&) = delete;
+  TraceScope& operator=(const TraceScope&) = delete;
+
+ private:
+  const char* name_;
+  cudaStream_t s_;
+  void* a_ = nullptr;
+  void* b_ = nullptr;
+};
+
+#define NB_LAUNCH(name, stream, ...)            \
+  do {                                          \
+    ::natbem::TraceScope nb_trace_(name, stream); \
+    __VA_ARGS__;                                \
+  } while (0)
+
+// ------------------------------------------------------------------------ device memory
+// Stream-ordered allocations from a library-owned pool per device that keeps freed blocks
+// cached (release threshold = unlimited), so repeated operators of the same size reuse memory
+// without going back to the driver.
+nat_bem_status dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <class T>
+nat_bem_status dev_alloc_n(T** p, size_t count, cudaStream_t s) {
+  return dev_alloc(reinterpret_cast<void**>(p), count * sizeof(T), s);
+}
+
+// Whether p is a device (or managed) pointer the GPU can read directly.
+bool is_device_pointer(const void* p);
+
+// -------------------------------------------------------------------------- geometry
+// Device-resident mesh records. Single-precision records serve the regular (FP32) pairs and
+// the field evaluation; double-precision arrays serve the self and vertex-sharing pairs.
+struct Geometry {
+  int64_t n = 0;              // triangles
+  int64_t ld = 0;             // leading dimension of the n x n operators (n rounded up to 32)
+  // FP32 records, one per element
+  float4* c_hi = nullptr;     // centroid, high part (x, y, z, 0)
+  float4* c_lo = nullptr;     // centroid, low part: c = hi + lo to ~2^-48 relative
+  float4* nrm = nullptr;      // unit outward normal (x, y, z, 0)
+  float4* qp = nullptr;       // 7 per element: (y_q - c, w_q A / (4 pi))
+  int4* vid = nullptr;        // vertex indices (a, b, c, 0)
+  // FP64 records
+  double* tri = nullptr;      // 9 per element: vertices a, b, c
+  double* cen = nullptr;      // 3 per element
+  double* nrm64 = nullptr;    // 3 per element
+  double* area = nullptr;     // 1 per element
+  // pairs handled in FP64: (i, j) with j == i or j sharing a vertex with i, grouped by row
+  int2* near_pairs = nullptr;
+  int64_t n_near = 0;
+};
+
+// Host-side mesh check and near-pair list (mesh.cpp). Returns NAT_BEM_EINVAL with a message
+// for an invalid mesh.
+nat_bem_status validate_mesh_host(const double* V, int64_t nv, const int32_t* T, int64_t nt);
+void build_near_pairs(const int32_t* T, int64_t nv, int64_t nt, std::vector<int2>& pairs);
+
+// Quadrature tables the kernels read from constant memory (assemble.cu).
+nat_bem_status upload_rules(int adj_levels, int self_pts);
+
+// ------------------------------------------------------------------------------- op
+struct Workspace;  // GMRES state (gmres.cu)
+
+}  // namespace natbem
+
+struct nat_bem_op {
+  int64_t n = 0;
+  double k = 0.0;
+  nat_bem_opts opts{};
+  int device = 0;
+  cudaStream_t stream = nullptr;       // stream the op was built on (frees are ordered there)
+  natbem::Geometry geo;
+  float2* L = nullptr;                 // n x ld complex64, row-major
+  float2* R = nullptr;                 // n x ld complex64, row-major (store_r)
+  uint32_t* Lb = nullptr;              // n x ld complex as packed bf16 pairs (mixed BF16)
+  natbem::Workspace* ws = nullptr;     // solver workspace, grown on demand
+};
+
+namespace natbem {
+
+// assemble.cu
+nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
+                              const std::vector<int2>& near_pairs, cudaStream_t s);
+nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s);
+
+// gmres.cu
+nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
+                          nat_bem_solve_info* info, cudaStream_t s);
+void workspace_free(Workspace* ws, cudaStream_t s);
+int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o);
+
+// eval.cu
+nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
+                         const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                         cudaStream_t s);
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace natbem

@@ -1,0 +1,98 @@
+// Launch counting and optional per-launch CUDA-event timing (tracing for benchmarks).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace natbem {
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<int> g_trace{0};
+std::mutex g_mu;
+struct Rec {
+  const char* name;
+  cudaEvent_t a, b;
+};
+std::vector<Rec> g_recs;
+std::vector<cudaEvent_t> g_free;
+
+cudaEvent_t get_event() {
+  if (!g_free.empty()) {
+    cudaEvent_t e = g_free.back();
+    g_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+TraceScope::TraceScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (g_trace.load(std::memory_order_relaxed)) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    a_ = get_event();
+    b_ = get_event();
+    cudaEventRecord((cudaEvent_t)a_, s_);
+  }
+}
+
+TraceScope::~TraceScope() {
+  if (a_) {
+    cudaEventRecord((cudaEvent_t)b_, s_);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_recs.push_back({name_, (cudaEvent_t)a_, (cudaEvent_t)b_});
+  }
+}
+
+}  // namespace natbem
+
+using namespace natbem;
+
+extern "C" {
+
+void nat_bem_trace_enable(int32_t enable) { g_trace.store(enable ? 1 : 0); }
+
+void nat_bem_trace_reset(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  for (auto& r : g_recs) {
+    cudaEventSynchronize(r.b);
+    g_free.push_back(r.a);
+    g_free.push_back(r.b);
+  }
+  g_recs.clear();
+  g_launches.store(0);
+}
+
+int64_t nat_bem_trace_launches(void) { return g_launches.load(); }
+
+nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms, int64_t* launches) {
+  clear_error();
+  std::lock_guard<std::mutex> lk(g_mu);
+  double t = 0.0;
+  int64_t c = 0;
+  const std::string want = name ? name : "";
+  for (auto& r : g_recs) {
+    if (!want.empty() && std::string(r.name).find(want) == std::string::npos) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      set_error(std::string("trace: ") + cudaGetErrorString(e));
+      return NAT_BEM_ECUDA;
+    }
+    t += ms;
+    ++c;
+  }
+  if (total_ms) *total_ms = t;
+  if (launches) *launches = c;
+  return NAT_BEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+"""The C-ABI library loads, exports every symbol include/nat_bem.h declares, and rejects bad
+arguments and invalid meshes on the host before any device work (CPU only: no compute calls)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import synthetic as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def nb():
+    from paper_2506_06190_gb300 import build
+    build.build()
+    import paper_2506_06190_gb300 as nb
+    return nb
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "nat_bem.h")).read()
+    return sorted(set(re.findall(r"NAT_BEM_API\s+[\w\s\*]*?\b(nat_bem_\w+)\s*\(", hdr)))
+
+
+def test_header_declares_the_binding_names(nb):
+    assert _declared() == sorted(nb.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(nb):
+    out = subprocess.run(["nm", "-D", "--defined-only", nb.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT\s+(nat_bem_\w+)", out))
+    for name in _declared():
+        assert name in exported, name
+        assert hasattr(nb.lib(), name)
+
+
+def test_opts_defaults(nb):
+    o = nb.nat_bem_opts_default()
+    assert o.adj_subdiv_levels == 2 and o.self_theta_pts == 16
+    assert o.tol == 1e-6 and o.max_iter == 200 and o.prec == nb.PREC_FP32
+    assert o.inner_max_iter == 60 and o.inner_tol == 1e-3 and o.max_refinements == 10
+
+
+def test_required_bytes(nb):
+    n = 10240
+    b = nb.nat_bem_required_bytes(n, 1)
+    ld = (n + 31) // 32 * 32
+    assert b >= 16 * n * ld                       # L and R in complex64
+    assert b < 16 * n * ld * 1.2
+    assert nb.nat_bem_required_bytes(n, 64) > b
+    assert nb.nat_bem_required_bytes(0, 1) == 0
+
+
+def _assemble_status(nb, V, F, k=2.0, opts=None):
+    op = ctypes.c_void_p()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    st = nb.lib().nat_bem_assemble(ctypes.c_void_p(V.ctypes.data), V.shape[0],
+                                   ctypes.c_void_p(F.ctypes.data), F.shape[0], k,
+                                   ctypes.byref(opts) if opts else None, None, ctypes.byref(op))
+    return st, op
+
+
+@pytest.mark.parametrize("case", ["inward", "open", "flipped_one", "index", "nan", "degenerate",
+                                  "k_zero", "k_nan", "empty", "bad_levels", "bad_maxit"])
+def test_assemble_rejects_bad_input(nb, case):
+    V, F = S.icosphere(1)
+    k, opts = 2.0, None
+    if case == "inward":
+        F = F[:, ::-1]
+    elif case == "open":
+        F = F[:-1]
+    elif case == "flipped_one":
+        F = F.copy(); F[3, 1], F[3, 2] = F[3, 2], F[3, 1]
+    elif case == "index":
+        F = F.copy(); F[0, 0] = V.shape[0] + 5
+    elif case == "nan":
+        V = V.copy(); V[2, 1] = np.nan
+    elif case == "degenerate":
+        V = V.copy(); V[F[0, 1]] = V[F[0, 0]]
+    elif case == "k_zero":
+        k = 0.0
+    elif case == "k_nan":
+        k = float("nan")
+    elif case == "empty":
+        F = F[:0]
+    elif case == "bad_levels":
+        opts = nb.nat_bem_opts_default(adj_subdiv_levels=7)
+    elif case == "bad_maxit":
+        opts = nb.nat_bem_opts_default(max_iter=0)
+    st, op = _assemble_status(nb, V, F, k, opts)
+    assert st == nb.NAT_BEM_EINVAL and not op.value
+    assert len(nb.nat_bem_last_error()) > 0
+
+
+def test_solve_and_eval_reject_null(nb):
+    L = nb.lib()
+    assert L.nat_bem_solve(None, None, 1, None, None, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_eval(None, None, 4, None, None, 1, None, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_op_rows(None, 0, 0, 1, None, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_op_size(None) == 0
+    L.nat_bem_destroy(None)
+
+
+def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
+    import paper_2506_06190_gb300 as nb
+    monkeypatch.setattr(nb, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(nb, "_lib", None)
+    with pytest.raises(ImportError):
+        nb.lib()

@@ -1,0 +1,183 @@
+"""GPU path against the FP64 oracle, element by element, through the C ABI (needs a GB300).
+
+Tolerances (from the arithmetic, stated where used):
+  * operator rows: relative L2 per row <= 1e-5. The regular entries are FP32 kernel values
+    summed over 7 points (about 40 FP32 operations each, relative rounding ~1e-6) with the
+    phase reduced to [-pi, pi] and taken from the hardware sine/cosine (absolute error ~4e-7);
+    the self and vertex-sharing entries are FP64 rounded once to complex64 (~6e-8).
+  * surface and field pressure: relative L2 <= 1e-4, the accuracy target of the solver. The
+    GPU solve stops at a relative residual of 1e-6 against an FP32 operator; the oracle solves
+    to 1e-12 in FP64.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+SOL_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import torch
+    assert torch.cuda.is_available(), "these tests need a CUDA GPU"
+    from paper_2506_06190_gb300 import build
+    build.build()
+    import paper_2506_06190_gb300 as nb
+    return nb
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _rowwise(gpu, ref):
+    return np.linalg.norm(gpu - ref, axis=1) / np.linalg.norm(ref, axis=1)
+
+
+@pytest.mark.parametrize("mesh", ["tetrahedron", "octahedron", "ico1", "ring1000"])
+@pytest.mark.parametrize("k", [0.7, 4.0])
+def test_operator_entries(nb, oracle_lib, mesh, k):
+    V, F = {"tetrahedron": S.tetrahedron, "octahedron": S.octahedron,
+            "ico1": lambda: S.icosphere(1), "ring1000": lambda: S.ring_sphere(1000)}[mesh]()
+    if mesh == "ring1000":
+        V = S.perturbed_ellipsoid(V, 11)
+    L, R = oracle_lib.assemble(V, F, k)
+    with nb.Operator.assemble(V, F, k) as op:
+        Lg = op.rows(0, 0, op.n).astype(np.complex128)
+        Rg = op.rows(1, 0, op.n).astype(np.complex128)
+    assert np.max(_rowwise(Lg, L)) < OP_TOL
+    assert np.max(_rowwise(Rg, R)) < OP_TOL
+    # the self and vertex-sharing entries (FP64 on the GPU) are accurate to complex64 rounding
+    near = np.array([[len(set(F[i]) & set(F[j])) > 0 for j in range(len(F))] for i in range(len(F))])
+    assert np.max(np.abs(Lg - L)[near] / np.abs(L)[near]) < 1e-6
+    assert np.max(np.abs(Rg - R)[near] / np.abs(R)[near]) < 1e-6
+
+
+def test_pulsating_sphere_solve_and_field(nb, oracle_lib):
+    prob = S.pulsating_sphere()
+    V, F, k = prob.V, prob.F, float(prob.ks[0])
+    g = prob.neumann[0][:, 0]
+    p_ref, info_ref = oracle_lib.solve(V, F, k, g)
+    f_ref = oracle_lib.evaluate(V, F, k, prob.points, p_ref, g)
+    with nb.Operator.assemble(V, F, k) as op:
+        rows = np.arange(0, op.n, 97)
+        Lg = op.rows(0, 0, op.n).astype(np.complex128)
+        assert np.max(_rowwise(Lg[rows], info_ref["L"][rows])) < OP_TOL
+        p, info, st = op.solve(g)
+        assert st == nb.NAT_BEM_OK and info.rel_residual < 1e-5 and info.iterations > 0
+        fld = op.evaluate(prob.points, p, g)
+    assert _rel(p, p_ref) < SOL_TOL
+    assert _rel(fld, f_ref) < SOL_TOL
+    # discretisation error against the closed form is the oracle's (about 1.7% here)
+    exact = 1.0 / (1j * k - 1.0)
+    assert _rel(p, np.full_like(p_ref, exact)) < 0.03
+
+
+@pytest.mark.parametrize("n_tri", [576, 1000, 2306])
+def test_ragged_sizes_interior_source(nb, oracle_lib, n_tri):
+    """Triangle counts that are not multiples of the 32-column padding or of the tiles."""
+    Vs, F = S.ring_sphere(n_tri)
+    V = S.perturbed_ellipsoid(Vs, 2000 + n_tri)
+    k = 5.3
+    g = S.monopole_neumann(V, F, k)
+    pts = S.fibonacci_points(77, 4.0)
+    p_ref, _ = oracle_lib.solve(V, F, k, g)
+    f_ref = oracle_lib.evaluate(V, F, k, pts, p_ref, g)
+    with nb.Operator.assemble(V, F, k) as op:
+        p, info, st = op.solve(g)
+        assert st == nb.NAT_BEM_OK
+        fld = op.evaluate(pts, p, g)
+    assert _rel(p, p_ref) < SOL_TOL
+    assert _rel(fld, f_ref) < SOL_TOL
+
+
+def test_multi_rhs_matches_oracle_and_single(nb, oracle_lib):
+    Vs, F = S.ring_sphere(800)
+    V = S.perturbed_ellipsoid(Vs, 7)
+    k = 3.1
+    G = S.sh_neumann(V, F, 5, 99)
+    pts = S.shell_points(64, 2.0, 5.0, 1)
+    L, R = oracle_lib.assemble(V, F, k)
+    with nb.Operator.assemble(V, F, k) as op:
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK
+        fld = op.evaluate(pts, P, G)
+        for s in range(G.shape[1]):
+            p_ref = np.linalg.solve(L, R @ G[:, s])
+            assert _rel(P[:, s], p_ref) < SOL_TOL
+            f_ref = oracle_lib.evaluate(V, F, k, pts, p_ref, G[:, s])
+            assert _rel(fld[:, s], f_ref) < SOL_TOL
+        # batch invariance: each RHS alone gives the same bits as inside the block
+        for s in (0, 3):
+            p1, _, _ = op.solve(G[:, s])
+            assert np.array_equal(p1, P[:, s])
+
+
+def test_device_pointers_match_host(nb):
+    import torch
+    V, F = S.icosphere(2)
+    k = 2.2
+    g = S.cos_theta_neumann(V, F).astype(np.complex64)
+    pts = S.fibonacci_points(40, 3.0)
+    with nb.Operator.assemble(V, F, k) as op:
+        p_h, _, _ = op.solve(g)
+        f_h = op.evaluate(pts, p_h, g)
+    Vd, Fd = torch.from_numpy(V).cuda(), torch.from_numpy(F).cuda()
+    gd = torch.from_numpy(g).cuda()
+    with nb.Operator.assemble(Vd, Fd, k) as op:
+        p_d, _, _ = op.solve(gd)
+        f_d = op.evaluate(torch.from_numpy(pts).cuda(), p_d, gd)
+        torch.cuda.synchronize()
+    assert np.array_equal(p_d.cpu().numpy(), p_h)
+    assert np.array_equal(f_d.cpu().numpy(), f_h)
+
+
+def test_nonconvergence_reports_enoconv(nb, oracle_lib):
+    V, F = S.icosphere(2)
+    opts = nb.nat_bem_opts_default(max_iter=2)
+    g = S.uniform_neumann(F)
+    with nb.Operator.assemble(V, F, 6.0, opts) as op:
+        p, info, st = op.solve(g)
+    assert st == nb.NAT_BEM_ENOCONV and info.iterations == 2
+    assert info.rel_residual > 1e-6 and np.all(np.isfinite(p))
+
+
+def test_empty_field_and_errors(nb):
+    V, F = S.icosphere(1)
+    with nb.Operator.assemble(V, F, 1.0) as op:
+        g = S.uniform_neumann(F)
+        p, _, _ = op.solve(g)
+        out = op.evaluate(np.zeros((0, 3)), p, g)
+        assert out.shape[0] == 0
+        with pytest.raises(nb.NatBemError):
+            nb.nat_bem_op_rows(op.handle, 0, op.n - 1, 5)
+
+
+@pytest.mark.parametrize("ka", [0.5, 20.0])
+def test_full_size_interior_source(nb, oracle_lib, ka):
+    """The 10240-triangle interior-source mesh as the bench runs it: sampled operator rows
+    against the oracle, the GPU solution against the oracle's full solve, the field at all
+    1024 points, and the discretisation error against the exact monopole field."""
+    prob = S.interior_source(n_k=1)
+    V, F = prob.V, prob.F
+    k = ka
+    g = S.monopole_neumann(V, F, k)
+    rows = np.unique(np.concatenate([np.arange(0, len(F), 331), [len(F) - 1]]))
+    Lr, Rr = oracle_lib.assemble_rows(V, F, k, rows)
+    with nb.Operator.assemble(V, F, k) as op:
+        Lg = np.concatenate([op.rows(0, int(r), 1) for r in rows]).astype(np.complex128)
+        Rg = np.concatenate([op.rows(1, int(r), 1) for r in rows]).astype(np.complex128)
+        p, info, st = op.solve(g)
+        assert st == nb.NAT_BEM_OK
+        fld = op.evaluate(prob.points, p, g)
+    assert np.max(_rowwise(Lg, Lr)) < OP_TOL and np.max(_rowwise(Rg, Rr)) < OP_TOL
+    p_ref, info_ref = oracle_lib.solve(V, F, k, g, tol=1e-10)
+    assert _rel(p, p_ref) < SOL_TOL
+    f_ref = oracle_lib.evaluate(V, F, k, prob.points, p_ref, g)
+    assert _rel(fld, f_ref) < SOL_TOL
+    c, _, _ = oracle_lib.geometry(V, F)
+    assert _rel(p, S.monopole_field(c, k)) < 0.1
