@@ -255,6 +255,8 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
     const size_t mat = (size_t)nt * (size_t)op->geo.ld;
     if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
     if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
+    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
+      return fail(st);
     if ((st = assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
     *out = op;
     return NAT_BEM_OK;

@@ -19,6 +19,7 @@
 //   dG/dn_y + beta H = G/r^2 [ (d.n_y - b/k) + i (a/k - rho d.n_y) ],
 //       a = (rho^2 - 3) q + n_x.n_y,   b = rho (3 q - n_x.n_y),
 //   G + beta dG/dn_x = G [ 1 - d.n_x / r - i d.n_x / (k r^2) ].
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -199,6 +200,12 @@ __device__ __forceinline__ bool shares_vertex(int4 a, int4 b) {
          a.z == b.x || a.z == b.y || a.z == b.z;
 }
 
+// complex value as two bf16 (real in the low half), round to nearest even
+__device__ __forceinline__ uint32_t pack_bf16(float re, float im) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(re, im);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
 constexpr int kRegThreads = 256;  // source columns per block
 constexpr int kRowStage = 64;     // collocation rows staged in shared memory at a time
 
@@ -208,7 +215,7 @@ __global__ void __launch_bounds__(kRegThreads)
 k_assemble_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
                    const float4* __restrict__ nrm, const float4* __restrict__ qp,
                    const int4* __restrict__ vid, int n, int ld, int rows_per_block, float k,
-                   float2* __restrict__ L, float2* __restrict__ R) {
+                   float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb) {
   __shared__ float4 s_hi[kRowStage], s_lo[kRowStage], s_n[kRowStage];
   __shared__ int4 s_v[kRowStage];
   const int j = blockIdx.x * kRegThreads + threadIdx.x;
@@ -251,6 +258,7 @@ k_assemble_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c
       if (col_pad) {
         L[off] = make_float2(0.f, 0.f);
         R[off] = make_float2(0.f, 0.f);
+        if (Lb) Lb[off] = 0u;
         continue;
       }
       if (!col_ok) continue;
@@ -296,6 +304,7 @@ k_assemble_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c
       }
       __stcs(L + off, make_float2(-Lr, -Li));
       __stcs(R + off, make_float2(-Rr, -Ri));
+      if (Lb) __stcs(Lb + off, pack_bf16(-Lr, -Li));
     }
   }
 }
@@ -323,7 +332,7 @@ __global__ void __launch_bounds__(256)
 k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
                 const double* __restrict__ cen, const double* __restrict__ nrm64,
                 const double* __restrict__ area, int ld, double k, float2* __restrict__ L,
-                float2* __restrict__ R) {
+                float2* __restrict__ R, uint32_t* __restrict__ Lb) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_pairs) return;
@@ -419,6 +428,7 @@ k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* _
   if (lane == 0) {
     L[(size_t)i * ld + j] = make_float2((float)Lre, (float)Lim);
     R[(size_t)i * ld + j] = make_float2((float)Rre, (float)Rim);
+    if (Lb) Lb[(size_t)i * ld + j] = pack_bf16((float)Lre, (float)Lim);
   }
 }
 
@@ -457,13 +467,13 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
   dim3 grid(col_blocks, row_blocks);
   NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld,
-                                                  rows_per_block, (float)op->k, op->L, op->R));
+                                                  rows_per_block, (float)op->k, op->L, op->R, op->Lb));
   NB_CHECK_LAUNCH();
   // near pairs overwrite the entries the regular kernel skipped
   const int64_t threads = 256, warps_per_block = threads / 32;
   const int64_t blocks = (g.n_near + warps_per_block - 1) / warps_per_block;
   NB_LAUNCH("assemble_near", s, k_assemble_near<<<(unsigned)blocks, (unsigned)threads, 0, s>>>(
-      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R));
+      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
   NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
 }

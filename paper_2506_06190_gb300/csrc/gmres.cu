@@ -35,14 +35,18 @@ struct Workspace {
   double2 *y = nullptr, *part = nullptr;
   double *cs = nullptr, *partn = nullptr, *bnorm = nullptr, *res = nullptr, *hnorm = nullptr;
   double* res_true = nullptr;
+  double2 *b0 = nullptr, *xacc = nullptr;  // refinement: R g and the accumulated solution
   float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
   int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
+  int* outer_done = nullptr;                               // refinement: converged RHS
   unsigned* cnt = nullptr;
   int* host_scal = nullptr;  // pinned mirror of scal[0..1]
 };
 
 struct GArgs {
   int n, ld, nrhs, m, nchunk;
+  int maxit;           // iteration cap of this GMRES run (<= m)
+  const int* skip;     // RHS to leave alone in this run (refinement), or null
   const float2* L;
   double2 *b, *V, *w, *x, *H, *hcol, *htmp, *sn, *gv, *y, *part;
   double *cs, *partn, *bnorm, *res, *hnorm, *res_true;
@@ -174,6 +178,78 @@ k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x
   }
 }
 
+// The same product with A stored as packed bf16 complex pairs (real in the low half): half
+// the bytes of the FP32 operator; products and partial sums in FP32, then FP64.
+template <int kRows, int kUnroll>
+__global__ void __launch_bounds__(256)
+k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
+            int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+            const int* __restrict__ scal) {
+  __shared__ double sh[2 * kRows][8];
+  if (scal && scal[1]) return;
+  const int s = blockIdx.y;
+  if (done && done[s]) return;
+  const int row0 = blockIdx.x * kRows;
+  const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
+  const uint4* a[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r)
+    a[r] = reinterpret_cast<const uint4*>(A + (size_t)min(row0 + r, n - 1) * ld);
+  const int n4 = ld >> 2;  // four complex per 16 bytes
+  double accr[kRows], acci[kRows];
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) accr[r] = acci[r] = 0.0;
+  for (int base = threadIdx.x; base < n4; base += 256 * kUnroll) {
+    float pr[kRows], pi[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) pr[r] = pi[r] = 0.f;
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const int idx = base + u * 256;
+      if (idx < n4) {
+        const float4 x0 = __ldg(xv + 2 * idx), x1 = __ldg(xv + 2 * idx + 1);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const uint4 q = __ldcs(a[r] + idx);
+          const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+          const float xr[4] = {x0.x, x0.z, x1.x, x1.z}, xi[4] = {x0.y, x0.w, x1.y, x1.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float ar = __uint_as_float(w[e] << 16), ai = __uint_as_float(w[e] & 0xffff0000u);
+            pr[r] = fmaf(ar, xr[e], fmaf(-ai, xi[e], pr[r]));
+            pi[r] = fmaf(ar, xi[e], fmaf(ai, xr[e], pi[r]));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      accr[r] += pr[r];
+      acci[r] += pi[r];
+    }
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    accr[r] = warp_sum(accr[r]);
+    acci[r] = warp_sum(acci[r]);
+    if (lane == 0) {
+      sh[2 * r][wid] = accr[r];
+      sh[2 * r + 1][wid] = acci[r];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
+    const int r = threadIdx.x;
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      sr += sh[2 * r][q];
+      si += sh[2 * r + 1][q];
+    }
+    y[(size_t)s * ystride + row0 + r] = make_double2(sr, si);
+  }
+}
+
 // ------------------------------------------------------------------------ GMRES steps
 // ||b_s|| (partials + last block per RHS); w_s = b_s; h_{0,-1} := ||b_s||, g_s[0] = ||b_s||.
 __global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
@@ -198,7 +274,7 @@ __global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
     a.gv[(size_t)s * (a.m + 1)] = make_double2(bn, 0.0);
     a.res[s] = bn;
     a.iters[s] = 0;
-    a.done[s] = (bn == 0.0);
+    a.done[s] = (bn == 0.0) || (a.skip && a.skip[s]);
     __threadfence();
     const unsigned t2 = atomicAdd((unsigned*)&a.scal[2], 1u);
     if (t2 == (unsigned)a.nrhs - 1) {
@@ -206,7 +282,7 @@ __global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
       int all = 1;
       for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
       a.scal[0] = 0;
-      a.scal[1] = all || a.m == 0;
+      a.scal[1] = all || a.maxit == 0;
     }
   }
 }
@@ -403,7 +479,7 @@ __global__ void __launch_bounds__(kChunk) k_update_norm(GArgs a) {
     for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
     const int jn = j + 1;
     a.scal[0] = jn;
-    a.scal[1] = all || jn >= a.m;
+    a.scal[1] = all || jn >= a.maxit;
   }
 }
 
@@ -432,14 +508,15 @@ __global__ void k_lsq(GArgs a) {
   }
 }
 
-// x = V y (FP64) and the complex64 output; also the FP32 copy of x for the residual matvec.
-__global__ void __launch_bounds__(kChunk) k_xupdate(GArgs a, float2* __restrict__ pout) {
+// x = V y (FP64), or x += V y when `accumulate` (refinement), with the complex64 output and
+// the FP32 copy of x for the residual matvec.
+__global__ void __launch_bounds__(kChunk) k_xupdate(GArgs a, float2* __restrict__ pout, int accumulate) {
   const int s = blockIdx.y;
   const int r = blockIdx.x * kChunk + threadIdx.x;
   if (r >= a.n) return;
-  const int kdim = a.iters[s];
+  const int kdim = (a.skip && a.skip[s]) ? 0 : a.iters[s];
   const double2* y = a.y + (size_t)s * a.m;
-  double2 acc = make_double2(0.0, 0.0);
+  double2 acc = accumulate ? a.x[(size_t)s * a.n + r] : make_double2(0.0, 0.0);
   for (int c = 0; c < kdim; ++c) acc = cadd(acc, cmul(a.V[vidx(a, c, s) + r], y[c]));
   a.x[(size_t)s * a.n + r] = acc;
   pout[(size_t)s * a.n + r] = make_float2((float)acc.x, (float)acc.y);
@@ -463,6 +540,41 @@ __global__ void __launch_bounds__(kChunk) k_resid(GArgs a) {
   }
 }
 
+// Refinement residual: b = b0 - w (w = L x with the FP32 operator) for the RHS not yet
+// converged, ||b0 - w|| / ||b0|| into res_true and the outer convergence flags.
+__global__ void __launch_bounds__(kChunk) k_ir_residual(GArgs a, const double2* __restrict__ b0,
+                                                        int* __restrict__ outer_done, double tol) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int r = chunk * kChunk + threadIdx.x;
+  const bool active = !outer_done[s];
+  double v = 0.0, vb = 0.0;
+  if (active && r < a.n) {
+    const double2 bb = b0[(size_t)s * a.n + r];
+    const double2 rr = csub(bb, a.w[(size_t)s * a.n + r]);
+    a.b[(size_t)s * a.n + r] = rr;
+    v = cabs2(rr);
+    vb = cabs2(bb);
+  }
+  v = block_sum(v, sh);
+  vb = block_sum(vb, sh);
+  if (threadIdx.x == 0) {
+    a.partn[(size_t)chunk * a.nrhs + s] = v;
+    a.part[(size_t)chunk * a.nrhs + s] = make_double2(vb, 0.0);
+  }
+  if (!last_block(a.cnt + s * kCounters + 5, gridDim.x)) return;
+  if (threadIdx.x == 0 && active) {
+    double t = 0.0, tb = 0.0;
+    for (int c = 0; c < a.nchunk; ++c) {
+      t += a.partn[(size_t)c * a.nrhs + s];
+      tb += a.part[(size_t)c * a.nrhs + s].x;
+    }
+    const double rel = tb > 0.0 ? sqrt(t / tb) : 0.0;
+    a.res_true[s] = rel;
+    if (rel <= tol) outer_done[s] = 1;
+  }
+}
+
 // complex64 (n) -> padded complex64 (ld), zero pad
 __global__ void k_pad_copy(const float2* __restrict__ src, int n, int ld, int nrhs,
                            float2* __restrict__ dst) {
@@ -478,7 +590,7 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   const int64_t ld = round_up(n, 32);
   const int64_t nchunk = (n + kChunk - 1) / kChunk;
   int64_t b = 0;
-  b += 16 * n * nrhs * 3;                 // b, w, x
+  b += 16 * n * nrhs * 5;                 // b, w, x, b0, xacc
   b += 16 * n * nrhs * (m + 1);           // V
   b += 8 * ld * nrhs * 3;                 // xf, gin, pout
   b += 16 * nrhs * (m + 1) * (m + 4);     // H, hcol, htmp, gv, sn, y
@@ -490,7 +602,8 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   if (!ws) return;
   void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
-                  ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt};
+                  ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
+                  ws->b0, ws->xacc, ws->outer_done};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -538,6 +651,9 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->iters, nr, s));
   NB_TRY(dev_alloc_n(&ws->scal, 4, s));
   NB_TRY(dev_alloc_n(&ws->cnt, nr * kCounters, s));
+  NB_TRY(dev_alloc_n(&ws->b0, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->xacc, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->outer_done, nr, s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->cnt, 0, nr * kCounters * sizeof(unsigned), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->scal, 0, 4 * sizeof(int), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->xf, 0, ld * nr * sizeof(float2), s));
@@ -576,6 +692,8 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
   a.scal = ws->scal;
   a.cnt = ws->cnt;
   a.tol = op->opts.tol;
+  a.maxit = ws->m;
+  a.skip = nullptr;
   return a;
 }
 
@@ -589,31 +707,35 @@ static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, con
   return NAT_BEM_OK;
 }
 
-nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
-                          nat_bem_solve_info* info, cudaStream_t s) {
-  NB_TRY(workspace_ensure(op, nrhs, s));
-  Workspace* ws = op->ws;
-  const int n = (int)op->n, ld = (int)op->geo.ld;
-  GArgs a = make_args(op, ws, op->L);
+static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int ld,
+                                const float2* x, double2* y, int nrhs, const int* done,
+                                const int* scal, cudaStream_t s) {
+  constexpr int kRows = 2;
+  dim3 grid((n + kRows - 1) / kRows, nrhs);
+  NB_LAUNCH(name, s, k_gemv_bf16<kRows, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+// One GMRES run on the right-hand sides in a.b (x0 = 0): init, iterations until every RHS
+// converged or a.maxit, least squares, and x = V y (or x += V y with `accumulate`) into a.x,
+// pout and the FP32 copy a.xf. `bf16` selects the operator copy used for the matvec.
+static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, bool bf16,
+                                int accumulate, float2* pout, cudaStream_t s) {
+  const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
   const dim3 vec_grid(ws->nchunk, nrhs);
-  // b = R g
-  {
-    const int64_t tot = (int64_t)ld * nrhs;
-    NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, n, ld, nrhs, ws->gin));
-    NB_CHECK_LAUNCH();
-    NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s));
-  }
   NB_LAUNCH("gmres_init", s, k_init<<<vec_grid, kChunk, 0, s>>>(a));
   NB_CHECK_LAUNCH();
-  const int m = ws->m;
-  const dim3 dots_grid(ws->nchunk, (m + 1 + kColGroup - 1) / kColGroup, nrhs);
-  int it = 0;
-  int chunk = 16;
-  while (it < m) {
-    const int c = std::min(chunk, m - it);
+  const dim3 dots_grid(ws->nchunk, (a.maxit + 1 + kColGroup - 1) / kColGroup, nrhs);
+  int it = 0, chunk = 16;
+  while (it < a.maxit) {
+    const int c = std::min(chunk, a.maxit - it);
     for (int q = 0; q < c; ++q) {
       NB_LAUNCH("gmres_normalize", s, k_normalize<<<vec_grid, kChunk, 0, s>>>(a));
-      NB_TRY(gemv("gemv", op->L, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
+      if (bf16)
+        NB_TRY(gemv_bf16("gemv_bf16", op->Lb, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
+      else
+        NB_TRY(gemv("gemv", op->L, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
       NB_LAUNCH("gmres_dots", s, k_dots<<<dots_grid, kChunk, 0, s>>>(a));
       NB_LAUNCH("gmres_update_dots", s, k_update_dots<<<vec_grid, kChunk, 0, s>>>(a));
       NB_LAUNCH("gmres_update_norm", s, k_update_norm<<<vec_grid, kChunk, 0, s>>>(a));
@@ -626,32 +748,94 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     chunk = 8;
   }
   NB_LAUNCH("gmres_lsq", s, k_lsq<<<nrhs, 32, 0, s>>>(a));
-  NB_LAUNCH("gmres_xupdate", s, k_xupdate<<<vec_grid, kChunk, 0, s>>>(a, d_p));
+  NB_LAUNCH("gmres_xupdate", s, k_xupdate<<<vec_grid, kChunk, 0, s>>>(a, pout, accumulate));
   NB_CHECK_LAUNCH();
-  // true residual ||R g - L p|| / ||R g|| with the FP32 operator
-  NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
-  NB_LAUNCH("gmres_resid", s, k_resid<<<vec_grid, kChunk, 0, s>>>(a));
-  NB_CHECK_LAUNCH();
-  std::vector<int> iters(nrhs), done(nrhs);
+  return NAT_BEM_OK;
+}
+
+nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
+                          nat_bem_solve_info* info, cudaStream_t s) {
+  NB_TRY(workspace_ensure(op, nrhs, s));
+  Workspace* ws = op->ws;
+  const nat_bem_opts& o = op->opts;
+  const int n = (int)op->n, ld = (int)op->geo.ld;
+  const dim3 vec_grid(ws->nchunk, nrhs);
+  // b = R g
+  {
+    const int64_t tot = (int64_t)ld * nrhs;
+    NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, n, ld, nrhs, ws->gin));
+    NB_CHECK_LAUNCH();
+    NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s));
+  }
+  std::vector<int> iters(nrhs), done(nrhs), total(nrhs, 0);
   std::vector<double> rt(nrhs);
-  NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-  NB_TRY_CUDA(cudaMemcpyAsync(done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-  NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-  NB_TRY_CUDA(cudaStreamSynchronize(s));
-  int maxit = 0, all_done = 1;
+  int refinements = 0;
+  bool converged = true;
+  const bool mixed = o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb != nullptr;
+  if (!mixed) {
+    GArgs a = make_args(op, ws, op->L);
+    a.maxit = o.max_iter;
+    NB_TRY(gmres_run(op, ws, a, false, 0, d_p, s));
+    // true residual ||R g - L p|| / ||R g|| with the FP32 operator
+    NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
+    NB_LAUNCH("gmres_resid", s, k_resid<<<vec_grid, kChunk, 0, s>>>(a));
+    NB_CHECK_LAUNCH();
+    NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaMemcpyAsync(done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int q = 0; q < nrhs; ++q) {
+      total[q] = iters[q];
+      converged = converged && done[q];
+    }
+  } else {
+    // Mixed precision iterative refinement: inner GMRES on the BF16 copy of L to inner_tol,
+    // x += d in FP64, residual b0 - L x with the FP32 operator and FP64 sums.
+    NB_TRY_CUDA(cudaMemcpyAsync(ws->b0, ws->b, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+    NB_TRY_CUDA(cudaMemsetAsync(ws->xacc, 0, (size_t)n * nrhs * sizeof(double2), s));
+    NB_TRY_CUDA(cudaMemsetAsync(ws->outer_done, 0, nrhs * sizeof(int), s));
+    GArgs a = make_args(op, ws, op->L);
+    a.x = ws->xacc;
+    a.skip = ws->outer_done;
+    a.tol = o.inner_tol;
+    int budget = o.max_iter;
+    converged = false;
+    std::vector<int> od(nrhs);
+    for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
+      a.maxit = std::min(o.inner_max_iter, budget);
+      NB_TRY(gmres_run(op, ws, a, true, 1, d_p, s));
+      NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
+      NB_LAUNCH("ir_residual", s, k_ir_residual<<<vec_grid, kChunk, 0, s>>>(a, ws->b0, ws->outer_done, o.tol));
+      NB_CHECK_LAUNCH();
+      NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaMemcpyAsync(od.data(), ws->outer_done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaStreamSynchronize(s));
+      int used = 0;
+      for (int q = 0; q < nrhs; ++q) {
+        total[q] += iters[q];
+        used = std::max(used, iters[q]);
+      }
+      budget -= std::max(used, 1);
+      ++refinements;
+      converged = true;
+      for (int q = 0; q < nrhs; ++q) converged = converged && od[q];
+      if (converged) break;
+    }
+  }
+  int maxit = 0;
   double maxres = 0.0;
   for (int q = 0; q < nrhs; ++q) {
-    maxit = std::max(maxit, iters[q]);
-    all_done &= done[q];
+    maxit = std::max(maxit, total[q]);
     maxres = std::max(maxres, rt[q]);
   }
   if (info) {
     info->iterations = maxit;
-    info->refinements = 0;
+    info->refinements = refinements;
     info->rel_residual = maxres;
   }
-  if (!all_done) {
-    set_error("GMRES did not reach the tolerance within max_iter");
+  if (!converged) {
+    set_error("GMRES did not reach the tolerance within the iteration limits");
     return NAT_BEM_ENOCONV;
   }
   return NAT_BEM_OK;

@@ -181,3 +181,25 @@ def test_full_size_interior_source(nb, oracle_lib, ka):
     assert _rel(fld, f_ref) < SOL_TOL
     c, _, _ = oracle_lib.geometry(V, F)
     assert _rel(p, S.monopole_field(c, k)) < 0.1
+
+
+@pytest.mark.parametrize("ka", [1.0, 12.0])
+def test_mixed_bf16_refinement_matches_oracle(nb, oracle_lib, ka):
+    """Inner GMRES on the BF16 operator copy, refined against the FP32 operator: the same
+    1e-4 bar against the FP64 oracle as the plain path."""
+    Vs, F = S.ring_sphere(2306)
+    V = S.perturbed_ellipsoid(Vs, 5)
+    g = S.monopole_neumann(V, F, ka)
+    G = np.stack([g, S.sh_neumann(V, F, 1, 3)[:, 0]], axis=1)
+    pts = S.fibonacci_points(64, 4.0)
+    L, R = oracle_lib.assemble(V, F, ka)
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16)
+    with nb.Operator.assemble(V, F, ka, opts) as op:
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        assert info.refinements >= 1 and info.rel_residual <= 1e-6
+        fld = op.evaluate(pts, P, G)
+    for s in range(2):
+        p_ref = np.linalg.solve(L, R @ G[:, s])
+        assert _rel(P[:, s], p_ref) < SOL_TOL
+        assert _rel(fld[:, s], oracle_lib.evaluate(V, F, ka, pts, p_ref, G[:, s])) < SOL_TOL
