@@ -97,8 +97,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def workload(n_k: int):
-    return S.interior_source(n_k=n_k)
+def workload(n_k: int, n_tri: int = 10240):
+    return S.interior_source(n_k=n_k, n_tri=n_tri)
 
 
 # ------------------------------------------------------------------------------ GPU arm
@@ -114,7 +114,7 @@ def run_gpu(args, rank: int, world: int):
         nb_build.build()
     if world > 1:
         torch.distributed.barrier()
-    prob = workload(args.n_k)
+    prob = workload(args.n_k, args.n_tri)
     n = prob.F.shape[0]
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
@@ -268,6 +268,7 @@ def main():
     ap.add_argument("--impl", default="natbem", choices=["natbem", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "tf32"])
     ap.add_argument("--n-k", type=int, default=64)
+    ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()
@@ -281,7 +282,7 @@ def main():
             return
         import oracle
         oracle.build()
-        prob = workload(args.n_k)
+        prob = workload(args.n_k, args.n_tri)
         nth = oracle.hardware_threads()
         for w in range(args.warmup):
             cpu_baseline(prob, nth)
@@ -324,7 +325,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": my_rate_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (+f64 near pairs and Krylov)",
         "data": "synthetic",
-        "config": {"workload": "interior_source_10240tri_64k", "n_tri": res["n"],
+        "config": {"workload": f"interior_source_{res['n']}tri_{len(prob.ks)}k", "n_tri": res["n"],
                    "n_wavenumbers": len(prob.ks), "ka_range": [0.5, 20.0], "field_points": 1024,
                    "precision": args.prec, "tol": 1e-6, "max_iter": 200,
                    "l2": "inputs larger than L2: each wavenumber's operators are 2 x 839 MB"},
