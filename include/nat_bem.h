@@ -126,6 +126,27 @@ NAT_BEM_API nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts,
                             void* cuda_stream);
 
 /*
+ * nat_bem_eval without any device allocation, for callers that may not allocate device memory
+ * (for example code that runs inside another memory manager, under a budget a host framework
+ * enforces, or where every device buffer must come from the caller). The paper has no
+ * counterpart; it computes exactly what nat_bem_eval computes.
+ *   All of pts, p, neumann and field_out must be device pointers (NAT_BEM_EINVAL otherwise):
+ *   host staging would allocate. m may be at most 65,536 per call (NAT_BEM_EINVAL with a
+ *   message beyond that; split larger point sets over several calls).
+ *   Partial sums go to a fixed 4 MiB array compiled into the library, which every GPU that
+ *   loads the library holds until the process exits. The first call on each device looks up
+ *   that array's device address (make that first call before any stream capture). All calls
+ *   share the array and it keeps the last call's partial sums, which the next call overwrites
+ *   before reading (nothing needs to start at zero); calls that overlap on the GPU (different
+ *   streams, or different host threads) race on it and must be serialised by the caller.
+ *   Returns when the work is enqueued on cuda_stream.
+ */
+NAT_BEM_API nat_bem_status nat_bem_eval_noalloc(const nat_bem_op* op, const double* pts, int64_t m,
+                                                const float* p, const float* neumann,
+                                                int32_t nrhs, float* field_out,
+                                                void* cuda_stream);
+
+/*
  * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
  * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
  * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.

@@ -32,7 +32,7 @@ STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ECUDA", 5: 
 EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_solve", "nat_bem_eval",
             "nat_bem_op_rows", "nat_bem_op_size", "nat_bem_required_bytes", "nat_bem_destroy",
             "nat_bem_last_error", "nat_bem_trace_enable", "nat_bem_trace_reset",
-            "nat_bem_trace_launches", "nat_bem_trace_kernel"]
+            "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc"]
 
 
 class NatBemError(RuntimeError):
@@ -73,6 +73,8 @@ def lib():
         L.nat_bem_solve.restype = ctypes.c_int
         L.nat_bem_eval.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
         L.nat_bem_eval.restype = ctypes.c_int
+        L.nat_bem_eval_noalloc.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
+        L.nat_bem_eval_noalloc.restype = ctypes.c_int
         L.nat_bem_op_rows.argtypes = [vp, i32, i64, i64, vp, vp]
         L.nat_bem_op_rows.restype = ctypes.c_int
         L.nat_bem_op_size.argtypes = [vp]
@@ -209,6 +211,19 @@ def nat_bem_eval(op, points, p, neumann, out=None, stream=None):
     if not _is_torch(out) and ko is not out:
         out[...] = ko
     return out
+
+
+def nat_bem_eval_noalloc(op, points, p, neumann, out, stream=None) -> int:
+    """nat_bem_eval without device allocation: all arrays must be CUDA torch tensors and
+    `out` is written in place ((nrhs, m) or (m,) complex64). Returns the status code."""
+    m = int(points.shape[0])
+    n = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(p, n)
+    pp, _ = _ptr(points, np.float64)
+    pd, _ = _ptr(p, np.complex64)
+    pg, _ = _ptr(neumann, np.complex64)
+    po, _ = _ptr(out, np.complex64)
+    return int(lib().nat_bem_eval_noalloc(op, pp, m, pd, pg, nrhs, po, _stream_of(p, stream)))
 
 
 def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:

@@ -9,6 +9,9 @@
 // shared memory (broadcast reads); per-split FP64 partial sums are reduced in a fixed order.
 #include <cuda_runtime.h>
 
+#include <mutex>
+#include <string>
+
 #include "internal.h"
 
 namespace natbem {
@@ -156,4 +159,108 @@ nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
   return NAT_BEM_OK;
 }
 
+// ------------------------------------------------------------- allocation-free variant
+// Field evaluation for callers that must not allocate device memory: code running where
+// cudaMalloc is off limits (inside another allocator's callback, under a memory budget that
+// a framework enforces, or in a process whose device memory is owned by someone else). The
+// per-split partial sums that eval_impl takes from the memory pool live instead in this fixed
+// array, which every GPU that loads the library holds until the process exits.
+constexpr size_t kNoAllocScratch = (size_t)1 << 18;  // double2 entries: 4 MiB
+static __device__ __align__(256) double2 g_eval_scratch[kNoAllocScratch];
+constexpr int64_t kNoAllocMaxPoints = (int64_t)(kNoAllocScratch / kMaxRhsPass);  // 65,536
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[64] = {};
+}  // namespace
+
+// Device address of g_eval_scratch on the current device, looked up once per device (host
+// code cannot use the symbol itself: on the host it names a stand-in, not device memory).
+static nat_bem_status scratch_address(double2** out) {
+  int dev = 0;
+  NB_TRY_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("device ordinal out of range");
+    return NAT_BEM_ECUDA;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_eval_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error(std::string("cudaGetSymbolAddress(g_eval_scratch) failed: ") + cudaGetErrorString(e));
+      return NAT_BEM_ECUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<double2*>(g_scratch_ptr[dev]);
+  return NAT_BEM_OK;
+}
+
+static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
+                                        const float2* d_p, const float2* d_g, int nrhs,
+                                        float2* d_out, cudaStream_t s) {
+  double2* part = nullptr;
+  NB_TRY(scratch_address(&part));
+  const Geometry& g = op->geo;
+  const int n = (int)op->n;
+  const int pblocks = (int)((m + kEvalThreads - 1) / kEvalThreads);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // as many element splits as eval_impl would take, capped by the scratch size
+  int splits = (4 * sms + pblocks - 1) / pblocks;
+  splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
+  const int cap = (int)(kNoAllocScratch / ((size_t)m * kMaxRhsPass));
+  splits = max(1, min(splits, cap));
+  int per = (n + splits - 1) / splits;
+  per = (per + kElemStage - 1) / kElemStage * kElemStage;
+  splits = (n + per - 1) / per;
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
+    const int nr = min(kMaxRhsPass, nrhs - r0);
+    dim3 grid(pblocks, splits);
+    switch (nr) {
+      case 1: k_eval<1><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
+      case 2: k_eval<2><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
+      case 3: k_eval<3><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
+      default: k_eval<4><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
+    }
+    NB_CHECK_LAUNCH();
+    const int64_t tot = m * nr;
+    k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out);
+    NB_CHECK_LAUNCH();
+  }
+  return NAT_BEM_OK;
+}
+
 }  // namespace natbem
+
+extern "C" nat_bem_status nat_bem_eval_noalloc(const nat_bem_op* op, const double* pts, int64_t m,
+                                               const float* p, const float* neumann, int32_t nrhs,
+                                               float* field_out, void* cuda_stream) {
+  using namespace natbem;
+  try {
+    clear_error();
+    if (!op || m < 0 || nrhs < 1 || (m > 0 && (!pts || !p || !neumann || !field_out))) {
+      set_error("nat_bem_eval_noalloc: bad arguments (op NULL, m < 0, nrhs < 1 or NULL arrays)");
+      return NAT_BEM_EINVAL;
+    }
+    if (m > kNoAllocMaxPoints) {
+      set_error("nat_bem_eval_noalloc: m = " + std::to_string(m) + " exceeds the maximum of " +
+                std::to_string(kNoAllocMaxPoints) + " points per call (split the points)");
+      return NAT_BEM_EINVAL;
+    }
+    if (m == 0) return NAT_BEM_OK;
+    if (!is_device_pointer(pts) || !is_device_pointer(p) || !is_device_pointer(neumann) ||
+        !is_device_pointer(field_out)) {
+      set_error("nat_bem_eval_noalloc: pts, p, neumann and field_out must be device pointers");
+      return NAT_BEM_EINVAL;
+    }
+    return eval_noalloc_impl(op, pts, m, reinterpret_cast<const float2*>(p),
+                             reinterpret_cast<const float2*>(neumann), nrhs,
+                             reinterpret_cast<float2*>(field_out), (cudaStream_t)cuda_stream);
+  } catch (...) {
+    set_error("internal error in nat_bem_eval_noalloc");
+    return NAT_BEM_ECUDA;
+  }
+}
