@@ -103,6 +103,14 @@ NAT_BEM_API nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, con
                                 nat_bem_op** out);
 
 /*
+ * Re-assembles L and R of an existing op at a new wavenumber k (> 0, finite): the mesh checks,
+ * the device geometry, the operator memory and the solver workspace are reused, so sweeping
+ * the frequencies of one body costs only the element-pair kernels. Work is ordered on
+ * cuda_stream after the op's earlier work on it. NAT_BEM_EINVAL: op NULL or bad k.
+ */
+NAT_BEM_API nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cuda_stream);
+
+/*
  * Solves L p = R g for nrhs right-hand sides (GMRES from p = 0, Sec. 6.1 settings by default).
  *   neumann: nt x nrhs complex64, column-major.  p_out: same layout, receives p.
  *   info: may be NULL.  Blocks until the solve is done.
@@ -147,6 +155,41 @@ NAT_BEM_API nat_bem_status nat_bem_eval_noalloc(const nat_bem_op* op, const doub
                                                 void* cuda_stream);
 
 /*
+ * One solve of a batch: the mesh, the wavenumber, the Neumann data (nt x nrhs) and the field
+ * points (m x 3, m may be 0) in, the surface pressure (nt x nrhs) and the field (m x nrhs)
+ * out, with the job's solve info and status. Arrays follow the conventions above (host or
+ * device). Jobs may share a mesh: pass the same verts / tris pointers.
+ */
+typedef struct {
+  const double* verts;
+  int64_t nv;
+  const int32_t* tris;
+  int64_t nt;
+  double k;
+  const float* neumann;
+  int32_t nrhs;
+  const double* pts;
+  int64_t m;
+  float* p_out;
+  float* field_out;
+  nat_bem_solve_info info; /* out */
+  nat_bem_status status;   /* out */
+  float device_ms;         /* out: device time from the job's assembly to its field (CUDA events) */
+} nat_bem_job;
+
+/*
+ * Runs njobs solves (assemble, GMRES, field) with `concurrency` workers (1..32), each on its
+ * own stream and op, largest meshes first. A worker that meets the same mesh again re-assembles
+ * its op at the new wavenumber (nat_bem_reassemble) instead of rebuilding it. Work starts after
+ * the caller's earlier work on cuda_stream; the call returns when every job is done. Returns
+ * NAT_BEM_OK when every job succeeded, otherwise the first failing status other than
+ * NAT_BEM_ENOCONV if any, else NAT_BEM_ENOCONV; each job's own status is in jobs[i].status.
+ */
+NAT_BEM_API nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
+                                             const nat_bem_opts* opts, int32_t concurrency,
+                                             void* cuda_stream);
+
+/*
  * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
  * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
  * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.
@@ -174,6 +217,9 @@ NAT_BEM_API void nat_bem_destroy(nat_bem_op* op);
  * The counters are process-wide and not thread-safe against concurrent resets.
  */
 NAT_BEM_API void nat_bem_trace_enable(int32_t enable);
+/* With tracing enabled, record events only for kernels whose name contains one of the
+ * comma-separated substrings in `names` (NULL or "" = every kernel). */
+NAT_BEM_API void nat_bem_trace_select(const char* names);
 NAT_BEM_API void nat_bem_trace_reset(void);
 NAT_BEM_API int64_t nat_bem_trace_launches(void);
 NAT_BEM_API nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms,

@@ -29,10 +29,11 @@ PREC_FP32, PREC_MIXED_TF32, PREC_MIXED_BF16 = 0, 1, 2
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ECUDA", 5: "ETIMEOUT", 6: "EBUSY"}
 
 # every symbol include/nat_bem.h declares
-EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_solve", "nat_bem_eval",
+EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "nat_bem_solve", "nat_bem_eval",
             "nat_bem_op_rows", "nat_bem_op_size", "nat_bem_required_bytes", "nat_bem_destroy",
             "nat_bem_last_error", "nat_bem_trace_enable", "nat_bem_trace_reset",
-            "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc"]
+            "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc",
+            "nat_bem_run_batch", "nat_bem_trace_select"]
 
 
 class NatBemError(RuntimeError):
@@ -53,6 +54,14 @@ class SolveInfo(ctypes.Structure):
                 ("rel_residual", ctypes.c_double)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p),
+                ("nt", ctypes.c_int64), ("k", ctypes.c_double), ("neumann", ctypes.c_void_p),
+                ("nrhs", ctypes.c_int32), ("pts", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("p_out", ctypes.c_void_p), ("field_out", ctypes.c_void_p), ("info", SolveInfo),
+                ("status", ctypes.c_int), ("device_ms", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -69,12 +78,16 @@ def lib():
         L.nat_bem_opts_default.restype = None
         L.nat_bem_assemble.argtypes = [vp, i64, vp, i64, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
         L.nat_bem_assemble.restype = ctypes.c_int
+        L.nat_bem_reassemble.argtypes = [vp, d, vp]
+        L.nat_bem_reassemble.restype = ctypes.c_int
         L.nat_bem_solve.argtypes = [vp, vp, i32, vp, ctypes.POINTER(SolveInfo), vp]
         L.nat_bem_solve.restype = ctypes.c_int
         L.nat_bem_eval.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
         L.nat_bem_eval.restype = ctypes.c_int
         L.nat_bem_eval_noalloc.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp]
         L.nat_bem_eval_noalloc.restype = ctypes.c_int
+        L.nat_bem_run_batch.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Opts), i32, vp]
+        L.nat_bem_run_batch.restype = ctypes.c_int
         L.nat_bem_op_rows.argtypes = [vp, i32, i64, i64, vp, vp]
         L.nat_bem_op_rows.restype = ctypes.c_int
         L.nat_bem_op_size.argtypes = [vp]
@@ -87,6 +100,8 @@ def lib():
         L.nat_bem_last_error.restype = ctypes.c_char_p
         L.nat_bem_trace_enable.argtypes = [i32]
         L.nat_bem_trace_enable.restype = None
+        L.nat_bem_trace_select.argtypes = [ctypes.c_char_p]
+        L.nat_bem_trace_select.restype = None
         L.nat_bem_trace_reset.argtypes = []
         L.nat_bem_trace_reset.restype = None
         L.nat_bem_trace_launches.argtypes = []
@@ -171,6 +186,11 @@ def nat_bem_assemble(V, F, k: float, opts: Opts | None = None, stream=None) -> c
     return op
 
 
+def nat_bem_reassemble(op, k: float, stream=None, like=None):
+    """Re-assemble an op at wavenumber k (same mesh, memory and workspace)."""
+    _check(lib().nat_bem_reassemble(op, float(k), _stream_of(like, stream)))
+
+
 def nat_bem_solve(op, neumann, out=None, stream=None, check=True):
     """Solve L p = R g. Returns (p, SolveInfo, status)."""
     n = int(lib().nat_bem_op_size(op))
@@ -226,6 +246,48 @@ def nat_bem_eval_noalloc(op, points, p, neumann, out, stream=None) -> int:
     return int(lib().nat_bem_eval_noalloc(op, pp, m, pd, pg, nrhs, po, _stream_of(p, stream)))
 
 
+def nat_bem_run_batch(jobs, opts: Opts | None = None, concurrency: int = 3, stream=None):
+    """Run a list of solves. Each job is a dict with V, F, k, neumann and optionally points;
+    arrays are numpy (host) or CUDA torch tensors. Returns (status, per-job list of
+    (p, field, SolveInfo, status))."""
+    keep = []
+    arr = (Job * len(jobs))()
+    outs = []
+    for i, jd in enumerate(jobs):
+        V, F, g = jd["V"], jd["F"], jd["neumann"]
+        pts = jd.get("points")
+        n = int(F.shape[0])
+        nrhs = _nrhs_of(g, n)
+        pv, kv = _ptr(V, np.float64)
+        pt, kt = _ptr(F, np.int32)
+        pg, kg = _ptr(g, np.complex64)
+        torch_out = _is_torch(g)
+        m = 0 if pts is None else int(pts.shape[0])
+        if torch_out:
+            import torch
+            p = torch.empty(tuple(g.shape), dtype=torch.complex64, device=g.device)
+            f = torch.empty((nrhs, m) if g.dim() == 2 else (m,), dtype=torch.complex64, device=g.device)
+        else:
+            p = np.zeros((n, nrhs) if np.ndim(g) == 2 else (n,), dtype=np.complex64, order="F")
+            f = np.zeros((m, nrhs) if np.ndim(g) == 2 else (m,), dtype=np.complex64, order="F")
+        pp, kp = _ptr(p, np.complex64)
+        pf, kf = _ptr(f, np.complex64)
+        if pts is not None:
+            ppt, kpt = _ptr(pts, np.float64)
+        else:
+            ppt, kpt = ctypes.c_void_p(0), None
+        keep += [kv, kt, kg, kp, kf, kpt]
+        arr[i] = Job(pv, int(V.shape[0]), pt, n, float(jd["k"]), pg, nrhs, ppt, m, pp, pf,
+                     SolveInfo(), 0, 0.0)
+        outs.append((p, f))
+    st = lib().nat_bem_run_batch(arr, len(jobs), ctypes.byref(opts) if opts else None,
+                                 int(concurrency), _stream_of(jobs[0]["V"] if jobs else None, stream))
+    res = [(outs[i][0], outs[i][1], arr[i].info, arr[i].status, arr[i].device_ms)
+           for i in range(len(jobs))]
+    del keep
+    return st, res
+
+
 def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:
     n = int(lib().nat_bem_op_size(op))
     out = np.zeros((nrows, n), dtype=np.complex64)
@@ -249,6 +311,10 @@ def nat_bem_last_error() -> str:
 
 def nat_bem_trace_enable(enable: bool = True):
     lib().nat_bem_trace_enable(1 if enable else 0)
+
+
+def nat_bem_trace_select(names: str = ""):
+    lib().nat_bem_trace_select(names.encode())
 
 
 def nat_bem_trace_reset():
@@ -276,6 +342,10 @@ class Operator:
     @classmethod
     def assemble(cls, V, F, k, opts=None, stream=None):
         return cls(nat_bem_assemble(V, F, k, opts, stream), int(F.shape[0]), float(k))
+
+    def reassemble(self, k, stream=None, like=None):
+        nat_bem_reassemble(self.handle, k, stream, like)
+        self.k = float(k)
 
     def solve(self, neumann, out=None, stream=None, check=True):
         return nat_bem_solve(self.handle, neumann, out, stream, check)

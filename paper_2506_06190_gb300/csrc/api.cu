@@ -240,6 +240,13 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
       nat_bem_destroy(op);
       return st;
     };
+    if (cudaStreamCreateWithFlags(&op->aux, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("could not create the op's auxiliary stream");
+      return fail(NAT_BEM_ECUDA);
+    }
     const double* dV = nullptr;
     const int32_t* dT = nullptr;
     double* tV = nullptr;
@@ -383,7 +390,33 @@ void nat_bem_destroy(nat_bem_op* op) {
                   g.near_pairs, op->L, op->R, op->Lb};
   for (void* p : ptrs) dev_free(p, s);
   workspace_free(op->ws, s);
+  if (op->ev_join) {
+    // the auxiliary stream's last work is ordered before `s` through ev_join
+    cudaEventDestroy(op->ev_join);
+  }
+  if (op->ev_fork) cudaEventDestroy(op->ev_fork);
+  if (op->aux) cudaStreamDestroy(op->aux);
   delete op;
+}
+
+nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cuda_stream) {
+  try {
+    clear_error();
+    if (!op) {
+      set_error("nat_bem_reassemble: op is NULL");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) {
+      set_error("k must be positive and finite");
+      return NAT_BEM_EINVAL;
+    }
+    NB_TRY(ensure_rules(op->opts.adj_subdiv_levels, op->opts.self_theta_pts));
+    op->k = k;
+    return assemble_operators(op, (cudaStream_t)cuda_stream);
+  } catch (...) {
+    set_error("internal error in nat_bem_reassemble");
+    return NAT_BEM_ECUDA;
+  }
 }
 
 }  // extern "C"

@@ -323,6 +323,11 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// 2 pi as a double hi/lo pair (Cody & Waite 1980 reduction in FP64)
+constexpr double kTwoPiHi64 = 6.283185307179586;
+constexpr double kTwoPiLo64 = 2.4492935982947064e-16;
+constexpr double kInvTwoPi64 = 0.15915494309189535;
+
 }  // namespace
 
 // One warp per (i, j) pair from the near list: j == i (analytic radial integration in polar
@@ -361,8 +366,13 @@ k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* _
       const double dny = d0 * m0 + d1 * m1 + d2 * m2;
       const double dnx = d0 * n0 + d1 * n1 + d2 * n2;
       const double rho = k * r;
-      double sn, cs;
-      sincos(rho, &sn, &cs);
+      // phase reduced to [-pi, pi] in FP64, sine and cosine of the reduced phase in FP32
+      // (|t| <= pi: the FP32 result is within ~1e-7 of e^{i rho})
+      const double nq = rint(rho * kInvTwoPi64);
+      const float th = (float)fma(-nq, kTwoPiLo64, fma(-nq, kTwoPiHi64, rho));
+      float snf, csf;
+      sincosf(th, &snf, &csf);
+      const double sn = snf, cs = csf;
       const double gw = rl.w * A * inv4pi * rinv;
       const double Gr = cs * gw, Gi = sn * gw;
       const double rinv2 = rinv * rinv;
@@ -461,20 +471,30 @@ nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* d
 nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const Geometry& g = op->geo;
   const int n = (int)op->n, ld = (int)g.ld;
+  // The near pairs write exactly the entries the regular kernel skips, so the FP64 kernel runs
+  // beside it on the op's auxiliary stream (the FP64 and FP32 pipes overlap).
+  cudaStream_t aux = op->aux ? op->aux : s;
+  if (aux != s) {
+    NB_TRY_CUDA(cudaEventRecord(op->ev_fork, s));
+    NB_TRY_CUDA(cudaStreamWaitEvent(aux, op->ev_fork, 0));
+  }
+  const int64_t threads = 256, warps_per_block = threads / 32;
+  const int64_t blocks = (g.n_near + warps_per_block - 1) / warps_per_block;
+  NB_LAUNCH("assemble_near", aux, k_assemble_near<<<(unsigned)blocks, (unsigned)threads, 0, aux>>>(
+      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
+  NB_CHECK_LAUNCH();
   // regular pairs: columns in blocks of 256, rows split so the grid holds a few waves
   const int col_blocks = (ld + kRegThreads - 1) / kRegThreads;
   const int rows_per_block = 64;
   const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
   dim3 grid(col_blocks, row_blocks);
-  NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld,
-                                                  rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+  NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
+      g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
   NB_CHECK_LAUNCH();
-  // near pairs overwrite the entries the regular kernel skipped
-  const int64_t threads = 256, warps_per_block = threads / 32;
-  const int64_t blocks = (g.n_near + warps_per_block - 1) / warps_per_block;
-  NB_LAUNCH("assemble_near", s, k_assemble_near<<<(unsigned)blocks, (unsigned)threads, 0, s>>>(
-      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
-  NB_CHECK_LAUNCH();
+  if (aux != s) {
+    NB_TRY_CUDA(cudaEventRecord(op->ev_join, aux));
+    NB_TRY_CUDA(cudaStreamWaitEvent(s, op->ev_join, 0));
+  }
   return NAT_BEM_OK;
 }
 

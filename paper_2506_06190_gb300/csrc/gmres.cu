@@ -23,8 +23,9 @@
 
 namespace natbem {
 
-constexpr int kChunk = 256;       // rows per block in the vector kernels
-constexpr int kColGroup = 8;      // Krylov vectors per block in the first dot kernel
+constexpr int kChunk = 256;       // rows per block in the element-wise vector kernels
+constexpr int kUpdRows = 64;      // rows per block in the Gram-Schmidt update (4 column groups)
+constexpr int kDotThreads = 512;  // threads of the per-vector dot-product blocks
 constexpr int kCounters = 8;      // per-RHS tickets
 
 struct Workspace {
@@ -110,16 +111,55 @@ __device__ __forceinline__ size_t vidx(const GArgs& a, int c, int s) {
 }  // namespace
 
 // ------------------------------------------------------------------------------ matvec
+// Compensated FP32 summation (Kahan 1965): after each call s - c equals the exact running sum
+// to about twice FP32 precision. The operator stream is bandwidth-bound with FP32 issue slots
+// to spare, while GB300's FP64 rate is far too low to accumulate the stream in FP64.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Sum over the block of (s - c) per row, combined in FP64 (8 warps of 32 lanes).
+template <int kRows>
+__device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], const float (&cr)[kRows],
+                                                  const float (&si)[kRows], const float (&ci)[kRows],
+                                                  int n, int row0, double2* __restrict__ y) {
+  __shared__ double sh[2 * kRows][8];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kRows; ++r) {
+    double vr = (double)sr[r] - (double)cr[r];
+    double vi = (double)si[r] - (double)ci[r];
+    vr = warp_sum(vr);
+    vi = warp_sum(vi);
+    if (lane == 0) {
+      sh[2 * r][wid] = vr;
+      sh[2 * r + 1][wid] = vi;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
+    const int r = threadIdx.x;
+    double tr = 0.0, ti = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      tr += sh[2 * r][q];
+      ti += sh[2 * r + 1][q];
+    }
+    y[row0 + r] = make_double2(tr, ti);
+  }
+}
+
 // y_s = A x_s for the RHS s = blockIdx.y: A is n x ld complex64 (row-major, ld even, pad
-// columns zero), x_s complex64 with ld entries, y_s complex128. kRows rows per block; the
-// block's threads stride over the row in 16-byte (two-complex) steps; FP32 products summed
-// in FP32 over kUnroll steps, then into FP64.
+// columns zero), x_s complex64 with ld entries, y_s complex128. kRows rows per block of 256
+// threads; each thread strides over the row in 16-byte (two-complex) steps with kUnroll
+// loads per row in flight, FP32 products and compensated FP32 running sums.
 template <int kRows, int kUnroll>
 __global__ void __launch_bounds__(256)
 k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x, int64_t xstride,
        double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
        const int* __restrict__ scal) {
-  __shared__ double sh[2 * kRows][8];
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
@@ -130,62 +170,41 @@ k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x
   for (int r = 0; r < kRows; ++r)
     a[r] = reinterpret_cast<const float4*>(A + (size_t)min(row0 + r, n - 1) * ld);
   const int n4 = ld >> 1;
-  double accr[kRows], acci[kRows];
+  float sr[kRows], cr[kRows], si[kRows], ci[kRows];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) accr[r] = acci[r] = 0.0;
+  for (int r = 0; r < kRows; ++r) sr[r] = cr[r] = si[r] = ci[r] = 0.f;
   for (int base = threadIdx.x; base < n4; base += 256 * kUnroll) {
-    float pr[kRows], pi[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) pr[r] = pi[r] = 0.f;
+    float4 xx[kUnroll], aa[kRows][kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int idx = base + u * 256;
-      if (idx < n4) {
-        const float4 xx = __ldg(xv + idx);
+      const bool ok = idx < n4;
+      xx[u] = ok ? __ldg(xv + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const float4 aa = __ldcs(a[r] + idx);
-          pr[r] = fmaf(aa.x, xx.x, fmaf(-aa.y, xx.y, fmaf(aa.z, xx.z, fmaf(-aa.w, xx.w, pr[r]))));
-          pi[r] = fmaf(aa.x, xx.y, fmaf(aa.y, xx.x, fmaf(aa.z, xx.w, fmaf(aa.w, xx.z, pi[r]))));
-        }
+      for (int r = 0; r < kRows; ++r) aa[r][u] = ok ? __ldcs(a[r] + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const float4 q = aa[r][u], v = xx[u];
+        const float pr = fmaf(q.x, v.x, fmaf(-q.y, v.y, fmaf(q.z, v.z, -q.w * v.w)));
+        const float pi = fmaf(q.x, v.y, fmaf(q.y, v.x, fmaf(q.z, v.w, q.w * v.z)));
+        kahan_add(sr[r], cr[r], pr);
+        kahan_add(si[r], ci[r], pi);
       }
     }
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      accr[r] += pr[r];
-      acci[r] += pi[r];
-    }
   }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    accr[r] = warp_sum(accr[r]);
-    acci[r] = warp_sum(acci[r]);
-    if (lane == 0) {
-      sh[2 * r][wid] = accr[r];
-      sh[2 * r + 1][wid] = acci[r];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
-    const int r = threadIdx.x;
-    double sr = 0.0, si = 0.0;
-    for (int q = 0; q < 8; ++q) {
-      sr += sh[2 * r][q];
-      si += sh[2 * r + 1][q];
-    }
-    y[(size_t)s * ystride + row0 + r] = make_double2(sr, si);
-  }
+  gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
 }
 
 // The same product with A stored as packed bf16 complex pairs (real in the low half): half
-// the bytes of the FP32 operator; products and partial sums in FP32, then FP64.
+// the bytes of the FP32 operator; 16-byte loads hold four complex entries.
 template <int kRows, int kUnroll>
 __global__ void __launch_bounds__(256)
 k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
             int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
             const int* __restrict__ scal) {
-  __shared__ double sh[2 * kRows][8];
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
@@ -196,66 +215,49 @@ k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restr
   for (int r = 0; r < kRows; ++r)
     a[r] = reinterpret_cast<const uint4*>(A + (size_t)min(row0 + r, n - 1) * ld);
   const int n4 = ld >> 2;  // four complex per 16 bytes
-  double accr[kRows], acci[kRows];
+  float sr[kRows], cr[kRows], si[kRows], ci[kRows];
 #pragma unroll
-  for (int r = 0; r < kRows; ++r) accr[r] = acci[r] = 0.0;
+  for (int r = 0; r < kRows; ++r) sr[r] = cr[r] = si[r] = ci[r] = 0.f;
   for (int base = threadIdx.x; base < n4; base += 256 * kUnroll) {
-    float pr[kRows], pi[kRows];
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) pr[r] = pi[r] = 0.f;
+    float4 x0[kUnroll], x1[kUnroll];
+    uint4 aa[kRows][kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const int idx = base + u * 256;
-      if (idx < n4) {
-        const float4 x0 = __ldg(xv + 2 * idx), x1 = __ldg(xv + 2 * idx + 1);
+      const bool ok = idx < n4;
+      x0[u] = ok ? __ldg(xv + 2 * idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      x1[u] = ok ? __ldg(xv + 2 * idx + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int r = 0; r < kRows; ++r) {
-          const uint4 q = __ldcs(a[r] + idx);
-          const uint32_t w[4] = {q.x, q.y, q.z, q.w};
-          const float xr[4] = {x0.x, x0.z, x1.x, x1.z}, xi[4] = {x0.y, x0.w, x1.y, x1.w};
+      for (int r = 0; r < kRows; ++r) aa[r][u] = ok ? __ldcs(a[r] + idx) : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float ar = __uint_as_float(w[e] << 16), ai = __uint_as_float(w[e] & 0xffff0000u);
-            pr[r] = fmaf(ar, xr[e], fmaf(-ai, xi[e], pr[r]));
-            pi[r] = fmaf(ar, xi[e], fmaf(ai, xr[e], pi[r]));
-          }
+    for (int u = 0; u < kUnroll; ++u) {
+      const float xr[4] = {x0[u].x, x0[u].z, x1[u].x, x1[u].z};
+      const float xi[4] = {x0[u].y, x0[u].w, x1[u].y, x1[u].w};
+#pragma unroll
+      for (int r = 0; r < kRows; ++r) {
+        const uint32_t w[4] = {aa[r][u].x, aa[r][u].y, aa[r][u].z, aa[r][u].w};
+        float pr = 0.f, pi = 0.f;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float ar = __uint_as_float(w[e] << 16), ai = __uint_as_float(w[e] & 0xffff0000u);
+          pr = fmaf(ar, xr[e], fmaf(-ai, xi[e], pr));
+          pi = fmaf(ar, xi[e], fmaf(ai, xr[e], pi));
         }
+        kahan_add(sr[r], cr[r], pr);
+        kahan_add(si[r], ci[r], pi);
       }
     }
-#pragma unroll
-    for (int r = 0; r < kRows; ++r) {
-      accr[r] += pr[r];
-      acci[r] += pi[r];
-    }
   }
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int r = 0; r < kRows; ++r) {
-    accr[r] = warp_sum(accr[r]);
-    acci[r] = warp_sum(acci[r]);
-    if (lane == 0) {
-      sh[2 * r][wid] = accr[r];
-      sh[2 * r + 1][wid] = acci[r];
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
-    const int r = threadIdx.x;
-    double sr = 0.0, si = 0.0;
-    for (int q = 0; q < 8; ++q) {
-      sr += sh[2 * r][q];
-      si += sh[2 * r + 1][q];
-    }
-    y[(size_t)s * ystride + row0 + r] = make_double2(sr, si);
-  }
+  gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
 }
 
 // ------------------------------------------------------------------------ GMRES steps
-// ||b_s|| (partials + last block per RHS); w_s = b_s; h_{0,-1} := ||b_s||, g_s[0] = ||b_s||.
-__global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
+// Start of a GMRES run: w = b and each block's partial ||b||^2 (kUpdRows rows per block).
+__global__ void __launch_bounds__(kUpdRows) k_start(GArgs a) {
   __shared__ double sh[32];
-  const int s = blockIdx.y, chunk = blockIdx.x;
-  const int r = chunk * kChunk + threadIdx.x;
+  const int s = blockIdx.y;
+  const int r = blockIdx.x * kUpdRows + threadIdx.x;
   double v = 0.0;
   if (r < a.n) {
     const double2 bb = a.b[(size_t)s * a.n + r];
@@ -263,186 +265,135 @@ __global__ void __launch_bounds__(kChunk) k_init(GArgs a) {
     v = cabs2(bb);
   }
   v = block_sum(v, sh);
-  if (threadIdx.x == 0) a.partn[(size_t)chunk * a.nrhs + s] = v;
-  if (!last_block(a.cnt + s * kCounters + 0, gridDim.x)) return;
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) t += a.partn[(size_t)c * a.nrhs + s];
-    const double bn = sqrt(t);
-    a.bnorm[s] = bn;
-    a.hnorm[s] = bn;
-    a.gv[(size_t)s * (a.m + 1)] = make_double2(bn, 0.0);
-    a.res[s] = bn;
-    a.iters[s] = 0;
-    a.done[s] = (bn == 0.0) || (a.skip && a.skip[s]);
-    __threadfence();
-    const unsigned t2 = atomicAdd((unsigned*)&a.scal[2], 1u);
-    if (t2 == (unsigned)a.nrhs - 1) {
-      a.scal[2] = 0;
-      int all = 1;
-      for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
-      a.scal[0] = 0;
-      a.scal[1] = all || a.maxit == 0;
-    }
-  }
+  if (threadIdx.x == 0) a.partn[(size_t)blockIdx.x * a.nrhs + s] = v;
 }
 
-// v_j = w / h_{j,j-1} into V[j] (FP64) and the FP32 copy used by the matvec.
-__global__ void __launch_bounds__(kChunk) k_normalize(GArgs a) {
-  if (a.scal[1]) return;
-  const int s = blockIdx.y;
-  if (a.done[s]) return;
-  const int j = a.scal[0];
-  const int r = blockIdx.x * kChunk + threadIdx.x;
-  if (r >= a.n) return;
-  const double inv = 1.0 / a.hnorm[s];
-  const double2 ww = a.w[(size_t)s * a.n + r];
-  const double2 v = make_double2(ww.x * inv, ww.y * inv);
-  a.V[vidx(a, j, s) + r] = v;
-  a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
-}
-
-// h_c = V[c]^H w for c <= j: block (chunk, column group, s); warp per column, lanes over
-// the chunk's rows. Last block per RHS sums the chunk partials into hcol.
-__global__ void __launch_bounds__(kChunk) k_dots(GArgs a) {
-  if (a.scal[1]) return;
-  const int s = blockIdx.z;
-  const int j = a.scal[0];
-  const int chunk = blockIdx.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = blockIdx.y * kColGroup + wid;
-  const bool active = !a.done[s];
-  if (active && c <= j) {
-    const double2* v = a.V + vidx(a, c, s);
-    const double2* w = a.w + (size_t)s * a.n;
-    double re = 0.0, im = 0.0;
-    const int r0 = chunk * kChunk;
-    const int r1 = min(a.n, r0 + kChunk);
-    for (int r = r0 + lane; r < r1; r += 32) {
-      const double2 p = cmulc(v[r], w[r]);
-      re += p.x;
-      im += p.y;
-    }
-    re = warp_sum(re);
-    im = warp_sum(im);
-    if (lane == 0) a.part[((size_t)chunk * a.nrhs + s) * (a.m + 1) + c] = make_double2(re, im);
-  }
-  if (!last_block(a.cnt + s * kCounters + 1, gridDim.x * gridDim.y)) return;
-  if (!active) return;
-  for (int cc = threadIdx.x; cc <= j; cc += blockDim.x) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int q = 0; q < a.nchunk; ++q) t = cadd(t, a.part[((size_t)q * a.nrhs + s) * (a.m + 1) + cc]);
-    a.hcol[(size_t)s * (a.m + 1) + cc] = t;
-  }
-}
-
-// w -= V h (first pass, h = hcol), then h' = V^H w over the block's rows; the last block per
-// RHS sums h' into htmp and accumulates hcol += h'.
-__global__ void __launch_bounds__(kChunk) k_update_dots(GArgs a) {
-  __shared__ double2 s_h[256];
-  __shared__ double2 s_w[kChunk];
-  if (a.scal[1]) return;
-  const int s = blockIdx.y, chunk = blockIdx.x;
-  const int j = a.scal[0];
-  const bool active = !a.done[s];
-  const int r = chunk * kChunk + threadIdx.x;
-  if (active) {
-    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = a.hcol[(size_t)s * (a.m + 1) + c];
-    __syncthreads();
-    double2 w = make_double2(0.0, 0.0);
-    if (r < a.n) {
-      w = a.w[(size_t)s * a.n + r];
-      double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
-      int c = 0;
-      for (; c + 1 <= j; c += 2) {
-        acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
-        acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 1, s) + r], s_h[c + 1]));
-      }
-      if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
-      w = csub(w, cadd(acc0, acc1));
-      a.w[(size_t)s * a.n + r] = w;
-    }
-    s_w[threadIdx.x] = w;
-    __syncthreads();
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r0 = chunk * kChunk;
-    const int cnt = min(kChunk, a.n - r0);
-    for (int c = wid; c <= j; c += kChunk / 32) {
-      const double2* v = a.V + vidx(a, c, s) + r0;
-      double re = 0.0, im = 0.0;
-      for (int q = lane; q < cnt; q += 32) {
-        const double2 p = cmulc(v[q], s_w[q]);
-        re += p.x;
-        im += p.y;
-      }
-      re = warp_sum(re);
-      im = warp_sum(im);
-      if (lane == 0) a.part[((size_t)chunk * a.nrhs + s) * (a.m + 1) + c] = make_double2(re, im);
-    }
-  }
-  if (!last_block(a.cnt + s * kCounters + 2, gridDim.x)) return;
-  if (!active) return;
-  for (int cc = threadIdx.x; cc <= j; cc += blockDim.x) {
-    double2 t = make_double2(0.0, 0.0);
-    for (int q = 0; q < a.nchunk; ++q) t = cadd(t, a.part[((size_t)q * a.nrhs + s) * (a.m + 1) + cc]);
-    a.htmp[(size_t)s * (a.m + 1) + cc] = t;
-    a.hcol[(size_t)s * (a.m + 1) + cc] = cadd(a.hcol[(size_t)s * (a.m + 1) + cc], t);
-  }
-}
-
-// w -= V h' (second pass) and ||w||; the last block per RHS applies the Givens rotations to
-// the new Hessenberg column, updates the residual estimate and the convergence flags; the
-// last RHS to finish advances j and sets the "all done" flag.
-__global__ void __launch_bounds__(kChunk) k_update_norm(GArgs a) {
-  __shared__ double2 s_h[256];
+// h_c = V[c]^H w for c <= j, one block per (c, RHS) summing all rows in FP64. Pass 0 stores h
+// in hcol; pass 1 (re-orthogonalisation) stores it in htmp and adds it to hcol.
+__global__ void __launch_bounds__(kDotThreads) k_dots(GArgs a, int pass) {
   __shared__ double sh[32];
   if (a.scal[1]) return;
-  const int s = blockIdx.y, chunk = blockIdx.x;
+  const int c = blockIdx.x, s = blockIdx.y;
   const int j = a.scal[0];
-  const bool active = !a.done[s];
-  const int r = chunk * kChunk + threadIdx.x;
-  double nv = 0.0;
-  if (active) {
-    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = a.htmp[(size_t)s * (a.m + 1) + c];
-    __syncthreads();
-    if (r < a.n) {
-      double2 w = a.w[(size_t)s * a.n + r];
-      double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
-      int c = 0;
-      for (; c + 1 <= j; c += 2) {
-        acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
-        acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 1, s) + r], s_h[c + 1]));
+  if (c > j || a.done[s]) return;
+  const double2* v = a.V + vidx(a, c, s);
+  const double2* w = a.w + (size_t)s * a.n;
+  double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int r0 = threadIdx.x; r0 < a.n; r0 += 4 * kDotThreads) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = r0 + u * kDotThreads;
+      if (r < a.n) {
+        const double2 p = cmulc(v[r], w[r]);
+        re[u] += p.x;
+        im[u] += p.y;
       }
-      if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
-      w = csub(w, cadd(acc0, acc1));
-      a.w[(size_t)s * a.n + r] = w;
-      nv = cabs2(w);
     }
   }
-  nv = block_sum(nv, sh);
-  if (threadIdx.x == 0) a.partn[(size_t)chunk * a.nrhs + s] = nv;
-  if (!last_block(a.cnt + s * kCounters + 3, gridDim.x)) return;
+  const double hr = block_sum((re[0] + re[1]) + (re[2] + re[3]), sh);
+  const double hi = block_sum((im[0] + im[1]) + (im[2] + im[3]), sh);
+  if (threadIdx.x == 0) {
+    const size_t o = (size_t)s * (a.m + 1) + c;
+    const double2 h = make_double2(hr, hi);
+    if (pass == 0) {
+      a.hcol[o] = h;
+    } else {
+      a.htmp[o] = h;
+      a.hcol[o] = cadd(a.hcol[o], h);
+    }
+  }
+}
+
+// w -= V h (h = hcol in pass 0, htmp in pass 1) on kUpdRows rows per block: thread (row, g)
+// sums the columns c = g, g + 4, ...; the four group sums are added in a fixed order. Pass 1
+// also writes the block's partial ||w||^2.
+__global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
+  __shared__ double2 s_h[256];
+  __shared__ double2 s_acc[4][kUpdRows];
+  __shared__ double sh[32];
+  if (a.scal[1]) return;
+  const int s = blockIdx.y;
+  const int j = a.scal[0];
+  const bool active = !a.done[s];
+  const double2* h = (pass == 0 ? a.hcol : a.htmp) + (size_t)s * (a.m + 1);
+  if (active)
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = h[c];
+  __syncthreads();
+  const int lr = threadIdx.x & (kUpdRows - 1), g = threadIdx.x / kUpdRows;
+  const int r = blockIdx.x * kUpdRows + lr;
+  double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+  if (active && r < a.n) {
+    int c = g;
+    for (; c + 4 <= j; c += 8) {
+      acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+      acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 4, s) + r], s_h[c + 4]));
+    }
+    if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+  }
+  s_acc[g][lr] = cadd(acc0, acc1);
+  __syncthreads();
+  double nv = 0.0;
+  if (g == 0 && active && r < a.n) {
+    const double2 t = cadd(cadd(s_acc[0][lr], s_acc[1][lr]), cadd(s_acc[2][lr], s_acc[3][lr]));
+    const double2 w = csub(a.w[(size_t)s * a.n + r], t);
+    a.w[(size_t)s * a.n + r] = w;
+    nv = cabs2(w);
+  }
+  if (pass == 1) {
+    nv = block_sum(nv, sh);
+    if (threadIdx.x == 0) a.partn[(size_t)blockIdx.x * a.nrhs + s] = nv;
+  }
+}
+
+// ||w|| from the block partials and v = w / ||w|| into V[jt] and the FP32 copy xf.
+// mode 0 starts a run (jt = 0, ||w|| = ||b||); mode 1 ends iteration j (jt = j + 1): the last
+// block per RHS applies the earlier Givens rotations to the new Hessenberg column, makes the
+// rotation that zeroes h_{j+1,j}, updates the residual estimate |g_{j+1}| and the convergence
+// flag; the last RHS to finish advances j and sets the "all done" flag.
+__global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
+  __shared__ double sh[32];
+  if (mode == 1 && a.scal[1]) return;
+  const int s = blockIdx.y;
+  const int j = a.scal[0];
+  const bool active = mode == 0 ? !(a.skip && a.skip[s]) : !a.done[s];
+  const int jt = mode == 0 ? 0 : j + 1;
+  double t = 0.0;
+  for (int q = threadIdx.x; q < a.nchunk; q += blockDim.x) t += a.partn[(size_t)q * a.nrhs + s];
+  t = block_sum(t, sh);
+  const double hn = sqrt(t);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (active && hn > 0.0 && r < a.n) {
+    const double inv = 1.0 / hn;
+    const double2 ww = a.w[(size_t)s * a.n + r];
+    const double2 v = make_double2(ww.x * inv, ww.y * inv);
+    a.V[vidx(a, jt, s) + r] = v;
+    a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+  }
+  if (!last_block(a.cnt + s * kCounters + 0, gridDim.x)) return;
   if (threadIdx.x != 0) return;
-  if (active) {
-    double t = 0.0;
-    for (int q = 0; q < a.nchunk; ++q) t += a.partn[(size_t)q * a.nrhs + s];
-    const double hn = sqrt(t);
+  const size_t ho = (size_t)s * (a.m + 1);
+  if (mode == 0) {
+    a.bnorm[s] = hn;
     a.hnorm[s] = hn;
-    const size_t ho = (size_t)s * (a.m + 1);
+    a.gv[ho] = make_double2(hn, 0.0);
+    a.res[s] = hn;
+    a.iters[s] = 0;
+    a.done[s] = (hn == 0.0) || !active;
+  } else if (active) {
+    a.hnorm[s] = hn;
     double2* hc = a.hcol + ho;
     double* cs = a.cs + (size_t)s * a.m;
     double2* sn = a.sn + (size_t)s * a.m;
     double2* gv = a.gv + ho;
-    // earlier rotations on the new column
     for (int i = 0; i < j; ++i) {
-      const double2 h0 = hc[i], h1 = hc[i + 1];
       // [t0; t1] = [c s; -conj(s) c] [h0; h1]
+      const double2 h0 = hc[i], h1 = hc[i + 1];
       const double2 t0 = cadd(make_double2(cs[i] * h0.x, cs[i] * h0.y), cmul(sn[i], h1));
       const double2 t1 = cadd(cmul(make_double2(-sn[i].x, sn[i].y), h0),
                               make_double2(cs[i] * h1.x, cs[i] * h1.y));
       hc[i] = t0;
       hc[i + 1] = t1;
     }
-    // new rotation zeroing h_{j+1,j} = hn
     const double2 h0 = hc[j];
     const double a0 = sqrt(cabs2(h0));
     const double rho = sqrt(a0 * a0 + hn * hn);
@@ -477,7 +428,7 @@ __global__ void __launch_bounds__(kChunk) k_update_norm(GArgs a) {
     a.scal[2] = 0;
     int all = 1;
     for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
-    const int jn = j + 1;
+    const int jn = mode == 0 ? 0 : j + 1;
     a.scal[0] = jn;
     a.scal[1] = all || jn >= a.maxit;
   }
@@ -535,7 +486,7 @@ __global__ void __launch_bounds__(kChunk) k_resid(GArgs a) {
   if (!last_block(a.cnt + s * kCounters + 4, gridDim.x)) return;
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) t += a.partn[(size_t)c * a.nrhs + s];
+    for (int c = 0; c < (int)gridDim.x; ++c) t += a.partn[(size_t)c * a.nrhs + s];
     a.res_true[s] = a.bnorm[s] > 0.0 ? sqrt(t) / a.bnorm[s] : 0.0;
   }
 }
@@ -565,7 +516,7 @@ __global__ void __launch_bounds__(kChunk) k_ir_residual(GArgs a, const double2* 
   if (!last_block(a.cnt + s * kCounters + 5, gridDim.x)) return;
   if (threadIdx.x == 0 && active) {
     double t = 0.0, tb = 0.0;
-    for (int c = 0; c < a.nchunk; ++c) {
+    for (int c = 0; c < (int)gridDim.x; ++c) {
       t += a.partn[(size_t)c * a.nrhs + s];
       tb += a.part[(size_t)c * a.nrhs + s].x;
     }
@@ -588,7 +539,7 @@ __global__ void k_pad_copy(const float2* __restrict__ src, int n, int ld, int nr
 int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   const int64_t m = std::max(1, o.max_iter);
   const int64_t ld = round_up(n, 32);
-  const int64_t nchunk = (n + kChunk - 1) / kChunk;
+  const int64_t nchunk = (n + kUpdRows - 1) / kUpdRows;
   int64_t b = 0;
   b += 16 * n * nrhs * 5;                 // b, w, x, b0, xacc
   b += 16 * n * nrhs * (m + 1);           // V
@@ -625,7 +576,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   ws->nrhs = nrhs;
   ws->cap = nrhs;
   ws->m = m;
-  ws->nchunk = (int)((n + kChunk - 1) / kChunk);
+  ws->nchunk = (int)((n + kUpdRows - 1) / kUpdRows);
   const size_t nr = (size_t)nrhs, mm = (size_t)m;
   NB_TRY(dev_alloc_n(&ws->b, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->w, n * nr, s));
@@ -723,22 +674,24 @@ static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int 
 static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, bool bf16,
                                 int accumulate, float2* pout, cudaStream_t s) {
   const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
-  const dim3 vec_grid(ws->nchunk, nrhs);
-  NB_LAUNCH("gmres_init", s, k_init<<<vec_grid, kChunk, 0, s>>>(a));
+  const dim3 upd_grid(ws->nchunk, nrhs), fin_grid((n + kChunk - 1) / kChunk, nrhs);
+  const dim3 dot_grid(std::max(1, a.maxit), nrhs);
+  NB_LAUNCH("gmres_start", s, k_start<<<upd_grid, kUpdRows, 0, s>>>(a));
+  NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 0));
   NB_CHECK_LAUNCH();
-  const dim3 dots_grid(ws->nchunk, (a.maxit + 1 + kColGroup - 1) / kColGroup, nrhs);
   int it = 0, chunk = 16;
   while (it < a.maxit) {
     const int c = std::min(chunk, a.maxit - it);
     for (int q = 0; q < c; ++q) {
-      NB_LAUNCH("gmres_normalize", s, k_normalize<<<vec_grid, kChunk, 0, s>>>(a));
       if (bf16)
         NB_TRY(gemv_bf16("gemv_bf16", op->Lb, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
       else
         NB_TRY(gemv("gemv", op->L, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
-      NB_LAUNCH("gmres_dots", s, k_dots<<<dots_grid, kChunk, 0, s>>>(a));
-      NB_LAUNCH("gmres_update_dots", s, k_update_dots<<<vec_grid, kChunk, 0, s>>>(a));
-      NB_LAUNCH("gmres_update_norm", s, k_update_norm<<<vec_grid, kChunk, 0, s>>>(a));
+      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a, 0));
+      NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 0));
+      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a, 1));
+      NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 1));
+      NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 1));
     }
     NB_CHECK_LAUNCH();
     it += c;
@@ -747,6 +700,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, b
     if (ws->host_scal[1]) break;
     chunk = 8;
   }
+  const dim3 vec_grid((n + kChunk - 1) / kChunk, nrhs);
   NB_LAUNCH("gmres_lsq", s, k_lsq<<<nrhs, 32, 0, s>>>(a));
   NB_LAUNCH("gmres_xupdate", s, k_xupdate<<<vec_grid, kChunk, 0, s>>>(a, pout, accumulate));
   NB_CHECK_LAUNCH();
@@ -759,7 +713,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
   const int n = (int)op->n, ld = (int)op->geo.ld;
-  const dim3 vec_grid(ws->nchunk, nrhs);
+  const dim3 vec_grid((n + kChunk - 1) / kChunk, nrhs);
   // b = R g
   {
     const int64_t tot = (int64_t)ld * nrhs;

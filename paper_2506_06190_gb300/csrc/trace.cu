@@ -20,6 +20,14 @@ struct Rec {
 };
 std::vector<Rec> g_recs;
 std::vector<cudaEvent_t> g_free;
+std::vector<std::string> g_select;  // empty: trace every kernel
+
+bool selected(const char* name) {
+  if (g_select.empty()) return true;
+  for (const auto& s : g_select)
+    if (std::string(name).find(s) != std::string::npos) return true;
+  return false;
+}
 
 cudaEvent_t get_event() {
   if (!g_free.empty()) {
@@ -37,6 +45,7 @@ TraceScope::TraceScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (g_trace.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_mu);
+    if (!selected(name)) return;
     a_ = get_event();
     b_ = get_event();
     cudaEventRecord((cudaEvent_t)a_, s_);
@@ -58,6 +67,22 @@ using namespace natbem;
 extern "C" {
 
 void nat_bem_trace_enable(int32_t enable) { g_trace.store(enable ? 1 : 0); }
+
+void nat_bem_trace_select(const char* names) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_select.clear();
+  if (!names) return;
+  std::string all(names), cur;
+  for (char ch : all) {
+    if (ch == ',') {
+      if (!cur.empty()) g_select.push_back(cur);
+      cur.clear();
+    } else {
+      cur.push_back(ch);
+    }
+  }
+  if (!cur.empty()) g_select.push_back(cur);
+}
 
 void nat_bem_trace_reset(void) {
   std::lock_guard<std::mutex> lk(g_mu);

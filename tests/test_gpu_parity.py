@@ -203,3 +203,50 @@ def test_mixed_bf16_refinement_matches_oracle(nb, oracle_lib, ka):
         p_ref = np.linalg.solve(L, R @ G[:, s])
         assert _rel(P[:, s], p_ref) < SOL_TOL
         assert _rel(fld[:, s], oracle_lib.evaluate(V, F, ka, pts, p_ref, G[:, s])) < SOL_TOL
+
+
+def test_reassemble_matches_fresh_assembly(nb):
+    """A new wavenumber on an existing op gives the same operator bits as a fresh assembly."""
+    Vs, F = S.ring_sphere(700)
+    V = S.perturbed_ellipsoid(Vs, 9)
+    g = S.monopole_neumann(V, F, 6.5)
+    with nb.Operator.assemble(V, F, 1.5) as op:
+        op.solve(S.monopole_neumann(V, F, 1.5))
+        op.reassemble(6.5)
+        L1 = op.rows(0, 0, op.n)
+        R1 = op.rows(1, 0, op.n)
+        p1, _, st1 = op.solve(g)
+    with nb.Operator.assemble(V, F, 6.5) as op2:
+        assert np.array_equal(op2.rows(0, 0, op2.n), L1) and np.array_equal(op2.rows(1, 0, op2.n), R1)
+        p2, _, st2 = op2.solve(g)
+    assert st1 == st2 == nb.NAT_BEM_OK and np.array_equal(p1, p2)
+    with pytest.raises(nb.NatBemError):
+        nb.nat_bem_reassemble(None, 1.0)
+
+
+def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib):
+    """Batched solves over meshes of uneven size (two jobs share a mesh) give the same bits as
+    one solve at a time, with any number of workers; one job is checked against the oracle."""
+    import torch
+    jobs = []
+    for i, n_tri in enumerate([520, 1300, 760, 2010]):
+        Vs, F = S.ring_sphere(n_tri)
+        V = S.perturbed_ellipsoid(Vs, 40 + i)
+        k = 1.0 + 2.5 * i
+        g = S.sh_neumann(V, F, 1, 50 + i)[:, 0]
+        jobs.append(dict(V=V, F=F, k=k, neumann=g, points=S.fibonacci_points(33, 4.0)))
+    jobs.append(dict(jobs[1], k=7.7, neumann=S.sh_neumann(jobs[1]["V"], jobs[1]["F"], 1, 77)[:, 0]))
+    singles = []
+    for jd in jobs:
+        with nb.Operator.assemble(jd["V"], jd["F"], jd["k"]) as op:
+            p, info, st = op.solve(jd["neumann"])
+            singles.append((p, op.evaluate(jd["points"], p, jd["neumann"])))
+    for conc in (1, 3):
+        st, res = nb.nat_bem_run_batch(jobs, concurrency=conc)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        for (p, f, info, s_, ms), (p1, f1) in zip(res, singles):
+            assert s_ == nb.NAT_BEM_OK and info.iterations > 0 and ms > 0
+            assert np.array_equal(p, p1) and np.array_equal(f, f1)
+    jd = jobs[4]
+    p_ref, _ = oracle_lib.solve(jd["V"], jd["F"], jd["k"], jd["neumann"])
+    assert _rel(res[4][0], p_ref) < SOL_TOL
