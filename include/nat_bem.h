@@ -190,6 +190,29 @@ NAT_BEM_API nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
                                              void* cuda_stream);
 
 /*
+ * Y = M X with the assembled M = L (which = 0) or R (which = 1) for nrhs complex64 vectors
+ * (X, Y: nt x nrhs, column-major; host or device), by the chosen product engine:
+ *   NAT_BEM_ENGINE_AUTO: the solver's accurate product (GEMV for one vector, FP32 GEMM else);
+ *   NAT_BEM_ENGINE_FP32: FP32 CUDA-core complex GEMM;
+ *   NAT_BEM_ENGINE_TF32 / NAT_BEM_ENGINE_BF16: tcgen05 tensor cores on L (TF32) or on its BF16
+ *     copy (op built with NAT_BEM_PREC_MIXED_BF16), FP32 accumulation, nrhs <= 128, L only;
+ *   NAT_BEM_ENGINE_GEMV0 + v: GEMV variant v (0..4; one vector).
+ * This is the operator product of the GMRES iterations (Sec. 4 operators of Eq. 6), exposed
+ * for checking and for callers that iterate themselves. Blocks until Y is written.
+ * NAT_BEM_EINVAL: bad which / engine / nrhs, engine not usable for this op.
+ */
+enum {
+  NAT_BEM_ENGINE_AUTO = 0,
+  NAT_BEM_ENGINE_FP32 = 1,
+  NAT_BEM_ENGINE_TF32 = 2,
+  NAT_BEM_ENGINE_BF16 = 3,
+  NAT_BEM_ENGINE_GEMV0 = 10
+};
+NAT_BEM_API nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t engine,
+                                            const float* X, int32_t nrhs, float* Y,
+                                            void* cuda_stream);
+
+/*
  * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
  * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
  * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.

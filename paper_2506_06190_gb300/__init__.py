@@ -33,7 +33,8 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_op_rows", "nat_bem_op_size", "nat_bem_required_bytes", "nat_bem_destroy",
             "nat_bem_last_error", "nat_bem_trace_enable", "nat_bem_trace_reset",
             "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc",
-            "nat_bem_run_batch", "nat_bem_trace_select"]
+            "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply"]
+ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 
 
 class NatBemError(RuntimeError):
@@ -88,6 +89,8 @@ def lib():
         L.nat_bem_eval_noalloc.restype = ctypes.c_int
         L.nat_bem_run_batch.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Opts), i32, vp]
         L.nat_bem_run_batch.restype = ctypes.c_int
+        L.nat_bem_op_apply.argtypes = [vp, i32, i32, vp, i32, vp, vp]
+        L.nat_bem_op_apply.restype = ctypes.c_int
         L.nat_bem_op_rows.argtypes = [vp, i32, i64, i64, vp, vp]
         L.nat_bem_op_rows.restype = ctypes.c_int
         L.nat_bem_op_size.argtypes = [vp]
@@ -288,6 +291,21 @@ def nat_bem_run_batch(jobs, opts: Opts | None = None, concurrency: int = 3, stre
     return st, res
 
 
+def nat_bem_op_apply(op, which: int, engine: int, X, stream=None):
+    """Y = M X (M = L for which 0, R for 1) with the chosen product engine."""
+    n = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(X, n)
+    px, kx = _ptr(X, np.complex64)
+    if _is_torch(X):
+        import torch
+        Y = torch.empty(tuple(X.shape), dtype=torch.complex64, device=X.device)
+    else:
+        Y = np.zeros((n, nrhs) if np.ndim(X) == 2 else (n,), dtype=np.complex64, order="F")
+    py, ky = _ptr(Y, np.complex64)
+    _check(lib().nat_bem_op_apply(op, int(which), int(engine), px, nrhs, py, _stream_of(X, stream)))
+    return Y
+
+
 def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:
     n = int(lib().nat_bem_op_size(op))
     out = np.zeros((nrows, n), dtype=np.complex64)
@@ -352,6 +370,9 @@ class Operator:
 
     def evaluate(self, points, p, neumann, out=None, stream=None):
         return nat_bem_eval(self.handle, points, p, neumann, out, stream)
+
+    def apply(self, which, engine, X):
+        return nat_bem_op_apply(self.handle, which, engine, X)
 
     def rows(self, which, row0, nrows):
         return nat_bem_op_rows(self.handle, which, row0, nrows)

@@ -362,6 +362,50 @@ nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts, int64_t m, 
   }
 }
 
+nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t engine,
+                                const float* X, int32_t nrhs, float* Y, void* cuda_stream) {
+  try {
+    clear_error();
+    const bool gemv_engine = engine >= NAT_BEM_ENGINE_GEMV0 && engine < NAT_BEM_ENGINE_GEMV0 + 5;
+    if (!op || !X || !Y || nrhs < 1 || which < 0 || which > 1 ||
+        !(engine == NAT_BEM_ENGINE_AUTO || engine == NAT_BEM_ENGINE_FP32 ||
+          engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16 || gemv_engine) ||
+        (gemv_engine && nrhs != 1) ||
+        ((engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16) && (which != 0 || nrhs > 128)) ||
+        (engine == NAT_BEM_ENGINE_BF16 && !op->Lb)) {
+      set_error("nat_bem_op_apply: bad arguments or engine not usable for this op");
+      return NAT_BEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t cnt = (size_t)op->n * nrhs;
+    const float2* dx = nullptr;
+    float2* tx = nullptr;
+    NB_TRY(to_device(reinterpret_cast<const float2*>(X), cnt, s, &dx, &tx));
+    const bool ydev = is_device_pointer(Y);
+    float2* dy = reinterpret_cast<float2*>(Y);
+    float2* ty = nullptr;
+    if (!ydev) {
+      NB_TRY(dev_alloc_n(&ty, cnt, s));
+      dy = ty;
+    }
+    nat_bem_status st = apply_impl(const_cast<nat_bem_op*>(op), which, engine, dx, nrhs, dy, s);
+    if (st == NAT_BEM_OK && !ydev) {
+      cudaError_t e = cudaMemcpyAsync(Y, ty, cnt * sizeof(float2), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copy of Y to the host failed: ") + cudaGetErrorString(e));
+        st = NAT_BEM_ECUDA;
+      }
+    }
+    dev_free(tx, s);
+    dev_free(ty, s);
+    return st;
+  } catch (...) {
+    set_error("internal error in nat_bem_op_apply");
+    return NAT_BEM_ECUDA;
+  }
+}
+
 nat_bem_status nat_bem_op_rows(const nat_bem_op* op, int32_t which, int64_t row0, int64_t nrows,
                                float* out, void* cuda_stream) {
   clear_error();

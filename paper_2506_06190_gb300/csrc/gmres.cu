@@ -17,6 +17,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "internal.h"
@@ -25,7 +30,8 @@ namespace natbem {
 
 constexpr int kChunk = 256;       // rows per block in the element-wise vector kernels
 constexpr int kUpdRows = 64;      // rows per block in the Gram-Schmidt update (4 column groups)
-constexpr int kDotThreads = 512;  // threads of the per-vector dot-product blocks
+constexpr int kDotThreads = 256;  // threads of the dot-product blocks
+constexpr int kDotChunks = 8;     // row ranges per Krylov vector in the dot products
 constexpr int kCounters = 8;      // per-RHS tickets
 
 struct Workspace {
@@ -40,6 +46,9 @@ struct Workspace {
   float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
   int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
   int* outer_done = nullptr;                               // refinement: converged RHS
+  void* tc_scratch = nullptr;                              // packed B + split-K partials
+  size_t tc_bytes = 0;
+  int* tc_err = nullptr;                                   // bounded-wait failures
   unsigned* cnt = nullptr;
   int* host_scal = nullptr;  // pinned mirror of scal[0..1]
 };
@@ -252,6 +261,140 @@ k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restr
   gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
 }
 
+// Bulk-copy GEMV for one RHS per blockIdx.y: each block streams a contiguous range of rows
+// through a ring of kStages shared-memory stages. A producer warp issues 1-D bulk async copies
+// (cp.async.bulk) of row segments of up to kSeg bytes, completed on mbarriers; eight consumer
+// warps multiply each segment with x (read through L1) into compensated FP32 sums, and at the
+// end of each row combine them in FP64. In-flight bytes no longer depend on registers.
+namespace {
+__device__ __forceinline__ uint32_t sa_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+  uint64_t t0;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+  for (uint32_t i = 0; i < (1u << 26); ++i) {
+    if (bar_try(bar, parity)) return true;
+    if ((i & 1023u) == 1023u) {
+      uint64_t t;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+      if (t - t0 > 2000000000ull) return false;
+    }
+  }
+  return false;
+}
+}  // namespace
+
+template <int kStages, int kSeg>
+__global__ void __launch_bounds__(288)
+k_gemv_bulk(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x,
+            int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+            const int* __restrict__ scal, int rows_per_block, int* __restrict__ err) {
+  extern __shared__ __align__(128) float4 ring_raw[];  // kStages x kSeg bytes (dynamic)
+  float4 (*ring)[kSeg / 16] = reinterpret_cast<float4 (*)[kSeg / 16]>(ring_raw);
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+  __shared__ double red[2][8];
+  __shared__ int s_abort;
+  if (scal && scal[1]) return;
+  const int s = blockIdx.y;
+  if (done && done[s]) return;
+  const int row_begin = blockIdx.x * rows_per_block;
+  const int row_end = min(n, row_begin + rows_per_block);
+  if (row_begin >= row_end) return;
+  const int row_bytes = ld * 8;
+  const int nseg = (row_bytes + kSeg - 1) / kSeg;
+  const int total = (row_end - row_begin) * nseg;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int q = 0; q < kStages; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa_u32(&full[q])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa_u32(&empty[q])), "r"(8) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == 8) {  // producer
+    if (lane == 0) {
+      for (int t = 0; t < total && !s_abort; ++t) {
+        const int q = t % kStages;
+        const uint32_t ph = (uint32_t)(t / kStages) & 1u;
+        if (!bar_wait(sa_u32(&empty[q]), ph ^ 1u)) {
+          atomicOr(err, 8);
+          s_abort = 1;
+          break;
+        }
+        const int row = row_begin + t / nseg, seg = t % nseg;
+        const int off = seg * kSeg;
+        const int bytes = min(kSeg, row_bytes - off);
+        const char* src = reinterpret_cast<const char*>(A + (size_t)row * ld) + off;
+        const uint32_t fb = sa_u32(&full[q]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                sa_u32(&ring[q][0])),
+            "l"(src), "r"(bytes), "r"(fb)
+            : "memory");
+      }
+    }
+    return;
+  }
+  const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+  for (int t = 0; t < total; ++t) {
+    const int q = t % kStages;
+    const uint32_t ph = (uint32_t)(t / kStages) & 1u;
+    if (!bar_wait(sa_u32(&full[q]), ph)) {
+      if (threadIdx.x == 0) atomicOr(err, 16);
+      s_abort = 1;
+      break;
+    }
+    const int row = row_begin + t / nseg, seg = t % nseg;
+    const int off4 = seg * (kSeg / 16);  // float4 index of the segment within the row
+    const int cnt4 = min(kSeg, row_bytes - seg * kSeg) / 16;
+    for (int e = threadIdx.x; e < cnt4; e += 256) {
+      const float4 a = ring[q][e];
+      const float4 v = __ldg(xv + off4 + e);
+      const float pr = fmaf(a.x, v.x, fmaf(-a.y, v.y, fmaf(a.z, v.z, -a.w * v.w)));
+      const float pi = fmaf(a.x, v.y, fmaf(a.y, v.x, fmaf(a.z, v.w, a.w * v.z)));
+      kahan_add(sr, cr, pr);
+      kahan_add(si, ci, pi);
+    }
+    __syncwarp();
+    if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa_u32(&empty[q])) : "memory");
+    if (seg == nseg - 1) {  // row complete: combine in FP64 (consumer warps only)
+      double vr = warp_sum((double)sr - (double)cr), vi = warp_sum((double)si - (double)ci);
+      if (lane == 0) {
+        red[0][warp] = vr;
+        red[1][warp] = vi;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (threadIdx.x == 0) {
+        double tr = 0.0, ti = 0.0;
+        for (int w = 0; w < 8; ++w) {
+          tr += red[0][w];
+          ti += red[1][w];
+        }
+        y[(size_t)s * ystride + row] = make_double2(tr, ti);
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      sr = cr = si = ci = 0.f;
+    }
+  }
+  if (s_abort && warp == 0 && lane == 0) {
+    // let the copies already in flight land before the block exits
+    for (int q = 0; q < kStages; ++q) bar_wait(sa_u32(&full[q]), 0), bar_wait(sa_u32(&full[q]), 1);
+  }
+}
+
 // ------------------------------------------------------------------------ GMRES steps
 // Start of a GMRES run: w = b and each block's partial ||b||^2 (kUpdRows rows per block).
 __global__ void __launch_bounds__(kUpdRows) k_start(GArgs a) {
@@ -268,45 +411,40 @@ __global__ void __launch_bounds__(kUpdRows) k_start(GArgs a) {
   if (threadIdx.x == 0) a.partn[(size_t)blockIdx.x * a.nrhs + s] = v;
 }
 
-// h_c = V[c]^H w for c <= j, one block per (c, RHS) summing all rows in FP64. Pass 0 stores h
-// in hcol; pass 1 (re-orthogonalisation) stores it in htmp and adds it to hcol.
-__global__ void __launch_bounds__(kDotThreads) k_dots(GArgs a, int pass) {
+// Partial h_c = V[c]^H w over one of kDotChunks row ranges, for c <= j: block (c, chunk, RHS),
+// FP64, into part[((s (m+1) + c) kDotChunks + chunk]. The consumer sums the chunks in order.
+__global__ void __launch_bounds__(kDotThreads) k_dots(GArgs a) {
   __shared__ double sh[32];
   if (a.scal[1]) return;
-  const int c = blockIdx.x, s = blockIdx.y;
+  const int c = blockIdx.x, chunk = blockIdx.y, s = blockIdx.z;
   const int j = a.scal[0];
   if (c > j || a.done[s]) return;
+  const int per = (a.n + kDotChunks - 1) / kDotChunks;
+  const int r_begin = chunk * per, r_end = min(a.n, r_begin + per);
   const double2* v = a.V + vidx(a, c, s);
   const double2* w = a.w + (size_t)s * a.n;
-  double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int r0 = threadIdx.x; r0 < a.n; r0 += 4 * kDotThreads) {
+  double re[2] = {0.0, 0.0}, im[2] = {0.0, 0.0};
+  for (int r0 = r_begin + threadIdx.x; r0 < r_end; r0 += 2 * kDotThreads) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 2; ++u) {
       const int r = r0 + u * kDotThreads;
-      if (r < a.n) {
+      if (r < r_end) {
         const double2 p = cmulc(v[r], w[r]);
         re[u] += p.x;
         im[u] += p.y;
       }
     }
   }
-  const double hr = block_sum((re[0] + re[1]) + (re[2] + re[3]), sh);
-  const double hi = block_sum((im[0] + im[1]) + (im[2] + im[3]), sh);
-  if (threadIdx.x == 0) {
-    const size_t o = (size_t)s * (a.m + 1) + c;
-    const double2 h = make_double2(hr, hi);
-    if (pass == 0) {
-      a.hcol[o] = h;
-    } else {
-      a.htmp[o] = h;
-      a.hcol[o] = cadd(a.hcol[o], h);
-    }
-  }
+  const double hr = block_sum(re[0] + re[1], sh);
+  const double hi = block_sum(im[0] + im[1], sh);
+  if (threadIdx.x == 0)
+    a.part[(((size_t)s * (a.m + 1) + c) * kDotChunks) + chunk] = make_double2(hr, hi);
 }
 
-// w -= V h (h = hcol in pass 0, htmp in pass 1) on kUpdRows rows per block: thread (row, g)
-// sums the columns c = g, g + 4, ...; the four group sums are added in a fixed order. Pass 1
-// also writes the block's partial ||w||^2.
+// w -= V h on kUpdRows rows per block, h_c = sum of the kDotChunks partials of k_dots (summed
+// in order by every block). Thread (row, g) sums the columns c = g, g + 4, ...; the four group
+// sums are added in a fixed order. Block 0 records h: pass 0 stores it in hcol, pass 1 adds it
+// (the re-orthogonalisation correction) to hcol. Pass 1 also writes the block's ||w||^2.
 __global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
   __shared__ double2 s_h[256];
   __shared__ double2 s_acc[4][kUpdRows];
@@ -315,9 +453,19 @@ __global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
   const int s = blockIdx.y;
   const int j = a.scal[0];
   const bool active = !a.done[s];
-  const double2* h = (pass == 0 ? a.hcol : a.htmp) + (size_t)s * (a.m + 1);
-  if (active)
-    for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = h[c];
+  if (active) {
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+      const double2* pc = a.part + ((size_t)s * (a.m + 1) + c) * kDotChunks;
+      double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < kDotChunks; ++q) t = cadd(t, pc[q]);
+      s_h[c] = t;
+      if (blockIdx.x == 0) {
+        const size_t o = (size_t)s * (a.m + 1) + c;
+        a.hcol[o] = pass == 0 ? t : cadd(a.hcol[o], t);
+      }
+    }
+  }
   __syncthreads();
   const int lr = threadIdx.x & (kUpdRows - 1), g = threadIdx.x / kUpdRows;
   const int r = blockIdx.x * kUpdRows + lr;
@@ -345,6 +493,48 @@ __global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
   }
 }
 
+// Thread 0 of the last block of k_finish: apply the earlier rotations (staged in s_hc / s_cs /
+// s_sn) to the new column, make the rotation zeroing h_{j+1,j} = hn, update g and the residual
+// estimate, write the column and the rotation back, and set the convergence flag.
+#define givens_step(a, s, j, hn)                                                              \
+  do {                                                                                        \
+    const size_t ho_ = (size_t)(s) * ((a).m + 1);                                             \
+    for (int i = 0; i < (j); ++i) {                                                           \
+      const double2 h0 = s_hc[i], h1 = s_hc[i + 1];                                           \
+      s_hc[i] = cadd(make_double2(s_cs[i] * h0.x, s_cs[i] * h0.y), cmul(s_sn[i], h1));        \
+      s_hc[i + 1] = cadd(cmul(make_double2(-s_sn[i].x, s_sn[i].y), h0),                        \
+                         make_double2(s_cs[i] * h1.x, s_cs[i] * h1.y));                         \
+    }                                                                                         \
+    const double2 h0 = s_hc[(j)];                                                             \
+    const double a0 = sqrt(cabs2(h0));                                                        \
+    const double rho = sqrt(a0 * a0 + (hn) * (hn));                                           \
+    double c_;                                                                                \
+    double2 sv, top;                                                                          \
+    if (a0 == 0.0) {                                                                          \
+      c_ = 0.0;                                                                               \
+      sv = make_double2(1.0, 0.0);                                                            \
+      top = make_double2((hn), 0.0);                                                          \
+    } else {                                                                                  \
+      c_ = a0 / rho;                                                                          \
+      const double2 ph = make_double2(h0.x / a0, h0.y / a0);                                  \
+      sv = make_double2(ph.x * (hn) / rho, ph.y * (hn) / rho);                                \
+      top = make_double2(ph.x * rho, ph.y * rho);                                             \
+    }                                                                                         \
+    (a).cs[(size_t)(s) * (a).m + (j)] = c_;                                                   \
+    (a).sn[(size_t)(s) * (a).m + (j)] = sv;                                                   \
+    s_hc[(j)] = top;                                                                          \
+    double2* gv_ = (a).gv + ho_;                                                              \
+    const double2 gj = gv_[(j)];                                                              \
+    gv_[(j) + 1] = cmul(make_double2(-sv.x, sv.y), gj);                                       \
+    gv_[(j)] = make_double2(c_ * gj.x, c_ * gj.y);                                            \
+    double2* Hcol = (a).H + ((size_t)(s) * (a).m + (j)) * ((a).m + 1);                        \
+    for (int i = 0; i <= (j); ++i) Hcol[i] = s_hc[i];                                         \
+    const double res_ = sqrt(cabs2(gv_[(j) + 1]));                                            \
+    (a).res[s] = res_;                                                                        \
+    (a).iters[s] = (j) + 1;                                                                   \
+    if (res_ <= (a).tol * (a).bnorm[s] || (hn) == 0.0) (a).done[s] = 1;                       \
+  } while (0)
+
 // ||w|| from the block partials and v = w / ||w|| into V[jt] and the FP32 copy xf.
 // mode 0 starts a run (jt = 0, ||w|| = ||b||); mode 1 ends iteration j (jt = j + 1): the last
 // block per RHS applies the earlier Givens rotations to the new Hessenberg column, makes the
@@ -352,6 +542,8 @@ __global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
 // flag; the last RHS to finish advances j and sets the "all done" flag.
 __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
   __shared__ double sh[32];
+  __shared__ double2 s_hc[256], s_sn[256];
+  __shared__ double s_cs[256];
   if (mode == 1 && a.scal[1]) return;
   const int s = blockIdx.y;
   const int j = a.scal[0];
@@ -370,6 +562,19 @@ __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
     a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
   }
   if (!last_block(a.cnt + s * kCounters + 0, gridDim.x)) return;
+  if (mode == 1 && active) {
+    // stage the Hessenberg column and the earlier rotations in shared memory (parallel loads),
+    // so the serial rotation chain below runs at shared-memory latency
+    const size_t ho = (size_t)s * (a.m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      s_hc[i] = a.hcol[ho + i];
+      if (i < j) {
+        s_cs[i] = a.cs[(size_t)s * a.m + i];
+        s_sn[i] = a.sn[(size_t)s * a.m + i];
+      }
+    }
+    __syncthreads();
+  }
   if (threadIdx.x != 0) return;
   const size_t ho = (size_t)s * (a.m + 1);
   if (mode == 0) {
@@ -381,46 +586,7 @@ __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
     a.done[s] = (hn == 0.0) || !active;
   } else if (active) {
     a.hnorm[s] = hn;
-    double2* hc = a.hcol + ho;
-    double* cs = a.cs + (size_t)s * a.m;
-    double2* sn = a.sn + (size_t)s * a.m;
-    double2* gv = a.gv + ho;
-    for (int i = 0; i < j; ++i) {
-      // [t0; t1] = [c s; -conj(s) c] [h0; h1]
-      const double2 h0 = hc[i], h1 = hc[i + 1];
-      const double2 t0 = cadd(make_double2(cs[i] * h0.x, cs[i] * h0.y), cmul(sn[i], h1));
-      const double2 t1 = cadd(cmul(make_double2(-sn[i].x, sn[i].y), h0),
-                              make_double2(cs[i] * h1.x, cs[i] * h1.y));
-      hc[i] = t0;
-      hc[i + 1] = t1;
-    }
-    const double2 h0 = hc[j];
-    const double a0 = sqrt(cabs2(h0));
-    const double rho = sqrt(a0 * a0 + hn * hn);
-    double c;
-    double2 sv, top;
-    if (a0 == 0.0) {
-      c = 0.0;
-      sv = make_double2(1.0, 0.0);
-      top = make_double2(hn, 0.0);
-    } else {
-      c = a0 / rho;
-      const double2 ph = make_double2(h0.x / a0, h0.y / a0);
-      sv = make_double2(ph.x * hn / rho, ph.y * hn / rho);  // (h0/|h0|) conj(hn) / rho, hn real
-      top = make_double2(ph.x * rho, ph.y * rho);
-    }
-    cs[j] = c;
-    sn[j] = sv;
-    hc[j] = top;
-    const double2 gj = gv[j];
-    gv[j + 1] = cmul(make_double2(-sv.x, sv.y), gj);  // -conj(s) g_j
-    gv[j] = make_double2(c * gj.x, c * gj.y);
-    double2* Hcol = a.H + ((size_t)s * a.m + j) * (a.m + 1);
-    for (int i = 0; i <= j; ++i) Hcol[i] = hc[i];
-    const double res = sqrt(cabs2(gv[j + 1]));
-    a.res[s] = res;
-    a.iters[s] = j + 1;
-    if (res <= a.tol * a.bnorm[s] || hn == 0.0) a.done[s] = 1;
+    givens_step(a, s, j, hn);
   }
   __threadfence();
   const unsigned t2 = atomicAdd((unsigned*)&a.scal[2], 1u);
@@ -554,7 +720,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
-                  ws->b0, ws->xacc, ws->outer_done};
+                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -588,7 +754,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->sn, nr * mm, s));
   NB_TRY(dev_alloc_n(&ws->gv, nr * (mm + 1), s));
   NB_TRY(dev_alloc_n(&ws->y, nr * mm, s));
-  NB_TRY(dev_alloc_n(&ws->part, (size_t)ws->nchunk * nr * (mm + 1), s));
+  NB_TRY(dev_alloc_n(&ws->part, std::max<size_t>((size_t)ws->nchunk, kDotChunks) * nr * (mm + 1), s));
   NB_TRY(dev_alloc_n(&ws->cs, nr * mm, s));
   NB_TRY(dev_alloc_n(&ws->partn, (size_t)ws->nchunk * nr, s));
   NB_TRY(dev_alloc_n(&ws->bnorm, nr, s));
@@ -605,6 +771,15 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->b0, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->xacc, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->outer_done, nr, s));
+  NB_TRY(dev_alloc_n(&ws->tc_err, 1, s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));
+  if (nrhs > 1) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    ws->tc_bytes = tc_workspace_bytes(n, ld, nrhs, sms);
+    NB_TRY(dev_alloc(&ws->tc_scratch, ws->tc_bytes, s));
+  }
   NB_TRY_CUDA(cudaMemsetAsync(ws->cnt, 0, nr * kCounters * sizeof(unsigned), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->scal, 0, 4 * sizeof(int), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->xf, 0, ld * nr * sizeof(float2), s));
@@ -648,14 +823,110 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
   return a;
 }
 
-// y_s = A x_s for all RHS (x padded to ld), skipping RHS flagged done when `done` is given.
-static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, const float2* x,
-                           double2* y, int nrhs, const int* done, const int* scal, cudaStream_t s) {
-  constexpr int kRows = 2;
-  dim3 grid((n + kRows - 1) / kRows, nrhs);
-  NB_LAUNCH(name, s, k_gemv<kRows, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+// GEMV variants for one RHS and the autotuner that picks one per (device, operator size).
+enum GemvVariant { kGemvR2U4 = 0, kGemvR4U4, kGemvR2U8, kGemvBulk4x16k, kGemvBulk6x16k, kGemvVariants };
+static const char* kGemvNames[kGemvVariants] = {"rows2_unroll4", "rows4_unroll4", "rows2_unroll8",
+                                                 "bulk_4x16KiB", "bulk_6x16KiB"};
+
+static nat_bem_status gemv_launch(int variant, const char* name, const float2* A, int n, int ld,
+                                  const float2* x, double2* y, int nrhs, const int* done,
+                                  const int* scal, int* err, cudaStream_t s) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  switch (variant) {
+    case kGemvR4U4: {
+      dim3 grid((n + 3) / 4, nrhs);
+      NB_LAUNCH(name, s, k_gemv<4, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      break;
+    }
+    case kGemvR2U8: {
+      dim3 grid((n + 1) / 2, nrhs);
+      NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      break;
+    }
+    case kGemvBulk4x16k:
+    case kGemvBulk6x16k: {
+      const int blocks = 2 * sms;
+      const int rpb = (n + blocks - 1) / blocks;
+      dim3 grid((n + rpb - 1) / rpb, nrhs);
+      static bool attr = false;
+      if (!attr) {
+        NB_TRY_CUDA(cudaFuncSetAttribute(k_gemv_bulk<4, 16384>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * 16384));
+        NB_TRY_CUDA(cudaFuncSetAttribute(k_gemv_bulk<6, 16384>, cudaFuncAttributeMaxDynamicSharedMemorySize, 6 * 16384));
+        attr = true;
+      }
+      if (variant == kGemvBulk4x16k)
+        NB_LAUNCH(name, s, k_gemv_bulk<4, 16384><<<grid, 288, 4 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
+      else
+        NB_LAUNCH(name, s, k_gemv_bulk<6, 16384><<<grid, 288, 6 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
+      break;
+    }
+    default: {
+      dim3 grid((n + 1) / 2, nrhs);
+      NB_LAUNCH(name, s, k_gemv<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+    }
+  }
   NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, n rounded to 1024) -> variant
+}  // namespace
+
+// The fastest variant for this operator size on this device: each variant is timed twice on
+// the operator itself (CUDA events, second run kept) the first time a size class is met.
+static int gemv_variant(const float2* A, int n, int ld, const float2* x, double2* y, int* err,
+                        cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_pair(dev, (int64_t)((n + 1023) / 1024));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  if (const char* env = std::getenv("NATBEM_GEMV_VARIANT")) {
+    const int v = std::atoi(env);
+    if (v >= 0 && v < kGemvVariants) return v;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = kGemvR2U4;
+  float best_ms = 1e30f;
+  for (int v = 0; v < kGemvVariants; ++v) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, s);
+      gemv_launch(v, "gemv_tune", A, n, ld, x, y, 1, nullptr, nullptr, err, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best;
+  return best;
+}
+
+// y_s = A x_s for all RHS (x padded to ld), skipping RHS flagged done when `done` is given.
+static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, const float2* x,
+                           double2* y, int nrhs, const int* done, const int* scal, cudaStream_t s,
+                           int* err = nullptr) {
+  int* e = err ? err : nullptr;
+  int variant = kGemvR2U4;
+  if (e) variant = gemv_variant(A, n, ld, x, y, e, s);
+  if (!e && (variant == kGemvBulk4x16k || variant == kGemvBulk6x16k)) variant = kGemvR2U4;
+  return gemv_launch(variant, name, A, n, ld, x, y, nrhs, done, scal, e, s);
 }
 
 static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int ld,
@@ -671,11 +942,27 @@ static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int 
 // One GMRES run on the right-hand sides in a.b (x0 = 0): init, iterations until every RHS
 // converged or a.maxit, least squares, and x = V y (or x += V y with `accumulate`) into a.x,
 // pout and the FP32 copy a.xf. `bf16` selects the operator copy used for the matvec.
-static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, bool bf16,
+// w = M x for every RHS with the given engine (x = ws->xf, padded to ld).
+static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engine, double2* y,
+                             const int* done, const int* scal, const char* name, cudaStream_t s) {
+  const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
+  const float2* M = which == 0 ? op->L : op->R;
+  switch (engine) {
+    case kEngineGemv:
+      return gemv(name, M, n, ld, ws->xf, y, nrhs, done, scal, s, ws->tc_err);
+    case kEngineGemvBf16:
+      return gemv_bf16(name, op->Lb, n, ld, ws->xf, y, nrhs, done, scal, s);
+    default:
+      return product(op, which, engine, ws->xf, nrhs, y, done, scal, ws->tc_scratch, ws->tc_bytes,
+                     ws->tc_err, s);
+  }
+}
+
+static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, int engine,
                                 int accumulate, float2* pout, cudaStream_t s) {
   const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
   const dim3 upd_grid(ws->nchunk, nrhs), fin_grid((n + kChunk - 1) / kChunk, nrhs);
-  const dim3 dot_grid(std::max(1, a.maxit), nrhs);
+  const dim3 dot_grid(std::max(1, a.maxit), kDotChunks, nrhs);
   NB_LAUNCH("gmres_start", s, k_start<<<upd_grid, kUpdRows, 0, s>>>(a));
   NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 0));
   NB_CHECK_LAUNCH();
@@ -683,13 +970,11 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, b
   while (it < a.maxit) {
     const int c = std::min(chunk, a.maxit - it);
     for (int q = 0; q < c; ++q) {
-      if (bf16)
-        NB_TRY(gemv_bf16("gemv_bf16", op->Lb, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
-      else
-        NB_TRY(gemv("gemv", op->L, n, ld, ws->xf, ws->w, nrhs, ws->done, ws->scal, s));
-      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a, 0));
+      NB_TRY(matvec(op, ws, 0, engine, ws->w, ws->done, ws->scal,
+                    engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
+      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 0));
-      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a, 1));
+      NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 1));
       NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 1));
     }
@@ -707,6 +992,74 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, b
   return NAT_BEM_OK;
 }
 
+__global__ void k_to_c64(const double2* __restrict__ y, int64_t count, float2* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = make_float2((float)y[i].x, (float)y[i].y);
+}
+
+nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d_x, int nrhs,
+                          float2* d_y, cudaStream_t s) {
+  const int n = (int)op->n, ld = (int)op->geo.ld;
+  float2* xpad = nullptr;
+  double2* y64 = nullptr;
+  void* scratch = nullptr;
+  int* err = nullptr;
+  size_t sbytes = 0;
+  nat_bem_status st = NAT_BEM_OK;
+  auto cleanup = [&]() {
+    dev_free(xpad, s);
+    dev_free(y64, s);
+    dev_free(scratch, s);
+    dev_free(err, s);
+  };
+  if ((st = dev_alloc_n(&xpad, (size_t)ld * nrhs, s)) != NAT_BEM_OK ||
+      (st = dev_alloc_n(&y64, (size_t)n * nrhs, s)) != NAT_BEM_OK ||
+      (st = dev_alloc_n(&err, 1, s)) != NAT_BEM_OK) {
+    cleanup();
+    return st;
+  }
+  cudaMemsetAsync(err, 0, sizeof(int), s);
+  const int64_t tot = (int64_t)ld * nrhs;
+  NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_x, n, ld, nrhs, xpad));
+  const float2* M = which == 0 ? op->L : op->R;
+  if (engine >= NAT_BEM_ENGINE_GEMV0) {
+    st = gemv_launch(engine - NAT_BEM_ENGINE_GEMV0, "gemv_apply", M, n, ld, xpad, y64, nrhs, nullptr,
+                     nullptr, err, s);
+  } else if (engine == NAT_BEM_ENGINE_AUTO && nrhs == 1) {
+    st = gemv("gemv_apply", M, n, ld, xpad, y64, 1, nullptr, nullptr, s, err);
+  } else {
+    const int eng = engine == NAT_BEM_ENGINE_TF32 ? kEngineTf32
+                    : engine == NAT_BEM_ENGINE_BF16 ? kEngineBf16 : kEngineFp32;
+    if (eng != kEngineFp32) {
+      int dev = 0, sms = 148;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      sbytes = tc_workspace_bytes(n, ld, nrhs, sms);
+      if ((st = dev_alloc(&scratch, sbytes, s)) != NAT_BEM_OK) {
+        cleanup();
+        return st;
+      }
+    }
+    st = product(op, which, eng, xpad, nrhs, y64, nullptr, nullptr, scratch, sbytes, err, s);
+  }
+  if (st == NAT_BEM_OK) {
+    const int64_t cnt = (int64_t)n * nrhs;
+    NB_LAUNCH("to_c64", s, k_to_c64<<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(y64, cnt, d_y));
+    int herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("nat_bem_op_apply: ") + cudaGetErrorString(e));
+      st = NAT_BEM_ECUDA;
+    } else if (herr) {
+      set_error("nat_bem_op_apply: a bounded wait gave up (code " + std::to_string(herr) + ")");
+      st = NAT_BEM_ECUDA;
+    }
+  }
+  cleanup();
+  return st;
+}
+
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
                           nat_bem_solve_info* info, cudaStream_t s) {
   NB_TRY(workspace_ensure(op, nrhs, s));
@@ -719,19 +1072,30 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     const int64_t tot = (int64_t)ld * nrhs;
     NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, n, ld, nrhs, ws->gin));
     NB_CHECK_LAUNCH();
-    NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s));
+    if (nrhs == 1)
+      NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s, ws->tc_err));
+    else
+      NB_TRY(product(op, 1, kEngineFp32, ws->gin, nrhs, ws->b, nullptr, nullptr, ws->tc_scratch,
+                     ws->tc_bytes, ws->tc_err, s));
   }
   std::vector<int> iters(nrhs), done(nrhs), total(nrhs, 0);
   std::vector<double> rt(nrhs);
   int refinements = 0;
   bool converged = true;
-  const bool mixed = o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb != nullptr;
+  // engines: the accurate product (FP32 GEMV for one RHS, FP32 CUDA-core GEMM for several) and
+  // the inner product of mixed refinement (BF16 GEMV for one RHS; tensor cores for several:
+  // TF32 on L or BF16 on its copy). TF32 with one RHS would save no bytes: it runs plain.
+  const int accurate = nrhs == 1 ? kEngineGemv : kEngineFp32;
+  int inner = accurate;
+  if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = nrhs == 1 ? kEngineGemvBf16 : kEngineBf16;
+  if (o.prec == NAT_BEM_PREC_MIXED_TF32 && nrhs > 1) inner = kEngineTf32;
+  const bool mixed = inner != accurate;
   if (!mixed) {
     GArgs a = make_args(op, ws, op->L);
     a.maxit = o.max_iter;
-    NB_TRY(gmres_run(op, ws, a, false, 0, d_p, s));
+    NB_TRY(gmres_run(op, ws, a, accurate, 0, d_p, s));
     // true residual ||R g - L p|| / ||R g|| with the FP32 operator
-    NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
+    NB_TRY(matvec(op, ws, 0, accurate, ws->w, nullptr, nullptr, "gemv_resid", s));
     NB_LAUNCH("gmres_resid", s, k_resid<<<vec_grid, kChunk, 0, s>>>(a));
     NB_CHECK_LAUNCH();
     NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -757,8 +1121,8 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     std::vector<int> od(nrhs);
     for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
       a.maxit = std::min(o.inner_max_iter, budget);
-      NB_TRY(gmres_run(op, ws, a, true, 1, d_p, s));
-      NB_TRY(gemv("gemv_resid", op->L, n, ld, ws->xf, ws->w, nrhs, nullptr, nullptr, s));
+      NB_TRY(gmres_run(op, ws, a, inner, 1, d_p, s));
+      NB_TRY(matvec(op, ws, 0, accurate, ws->w, nullptr, nullptr, "gemv_resid", s));
       NB_LAUNCH("ir_residual", s, k_ir_residual<<<vec_grid, kChunk, 0, s>>>(a, ws->b0, ws->outer_done, o.tol));
       NB_CHECK_LAUNCH();
       NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -776,6 +1140,13 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       for (int q = 0; q < nrhs; ++q) converged = converged && od[q];
       if (converged) break;
     }
+  }
+  int tc_err = 0;
+  NB_TRY_CUDA(cudaMemcpyAsync(&tc_err, ws->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NB_TRY_CUDA(cudaStreamSynchronize(s));
+  if (tc_err) {
+    set_error("tensor-core product: a bounded wait gave up (code " + std::to_string(tc_err) + ")");
+    return NAT_BEM_ECUDA;
   }
   int maxit = 0;
   double maxres = 0.0;

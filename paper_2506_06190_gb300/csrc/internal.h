@@ -133,7 +133,18 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s);
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
                           nat_bem_solve_info* info, cudaStream_t s);
 void workspace_free(Workspace* ws, cudaStream_t s);
+nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d_x, int nrhs,
+                          float2* d_y, cudaStream_t s);
 int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o);
+
+// products.cu: Y = M X for nrhs right-hand sides (M = L for which == 0, R for 1).
+// kEngineFp32: FP32 CUDA-core complex GEMM; kEngineTf32 / kEngineBf16: tcgen05 tensor cores
+// on L (TF32) or its BF16 copy, using `scratch` for the packed B and the split-K partials.
+enum Engine { kEngineGemv = 0, kEngineGemvBf16 = 1, kEngineFp32 = 2, kEngineTf32 = 3, kEngineBf16 = 4 };
+nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
+                       double2* Y, const int* done, const int* scal, void* scratch,
+                       size_t scratch_bytes, int* err, cudaStream_t s);
+size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms);
 
 // eval.cu
 nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,

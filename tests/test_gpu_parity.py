@@ -250,3 +250,75 @@ def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib):
     jd = jobs[4]
     p_ref, _ = oracle_lib.solve(jd["V"], jd["F"], jd["k"], jd["neumann"])
     assert _rel(res[4][0], p_ref) < SOL_TOL
+
+
+@pytest.fixture(scope="module")
+def product_case(oracle_lib):
+    Vs, F = S.ring_sphere(1500)          # 1500 rows: the last 128-row tile is partial
+    V = S.perturbed_ellipsoid(Vs, 77)
+    k = 4.0
+    L, R = oracle_lib.assemble(V, F, k)
+    rng = np.random.default_rng(5)
+    X = (rng.normal(size=(len(F), 100)) + 1j * rng.normal(size=(len(F), 100))).astype(np.complex64)
+    return V, F, k, L, R, np.asfortranarray(X)
+
+
+@pytest.mark.parametrize("variant", range(5))
+def test_gemv_variants_match_oracle(nb, product_case, variant):
+    """Every GEMV variant (register-tiled and bulk-copy) computes L x and R x to FP32 accuracy."""
+    V, F, k, L, R, X = product_case
+    x = X[:, 0].copy()
+    with nb.Operator.assemble(V, F, k) as op:
+        for which, M in ((0, L), (1, R)):
+            y = op.apply(which, nb.ENGINE_GEMV0 + variant, x)
+            assert _rel(y, M @ x.astype(np.complex128)) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 6, 40])
+def test_fp32_gemm_matches_oracle(nb, product_case, nrhs):
+    V, F, k, L, R, X = product_case
+    Xs = np.asfortranarray(X[:, :nrhs])
+    with nb.Operator.assemble(V, F, k) as op:
+        for which, M in ((0, L), (1, R)):
+            Y = op.apply(which, nb.ENGINE_FP32, Xs)
+            ref = M @ Xs.astype(np.complex128)
+            assert _rel(Y, ref) < 1e-5
+            assert np.max(np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 6, 40, 64, 100])
+def test_tensor_core_products_match_oracle(nb, product_case, nrhs):
+    """tcgen05 TF32 (on L) and BF16 (on its copy) products: FP32 accumulation of operands
+    carrying 10 (TF32, truncated by the MMA) and 8 (BF16, rounded) fraction bits, so the
+    relative error is bounded by about 2^-10 and 2^-8 per product."""
+    V, F, k, L, R, X = product_case
+    Xs = np.asfortranarray(X[:, :nrhs])
+    ref = L @ Xs.astype(np.complex128)
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16)
+    with nb.Operator.assemble(V, F, k, opts) as op:
+        Yt = op.apply(0, nb.ENGINE_TF32, Xs)
+        Yb = op.apply(0, nb.ENGINE_BF16, Xs)
+    for Y, tol in ((Yt, 2e-3), (Yb, 8e-3)):
+        err = np.linalg.norm(Y.reshape(len(F), -1) - ref.reshape(len(F), -1), axis=0) / \
+            np.linalg.norm(ref.reshape(len(F), -1), axis=0)
+        assert np.all(err < tol), (err.max(), tol)
+        assert np.all(err > 1e-7)  # really the reduced-precision path
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_multi_rhs_mixed_tensor_core_solve(nb, oracle_lib, prec):
+    """Inner GMRES products on tensor cores, refinement against the FP32 operator: each RHS
+    within 1e-4 of the FP64 oracle."""
+    Vs, F = S.ring_sphere(1200)
+    V = S.perturbed_ellipsoid(Vs, 8)
+    k = 3.3
+    G = S.sh_neumann(V, F, 8, 12)
+    L, R = oracle_lib.assemble(V, F, k)
+    p_const = nb.PREC_MIXED_TF32 if prec == "tf32" else nb.PREC_MIXED_BF16
+    opts = nb.nat_bem_opts_default(prec=p_const)
+    with nb.Operator.assemble(V, F, k, opts) as op:
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        assert info.refinements >= 1 and info.rel_residual <= 1e-6
+    for s in range(G.shape[1]):
+        assert _rel(P[:, s], np.linalg.solve(L, R @ G[:, s])) < SOL_TOL
