@@ -216,6 +216,177 @@ def run_gpu(args, rank: int, world: int):
     return out
 
 
+# ------------------------------------------------------------------------- other workloads
+def _percentiles(xs):
+    return {"p50": float(np.percentile(xs, 50)), "p99": float(np.percentile(xs, 99))}
+
+
+def run_modal(args):
+    """Multi-RHS modal transfer: one perturbed 20480-triangle icosphere (or a ring sphere of
+    --n-tri triangles), --nrhs smooth real SH Neumann fields (l <= 8) shared by --n-k
+    wavenumbers in ka [1, 15], 4096 shell points r in [2, 5]. One step: for each wavenumber,
+    re-assemble, solve all right-hand sides in one block, evaluate the field. A solve is one
+    (mesh, k, RHS)."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    if args.n_tri == 20480:
+        prob = S.modal_multirhs(nrhs=args.nrhs, n_k=args.n_k)
+    else:
+        Vs, F = S.ring_sphere(args.n_tri)
+        V = S.perturbed_ellipsoid(Vs, 3000)
+        prob = S.Problem("modal_multirhs", V, F, S.log_uniform(args.n_k, 1.0, 15.0, 3001),
+                         [S.sh_neumann(V, F, args.nrhs, 3002)] * args.n_k, S.shell_points(4096, 2.0, 5.0, 3003))
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    Vd, Fd = torch.from_numpy(prob.V).to(dev), torch.from_numpy(prob.F).to(dev)
+    G = torch.from_numpy(np.ascontiguousarray(prob.neumann[0].T).astype(np.complex64)).to(dev)
+    Pd = torch.from_numpy(prob.points).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = nb.Operator.assemble(Vd, Fd, float(prob.ks[0]), opts)
+    infos = []
+
+    def step(record=None):
+        for k in prob.ks:
+            op.reassemble(float(k), like=Vd)
+            p, info, st = op.solve(G)
+            f = op.evaluate(Pd, p, G)
+            if record is not None:
+                record.append((info.iterations, info.refinements, info.rel_residual, st))
+        return p, f
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            p, f = step(infos)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    n_solves = args.steps * len(prob.ks) * args.nrhs
+    # accuracy of the last wavenumber against the FP64 oracle on two right-hand sides
+    acc = None
+    if args.cpu and len(prob.F) <= 6000:
+        import oracle
+        L, R = oracle.assemble(prob.V, prob.F, float(prob.ks[-1]))
+        pc = p.cpu().numpy()
+        errs = []
+        for c in (0, args.nrhs - 1):
+            pref = np.linalg.solve(L, R @ prob.neumann[0][:, c])
+            errs.append(float(np.linalg.norm(pc[c] - pref) / np.linalg.norm(pref)))
+        acc = {"max_rel_err_vs_oracle": max(errs), "checked": "2 RHS of the last wavenumber"}
+    op.close()
+    return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32 tensor cores + f32 refinement", "bf16": "bf16 tensor cores + f32 refinement"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": f"modal_multirhs_{len(prob.F)}tri_{args.nrhs}rhs_{len(prob.ks)}k",
+                       "precision": args.prec, "field_points": 4096},
+            "gmres": {"iterations_max": max(i[0] for i in infos), "refinements_max": max(i[1] for i in infos),
+                      "max_rel_residual": max(i[2] for i in infos),
+                      "not_converged": sum(1 for i in infos if i[3] != 0)},
+            "accuracy": acc, "clocks": clk.summary()}
+
+
+def run_uneven(args):
+    """Uneven batch: --n-mesh perturbed ring spheres of 500-8000 triangles (log-uniform), one
+    wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4, through the
+    batch driver (largest first, --concurrency workers)."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    probs = S.uneven_batch(n_mesh=args.n_mesh)
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    jobs = []
+    for pr in probs:
+        jobs.append(dict(V=torch.from_numpy(pr.V).to(dev), F=torch.from_numpy(pr.F).to(dev), k=float(pr.ks[0]),
+                         neumann=torch.from_numpy(np.ascontiguousarray(pr.neumann[0][:, 0]).astype(np.complex64)).to(dev),
+                         points=torch.from_numpy(pr.points).to(dev)))
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        nb.nat_bem_run_batch(jobs, opts, concurrency=args.concurrency)
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lats = []
+    with ClockSampler(0) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            st, res = nb.nat_bem_run_batch(jobs, opts, concurrency=args.concurrency)
+            lats += [r[4] for r in res]
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    sizes = [int(pr.F.shape[0]) for pr in probs]
+    return {"metric": METRIC, "value": args.steps * len(jobs) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+            "data": "synthetic",
+            "config": {"workload": f"uneven_batch_{len(jobs)}meshes", "n_tri_range": [min(sizes), max(sizes)],
+                       "mean_n_tri": float(np.mean(sizes)), "concurrency": args.concurrency},
+            "latency_ms": dict(_percentiles(lats), per="one solve, device time, in the batch"),
+            "not_converged": sum(1 for r in res if r[3] != 0), "clocks": clk.summary()}
+
+
+def run_serving(args):
+    """Serving stream: Poisson arrivals (--rate per second) of --n-req requests with meshes of
+    1k-40k triangles (log-uniform; drawn from a pool of pre-built perturbed ring spheres), ka in
+    [0.5, 20], 1-32 right-hand sides, admitted by dense-operator memory under --budget-gb of HBM.
+    Requests are submitted at their arrival times; latency is submit to completion."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    stream_def = S.serving_stream(n_req=args.n_req, rate=args.rate)
+    pool_sizes = np.unique(np.geomspace(1000, 40000, 12).astype(int) // 2 * 2)
+    pool = {}
+    for nt in pool_sizes:
+        Vs, F = S.ring_sphere(int(nt))
+        pool[int(nt)] = (S.perturbed_ellipsoid(Vs, 5000 + int(nt)), F)
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    reqs = []
+    pts = torch.from_numpy(S.fibonacci_points(256, 4.0)).to(dev)
+    for (t_arr, nt_target, ka, nrhs, seed) in stream_def:
+        nt = int(pool_sizes[np.argmin(np.abs(pool_sizes - nt_target))])
+        V, F = pool[nt]
+        g = S.sh_neumann(V, F, nrhs, seed)
+        reqs.append((t_arr, dict(V=torch.from_numpy(V).to(dev), F=torch.from_numpy(F).to(dev), k=float(ka),
+                                 neumann=torch.from_numpy(np.ascontiguousarray(g.T).astype(np.complex64)).to(dev),
+                                 points=pts), nrhs))
+    torch.cuda.synchronize()
+    budget = int(args.budget_gb * (1 << 30))
+    with nb.Server(budget, opts, slots=args.concurrency) as srv:
+        t_start = time.perf_counter()
+        tickets = []
+        for t_arr, jd, nrhs in reqs:
+            while time.perf_counter() - t_start < t_arr:
+                time.sleep(0.0005)
+            tickets.append((srv.submit(jd), nrhs))
+        res = [(srv.wait(t, -1), nrhs) for t, nrhs in tickets]
+        t_end = time.perf_counter()
+    lat = [r[0][6] for r in res]
+    solves = sum(nrhs for r, nrhs in res if r[0] == 0)
+    return {"metric": METRIC, "value": solves / (t_end - t_start), "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * (t_end - t_start), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": f"serving_poisson_{args.rate}per_s_{args.n_req}req", "budget_gb": args.budget_gb,
+                       "slots": args.concurrency, "offered_rate_req_s": args.rate},
+            "requests_per_s": len(res) / (t_end - t_start),
+            "latency_ms": dict(_percentiles(lat), per="request, submit to completion (queueing included)"),
+            "queue_ms": _percentiles([r[0][5] for r in res]),
+            "statuses": {str(k): int(v) for k, v in zip(*np.unique([r[0][0] for r in res], return_counts=True))}}
+
+
 def roofline(res, peaks, peak_kind):
     """Dominant kernel's achieved rate against its ceiling."""
     n = res["n"]
@@ -281,6 +452,12 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
+    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve"])
+    ap.add_argument("--nrhs", type=int, default=64)
+    ap.add_argument("--n-mesh", type=int, default=512)
+    ap.add_argument("--n-req", type=int, default=300)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()
@@ -316,6 +493,15 @@ def main():
         return
 
     import torch
+    if args.workload != "interior":
+        if rank == 0:
+            fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving}[args.workload]
+            if args.workload == "modal" and args.n_k == 64:
+                args.n_k = 16
+            if args.workload == "modal" and args.n_tri == 10240:
+                args.n_tri = 20480
+            print(json.dumps(fn(args)))
+        return
     if world > 1:
         torch.distributed.init_process_group("nccl")
     res = run_gpu(args, rank, world)

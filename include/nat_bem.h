@@ -213,6 +213,44 @@ NAT_BEM_API nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which,
                                             void* cuda_stream);
 
 /*
+ * Serving (no counterpart in the paper; it serves the data-generation loop of Sec. 3.4). A
+ * server runs `slots` workers, each with its own stream. Requests (nat_bem_job, as for the
+ * batch driver) are admitted in arrival order as soon as a worker is free and the device
+ * bytes the request needs (nat_bem_required_bytes) fit under budget_bytes next to the requests
+ * already running; admitted requests overlap on the device. A request that needs more than the
+ * whole budget finishes with status NAT_BEM_ENOMEM. The job struct and its arrays must stay
+ * valid until nat_bem_wait returns for its ticket. Results do not depend on what else runs:
+ * every reduction has a fixed order.
+ *   nat_bem_server_create: NAT_BEM_EINVAL (budget <= 0, slots not in 1..64), NAT_BEM_ECUDA
+ *     (no device). With the environment variable NATBEM_SERVER_FAKE=1 the workers do no device
+ *     work (a request "takes" nt x 10 us and succeeds): a mode for testing the host logic.
+ *   nat_bem_submit: enqueue; *ticket identifies the request. NAT_BEM_EBUSY after destroy began.
+ *   nat_bem_wait: waits up to timeout_ms (< 0: forever) and returns the request's status, or
+ *     NAT_BEM_ETIMEOUT (the request stays queued; wait again). queue_ms / total_ms (may be
+ *     NULL): host time from submit to admission and to completion.
+ *   nat_bem_server_reserved: device bytes reserved by running requests.
+ *   nat_bem_server_destroy: finishes queued and running requests, then stops the workers.
+ */
+typedef struct nat_bem_server nat_bem_server;
+NAT_BEM_API nat_bem_status nat_bem_server_create(int64_t budget_bytes, const nat_bem_opts* opts,
+                                                 int32_t slots, nat_bem_server** out);
+NAT_BEM_API nat_bem_status nat_bem_submit(nat_bem_server* srv, nat_bem_job* job, int64_t* ticket);
+NAT_BEM_API nat_bem_status nat_bem_wait(nat_bem_server* srv, int64_t ticket, int32_t timeout_ms,
+                                        double* queue_ms, double* total_ms);
+NAT_BEM_API int64_t nat_bem_server_reserved(nat_bem_server* srv);
+NAT_BEM_API void nat_bem_server_destroy(nat_bem_server* srv);
+
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper). A kernel waits on an
+ * mbarrier that nothing ever completes, with the same bounded-wait code the tensor-core and
+ * bulk-copy kernels use but a deadline of timeout_ms (1..10000); it must give up, report it
+ * through a device flag and return. Returns NAT_BEM_ETIMEOUT when it did (the expected
+ * result; the CUDA context stays usable), NAT_BEM_OK if the wait completed (never expected),
+ * NAT_BEM_EINVAL for a bad timeout, NAT_BEM_ECUDA for a CUDA failure. Blocks until done.
+ */
+NAT_BEM_API nat_bem_status nat_bem_selftest_bounded_wait(int32_t timeout_ms, void* cuda_stream);
+
+/*
  * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
  * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
  * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.

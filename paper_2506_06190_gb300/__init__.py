@@ -33,7 +33,9 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_op_rows", "nat_bem_op_size", "nat_bem_required_bytes", "nat_bem_destroy",
             "nat_bem_last_error", "nat_bem_trace_enable", "nat_bem_trace_reset",
             "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc",
-            "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply"]
+            "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply",
+            "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
+            "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 
 
@@ -89,6 +91,18 @@ def lib():
         L.nat_bem_eval_noalloc.restype = ctypes.c_int
         L.nat_bem_run_batch.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Opts), i32, vp]
         L.nat_bem_run_batch.restype = ctypes.c_int
+        L.nat_bem_server_create.argtypes = [i64, ctypes.POINTER(Opts), i32, ctypes.POINTER(vp)]
+        L.nat_bem_server_create.restype = ctypes.c_int
+        L.nat_bem_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(i64)]
+        L.nat_bem_submit.restype = ctypes.c_int
+        L.nat_bem_wait.argtypes = [vp, i64, i32, ctypes.POINTER(d), ctypes.POINTER(d)]
+        L.nat_bem_wait.restype = ctypes.c_int
+        L.nat_bem_server_reserved.argtypes = [vp]
+        L.nat_bem_server_reserved.restype = i64
+        L.nat_bem_server_destroy.argtypes = [vp]
+        L.nat_bem_server_destroy.restype = None
+        L.nat_bem_selftest_bounded_wait.argtypes = [i32, vp]
+        L.nat_bem_selftest_bounded_wait.restype = ctypes.c_int
         L.nat_bem_op_apply.argtypes = [vp, i32, i32, vp, i32, vp, vp]
         L.nat_bem_op_apply.restype = ctypes.c_int
         L.nat_bem_op_rows.argtypes = [vp, i32, i64, i64, vp, vp]
@@ -304,6 +318,77 @@ def nat_bem_op_apply(op, which: int, engine: int, X, stream=None):
     py, ky = _ptr(Y, np.complex64)
     _check(lib().nat_bem_op_apply(op, int(which), int(engine), px, nrhs, py, _stream_of(X, stream)))
     return Y
+
+
+def _make_job(jd):
+    """A Job struct for a job dict, with its output arrays and the references that keep the
+    inputs alive (see nat_bem_run_batch for the dict keys)."""
+    V, F, g = jd["V"], jd["F"], jd["neumann"]
+    pts = jd.get("points")
+    n = int(F.shape[0])
+    nrhs = _nrhs_of(g, n)
+    pv, kv = _ptr(V, np.float64)
+    pt, kt = _ptr(F, np.int32)
+    pg, kg = _ptr(g, np.complex64)
+    m = 0 if pts is None else int(pts.shape[0])
+    if _is_torch(g):
+        import torch
+        p = torch.empty(tuple(g.shape), dtype=torch.complex64, device=g.device)
+        f = torch.empty((nrhs, m) if g.dim() == 2 else (m,), dtype=torch.complex64, device=g.device)
+    else:
+        p = np.zeros((n, nrhs) if np.ndim(g) == 2 else (n,), dtype=np.complex64, order="F")
+        f = np.zeros((m, nrhs) if np.ndim(g) == 2 else (m,), dtype=np.complex64, order="F")
+    pp, kp = _ptr(p, np.complex64)
+    pf, kf = _ptr(f, np.complex64)
+    ppt, kpt = _ptr(pts, np.float64) if pts is not None else (ctypes.c_void_p(0), None)
+    job = Job(pv, int(V.shape[0]), pt, n, float(jd["k"]), pg, nrhs, ppt, m, pp, pf, SolveInfo(), 0, 0.0)
+    return job, p, f, [kv, kt, kg, kp, kf, kpt]
+
+
+class Server:
+    """Serving loop of the library (nat_bem_server_*): submit job dicts, wait for tickets."""
+
+    def __init__(self, budget_bytes: int, opts: Opts | None = None, slots: int = 4):
+        self.handle = ctypes.c_void_p()
+        _check(lib().nat_bem_server_create(int(budget_bytes), ctypes.byref(opts) if opts else None,
+                                           int(slots), ctypes.byref(self.handle)))
+        self._live = {}
+
+    def submit(self, jd) -> int:
+        job, p, f, keep = _make_job(jd)
+        t = ctypes.c_int64(0)
+        _check(lib().nat_bem_submit(self.handle, ctypes.byref(job), ctypes.byref(t)))
+        self._live[t.value] = (job, p, f, keep)
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(status, p, field, SolveInfo, device_ms, queue_ms, total_ms); status ETIMEOUT leaves
+        the request queued."""
+        q, tot = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        st = lib().nat_bem_wait(self.handle, int(ticket), int(timeout_ms), ctypes.byref(q), ctypes.byref(tot))
+        if st == NAT_BEM_ETIMEOUT:
+            return st, None, None, None, None, None, None
+        job, p, f, keep = self._live.pop(ticket)
+        return st, p, f, job.info, job.device_ms, q.value, tot.value
+
+    def reserved(self) -> int:
+        return int(lib().nat_bem_server_reserved(self.handle))
+
+    def close(self):
+        if self.handle:
+            lib().nat_bem_server_destroy(self.handle)
+            self.handle = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def nat_bem_selftest_bounded_wait(timeout_ms: int = 50, stream=None) -> int:
+    return int(lib().nat_bem_selftest_bounded_wait(int(timeout_ms), _stream_of(None, stream)))
 
 
 def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:

@@ -962,7 +962,8 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
                                 int accumulate, float2* pout, cudaStream_t s) {
   const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
   const dim3 upd_grid(ws->nchunk, nrhs), fin_grid((n + kChunk - 1) / kChunk, nrhs);
-  const dim3 dot_grid(std::max(1, a.maxit), kDotChunks, nrhs);
+  // the dot-product grid covers the Krylov vectors 0..j of the iteration being launched (the
+  // device's j equals the host's launch count until every RHS is done)
   NB_LAUNCH("gmres_start", s, k_start<<<upd_grid, kUpdRows, 0, s>>>(a));
   NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 0));
   NB_CHECK_LAUNCH();
@@ -972,6 +973,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
     for (int q = 0; q < c; ++q) {
       NB_TRY(matvec(op, ws, 0, engine, ws->w, ws->done, ws->scal,
                     engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
+      const dim3 dot_grid(std::min(it + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
       NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 0));
       NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));

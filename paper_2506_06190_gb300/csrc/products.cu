@@ -69,13 +69,14 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// Bounded wait: false if the phase did not complete within about two seconds (or kSpinLimit
-// polls, whichever comes first).
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Bounded wait: false if the phase did not complete within timeout_ns (default about two
+// seconds) or kSpinLimit polls, whichever comes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint64_t timeout_ns = 2000000000ull) {
   const uint64_t t0 = globaltimer_ns();
   for (uint32_t i = 0; i < kSpinLimit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 1023u) == 1023u && globaltimer_ns() - t0 > 2000000000ull) return false;
+    if ((i & 1023u) == 1023u && globaltimer_ns() - t0 > timeout_ns) return false;
   }
   return false;
 }
@@ -388,6 +389,18 @@ k_cgemm_fp32(const float2* __restrict__ A, int n, int ld, const float2* __restri
     }
 }
 
+// An mbarrier that nothing completes: the bounded wait must give up (result 2) and return.
+__global__ void k_selftest_wait(uint64_t timeout_ns, int* __restrict__ result) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(smem_u32(&bar), 0, timeout_ns);
+  if (threadIdx.x == 0) *result = ok ? 1 : 2;
+}
+
 // --------------------------------------------------------------------------- host side
 namespace {
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -497,21 +510,20 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
   NB_TRY(make_map(&tb, dt, B, (uint64_t)Kt, (uint64_t)Ng, (uint64_t)Kt * esz, (uint32_t)BK, (uint32_t)Ng));
   const size_t smem = 1024 + (size_t)kTcStages * (kTcRows * 128 + (size_t)Ng * 128) + 8 * (2 * kTcStages + 2);
   dim3 grid(m_tiles, nsplit);
-  if (engine == kEngineTf32) {
-    static bool attr0 = false;
-    if (!attr0) {
-      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      attr0 = true;
-    }
-    NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
-  } else {
-    static bool attr1 = false;
-    if (!attr1) {
-      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      attr1 = true;
-    }
-    NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
+  // opt in to the dynamic shared memory this launch needs (once per size increase)
+  static size_t attr_set[2] = {0, 0};
+  const int ki = engine == kEngineTf32 ? 0 : 1;
+  if (smem > attr_set[ki]) {
+    if (ki == 0)
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    else
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr_set[ki] = smem;
   }
+  if (ki == 0)
+    NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
+  else
+    NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
   NB_CHECK_LAUNCH();
   const int64_t tot = (int64_t)nrhs * n;
   NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, n, Ng, P, nrhs, nsplit, Y, done, scal));
@@ -520,3 +532,29 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
 }
 
 }  // namespace natbem
+
+extern "C" nat_bem_status nat_bem_selftest_bounded_wait(int32_t timeout_ms, void* cuda_stream) {
+  using namespace natbem;
+  clear_error();
+  if (timeout_ms < 1 || timeout_ms > 10000) {
+    set_error("nat_bem_selftest_bounded_wait: timeout_ms must be in [1, 10000]");
+    return NAT_BEM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* d = nullptr;
+  NB_TRY(dev_alloc_n(&d, 1, s));
+  NB_TRY_CUDA(cudaMemsetAsync(d, 0, sizeof(int), s));
+  NB_LAUNCH("selftest_wait", s, k_selftest_wait<<<1, 32, 0, s>>>((uint64_t)timeout_ms * 1000000ull, d));
+  NB_CHECK_LAUNCH();
+  int h = 0;
+  NB_TRY_CUDA(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+  NB_TRY_CUDA(cudaStreamSynchronize(s));
+  dev_free(d, s);
+  if (h == 2) {
+    set_error("bounded device wait gave up as intended");
+    return NAT_BEM_ETIMEOUT;
+  }
+  if (h == 1) return NAT_BEM_OK;
+  set_error("self-test kernel did not report");
+  return NAT_BEM_ECUDA;
+}

@@ -111,10 +111,12 @@ def test_multi_rhs_matches_oracle_and_single(nb, oracle_lib):
             assert _rel(P[:, s], p_ref) < SOL_TOL
             f_ref = oracle_lib.evaluate(V, F, k, pts, p_ref, G[:, s])
             assert _rel(fld[:, s], f_ref) < SOL_TOL
-        # batch invariance: each RHS alone gives the same bits as inside the block
+        # alone (GEMV products) and inside the block (FP32 GEMM products) the same RHS agrees
+        # to FP32 rounding; the bitwise check of the same request alone and in a mix is in
+        # test_serving.py
         for s in (0, 3):
             p1, _, _ = op.solve(G[:, s])
-            assert np.array_equal(p1, P[:, s])
+            assert _rel(p1, P[:, s]) < 1e-5
 
 
 def test_device_pointers_match_host(nb):
