@@ -251,7 +251,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (ok && !s_abort) {
     const int row = m0 + warp * 32 + lane;
     float* out = part + ((size_t)ks * n + (size_t)row) * Ng;
-    for (int c0 = 0; c0 < Ng; c0 += 32) {
+    for (int c0 = 0; c0 < Ng; c0 += 32) {  // Ng is a multiple of 32
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
       if (row < n && nk > 0) {
@@ -271,7 +271,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
-// B for the tensor-core product from nrhs complex64 vectors (x_c at X + c * ld): rows c < P
+// B for the tensor-core product from nrhs complex64 vectors (x_c at X + c * ld), P = nrhs
+// rounded up to 16 (so the epilogue reads whole 32-column TMEM chunks): rows c < P
 // (Re, -Im) pairs, rows P + c (Im, Re) pairs; rows of absent RHS are zero. TF32: FP32 storage;
 // BF16: round to nearest.
 template <int kKind>
@@ -447,7 +448,7 @@ nat_bem_status make_map(CUtensorMap* map, CUtensorMapDataType dt, const void* pt
 }  // namespace
 
 size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
-  const int P = (int)round_up(nrhs, 8);
+  const int P = (int)round_up(nrhs, 16);  // N = 2P is a multiple of 32: whole TMEM loads
   const int Ng = 2 * P;
   const int64_t m_tiles = (n + kTcRows - 1) / kTcRows;
   const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(16, (4 * sms + m_tiles - 1) / m_tiles));
@@ -473,7 +474,7 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int P = (int)round_up(nrhs, 8);
+  const int P = (int)round_up(nrhs, 16);  // N = 2P is a multiple of 32: whole TMEM loads
   const int Ng = 2 * P;
   if (Ng > 256) {
     set_error("tensor-core product takes at most 128 right-hand sides per call");
