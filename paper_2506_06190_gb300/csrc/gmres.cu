@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -46,6 +47,9 @@ struct Workspace {
   float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
   int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
   int* outer_done = nullptr;                               // refinement: converged RHS
+  // captured iteration chunks: key (engine, first iteration, count, cap, tol, refinement mode)
+  std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+  bool graphs_off = false;
   void* tc_scratch = nullptr;                              // packed B + split-K partials
   size_t tc_bytes = 0;
   int* tc_err = nullptr;                                   // bounded-wait failures
@@ -130,22 +134,50 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
   s = t;
 }
 
-// Sum over the block of (s - c) per row, combined in FP64 (8 warps of 32 lanes).
+// Error-free transformation (Knuth's TwoSum): s + e == a + b exactly in FP32 arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) += (hi2, lo2) as double-float (an unevaluated FP32 pair, about 48 bits).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo2) {
+  float s, e;
+  two_sum(hi, hi2, s, e);
+  e += lo + lo2;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
+// Warp sum of a compensated running sum (s, c) as a double-float, all in FP32 (GB300's FP64
+// rate is ~1/64 of FP32, too low even for per-thread FP64 shuffles at the end of each row).
+__device__ __forceinline__ void warp_sum_df(float s, float c, float& hi, float& lo) {
+  two_sum(s, -c, hi, lo);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    df_add(hi, lo, h2, l2);
+  }
+}
+
+// Sum over the block (8 warps) of (s - c) per row: double-float warp sums, then one thread
+// per row adds the eight warp results in FP64.
 template <int kRows>
 __device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], const float (&cr)[kRows],
                                                   const float (&si)[kRows], const float (&ci)[kRows],
                                                   int n, int row0, double2* __restrict__ y) {
-  __shared__ double sh[2 * kRows][8];
+  __shared__ float2 sh[2 * kRows][8];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
-    double vr = (double)sr[r] - (double)cr[r];
-    double vi = (double)si[r] - (double)ci[r];
-    vr = warp_sum(vr);
-    vi = warp_sum(vi);
+    float hr, lr, hi, li;
+    warp_sum_df(sr[r], cr[r], hr, lr);
+    warp_sum_df(si[r], ci[r], hi, li);
     if (lane == 0) {
-      sh[2 * r][wid] = vr;
-      sh[2 * r + 1][wid] = vi;
+      sh[2 * r][wid] = make_float2(hr, lr);
+      sh[2 * r + 1][wid] = make_float2(hi, li);
     }
   }
   __syncthreads();
@@ -153,8 +185,8 @@ __device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], cons
     const int r = threadIdx.x;
     double tr = 0.0, ti = 0.0;
     for (int q = 0; q < 8; ++q) {
-      tr += sh[2 * r][q];
-      ti += sh[2 * r + 1][q];
+      tr += (double)sh[2 * r][q].x + (double)sh[2 * r][q].y;
+      ti += (double)sh[2 * r + 1][q].x + (double)sh[2 * r + 1][q].y;
     }
     y[row0 + r] = make_double2(tr, ti);
   }
@@ -370,11 +402,13 @@ k_gemv_bulk(const float2* __restrict__ A, int n, int ld, const float2* __restric
     }
     __syncwarp();
     if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa_u32(&empty[q])) : "memory");
-    if (seg == nseg - 1) {  // row complete: combine in FP64 (consumer warps only)
-      double vr = warp_sum((double)sr - (double)cr), vi = warp_sum((double)si - (double)ci);
+    if (seg == nseg - 1) {  // row complete: double-float warp sums, FP64 across warps
+      float hr, lr, hi, li;
+      warp_sum_df(sr, cr, hr, lr);
+      warp_sum_df(si, ci, hi, li);
       if (lane == 0) {
-        red[0][warp] = vr;
-        red[1][warp] = vi;
+        red[0][warp] = (double)hr + (double)lr;
+        red[1][warp] = (double)hi + (double)li;
       }
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (threadIdx.x == 0) {
@@ -724,6 +758,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
+  for (auto& kv : ws->graphs) cudaGraphExecDestroy(kv.second.first);
   delete ws;
 }
 
@@ -968,18 +1003,54 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
   NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 0));
   NB_CHECK_LAUNCH();
   int it = 0, chunk = 16;
-  while (it < a.maxit) {
-    const int c = std::min(chunk, a.maxit - it);
+  // Direct launches, or a CUDA graph of the chunk captured once per configuration: graphs need
+  // a capturable (non-legacy) stream and are skipped while per-launch tracing is on.
+  static const bool env_off = std::getenv("NATBEM_NO_GRAPHS") != nullptr;
+  const bool use_graphs = !env_off && !ws->graphs_off && s != nullptr && !tracing_enabled();
+  auto launch_chunk = [&](int it0, int c) -> nat_bem_status {
     for (int q = 0; q < c; ++q) {
       NB_TRY(matvec(op, ws, 0, engine, ws->w, ws->done, ws->scal,
                     engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
-      const dim3 dot_grid(std::min(it + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
+      const dim3 dot_grid(std::min(it0 + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
       NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 0));
       NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 1));
       NB_LAUNCH("gmres_finish", s, k_finish<<<fin_grid, kChunk, 0, s>>>(a, 1));
     }
+    return NAT_BEM_OK;
+  };
+  while (it < a.maxit) {
+    const int c = std::min(chunk, a.maxit - it);
+    bool done_direct = true;
+    if (use_graphs) {
+      const auto key = std::make_tuple(engine, it, c, a.maxit, a.tol, (a.skip ? 1 : 0) + (accumulate ? 2 : 0));
+      auto f = ws->graphs.find(key);
+      if (f == ws->graphs.end()) {
+        const int64_t l0 = launch_count();
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        nat_bem_status cs = ok ? launch_chunk(it, c) : NAT_BEM_ECUDA;
+        ok = (cudaStreamEndCapture(s, &g) == cudaSuccess) && ok && cs == NAT_BEM_OK;
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        const int64_t captured = launch_count() - l0;
+        add_launches(-captured);  // capturing launches nothing
+        if (ok) {
+          f = ws->graphs.emplace(key, std::make_pair(ge, captured)).first;
+        } else {
+          cudaGetLastError();
+          ws->graphs_off = true;  // fall back to direct launches for this workspace
+        }
+      }
+      if (f != ws->graphs.end()) {
+        NB_TRY_CUDA(cudaGraphLaunch(f->second.first, s));
+        add_launches(f->second.second);
+        done_direct = false;
+      }
+    }
+    if (done_direct) NB_TRY(launch_chunk(it, c));
     NB_CHECK_LAUNCH();
     it += c;
     NB_TRY_CUDA(cudaMemcpyAsync(ws->host_scal, ws->scal, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));

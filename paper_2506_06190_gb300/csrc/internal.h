@@ -51,6 +51,10 @@ class TraceScope {
   void* b_ = nullptr;
 };
 
+bool tracing_enabled();
+int64_t launch_count();
+void add_launches(int64_t n);  // kernels launched through a replayed CUDA graph
+
 #define NB_LAUNCH(name, stream, ...)            \
   do {                                          \
     ::natbem::TraceScope nb_trace_(name, stream); \

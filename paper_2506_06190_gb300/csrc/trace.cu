@@ -60,6 +60,10 @@ TraceScope::~TraceScope() {
   }
 }
 
+bool tracing_enabled() { return g_trace.load(std::memory_order_relaxed) != 0; }
+int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 }  // namespace natbem
 
 using namespace natbem;
