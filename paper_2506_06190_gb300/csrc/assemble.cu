@@ -12,8 +12,10 @@
 //                       column j holding that element's rule in registers, collocation rows
 //                       staged through shared memory and read as broadcasts, coalesced row
 //                       stores of L and R. Pairs that share a vertex are skipped.
-//   k_assemble_near     the self pair and vertex-sharing pairs in FP64, one warp per pair with
-//                       the lanes over quadrature points and a shuffle reduction.
+//   k_assemble_near     the self pair and vertex-sharing pairs, one warp per pair with the
+//                       lanes over quadrature points and a shuffle reduction: FP64 geometry
+//                       (points, d = x - y, r, normal components) and FP64 sums, FP32 for the
+//                       smooth kernel factors; the self pair's angular integral in FP64.
 //
 // With d = x - y, r = |d|, rho = k r, q = (d.n_x)(d.n_y)/r^2 the integrands reduce to
 //   dG/dn_y + beta H = G/r^2 [ (d.n_y - b/k) + i (a/k - rho d.n_y) ],
@@ -24,6 +26,7 @@
 
 #include <array>
 #include <cmath>
+#include <cstdlib>
 #include <vector>
 
 #include "internal.h"
@@ -309,6 +312,178 @@ k_assemble_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c
   }
 }
 
+// ---------------------------------------------------- regular pairs, paired FP32 (f32x2)
+// The same arithmetic as k_assemble_regular for two adjacent source columns per thread, with
+// the FP32 operations issued as sm_100 paired instructions (add/sub/mul/fma .rn.f32x2): one
+// instruction does the operation for both columns. The kernel is issue-bound, so this halves
+// the cost of everything except the MUFU operations (rsqrt, sin, cos), which stay scalar.
+namespace {
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk(u64 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 add2(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 sub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 mul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 bc(float x) { return pk(x, x); }
+constexpr int kX2Threads = 128;  // 256 source columns per block, two per thread
+}  // namespace
+
+__global__ void __launch_bounds__(kX2Threads)
+k_assemble_regular_x2(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
+                      const float4* __restrict__ nrm, const float4* __restrict__ qp,
+                      const int4* __restrict__ vid, int n, int ld, int rows_per_block, float k,
+                      float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb) {
+  __shared__ float4 s_hi[kRowStage], s_lo[kRowStage], s_n[kRowStage];
+  __shared__ int4 s_v[kRowStage];
+  const int j0 = (blockIdx.x * kX2Threads + threadIdx.x) * 2;  // columns j0, j0 + 1
+  const bool ok0 = j0 < n, ok1 = j0 + 1 < n;
+  const bool pad0 = !ok0 && j0 < ld, pad1 = !ok1 && j0 + 1 < ld;
+  // column records as pairs (column j0 in the low half, j0 + 1 in the high half)
+  u64 chx, chy, chz, clx, cly, clz, njx, njy, njz, qx[7], qy[7], qz[7], qw[7];
+  int4 v0 = make_int4(-1, -1, -1, 0), v1 = v0;
+  {
+    const int ja = ok0 ? j0 : 0, jb = ok1 ? j0 + 1 : ja;
+    const float4 a = c_hi[ja], b = c_hi[jb];
+    chx = pk(a.x, b.x), chy = pk(a.y, b.y), chz = pk(a.z, b.z);
+    const float4 al = c_lo[ja], bl = c_lo[jb];
+    clx = pk(al.x, bl.x), cly = pk(al.y, bl.y), clz = pk(al.z, bl.z);
+    const float4 an = nrm[ja], bn = nrm[jb];
+    njx = pk(an.x, bn.x), njy = pk(an.y, bn.y), njz = pk(an.z, bn.z);
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+      const float4 qa = qp[7 * ja + p], qb = qp[7 * jb + p];
+      qx[p] = pk(qa.x, qb.x), qy[p] = pk(qa.y, qb.y), qz[p] = pk(qa.z, qb.z), qw[p] = pk(qa.w, qb.w);
+    }
+    if (ok0) v0 = vid[j0];
+    if (ok1) v1 = vid[j0 + 1];
+  }
+  const float kinv = 1.0f / k;
+  const u64 k2 = bc(k), kinv2 = bc(kinv), mkinv2 = bc(-kinv), inv2pi2 = bc(kInvTwoPi);
+  const u64 m2pihi = bc(-kTwoPiHi), m2pilo = bc(-kTwoPiLo), one2 = bc(1.0f), m3 = bc(-3.0f), three2 = bc(3.0f);
+  const int i_begin = blockIdx.y * rows_per_block;
+  const int i_end = min(n, i_begin + rows_per_block);
+  for (int ib = i_begin; ib < i_end; ib += kRowStage) {
+    const int cnt = min(kRowStage, i_end - ib);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      const int i = ib + threadIdx.x;
+      s_hi[threadIdx.x] = c_hi[i];
+      s_lo[threadIdx.x] = c_lo[i];
+      s_n[threadIdx.x] = nrm[i];
+      s_v[threadIdx.x] = vid[i];
+    }
+    __syncthreads();
+    for (int t = 0; t < cnt; ++t) {
+      const int i = ib + t;
+      const size_t off = (size_t)i * ld + j0;
+      if (pad0 || pad1) {  // zero the padding columns (ld > n)
+        if (pad0) {
+          L[off] = make_float2(0.f, 0.f);
+          R[off] = make_float2(0.f, 0.f);
+          if (Lb) Lb[off] = 0u;
+        }
+        if (pad1) {
+          L[off + 1] = make_float2(0.f, 0.f);
+          R[off + 1] = make_float2(0.f, 0.f);
+          if (Lb) Lb[off + 1] = 0u;
+        }
+      }
+      if (!ok0) continue;
+      const int4 vi = s_v[t];
+      const bool w0 = !shares_vertex(vi, v0), w1 = ok1 && !shares_vertex(vi, v1);
+      if (!w0 && !w1) continue;
+      const float4 xh = s_hi[t], xl = s_lo[t], ni = s_n[t];
+      const u64 nix = bc(ni.x), niy = bc(ni.y), niz = bc(ni.z);
+      const u64 Dx = add2(sub2(bc(xh.x), chx), sub2(bc(xl.x), clx));
+      const u64 Dy = add2(sub2(bc(xh.y), chy), sub2(bc(xl.y), cly));
+      const u64 Dz = add2(sub2(bc(xh.z), chz), sub2(bc(xl.z), clz));
+      const u64 dny = fma2(Dx, njx, fma2(Dy, njy, mul2(Dz, njz)));
+      const u64 Dni = fma2(Dx, nix, fma2(Dy, niy, mul2(Dz, niz)));
+      const u64 nxny = fma2(nix, njx, fma2(niy, njy, mul2(niz, njz)));
+      const u64 mnxny = sub2(bc(0.f), nxny);
+      u64 Lr = bc(0.f), Li = Lr, Rr = Lr, Ri = Lr;
+#pragma unroll
+      for (int p = 0; p < 7; ++p) {
+        const u64 dx = sub2(Dx, qx[p]), dy = sub2(Dy, qy[p]), dz = sub2(Dz, qz[p]);
+        const u64 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+        float r2a, r2b;
+        upk(r2, r2a, r2b);
+        const u64 rinv = pk(rsqrtf(r2a), rsqrtf(r2b));
+        const u64 r = mul2(r2, rinv);
+        const u64 dnx = sub2(Dni, fma2(qx[p], nix, fma2(qy[p], niy, mul2(qz[p], niz))));
+        const u64 rho = mul2(k2, r);
+        float ua, ub;
+        upk(mul2(rho, inv2pi2), ua, ub);
+        const u64 nq = pk(rintf(ua), rintf(ub));
+        const u64 th = fma2(nq, m2pilo, fma2(nq, m2pihi, rho));
+        float tha, thb, sa, ca, sb, cb;
+        upk(th, tha, thb);
+        __sincosf(tha, &sa, &ca);
+        __sincosf(thb, &sb, &cb);
+        const u64 gw = mul2(rinv, qw[p]);
+        const u64 Gr = mul2(pk(ca, cb), gw), Gi = mul2(pk(sa, sb), gw);
+        const u64 ri2 = mul2(rinv, rinv);
+        const u64 qq = mul2(mul2(dnx, dny), ri2);
+        const u64 a = fma2(fma2(rho, rho, m3), qq, nxny);
+        const u64 b = mul2(rho, fma2(three2, qq, mnxny));
+        const u64 lr = fma2(b, mkinv2, dny);                 // dny - b/k
+        const u64 nli = fma2(a, mkinv2, mul2(rho, dny));     // -(a/k - rho dny)
+        const u64 Hr = mul2(Gr, ri2), Hi = mul2(Gi, ri2);
+        Lr = fma2(Hr, lr, fma2(Hi, nli, Lr));                // += Hr lr - Hi li
+        Li = sub2(fma2(Hi, lr, Li), mul2(Hr, nli));          // += Hr li + Hi lr
+        const u64 t1 = sub2(one2, mul2(dnx, rinv));          // 1 - dnx/r
+        const u64 nt2 = mul2(mul2(dnx, ri2), kinv2);         // -t2 = dnx/(k r^2)
+        Rr = fma2(Gr, t1, fma2(Gi, nt2, Rr));                // += Gr t1 - Gi t2
+        Ri = sub2(fma2(Gi, t1, Ri), mul2(Gr, nt2));          // += Gr t2 + Gi t1
+      }
+      float lr0, lr1, li0, li1, rr0, rr1, ri0, ri1;
+      upk(Lr, lr0, lr1);
+      upk(Li, li0, li1);
+      upk(Rr, rr0, rr1);
+      upk(Ri, ri0, ri1);
+      if (w0 && w1) {
+        __stcs(reinterpret_cast<float4*>(L + off), make_float4(-lr0, -li0, -lr1, -li1));
+        __stcs(reinterpret_cast<float4*>(R + off), make_float4(-rr0, -ri0, -rr1, -ri1));
+        if (Lb) __stcs(reinterpret_cast<uint2*>(Lb + off), make_uint2(pack_bf16(-lr0, -li0), pack_bf16(-lr1, -li1)));
+      } else {
+        if (w0) {
+          __stcs(L + off, make_float2(-lr0, -li0));
+          __stcs(R + off, make_float2(-rr0, -ri0));
+          if (Lb) __stcs(Lb + off, pack_bf16(-lr0, -li0));
+        }
+        if (w1) {
+          __stcs(L + off + 1, make_float2(-lr1, -li1));
+          __stcs(R + off + 1, make_float2(-rr1, -ri1));
+          if (Lb) __stcs(Lb + off + 1, pack_bf16(-lr1, -li1));
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ near pairs (FP64)
 namespace {
 
@@ -354,6 +529,10 @@ k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* _
     const double A = area[j];
     const double nxny = n0 * m0 + n1 * m1 + n2 * m2;
     const int np = c_adj_npts;
+    // FP64 where the near-singular geometry cancels (the point y, d = x - y, r, d.n_x, d.n_y)
+    // and for the sums; the smooth factors (phase, G, the hypersingular combination) in FP32
+    // from those accurate values, each term accurate to ~1e-7 relative.
+    const float kf = (float)k, kinvf = (float)kinv, nxnyf = (float)nxny;
     for (int p = lane; p < np; p += 32) {
       const double4 rl = g_adj_rule[p];
       const double y0 = rl.x * t[0] + rl.y * t[3] + rl.z * t[6];
@@ -361,31 +540,31 @@ k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* _
       const double y2 = rl.x * t[2] + rl.y * t[5] + rl.z * t[8];
       const double d0 = x0 - y0, d1 = x1 - y1, d2 = x2 - y2;
       const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-      const double rinv = rsqrt(r2);
-      const double r = r2 * rinv;
-      const double dny = d0 * m0 + d1 * m1 + d2 * m2;
-      const double dnx = d0 * n0 + d1 * n1 + d2 * n2;
-      const double rho = k * r;
+      const double r = sqrt(r2);
+      const float rf = (float)r;
+      const float rinv = 1.0f / rf;
+      const float dny = (float)(d0 * m0 + d1 * m1 + d2 * m2);
+      const float dnx = (float)(d0 * n0 + d1 * n1 + d2 * n2);
       // phase reduced to [-pi, pi] in FP64, sine and cosine of the reduced phase in FP32
-      // (|t| <= pi: the FP32 result is within ~1e-7 of e^{i rho})
-      const double nq = rint(rho * kInvTwoPi64);
-      const float th = (float)fma(-nq, kTwoPiLo64, fma(-nq, kTwoPiHi64, rho));
-      float snf, csf;
-      sincosf(th, &snf, &csf);
-      const double sn = snf, cs = csf;
-      const double gw = rl.w * A * inv4pi * rinv;
-      const double Gr = cs * gw, Gi = sn * gw;
-      const double rinv2 = rinv * rinv;
-      const double qq = dnx * dny * rinv2;
-      const double a = (rho * rho - 3.0) * qq + nxny;
-      const double b = rho * (3.0 * qq - nxny);
-      const dc lint = {dny - b * kinv, a * kinv - rho * dny};
-      const dc Lc = dmul({Gr * rinv2, Gi * rinv2}, lint);
-      const dc Rc = dmul({Gr, Gi}, {1.0 - dnx * rinv, -dnx * rinv2 * kinv});
-      Lre += Lc.re;
-      Lim += Lc.im;
-      Rre += Rc.re;
-      Rim += Rc.im;
+      const double rho64 = k * r;
+      const double nq = rint(rho64 * kInvTwoPi64);
+      const float th = (float)fma(-nq, kTwoPiLo64, fma(-nq, kTwoPiHi64, rho64));
+      float sn, cs;
+      sincosf(th, &sn, &cs);
+      const float rho = kf * rf;
+      const float gw = (float)(rl.w * A * inv4pi) * rinv;
+      const float Gr = cs * gw, Gi = sn * gw;
+      const float rinv2 = rinv * rinv;
+      const float qq = dnx * dny * rinv2;
+      const float a = fmaf(fmaf(rho, rho, -3.0f), qq, nxnyf);
+      const float b = rho * fmaf(3.0f, qq, -nxnyf);
+      const float lr = fmaf(-b, kinvf, dny), li = fmaf(a, kinvf, -rho * dny);
+      const float Hr = Gr * rinv2, Hi = Gi * rinv2;
+      const float t1 = fmaf(-dnx, rinv, 1.0f), t2 = -dnx * rinv2 * kinvf;
+      Lre += (double)fmaf(Hr, lr, -Hi * li);
+      Lim += (double)fmaf(Hr, li, Hi * lr);
+      Rre += (double)fmaf(Gr, t1, -Gi * t2);
+      Rim += (double)fmaf(Gr, t2, Gi * t1);
     }
     Lre = -warp_sum(Lre);
     Lim = -warp_sum(Lim);
@@ -488,8 +667,13 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const int rows_per_block = 64;
   const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
   dim3 grid(col_blocks, row_blocks);
-  NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
-      g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+  static const bool scalar = std::getenv("NATBEM_ASSEMBLY_SCALAR") != nullptr;
+  if (scalar)
+    NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
+        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+  else
+    NB_LAUNCH("assemble_regular", s, k_assemble_regular_x2<<<grid, kX2Threads, 0, s>>>(
+        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
   NB_CHECK_LAUNCH();
   if (aux != s) {
     NB_TRY_CUDA(cudaEventRecord(op->ev_join, aux));

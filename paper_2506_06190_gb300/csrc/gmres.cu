@@ -47,6 +47,8 @@ struct Workspace {
   float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
   int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
   int* outer_done = nullptr;                               // refinement: converged RHS
+  unsigned* gbar = nullptr;                                // grid barrier state (count, gen)
+  int coop_blocks = 0;                                     // 0: fused kernel not usable
   // captured iteration chunks: key (engine, first iteration, count, cap, tol, refinement mode)
   std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
@@ -634,6 +636,162 @@ __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
   }
 }
 
+// ------------------------------------------------- fused Krylov step (cooperative launch)
+// Grid barrier for a cooperative launch (every block co-resident): arrival count plus a
+// generation number. Bounded: a wait longer than about two seconds sets err bit 64 and goes on.
+__device__ __forceinline__ void grid_sync(unsigned* count, unsigned* gen, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vg = gen;
+    const unsigned g = *vg;
+    __threadfence();
+    if (atomicAdd(count, 1u) == nblocks - 1u) {
+      *count = 0u;
+      __threadfence();
+      atomicAdd(gen, 1u);
+    } else {
+      uint64_t t0, t;
+      asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
+      for (unsigned it = 1; *vg == g; ++it) {
+        if ((it & 255u) == 0u) {
+          asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+          if (t - t0 > 2000000000ull) {
+            atomicOr(err, 64);
+            break;
+          }
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// One GMRES iteration after the matvec, in one launch: both classical Gram-Schmidt passes
+// (partial dot products over kDotChunks row ranges per Krylov vector, then w -= V h on each
+// block's own rows), ||w||, v_{j+1} = w / ||w||, and block 0's Givens update and convergence
+// test. The same arithmetic and fixed reduction orders as the five separate kernels.
+__global__ void __launch_bounds__(256) k_krylov(GArgs a, unsigned* __restrict__ bar, int* __restrict__ err) {
+  __shared__ double2 s_h[256];
+  __shared__ double2 s_acc[4][kUpdRows];
+  __shared__ double sh[32];
+  __shared__ double2 s_hc[256], s_sn[256];
+  __shared__ double s_cs[256];
+  if (a.scal[1]) return;
+  const int j = a.scal[0];
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x;
+  const int R = (a.n + (int)G - 1) / (int)G;
+  const int r_begin = b * R, r_end = min(a.n, r_begin + R);
+  const int per = (a.n + kDotChunks - 1) / kDotChunks;
+  for (int pass = 0; pass < 2; ++pass) {
+    // partial dot products: work items (s, c, chunk)
+    const int items = a.nrhs * (j + 1) * kDotChunks;
+    for (int item = b; item < items; item += G) {
+      const int s = item / ((j + 1) * kDotChunks);
+      const int rem = item % ((j + 1) * kDotChunks);
+      const int c = rem / kDotChunks, chunk = rem % kDotChunks;
+      if (a.done[s]) continue;  // uniform over the block
+      const int q0 = chunk * per, q1 = min(a.n, q0 + per);
+      const double2* v = a.V + vidx(a, c, s);
+      const double2* w = a.w + (size_t)s * a.n;
+      double re = 0.0, im = 0.0;
+      for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
+        const double2 p = cmulc(v[r], w[r]);
+        re += p.x;
+        im += p.y;
+      }
+      const double hr = block_sum(re, sh), hi = block_sum(im, sh);
+      if (threadIdx.x == 0) a.part[(((size_t)s * (a.m + 1) + c) * kDotChunks) + chunk] = make_double2(hr, hi);
+    }
+    grid_sync(bar, bar + 1, G, err);
+    // w -= V h on this block's rows
+    for (int s = 0; s < a.nrhs; ++s) {
+      if (a.done[s]) continue;
+      for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+        const double2* pc = a.part + ((size_t)s * (a.m + 1) + c) * kDotChunks;
+        double2 t = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int q = 0; q < kDotChunks; ++q) t = cadd(t, pc[q]);
+        s_h[c] = t;
+        if (b == 0) {
+          const size_t o = (size_t)s * (a.m + 1) + c;
+          a.hcol[o] = pass == 0 ? t : cadd(a.hcol[o], t);
+        }
+      }
+      __syncthreads();
+      double nv = 0.0;
+      for (int rb = r_begin; rb < r_end; rb += kUpdRows) {
+        const int lr = threadIdx.x & (kUpdRows - 1), g = threadIdx.x / kUpdRows;
+        const int r = rb + lr;
+        double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+        if (r < r_end) {
+          int c = g;
+          for (; c + 4 <= j; c += 8) {
+            acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+            acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 4, s) + r], s_h[c + 4]));
+          }
+          if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
+        }
+        s_acc[g][lr] = cadd(acc0, acc1);
+        __syncthreads();
+        if (g == 0 && r < r_end) {
+          const double2 t = cadd(cadd(s_acc[0][lr], s_acc[1][lr]), cadd(s_acc[2][lr], s_acc[3][lr]));
+          const double2 w = csub(a.w[(size_t)s * a.n + r], t);
+          a.w[(size_t)s * a.n + r] = w;
+          nv += cabs2(w);
+        }
+        __syncthreads();
+      }
+      if (pass == 1) {
+        nv = block_sum(nv, sh);
+        if (threadIdx.x == 0) a.partn[(size_t)b * a.nrhs + s] = nv;
+      }
+      __syncthreads();
+    }
+    grid_sync(bar, bar + 1, G, err);
+  }
+  // ||w||, v_{j+1} = w / ||w|| on this block's rows; block 0: Givens
+  for (int s = 0; s < a.nrhs; ++s) {
+    if (a.done[s]) continue;
+    double t = 0.0;
+    for (int q = threadIdx.x; q < (int)G; q += blockDim.x) t += a.partn[(size_t)q * a.nrhs + s];
+    t = block_sum(t, sh);
+    const double hn = sqrt(t);
+    if (hn > 0.0) {
+      const double inv = 1.0 / hn;
+      for (int r = r_begin + threadIdx.x; r < r_end; r += blockDim.x) {
+        const double2 ww = a.w[(size_t)s * a.n + r];
+        const double2 v = make_double2(ww.x * inv, ww.y * inv);
+        a.V[vidx(a, j + 1, s) + r] = v;
+        a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+    if (b == 0) {
+      const size_t ho = (size_t)s * (a.m + 1);
+      for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+        s_hc[i] = a.hcol[ho + i];
+        if (i < j) {
+          s_cs[i] = a.cs[(size_t)s * a.m + i];
+          s_sn[i] = a.sn[(size_t)s * a.m + i];
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        a.hnorm[s] = hn;
+        givens_step(a, s, j, hn);
+      }
+      __syncthreads();
+    }
+  }
+  if (b == 0 && threadIdx.x == 0) {
+    int all = 1;
+    for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
+    a.scal[0] = j + 1;
+    a.scal[1] = all || j + 1 >= a.maxit;
+  }
+}
+
 // Back substitution R y = g on the rotated Hessenberg matrix, one warp per RHS.
 __global__ void k_lsq(GArgs a) {
   const int s = blockIdx.x, lane = threadIdx.x;
@@ -745,7 +903,8 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 16 * n * nrhs * (m + 1);           // V
   b += 8 * ld * nrhs * 3;                 // xf, gin, pout
   b += 16 * nrhs * (m + 1) * (m + 4);     // H, hcol, htmp, gv, sn, y
-  b += 16 * nchunk * nrhs * (m + 1);      // partial dots
+  b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
+  b += 8 * std::max<int64_t>(nchunk, 1024) * nrhs;                  // partial norms
   return b;
 }
 
@@ -754,7 +913,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
-                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err};
+                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -791,7 +950,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->y, nr * mm, s));
   NB_TRY(dev_alloc_n(&ws->part, std::max<size_t>((size_t)ws->nchunk, kDotChunks) * nr * (mm + 1), s));
   NB_TRY(dev_alloc_n(&ws->cs, nr * mm, s));
-  NB_TRY(dev_alloc_n(&ws->partn, (size_t)ws->nchunk * nr, s));
+  NB_TRY(dev_alloc_n(&ws->partn, (size_t)std::max(ws->nchunk, 1024) * nr, s));  // >= blocks of k_krylov
   NB_TRY(dev_alloc_n(&ws->bnorm, nr, s));
   NB_TRY(dev_alloc_n(&ws->res, nr, s));
   NB_TRY(dev_alloc_n(&ws->hnorm, nr, s));
@@ -807,6 +966,17 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->xacc, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->outer_done, nr, s));
   NB_TRY(dev_alloc_n(&ws->tc_err, 1, s));
+  NB_TRY(dev_alloc_n(&ws->gbar, 2, s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
+  {
+    // the fused Krylov kernel runs one block per SM when every block fits at once
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_krylov, 256, 0);
+    ws->coop_blocks = (coop && per_sm >= 1 && !std::getenv("NATBEM_NO_FUSED_KRYLOV")) ? sms : 0;
+  }
   NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));
   if (nrhs > 1) {
     int dev = 0, sms = 148;
@@ -1011,6 +1181,14 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
     for (int q = 0; q < c; ++q) {
       NB_TRY(matvec(op, ws, 0, engine, ws->w, ws->done, ws->scal,
                     engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
+      if (ws->coop_blocks > 0) {
+        GArgs ac = a;
+        unsigned* bar = ws->gbar;
+        int* errp = ws->tc_err;
+        void* args[] = {&ac, &bar, &errp};
+        NB_LAUNCH("gmres_krylov", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_krylov, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
+        continue;
+      }
       const dim3 dot_grid(std::min(it0 + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
       NB_LAUNCH("gmres_dots", s, k_dots<<<dot_grid, kDotThreads, 0, s>>>(a));
       NB_LAUNCH("gmres_update", s, k_update<<<upd_grid, 256, 0, s>>>(a, 0));
@@ -1138,6 +1316,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   NB_TRY(workspace_ensure(op, nrhs, s));
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
+  NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
   const int n = (int)op->n, ld = (int)op->geo.ld;
   const dim3 vec_grid((n + kChunk - 1) / kChunk, nrhs);
   // b = R g
