@@ -430,6 +430,21 @@ FP32_LANES_PER_SM = 128
 SMS = 152
 
 
+def aggregate_ranks(n_solves_local: float, ms_local: float, world: int, device=None):
+    """Whole-job throughput for replicas: every rank solves its own copy of the workload with
+    no exchange; value = total solves over all ranks / the slowest rank's time. Returns
+    (value, max_ms)."""
+    if world == 1:
+        return n_solves_local / (ms_local * 1e-3), ms_local
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([n_solves_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(n.item()) / (float(t.item()) * 1e-3), float(t.item())
+
+
 def cpu_baseline(prob, nthreads: int):
     import oracle
     k = float(prob.ks[0])
@@ -506,13 +521,7 @@ def main():
     res = run_gpu(args, rank, world)
     prob = res.pop("prob")
     n_solves = args.steps * len(prob.ks)
-    ms = res["ms_total"]
-    my_rate_time = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        my_rate_time = float(t.item())
-    value = n_solves * world / (my_rate_time * 1e-3)
+    value, my_rate_time = aggregate_ranks(n_solves, res["ms_total"], world, device="cuda" if world > 1 else None)
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
