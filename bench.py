@@ -104,8 +104,8 @@ def workload(n_k: int, n_tri: int = 10240):
 
 
 # ------------------------------------------------------------------------------ GPU arm
-KERNELS = ("assemble_regular", "assemble_near", "geometry", "gemv_rhs", "gemv_resid", "gemv_bf16",
-           "gmres_start", "gmres_krylov", "gmres_dots", "gmres_update", "gmres_finish", "gmres_lsq",
+KERNELS = ("assemble_regular", "assemble_near", "assemble_self", "geometry", "gemv_rhs", "gemv_resid", "gemv_bf16",
+           "gmres_start", "gmres_arnoldi", "gmres_dots", "gmres_update", "gmres_finish", "gmres_lsq",
            "gmres_xupdate", "eval_reduce", "ir_residual", "pad_copy", "cgemm_fp32", "tc_gemm", "tc_pack",
            "tc_reduce")
 

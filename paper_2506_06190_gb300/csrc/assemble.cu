@@ -4,18 +4,18 @@
 //   L_ij = 1/2 d_ij - int_j [dG/dn_y + beta d2G/dn_x dn_y] dS_y
 //   R_ij = -int_j [G + beta dG/dn_x] dS_y - (beta/2) d_ij,     G = e^{ikr}/(4 pi r), beta = i/k
 //
-// Three kernels:
-//   k_geometry          per element: centroid (as a float hi/lo pair), normal, area, the 7
-//                       quadrature points as offsets from the centroid with their weights, and
-//                       the FP64 copies used by the near-pair kernel.
-//   k_assemble_regular  every pair (i, j) that shares no vertex, in FP32: one thread per source
-//                       column j holding that element's rule in registers, collocation rows
-//                       staged through shared memory and read as broadcasts, coalesced row
-//                       stores of L and R. Pairs that share a vertex are skipped.
-//   k_assemble_near     the self pair and vertex-sharing pairs, one warp per pair with the
-//                       lanes over quadrature points and a shuffle reduction: FP64 geometry
-//                       (points, d = x - y, r, normal components) and FP64 sums, FP32 for the
-//                       smooth kernel factors; the self pair's angular integral in FP64.
+// Four kernels:
+//   k_geometry           per element: centroid (as a float hi/lo pair), normal, area, the 7
+//                        quadrature points as offsets from the centroid with their weights, and
+//                        the FP64 copies used by the near-pair kernels.
+//   k_assemble_regular   every pair (i, j) that shares no vertex, in FP32: one thread per source
+//                        column j holding that element's rule in registers, collocation rows
+//                        staged through shared memory and read as broadcasts, coalesced row
+//                        stores of L and R. Pairs that share a vertex are skipped.
+//   k_assemble_adjacent  vertex-sharing pairs (j != i), 16 lanes per pair over the subdivided
+//                        rule: d = x - y formed in FP64 (where it cancels), everything after it
+//                        in FP32 with compensated sums.
+//   k_assemble_self      the self pair, one warp per element: the angular integrals in FP64.
 //
 // With d = x - y, r = |d|, rho = k r, q = (d.n_x)(d.n_y)/r^2 the integrands reduce to
 //   dG/dn_y + beta H = G/r^2 [ (d.n_y - b/k) + i (a/k - rho d.n_y) ],
@@ -487,137 +487,192 @@ k_assemble_regular_x2(const float4* __restrict__ c_hi, const float4* __restrict_
 // ------------------------------------------------------------------ near pairs (FP64)
 namespace {
 
-struct dc {
-  double re, im;
-};
-__device__ __forceinline__ dc dmul(dc a, dc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
-
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// 2 pi as a double hi/lo pair (Cody & Waite 1980 reduction in FP64)
-constexpr double kTwoPiHi64 = 6.283185307179586;
-constexpr double kTwoPiLo64 = 2.4492935982947064e-16;
-constexpr double kInvTwoPi64 = 0.15915494309189535;
+// Compensated FP32 running sum (Kahan 1965): s - c is the exact sum to about twice FP32 precision.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Knuth's TwoSum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Sum over the 16 lanes of a half warp of the compensated sums (s, c), as a double-float
+// (hi, lo); every lane of the warp must call it.
+__device__ __forceinline__ void half_warp_sum_df(float s, float c, float& hi, float& lo) {
+  two_sum(s, -c, hi, lo);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float t, e;
+    two_sum(hi, h2, t, e);
+    e += lo + l2;
+    hi = t + e;
+    lo = e - (hi - t);
+  }
+}
 
 }  // namespace
 
-// One warp per (i, j) pair from the near list: j == i (analytic radial integration in polar
-// coordinates about the centroid, Hadamard finite part of the hypersingular term) or j
-// sharing a vertex with i (7-point rule on the 4^levels sub-triangles of element j).
+// Vertex-sharing pairs (i, j != i): the 7-point rule on the 4^levels sub-triangles of element j,
+// 16 lanes per pair (two pairs per warp; 112 points at levels = 2 is seven per lane). The
+// quadrature point and x_i are close compared with their distance from the origin, so the
+// offset of the point from vertex a of j and d = x_i - y are formed in FP64 from the FP64
+// vertices; d is then exact to FP32 rounding and every factor after it (r, d.n, the phase,
+// G and the hypersingular combination) runs on the FP32 pipe, which GB300 issues ~60x faster
+// than FP64. Per-lane sums are compensated (Kahan) and the 16 lanes are added as double-float.
 __global__ void __launch_bounds__(256)
-k_assemble_near(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
-                const double* __restrict__ cen, const double* __restrict__ nrm64,
-                const double* __restrict__ area, int ld, double k, float2* __restrict__ L,
-                float2* __restrict__ R, uint32_t* __restrict__ Lb) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
+                    const double* __restrict__ cen, const double* __restrict__ nrm64,
+                    const double* __restrict__ area, int ld, double k, float2* __restrict__ L,
+                    float2* __restrict__ R, uint32_t* __restrict__ Lb) {
+  const int64_t pr_idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
+  const int l16 = threadIdx.x & 15;
+  const bool valid = pr_idx < n_pairs;  // no early exit: the lane sums use full-warp shuffles
+  int i = 0, j = 0;
+  if (valid) {
+    const int2 pr = pairs[pr_idx];
+    i = pr.x;
+    j = pr.y;
+  }
+  const double* t = tri + 9 * j;
+  const double D0 = cen[3 * i] - t[0], D1 = cen[3 * i + 1] - t[1], D2 = cen[3 * i + 2] - t[2];
+  const double e10 = t[3] - t[0], e11 = t[4] - t[1], e12 = t[5] - t[2];
+  const double e20 = t[6] - t[0], e21 = t[7] - t[1], e22 = t[8] - t[2];
+  const float ni0 = (float)nrm64[3 * i], ni1 = (float)nrm64[3 * i + 1], ni2 = (float)nrm64[3 * i + 2];
+  const float nj0 = (float)nrm64[3 * j], nj1 = (float)nrm64[3 * j + 1], nj2 = (float)nrm64[3 * j + 2];
+  const float nxny = ni0 * nj0 + ni1 * nj1 + ni2 * nj2;
+  const float scale = (float)(area[j] * (0.25 / 3.14159265358979323846));
+  const float kf = (float)k, kinvf = (float)(1.0 / k);
+  float Lr = 0.f, Li = 0.f, Rr = 0.f, Ri = 0.f, cLr = 0.f, cLi = 0.f, cRr = 0.f, cRi = 0.f;
+  const int np = valid ? c_adj_npts : 0;
+  for (int p = l16; p < np; p += 16) {
+    const double4 rl = g_adj_rule[p];
+    const float d0 = (float)(D0 - fma(rl.z, e20, rl.y * e10));
+    const float d1 = (float)(D1 - fma(rl.z, e21, rl.y * e11));
+    const float d2 = (float)(D2 - fma(rl.z, e22, rl.y * e12));
+    const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float dnx = fmaf(d0, ni0, fmaf(d1, ni1, d2 * ni2));
+    const float dny = fmaf(d0, nj0, fmaf(d1, nj1, d2 * nj2));
+    const float rho = kf * r;
+    const float nq = rintf(rho * kInvTwoPi);
+    const float th = fmaf(-nq, kTwoPiLo, fmaf(-nq, kTwoPiHi, rho));
+    float sn, cs;
+    sincosf(th, &sn, &cs);
+    const float gw = (float)rl.w * scale * rinv;
+    const float Gr = cs * gw, Gi = sn * gw;
+    const float rinv2 = rinv * rinv;
+    const float qq = dnx * dny * rinv2;
+    const float a = fmaf(fmaf(rho, rho, -3.0f), qq, nxny);
+    const float b = rho * fmaf(3.0f, qq, -nxny);
+    const float lr = fmaf(-b, kinvf, dny), li = fmaf(a, kinvf, -rho * dny);
+    const float Hr = Gr * rinv2, Hi = Gi * rinv2;
+    const float t1 = fmaf(-dnx, rinv, 1.0f), t2 = -dnx * rinv2 * kinvf;
+    kahan_add(Lr, cLr, fmaf(Hr, lr, -Hi * li));
+    kahan_add(Li, cLi, fmaf(Hr, li, Hi * lr));
+    kahan_add(Rr, cRr, fmaf(Gr, t1, -Gi * t2));
+    kahan_add(Ri, cRi, fmaf(Gr, t2, Gi * t1));
+  }
+  float hLr, lLr, hLi, lLi, hRr, lRr, hRi, lRi;
+  half_warp_sum_df(Lr, cLr, hLr, lLr);
+  half_warp_sum_df(Li, cLi, hLi, lLi);
+  half_warp_sum_df(Rr, cRr, hRr, lRr);
+  half_warp_sum_df(Ri, cRi, hRi, lRi);
+  if (valid && l16 == 0) {
+    const float2 lv = make_float2(-(hLr + lLr), -(hLi + lLi));
+    const float2 rv = make_float2(-(hRr + lRr), -(hRi + lRi));
+    L[(size_t)i * ld + j] = lv;
+    R[(size_t)i * ld + j] = rv;
+    if (Lb) Lb[(size_t)i * ld + j] = pack_bf16(lv.x, lv.y);
+  }
+}
+
+// Self terms (flat element, collocation at the centroid), one warp per element, FP64:
+//   S = (1/4pi) sum_e int (e^{ikR} - 1)/(ik) dpsi,   FP = (1/4pi) sum_e int (ik - e^{ikR}/R) dpsi,
+// with R = d_e / cos(psi) the distance from the centroid to edge e along the ray (radial part
+// analytic, Hadamard finite part of the hypersingular term); L_ii = 1/2 - beta FP and
+// R_ii = -S - beta/2 with beta = i/k.
+__global__ void __launch_bounds__(256)
+k_assemble_self(int n, const double* __restrict__ tri, const double* __restrict__ cen, int ld,
+                double k, float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb) {
+  const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (w >= n_pairs) return;
-  const int2 pr = pairs[w];
-  const int i = pr.x, j = pr.y;
+  if (i >= n) return;  // whole warps
   const double kinv = 1.0 / k;
   const double inv4pi = 0.25 / 3.14159265358979323846;
   const double x0 = cen[3 * i], x1 = cen[3 * i + 1], x2 = cen[3 * i + 2];
-  const double n0 = nrm64[3 * i], n1 = nrm64[3 * i + 1], n2 = nrm64[3 * i + 2];
-  double Lre = 0, Lim = 0, Rre = 0, Rim = 0;
-  if (i != j) {
-    const double* t = tri + 9 * j;
-    const double m0 = nrm64[3 * j], m1 = nrm64[3 * j + 1], m2 = nrm64[3 * j + 2];
-    const double A = area[j];
-    const double nxny = n0 * m0 + n1 * m1 + n2 * m2;
-    const int np = c_adj_npts;
-    // FP64 where the near-singular geometry cancels (the point y, d = x - y, r, d.n_x, d.n_y)
-    // and for the sums; the smooth factors (phase, G, the hypersingular combination) in FP32
-    // from those accurate values, each term accurate to ~1e-7 relative.
-    const float kf = (float)k, kinvf = (float)kinv, nxnyf = (float)nxny;
-    for (int p = lane; p < np; p += 32) {
-      const double4 rl = g_adj_rule[p];
-      const double y0 = rl.x * t[0] + rl.y * t[3] + rl.z * t[6];
-      const double y1 = rl.x * t[1] + rl.y * t[4] + rl.z * t[7];
-      const double y2 = rl.x * t[2] + rl.y * t[5] + rl.z * t[8];
-      const double d0 = x0 - y0, d1 = x1 - y1, d2 = x2 - y2;
-      const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-      const double r = sqrt(r2);
-      const float rf = (float)r;
-      const float rinv = 1.0f / rf;
-      const float dny = (float)(d0 * m0 + d1 * m1 + d2 * m2);
-      const float dnx = (float)(d0 * n0 + d1 * n1 + d2 * n2);
-      // phase reduced to [-pi, pi] in FP64, sine and cosine of the reduced phase in FP32
-      const double rho64 = k * r;
-      const double nq = rint(rho64 * kInvTwoPi64);
-      const float th = (float)fma(-nq, kTwoPiLo64, fma(-nq, kTwoPiHi64, rho64));
-      float sn, cs;
-      sincosf(th, &sn, &cs);
-      const float rho = kf * rf;
-      const float gw = (float)(rl.w * A * inv4pi) * rinv;
-      const float Gr = cs * gw, Gi = sn * gw;
-      const float rinv2 = rinv * rinv;
-      const float qq = dnx * dny * rinv2;
-      const float a = fmaf(fmaf(rho, rho, -3.0f), qq, nxnyf);
-      const float b = rho * fmaf(3.0f, qq, -nxnyf);
-      const float lr = fmaf(-b, kinvf, dny), li = fmaf(a, kinvf, -rho * dny);
-      const float Hr = Gr * rinv2, Hi = Gi * rinv2;
-      const float t1 = fmaf(-dnx, rinv, 1.0f), t2 = -dnx * rinv2 * kinvf;
-      Lre += (double)fmaf(Hr, lr, -Hi * li);
-      Lim += (double)fmaf(Hr, li, Hi * lr);
-      Rre += (double)fmaf(Gr, t1, -Gi * t2);
-      Rim += (double)fmaf(Gr, t2, Gi * t1);
-    }
-    Lre = -warp_sum(Lre);
-    Lim = -warp_sum(Lim);
-    Rre = -warp_sum(Rre);
-    Rim = -warp_sum(Rim);
-  } else {
-    // S = (1/4pi) sum_e int (e^{ikR} - 1)/(ik) dpsi,  FP = (1/4pi) sum_e int (ik - e^{ikR}/R) dpsi
-    // with R = d_e / cos(psi) the distance from the centroid to edge e along the ray.
-    const double* t = tri + 9 * i;
-    const int ns = c_self_pts;
-    double Sre = 0, Sim = 0, Fre = 0, Fim = 0;
-    for (int p = lane; p < 3 * ns; p += 32) {
-      const int e = p / ns, g = p - e * ns;
-      const double* P = t + 3 * e;
-      const double* Q = t + 3 * ((e + 1) % 3);
-      double u0 = Q[0] - P[0], u1 = Q[1] - P[1], u2 = Q[2] - P[2];
-      const double ul = rsqrt(u0 * u0 + u1 * u1 + u2 * u2);
-      u0 *= ul;
-      u1 *= ul;
-      u2 *= ul;
-      // positions of P and Q along the edge line, relative to the foot of the perpendicular
-      const double sP = (P[0] - x0) * u0 + (P[1] - x1) * u1 + (P[2] - x2) * u2;
-      const double sQ = (Q[0] - x0) * u0 + (Q[1] - x1) * u1 + (Q[2] - x2) * u2;
-      const double f0 = P[0] - x0 - sP * u0, f1 = P[1] - x1 - sP * u1, f2 = P[2] - x2 - sP * u2;
-      const double de = sqrt(f0 * f0 + f1 * f1 + f2 * f2);
-      const double psiP = atan2(sP, de), psiQ = atan2(sQ, de);
-      const double half = 0.5 * (psiQ - psiP), mid = 0.5 * (psiQ + psiP);
-      const double2 gl = g_gl[g];
-      const double psi = mid + half * gl.x;
-      const double Rr = de / cos(psi);
-      const double wq = half * gl.y;
-      double sn, cs;
-      sincos(k * Rr, &sn, &cs);
-      // (e^{ikR} - 1)/(ik) = sin(kR)/k + i (1 - cos(kR))/k
-      Sre += wq * sn * kinv;
-      Sim += wq * (1.0 - cs) * kinv;
-      Fre += -wq * cs / Rr;
-      Fim += wq * (k - sn / Rr);
-    }
-    Sre = warp_sum(Sre) * inv4pi;
-    Sim = warp_sum(Sim) * inv4pi;
-    Fre = warp_sum(Fre) * inv4pi;
-    Fim = warp_sum(Fim) * inv4pi;
-    // L_ii = 1/2 - beta FP, R_ii = -S - beta/2, beta = i/k
-    Lre = 0.5 + Fim * kinv;
-    Lim = -Fre * kinv;
-    Rre = -Sre;
-    Rim = -Sim - 0.5 * kinv;
+  const double* t = tri + 9 * i;
+  const int ns = c_self_pts;
+  // per edge e (lanes 0..2): the distance d_e from the centroid to the edge line and the
+  // angles of the edge's end points seen from the centroid, measured from the perpendicular
+  double de = 0.0, mid = 0.0, half = 0.0;
+  if (lane < 3) {
+    const double* P = t + 3 * lane;
+    const double* Q = t + 3 * ((lane + 1) % 3);
+    double u0 = Q[0] - P[0], u1 = Q[1] - P[1], u2 = Q[2] - P[2];
+    const double ul = rsqrt(u0 * u0 + u1 * u1 + u2 * u2);
+    u0 *= ul;
+    u1 *= ul;
+    u2 *= ul;
+    // positions of P and Q along the edge line, relative to the foot of the perpendicular
+    const double sP = (P[0] - x0) * u0 + (P[1] - x1) * u1 + (P[2] - x2) * u2;
+    const double sQ = (Q[0] - x0) * u0 + (Q[1] - x1) * u1 + (Q[2] - x2) * u2;
+    const double f0 = P[0] - x0 - sP * u0, f1 = P[1] - x1 - sP * u1, f2 = P[2] - x2 - sP * u2;
+    de = sqrt(f0 * f0 + f1 * f1 + f2 * f2);
+    const double psiP = atan2(sP, de), psiQ = atan2(sQ, de);
+    half = 0.5 * (psiQ - psiP);
+    mid = 0.5 * (psiQ + psiP);
   }
+  double de_e[3], mid_e[3], half_e[3];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    de_e[e] = __shfl_sync(0xffffffffu, de, e);
+    mid_e[e] = __shfl_sync(0xffffffffu, mid, e);
+    half_e[e] = __shfl_sync(0xffffffffu, half, e);
+  }
+  double Sre = 0, Sim = 0, Fre = 0, Fim = 0;
+  for (int p = lane; p < 3 * ns; p += 32) {
+    const int e = p / ns, g = p - e * ns;
+    const double dE = e == 0 ? de_e[0] : (e == 1 ? de_e[1] : de_e[2]);
+    const double mE = e == 0 ? mid_e[0] : (e == 1 ? mid_e[1] : mid_e[2]);
+    const double hE = e == 0 ? half_e[0] : (e == 1 ? half_e[1] : half_e[2]);
+    const double2 gl = g_gl[g];
+    const double psi = mE + hE * gl.x;
+    const double cpsi = cos(psi);
+    const double Rr = dE / cpsi;
+    const double invR = cpsi / dE;
+    const double wq = hE * gl.y;
+    double sn, cs;
+    sincos(k * Rr, &sn, &cs);
+    // (e^{ikR} - 1)/(ik) = sin(kR)/k + i (1 - cos(kR))/k
+    Sre += wq * sn * kinv;
+    Sim += wq * (1.0 - cs) * kinv;
+    Fre -= wq * cs * invR;
+    Fim += wq * (k - sn * invR);
+  }
+  Sre = warp_sum(Sre) * inv4pi;
+  Sim = warp_sum(Sim) * inv4pi;
+  Fre = warp_sum(Fre) * inv4pi;
+  Fim = warp_sum(Fim) * inv4pi;
   if (lane == 0) {
-    L[(size_t)i * ld + j] = make_float2((float)Lre, (float)Lim);
-    R[(size_t)i * ld + j] = make_float2((float)Rre, (float)Rim);
-    if (Lb) Lb[(size_t)i * ld + j] = pack_bf16((float)Lre, (float)Lim);
+    const float2 lv = make_float2((float)(0.5 + Fim * kinv), (float)(-Fre * kinv));
+    L[(size_t)i * ld + i] = lv;
+    R[(size_t)i * ld + i] = make_float2((float)(-Sre), (float)(-Sim - 0.5 * kinv));
+    if (Lb) Lb[(size_t)i * ld + i] = pack_bf16(lv.x, lv.y);
   }
 }
 
@@ -657,11 +712,17 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
     NB_TRY_CUDA(cudaEventRecord(op->ev_fork, s));
     NB_TRY_CUDA(cudaStreamWaitEvent(aux, op->ev_fork, 0));
   }
-  const int64_t threads = 256, warps_per_block = threads / 32;
-  const int64_t blocks = (g.n_near + warps_per_block - 1) / warps_per_block;
-  NB_LAUNCH("assemble_near", aux, k_assemble_near<<<(unsigned)blocks, (unsigned)threads, 0, aux>>>(
-      g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
-  NB_CHECK_LAUNCH();
+  {
+    const int64_t threads = 256;
+    const int64_t adj_blocks = (g.n_near * 16 + threads - 1) / threads;
+    if (adj_blocks > 0)
+      NB_LAUNCH("assemble_near", aux, k_assemble_adjacent<<<(unsigned)adj_blocks, (unsigned)threads, 0, aux>>>(
+          g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
+    const int64_t self_blocks = ((int64_t)n * 32 + threads - 1) / threads;
+    NB_LAUNCH("assemble_self", aux, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, aux>>>(
+        n, g.tri, g.cen, ld, op->k, op->L, op->R, op->Lb));
+    NB_CHECK_LAUNCH();
+  }
   // regular pairs: columns in blocks of 256, rows split so the grid holds a few waves
   const int col_blocks = (ld + kRegThreads - 1) / kRegThreads;
   const int rows_per_block = 64;

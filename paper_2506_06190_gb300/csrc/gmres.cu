@@ -49,6 +49,8 @@ struct Workspace {
   int* outer_done = nullptr;                               // refinement: converged RHS
   unsigned* gbar = nullptr;                                // grid barrier state (count, gen)
   int coop_blocks = 0;                                     // 0: fused kernel not usable
+  double2 *pblk = nullptr, *hred = nullptr;                // fused kernel: block partials, totals
+  int arn_smem = 0;                                        // fused kernel: dynamic shared bytes
   // captured iteration chunks: key (engine, first iteration, count, cap, tol, refinement mode)
   std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
@@ -667,123 +669,362 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned* gen, unsign
   __syncthreads();
 }
 
-// One GMRES iteration after the matvec, in one launch: both classical Gram-Schmidt passes
-// (partial dot products over kDotChunks row ranges per Krylov vector, then w -= V h on each
-// block's own rows), ||w||, v_{j+1} = w / ||w||, and block 0's Givens update and convergence
-// test. The same arithmetic and fixed reduction orders as the five separate kernels.
-__global__ void __launch_bounds__(256) k_krylov(GArgs a, unsigned* __restrict__ bar, int* __restrict__ err) {
+// One GMRES iteration after the matvec, in one cooperative launch: classical Gram-Schmidt with
+// selective re-orthogonalisation (a second pass on strong cancellation, the test of Daniel,
+// Gragg, Kaufman and Stewart 1976 with a tighter threshold), ||w||, v_{j+1} and the Givens
+// update, all in FP64.
+//
+// Blocks 1..G-1 own contiguous row ranges of every vector; block 0 owns no rows and runs the
+// Givens steps, so the rotation scan overlaps the other blocks' row updates. A pass is
+//   (A) per block and RHS, partial sums over its rows of conj(V_c) . w for c <= j and of ||w||^2
+//       (eight lanes per column, reduced with three shuffle levels), stored per block; the
+//       block's panel of V is first staged in shared memory with 16-byte asynchronous copies
+//       when it fits, so the pass costs one round trip to memory;
+//   barrier; (R) each (RHS, column) total summed over the blocks in a fixed order by one warp;
+//   barrier; (B) every block reads h and ||w||^2 and takes ||w - V h||^2 = ||w||^2 - ||h||^2
+//       (V orthonormal), then updates its rows: w -= V h.
+// If ||w - V h||^2 <= 1e-4 ||w||^2 (w within 1% of span V), a second pass runs on the updated w
+// and its h is added to the first. Otherwise v_{j+1} = (w - V h) / ||w - V h|| is written
+// directly by the update, so the common iteration has two grid barriers. Every block computes
+// the same totals in the same order, so all blocks take the same decisions.
+// 1 / sqrt(x) for x > 0: an FP32 seed (about 22 bits) and two Newton steps y += y (1 - x y^2) / 2,
+// each doubling the correct bits. GB300 runs a dependent FP64 operation in ~66 clocks and an
+// FP64 square root or division in ~650, so this is half the latency of sqrt plus a division.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-36 && x < 1e36)) return 1.0 / sqrt(x);  // outside the FP32 seed's range
+  double y = (double)rsqrtf((float)x);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const double r = fma(-x * y, y, 1.0);
+    y = fma(0.5 * y, r, y);
+  }
+  return y;
+}
+
+// The Givens update of GMRES for RHS s after iteration j, by one warp. The new Hessenberg column
+// hc[0..j] (shared memory) gets the earlier rotations (c_i real, s_i complex) applied in order:
+//   out_i = c_i t_i + s_i h_{i+1},   t_{i+1} = -conj(s_i) t_i + c_i h_{i+1},   t_0 = h_0,
+// an affine recurrence in t, so the warp computes all t_i by a prefix scan of the maps
+// t -> a t + b (each lane composes a contiguous segment, then five shuffle levels) instead of a
+// serial chain of j rotations. The new rotation zeroes h_{j+1,j} = hn against t_j; |g_{j+1}| =
+// |s_j| |g_j| gives the residual estimate without a square root.
+__device__ void givens_warp(const GArgs& a, int s, int j, double hn, double2* hc, const double* cs,
+                            const double2* sn, int lane) {
+  const int S = (j + 31) / 32;                 // recurrence steps per lane
+  const int i0 = min(j, lane * S), i1 = min(j, i0 + S);
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);  // segment map t -> A t + B
+  for (int i = i0; i < i1; ++i) {
+    const double2 ai = make_double2(-sn[i].x, sn[i].y);
+    const double2 bi = make_double2(cs[i] * hc[i + 1].x, cs[i] * hc[i + 1].y);
+    A = cmul(ai, A);
+    B = cadd(cmul(ai, B), bi);
+  }
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {  // inclusive scan: this map after the earlier lanes' maps
+    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, o), __shfl_up_sync(0xffffffffu, A.y, o));
+    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, B.x, o), __shfl_up_sync(0xffffffffu, B.y, o));
+    if (lane >= o) {
+      B = cadd(cmul(A, Bp), B);
+      A = cmul(A, Ap);
+    }
+  }
+  // exclusive prefix: the map from t_0 to t_{i0}
+  double2 Ae = make_double2(__shfl_up_sync(0xffffffffu, A.x, 1), __shfl_up_sync(0xffffffffu, A.y, 1));
+  double2 Be = make_double2(__shfl_up_sync(0xffffffffu, B.x, 1), __shfl_up_sync(0xffffffffu, B.y, 1));
+  if (lane == 0) {
+    Ae = make_double2(1.0, 0.0);
+    Be = make_double2(0.0, 0.0);
+  }
+  const double2 h0 = hc[0];
+  double2 t = cadd(cmul(Ae, h0), Be);
+  const size_t ho = (size_t)s * (a.m + 1);
+  double2* Hcol = a.H + ((size_t)s * a.m + j) * (a.m + 1);
+  for (int i = i0; i < i1; ++i) {  // rotated entries 0..j-1 straight to the Hessenberg matrix
+    const double2 h1 = hc[i + 1];
+    Hcol[i] = cadd(make_double2(cs[i] * t.x, cs[i] * t.y), cmul(sn[i], h1));
+    t = cadd(cmul(make_double2(-sn[i].x, sn[i].y), t), make_double2(cs[i] * h1.x, cs[i] * h1.y));
+  }
+  // t_j sits in the lane whose segment ends at j (lane 0 when j == 0)
+  const int owner = j == 0 ? 0 : (j - 1) / S;
+  t = make_double2(__shfl_sync(0xffffffffu, t.x, owner), __shfl_sync(0xffffffffu, t.y, owner));
+  if (lane == 0) {
+    const double q = cabs2(t);
+    double c, absS;
+    double2 sv, top;
+    if (q == 0.0) {
+      c = 0.0;
+      absS = 1.0;
+      sv = make_double2(1.0, 0.0);
+      top = make_double2(hn, 0.0);
+    } else {
+      const double ia = rsqrt_nr(q);             // 1 / |t_j|
+      const double rho2 = q + hn * hn;
+      const double ir = rsqrt_nr(rho2);          // 1 / rho
+      const double rho = rho2 * ir;
+      const double2 ph = make_double2(t.x * ia, t.y * ia);
+      c = q * ia * ir;                           // |t_j| / rho
+      absS = hn * ir;
+      sv = make_double2(ph.x * absS, ph.y * absS);
+      top = make_double2(ph.x * rho, ph.y * rho);
+    }
+    a.cs[(size_t)s * a.m + j] = c;
+    a.sn[(size_t)s * a.m + j] = sv;
+    Hcol[j] = top;
+    double2* gv = a.gv + ho;
+    const double2 gj = gv[j];
+    gv[j + 1] = cmul(make_double2(-sv.x, sv.y), gj);
+    gv[j] = make_double2(c * gj.x, c * gj.y);
+    const double res = absS * a.res[s];
+    a.res[s] = res;
+    a.hnorm[s] = hn;
+    a.iters[s] = j + 1;
+    if (res <= a.tol * a.bnorm[s] || hn == 0.0) a.done[s] = 1;
+  }
+}
+
+constexpr int kArnMaxRows = 512;           // rows per block (n <= 151 * 512 with 152 blocks)
+// dynamic shared memory for the V panel: two blocks still fit on an SM, so two solves' fused
+// kernels can be resident together
+constexpr int kArnPanelBytes = 96 * 1024;
+constexpr int kArnMaxRhs = 256;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict__ pb, double2* __restrict__ hr,
+                                                 unsigned* __restrict__ bar, int* __restrict__ err,
+                                                 int pcap) {
+  extern __shared__ double2 s_panel[];  // V_0..V_j on this block's rows (one RHS), when it fits
+  __shared__ double2 s_w[kArnMaxRows];
   __shared__ double2 s_h[256];
-  __shared__ double2 s_acc[4][kUpdRows];
-  __shared__ double sh[32];
-  __shared__ double2 s_hc[256], s_sn[256];
+  __shared__ double2 s_acc[256];
+  __shared__ double2 s_sn[256];
   __shared__ double s_cs[256];
+  __shared__ unsigned char s_act[kArnMaxRhs];  // 1: active, 2: active and re-orthogonalised
+  __shared__ double s_hn[kArnMaxRhs], s_inv[kArnMaxRhs];
   if (a.scal[1]) return;
   const int j = a.scal[0];
-  const unsigned G = gridDim.x;
-  const int b = blockIdx.x;
-  const int R = (a.n + (int)G - 1) / (int)G;
-  const int r_begin = b * R, r_end = min(a.n, r_begin + R);
-  const int per = (a.n + kDotChunks - 1) / kDotChunks;
+  const int G = (int)gridDim.x, b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = (a.n + G - 2) / (G - 1);
+  const int r0 = b == 0 ? 0 : min(a.n, (b - 1) * R), r1 = b == 0 ? 0 : min(a.n, r0 + R);
+  const int rows = r1 - r0;
+  const int np = j + 2;                   // columns 0..j and ||w||^2
+  const size_t ps = (size_t)(a.m + 2);    // per-RHS stride of pb (times G) and hr
+  const bool panel = (j + 1) * rows <= pcap;  // the block's V panel is staged in shared memory
+  for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x) s_act[s] = a.done[s] ? 0 : 1;
+  __syncthreads();
+
   for (int pass = 0; pass < 2; ++pass) {
-    // partial dot products: work items (s, c, chunk)
-    const int items = a.nrhs * (j + 1) * kDotChunks;
-    for (int item = b; item < items; item += G) {
-      const int s = item / ((j + 1) * kDotChunks);
-      const int rem = item % ((j + 1) * kDotChunks);
-      const int c = rem / kDotChunks, chunk = rem % kDotChunks;
-      if (a.done[s]) continue;  // uniform over the block
-      const int q0 = chunk * per, q1 = min(a.n, q0 + per);
-      const double2* v = a.V + vidx(a, c, s);
-      const double2* w = a.w + (size_t)s * a.n;
-      double re = 0.0, im = 0.0;
-      for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
-        const double2 p = cmulc(v[r], w[r]);
-        re += p.x;
-        im += p.y;
-      }
-      const double hr = block_sum(re, sh), hi = block_sum(im, sh);
-      if (threadIdx.x == 0) a.part[(((size_t)s * (a.m + 1) + c) * kDotChunks) + chunk] = make_double2(hr, hi);
-    }
-    grid_sync(bar, bar + 1, G, err);
-    // w -= V h on this block's rows
-    for (int s = 0; s < a.nrhs; ++s) {
-      if (a.done[s]) continue;
-      for (int c = threadIdx.x; c <= j; c += blockDim.x) {
-        const double2* pc = a.part + ((size_t)s * (a.m + 1) + c) * kDotChunks;
-        double2 t = make_double2(0.0, 0.0);
-#pragma unroll
-        for (int q = 0; q < kDotChunks; ++q) t = cadd(t, pc[q]);
-        s_h[c] = t;
-        if (b == 0) {
-          const size_t o = (size_t)s * (a.m + 1) + c;
-          a.hcol[o] = pass == 0 ? t : cadd(a.hcol[o], t);
-        }
-      }
-      __syncthreads();
-      double nv = 0.0;
-      for (int rb = r_begin; rb < r_end; rb += kUpdRows) {
-        const int lr = threadIdx.x & (kUpdRows - 1), g = threadIdx.x / kUpdRows;
-        const int r = rb + lr;
-        double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
-        if (r < r_end) {
-          int c = g;
-          for (; c + 4 <= j; c += 8) {
-            acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
-            acc1 = cadd(acc1, cmul(a.V[vidx(a, c + 4, s) + r], s_h[c + 4]));
+    const unsigned char want = pass == 0 ? 1 : 2;
+    bool any = false;
+    for (int s = 0; s < a.nrhs; ++s) any |= (s_act[s] >= want);
+    if (!any) break;  // uniform: every block holds the same flags
+    // (A) partial sums over this block's rows
+    if (b > 0) {
+      const int l8 = lane & 7;
+      for (int s = 0; s < a.nrhs; ++s) {
+        if (s_act[s] < want) continue;
+        const double2* w = a.w + (size_t)s * a.n + r0;
+        if (panel) {  // one round trip for the whole panel: 16-byte asynchronous copies
+          for (int e = threadIdx.x; e < (j + 1) * rows; e += blockDim.x) {
+            const int c = e / rows, r = e - c * rows;
+            cp_async16(&s_panel[e], a.V + vidx(a, c, s) + r0 + r);
           }
-          if (c <= j) acc0 = cadd(acc0, cmul(a.V[vidx(a, c, s) + r], s_h[c]));
         }
-        s_acc[g][lr] = cadd(acc0, acc1);
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) s_w[r] = w[r];
+        if (panel) cp_async_wait_all();
         __syncthreads();
-        if (g == 0 && r < r_end) {
-          const double2 t = cadd(cadd(s_acc[0][lr], s_acc[1][lr]), cadd(s_acc[2][lr], s_acc[3][lr]));
-          const double2 w = csub(a.w[(size_t)s * a.n + r], t);
-          a.w[(size_t)s * a.n + r] = w;
-          nv += cabs2(w);
+        for (int c0 = warp * 4; c0 < np; c0 += 32) {  // same trip count in every lane of a warp
+          const int c = c0 + (lane >> 3);
+          double re0 = 0.0, im0 = 0.0, re1 = 0.0, im1 = 0.0;
+          if (c <= j && panel) {
+            const double2* v = s_panel + c * rows;
+            for (int r = l8; r < rows; r += 16) {
+              const double2 v0 = v[r], w0 = s_w[r];
+              re0 = fma(v0.x, w0.x, re0);
+              re0 = fma(v0.y, w0.y, re0);
+              im0 = fma(v0.x, w0.y, im0);
+              im0 = fma(-v0.y, w0.x, im0);
+              if (r + 8 < rows) {
+                const double2 v1 = v[r + 8], w1 = s_w[r + 8];
+                re1 = fma(v1.x, w1.x, re1);
+                re1 = fma(v1.y, w1.y, re1);
+                im1 = fma(v1.x, w1.y, im1);
+                im1 = fma(-v1.y, w1.x, im1);
+              }
+            }
+          } else if (c <= j) {
+            // conj(v) . w as four FMA chains; eight loads issued before they are used
+            const double2* v = a.V + vidx(a, c, s) + r0;
+            for (int rb = l8; rb < rows; rb += 64) {
+              double2 vv[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int r = rb + 8 * u;
+                vv[u] = r < rows ? v[r] : make_double2(0.0, 0.0);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int r = rb + 8 * u;
+                const double2 ww = r < rows ? s_w[r] : make_double2(0.0, 0.0);
+                double& re = (u & 1) ? re1 : re0;
+                double& im = (u & 1) ? im1 : im0;
+                re = fma(vv[u].x, ww.x, re);
+                re = fma(vv[u].y, ww.y, re);
+                im = fma(vv[u].x, ww.y, im);
+                im = fma(-vv[u].y, ww.x, im);
+              }
+            }
+          } else if (c == j + 1) {
+            for (int r = l8; r < rows; r += 16) {
+              const double2 w0 = s_w[r];
+              re0 = fma(w0.x, w0.x, re0);
+              re0 = fma(w0.y, w0.y, re0);
+              if (r + 8 < rows) {
+                const double2 w1 = s_w[r + 8];
+                re1 = fma(w1.x, w1.x, re1);
+                re1 = fma(w1.y, w1.y, re1);
+              }
+            }
+          }
+          double re = re0 + re1, im = im0 + im1;
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+          }
+          if (l8 == 0 && c < np) pb[((size_t)s * ps + c) * G + b] = make_double2(re, im);
         }
         __syncthreads();
       }
-      if (pass == 1) {
-        nv = block_sum(nv, sh);
-        if (threadIdx.x == 0) a.partn[(size_t)b * a.nrhs + s] = nv;
-      }
-      __syncthreads();
     }
     grid_sync(bar, bar + 1, G, err);
-  }
-  // ||w||, v_{j+1} = w / ||w|| on this block's rows; block 0: Givens
-  for (int s = 0; s < a.nrhs; ++s) {
-    if (a.done[s]) continue;
-    double t = 0.0;
-    for (int q = threadIdx.x; q < (int)G; q += blockDim.x) t += a.partn[(size_t)q * a.nrhs + s];
-    t = block_sum(t, sh);
-    const double hn = sqrt(t);
-    if (hn > 0.0) {
-      const double inv = 1.0 / hn;
-      for (int r = r_begin + threadIdx.x; r < r_end; r += blockDim.x) {
-        const double2 ww = a.w[(size_t)s * a.n + r];
-        const double2 v = make_double2(ww.x * inv, ww.y * inv);
-        a.V[vidx(a, j + 1, s) + r] = v;
-        a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+    // (R) totals over blocks 1..G-1, one warp per (RHS, column), fixed order
+    {
+      const int items = a.nrhs * np;
+      for (int it = b * 8 + warp; it < items; it += G * 8) {
+        const int s = it / np, c = it % np;
+        if (s_act[s] < want) continue;
+        const double2* src = pb + ((size_t)s * ps + c) * G;
+        double re = 0.0, im = 0.0;
+        for (int qb = 1 + lane; qb < G; qb += 256) {  // eight loads in flight per lane
+          double2 t[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) t[u] = qb + 32 * u < G ? src[qb + 32 * u] : make_double2(0.0, 0.0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            re += t[u].x;
+            im += t[u].y;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_xor_sync(0xffffffffu, re, o);
+          im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) hr[(size_t)s * ps + c] = make_double2(re, im);
       }
     }
-    if (b == 0) {
-      const size_t ho = (size_t)s * (a.m + 1);
-      for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        s_hc[i] = a.hcol[ho + i];
-        if (i < j) {
-          s_cs[i] = a.cs[(size_t)s * a.m + i];
-          s_sn[i] = a.sn[(size_t)s * a.m + i];
+    grid_sync(bar, bar + 1, G, err);
+    // (B) decisions, row updates, v_{j+1}; block s mod G: Hessenberg column and Givens of RHS s
+    for (int s = 0; s < a.nrhs; ++s) {
+      if (s_act[s] < want) continue;
+      const double2* hs = hr + (size_t)s * ps;
+      for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = hs[c];
+      __syncthreads();
+      if (warp == 0) {
+        double t = 0.0;
+        for (int c = lane; c <= j; c += 32) t += cabs2(s_h[c]);
+        t = warp_sum(t);
+        if (lane == 0) {
+          const double wn2 = hs[j + 1].x;
+          const double hn2 = fmax(wn2 - t, 0.0);
+          // second pass only after cancellation by more than 100x in ||w - V h||: one FP64
+          // pass then leaves components ~1e-14 along V, far below what GMRES notices
+          const bool again = pass == 0 && !(hn2 > 1e-4 * wn2);
+          const double inv = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
+          s_hn[s] = again ? -1.0 : hn2 * inv;
+          s_inv[s] = inv;
+          if (again) s_act[s] = 2;
         }
       }
       __syncthreads();
-      if (threadIdx.x == 0) {
-        a.hnorm[s] = hn;
-        givens_step(a, s, j, hn);
+      const double hn = s_hn[s];
+      const bool last = hn >= 0.0;  // this pass finishes the column
+      if (b == s % G) {
+        // the Hessenberg column: h of this pass, plus the first pass's h after a second pass
+        const size_t ho = (size_t)s * (a.m + 1);
+        for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+          const double2 t = pass == 0 ? s_h[c] : cadd(a.hcol[ho + c], s_h[c]);
+          if (!last) a.hcol[ho + c] = t;
+          s_acc[c] = t;
+          if (c < j) {
+            s_cs[c] = a.cs[(size_t)s * a.m + c];
+            s_sn[c] = a.sn[(size_t)s * a.m + c];
+          }
+        }
+        __syncthreads();
+        if (last && warp == 0) givens_warp(a, s, j, hn, s_acc, s_cs, s_sn, lane);
+        __syncthreads();
       }
-      __syncthreads();
+      if (b > 0 && rows > 0) {
+        const double inv = s_inv[s];
+        for (int rc = 0; rc < rows; rc += 256) {
+          const int nr = min(256, rows - rc);
+          const int ng = 256 / nr;
+          const int lr = threadIdx.x % nr, g = threadIdx.x / nr;
+          const int r = r0 + rc + lr;
+          double2 acc0 = make_double2(0.0, 0.0), acc1 = acc0;
+          if (g < ng) {
+            // sum over c = g, g + ng, ... of V_c h_c: eight loads in flight, FMA chains; the
+            // staged panel still holds V when there is one RHS
+            const bool from_panel = panel && a.nrhs == 1;
+            for (int cb = g; cb <= j; cb += 8 * ng) {
+              double2 vv[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int c = cb + u * ng;
+                vv[u] = c > j ? make_double2(0.0, 0.0)
+                              : (from_panel ? s_panel[c * rows + rc + lr] : a.V[vidx(a, c, s) + r]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int c = cb + u * ng;
+                const double2 h = c <= j ? s_h[c] : make_double2(0.0, 0.0);
+                double2& acc = (u & 1) ? acc1 : acc0;
+                acc.x = fma(vv[u].x, h.x, acc.x);
+                acc.x = fma(-vv[u].y, h.y, acc.x);
+                acc.y = fma(vv[u].x, h.y, acc.y);
+                acc.y = fma(vv[u].y, h.x, acc.y);
+              }
+            }
+          }
+          s_acc[threadIdx.x] = cadd(acc0, acc1);
+          __syncthreads();
+          if (threadIdx.x < nr) {
+            double2 t = s_acc[threadIdx.x];
+            for (int q = 1; q < ng; ++q) t = cadd(t, s_acc[q * nr + threadIdx.x]);
+            const double2 w = csub(a.w[(size_t)s * a.n + r], t);
+            if (!last) {
+              a.w[(size_t)s * a.n + r] = w;
+            } else if (hn > 0.0) {
+              const double2 v = make_double2(w.x * inv, w.y * inv);
+              a.V[vidx(a, j + 1, s) + r] = v;
+              a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+            }
+          }
+          __syncthreads();
+        }
+      }
     }
   }
+  if (a.nrhs > 1) grid_sync(bar, bar + 1, G, err);  // every Givens update before the flags are read
   if (b == 0 && threadIdx.x == 0) {
     int all = 1;
     for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
@@ -904,7 +1145,8 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 8 * ld * nrhs * 3;                 // xf, gin, pout
   b += 16 * nrhs * (m + 1) * (m + 4);     // H, hcol, htmp, gv, sn, y
   b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
-  b += 8 * std::max<int64_t>(nchunk, 1024) * nrhs;                  // partial norms
+  b += 8 * nchunk * nrhs;                                            // partial norms
+  b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
   return b;
 }
 
@@ -913,7 +1155,8 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
-                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar};
+                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar,
+                  ws->pblk, ws->hred};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -950,7 +1193,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->y, nr * mm, s));
   NB_TRY(dev_alloc_n(&ws->part, std::max<size_t>((size_t)ws->nchunk, kDotChunks) * nr * (mm + 1), s));
   NB_TRY(dev_alloc_n(&ws->cs, nr * mm, s));
-  NB_TRY(dev_alloc_n(&ws->partn, (size_t)std::max(ws->nchunk, 1024) * nr, s));  // >= blocks of k_krylov
+  NB_TRY(dev_alloc_n(&ws->partn, (size_t)ws->nchunk * nr, s));
   NB_TRY(dev_alloc_n(&ws->bnorm, nr, s));
   NB_TRY(dev_alloc_n(&ws->res, nr, s));
   NB_TRY(dev_alloc_n(&ws->hnorm, nr, s));
@@ -969,13 +1212,36 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->gbar, 2, s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
   {
-    // the fused Krylov kernel runs one block per SM when every block fits at once
+    // the fused Arnoldi kernel runs one block per SM when every block fits at once and the
+    // rows per block and the RHS count fit its shared-memory staging
     int dev = 0, sms = 0, coop = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_krylov, 256, 0);
-    ws->coop_blocks = (coop && per_sm >= 1 && !std::getenv("NATBEM_NO_FUSED_KRYLOV")) ? sms : 0;
+    // dynamic shared memory for the V panel: up to kArnPanelBytes, or all m+1 vectors of a
+    // block's rows
+    const int64_t rows_max = sms >= 2 ? (n + sms - 2) / (sms - 1) : n;
+    const int64_t want = std::min<int64_t>(kArnPanelBytes, 16 * rows_max * (m + 1));
+    // the attribute is per function, shared by every op and thread: set once to the largest
+    // size any launch uses, never lowered
+    static std::mutex attr_mu;
+    static int attr_set[64] = {0};
+    {
+      std::lock_guard<std::mutex> lk(attr_mu);
+      if (dev >= 0 && dev < 64 && attr_set[dev] == 0) {
+        attr_set[dev] = cudaFuncSetAttribute(k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kArnPanelBytes) == cudaSuccess ? 1 : -1;
+        if (attr_set[dev] < 0) cudaGetLastError();
+      }
+      ws->arn_smem = (dev >= 0 && dev < 64 && attr_set[dev] == 1) ? (int)want : 0;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, 256, ws->arn_smem);
+    const bool fits = sms >= 2 && n <= (int64_t)(sms - 1) * kArnMaxRows && nrhs <= kArnMaxRhs;
+    ws->coop_blocks = (coop && per_sm >= 1 && fits && !std::getenv("NATBEM_NO_FUSED_KRYLOV")) ? sms : 0;
+    if (ws->coop_blocks > 0) {
+      NB_TRY(dev_alloc_n(&ws->pblk, nr * (mm + 2) * (size_t)ws->coop_blocks, s));
+      NB_TRY(dev_alloc_n(&ws->hred, nr * (mm + 2), s));
+    }
   }
   NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));
   if (nrhs > 1) {
@@ -1183,10 +1449,13 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
                     engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
       if (ws->coop_blocks > 0) {
         GArgs ac = a;
+        double2* pb = ws->pblk;
+        double2* hr = ws->hred;
         unsigned* bar = ws->gbar;
         int* errp = ws->tc_err;
-        void* args[] = {&ac, &bar, &errp};
-        NB_LAUNCH("gmres_krylov", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_krylov, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
+        int pcap = ws->arn_smem / (int)sizeof(double2);
+        void* args[] = {&ac, &pb, &hr, &bar, &errp, &pcap};
+        NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(ws->coop_blocks), dim3(256), args, (size_t)ws->arn_smem, s)));
         continue;
       }
       const dim3 dot_grid(std::min(it0 + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
@@ -1370,9 +1639,12 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     a.tol = o.inner_tol;
     int budget = o.max_iter;
     converged = false;
+    bool fallback = false;
     std::vector<int> od(nrhs);
-    for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
-      a.maxit = std::min(o.inner_max_iter, budget);
+    std::vector<double> prev(nrhs, 1.0);
+    // one refinement sweep: inner GMRES on the correction equation, x += d, true residual
+    auto sweep_once = [&]() -> nat_bem_status {
+      a.maxit = fallback ? budget : std::min(o.inner_max_iter, budget);
       NB_TRY(gmres_run(op, ws, a, inner, 1, d_p, s));
       NB_TRY(matvec(op, ws, 0, accurate, ws->w, nullptr, nullptr, "gemv_resid", s));
       NB_LAUNCH("ir_residual", s, k_ir_residual<<<vec_grid, kChunk, 0, s>>>(a, ws->b0, ws->outer_done, o.tol));
@@ -1390,7 +1662,39 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       ++refinements;
       converged = true;
       for (int q = 0; q < nrhs; ++q) converged = converged && od[q];
-      if (converged) break;
+      return NAT_BEM_OK;
+    };
+    for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
+      NB_TRY(sweep_once());
+      if (converged || fallback) break;
+      // A sweep that shrank some residual by less than 10x (the low-precision operator's error
+      // is comparable to the inner tolerance: high k, ill-conditioned L) or that used up the
+      // budget: the rest is one solve of the correction equation with the FP32 operator, to
+      // the full tolerance relative to b0, with a fresh iteration budget. It runs even when
+      // the refinement count is spent.
+      double worst = 0.0, maxrt = 0.0;
+      for (int q = 0; q < nrhs; ++q)
+        if (!od[q]) {
+          worst = std::max(worst, rt[q] / prev[q]);
+          maxrt = std::max(maxrt, rt[q]);
+        }
+      if (worst > 0.1 || budget <= 0 || sweep + 1 >= o.max_refinements) {
+        fallback = true;
+        inner = accurate;
+        a.tol = std::max(0.5 * o.tol / std::max(maxrt, o.tol), 1e-14);
+        budget = o.max_iter;
+        NB_TRY(sweep_once());
+        // The FP32 solve meets the tolerance by GMRES's own residual, the criterion of the
+        // plain FP32 path; the true residual (info.rel_residual) then sits at the FP32
+        // operator's floor, which at high k can lie above the tolerance.
+        std::vector<int> inner_done(nrhs);
+        NB_TRY_CUDA(cudaMemcpyAsync(inner_done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+        NB_TRY_CUDA(cudaStreamSynchronize(s));
+        converged = true;
+        for (int q = 0; q < nrhs; ++q) converged = converged && (od[q] || inner_done[q]);
+        break;
+      }
+      prev = rt;
     }
   }
   int tc_err = 0;

@@ -93,7 +93,7 @@ struct Geometry {
   double* cen = nullptr;      // 3 per element
   double* nrm64 = nullptr;    // 3 per element
   double* area = nullptr;     // 1 per element
-  // pairs handled in FP64: (i, j) with j == i or j sharing a vertex with i, grouped by row
+  // vertex-sharing pairs (i, j != i), grouped by row; the self pairs (i, i) are implicit
   int2* near_pairs = nullptr;
   int64_t n_near = 0;
 };

@@ -98,7 +98,8 @@ void build_near_pairs(const int32_t* T, int64_t nv, int64_t nt, std::vector<int2
     }
     std::sort(row.begin(), row.end());
     row.erase(std::unique(row.begin(), row.end()), row.end());
-    for (int32_t j : row) pairs.push_back(make_int2((int)t, j));  // includes j == t
+    for (int32_t j : row)
+      if (j != t) pairs.push_back(make_int2((int)t, j));  // the self pair has its own kernel
   }
 }
 
