@@ -196,7 +196,9 @@ NAT_BEM_API nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
  *   NAT_BEM_ENGINE_FP32: FP32 CUDA-core complex GEMM;
  *   NAT_BEM_ENGINE_TF32 / NAT_BEM_ENGINE_BF16: tcgen05 tensor cores on L (TF32) or on its BF16
  *     copy (op built with NAT_BEM_PREC_MIXED_BF16), FP32 accumulation, nrhs <= 128, L only;
- *   NAT_BEM_ENGINE_GEMV0 + v: GEMV variant v (0..4; one vector).
+ *   NAT_BEM_ENGINE_GEMV0 + v: GEMV variant v (0 <= v < NAT_BEM_GEMV_VARIANTS; one vector):
+ *     0-2 register-tiled (2 or 4 rows per block), 3-4 bulk-copy staged, 5-7 persistent blocks
+ *     with x staged in shared memory (plain variant when 8 * ld bytes exceed 200 KiB).
  * This is the operator product of the GMRES iterations (Sec. 4 operators of Eq. 6), exposed
  * for checking and for callers that iterate themselves. Blocks until Y is written.
  * NAT_BEM_EINVAL: bad which / engine / nrhs, engine not usable for this op.
@@ -206,7 +208,8 @@ enum {
   NAT_BEM_ENGINE_FP32 = 1,
   NAT_BEM_ENGINE_TF32 = 2,
   NAT_BEM_ENGINE_BF16 = 3,
-  NAT_BEM_ENGINE_GEMV0 = 10
+  NAT_BEM_ENGINE_GEMV0 = 10,
+  NAT_BEM_GEMV_VARIANTS = 8
 };
 NAT_BEM_API nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t engine,
                                             const float* X, int32_t nrhs, float* Y,

@@ -37,6 +37,7 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
+GEMV_VARIANTS = 8
 
 
 class NatBemError(RuntimeError):

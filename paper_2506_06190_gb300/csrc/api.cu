@@ -366,7 +366,7 @@ nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t eng
                                 const float* X, int32_t nrhs, float* Y, void* cuda_stream) {
   try {
     clear_error();
-    const bool gemv_engine = engine >= NAT_BEM_ENGINE_GEMV0 && engine < NAT_BEM_ENGINE_GEMV0 + 5;
+    const bool gemv_engine = engine >= NAT_BEM_ENGINE_GEMV0 && engine < NAT_BEM_ENGINE_GEMV0 + NAT_BEM_GEMV_VARIANTS;
     if (!op || !X || !Y || nrhs < 1 || which < 0 || which > 1 ||
         !(engine == NAT_BEM_ENGINE_AUTO || engine == NAT_BEM_ENGINE_FP32 ||
           engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16 || gemv_engine) ||

@@ -166,31 +166,35 @@ __device__ __forceinline__ void warp_sum_df(float s, float c, float& hi, float& 
   }
 }
 
-// Sum over the block (8 warps) of (s - c) per row: double-float warp sums, then one thread
-// per row adds the eight warp results in FP64.
+// Sum over the block (8 warps) of the compensated per-thread sums (s - c) per row: a fixed
+// FP32 shuffle tree per warp, then one thread per row adds the eight warp sums in order. The
+// per-thread sums carry the long accumulations; the 8 + 5 roundings of the tree are at the
+// level of the FP32 operator entries' own rounding. Double-float trees or an FP64 combine here
+// hold every block's exit on serial dependent chains and cost 3-15% of the bandwidth.
 template <int kRows>
 __device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], const float (&cr)[kRows],
                                                   const float (&si)[kRows], const float (&ci)[kRows],
                                                   int n, int row0, double2* __restrict__ y) {
-  __shared__ float2 sh[2 * kRows][8];
+  __shared__ float2 sh[kRows][8];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int r = 0; r < kRows; ++r) {
-    float hr, lr, hi, li;
-    warp_sum_df(sr[r], cr[r], hr, lr);
-    warp_sum_df(si[r], ci[r], hi, li);
-    if (lane == 0) {
-      sh[2 * r][wid] = make_float2(hr, lr);
-      sh[2 * r + 1][wid] = make_float2(hi, li);
+    float a = sr[r] - cr[r], b = si[r] - ci[r];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
     }
+    if (lane == 0) sh[r][wid] = make_float2(a, b);
   }
   __syncthreads();
   if (threadIdx.x < kRows && row0 + (int)threadIdx.x < n) {
     const int r = threadIdx.x;
-    double tr = 0.0, ti = 0.0;
+    float tr = 0.f, ti = 0.f;
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
-      tr += (double)sh[2 * r][q].x + (double)sh[2 * r][q].y;
-      ti += (double)sh[2 * r + 1][q].x + (double)sh[2 * r + 1][q].y;
+      tr += sh[r][q].x;
+      ti += sh[r][q].y;
     }
     y[row0 + r] = make_double2(tr, ti);
   }
@@ -241,6 +245,59 @@ k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x
     }
   }
   gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
+}
+
+// The same product by persistent blocks with x staged once per block in shared memory: each
+// block takes row groups blockIdx.x, blockIdx.x + gridDim.x, ... (kRows rows each), so the
+// operator is the only stream from memory; a block otherwise re-reads all of x for every
+// kRows rows through L1/L2. Dynamic shared memory: 8 ld bytes.
+template <int kRows, int kUnroll>
+__global__ void __launch_bounds__(256)
+k_gemv_xs(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x, int64_t xstride,
+          double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+          const int* __restrict__ scal) {
+  extern __shared__ float4 s_x[];
+  if (scal && scal[1]) return;
+  const int s = blockIdx.y;
+  if (done && done[s]) return;
+  const int n4 = ld >> 1;
+  const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
+  for (int i = threadIdx.x; i < n4; i += 256) s_x[i] = __ldg(xv + i);
+  __syncthreads();
+  for (int row0 = blockIdx.x * kRows; row0 < n; row0 += gridDim.x * kRows) {
+    const float4* a[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      a[r] = reinterpret_cast<const float4*>(A + (size_t)min(row0 + r, n - 1) * ld);
+    float sr[kRows], cr[kRows], si[kRows], ci[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) sr[r] = cr[r] = si[r] = ci[r] = 0.f;
+    for (int base = threadIdx.x; base < n4; base += 256 * kUnroll) {
+      float4 aa[kRows][kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int idx = base + u * 256;
+        const bool ok = idx < n4;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) aa[r][u] = ok ? __ldcs(a[r] + idx) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const int idx = base + u * 256;
+        const float4 v = idx < n4 ? s_x[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+          const float4 q = aa[r][u];
+          const float pr = fmaf(q.x, v.x, fmaf(-q.y, v.y, fmaf(q.z, v.z, -q.w * v.w)));
+          const float pi = fmaf(q.x, v.y, fmaf(q.y, v.x, fmaf(q.z, v.w, q.w * v.z)));
+          kahan_add(sr[r], cr[r], pr);
+          kahan_add(si[r], ci[r], pi);
+        }
+      }
+    }
+    gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
+    __syncthreads();  // the reduction's shared staging is reused by the next row group
+  }
 }
 
 // The same product with A stored as packed bf16 complex pairs (real in the low half): half
@@ -1295,9 +1352,37 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
 }
 
 // GEMV variants for one RHS and the autotuner that picks one per (device, operator size).
-enum GemvVariant { kGemvR2U4 = 0, kGemvR4U4, kGemvR2U8, kGemvBulk4x16k, kGemvBulk6x16k, kGemvVariants };
+enum GemvVariant { kGemvR2U4 = 0, kGemvR4U4, kGemvR2U8, kGemvBulk4x16k, kGemvBulk6x16k,
+                   kGemvXsR2U8, kGemvXsR4U4, kGemvXsR2U4, kGemvVariants };
 static const char* kGemvNames[kGemvVariants] = {"rows2_unroll4", "rows4_unroll4", "rows2_unroll8",
-                                                 "bulk_4x16KiB", "bulk_6x16KiB"};
+                                                 "bulk_4x16KiB", "bulk_6x16KiB", "xs_rows2_unroll8",
+                                                 "xs_rows4_unroll4", "xs_rows2_unroll4"};
+static_assert(kGemvVariants == NAT_BEM_GEMV_VARIANTS, "GEMV variants and the C ABI disagree");
+constexpr int kGemvXsMaxBytes = 200 * 1024;  // x staged in shared memory up to ld = 25600
+
+// Grid of the staged-x GEMV: as many blocks per SM as shared memory and registers allow.
+template <int kRows, int kUnroll>
+static int gemv_xs_blocks(int ld, int sms) {
+  static std::mutex mu;
+  static int attr_set[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && attr_set[dev] == 0) {
+      attr_set[dev] = cudaFuncSetAttribute(k_gemv_xs<kRows, kUnroll>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kGemvXsMaxBytes) == cudaSuccess ? 1 : -1;
+      if (attr_set[dev] < 0) cudaGetLastError();
+    }
+    if (dev < 0 || dev >= 64 || attr_set[dev] != 1) return 0;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemv_xs<kRows, kUnroll>, 256, 8 * (size_t)ld) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return per_sm * sms;
+}
 
 static nat_bem_status gemv_launch(int variant, const char* name, const float2* A, int n, int ld,
                                   const float2* x, double2* y, int nrhs, const int* done,
@@ -1331,6 +1416,28 @@ static nat_bem_status gemv_launch(int variant, const char* name, const float2* A
         NB_LAUNCH(name, s, k_gemv_bulk<4, 16384><<<grid, 288, 4 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
       else
         NB_LAUNCH(name, s, k_gemv_bulk<6, 16384><<<grid, 288, 6 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
+      break;
+    }
+    case kGemvXsR2U8:
+    case kGemvXsR4U4:
+    case kGemvXsR2U4: {
+      const size_t smem = 8 * (size_t)ld;
+      const int rows = variant == kGemvXsR4U4 ? 4 : 2;
+      int blocks = variant == kGemvXsR2U8 ? gemv_xs_blocks<2, 8>(ld, sms)
+                 : variant == kGemvXsR4U4 ? gemv_xs_blocks<4, 4>(ld, sms) : gemv_xs_blocks<2, 4>(ld, sms);
+      if (smem > (size_t)kGemvXsMaxBytes || blocks <= 0) {  // x does not fit: plain variant
+        dim3 grid((n + 1) / 2, nrhs);
+        NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+        break;
+      }
+      blocks = std::min(blocks, (n + rows - 1) / rows);
+      dim3 grid(blocks, nrhs);
+      if (variant == kGemvXsR2U8)
+        NB_LAUNCH(name, s, k_gemv_xs<2, 8><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      else if (variant == kGemvXsR4U4)
+        NB_LAUNCH(name, s, k_gemv_xs<4, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      else
+        NB_LAUNCH(name, s, k_gemv_xs<2, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
       break;
     }
     default: {

@@ -285,9 +285,10 @@ def product_case(oracle_lib):
     return V, F, k, L, R, np.asfortranarray(X)
 
 
-@pytest.mark.parametrize("variant", range(5))
+@pytest.mark.parametrize("variant", range(8))
 def test_gemv_variants_match_oracle(nb, product_case, variant):
-    """Every GEMV variant (register-tiled and bulk-copy) computes L x and R x to FP32 accuracy."""
+    """Every GEMV variant (register-tiled, bulk-copy, staged-x persistent) computes L x and R x
+    to FP32 accuracy."""
     V, F, k, L, R, X = product_case
     x = X[:, 0].copy()
     with nb.Operator.assemble(V, F, k) as op:
