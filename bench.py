@@ -9,8 +9,10 @@ points. A "solve" is one (mesh, k, Neumann data) through all three stages. The s
 through the library's batch driver (nat_bem_run_batch) with a few in flight at once; each
 worker checks the mesh and builds its geometry once, then re-assembles per wavenumber.
 
-Prints one JSON line. `value` is solves/s with inputs resident in HBM; `e2e` is the same
-metric through the public API with host (numpy) buffers, host-device copies included.
+Prints one JSON line. `value` is solves/s of the mixed-precision path (inner GMRES on the BF16
+copy of L, refinement against the FP32 operator; --prec selects) with inputs resident in HBM;
+`plain_fp32` is the same workload through the plain FP32 path, measured in the same run; `e2e`
+is the metric through the public API with host (numpy) buffers, host-device copies included.
 `--impl reference` times the FP64 CPU oracle on the same workload instead.
 
 Multi-GPU: independent solves shard with no exchange (replicas only): each rank runs the
@@ -119,7 +121,9 @@ def _kernel_table(nb):
     return kern
 
 
-def run_gpu(args, rank: int, world: int):
+def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
+    """One timed measurement of the interior workload at precision `prec_name`; with `full`
+    also the traced per-kernel step and the end-to-end pass."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -133,7 +137,7 @@ def run_gpu(args, rank: int, world: int):
         torch.distributed.barrier()
     prob = workload(args.n_k, args.n_tri)
     n = prob.F.shape[0]
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[prec_name]
     opts = nb.nat_bem_opts_default(prec=prec)
     Vd = torch.from_numpy(prob.V).to(dev)
     Fd = torch.from_numpy(prob.F).to(dev)
@@ -171,6 +175,15 @@ def run_gpu(args, rank: int, world: int):
             torch.distributed.barrier()
     ms_total = t0.elapsed_time(t1)
     launches = nb.nat_bem_trace_launches() - launches0
+    lats = sorted(r[4] for res in results for r in res)
+    iters = [r[2].iterations for res in results for r in res]
+    statuses = [r[3] for res in results for r in res]
+    summary = dict(ms_total=ms_total, launches=launches, lat=lats, iters=iters, clocks=clk.summary(), n=n,
+                   max_rel_res=max(r[2].rel_residual for res in results for r in res),
+                   n_enoconv=sum(1 for s_ in statuses if s_ != nb.NAT_BEM_OK),
+                   refinements=max(r[2].refinements for res in results for r in res), prob=prob)
+    if not full:
+        return summary
     # One more (untimed) step, one solve at a time, with every kernel bracketed by CUDA events
     # on its stream: the per-kernel table and the dominant kernel's roofline (each kernel runs
     # without other solves sharing HBM; per-launch events switch the graph replay off).
@@ -181,17 +194,9 @@ def run_gpu(args, rank: int, world: int):
     torch.cuda.synchronize()
     nb.nat_bem_trace_enable(False)
     kern = _kernel_table(nb)
-    measured = kern
     nb.nat_bem_trace_reset()
-    lats = sorted(r[4] for res in results for r in res)
-    iters = [r[2].iterations for res in results for r in res]
-    statuses = [r[3] for res in results for r in res]
     first = results[0][0]
-    out = dict(ms_total=ms_total, launches=launches, kern=kern, measured=measured, lat=lats, iters=iters,
-               p0=first[0].cpu().numpy(), f0=first[1].cpu().numpy(), clocks=clk.summary(), n=n,
-               max_rel_res=max(r[2].rel_residual for res in results for r in res),
-               n_enoconv=sum(1 for s_ in statuses if s_ != nb.NAT_BEM_OK),
-               refinements=max(r[2].refinements for res in results for r in res))
+    out = dict(summary, kern=kern, measured=kern, p0=first[0].cpu().numpy(), f0=first[1].cpu().numpy())
 
     # end to end through the public API with host buffers
     e2e = None
@@ -212,7 +217,6 @@ def run_gpu(args, rank: int, world: int):
         e2e = {"value": nk / (tb - ta), "unit": UNIT, "h2d_bytes_per_step": int(h2d * nk),
                "d2h_bytes_per_step": int(d2h * nk), "solves_per_step": nk}
     out["e2e"] = e2e
-    out["prob"] = prob
     return out
 
 
@@ -463,7 +467,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="natbem", choices=["natbem", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "tf32"])
+    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "tf32"],
+                    help="interior workload: bf16 = mixed (BF16 inner GMRES, FP32 refinement)")
+    ap.add_argument("--no-compare", dest="compare", action="store_false",
+                    help="skip the plain FP32 comparison run of the interior workload")
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
@@ -519,10 +526,22 @@ def main():
         return
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    res = run_gpu(args, rank, world)
+    res = run_gpu(args, rank, world, args.prec)
     prob = res.pop("prob")
     n_solves = args.steps * len(prob.ks)
     value, my_rate_time = aggregate_ranks(n_solves, res["ms_total"], world, device="cuda" if world > 1 else None)
+    # the plain FP32 form on the same workload, same launch configuration, for comparison
+    cmp = None
+    if args.compare and args.prec != "fp32":
+        cres = run_gpu(args, rank, world, "fp32", full=False)
+        cres.pop("prob")
+        cvalue, cms = aggregate_ranks(n_solves, cres["ms_total"], world, device="cuda" if world > 1 else None)
+        cmp = {"value": cvalue, "unit": UNIT, "ms_per_step": cms / args.steps,
+               "latency_ms": {"p50": float(np.percentile(cres["lat"], 50)),
+                              "p99": float(np.percentile(cres["lat"], 99))},
+               "gmres_iterations": {"median": float(np.median(cres["iters"])), "max": max(cres["iters"])},
+               "max_rel_residual": cres["max_rel_res"], "not_converged": cres["n_enoconv"],
+               "clocks": cres["clocks"]}
     if rank != 0:
         torch.distributed.destroy_process_group()
         return
@@ -530,7 +549,10 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": my_rate_time / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (+f64 near pairs and Krylov)",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32 (+f64 near pairs and Krylov)",
+                  "bf16": "bf16 inner GMRES + f32 refinement (+f64 near pairs and Krylov)",
+                  "tf32": "f32 (one RHS: TF32 saves no bytes)"}[args.prec],
         "data": "synthetic",
         "config": {"workload": f"interior_source_{res['n']}tri_{len(prob.ks)}k", "n_tri": res["n"],
                    "n_wavenumbers": len(prob.ks), "ka_range": [0.5, 20.0], "field_points": 1024,
@@ -554,6 +576,8 @@ def main():
                             "unit": d["unit"], "frac": d["frac"], "traffic": None,
                             "measured_on": "one untimed step of the workload, one solve at a time, CUDA events per launch",
                             "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else 'derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock'})"}
+    if cmp:
+        line["plain_fp32"] = cmp
     line["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in res["kern"].items()}
     line["rooflines"] = table
     if res["e2e"]:

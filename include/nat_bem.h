@@ -67,7 +67,7 @@ typedef struct {
   int32_t adj_subdiv_levels; /* vertex-sharing pairs: 7-point rule on 4^levels sub-triangles (2) */
   int32_t self_theta_pts;    /* self pair: Gauss-Legendre points per edge in the angle (16)      */
   double tol;                /* relative residual ||b - L p|| / ||b|| to stop at (1e-6)         */
-  int32_t max_iter;          /* GMRES iterations (plain) or total inner iterations (mixed) (200) */
+  int32_t max_iter;          /* GMRES iterations (plain), total inner iterations (mixed) (200) */
   nat_bem_precision prec;    /* arithmetic of the solve (NAT_BEM_PREC_FP32)                      */
   int32_t inner_max_iter;    /* mixed: iterations per inner solve (60)                            */
   double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-3)              */
@@ -114,6 +114,11 @@ NAT_BEM_API nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cu
  * Solves L p = R g for nrhs right-hand sides (GMRES from p = 0, Sec. 6.1 settings by default).
  *   neumann: nt x nrhs complex64, column-major.  p_out: same layout, receives p.
  *   info: may be NULL.  Blocks until the solve is done.
+ * Convergence: plain FP32, GMRES's residual estimate reaches tol (the true residual with the
+ * FP32 operator, reported in info->rel_residual, can sit above tol at high k). Mixed: the true
+ * residual reaches tol after a refinement sweep; when a sweep shrinks a residual by less than
+ * 10x, or the sweeps or max_iter inner iterations are spent, one final solve of the correction
+ * equation on the FP32 operator (its own max_iter) finishes by the plain criterion.
  * NAT_BEM_EINVAL: op NULL, nrhs < 1, NULL arrays.
  * NAT_BEM_ENOCONV: the tolerance was not met within the iteration limit; p_out holds the
  * best iterate and info is filled.
