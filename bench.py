@@ -427,6 +427,11 @@ def roofline(res, peaks, peak_kind):
     return dom, table
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of each matvec kernel on the
+# 10240-triangle workload (profiles/k_gemv_interior_source_10240tri.md); None elsewhere.
+NCU_TRAFFIC_10240 = {"gemv": 838.986e6 + 3.255e6, "gemv_bf16": 419.534e6 + 3.466e6}
+
+
 # FP32 operations of k_assemble_regular per (i, j) pair: per quadrature point 29 FMA + 19
 # other FP32 operations (2 x 29 + 19 = 77 flops) plus 3 MUFU operations (rsqrt, sin, cos) not
 # counted; per pair 6 + 15 operations for the centroid difference and the three dot products.
@@ -573,7 +578,8 @@ def main():
     if dom:
         d = table[dom]
         line["roofline"] = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
-                            "unit": d["unit"], "frac": d["frac"], "traffic": None,
+                            "unit": d["unit"], "frac": d["frac"],
+                            "traffic": NCU_TRAFFIC_10240.get(dom) if res["n"] == 10240 else None,
                             "measured_on": "one untimed step of the workload, one solve at a time, CUDA events per launch",
                             "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else 'derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock'})"}
     if cmp:
