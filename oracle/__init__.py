@@ -85,6 +85,8 @@ def _configure(L):
         L.oracle_eval.argtypes = [dp, i64, ip, i64, c_d, dp, i64, dp, dp, dp, c_int]
         L.oracle_bem_solve.argtypes = [dp, i64, ip, i64, c_d, c_int, c_int, dp, dp, i64, c_d, c_int,
                                        c_int, dp, dp, ctypes.POINTER(c_int), dp, dp]
+        L.oracle_mc_assemble.argtypes = [dp, dp, i64, c_d, c_d, dp, dp, c_int]
+        L.oracle_mc_eval.argtypes = [dp, dp, i64, c_d, c_d, dp, i64, dp, dp, dp, c_int]
         L.oracle_hardware_threads.argtypes = []
     return L
 
@@ -246,3 +248,46 @@ def bem_solve(V, F, k, g, points, tol=1e-6, maxit=200, nthreads=0):
                                 ctypes.byref(it), ctypes.byref(rr), _d(times))
     return p, fld, dict(iterations=it.value, rel_residual=rr.value, converged=rc == 0,
                         times=times.tolist())
+
+
+# ---------------------------------------------------------------------------------- BEM-MC
+def _samples(Y, N):
+    Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(-1, 3)
+    N = np.ascontiguousarray(N, dtype=np.float64).reshape(-1, 3)
+    return Y, N
+
+
+def mc_assemble(Y, N, area, k, nthreads=0):
+    """L and R (M x M complex128) of the Monte-Carlo conventional BIE (paper Sec. 4.1.1 and
+    4.2) at samples Y with unit outward normals N on a surface of total area `area`."""
+    Y, N = _samples(Y, N)
+    M = Y.shape[0]
+    L = np.zeros((M, M), dtype=np.complex128)
+    R = np.zeros((M, M), dtype=np.complex128)
+    rc = lib().oracle_mc_assemble(_d(Y), _d(N), M, float(area), float(k), _d(L.view(np.float64)),
+                                  _d(R.view(np.float64)), nthreads)
+    if rc:
+        raise ValueError(f"oracle_mc_assemble failed ({rc})")
+    return L, R
+
+
+def mc_evaluate(Y, N, area, k, points, p, g, nthreads=0):
+    """Field at `points` from the samples' Dirichlet p and Neumann g (Monte-Carlo sum)."""
+    Y, N = _samples(Y, N)
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    p, g = _c(p), _c(g)
+    out = np.zeros(pts.shape[0], dtype=np.complex128)
+    rc = lib().oracle_mc_eval(_d(Y), _d(N), Y.shape[0], float(area), float(k), _d(pts), pts.shape[0],
+                              _d(p.view(np.float64)), _d(g.view(np.float64)), _d(out.view(np.float64)),
+                              nthreads)
+    if rc:
+        raise ValueError(f"oracle_mc_eval failed ({rc})")
+    return out
+
+
+def mc_solve(Y, N, area, k, g, tol=1e-12, maxit=400, nthreads=0):
+    """Sample Dirichlet data p of the Monte-Carlo system L p = R g, with GMRES info."""
+    L, R = mc_assemble(Y, N, area, k, nthreads=nthreads)
+    b = R @ _c(g)
+    x, it, rr, ok = gmres(L, b, tol=tol, maxit=maxit, nthreads=nthreads)
+    return x, dict(iterations=it, rel_residual=rr, converged=ok, L=L, R=R, b=b)

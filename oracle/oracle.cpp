@@ -550,6 +550,70 @@ int oracle_bem_solve(const double* V, int64_t nv, const int32_t* T, int64_t nt, 
   return st;
 }
 
+// ---------------------------------------------------------------------------------------
+// BEM-MC (paper Sec. 4.1.1 and 4.2): the conventional boundary integral equation (beta = 0 in
+// Eq. 6) with the surface integral replaced by a Monte-Carlo sum over M sample points y_j of
+// uniform density on the surface (1/q = |Gamma|), and collocated at the same samples:
+//   1/2 p_i = sum_{j != i} w [ dG/dn_y(y_i, y_j) p_j - G(y_i, y_j) g_j ] - (eps/2) g_i.
+// The sample's own neighbourhood is the disk of radius eps about y_i: with one sample at its
+// centre, the single layer over the disk is 2 pi eps/(4 pi) g_i = (eps/2) g_i, and the double
+// layer vanishes there (d is perpendicular to the normal on the flat disk). The paper gives no
+// value for eps; the reading taken is the sample's share of the surface, pi eps^2 = |Gamma|/M,
+// so the other samples share |Gamma| - pi eps^2 and each weighs
+// w = (|Gamma| - pi eps^2)/(M - 1) = |Gamma|/M. Normals are outward (the paper's equation is
+// written with the opposite normal, which flips both terms). In the L p = R g form:
+//   L_ij = 1/2 delta_ij - w dG/dn_y(y_i, y_j) (1 - delta_ij)
+//   R_ij = -w G(y_i, y_j) (1 - delta_ij) - (eps/2) delta_ij.
+// The field at x off the surface is the same Monte-Carlo sum of the exterior representation:
+//   p(x) = sum_j w [ p_j dG/dn_y(x, y_j) - g_j G(x, y_j) ].
+
+// L and R (M x M complex, row-major, interleaved re/im) for samples Y (M x 3) with unit
+// outward normals N (M x 3) on a surface of area `area`.
+int oracle_mc_assemble(const double* Y, const double* N, int64_t M, double area, double k,
+                       double* L, double* R, int nthreads) {
+  if (!(k > 0.0) || M < 2 || !(area > 0.0)) return 1;
+  const double w = area / (double)M;
+  const double eps = std::sqrt(area / (kPi * (double)M));
+  cplx* Lc = reinterpret_cast<cplx*>(L);
+  cplx* Rc = reinterpret_cast<cplx*>(R);
+  parallel_for(M, nthreads, [&](int64_t i) {
+    const vec3 x = load3(Y + 3 * i), nx = load3(N + 3 * i);
+    for (int64_t j = 0; j < M; ++j) {
+      if (j == i) {
+        Lc[i * M + j] = 0.5;
+        Rc[i * M + j] = ORACLE_PLANT == 5 ? 0.5 * eps : (ORACLE_PLANT == 7 ? 0.0 : -0.5 * eps);
+        continue;
+      }
+      Kernels kv = kernels(k, x, nx, load3(Y + 3 * j), load3(N + 3 * j));
+      Lc[i * M + j] = -w * (ORACLE_PLANT == 6 ? kv.dGdnx : kv.dGdny);
+      Rc[i * M + j] = -w * kv.G;
+    }
+  });
+  return 0;
+}
+
+// Field at points pts (Q x 3) from the samples' Dirichlet (p) and Neumann (g) values.
+int oracle_mc_eval(const double* Y, const double* N, int64_t M, double area, double k,
+                   const double* pts, int64_t Q, const double* p, const double* g, double* out,
+                   int nthreads) {
+  if (!(k > 0.0) || M < 1 || !(area > 0.0) || Q < 0) return 1;
+  const double w = area / (double)M;
+  const cplx* pv = reinterpret_cast<const cplx*>(p);
+  const cplx* gv = reinterpret_cast<const cplx*>(g);
+  cplx* o = reinterpret_cast<cplx*>(out);
+  const vec3 zero = {0.0, 0.0, 0.0};
+  parallel_for(Q, nthreads, [&](int64_t q) {
+    const vec3 x = load3(pts + 3 * q);
+    cplx s = 0.0;
+    for (int64_t j = 0; j < M; ++j) {
+      Kernels kv = kernels(k, x, zero, load3(Y + 3 * j), load3(N + 3 * j));
+      s += w * (pv[j] * kv.dGdny + (ORACLE_PLANT == 8 ? 1.0 : -1.0) * gv[j] * kv.G);
+    }
+    o[q] = s;
+  });
+  return 0;
+}
+
 int oracle_hardware_threads(void) { return (int)std::thread::hardware_concurrency(); }
 
 }  // extern "C"

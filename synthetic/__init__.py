@@ -295,6 +295,82 @@ def monopole_neumann(V: np.ndarray, F: np.ndarray, k: float, x0=(0.0, 0.0, 0.0))
     return du * (d * n).sum(axis=1) / rho
 
 
+def monopole_neumann_at(Y: np.ndarray, N: np.ndarray, k: float, x0=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """du/dn of the interior point source at surface points Y with unit normals N."""
+    d = np.asarray(Y) - np.asarray(x0)
+    rho = np.linalg.norm(d, axis=1)
+    u = np.exp(1j * k * rho) / (4.0 * math.pi * rho)
+    du = u * (1j * k - 1.0 / rho)
+    return du * (d * np.asarray(N)).sum(axis=1) / rho
+
+
+# ------------------------------------------------------------------- surface sample points
+# Sample sets for the Monte-Carlo solver: points on the surface, their unit outward normals and
+# the total surface area. These are the random draws of the method, made here and passed in.
+def sphere_samples(M: int, radius: float = 1.0):
+    """Fibonacci-lattice points on a sphere (quasi-uniform), exact normals and area."""
+    Y = fibonacci_points(M, radius)
+    return Y, Y / radius, 4.0 * math.pi * radius * radius
+
+
+def _triangle_table(V: np.ndarray, F: np.ndarray):
+    a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    cr = np.cross(b - a, c - a)
+    dbl = np.linalg.norm(cr, axis=1)
+    return a, b, c, cr / dbl[:, None], 0.5 * dbl
+
+
+def mesh_random_samples(V: np.ndarray, F: np.ndarray, M: int, seed: int):
+    """M points of uniform density on a triangle mesh (triangle by area, then uniform
+    barycentrics), with the triangle's outward normal; returns (Y, N, total area)."""
+    rng = np.random.default_rng(seed)
+    a, b, c, n, area = _triangle_table(V, F)
+    t = rng.choice(len(F), size=M, p=area / area.sum())
+    r1, r2 = rng.random(M), rng.random(M)
+    s1 = np.sqrt(r1)
+    Y = (1 - s1)[:, None] * a[t] + (s1 * (1 - r2))[:, None] * b[t] + (s1 * r2)[:, None] * c[t]
+    return Y, n[t].copy(), float(area.sum())
+
+
+def mesh_poisson_samples(V: np.ndarray, F: np.ndarray, M: int, seed: int, oversample: int = 8):
+    """About M points on a triangle mesh with a minimum spacing (Poisson-disk sampling by
+    greedy dart throwing over an oversampled uniform candidate set, in a hash grid), the
+    radius shrunk until M points are accepted; returns (Y, N, total area)."""
+    Yc, Nc, total = mesh_random_samples(V, F, oversample * M, seed)
+    d_hex = math.sqrt(2.0 * total / (math.sqrt(3.0) * M))  # spacing of a hexagonal packing
+    for frac in (0.8, 0.75, 0.7, 0.65, 0.6, 0.55, 0.5):
+        r = frac * d_hex
+        cell = {}
+        keep = []
+        inv = 1.0 / r
+        for i, y in enumerate(Yc):
+            key = tuple(np.floor(y * inv).astype(int))
+            ok = True
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        for j in cell.get((key[0] + dx, key[1] + dy, key[2] + dz), ()):
+                            if np.sum((Yc[j] - y) ** 2) < r * r:
+                                ok = False
+                                break
+                        if not ok:
+                            break
+                    if not ok:
+                        break
+                if not ok:
+                    break
+            if ok:
+                cell.setdefault(key, []).append(i)
+                keep.append(i)
+                if len(keep) == M:
+                    break
+        if len(keep) == M:
+            idx = np.array(keep)
+            return Yc[idx].copy(), Nc[idx].copy(), total
+    idx = np.array(keep)
+    return Yc[idx].copy(), Nc[idx].copy(), total
+
+
 # -------------------------------------------------------------------------- named workloads
 @dataclass
 class Problem:
@@ -370,3 +446,18 @@ def serving_stream(seed: int = 5000, n_req: int = 2000, rate: float = 200.0,
     ka = rng.uniform(ka_range[0], ka_range[1], n_req)
     nrhs = rng.integers(1, nrhs_max + 1, n_req)
     return [(float(t[i]), int(f[i]), float(ka[i]), int(nrhs[i]), seed + 7 + i) for i in range(n_req)]
+
+
+def mc_interior_source(seed: int = 6000, n_tri: int = 10240, M: int = 4096, n_k: int = 64,
+                       ka_range=(0.5, 12.0), n_points: int = 1024, R: float = 4.0, poisson: bool = True):
+    """Monte-Carlo workload: the interior-source body (perturbed ellipsoid, l <= 6) sampled with
+    M Poisson-disk (or uniform random) points, monopole Neumann data at the samples, n_k
+    wavenumbers log-uniform in ka_range, field points at radius R. Returns
+    (Y, N, area, ks, [g per k], points, [exact field per k])."""
+    Vs, F = ring_sphere(n_tri)
+    V = perturbed_ellipsoid(Vs, seed)
+    Y, N, area = (mesh_poisson_samples if poisson else mesh_random_samples)(V, F, M, seed + 1)
+    ks = log_uniform(n_k, ka_range[0], ka_range[1], seed + 2)
+    pts = fibonacci_points(n_points, R)
+    return (Y, N, area, ks, [monopole_neumann_at(Y, N, k) for k in ks], pts,
+            [monopole_field(pts, k) for k in ks])
