@@ -298,6 +298,76 @@ def run_modal(args):
             "accuracy": acc, "clocks": clk.summary()}
 
 
+def run_mc(args):
+    """Monte-Carlo BEM (paper Sec. 4.1.1, 4.2): the interior-source body sampled with --n-samples
+    Poisson-disk points (uniform random with --random-samples), monopole Neumann data at the
+    samples, --n-k wavenumbers in ka [0.5, 12], 1024 field points at radius 4. One step: for
+    each wavenumber, re-assemble the sample operators, solve, evaluate the field."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    Y, N, area, ks, gs, pts, exact = S.mc_interior_source(M=args.n_samples, n_k=args.n_k,
+                                                          poisson=not args.random_samples)
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    Yd, Nd, Pd = (torch.from_numpy(a).to(dev) for a in (Y, N, pts))
+    Gd = [torch.from_numpy(g.astype(np.complex64)).to(dev) for g in gs]
+    stream = torch.cuda.current_stream(dev)
+    op = nb.Operator.assemble_mc(Yd, Nd, area, float(ks[0]), opts)
+    infos = []
+
+    def step(record=None):
+        out = []
+        for i, k in enumerate(ks):
+            op.reassemble(float(k), like=Yd)
+            p, info, st = op.solve(Gd[i])
+            f = op.evaluate(Pd, p, Gd[i])
+            out.append((p, f))
+            if record is not None:
+                record.append((info.iterations, info.rel_residual, st))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            res = step(infos)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    n_solves = args.steps * len(ks)
+    p0 = res[0][0].cpu().numpy()
+    f0 = res[0][1].cpu().numpy()
+    acc = {"surface_rel_err_vs_exact": float(np.linalg.norm(p0 - S.monopole_field(Y, float(ks[0])))
+                                             / np.linalg.norm(S.monopole_field(Y, float(ks[0])))),
+           "field_rel_err_vs_exact": float(np.linalg.norm(f0 - exact[0]) / np.linalg.norm(exact[0])),
+           "k": float(ks[0])}
+    if args.cpu:
+        import oracle
+        L, R = oracle.mc_assemble(Y, N, area, float(ks[0]))
+        pref = np.linalg.solve(L, R @ gs[0])
+        fref = oracle.mc_evaluate(Y, N, area, float(ks[0]), pts, pref, gs[0])
+        acc["surface_rel_err_vs_oracle"] = float(np.linalg.norm(p0 - pref) / np.linalg.norm(pref))
+        acc["field_rel_err_vs_oracle"] = float(np.linalg.norm(f0 - fref) / np.linalg.norm(fref))
+    op.close()
+    return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16 inner GMRES + f32 refinement", "tf32": "f32"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": f"bem_mc_{'random' if args.random_samples else 'poisson'}_{len(Y)}samples_{len(ks)}k",
+                       "samples": len(Y), "ka_range": [0.5, 12.0], "field_points": len(pts), "precision": args.prec},
+            "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
+            "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
+                      "not_converged": sum(1 for i in infos if i[2] != 0)},
+            "accuracy": acc, "clocks": clk.summary()}
+
+
 def run_uneven(args):
     """Uneven batch: --n-mesh perturbed ring spheres of 500-8000 triangles (log-uniform), one
     wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4, through the
@@ -479,7 +549,9 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
-    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve"])
+    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc"])
+    ap.add_argument("--n-samples", type=int, default=4096, help="Monte-Carlo workload: surface samples")
+    ap.add_argument("--random-samples", action="store_true", help="Monte-Carlo workload: uniform random samples")
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--n-mesh", type=int, default=512)
     ap.add_argument("--n-req", type=int, default=300)
@@ -522,7 +594,7 @@ def main():
     import torch
     if args.workload != "interior":
         if rank == 0:
-            fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving}[args.workload]
+            fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc}[args.workload]
             if args.workload == "modal" and args.n_k == 64:
                 args.n_k = 16
             if args.workload == "modal" and args.n_tri == 10240:

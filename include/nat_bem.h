@@ -103,6 +103,29 @@ NAT_BEM_API nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, con
                                 nat_bem_op** out);
 
 /*
+ * Monte-Carlo BEM (paper Sec. 4.1.1 "Monte-Carlo-based integration approximation" and Sec. 4.2
+ * "Singularity handling"): the conventional boundary integral equation (beta = 0 in Eq. 6)
+ * with the surface integral replaced by a sum over m sample points of uniform density on the
+ * surface, collocated at the samples. With w = area / m and the sample's own disk of radius
+ * eps, pi eps^2 = area / m (single layer over the disk = (eps/2) g_i, double layer 0):
+ *
+ *   L_ij = 1/2 d_ij - w dG/dn_y(y_i, y_j) (1 - d_ij),   R_ij = -w G(y_i, y_j) (1 - d_ij) - (eps/2) d_ij.
+ *
+ * The op then works with nat_bem_solve (p at the samples from g at the samples),
+ * nat_bem_eval (field = sum_j w [p_j dG/dn_y - g_j G]), nat_bem_reassemble and mixed
+ * precision; nat_bem_run_batch and the server take meshes only. The samples are the caller's
+ * draw (uniform random or Poisson-disk, Sec. 4.2); the solver does not sample.
+ *   pts: m x 3 float64 sample positions; normals: m x 3 float64 unit outward normals
+ *   (|n|^2 within 1e-6 of 1); area: total surface area (> 0); host or device pointers.
+ * NAT_BEM_EINVAL: out or arrays NULL, m < 2, area or k not positive and finite, a non-finite
+ * position, a normal that is not a unit vector. NAT_BEM_ENOMEM / NAT_BEM_ECUDA as for
+ * nat_bem_assemble.
+ */
+NAT_BEM_API nat_bem_status nat_bem_assemble_mc(const double* pts, const double* normals, int64_t m,
+                                               double area, double k, const nat_bem_opts* opts,
+                                               void* cuda_stream, nat_bem_op** out);
+
+/*
  * Re-assembles L and R of an existing op at a new wavenumber k (> 0, finite): the mesh checks,
  * the device geometry, the operator memory and the solver workspace are reused, so sweeping
  * the frequencies of one body costs only the element-pair kernels. Work is ordered on

@@ -35,7 +35,7 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc",
             "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply",
             "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
-            "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait"]
+            "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -82,6 +82,8 @@ def lib():
         L.nat_bem_opts_default.restype = None
         L.nat_bem_assemble.argtypes = [vp, i64, vp, i64, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
         L.nat_bem_assemble.restype = ctypes.c_int
+        L.nat_bem_assemble_mc.argtypes = [vp, vp, i64, d, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+        L.nat_bem_assemble_mc.restype = ctypes.c_int
         L.nat_bem_reassemble.argtypes = [vp, d, vp]
         L.nat_bem_reassemble.restype = ctypes.c_int
         L.nat_bem_solve.argtypes = [vp, vp, i32, vp, ctypes.POINTER(SolveInfo), vp]
@@ -200,6 +202,22 @@ def nat_bem_assemble(V, F, k: float, opts: Opts | None = None, stream=None) -> c
     st = lib().nat_bem_assemble(pv, nv, pt, nt, float(k), ctypes.byref(opts) if opts else None,
                                 _stream_of(V, stream), ctypes.byref(op))
     del kv, kt
+    _check(st)
+    return op
+
+
+def nat_bem_assemble_mc(Y, N, area: float, k: float, opts: Opts | None = None, stream=None) -> ctypes.c_void_p:
+    """Monte-Carlo op from surface samples Y (m x 3), unit outward normals N (m x 3) and the
+    total surface area; returns the opaque op handle."""
+    py, ky = _ptr(Y, np.float64)
+    pn, kn = _ptr(N, np.float64)
+    m = int(Y.shape[0])
+    if int(N.shape[0]) != m:
+        raise ValueError("Y and N must have the same number of samples")
+    op = ctypes.c_void_p()
+    st = lib().nat_bem_assemble_mc(py, pn, m, float(area), float(k), ctypes.byref(opts) if opts else None,
+                                   _stream_of(Y, stream), ctypes.byref(op))
+    del ky, kn
     _check(st)
     return op
 
@@ -446,6 +464,10 @@ class Operator:
     @classmethod
     def assemble(cls, V, F, k, opts=None, stream=None):
         return cls(nat_bem_assemble(V, F, k, opts, stream), int(F.shape[0]), float(k))
+
+    @classmethod
+    def assemble_mc(cls, Y, N, area, k, opts=None, stream=None):
+        return cls(nat_bem_assemble_mc(Y, N, area, k, opts, stream), int(Y.shape[0]), float(k))
 
     def reassemble(self, k, stream=None, like=None):
         nat_bem_reassemble(self.handle, k, stream, like)

@@ -273,6 +273,107 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
   }
 }
 
+nat_bem_status nat_bem_assemble_mc(const double* pts, const double* normals, int64_t m, double area,
+                                   double k, const nat_bem_opts* opts, void* cuda_stream,
+                                   nat_bem_op** out) {
+  try {
+    clear_error();
+    if (!out) {
+      set_error("out is NULL");
+      return NAT_BEM_EINVAL;
+    }
+    *out = nullptr;
+    if (!pts || !normals) {
+      set_error("pts and normals must not be NULL");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) {
+      set_error("k must be positive and finite");
+      return NAT_BEM_EINVAL;
+    }
+    if (m < 2 || m > ((int64_t)1 << 30)) {
+      set_error("nat_bem_assemble_mc: need 2 <= m < 2^30 samples");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(area > 0.0) || !std::isfinite(area)) {
+      set_error("nat_bem_assemble_mc: area must be positive and finite");
+      return NAT_BEM_EINVAL;
+    }
+    nat_bem_opts o;
+    nat_bem_opts_default(&o);
+    if (opts) o = *opts;
+    NB_TRY(check_opts(o));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    // host copies for the checks: finite positions, unit normals
+    std::vector<double> hY(3 * m), hN(3 * m);
+    NB_TRY_CUDA(cudaMemcpyAsync(hY.data(), pts, 3 * m * sizeof(double), cudaMemcpyDefault, s));
+    NB_TRY_CUDA(cudaMemcpyAsync(hN.data(), normals, 3 * m * sizeof(double), cudaMemcpyDefault, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    for (int64_t j = 0; j < m; ++j) {
+      const double* y = &hY[3 * j];
+      const double* nv = &hN[3 * j];
+      if (!std::isfinite(y[0]) || !std::isfinite(y[1]) || !std::isfinite(y[2])) {
+        set_error("nat_bem_assemble_mc: sample " + std::to_string(j) + " is not finite");
+        return NAT_BEM_EINVAL;
+      }
+      const double nn = nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2];
+      if (!(std::fabs(nn - 1.0) < 1e-6)) {
+        set_error("nat_bem_assemble_mc: normal " + std::to_string(j) + " is not a unit vector");
+        return NAT_BEM_EINVAL;
+      }
+    }
+    nat_bem_op* op = new (std::nothrow) nat_bem_op();
+    if (!op) {
+      set_error("host allocation failed");
+      return NAT_BEM_ENOMEM;
+    }
+    op->n = m;
+    op->k = k;
+    op->opts = o;
+    op->stream = s;
+    op->mc = true;
+    op->mc_area = area;
+    cudaGetDevice(&op->device);
+    op->geo.n = m;
+    op->geo.ld = round_up(m, 32);
+    auto fail = [&](nat_bem_status st) {
+      nat_bem_destroy(op);
+      return st;
+    };
+    double *dY = nullptr, *dN = nullptr;
+    nat_bem_status st = dev_alloc_n(&dY, (size_t)(3 * m), s);
+    if (st == NAT_BEM_OK) st = dev_alloc_n(&dN, (size_t)(3 * m), s);
+    if (st != NAT_BEM_OK) {
+      dev_free(dY, s);
+      return fail(st);
+    }
+    if (cudaMemcpyAsync(dY, hY.data(), 3 * m * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(dN, hN.data(), 3 * m * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+      cudaGetLastError();
+      dev_free(dY, s);
+      dev_free(dN, s);
+      set_error("nat_bem_assemble_mc: copy of the samples failed");
+      return fail(NAT_BEM_ECUDA);
+    }
+    st = mc_geometry_build(op, dY, dN, s);
+    if (st == NAT_BEM_OK) NB_TRY_CUDA(cudaStreamSynchronize(s));  // hY, hN are the copies' sources
+    dev_free(dY, s);
+    dev_free(dN, s);
+    if (st != NAT_BEM_OK) return fail(st);
+    const size_t mat = (size_t)m * (size_t)op->geo.ld;
+    if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
+    if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
+    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
+      return fail(st);
+    if ((st = mc_assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
+    *out = op;
+    return NAT_BEM_OK;
+  } catch (...) {
+    set_error("internal error in nat_bem_assemble_mc");
+    return NAT_BEM_ECUDA;
+  }
+}
+
 nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, int32_t nrhs, float* p_out,
                              nat_bem_solve_info* info, void* cuda_stream) {
   try {
@@ -454,8 +555,9 @@ nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cuda_stream) {
       set_error("k must be positive and finite");
       return NAT_BEM_EINVAL;
     }
-    NB_TRY(ensure_rules(op->opts.adj_subdiv_levels, op->opts.self_theta_pts));
     op->k = k;
+    if (op->mc) return mc_assemble_operators(op, (cudaStream_t)cuda_stream);
+    NB_TRY(ensure_rules(op->opts.adj_subdiv_levels, op->opts.self_theta_pts));
     return assemble_operators(op, (cudaStream_t)cuda_stream);
   } catch (...) {
     set_error("internal error in nat_bem_reassemble");

@@ -1,7 +1,8 @@
 // Field evaluation: the exterior representation p(x) = int [p dG/dn_y - G g] dS_y with the
 // piecewise-constant surface data (pressure anywhere from the Neumann and Dirichlet data,
-// paper Sec. 3.4; its surface limit is the first line of Sec. 4, Eq. 6). The 7-point rule
-// is applied on every element:
+// paper Sec. 3.4; its surface limit is the first line of Sec. 4, Eq. 6). For a Monte-Carlo op
+// (Sec. 4.1.1) the same sum runs over the samples with weight |Gamma| / M each, one point per
+// sample. Otherwise the 7-point rule is applied on every element:
 //
 //   field(x_q) = sum_j [ p_j sum_p w_p A_j dG/dn_y(x_q, y_jp) - g_j sum_p w_p A_j G(x_q, y_jp) ]
 //
@@ -25,14 +26,14 @@ constexpr int kElemStage = 32;     // elements staged per shared-memory round
 constexpr int kMaxRhsPass = 4;     // right-hand sides accumulated per pass
 }  // namespace
 
-template <int NR>
+template <int NR, int NQ>
 __global__ void __launch_bounds__(kEvalThreads)
 k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
        const float4* __restrict__ nrm, const float4* __restrict__ qp, int n,
        const double* __restrict__ pts, int m, float k, const float2* __restrict__ p,
        const float2* __restrict__ g, int rhs0, int elems_per_split, double2* __restrict__ part) {
   __shared__ float4 s_hi[kElemStage], s_lo[kElemStage], s_n[kElemStage];
-  __shared__ float4 s_q[kElemStage * 7];
+  __shared__ float4 s_q[kElemStage * NQ];
   __shared__ float2 s_p[kElemStage * NR], s_g[kElemStage * NR];
   const int qi = blockIdx.x * kEvalThreads + threadIdx.x;
   const bool ok = qi < m;
@@ -51,7 +52,7 @@ k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
   for (int jb = j_begin; jb < j_end; jb += kElemStage) {
     const int cnt = min(kElemStage, j_end - jb);
     __syncthreads();
-    for (int t = threadIdx.x; t < cnt * 7; t += kEvalThreads) s_q[t] = qp[7 * (size_t)jb + t];
+    for (int t = threadIdx.x; t < cnt * NQ; t += kEvalThreads) s_q[t] = qp[NQ * (size_t)jb + t];
     if (threadIdx.x < cnt) {
       const int j = jb + threadIdx.x;
       s_hi[threadIdx.x] = c_hi[j];
@@ -73,8 +74,8 @@ k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
       const float dny = Dx * nj.x + Dy * nj.y + Dz * nj.z;
       float Gr = 0.f, Gi = 0.f, Dr = 0.f, Di = 0.f;  // sums of w A G and w A dG/dn_y
 #pragma unroll
-      for (int q = 0; q < 7; ++q) {
-        const float4 o = s_q[7 * t + q];
+      for (int q = 0; q < NQ; ++q) {
+        const float4 o = s_q[NQ * t + q];
         const float dx = Dx - o.x, dy = Dy - o.y, dz = Dz - o.z;
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         const float rinv = rsqrtf(r2);
@@ -123,6 +124,28 @@ __global__ void k_eval_reduce(const double2* __restrict__ part, int m, int split
   out[(size_t)(rhs0 + s) * m + qi] = make_float2((float)re, (float)im);
 }
 
+// One k_eval launch for nr right-hand sides: seven quadrature points per element, or one
+// sample point per Monte-Carlo sample (weight w / (4 pi) at offset 0).
+template <int NQ>
+static void eval_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, int n,
+                           const double* d_pts, int m, float k, const float2* d_p,
+                           const float2* d_g, int r0, int per, double2* part) {
+  switch (nr) {
+    case 1: k_eval<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
+    case 2: k_eval<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
+    case 3: k_eval<3, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
+    default: k_eval<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
+  }
+}
+
+static void eval_launch(const nat_bem_op* op, int nr, dim3 grid, cudaStream_t s, const double* d_pts,
+                        int m, const float2* d_p, const float2* d_g, int r0, int per, double2* part) {
+  if (op->mc)
+    eval_launch_nq<1>(nr, grid, s, op->geo, (int)op->n, d_pts, m, (float)op->k, d_p, d_g, r0, per, part);
+  else
+    eval_launch_nq<7>(nr, grid, s, op->geo, (int)op->n, d_pts, m, (float)op->k, d_p, d_g, r0, per, part);
+}
+
 nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
                          const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
                          cudaStream_t s) {
@@ -144,12 +167,7 @@ nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    switch (nr) {
-      case 1: NB_LAUNCH("eval", s, k_eval<1><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
-      case 2: NB_LAUNCH("eval", s, k_eval<2><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
-      case 3: NB_LAUNCH("eval", s, k_eval<3><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
-      default: NB_LAUNCH("eval", s, k_eval<4><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part)); break;
-    }
+    NB_LAUNCH("eval", s, eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
     NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out));
@@ -219,12 +237,7 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    switch (nr) {
-      case 1: k_eval<1><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
-      case 2: k_eval<2><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
-      case 3: k_eval<3><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
-      default: k_eval<4><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, (int)m, (float)op->k, d_p, d_g, r0, per, part); break;
-    }
+    eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part);
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
     k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out);

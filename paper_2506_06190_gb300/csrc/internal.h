@@ -124,6 +124,8 @@ struct nat_bem_op {
   float2* R = nullptr;                 // n x ld complex64, row-major (store_r)
   uint32_t* Lb = nullptr;              // n x ld complex as packed bf16 pairs (mixed BF16)
   natbem::Workspace* ws = nullptr;     // solver workspace, grown on demand
+  bool mc = false;                     // Monte-Carlo op (nat_bem_assemble_mc): n samples
+  double mc_area = 0.0;                // Monte-Carlo op: total surface area
 };
 
 namespace natbem {
@@ -132,6 +134,10 @@ namespace natbem {
 nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
                               const std::vector<int2>& near_pairs, cudaStream_t s);
 nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s);
+
+// mc.cu
+nat_bem_status mc_geometry_build(nat_bem_op* op, const double* dY, const double* dN, cudaStream_t s);
+nat_bem_status mc_assemble_operators(nat_bem_op* op, cudaStream_t s);
 
 // gmres.cu
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,

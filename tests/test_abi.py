@@ -97,6 +97,29 @@ def test_assemble_rejects_bad_input(nb, case):
     assert len(nb.nat_bem_last_error()) > 0
 
 
+@pytest.mark.parametrize("case", ["one_sample", "area_zero", "area_nan", "k_zero", "null"])
+def test_assemble_mc_rejects_bad_input(nb, case):
+    """Argument checks that need no device (normals and positions are checked on the GPU machine)."""
+    Y, N, A = S.sphere_samples(64)
+    m, area, k = 64, A, 2.0
+    if case == "one_sample":
+        m = 1
+    elif case == "area_zero":
+        area = 0.0
+    elif case == "area_nan":
+        area = float("nan")
+    elif case == "k_zero":
+        k = 0.0
+    Y = np.ascontiguousarray(Y)
+    N = np.ascontiguousarray(N)
+    op = ctypes.c_void_p()
+    py = None if case == "null" else ctypes.c_void_p(Y.ctypes.data)
+    st = nb.lib().nat_bem_assemble_mc(py, ctypes.c_void_p(N.ctypes.data), m, area, k, None, None,
+                                      ctypes.byref(op))
+    assert st == nb.NAT_BEM_EINVAL and not op.value
+    assert len(nb.nat_bem_last_error()) > 0
+
+
 def test_solve_and_eval_reject_null(nb):
     L = nb.lib()
     assert L.nat_bem_solve(None, None, 1, None, None, None) == nb.NAT_BEM_EINVAL
