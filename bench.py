@@ -368,6 +368,63 @@ def run_mc(args):
             "accuracy": acc, "clocks": clk.summary()}
 
 
+def run_dataset(args):
+    """Training-data generation (paper Sec. 3.4): for each of --n-k wavenumbers of the
+    interior-source body, re-assemble, solve, draw 10,000 samples at (theta, phi, r) with r in
+    [1.5, 3] bounding radii and take |p| there, and compute the 64 x 32 FFAT map of the far
+    field. Reports solves/s and training samples/s."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    prob = workload(args.n_k, args.n_tri)
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    Vd, Fd = torch.from_numpy(prob.V).to(dev), torch.from_numpy(prob.F).to(dev)
+    Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
+    lo, hi = prob.V.min(axis=0), prob.V.max(axis=0)
+    center, rb = 0.5 * (lo + hi), 0.5 * float(np.linalg.norm(hi - lo))
+    n_samples = 10000
+    rng = np.random.default_rng(7000)
+    U = [torch.from_numpy(rng.random((n_samples, 3))).to(dev) for _ in prob.ks]
+    th = (np.arange(32) + 0.5) * np.pi / 32
+    ph = (np.arange(64) + 0.5) * 2 * np.pi / 64
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dirs = torch.from_numpy(np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    op = nb.Operator.assemble(Vd, Fd, float(prob.ks[0]), opts)
+
+    def step():
+        for i, k in enumerate(prob.ks):
+            op.reassemble(float(k), like=Vd)
+            p, info, st = op.solve(Gd[i])
+            op.sample_field(U[i], center, 1.5 * rb, 3.0 * rb, p, Gd[i])
+            op.far_field(dirs, p, Gd[i])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    n_solves = args.steps * len(prob.ks)
+    op.close()
+    return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
+            "data": "synthetic",
+            "config": {"workload": f"dataset_{len(prob.F)}tri_{len(prob.ks)}k_{n_samples}samples_ffat64x32",
+                       "samples_per_solve": n_samples, "ffat": [64, 32], "shell": [1.5, 3.0]},
+            "training_samples_per_s": n_solves * n_samples / (ms * 1e-3),
+            "clocks": clk.summary()}
+
+
 def run_uneven(args):
     """Uneven batch: --n-mesh perturbed ring spheres of 500-8000 triangles (log-uniform), one
     wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4, through the
@@ -549,7 +606,7 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
-    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc"])
+    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset"])
     ap.add_argument("--n-samples", type=int, default=4096, help="Monte-Carlo workload: surface samples")
     ap.add_argument("--random-samples", action="store_true", help="Monte-Carlo workload: uniform random samples")
     ap.add_argument("--nrhs", type=int, default=64)
@@ -594,7 +651,8 @@ def main():
     import torch
     if args.workload != "interior":
         if rank == 0:
-            fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc}[args.workload]
+            fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc,
+                  "dataset": run_dataset}[args.workload]
             if args.workload == "modal" and args.n_k == 64:
                 args.n_k = 16
             if args.workload == "modal" and args.n_tri == 10240:

@@ -218,6 +218,36 @@ NAT_BEM_API nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
                                              void* cuda_stream);
 
 /*
+ * Far-field pattern, the leading term Phi_1 of the FFAT expansion |p(x)| = sum_i Phi_i(theta,
+ * phi) / r^i (paper Sec. 3.1): for unit directions d_q,
+ *   F(d) = lim_{r -> inf} r e^{-ikr} p(r d) = (1/4pi) int [ p (-i k d.n_y) - g ] e^{-ik d.y} dS_y,
+ * with the rule of nat_bem_eval (7 points per element; one point of weight area/m per sample
+ * for a Monte-Carlo op). |F| over a (theta, phi) grid of directions is the FFAT map (the paper
+ * uses 64 x 32, Sec. 5).
+ *   dirs: nd x 3 float64 unit vectors.  p, neumann: nt x nrhs complex64 column-major.
+ *   out: nd x nrhs complex64 column-major.  Host or device pointers; nd = 0 does nothing.
+ * NAT_BEM_EINVAL: op NULL, nd < 0, nrhs < 1, NULL arrays.
+ */
+NAT_BEM_API nat_bem_status nat_bem_far_field(const nat_bem_op* op, const double* dirs, int64_t nd,
+                                             const float* p, const float* neumann, int32_t nrhs,
+                                             float* out, void* cuda_stream);
+
+/*
+ * Training samples of the neural transfer field (paper Sec. 3.4): n points at spherical
+ * coordinates theta = pi u0, phi = 2 pi u1, r = r_lo + (r_hi - r_lo) u2 about `center` (the
+ * paper draws them uniformly with r between 1.5 and 3 times the scene's bounding radius), and
+ * the pressure amplitude |p| there (the paper trains on the amplitude only).
+ *   u: n x 3 float64 draws in [0, 1) (the caller's random numbers).  center: 3 float64 (host).
+ *   p, neumann: nt x nrhs complex64.  coords_out: n x 3 float64 (theta, phi, r).
+ *   amp_out: n x nrhs float32 column-major.  Host or device pointers; n = 0 does nothing.
+ * NAT_BEM_EINVAL: op or center NULL, n < 0, nrhs < 1, NULL arrays, not 0 < r_lo <= r_hi finite.
+ */
+NAT_BEM_API nat_bem_status nat_bem_sample_field(const nat_bem_op* op, const double* u, int64_t n,
+                                                const double* center, double r_lo, double r_hi,
+                                                const float* p, const float* neumann, int32_t nrhs,
+                                                double* coords_out, float* amp_out, void* cuda_stream);
+
+/*
  * Y = M X with the assembled M = L (which = 0) or R (which = 1) for nrhs complex64 vectors
  * (X, Y: nt x nrhs, column-major; host or device), by the chosen product engine:
  *   NAT_BEM_ENGINE_AUTO: the solver's accurate product (GEMV for one vector, FP32 GEMM else);

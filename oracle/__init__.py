@@ -87,6 +87,8 @@ def _configure(L):
                                        c_int, dp, dp, ctypes.POINTER(c_int), dp, dp]
         L.oracle_mc_assemble.argtypes = [dp, dp, i64, c_d, c_d, dp, dp, c_int]
         L.oracle_mc_eval.argtypes = [dp, dp, i64, c_d, c_d, dp, i64, dp, dp, dp, c_int]
+        L.oracle_far_field.argtypes = [dp, i64, ip, i64, c_d, dp, i64, dp, dp, dp, c_int]
+        L.oracle_mc_far_field.argtypes = [dp, dp, i64, c_d, c_d, dp, i64, dp, dp, dp, c_int]
         L.oracle_hardware_threads.argtypes = []
     return L
 
@@ -291,3 +293,52 @@ def mc_solve(Y, N, area, k, g, tol=1e-12, maxit=400, nthreads=0):
     b = R @ _c(g)
     x, it, rr, ok = gmres(L, b, tol=tol, maxit=maxit, nthreads=nthreads)
     return x, dict(iterations=it, rel_residual=rr, converged=ok, L=L, R=R, b=b)
+
+
+# ------------------------------------------------------------------ far field and samples
+def far_field(V, F, k, dirs, p, g, nthreads=0):
+    """Far-field pattern F(d) = lim r e^{-ikr} p(r d) for unit directions `dirs` (nd x 3)."""
+    V, F = _mesh(V, F)
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    p, g = _c(p), _c(g)
+    out = np.zeros(d.shape[0], dtype=np.complex128)
+    rc = lib().oracle_far_field(_d(V), V.shape[0], _i(F), F.shape[0], float(k), _d(d), d.shape[0],
+                                _d(p.view(np.float64)), _d(g.view(np.float64)), _d(out.view(np.float64)),
+                                nthreads)
+    if rc:
+        raise ValueError(f"oracle_far_field failed ({rc})")
+    return out
+
+
+def mc_far_field(Y, N, area, k, dirs, p, g, nthreads=0):
+    """Far-field pattern of a Monte-Carlo solution (samples Y, normals N, total area)."""
+    Y, N = _samples(Y, N)
+    d = np.ascontiguousarray(dirs, dtype=np.float64).reshape(-1, 3)
+    p, g = _c(p), _c(g)
+    out = np.zeros(d.shape[0], dtype=np.complex128)
+    rc = lib().oracle_mc_far_field(_d(Y), _d(N), Y.shape[0], float(area), float(k), _d(d), d.shape[0],
+                                   _d(p.view(np.float64)), _d(g.view(np.float64)),
+                                   _d(out.view(np.float64)), nthreads)
+    if rc:
+        raise ValueError(f"oracle_mc_far_field failed ({rc})")
+    return out
+
+
+def ffat_directions(n_phi=64, n_theta=32):
+    """Unit directions of an n_phi x n_theta FFAT map: cell centres in phi (azimuth, fastest
+    varying) and theta (polar angle), row-major (theta, phi)."""
+    th = (np.arange(n_theta) + 0.5) * np.pi / n_theta
+    ph = (np.arange(n_phi) + 0.5) * 2.0 * np.pi / n_phi
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    return np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], axis=-1).reshape(-1, 3)
+
+
+def sample_coords(u, center, r_lo, r_hi):
+    """Training-sample coordinates (paper Sec. 3.4): theta = pi u0, phi = 2 pi u1,
+    r = r_lo + (r_hi - r_lo) u2 about `center`; returns ((theta, phi, r), Cartesian points)."""
+    u = np.asarray(u, dtype=np.float64).reshape(-1, 3)
+    th, ph = np.pi * u[:, 0], 2.0 * np.pi * u[:, 1]
+    r = r_lo + (r_hi - r_lo) * u[:, 2]
+    xyz = np.asarray(center, dtype=np.float64) + r[:, None] * np.stack(
+        [np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    return np.stack([th, ph, r], axis=1), xyz

@@ -614,6 +614,60 @@ int oracle_mc_eval(const double* Y, const double* N, int64_t M, double area, dou
   return 0;
 }
 
+// ---------------------------------------------------------------------------------------
+// Far-field pattern, the leading term Phi_1 of the FFAT expansion |p(x)| = sum_i Phi_i / r^i
+// (paper Sec. 3.1, the equation after the FFAT citation): as |x| = r -> infinity along the unit
+// direction d, G(x, y) -> e^{ikr}/(4 pi r) e^{-ik d.y} and dG/dn_y -> that times (-ik d.n_y),
+// so F(d) = lim r e^{-ikr} p(r d) = (1/4pi) int [ p (-ik d.n_y) - g ] e^{-ik d.y} dS_y,
+// with the 7-point rule on every element (the rule of the field evaluation).
+int oracle_far_field(const double* V, int64_t nv, const int32_t* T, int64_t nt, double k,
+                     const double* dirs, int64_t nd, const double* p, const double* g, double* out,
+                     int nthreads) {
+  if (!(k > 0.0) || nt <= 0 || nv <= 0 || nd < 0) return 1;
+  const cplx* pv = reinterpret_cast<const cplx*>(p);
+  const cplx* gv = reinterpret_cast<const cplx*>(g);
+  cplx* o = reinterpret_cast<cplx*>(out);
+  const std::vector<QuadPoint> rule = radon7();
+  parallel_for(nd, nthreads, [&](int64_t q) {
+    const vec3 d = load3(dirs + 3 * q);
+    cplx s = 0.0;
+    for (int64_t j = 0; j < nt; ++j) {
+      const Tri t = triangle_of(V, T, j);
+      const vec3 n = tri_normal(t);
+      const double A = tri_area(t);
+      cplx e = 0.0;
+      for (const QuadPoint& qp : rule) {
+        const vec3 y = add(add(scale(t.a, qp.l0), scale(t.b, qp.l1)), scale(t.c, qp.l2));
+        e += qp.w * A * std::exp(-kI * (k * dot(d, y)));
+      }
+      s += (pv[j] * ((ORACLE_PLANT == 9 ? kI : -kI) * k * dot(d, n)) - gv[j]) * e;
+    }
+    o[q] = s / (4.0 * kPi);
+  });
+  return 0;
+}
+
+// The same far field for a Monte-Carlo op: samples Y with normals N, each of weight area/M.
+int oracle_mc_far_field(const double* Y, const double* N, int64_t M, double area, double k,
+                        const double* dirs, int64_t nd, const double* p, const double* g,
+                        double* out, int nthreads) {
+  if (!(k > 0.0) || M < 1 || !(area > 0.0) || nd < 0) return 1;
+  const double w = area / (double)M;
+  const cplx* pv = reinterpret_cast<const cplx*>(p);
+  const cplx* gv = reinterpret_cast<const cplx*>(g);
+  cplx* o = reinterpret_cast<cplx*>(out);
+  parallel_for(nd, nthreads, [&](int64_t q) {
+    const vec3 d = load3(dirs + 3 * q);
+    cplx s = 0.0;
+    for (int64_t j = 0; j < M; ++j) {
+      const vec3 y = load3(Y + 3 * j), n = load3(N + 3 * j);
+      s += w * (pv[j] * (-kI * k * dot(d, n)) - gv[j]) * std::exp(-kI * (k * dot(d, y)));
+    }
+    o[q] = s / (4.0 * kPi);
+  });
+  return 0;
+}
+
 int oracle_hardware_threads(void) { return (int)std::thread::hardware_concurrency(); }
 
 }  // extern "C"

@@ -35,7 +35,8 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_trace_launches", "nat_bem_trace_kernel", "nat_bem_eval_noalloc",
             "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply",
             "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
-            "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc"]
+            "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
+            "nat_bem_far_field", "nat_bem_sample_field"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -84,6 +85,10 @@ def lib():
         L.nat_bem_assemble.restype = ctypes.c_int
         L.nat_bem_assemble_mc.argtypes = [vp, vp, i64, d, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
         L.nat_bem_assemble_mc.restype = ctypes.c_int
+        L.nat_bem_far_field.argtypes = [vp, vp, i64, vp, vp, ctypes.c_int32, vp, vp]
+        L.nat_bem_far_field.restype = ctypes.c_int
+        L.nat_bem_sample_field.argtypes = [vp, vp, i64, vp, d, d, vp, vp, ctypes.c_int32, vp, vp, vp]
+        L.nat_bem_sample_field.restype = ctypes.c_int
         L.nat_bem_reassemble.argtypes = [vp, d, vp]
         L.nat_bem_reassemble.restype = ctypes.c_int
         L.nat_bem_solve.argtypes = [vp, vp, i32, vp, ctypes.POINTER(SolveInfo), vp]
@@ -267,6 +272,51 @@ def nat_bem_eval(op, points, p, neumann, out=None, stream=None):
     if not _is_torch(out) and ko is not out:
         out[...] = ko
     return out
+
+
+def nat_bem_far_field(op, dirs, p, neumann, out=None, stream=None):
+    """Far-field pattern F(d) = lim r e^{-ikr} p(r d) at unit directions (nd, 3)."""
+    n = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(p, n)
+    nd = int(dirs.shape[0])
+    pdir, kdir = _ptr(dirs, np.float64)
+    pd, kp = _ptr(p, np.complex64)
+    pg, kg = _ptr(neumann, np.complex64)
+    if out is None:
+        if _is_torch(p):
+            import torch
+            out = torch.empty((nrhs, nd) if p.dim() == 2 else (nd,), dtype=torch.complex64, device=p.device)
+        else:
+            out = np.zeros((nd, nrhs) if np.ndim(p) == 2 else (nd,), dtype=np.complex64, order="F")
+    po, ko = _ptr(out, np.complex64)
+    _check(lib().nat_bem_far_field(op, pdir, nd, pd, pg, nrhs, po, _stream_of(p, stream)))
+    if not _is_torch(out) and ko is not out:
+        out[...] = ko
+    return out
+
+
+def nat_bem_sample_field(op, u, center, r_lo, r_hi, p, neumann, stream=None):
+    """Training samples (paper Sec. 3.4) from draws u (n, 3) in [0, 1): returns
+    (coords (n, 3) = theta, phi, r; amplitudes |p| (n,) or (n, nrhs)), numpy or torch like u."""
+    n_el = int(lib().nat_bem_op_size(op))
+    nrhs = _nrhs_of(p, n_el)
+    n = int(u.shape[0])
+    pu, ku = _ptr(u, np.float64)
+    pd, kp = _ptr(p, np.complex64)
+    pg, kg = _ptr(neumann, np.complex64)
+    c = np.ascontiguousarray(center, dtype=np.float64).reshape(3)
+    if _is_torch(u):
+        import torch
+        coords = torch.empty((n, 3), dtype=torch.float64, device=u.device)
+        amp = torch.empty((nrhs, n) if nrhs > 1 else (n,), dtype=torch.float32, device=u.device)
+        pc, pa = ctypes.c_void_p(coords.data_ptr()), ctypes.c_void_p(amp.data_ptr())
+    else:
+        coords = np.zeros((n, 3), dtype=np.float64)
+        amp = np.zeros((n, nrhs) if nrhs > 1 else (n,), dtype=np.float32, order="F")
+        pc, pa = ctypes.c_void_p(coords.ctypes.data), ctypes.c_void_p(amp.ctypes.data)
+    _check(lib().nat_bem_sample_field(op, pu, n, ctypes.c_void_p(c.ctypes.data), float(r_lo), float(r_hi),
+                                      pd, pg, nrhs, pc, pa, _stream_of(u, stream)))
+    return coords, amp
 
 
 def nat_bem_eval_noalloc(op, points, p, neumann, out, stream=None) -> int:
@@ -478,6 +528,12 @@ class Operator:
 
     def evaluate(self, points, p, neumann, out=None, stream=None):
         return nat_bem_eval(self.handle, points, p, neumann, out, stream)
+
+    def far_field(self, dirs, p, neumann, out=None, stream=None):
+        return nat_bem_far_field(self.handle, dirs, p, neumann, out, stream)
+
+    def sample_field(self, u, center, r_lo, r_hi, p, neumann, stream=None):
+        return nat_bem_sample_field(self.handle, u, center, r_lo, r_hi, p, neumann, stream)
 
     def apply(self, which, engine, X):
         return nat_bem_op_apply(self.handle, which, engine, X)

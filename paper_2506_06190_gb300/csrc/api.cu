@@ -463,6 +463,121 @@ nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts, int64_t m, 
   }
 }
 
+nat_bem_status nat_bem_far_field(const nat_bem_op* op, const double* dirs, int64_t nd, const float* p,
+                                 const float* neumann, int32_t nrhs, float* out, void* cuda_stream) {
+  try {
+    clear_error();
+    if (!op || nd < 0 || nrhs < 1 || (nd > 0 && (!dirs || !p || !neumann || !out))) {
+      set_error("nat_bem_far_field: bad arguments (op NULL, nd < 0, nrhs < 1 or NULL arrays)");
+      return NAT_BEM_EINVAL;
+    }
+    if (nd == 0) return NAT_BEM_OK;
+    if (nd > ((int64_t)1 << 31) - 1) {
+      set_error("nat_bem_far_field: too many directions");
+      return NAT_BEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t cnt = (size_t)op->n * nrhs;
+    const double* dd = nullptr;
+    double* td = nullptr;
+    const float2 *dp = nullptr, *dg = nullptr;
+    float2 *tp = nullptr, *tg = nullptr;
+    NB_TRY(to_device(dirs, (size_t)(3 * nd), s, &dd, &td));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    const bool odev = is_device_pointer(out);
+    float2* dout = reinterpret_cast<float2*>(out);
+    float2* tout = nullptr;
+    if (!odev) {
+      NB_TRY(dev_alloc_n(&tout, (size_t)nd * nrhs, s));
+      dout = tout;
+    }
+    nat_bem_status st = far_field_impl(op, dd, nd, dp, dg, nrhs, dout, s);
+    if (st == NAT_BEM_OK && !odev) {
+      cudaError_t e = cudaMemcpyAsync(out, tout, (size_t)nd * nrhs * sizeof(float2), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copy of the far field to the host failed: ") + cudaGetErrorString(e));
+        st = NAT_BEM_ECUDA;
+      }
+    }
+    dev_free(td, s);
+    dev_free(tp, s);
+    dev_free(tg, s);
+    dev_free(tout, s);
+    return st;
+  } catch (...) {
+    set_error("internal error in nat_bem_far_field");
+    return NAT_BEM_ECUDA;
+  }
+}
+
+nat_bem_status nat_bem_sample_field(const nat_bem_op* op, const double* u, int64_t n, const double* center,
+                                    double r_lo, double r_hi, const float* p, const float* neumann,
+                                    int32_t nrhs, double* coords_out, float* amp_out, void* cuda_stream) {
+  try {
+    clear_error();
+    if (!op || n < 0 || nrhs < 1 || !center ||
+        (n > 0 && (!u || !p || !neumann || !coords_out || !amp_out))) {
+      set_error("nat_bem_sample_field: bad arguments (op or center NULL, n < 0, nrhs < 1, NULL arrays)");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(r_lo > 0.0) || !(r_hi >= r_lo) || !std::isfinite(r_hi) || !std::isfinite(center[0]) ||
+        !std::isfinite(center[1]) || !std::isfinite(center[2])) {
+      set_error("nat_bem_sample_field: need 0 < r_lo <= r_hi, finite, and a finite centre");
+      return NAT_BEM_EINVAL;
+    }
+    if (n == 0) return NAT_BEM_OK;
+    if (n > ((int64_t)1 << 31) - 1) {
+      set_error("nat_bem_sample_field: too many samples");
+      return NAT_BEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const size_t cnt = (size_t)op->n * nrhs;
+    const double* du = nullptr;
+    double* tu = nullptr;
+    const float2 *dp = nullptr, *dg = nullptr;
+    float2 *tp = nullptr, *tg = nullptr;
+    NB_TRY(to_device(u, (size_t)(3 * n), s, &du, &tu));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    const bool cdev = is_device_pointer(coords_out), adev = is_device_pointer(amp_out);
+    double* dco = coords_out;
+    float* dam = amp_out;
+    double* tco = nullptr;
+    float* tam = nullptr;
+    if (!cdev) {
+      NB_TRY(dev_alloc_n(&tco, (size_t)(3 * n), s));
+      dco = tco;
+    }
+    if (!adev) {
+      NB_TRY(dev_alloc_n(&tam, (size_t)n * nrhs, s));
+      dam = tam;
+    }
+    nat_bem_status st = sample_field_impl(op, du, n, center, r_lo, r_hi, dp, dg, nrhs, dco, dam, s);
+    if (st == NAT_BEM_OK && (!cdev || !adev)) {
+      cudaError_t e = cudaSuccess;
+      if (!cdev) e = cudaMemcpyAsync(coords_out, tco, (size_t)(3 * n) * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess && !adev)
+        e = cudaMemcpyAsync(amp_out, tam, (size_t)n * nrhs * sizeof(float), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) {
+        set_error(std::string("copy of the samples to the host failed: ") + cudaGetErrorString(e));
+        st = NAT_BEM_ECUDA;
+      }
+    }
+    dev_free(tu, s);
+    dev_free(tp, s);
+    dev_free(tg, s);
+    dev_free(tco, s);
+    dev_free(tam, s);
+    return st;
+  } catch (...) {
+    set_error("internal error in nat_bem_sample_field");
+    return NAT_BEM_ECUDA;
+  }
+}
+
 nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t engine,
                                 const float* X, int32_t nrhs, float* Y, void* cuda_stream) {
   try {

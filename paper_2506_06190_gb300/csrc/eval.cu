@@ -109,6 +109,110 @@ k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
   }
 }
 
+// Far-field pattern, the leading FFAT term (paper Sec. 3.1): for unit directions d,
+//   F(d) = lim r e^{-ikr} p(r d) = sum_j sum_q (w_q A_j / 4pi) [p_j (-i k d.n_j) - g_j] e^{-ik d.y_jq}
+// with the same per-element rule (or one point per Monte-Carlo sample) as the field; one thread
+// per direction, elements staged in shared memory, per-split FP64 partials as in k_eval.
+template <int NR, int NQ>
+__global__ void __launch_bounds__(kEvalThreads)
+k_far_field(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
+            const float4* __restrict__ nrm, const float4* __restrict__ qp, int n,
+            const double* __restrict__ dirs, int nd, float k, const float2* __restrict__ p,
+            const float2* __restrict__ g, int rhs0, int elems_per_split, double2* __restrict__ part) {
+  __shared__ float4 s_hi[kElemStage], s_lo[kElemStage], s_n[kElemStage];
+  __shared__ float4 s_q[kElemStage * NQ];
+  __shared__ float2 s_p[kElemStage * NR], s_g[kElemStage * NR];
+  const int qi = blockIdx.x * kEvalThreads + threadIdx.x;
+  const bool ok = qi < nd;
+  float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+  if (ok) {
+    d0 = (float)dirs[3 * (size_t)qi];
+    d1 = (float)dirs[3 * (size_t)qi + 1];
+    d2 = (float)dirs[3 * (size_t)qi + 2];
+  }
+  const int j_begin = blockIdx.y * elems_per_split;
+  const int j_end = min(n, j_begin + elems_per_split);
+  float accr[NR], acci[NR];
+#pragma unroll
+  for (int s = 0; s < NR; ++s) accr[s] = acci[s] = 0.f;
+  for (int jb = j_begin; jb < j_end; jb += kElemStage) {
+    const int cnt = min(kElemStage, j_end - jb);
+    __syncthreads();
+    for (int t = threadIdx.x; t < cnt * NQ; t += kEvalThreads) s_q[t] = qp[NQ * (size_t)jb + t];
+    if (threadIdx.x < cnt) {
+      const int j = jb + threadIdx.x;
+      s_hi[threadIdx.x] = c_hi[j];
+      s_lo[threadIdx.x] = c_lo[j];
+      s_n[threadIdx.x] = nrm[j];
+#pragma unroll
+      for (int s = 0; s < NR; ++s) {
+        s_p[threadIdx.x * NR + s] = p[(size_t)(rhs0 + s) * n + j];
+        s_g[threadIdx.x * NR + s] = g[(size_t)(rhs0 + s) * n + j];
+      }
+    }
+    __syncthreads();
+    if (!ok) continue;
+    for (int t = 0; t < cnt; ++t) {
+      const float4 ch = s_hi[t], cl = s_lo[t], nj = s_n[t];
+      const float dc = fmaf(d0, ch.x, fmaf(d1, ch.y, d2 * ch.z)) + fmaf(d0, cl.x, fmaf(d1, cl.y, d2 * cl.z));
+      const float kdn = k * fmaf(d0, nj.x, fmaf(d1, nj.y, d2 * nj.z));
+      float Er = 0.f, Ei = 0.f;  // sum_q (w A / 4pi) e^{-ik d.y}
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const float4 o = s_q[NQ * t + q];
+        const float ph = -k * (dc + fmaf(d0, o.x, fmaf(d1, o.y, d2 * o.z)));
+        const float nq = rintf(ph * kInvTwoPi);
+        float th = fmaf(-nq, kTwoPiHi, ph);
+        th = fmaf(-nq, kTwoPiLo, th);
+        float sn, cs;
+        __sincosf(th, &sn, &cs);
+        Er = fmaf(o.w, cs, Er);
+        Ei = fmaf(o.w, sn, Ei);
+      }
+#pragma unroll
+      for (int s = 0; s < NR; ++s) {
+        const float2 pj = s_p[t * NR + s], gj = s_g[t * NR + s];
+        // a = p (-i k d.n) - g
+        const float ar = fmaf(kdn, pj.y, -gj.x), ai = fmaf(-kdn, pj.x, -gj.y);
+        accr[s] += ar * Er - ai * Ei;
+        acci[s] += ar * Ei + ai * Er;
+      }
+    }
+  }
+  if (ok) {
+#pragma unroll
+    for (int s = 0; s < NR; ++s)
+      part[((size_t)blockIdx.y * nd + qi) * kMaxRhsPass + s] = make_double2(accr[s], acci[s]);
+  }
+}
+
+// Training-sample coordinates (paper Sec. 3.4): theta = pi u0, phi = 2 pi u1,
+// r = r_lo + (r_hi - r_lo) u2 about the centre; writes (theta, phi, r) and the Cartesian point.
+__global__ void k_sample_points(const double* __restrict__ u, int64_t n, double cx, double cy, double cz,
+                                double r_lo, double r_hi, double* __restrict__ coords,
+                                double* __restrict__ pts) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double th = 3.14159265358979323846 * u[3 * i];
+  const double ph = 6.28318530717958647692 * u[3 * i + 1];
+  const double r = r_lo + (r_hi - r_lo) * u[3 * i + 2];
+  double st, ct, sp, cp;
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  coords[3 * i] = th;
+  coords[3 * i + 1] = ph;
+  coords[3 * i + 2] = r;
+  pts[3 * i] = cx + r * st * cp;
+  pts[3 * i + 1] = cy + r * st * sp;
+  pts[3 * i + 2] = cz + r * ct;
+}
+
+// |p| of complex64 values
+__global__ void k_abs(const float2* __restrict__ v, int64_t count, float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) out[i] = hypotf(v[i].x, v[i].y);
+}
+
 // out[q, rhs0 + s] = sum over splits of the partials, complex64, column-major (m x nrhs)
 __global__ void k_eval_reduce(const double2* __restrict__ part, int m, int splits, int nr,
                               int rhs0, float2* __restrict__ out) {
@@ -176,6 +280,79 @@ nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
   dev_free(part, s);
   return NAT_BEM_OK;
 }
+
+template <int NQ>
+static void far_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, int n,
+                          const double* d_dirs, int nd, float k, const float2* d_p,
+                          const float2* d_g, int r0, int per, double2* part) {
+  switch (nr) {
+    case 1: k_far_field<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
+    case 2: k_far_field<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
+    case 3: k_far_field<3, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
+    default: k_far_field<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
+  }
+}
+
+nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_t nd,
+                              const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                              cudaStream_t s) {
+  if (nd == 0) return NAT_BEM_OK;
+  const int n = (int)op->n;
+  const int pblocks = (int)((nd + kEvalThreads - 1) / kEvalThreads);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int splits = (4 * sms + pblocks - 1) / pblocks;
+  splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
+  int per = (n + splits - 1) / splits;
+  per = (per + kElemStage - 1) / kElemStage * kElemStage;
+  splits = (n + per - 1) / per;
+  double2* part = nullptr;
+  NB_TRY(dev_alloc_n(&part, (size_t)splits * nd * kMaxRhsPass, s));
+  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
+    const int nr = min(kMaxRhsPass, nrhs - r0);
+    dim3 grid(pblocks, splits);
+    if (op->mc)
+      NB_LAUNCH("far_field", s, far_launch_nq<1>(nr, grid, s, op->geo, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
+    else
+      NB_LAUNCH("far_field", s, far_launch_nq<7>(nr, grid, s, op->geo, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
+    NB_CHECK_LAUNCH();
+    const int64_t tot = nd * nr;
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)nd, splits, nr, r0, d_out));
+    NB_CHECK_LAUNCH();
+  }
+  dev_free(part, s);
+  return NAT_BEM_OK;
+}
+
+nat_bem_status sample_field_impl(const nat_bem_op* op, const double* d_u, int64_t n, const double* center,
+                                 double r_lo, double r_hi, const float2* d_p, const float2* d_g, int nrhs,
+                                 double* d_coords, float* d_amp, cudaStream_t s) {
+  if (n == 0) return NAT_BEM_OK;
+  double* pts = nullptr;
+  float2* field = nullptr;
+  NB_TRY(dev_alloc_n(&pts, (size_t)(3 * n), s));
+  nat_bem_status st = dev_alloc_n(&field, (size_t)n * nrhs, s);
+  if (st != NAT_BEM_OK) {
+    dev_free(pts, s);
+    return st;
+  }
+  NB_LAUNCH("sample_points", s, k_sample_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      d_u, n, center[0], center[1], center[2], r_lo, r_hi, d_coords, pts));
+  st = eval_impl(op, pts, n, d_p, d_g, nrhs, field, s);
+  if (st == NAT_BEM_OK) {
+    const int64_t tot = n * nrhs;
+    NB_LAUNCH("sample_abs", s, k_abs<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(field, tot, d_amp));
+    if (cudaGetLastError() != cudaSuccess) {
+      set_error("sample_field: launch failed");
+      st = NAT_BEM_ECUDA;
+    }
+  }
+  dev_free(pts, s);
+  dev_free(field, s);
+  return st;
+}
+
 
 // ------------------------------------------------------------- allocation-free variant
 // Field evaluation for callers that must not allocate device memory: code running where

@@ -86,7 +86,7 @@ struct Geometry {
   float4* c_hi = nullptr;     // centroid, high part (x, y, z, 0)
   float4* c_lo = nullptr;     // centroid, low part: c = hi + lo to ~2^-48 relative
   float4* nrm = nullptr;      // unit outward normal (x, y, z, 0)
-  float4* qp = nullptr;       // 7 per element: (y_q - c, w_q A / (4 pi))
+  float4* qp = nullptr;       // 7 per element: (y_q - c, w_q A / (4 pi)); 1 per Monte-Carlo sample
   int4* vid = nullptr;        // vertex indices (a, b, c, 0)
   // FP64 records
   double* tri = nullptr;      // 9 per element: vertices a, b, c
@@ -160,6 +160,12 @@ size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms);
 nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
                          const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
                          cudaStream_t s);
+nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_t nd,
+                              const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                              cudaStream_t s);
+nat_bem_status sample_field_impl(const nat_bem_op* op, const double* d_u, int64_t n, const double* center,
+                                 double r_lo, double r_hi, const float2* d_p, const float2* d_g, int nrhs,
+                                 double* d_coords, float* d_amp, cudaStream_t s);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 

@@ -126,6 +126,9 @@ def test_solve_and_eval_reject_null(nb):
     assert L.nat_bem_eval(None, None, 4, None, None, 1, None, None) == nb.NAT_BEM_EINVAL
     assert L.nat_bem_op_rows(None, 0, 0, 1, None, None) == nb.NAT_BEM_EINVAL
     assert L.nat_bem_op_size(None) == 0
+    assert L.nat_bem_far_field(None, None, 4, None, None, 1, None, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_sample_field(None, None, 4, None, 1.0, 2.0, None, None, 1, None, None,
+                                  None) == nb.NAT_BEM_EINVAL
     L.nat_bem_destroy(None)
 
 
