@@ -23,7 +23,8 @@ constexpr float kTwoPiLo = -1.7484555314695172e-7f;
 constexpr float kInvTwoPi = 0.159154943091895336f;
 constexpr int kEvalThreads = 128;  // field points per block
 constexpr int kElemStage = 32;     // elements staged per shared-memory round
-constexpr int kMaxRhsPass = 4;     // right-hand sides accumulated per pass
+constexpr int kMaxRhsPass = 16;    // right-hand sides accumulated per pass (kernel values reused)
+constexpr int kNoAllocRhsPass = 4; // the allocation-free path: passes of four (scratch sizing)
 }  // namespace
 
 template <int NR, int NQ>
@@ -31,7 +32,7 @@ __global__ void __launch_bounds__(kEvalThreads)
 k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
        const float4* __restrict__ nrm, const float4* __restrict__ qp, int n,
        const double* __restrict__ pts, int m, float k, const float2* __restrict__ p,
-       const float2* __restrict__ g, int rhs0, int elems_per_split, double2* __restrict__ part) {
+       const float2* __restrict__ g, int rhs0, int nr, int elems_per_split, double2* __restrict__ part) {
   __shared__ float4 s_hi[kElemStage], s_lo[kElemStage], s_n[kElemStage];
   __shared__ float4 s_q[kElemStage * NQ];
   __shared__ float2 s_p[kElemStage * NR], s_g[kElemStage * NR];
@@ -59,9 +60,9 @@ k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
       s_lo[threadIdx.x] = c_lo[j];
       s_n[threadIdx.x] = nrm[j];
 #pragma unroll
-      for (int s = 0; s < NR; ++s) {
-        s_p[threadIdx.x * NR + s] = p[(size_t)(rhs0 + s) * n + j];
-        s_g[threadIdx.x * NR + s] = g[(size_t)(rhs0 + s) * n + j];
+      for (int s = 0; s < NR; ++s) {  // right-hand sides past nr read as zero
+        s_p[threadIdx.x * NR + s] = s < nr ? p[(size_t)(rhs0 + s) * n + j] : make_float2(0.f, 0.f);
+        s_g[threadIdx.x * NR + s] = s < nr ? g[(size_t)(rhs0 + s) * n + j] : make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
@@ -105,7 +106,7 @@ k_eval(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
   if (ok) {
 #pragma unroll
     for (int s = 0; s < NR; ++s)
-      part[((size_t)blockIdx.y * m + qi) * kMaxRhsPass + s] = make_double2(accr[s], acci[s]);
+      part[((size_t)blockIdx.y * m + qi) * NR + s] = make_double2(accr[s], acci[s]);
   }
 }
 
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(kEvalThreads)
 k_far_field(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
             const float4* __restrict__ nrm, const float4* __restrict__ qp, int n,
             const double* __restrict__ dirs, int nd, float k, const float2* __restrict__ p,
-            const float2* __restrict__ g, int rhs0, int elems_per_split, double2* __restrict__ part) {
+            const float2* __restrict__ g, int rhs0, int nr, int elems_per_split, double2* __restrict__ part) {
   __shared__ float4 s_hi[kElemStage], s_lo[kElemStage], s_n[kElemStage];
   __shared__ float4 s_q[kElemStage * NQ];
   __shared__ float2 s_p[kElemStage * NR], s_g[kElemStage * NR];
@@ -145,9 +146,9 @@ k_far_field(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
       s_lo[threadIdx.x] = c_lo[j];
       s_n[threadIdx.x] = nrm[j];
 #pragma unroll
-      for (int s = 0; s < NR; ++s) {
-        s_p[threadIdx.x * NR + s] = p[(size_t)(rhs0 + s) * n + j];
-        s_g[threadIdx.x * NR + s] = g[(size_t)(rhs0 + s) * n + j];
+      for (int s = 0; s < NR; ++s) {  // right-hand sides past nr read as zero
+        s_p[threadIdx.x * NR + s] = s < nr ? p[(size_t)(rhs0 + s) * n + j] : make_float2(0.f, 0.f);
+        s_g[threadIdx.x * NR + s] = s < nr ? g[(size_t)(rhs0 + s) * n + j] : make_float2(0.f, 0.f);
       }
     }
     __syncthreads();
@@ -182,7 +183,7 @@ k_far_field(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo,
   if (ok) {
 #pragma unroll
     for (int s = 0; s < NR; ++s)
-      part[((size_t)blockIdx.y * nd + qi) * kMaxRhsPass + s] = make_double2(accr[s], acci[s]);
+      part[((size_t)blockIdx.y * nd + qi) * NR + s] = make_double2(accr[s], acci[s]);
   }
 }
 
@@ -214,31 +215,37 @@ __global__ void k_abs(const float2* __restrict__ v, int64_t count, float* __rest
 }
 
 // out[q, rhs0 + s] = sum over splits of the partials, complex64, column-major (m x nrhs)
-__global__ void k_eval_reduce(const double2* __restrict__ part, int m, int splits, int nr,
+__global__ void k_eval_reduce(const double2* __restrict__ part, int m, int splits, int nr, int stride,
                               int rhs0, float2* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)m * nr) return;
   const int qi = (int)(i / nr), s = (int)(i % nr);
   double re = 0.0, im = 0.0;
   for (int t = 0; t < splits; ++t) {
-    const double2 v = part[((size_t)t * m + qi) * kMaxRhsPass + s];
+    const double2 v = part[((size_t)t * m + qi) * stride + s];
     re += v.x;
     im += v.y;
   }
   out[(size_t)(rhs0 + s) * m + qi] = make_float2((float)re, (float)im);
 }
 
+// Pass width for nr right-hand sides: the smallest of 1, 2, 4, 8, 16 that holds them. Each
+// (point, element) kernel value is computed once per pass and applied to every RHS of it.
+static int pass_width(int nr) { return nr <= 1 ? 1 : nr <= 2 ? 2 : nr <= 4 ? 4 : nr <= 8 ? 8 : 16; }
+
 // One k_eval launch for nr right-hand sides: seven quadrature points per element, or one
-// sample point per Monte-Carlo sample (weight w / (4 pi) at offset 0).
+// sample point per Monte-Carlo sample (weight w / (4 pi) at offset 0). Partials are strided by
+// pass_width(nr).
 template <int NQ>
 static void eval_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, int n,
                            const double* d_pts, int m, float k, const float2* d_p,
                            const float2* d_g, int r0, int per, double2* part) {
-  switch (nr) {
-    case 1: k_eval<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
-    case 2: k_eval<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
-    case 3: k_eval<3, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
-    default: k_eval<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, per, part); break;
+  switch (pass_width(nr)) {
+    case 1: k_eval<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    case 2: k_eval<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    case 4: k_eval<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    case 8: k_eval<8, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    default: k_eval<16, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
   }
 }
 
@@ -267,14 +274,14 @@ nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
   per = (per + kElemStage - 1) / kElemStage * kElemStage;
   splits = (n + per - 1) / per;
   double2* part = nullptr;
-  NB_TRY(dev_alloc_n(&part, (size_t)splits * m * kMaxRhsPass, s));
+  NB_TRY(dev_alloc_n(&part, (size_t)splits * m * pass_width(min(kMaxRhsPass, nrhs)), s));
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
     NB_LAUNCH("eval", s, eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
-    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out));
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
   }
   dev_free(part, s);
@@ -285,11 +292,12 @@ template <int NQ>
 static void far_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, int n,
                           const double* d_dirs, int nd, float k, const float2* d_p,
                           const float2* d_g, int r0, int per, double2* part) {
-  switch (nr) {
-    case 1: k_far_field<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
-    case 2: k_far_field<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
-    case 3: k_far_field<3, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
-    default: k_far_field<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, per, part); break;
+  switch (pass_width(nr)) {
+    case 1: k_far_field<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, nr, per, part); break;
+    case 2: k_far_field<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, nr, per, part); break;
+    case 4: k_far_field<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, nr, per, part); break;
+    case 8: k_far_field<8, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, nr, per, part); break;
+    default: k_far_field<16, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_dirs, nd, k, d_p, d_g, r0, nr, per, part); break;
   }
 }
 
@@ -308,7 +316,7 @@ nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_
   per = (per + kElemStage - 1) / kElemStage * kElemStage;
   splits = (n + per - 1) / per;
   double2* part = nullptr;
-  NB_TRY(dev_alloc_n(&part, (size_t)splits * nd * kMaxRhsPass, s));
+  NB_TRY(dev_alloc_n(&part, (size_t)splits * nd * pass_width(min(kMaxRhsPass, nrhs)), s));
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
@@ -318,7 +326,7 @@ nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_
       NB_LAUNCH("far_field", s, far_launch_nq<7>(nr, grid, s, op->geo, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = nd * nr;
-    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)nd, splits, nr, r0, d_out));
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)nd, splits, nr, pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
   }
   dev_free(part, s);
@@ -362,7 +370,7 @@ nat_bem_status sample_field_impl(const nat_bem_op* op, const double* d_u, int64_
 // array, which every GPU that loads the library holds until the process exits.
 constexpr size_t kNoAllocScratch = (size_t)1 << 18;  // double2 entries: 4 MiB
 static __device__ __align__(256) double2 g_eval_scratch[kNoAllocScratch];
-constexpr int64_t kNoAllocMaxPoints = (int64_t)(kNoAllocScratch / kMaxRhsPass);  // 65,536
+constexpr int64_t kNoAllocMaxPoints = (int64_t)(kNoAllocScratch / kNoAllocRhsPass);  // 65,536
 
 namespace {
 std::mutex g_scratch_mu;
@@ -406,18 +414,18 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
   // as many element splits as eval_impl would take, capped by the scratch size
   int splits = (4 * sms + pblocks - 1) / pblocks;
   splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
-  const int cap = (int)(kNoAllocScratch / ((size_t)m * kMaxRhsPass));
+  const int cap = (int)(kNoAllocScratch / ((size_t)m * kNoAllocRhsPass));
   splits = max(1, min(splits, cap));
   int per = (n + splits - 1) / splits;
   per = (per + kElemStage - 1) / kElemStage * kElemStage;
   splits = (n + per - 1) / per;
-  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
-    const int nr = min(kMaxRhsPass, nrhs - r0);
+  for (int r0 = 0; r0 < nrhs; r0 += kNoAllocRhsPass) {
+    const int nr = min(kNoAllocRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
     eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part);
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
-    k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, r0, d_out);
+    k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out);
     NB_CHECK_LAUNCH();
   }
   return NAT_BEM_OK;

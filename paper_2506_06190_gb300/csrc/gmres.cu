@@ -51,6 +51,7 @@ struct Workspace {
   int coop_blocks = 0;                                     // 0: fused kernel not usable
   double2 *pblk = nullptr, *hred = nullptr;                // fused kernel: block partials, totals
   int arn_smem = 0;                                        // fused kernel: dynamic shared bytes
+  double2* pbu = nullptr;                                  // multi-RHS fused kernel: unit partials
   // captured iteration chunks: key (engine, first iteration, count, cap, tol, refinement mode)
   std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
@@ -846,6 +847,14 @@ constexpr int kArnMaxRows = 512;           // rows per block (n <= 151 * 512 wit
 // matvec blocks share an SM (75 solves/s).
 constexpr int kArnPanelBytes = 96 * 1024;
 constexpr int kArnMaxRhs = 256;
+constexpr int kArnUnitsMinRhs = 4;  // more right-hand sides than this: k_arnoldi_units
+
+// Rows per work unit of k_arnoldi_units: about four units per block, 64 <= unit <= n.
+inline int arnoldi_unit(int n, int nrhs, int blocks) {
+  int64_t u = ((int64_t)n * nrhs / (4 * (int64_t)blocks) + 31) / 32 * 32;
+  u = std::max<int64_t>(64, u);
+  return (int)std::min<int64_t>(u, n);
+}
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -1092,6 +1101,182 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
   }
 }
 
+// The same iteration for several right-hand sides, one cooperative launch. The work is dealt
+// in units of (RHS s, row range of `unit` rows): block b takes units b, b + G, ..., so every
+// block streams long coalesced row ranges of V with no per-RHS barrier, and the FP64 pipe stays
+// busy. Per unit and pass: (A) partial dots of its rows for c <= j and ||w||^2 (warp c % 8 per
+// column, lanes over rows, four accumulators), stored per (RHS, column, chunk); barrier; (R)
+// totals over the chunks of each RHS, one thread per (RHS, column), fixed order; barrier; (B)
+// every block takes the decisions for every RHS from the totals (so all blocks agree on the
+// barrier count), then updates its units' rows, and the owner of chunk 0 of an RHS applies
+// its Givens rotation. Same arithmetic and second-pass test as k_arnoldi.
+__global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restrict__ pbu, double2* __restrict__ hr,
+                                                       unsigned* __restrict__ bar, int* __restrict__ err,
+                                                       int unit, int cps) {
+  __shared__ double2 s_h[256];
+  __shared__ double2 s_acc[256];
+  __shared__ double2 s_sn[256];
+  __shared__ double s_cs[256];
+  __shared__ unsigned char s_act[kArnMaxRhs];
+  __shared__ double s_hn[kArnMaxRhs], s_inv[kArnMaxRhs];
+  if (a.scal[1]) return;
+  const int j = a.scal[0];
+  const int G = (int)gridDim.x, b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int np = j + 2;
+  const size_t ps = (size_t)(a.m + 2);
+  const int nunits = a.nrhs * cps;
+  for (int q = threadIdx.x; q < a.nrhs; q += blockDim.x) s_act[q] = a.done[q] ? 0 : 1;
+  __syncthreads();
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const unsigned char want = pass == 0 ? 1 : 2;
+    bool any = false;
+    for (int q = 0; q < a.nrhs; ++q) any |= (s_act[q] >= want);
+    if (!any) break;
+    // (A) partial sums over each unit's rows
+    for (int u = b; u < nunits; u += G) {
+      const int s = u / cps, chunk = u % cps;
+      if (s_act[s] < want) continue;
+      const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
+      const double2* w = a.w + (size_t)s * a.n;
+      for (int c = warp; c < np; c += 8) {
+        double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
+        if (c <= j) {
+          const double2* v = a.V + vidx(a, c, s);
+          for (int r = q0 + lane; r < q1; r += 128) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int rr = r + 32 * t;
+              if (rr < q1) {
+                const double2 vv = v[rr], ww = w[rr];
+                re[t] = fma(vv.x, ww.x, re[t]);
+                re[t] = fma(vv.y, ww.y, re[t]);
+                im[t] = fma(vv.x, ww.y, im[t]);
+                im[t] = fma(-vv.y, ww.x, im[t]);
+              }
+            }
+          }
+        } else {
+          for (int r = q0 + lane; r < q1; r += 128) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const int rr = r + 32 * t;
+              if (rr < q1) {
+                const double2 ww = w[rr];
+                re[t] = fma(ww.x, ww.x, re[t]);
+                re[t] = fma(ww.y, ww.y, re[t]);
+              }
+            }
+          }
+        }
+        double sr = (re[0] + re[1]) + (re[2] + re[3]), si = (im[0] + im[1]) + (im[2] + im[3]);
+        sr = warp_sum(sr);
+        si = warp_sum(si);
+        if (lane == 0) pbu[((size_t)s * ps + c) * cps + chunk] = make_double2(sr, si);
+      }
+    }
+    grid_sync(bar, bar + 1, G, err);
+    // (R) totals over the chunks, one thread per (RHS, column)
+    for (int it = b * blockDim.x + threadIdx.x; it < a.nrhs * np; it += G * blockDim.x) {
+      const int s = it / np, c = it % np;
+      if (s_act[s] < want) continue;
+      const double2* src = pbu + ((size_t)s * ps + c) * cps;
+      double re = 0.0, im = 0.0;
+      for (int q = 0; q < cps; ++q) {
+        re += src[q].x;
+        im += src[q].y;
+      }
+      hr[(size_t)s * ps + c] = make_double2(re, im);
+    }
+    grid_sync(bar, bar + 1, G, err);
+    // (B) decisions for every RHS (identical in every block)
+    for (int s = warp; s < a.nrhs; s += 8) {
+      if (s_act[s] < want) continue;
+      const double2* hs = hr + (size_t)s * ps;
+      double t = 0.0;
+      for (int c = lane; c <= j; c += 32) t += cabs2(hs[c]);
+      t = warp_sum(t);
+      if (lane == 0) {
+        const double wn2 = hs[j + 1].x;
+        const double hn2 = fmax(wn2 - t, 0.0);
+        const bool again = pass == 0 && !(hn2 > 1e-4 * wn2);
+        const double inv = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
+        s_hn[s] = again ? -1.0 : hn2 * inv;
+        s_inv[s] = inv;
+      }
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x)
+      if (s_act[s] >= want && s_hn[s] < 0.0) s_act[s] = 2;
+    __syncthreads();
+    // (B) row updates of each unit, v_{j+1}; chunk 0's owner: Hessenberg column and Givens
+    for (int u = b; u < nunits; u += G) {
+      const int s = u / cps, chunk = u % cps;
+      if (s_act[s] < want) continue;
+      const double hn = s_hn[s], inv = s_inv[s];
+      const bool last = hn >= 0.0;
+      const double2* hs = hr + (size_t)s * ps;
+      __syncthreads();
+      for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = hs[c];
+      __syncthreads();
+      const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
+      for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
+        double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                          make_double2(0.0, 0.0)};
+        int c = 0;
+        for (; c + 4 <= j + 1; c += 4) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const double2 vv = a.V[vidx(a, c + t, s) + r], h = s_h[c + t];
+            acc[t].x = fma(vv.x, h.x, acc[t].x);
+            acc[t].x = fma(-vv.y, h.y, acc[t].x);
+            acc[t].y = fma(vv.x, h.y, acc[t].y);
+            acc[t].y = fma(vv.y, h.x, acc[t].y);
+          }
+        }
+        for (; c <= j; ++c) {
+          const double2 vv = a.V[vidx(a, c, s) + r], h = s_h[c];
+          acc[0].x = fma(vv.x, h.x, acc[0].x);
+          acc[0].x = fma(-vv.y, h.y, acc[0].x);
+          acc[0].y = fma(vv.x, h.y, acc[0].y);
+          acc[0].y = fma(vv.y, h.x, acc[0].y);
+        }
+        const double2 tsum = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
+        const double2 wv = csub(a.w[(size_t)s * a.n + r], tsum);
+        if (!last) {
+          a.w[(size_t)s * a.n + r] = wv;
+        } else if (hn > 0.0) {
+          const double2 v = make_double2(wv.x * inv, wv.y * inv);
+          a.V[vidx(a, j + 1, s) + r] = v;
+          a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+        }
+      }
+      if (chunk == 0) {
+        const size_t ho = (size_t)s * (a.m + 1);
+        for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+          const double2 t = pass == 0 ? s_h[c] : cadd(a.hcol[ho + c], s_h[c]);
+          if (!last) a.hcol[ho + c] = t;
+          s_acc[c] = t;
+          if (c < j) {
+            s_cs[c] = a.cs[(size_t)s * a.m + c];
+            s_sn[c] = a.sn[(size_t)s * a.m + c];
+          }
+        }
+        __syncthreads();
+        if (last && warp == 0) givens_warp(a, s, j, hn, s_acc, s_cs, s_sn, lane);
+      }
+    }
+  }
+  grid_sync(bar, bar + 1, G, err);  // every Givens update before the flags are read
+  if (b == 0 && threadIdx.x == 0) {
+    int all = 1;
+    for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
+    a.scal[0] = j + 1;
+    a.scal[1] = all || j + 1 >= a.maxit;
+  }
+}
+
 // Back substitution R y = g on the rotated Hessenberg matrix, one 256-thread block per RHS,
 // column by column: thread k holds g_k and 1/R_kk (all reciprocals formed in parallel first);
 // step i sets y_i = g_i / R_ii and every k < i subtracts R_ki y_i. The columns of R are staged
@@ -1222,6 +1407,7 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
   b += 8 * nchunk * nrhs;                                            // partial norms
   b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
+  if (nrhs > kArnUnitsMinRhs) b += 16 * (m + 2) * (4 * 256 + nrhs);  // multi-RHS unit partials
   return b;
 }
 
@@ -1231,7 +1417,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
                   ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar,
-                  ws->pblk, ws->hred};
+                  ws->pblk, ws->hred, ws->pbu};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -1316,6 +1502,14 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
     if (ws->coop_blocks > 0) {
       NB_TRY(dev_alloc_n(&ws->pblk, nr * (mm + 2) * (size_t)ws->coop_blocks, s));
       NB_TRY(dev_alloc_n(&ws->hred, nr * (mm + 2), s));
+      if (nrhs > kArnUnitsMinRhs) {  // the multi-RHS kernel: partials for the largest unit count
+        size_t most = 0;
+        for (int q = kArnUnitsMinRhs + 1; q <= nrhs; ++q) {
+          const int u = arnoldi_unit((int)n, q, ws->coop_blocks);
+          most = std::max(most, (size_t)q * (size_t)((n + u - 1) / u));
+        }
+        NB_TRY(dev_alloc_n(&ws->pbu, most * (mm + 2), s));
+      }
     }
   }
   NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));
@@ -1580,6 +1774,14 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
         double2* hr = ws->hred;
         unsigned* bar = ws->gbar;
         int* errp = ws->tc_err;
+        if (nrhs > kArnUnitsMinRhs && ws->pbu) {
+          double2* pu = ws->pbu;
+          int unit = arnoldi_unit(n, nrhs, ws->coop_blocks);
+          int cps = (n + unit - 1) / unit;
+          void* args[] = {&ac, &pu, &hr, &bar, &errp, &unit, &cps};
+          NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_units, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
+          continue;
+        }
         int pcap = ws->arn_smem / (int)sizeof(double2);
         void* args[] = {&ac, &pb, &hr, &bar, &errp, &pcap};
         NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(ws->coop_blocks), dim3(256), args, (size_t)ws->arn_smem, s)));
