@@ -240,13 +240,6 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
       nat_bem_destroy(op);
       return st;
     };
-    if (cudaStreamCreateWithFlags(&op->aux, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&op->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&op->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-      cudaGetLastError();
-      set_error("could not create the op's auxiliary stream");
-      return fail(NAT_BEM_ECUDA);
-    }
     const double* dV = nullptr;
     const int32_t* dT = nullptr;
     double* tV = nullptr;
@@ -650,12 +643,6 @@ void nat_bem_destroy(nat_bem_op* op) {
                   g.near_pairs, op->L, op->R, op->Lb};
   for (void* p : ptrs) dev_free(p, s);
   workspace_free(op->ws, s);
-  if (op->ev_join) {
-    // the auxiliary stream's last work is ordered before `s` through ev_join
-    cudaEventDestroy(op->ev_join);
-  }
-  if (op->ev_fork) cudaEventDestroy(op->ev_fork);
-  if (op->aux) cudaStreamDestroy(op->aux);
   delete op;
 }
 

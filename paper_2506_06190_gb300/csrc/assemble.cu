@@ -705,21 +705,18 @@ nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* d
 nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const Geometry& g = op->geo;
   const int n = (int)op->n, ld = (int)g.ld;
-  // The near pairs write exactly the entries the regular kernel skips, so the FP64 kernel runs
-  // beside it on the op's auxiliary stream (the FP64 and FP32 pipes overlap).
-  cudaStream_t aux = op->aux ? op->aux : s;
-  if (aux != s) {
-    NB_TRY_CUDA(cudaEventRecord(op->ev_fork, s));
-    NB_TRY_CUDA(cudaStreamWaitEvent(aux, op->ev_fork, 0));
-  }
+  // The near pairs write exactly the entries the regular kernel skips. The three kernels run in
+  // order on the solve's stream: beside the FP32 regular kernel on a second stream the FP64
+  // kernels saved ~0.3 ms per solve with one solve in flight and nothing with several, and
+  // they slowed the regular kernel they shared the SMs with.
   {
     const int64_t threads = 256;
     const int64_t adj_blocks = (g.n_near * 16 + threads - 1) / threads;
     if (adj_blocks > 0)
-      NB_LAUNCH("assemble_near", aux, k_assemble_adjacent<<<(unsigned)adj_blocks, (unsigned)threads, 0, aux>>>(
+      NB_LAUNCH("assemble_near", s, k_assemble_adjacent<<<(unsigned)adj_blocks, (unsigned)threads, 0, s>>>(
           g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
     const int64_t self_blocks = ((int64_t)n * 32 + threads - 1) / threads;
-    NB_LAUNCH("assemble_self", aux, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, aux>>>(
+    NB_LAUNCH("assemble_self", s, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, s>>>(
         n, g.tri, g.cen, ld, op->k, op->L, op->R, op->Lb));
     NB_CHECK_LAUNCH();
   }
@@ -736,10 +733,6 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
     NB_LAUNCH("assemble_regular", s, k_assemble_regular_x2<<<grid, kX2Threads, 0, s>>>(
         g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
   NB_CHECK_LAUNCH();
-  if (aux != s) {
-    NB_TRY_CUDA(cudaEventRecord(op->ev_join, aux));
-    NB_TRY_CUDA(cudaStreamWaitEvent(s, op->ev_join, 0));
-  }
   return NAT_BEM_OK;
 }
 

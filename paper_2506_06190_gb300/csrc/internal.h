@@ -117,8 +117,6 @@ struct nat_bem_op {
   nat_bem_opts opts{};
   int device = 0;
   cudaStream_t stream = nullptr;       // stream the op was built on (frees are ordered there)
-  cudaStream_t aux = nullptr;          // library-owned stream for work beside `stream`
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   natbem::Geometry geo;
   float2* L = nullptr;                 // n x ld complex64, row-major
   float2* R = nullptr;                 // n x ld complex64, row-major (store_r)
