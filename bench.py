@@ -50,35 +50,53 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every `interval_ms` during the timed
+    region. A reader thread timestamps each sample; the summary keeps those taken inside the
+    context (nvidia-smi takes a moment to start, so it is started `lead_s` before)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, interval_ms: int = 200, lead_s: float = 0.5):
         self.index = index
+        self.interval_ms = interval_ms
+        self.lead_s = lead_s
         self.proc = None
+        self.samples = []
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.samples.append((time.monotonic(), ln))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+            time.sleep(self.lead_s)
         except OSError:
             self.proc = None
+        self.t0 = time.monotonic()
         return self
 
     def __exit__(self, *exc):
+        self.t1 = time.monotonic()
         self.lines = []
         if self.proc:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+                self.proc.wait()
+            self.reader.join(timeout=5)
+            inside = [ln for t, ln in self.samples if self.t0 <= t <= self.t1 + 0.05]
+            self.lines = inside
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -425,6 +443,115 @@ def run_dataset(args):
             "clocks": clk.summary()}
 
 
+def run_nat(args):
+    """Neural acoustic transfer field inference (paper Sec. 3.3, 3.4): --n-queries listening
+    points (theta/pi, phi/2pi, r_norm, v_1, v_2, f) uniform in [0, 1]^6 through the grid +
+    positional encoding and the 4 x 128 MLP to 8 outputs (e.g. 8 modes), one fused tensor-core
+    kernel per call. Random BF16 weights and hash tables of 2^18 rows (the trained model is not
+    available). Reports queries/s; the roofline counts the MLP's algorithmic FLOPs (first layer
+    52 wide, no padding) against the measured BF16 peak."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    from oracle import nat as O  # parameter generator and, for the CPU leg, the reference
+    nb_build.build()
+    n = args.n_queries
+    m = O.random_model(n_cond=2, n_out=8, table_log2=18, seed=0)
+    tables = np.concatenate(m["tables"], axis=0).astype(np.float32)
+    w = np.concatenate([O.bf16_bits(W).ravel() for W in m["weights"]])
+    b = np.concatenate(m["biases"]).astype(np.float32)
+    dev = torch.device("cuda", 0)
+    x = np.random.default_rng(11).random((n, 6)).astype(np.float32)
+    xd = torch.from_numpy(x).to(dev)
+    out = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    f = nb.NatField(2, 8, 18, tables, w, b)
+    batches = 64  # one step: 64 calls of n queries
+
+    def step():
+        for _ in range(batches):
+            f.forward(xd, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    nb.nat_bem_trace_enable(True)
+    nb.nat_bem_trace_select("nat_forward")
+    nb.nat_bem_trace_reset()
+    launches0 = nb.nat_bem_trace_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0, interval_ms=50) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            step()
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    k_ms, k_launches = nb.nat_bem_trace_kernel("nat_forward")
+    launches = nb.nat_bem_trace_launches() - launches0
+    nb.nat_bem_trace_enable(False)
+    # end to end: host inputs in, host outputs back, every step
+    xh = torch.from_numpy(x).pin_memory()
+    oh = torch.empty((n, 8), dtype=torch.float32).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps * batches):
+        xd.copy_(xh, non_blocking=True)
+        f.forward(xd, out)
+        oh.copy_(out, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    width0 = 16 + 12 * 3  # grid features + P(v_1, v_2) + P(f)
+    flops_q = 2 * (width0 * 128 + 3 * 128 * 128 + 128 * 8)  # the MLP's multiply-adds, unpadded
+    kernel_ms = k_ms / max(k_launches, 1)
+    peaks, peak_kind = _peaks()
+    achieved = flops_q * n / (kernel_ms * 1e-3) / 1e12
+    line = {"metric": "NAT field queries/s (grid + PE encoding, 4 x 128 MLP, 8 outputs)",
+            "value": args.steps * batches * n / (ms * 1e-3), "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (FP32 accumulation)", "data": "synthetic (random weights and tables)",
+            "config": {"workload": f"nat_inference_{n}queries", "queries": n, "calls_per_step": batches,
+                       "inputs": 6, "outputs": 8,
+                       "table_log2": 18, "levels": [8, 16, 32, 64], "width": 128, "hidden_layers": 4,
+                       "l2": "inputs + outputs 235 MB per step, larger than L2"},
+            "e2e": {"value": args.steps * batches * n / (e2e_ms * 1e-3), "unit": "queries/s",
+                    "h2d_bytes_per_step": int(batches * x.nbytes), "d2h_bytes_per_step": int(batches * n * 8 * 4)},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "nat_forward", "bound": "tensor", "achieved": achieved,
+                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": achieved / peaks["bf16_tflops"],
+                         "traffic": NCU_TRAFFIC_NAT_PER_MQUERY * n / (1 << 20),
+                         "flops_per_query": flops_q, "peak_source": f"{peak_kind} (bf16_tflops)"},
+            "clocks": clk.summary()}
+    if args.cpu:
+        ns = 1 << 16
+        xs = x[:ns].astype(np.float64)
+        t = time.perf_counter()
+        ref = O.forward(xs, m["tables"], m["weights"], m["biases"], 18)
+        dt = time.perf_counter() - t
+        got = out[:ns].cpu().numpy().astype(np.float64)
+        line["cpu_baseline"] = {"value": ns / dt, "unit": "queries/s", "cores": _numpy_threads(),
+                                "kind": "oracle", "sample": f"first {ns} queries"}
+        line["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    f.close()
+    return line
+
+
+def _numpy_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# DRAM bytes (read + write) of one k_nat_forward launch per 2^20 queries, from the committed ncu
+# capture (profiles/k_nat_forward_nat_inference_1Mqueries.md); traffic grows with the queries.
+NCU_TRAFFIC_NAT_PER_MQUERY = 29.014016e6 + 25.856e6
+
+
 def run_uneven(args):
     """Uneven batch: --n-mesh perturbed ring spheres of 500-8000 triangles (log-uniform), one
     wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4, through the
@@ -606,9 +733,10 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
-    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset"])
+    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset", "nat"])
     ap.add_argument("--n-samples", type=int, default=4096, help="Monte-Carlo workload: surface samples")
     ap.add_argument("--random-samples", action="store_true", help="Monte-Carlo workload: uniform random samples")
+    ap.add_argument("--n-queries", type=int, default=1 << 22, help="NAT inference workload: queries per step")
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--n-mesh", type=int, default=512)
     ap.add_argument("--n-req", type=int, default=300)
@@ -652,7 +780,7 @@ def main():
     if args.workload != "interior":
         if rank == 0:
             fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc,
-                  "dataset": run_dataset}[args.workload]
+                  "dataset": run_dataset, "nat": run_nat}[args.workload]
             if args.workload == "modal" and args.n_k == 64:
                 args.n_k = 16
             if args.workload == "modal" and args.n_tri == 10240:

@@ -273,6 +273,12 @@ NAT_BEM_API nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which,
                                             const float* X, int32_t nrhs, float* Y,
                                             void* cuda_stream);
 
+/* The GEMV variant (0 <= v < NAT_BEM_GEMV_VARIANTS) the solver's autotuner chose on the current
+ * device for operators of nt elements (sizes are grouped by nt rounded up to 1024), or -1 if
+ * no solve of that size has run yet. The tuner times every variant on the operator itself the
+ * first time a size is met; NATBEM_GEMV_VARIANT=v in the environment bypasses it. */
+NAT_BEM_API int32_t nat_bem_gemv_variant(int64_t nt);
+
 /*
  * Serving (no counterpart in the paper; it serves the data-generation loop of Sec. 3.4). A
  * server runs `slots` workers, each with its own stream. Requests (nat_bem_job, as for the
@@ -346,6 +352,44 @@ NAT_BEM_API void nat_bem_trace_reset(void);
 NAT_BEM_API int64_t nat_bem_trace_launches(void);
 NAT_BEM_API nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms,
                                                 int64_t* launches);
+
+/*
+ * Neural acoustic transfer field (Sec. 3.3, Eq. 3 and 4; Sec. 3.4): the learned map from the
+ * spherical coordinates of a listening point, the condition variables and the frequency to the
+ * outputs (one per mode, or one pressure amplitude). One forward pass per query:
+ *   inputs  x = (theta/pi, phi/(2 pi), r_norm, v_1..v_c, f), D = 4 + n_cond values in [0, 1];
+ *   grid    4 levels of 8, 16, 32, 64 cells per axis over (x_0, x_1, x_2), 4 features per
+ *           vertex, trilinear interpolation; a level with (N + 1)^3 <= 2^table_log2 vertices is
+ *           dense (row i + (N + 1)(j + (N + 1) k)), a finer one hashed: row
+ *           (i xor j * 2654435761 xor k * 805459861) mod 2^table_log2 (32-bit arithmetic);
+ *   PE      sin and cos of 2^l pi x_d, l = 0..5, for d = 3..D-1 (v, then f), ordered (d, l,
+ *           sin/cos);
+ *   MLP     [16 grid features, PE, zeros] (128 wide) -> 4 x (128, ReLU) -> n_out, linear.
+ * The layers run on the tensor cores with BF16 weights and BF16 layer inputs (each layer's
+ * input is rounded to nearest-even BF16) and FP32 accumulation, bias and output.
+ *
+ * nat_field_create copies the parameters to the device of the current context (host or device
+ * pointers; the caller keeps ownership of its arrays):
+ *   tables  float32, the four levels' rows one level after the other, 4 features per row;
+ *           level l has min((N_l + 1)^3, 2^table_log2) rows;
+ *   weights BF16 bit patterns (uint16), row-major [out][in]: four 128 x 128 hidden layers, then
+ *           the n_out x 128 output layer;
+ *   biases  float32: 4 x 128, then n_out.
+ *   NAT_BEM_EINVAL: NULL argument, n_cond not in 0..8, n_out not in 1..128, table_log2 not in
+ *   12..24. NAT_BEM_ENOMEM / NAT_BEM_ECUDA: device allocation or copy failed.
+ * nat_field_forward: x n x D float32 row-major, out n x n_out float32 row-major, host or device
+ *   pointers, on cuda_stream; blocks until out is written; n = 0 does nothing. NAT_BEM_EINVAL
+ *   for NULL or n < 0; NAT_BEM_ETIMEOUT if a bounded wait on the tensor cores gave up (the
+ *   output is then incomplete).
+ * nat_field_destroy frees the device copies (NULL is a no-op).
+ */
+typedef struct nat_field nat_field;
+NAT_BEM_API nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log2,
+                                            const float* tables, const uint16_t* weights,
+                                            const float* biases, void* cuda_stream, nat_field** out);
+NAT_BEM_API nat_bem_status nat_field_forward(const nat_field* f, const float* x, int64_t n,
+                                             float* out, void* cuda_stream);
+NAT_BEM_API void nat_field_destroy(nat_field* f);
 
 /* Message of the last failed call on this thread ("" if none). */
 NAT_BEM_API const char* nat_bem_last_error(void);

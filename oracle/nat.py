@@ -4,15 +4,17 @@
 TEST INFRASTRUCTURE ONLY, like the rest of oracle/: the tests, the smoke check and the bench's
 CPU leg use it; the product library never does. It shares no code with the CUDA path.
 
-The network, as this build reads the paper:
-  * inputs: x = (theta/pi, phi/(2 pi), (r - r_lo)/(r_hi - r_lo), f, v_1..v_c), each in [0, 1];
-  * positional encoding: sin(2^l pi x_d), cos(2^l pi x_d), l = 0..5, for every input d;
-  * multi-resolution grid over (x_0, x_1, x_2): 4 levels of N_l = 8, 16, 32, 64 cells per axis,
-    4 features per vertex, trilinear interpolation of the 8 surrounding vertices; a level with
-    (N_l + 1)^3 <= T vertices is stored densely, a finer one through the spatial hash of
+The network, as this build reads the paper (Sec. 3.3, Eq. 3 and 4; Sec. 3.4):
+  * inputs: x = (theta/pi, phi/(2 pi), (r - r_lo)/(r_hi - r_lo), v_1..v_c, f), each in [0, 1]:
+    the listener's spherical coordinates, then the condition variables and the frequency;
+  * multi-resolution grid G over (x_0, x_1, x_2): 4 levels of N_l = 8, 16, 32, 64 cells per
+    axis, 4 features per vertex, trilinear interpolation of the 8 surrounding vertices; a level
+    with (N_l + 1)^3 <= T vertices is stored densely, a finer one through the spatial hash of
     Mueller et al. (2022), (i * 1) xor (j * 2654435761) xor (k * 805459861) mod T;
-  * MLP: the 16 grid features and the positional encoding (zero-padded to 128) through four
-    128-wide layers with ReLU, then a linear layer to the outputs (Sec. 3.4).
+  * positional encoding P of the condition variables and the frequency only (x_3 onwards):
+    sin(2^l pi x_d), cos(2^l pi x_d), l = 0..5;
+  * MLP on [G, P(v), P(f)] (zero-padded to 128): four 128-wide layers with ReLU, then a linear
+    layer to the outputs (Sec. 3.4).
 The GPU kernel feeds the tensor cores BF16 activations and weights with FP32 accumulation; this
 reference takes the same BF16 weights and rounds every layer's input to BF16 the same way, and
 computes everything else in FP64.
@@ -86,8 +88,9 @@ def positional(x):
 
 
 def encode(x, tables, table_log2):
-    """The 128-wide MLP input: 16 grid features, the positional encoding, zeros."""
-    e = np.concatenate([grid_features(x[:, :3], tables, table_log2), positional(x)], axis=1)
+    """The 128-wide MLP input: 16 grid features of (x_0, x_1, x_2), the positional encoding of
+    x_3 onwards (v, then f), zeros."""
+    e = np.concatenate([grid_features(x[:, :3], tables, table_log2), positional(x[:, 3:])], axis=1)
     if e.shape[1] > WIDTH:
         raise ValueError("too many inputs for a 128-wide first layer")
     return np.pad(e, ((0, 0), (0, WIDTH - e.shape[1])))

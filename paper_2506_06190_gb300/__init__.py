@@ -36,7 +36,8 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_run_batch", "nat_bem_trace_select", "nat_bem_op_apply",
             "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
-            "nat_bem_far_field", "nat_bem_sample_field"]
+            "nat_bem_far_field", "nat_bem_sample_field", "nat_bem_gemv_variant", "nat_field_create",
+            "nat_field_forward", "nat_field_destroy"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -133,6 +134,14 @@ def lib():
         L.nat_bem_trace_launches.restype = i64
         L.nat_bem_trace_kernel.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.nat_bem_trace_kernel.restype = ctypes.c_int
+        L.nat_bem_gemv_variant.argtypes = [i64]
+        L.nat_bem_gemv_variant.restype = i32
+        L.nat_field_create.argtypes = [i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
+        L.nat_field_create.restype = ctypes.c_int
+        L.nat_field_forward.argtypes = [vp, vp, i64, vp, vp]
+        L.nat_field_forward.restype = ctypes.c_int
+        L.nat_field_destroy.argtypes = [vp]
+        L.nat_field_destroy.restype = None
         _lib = L
     return _lib
 
@@ -544,6 +553,92 @@ class Operator:
     def close(self):
         if self.handle:
             nat_bem_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nat_bem_gemv_variant(nt: int) -> int:
+    """The GEMV variant the autotuner chose for nt elements on the current device (-1: not yet)."""
+    return int(lib().nat_bem_gemv_variant(int(nt)))
+
+
+# ------------------------------------------------------------- neural acoustic transfer field
+def _f32_ptr(x, width=None):
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise TypeError("expected a contiguous float32 torch tensor")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def nat_field_create(n_cond: int, n_out: int, table_log2: int, tables, weights_bf16, biases,
+                     stream=None) -> ctypes.c_void_p:
+    """tables: float32 rows of the four levels back to back (rows x 4); weights_bf16: uint16
+    BF16 bit patterns, four 128 x 128 layers then n_out x 128, concatenated; biases: float32."""
+    pt, kt = _f32_ptr(tables)
+    w = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+    pb, kb = _f32_ptr(biases)
+    h = ctypes.c_void_p()
+    _check(lib().nat_field_create(int(n_cond), int(n_out), int(table_log2), pt,
+                                  ctypes.c_void_p(w.ctypes.data), pb, _stream_of(None, stream),
+                                  ctypes.byref(h)))
+    return h
+
+
+def nat_field_forward(field, x, n_out: int, out=None, stream=None):
+    """x: (n, 4 + n_cond) float32 (numpy or torch, host or CUDA); returns (n, n_out) float32 of
+    the same kind (or writes `out`)."""
+    n = int(x.shape[0])
+    if out is None:
+        if _is_torch(x):
+            import torch
+            out = torch.empty((n, n_out), dtype=torch.float32, device=x.device)
+        else:
+            out = np.empty((n, n_out), dtype=np.float32)
+    px, kx = _f32_ptr(x)
+    if _is_torch(out):
+        po = ctypes.c_void_p(out.data_ptr())
+    else:
+        if out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise TypeError("out must be a C-contiguous float32 array")
+        po = ctypes.c_void_p(out.ctypes.data)
+    _check(lib().nat_field_forward(field, px, n, po, _stream_of(x, stream)))
+    return out
+
+
+def nat_field_destroy(field):
+    if field:
+        lib().nat_field_destroy(field)
+
+
+class NatField:
+    """Owning wrapper of a nat_field handle (parameters as the oracle's random_model returns)."""
+
+    def __init__(self, n_cond, n_out, table_log2, tables, weights_bf16, biases, stream=None):
+        self.n_cond, self.n_out = int(n_cond), int(n_out)
+        self.handle = nat_field_create(n_cond, n_out, table_log2, tables, weights_bf16, biases, stream)
+
+    def forward(self, x, out=None, stream=None):
+        if int(x.shape[1]) != 4 + self.n_cond:
+            raise ValueError(f"inputs must be (n, {4 + self.n_cond})")
+        return nat_field_forward(self.handle, x, self.n_out, out, stream)
+
+    def close(self):
+        if self.handle:
+            nat_field_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -123,21 +123,6 @@ static nat_bem_status check_opts(const nat_bem_opts& o) {
   return NAT_BEM_OK;
 }
 
-// A device copy of `count` elements of p (which may be a host pointer). Sets *tmp when it
-// allocated one; the caller frees it on the same stream.
-template <class T>
-static nat_bem_status to_device(const T* p, size_t count, cudaStream_t s, const T** dp, T** tmp) {
-  *tmp = nullptr;
-  if (is_device_pointer(p)) {
-    *dp = p;
-    return NAT_BEM_OK;
-  }
-  NB_TRY(dev_alloc_n(tmp, count, s));
-  NB_TRY_CUDA(cudaMemcpyAsync(*tmp, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
-  *dp = *tmp;
-  return NAT_BEM_OK;
-}
-
 }  // namespace natbem
 
 using namespace natbem;
@@ -158,6 +143,8 @@ void nat_bem_opts_default(nat_bem_opts* o) {
 }
 
 const char* nat_bem_last_error(void) { return g_last_error.c_str(); }
+
+int32_t nat_bem_gemv_variant(int64_t nt) { return nt > 0 ? gemv_tuned_variant(nt) : -1; }
 
 int64_t nat_bem_op_size(const nat_bem_op* op) { return op ? op->n : 0; }
 

@@ -1666,8 +1666,11 @@ std::mutex g_tune_mu;
 std::map<std::pair<int, int64_t>, int> g_tuned;  // (device, n rounded to 1024) -> variant
 }  // namespace
 
-// The fastest variant for this operator size on this device: each variant runs three times on
-// the operator itself (CUDA events; best of the last two) the first time a size class is met.
+// The fastest variant for this operator size on this device, measured on the operator itself
+// (CUDA events) the first time a size class is met: one warm-up pass over all variants, then
+// four interleaved rounds, keeping each variant's minimum. Other streams' kernels only slow a
+// run down, so the minimum over interleaved rounds is the uncontended time. The first variant
+// (two rows per block, unroll 4) wins ties within 2%.
 static int gemv_variant(const float2* A, int n, int ld, const float2* x, double2* y, int* err,
                         cudaStream_t s) {
   int dev = 0;
@@ -1685,29 +1688,36 @@ static int gemv_variant(const float2* A, int n, int ld, const float2* x, double2
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  int best = kGemvR2U4;
-  float best_ms = 1e30f;
-  for (int v = 0; v < kGemvVariants; ++v) {
-    float vbest = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {  // the first run is a warm-up; best of the other two
+  float vmin[kGemvVariants];
+  for (int v = 0; v < kGemvVariants; ++v) vmin[v] = 1e30f;
+  for (int round = 0; round < 5; ++round) {
+    for (int v = 0; v < kGemvVariants; ++v) {
       float ms = 1e30f;
       cudaEventRecord(e0, s);
       gemv_launch(v, "gemv_tune", A, n, ld, x, y, 1, nullptr, nullptr, err, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) vbest = std::min(vbest, ms);
-    }
-    if (vbest < best_ms) {
-      best_ms = vbest;
-      best = v;
+      if (round > 0) vmin[v] = std::min(vmin[v], ms);
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  int best = kGemvR2U4;
+  for (int v = 1; v < kGemvVariants; ++v)
+    if (vmin[v] < vmin[best] && vmin[v] < 0.98f * vmin[kGemvR2U4]) best = v;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tuned[key] = best;
   return best;
+}
+
+// The variant the autotuner chose for this size on the current device, or -1 before it has run.
+int gemv_tuned_variant(int64_t n) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(std::make_pair(dev, (int64_t)((n + 1023) / 1024)));
+  return it == g_tuned.end() ? -1 : it->second;
 }
 
 // y_s = A x_s for all RHS (x padded to ld), skipping RHS flagged done when `done` is given.

@@ -76,6 +76,22 @@ nat_bem_status dev_alloc_n(T** p, size_t count, cudaStream_t s) {
 // Whether p is a device (or managed) pointer the GPU can read directly.
 bool is_device_pointer(const void* p);
 
+// A device copy of `count` elements of p (which may be a host pointer). Sets *tmp when it
+// allocated one; the caller frees it on the same stream.
+template <class T>
+inline nat_bem_status to_device(const T* p, size_t count, cudaStream_t s, const T** dp, T** tmp) {
+  *tmp = nullptr;
+  if (is_device_pointer(p)) {
+    *dp = p;
+    return NAT_BEM_OK;
+  }
+  NB_TRY(dev_alloc_n(tmp, count, s));
+  NB_TRY_CUDA(cudaMemcpyAsync(*tmp, p, count * sizeof(T), cudaMemcpyHostToDevice, s));
+  *dp = *tmp;
+  return NAT_BEM_OK;
+}
+
+
 // -------------------------------------------------------------------------- geometry
 // Device-resident mesh records. Single-precision records serve the regular (FP32) pairs and
 // the field evaluation; double-precision arrays serve the self and vertex-sharing pairs.
@@ -144,6 +160,7 @@ void workspace_free(Workspace* ws, cudaStream_t s);
 nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d_x, int nrhs,
                           float2* d_y, cudaStream_t s);
 int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o);
+int gemv_tuned_variant(int64_t n);  // -1 before the autotuner met this size
 
 // products.cu: Y = M X for nrhs right-hand sides (M = L for which == 0, R for 1).
 // kEngineFp32: FP32 CUDA-core complex GEMM; kEngineTf32 / kEngineBf16: tcgen05 tensor cores

@@ -23,7 +23,7 @@ def nb():
 
 def _declared():
     hdr = open(os.path.join(ROOT, "include", "nat_bem.h")).read()
-    return sorted(set(re.findall(r"NAT_BEM_API\s+[\w\s\*]*?\b(nat_bem_\w+)\s*\(", hdr)))
+    return sorted(set(re.findall(r"NAT_BEM_API\s+[\w\s\*]*?\b(nat_(?:bem|field)_\w+)\s*\(", hdr)))
 
 
 def test_header_declares_the_binding_names(nb):
@@ -32,7 +32,7 @@ def test_header_declares_the_binding_names(nb):
 
 def test_library_exports_every_declared_symbol(nb):
     out = subprocess.run(["nm", "-D", "--defined-only", nb.LIB_PATH], capture_output=True, text=True).stdout
-    exported = set(re.findall(r"\bT\s+(nat_bem_\w+)", out))
+    exported = set(re.findall(r"\bT\s+(nat_(?:bem|field)_\w+)", out))
     for name in _declared():
         assert name in exported, name
         assert hasattr(nb.lib(), name)
@@ -130,6 +130,24 @@ def test_solve_and_eval_reject_null(nb):
     assert L.nat_bem_sample_field(None, None, 4, None, 1.0, 2.0, None, None, 1, None, None,
                                   None) == nb.NAT_BEM_EINVAL
     L.nat_bem_destroy(None)
+
+
+def test_nat_field_rejects_bad_arguments(nb):
+    """Host-side checks of the neural-field entry points (before any device call)."""
+    L = nb.lib()
+    h = ctypes.c_void_p()
+    t = np.zeros(16, np.float32)
+    w = np.zeros(16, np.uint16)
+    b = np.zeros(16, np.float32)
+    ok = (ctypes.c_void_p(t.ctypes.data), ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(b.ctypes.data))
+    assert L.nat_field_create(2, 8, 18, None, ok[1], ok[2], None, ctypes.byref(h)) == nb.NAT_BEM_EINVAL
+    assert L.nat_field_create(2, 8, 18, *ok, None, None) == nb.NAT_BEM_EINVAL
+    for n_cond, n_out, log2 in ((-1, 8, 18), (9, 8, 18), (2, 0, 18), (2, 129, 18), (2, 8, 11), (2, 8, 25)):
+        assert L.nat_field_create(n_cond, n_out, log2, *ok, None, ctypes.byref(h)) == nb.NAT_BEM_EINVAL
+        assert not h.value
+    assert L.nat_field_forward(None, None, 4, None, None) == nb.NAT_BEM_EINVAL
+    assert nb.nat_bem_gemv_variant(0) == -1
+    L.nat_field_destroy(None)
 
 
 def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):

@@ -1,0 +1,112 @@
+"""GPU parity of the neural acoustic transfer field's forward pass (paper Sec. 3.3 and 3.4:
+grid encoding, positional encoding, 4 x 128 MLP) against the FP64 oracle that rounds every
+layer input to BF16 like the tensor-core kernel.
+
+Tolerance: both sides round the same layer inputs to BF16; they differ only where FP32
+accumulation (kernel) and FP64 (oracle) put a pre-rounding value on different sides of a BF16
+rounding boundary, which moves that activation by one BF16 step (2^-8 relative) and the outputs
+by far less. Relative L2 over all outputs <= 1e-3, largest deviation <= 1e-2 of the outputs' RMS.
+"""
+import numpy as np
+import pytest
+
+from oracle import nat as O
+
+pytestmark = pytest.mark.gpu
+
+REL_L2 = 1e-3
+MAX_REL = 1e-2
+
+
+@pytest.fixture(scope="module")
+def nb():
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build
+    build.build()
+    return nb
+
+
+def _field(nb, m):
+    tables = np.concatenate(m["tables"], axis=0).astype(np.float32)
+    w = np.concatenate([O.bf16_bits(W).ravel() for W in m["weights"]])
+    b = np.concatenate(m["biases"]).astype(np.float32)
+    return nb.NatField(m["n_cond"], m["n_out"], m["table_log2"], tables, w, b)
+
+
+def _inputs(n, D, seed):
+    return np.random.default_rng(seed).random((n, D)).astype(np.float32)
+
+
+def _check(out, ref):
+    out = np.asarray(out, dtype=np.float64)
+    rms = np.sqrt(np.mean(ref ** 2))
+    rel = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    mx = np.max(np.abs(out - ref)) / rms
+    assert rel <= REL_L2, rel
+    assert mx <= MAX_REL, mx
+
+
+@pytest.mark.parametrize("n", [1, 127, 128, 1000, 5000])
+def test_forward_matches_oracle(nb, n):
+    m = O.random_model(n_cond=2, n_out=8, table_log2=18, seed=1)
+    x = _inputs(n, 6, n)
+    with _field(nb, m) as f:
+        out = f.forward(x)
+    ref = O.forward(x.astype(np.float64), m["tables"], m["weights"], m["biases"], m["table_log2"])
+    assert out.shape == (n, 8)
+    _check(out, ref)
+
+
+@pytest.mark.parametrize("n_cond,n_out,log2", [(0, 1, 12), (5, 33, 20), (1, 128, 14), (8, 64, 16)])
+def test_shapes_and_table_sizes(nb, n_cond, n_out, log2):
+    """Hashed levels (2^12: all but the coarsest), all-dense tables (2^20), the widest input
+    (D = 12: 8 condition variables), one output and the full 128 outputs."""
+    m = O.random_model(n_cond=n_cond, n_out=n_out, table_log2=log2, seed=2 + n_cond)
+    x = _inputs(777, 4 + n_cond, 11)
+    with _field(nb, m) as f:
+        out = f.forward(x)
+    ref = O.forward(x.astype(np.float64), m["tables"], m["weights"], m["biases"], log2)
+    _check(out, ref)
+
+
+def test_boundary_inputs(nb):
+    """Queries on the grid's faces and corners (x = 0 and x = 1 exactly) and on vertex planes."""
+    m = O.random_model(seed=4)
+    g = np.array([0.0, 1.0, 0.5, 0.25, 1.0 / 64, 63.0 / 64], np.float32)
+    x = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    x = np.concatenate([x, np.tile(np.array([[0.0, 1.0, 0.3]], np.float32), (len(x), 1))], axis=1)
+    with _field(nb, m) as f:
+        out = f.forward(x)
+    ref = O.forward(x.astype(np.float64), m["tables"], m["weights"], m["biases"], m["table_log2"])
+    _check(out, ref)
+
+
+def test_device_tensors_and_empty_input(nb):
+    torch = pytest.importorskip("torch")
+    m = O.random_model(seed=5)
+    x = _inputs(3000, 6, 21)
+    with _field(nb, m) as f:
+        xt = torch.from_numpy(x).cuda()
+        out = f.forward(xt)
+        torch.cuda.synchronize()
+        assert out.is_cuda
+        host = f.forward(x)
+        assert np.array_equal(out.cpu().numpy(), host)  # one kernel, same bits
+        empty = f.forward(np.zeros((0, 6), np.float32))
+        assert empty.shape == (0, 8)
+
+
+def test_full_size_sampled(nb):
+    """2^22 queries (the bench's size) in one call: sampled rows against the oracle, and the
+    outputs of a repeated call identical (fixed reduction order)."""
+    m = O.random_model(seed=6)
+    n = 1 << 22
+    x = _inputs(n, 6, 31)
+    with _field(nb, m) as f:
+        out = f.forward(x)
+        again = f.forward(x)
+    assert np.array_equal(out, again)
+    rows = np.random.default_rng(3).choice(n, 4096, replace=False)
+    rows = np.concatenate([rows, [0, n - 1]])
+    ref = O.forward(x[rows].astype(np.float64), m["tables"], m["weights"], m["biases"], m["table_log2"])
+    _check(out[rows], ref)

@@ -60,13 +60,15 @@ def test_mlp_layer_order_and_transposes():
     """Identity hidden layers and a one-hot output layer pass one encoded input through."""
     m = nat.random_model(n_cond=1, n_out=3, table_log2=12, seed=3)
     W = [np.eye(128) for _ in range(4)] + [np.zeros((3, 128))]
-    W[4][0, 16] = 1.0   # the first positional feature: sin(pi x_0)
+    W[4][0, 16] = 1.0   # the first positional feature: sin(pi x_3)
     W[4][2, 0] = 2.0    # twice the first grid feature
     bias = [np.zeros(128)] * 4 + [np.array([0.0, 0.75, 0.0])]
     x = np.random.default_rng(1).random((64, 5))
     out = nat.forward(x, m["tables"], W, bias, 12)
     enc = nat.to_bf16(nat.encode(x, m["tables"], 12))
     assert np.allclose(out[:, 0], np.maximum(enc[:, 16], 0.0))
+    assert np.allclose(enc[:, 16], nat.to_bf16(np.sin(np.pi * x[:, 3])))
+    assert np.allclose(enc[:, 16 + 12 * 2:], 0.0)  # two encoded inputs (v_1, f), then padding
     assert np.allclose(out[:, 1], 0.75)
     assert np.allclose(out[:, 2], 2.0 * np.maximum(enc[:, 0], 0.0))
 
