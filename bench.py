@@ -443,6 +443,97 @@ def run_dataset(args):
             "clocks": clk.summary()}
 
 
+# FP32 flops of one regular Galerkin element pair in k_gal_regular: 49 point pairs of about 71
+# (x - y, r, phase, G and both normal derivatives, and the three trial-function sums) plus 7
+# test-point updates of 84 (the 3 x 3 blocks of K and G and the 3 K' sums), an FMA counting 2.
+GAL_FLOPS_PER_PAIR = 49 * 71 + 7 * 84
+
+
+def run_galerkin(args):
+    """Galerkin Burton-Miller (paper Sec. 4, Eq. 6, element-to-element integration of Sec. 4.1):
+    the interior-source body on --n-tri triangles (default 5120, 2562 vertices; P1 pressure, P0
+    Neumann data), monopole Neumann data, --n-k wavenumbers log-uniform in ka [0.5, 10], 1024
+    field points at radius 4. One step: for each wavenumber, re-assemble (element-pair blocks
+    and their gathers), solve, evaluate the field."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    prob = S.interior_source(n_tri=args.n_tri, n_k=args.n_k, ka_range=(0.5, 10.0))
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    opts = nb.nat_bem_opts_default(prec=prec)
+    dev = torch.device("cuda", 0)
+    Vd, Fd, Pd = (torch.from_numpy(a).to(dev) for a in (prob.V, prob.F, prob.points))
+    Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
+    stream = torch.cuda.current_stream(dev)
+    op = nb.Operator.assemble_galerkin(Vd, Fd, float(prob.ks[0]), opts)
+    infos = []
+
+    def step(record=None):
+        out = []
+        for i, k in enumerate(prob.ks):
+            op.reassemble(float(k), like=Vd)
+            p, info, st = op.solve(Gd[i])
+            f = op.evaluate(Pd, p, Gd[i])
+            out.append((p, f))
+            if record is not None:
+                record.append((info.iterations, info.rel_residual, st))
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # per-kernel device times from one untimed step
+    nb.nat_bem_trace_enable(True)
+    nb.nat_bem_trace_select("")
+    nb.nat_bem_trace_reset()
+    step()
+    torch.cuda.synchronize()
+    names = ["gal_regular", "gal_singular", "gal_gather_L", "gal_gather_R", "gemv_bf16", "gemv_rhs",
+             "gemv_resid", "gmres_arnoldi", "eval", "gal_expand"]
+    kern = {nm: nb.nat_bem_trace_kernel(nm) for nm in names}
+    nb.nat_bem_trace_enable(False)
+    launches0 = nb.nat_bem_trace_launches()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        t0.record(stream)
+        for _ in range(args.steps):
+            res = step(infos)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    launches = nb.nat_bem_trace_launches() - launches0
+    n_solves = args.steps * len(prob.ks)
+    f0 = res[0][1].cpu().numpy()
+    acc = {"field_rel_err_vs_exact": float(np.linalg.norm(f0 - prob.exact_field[0]) / np.linalg.norm(prob.exact_field[0])),
+           "k": float(prob.ks[0])}
+    nt = len(prob.F)
+    t, c = kern["gal_regular"]
+    peaks, peak_kind = _peaks()
+    fp32_peak = FP32_LANES_PER_SM * SMS * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    flops = float(nt) * nt * GAL_FLOPS_PER_PAIR
+    tf = flops / (t / c * 1e-3) / 1e12 if c else None
+    op.close()
+    return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16 inner GMRES + f32 refinement", "tf32": "f32"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": f"galerkin_interior_source_{nt}tri_{len(prob.V)}vert_{len(prob.ks)}k",
+                       "n_tri": nt, "n_vert": len(prob.V), "ka_range": [0.5, 10.0],
+                       "field_points": len(prob.points), "precision": args.prec},
+            "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
+            "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
+                      "not_converged": sum(1 for i in infos if i[2] != 0)},
+            "gpu_launches": int(launches),
+            "kernels_ms_per_step": {nm: {"ms_total": v[0], "launches": v[1]} for nm, v in kern.items()},
+            "roofline": {"kernel": "gal_regular", "bound": "alu", "achieved": tf, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": (tf / fp32_peak) if tf else None, "traffic": None,
+                         "flops_per_pair": GAL_FLOPS_PER_PAIR,
+                         "peak_source": "derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock"},
+            "accuracy": acc, "clocks": clk.summary()}
+
+
 def run_nat(args):
     """Neural acoustic transfer field inference (paper Sec. 3.3, 3.4): --n-queries listening
     points (theta/pi, phi/2pi, r_norm, v_1, v_2, f) uniform in [0, 1]^6 through the grid +
@@ -733,7 +824,7 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
-    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset", "nat"])
+    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset", "nat", "galerkin"])
     ap.add_argument("--n-samples", type=int, default=4096, help="Monte-Carlo workload: surface samples")
     ap.add_argument("--random-samples", action="store_true", help="Monte-Carlo workload: uniform random samples")
     ap.add_argument("--n-queries", type=int, default=1 << 22, help="NAT inference workload: queries per step")
@@ -780,11 +871,15 @@ def main():
     if args.workload != "interior":
         if rank == 0:
             fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc,
-                  "dataset": run_dataset, "nat": run_nat}[args.workload]
+                  "dataset": run_dataset, "nat": run_nat, "galerkin": run_galerkin}[args.workload]
             if args.workload == "modal" and args.n_k == 64:
                 args.n_k = 16
             if args.workload == "modal" and args.n_tri == 10240:
                 args.n_tri = 20480
+            if args.workload == "galerkin" and args.n_k == 64:
+                args.n_k = 16
+            if args.workload == "galerkin" and args.n_tri == 10240:
+                args.n_tri = 5120
             print(json.dumps(fn(args)))
         return
     if world > 1:

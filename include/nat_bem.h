@@ -103,6 +103,38 @@ NAT_BEM_API nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, con
                                 nat_bem_op** out);
 
 /*
+ * Galerkin form (paper Sec. 4, Eq. 6 tested with the P1 hat functions; the element-to-element
+ * integration of Sec. 4.1, as bempp does it): P1 (continuous, piecewise linear) Dirichlet data
+ * p at the nv vertices, P0 Neumann data g per triangle, P1 test functions psi_i:
+ *
+ *   L p = R g,   L = 1/2 M11 - K - beta H  (nv x nv),   R = -V - beta K' - (beta/2) M10  (nv x nt),
+ *   H_ij = int int G(x, y) [k^2 (n_x . n_y) phi_j(y) psi_i(x) - curl phi_j(y) . curl psi_i(x)],
+ *
+ * the hypersingular term in Maue's integrated-by-parts form (curl u = n x grad u, constant per
+ * triangle for P1), M11 and M10 the P1-P1 and P0-P1 mass matrices, K, K', V the double, adjoint
+ * double and single layer forms. Quadrature per element pair: the 7-point rule on both
+ * triangles for pairs sharing no vertex; for pairs sharing a vertex (2 regions), an edge (6) or
+ * identical (6), each region of a transformation to the unit 4-cube whose Jacobian cancels the
+ * 1/r singularity, with 4 Gauss-Legendre points per dimension.
+ * The op works with nat_bem_solve (neumann: nt x nrhs, p_out: nv x nrhs, P1 values at the
+ * vertices), nat_bem_eval, nat_bem_far_field and nat_bem_sample_field (p: nv x nrhs, neumann:
+ * nt x nrhs; the 7-point rule on every element with p interpolated), nat_bem_reassemble, mixed
+ * precision, nat_bem_op_apply (R takes nt x nrhs) and nat_bem_op_rows (R rows have nt
+ * columns); not with nat_bem_eval_noalloc, nat_bem_run_batch or the server.
+ * Arguments as for nat_bem_assemble. Device scratch during assembly: min(nt, 4096) x nt x 96
+ * bytes of element-pair blocks, released before returning.
+ * NAT_BEM_EINVAL: as for nat_bem_assemble, a vertex that belongs to no triangle, nt > 65536.
+ * NAT_BEM_ENOMEM / NAT_BEM_ECUDA as for nat_bem_assemble.
+ */
+NAT_BEM_API nat_bem_status nat_bem_assemble_galerkin(const double* verts, int64_t nv, const int32_t* tris,
+                                                     int64_t nt, double k, const nat_bem_opts* opts,
+                                                     void* cuda_stream, nat_bem_op** out);
+
+/* Number of Neumann values per right-hand side the op takes (columns of R): the triangles of
+ * a Galerkin op, else the unknowns (nat_bem_op_size). 0 for NULL. */
+NAT_BEM_API int64_t nat_bem_op_neumann_size(const nat_bem_op* op);
+
+/*
  * Monte-Carlo BEM (paper Sec. 4.1.1 "Monte-Carlo-based integration approximation" and Sec. 4.2
  * "Singularity handling"): the conventional boundary integral equation (beta = 0 in Eq. 6)
  * with the surface integral replaced by a sum over m sample points of uniform density on the
@@ -319,13 +351,15 @@ NAT_BEM_API nat_bem_status nat_bem_selftest_bounded_wait(int32_t timeout_ms, voi
 
 /*
  * Copies rows [row0, row0 + nrows) of the assembled L (which = 0) or R (which = 1) into
- * out (nrows x nt complex64, row-major). For checking the operator; not on the solve path.
+ * out (nrows x cols complex64, row-major; cols = nat_bem_op_size for L,
+ * nat_bem_op_neumann_size for R). For checking the operator; not on the solve path.
  * NAT_BEM_EINVAL: rows out of range, which not 0/1, R not stored.
  */
 NAT_BEM_API nat_bem_status nat_bem_op_rows(const nat_bem_op* op, int32_t which, int64_t row0, int64_t nrows,
                                float* out, void* cuda_stream);
 
-/* Number of triangles of the op (0 for NULL). */
+/* Number of unknowns of the op: triangles (nat_bem_assemble), samples (nat_bem_assemble_mc)
+ * or vertices (nat_bem_assemble_galerkin); 0 for NULL. */
 NAT_BEM_API int64_t nat_bem_op_size(const nat_bem_op* op);
 
 /* Device bytes an op of nt triangles with nrhs right-hand sides holds under opts (NULL =

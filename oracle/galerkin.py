@@ -304,6 +304,47 @@ def assemble_parts(V, F, k, n_sing=N_SING):
     return out
 
 
+def assemble_rows(V, F, k, rows, n_sing=N_SING):
+    """Rows `rows` (vertex indices) of L and R, from the element pairs whose test triangle
+    contains one of them: the same sums as assemble, restricted."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F, np.int64)
+    nv, nt = len(V), len(F)
+    beta = 1j / k
+    geo = geometry(V, F)
+    area, nrm, curl = geo
+    rows = np.asarray(rows)
+    pos = {int(r): i for i, r in enumerate(rows)}
+    L = np.zeros((len(rows), nv), complex)
+    R = np.zeros((len(rows), nt), complex)
+    for t in np.nonzero(np.any(np.isin(F, rows), axis=1))[0]:
+        touch = np.any(np.isin(F, F[t]), axis=1)
+        S = np.nonzero(~touch)[0]
+        Kb, Gb, G0, Vb, Kp = _regular_blocks(V, F, k, t, S, geo)
+        nn = nrm[S] @ nrm[t]
+        cc = np.einsum("ad,sbd->sab", curl[t], curl[S])
+        blk = -Kb - beta * (k * k * nn[:, None, None] * Gb - cc * G0[:, None, None])
+        rblk = -Vb - beta * Kp
+        sing = []
+        for s in np.nonzero(touch)[0]:
+            Kb1, Gb1, G01, Vb1, Kp1 = pair_blocks(V, F, k, t, s, geo, n_sing)
+            H1 = k * k * float(nrm[t] @ nrm[s]) * Gb1 - (curl[t] @ curl[s].T) * G01
+            sing.append((s, -Kb1 - beta * H1, -Vb1 - beta * Kp1))
+        for a in range(3):
+            i = pos.get(int(F[t][a]))
+            if i is None:
+                continue
+            for b in range(3):
+                np.add.at(L[i], F[S][:, b], blk[:, a, b])
+            R[i, S] += rblk[:, a]
+            for s, lb, rb in sing:
+                L[i, F[s]] += lb[a]
+                R[i, s] += rb[a]
+            L[i, F[t]] += 0.5 * area[t] / 12.0 * (np.ones(3) + (np.arange(3) == a))
+            R[i, t] += -0.5 * beta * area[t] / 3.0
+    return L, R
+
+
 def assemble(V, F, k, n_sing=N_SING):
     """Dense L (nv x nv) and R (nv x nt), complex128: L p = R g."""
     m = assemble_parts(V, F, k, n_sing)
@@ -336,4 +377,21 @@ def evaluate(V, F, k, points, p, g):
         G = np.exp(1j * k * r) / (4 * np.pi * r)
         dGy = G * (1 - 1j * k * r) / r ** 2 * np.einsum("tqd,td->tq", d, nrm)
         out[m] = np.sum(wy * (py * dGy - G * np.asarray(g)[:, None]))
+    return out
+
+
+def far_field(V, F, k, dirs, p, g):
+    """Far-field pattern F(d) = sum over elements and points (w A / 4 pi) [p(y) (-ik d.n) - g]
+    e^{-ik d.y}, with P1 p interpolated at the 7 points of every element."""
+    V = np.asarray(V, np.float64)
+    F = np.asarray(F, np.int64)
+    area, nrm, _ = geometry(V, F)
+    y = np.einsum("qa,tad->tqd", RULE7_BARY, V[F])
+    py = np.einsum("qa,ta->tq", RULE7_BARY, np.asarray(p)[F])
+    wy = RULE7_W[None, :] * area[:, None] / (4 * np.pi)
+    out = np.zeros(len(dirs), complex)
+    for m, dvec in enumerate(np.asarray(dirs, np.float64)):
+        ph = np.exp(-1j * k * (y @ dvec))
+        dn = (nrm @ dvec)[:, None]
+        out[m] = np.sum(wy * ph * (py * (-1j * k * dn) - np.asarray(g)[:, None]))
     return out

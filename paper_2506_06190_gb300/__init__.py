@@ -37,7 +37,8 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_server_create", "nat_bem_submit", "nat_bem_wait", "nat_bem_server_reserved",
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
             "nat_bem_far_field", "nat_bem_sample_field", "nat_bem_gemv_variant", "nat_field_create",
-            "nat_field_forward", "nat_field_destroy"]
+            "nat_field_forward", "nat_field_destroy", "nat_bem_assemble_galerkin",
+            "nat_bem_op_neumann_size"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -134,6 +135,10 @@ def lib():
         L.nat_bem_trace_launches.restype = i64
         L.nat_bem_trace_kernel.argtypes = [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(i64)]
         L.nat_bem_trace_kernel.restype = ctypes.c_int
+        L.nat_bem_assemble_galerkin.argtypes = [vp, i64, vp, i64, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
+        L.nat_bem_assemble_galerkin.restype = ctypes.c_int
+        L.nat_bem_op_neumann_size.argtypes = [vp]
+        L.nat_bem_op_neumann_size.restype = i64
         L.nat_bem_gemv_variant.argtypes = [i64]
         L.nat_bem_gemv_variant.restype = i32
         L.nat_field_create.argtypes = [i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
@@ -220,6 +225,23 @@ def nat_bem_assemble(V, F, k: float, opts: Opts | None = None, stream=None) -> c
     return op
 
 
+def nat_bem_assemble_galerkin(V, F, k: float, opts: Opts | None = None, stream=None) -> ctypes.c_void_p:
+    """Galerkin op (P1 pressure at the vertices, P0 Neumann data per triangle)."""
+    pv, kv = _ptr(V, np.float64)
+    pt, kt = _ptr(F, np.int32)
+    nv, nt = int(V.shape[0]), int(F.shape[0])
+    op = ctypes.c_void_p()
+    st = lib().nat_bem_assemble_galerkin(pv, nv, pt, nt, float(k), ctypes.byref(opts) if opts else None,
+                                         _stream_of(V, stream), ctypes.byref(op))
+    del kv, kt
+    _check(st)
+    return op
+
+
+def nat_bem_op_neumann_size(op) -> int:
+    return int(lib().nat_bem_op_neumann_size(op))
+
+
 def nat_bem_assemble_mc(Y, N, area: float, k: float, opts: Opts | None = None, stream=None) -> ctypes.c_void_p:
     """Monte-Carlo op from surface samples Y (m x 3), unit outward normals N (m x 3) and the
     total surface area; returns the opaque op handle."""
@@ -244,12 +266,13 @@ def nat_bem_reassemble(op, k: float, stream=None, like=None):
 def nat_bem_solve(op, neumann, out=None, stream=None, check=True):
     """Solve L p = R g. Returns (p, SolveInfo, status)."""
     n = int(lib().nat_bem_op_size(op))
-    nrhs = _nrhs_of(neumann, n)
+    nrhs = _nrhs_of(neumann, int(lib().nat_bem_op_neumann_size(op)))
     pg, kg = _ptr(neumann, np.complex64)
     if out is None:
         if _is_torch(neumann):
             import torch
-            out = torch.empty(tuple(neumann.shape), dtype=torch.complex64, device=neumann.device)
+            shape = (nrhs, n) if neumann.dim() == 2 else (n,)
+            out = torch.empty(shape, dtype=torch.complex64, device=neumann.device)
         else:
             out = np.zeros((n, nrhs) if np.ndim(neumann) == 2 else (n,), dtype=np.complex64, order="F")
     po, ko = _ptr(out, np.complex64)
@@ -386,11 +409,12 @@ def nat_bem_run_batch(jobs, opts: Opts | None = None, concurrency: int = 3, stre
 def nat_bem_op_apply(op, which: int, engine: int, X, stream=None):
     """Y = M X (M = L for which 0, R for 1) with the chosen product engine."""
     n = int(lib().nat_bem_op_size(op))
-    nrhs = _nrhs_of(X, n)
+    cols = int(lib().nat_bem_op_neumann_size(op)) if which == 1 else n
+    nrhs = _nrhs_of(X, cols)
     px, kx = _ptr(X, np.complex64)
     if _is_torch(X):
         import torch
-        Y = torch.empty(tuple(X.shape), dtype=torch.complex64, device=X.device)
+        Y = torch.empty((nrhs, n) if X.dim() == 2 else (n,), dtype=torch.complex64, device=X.device)
     else:
         Y = np.zeros((n, nrhs) if np.ndim(X) == 2 else (n,), dtype=np.complex64, order="F")
     py, ky = _ptr(Y, np.complex64)
@@ -471,7 +495,8 @@ def nat_bem_selftest_bounded_wait(timeout_ms: int = 50, stream=None) -> int:
 
 def nat_bem_op_rows(op, which: int, row0: int, nrows: int, stream=None) -> np.ndarray:
     n = int(lib().nat_bem_op_size(op))
-    out = np.zeros((nrows, n), dtype=np.complex64)
+    cols = int(lib().nat_bem_op_neumann_size(op)) if which == 1 else n
+    out = np.zeros((nrows, cols), dtype=np.complex64)
     _check(lib().nat_bem_op_rows(op, int(which), int(row0), int(nrows),
                                  ctypes.c_void_p(out.ctypes.data), _stream_of(None, stream)))
     return out
@@ -523,6 +548,10 @@ class Operator:
     @classmethod
     def assemble(cls, V, F, k, opts=None, stream=None):
         return cls(nat_bem_assemble(V, F, k, opts, stream), int(F.shape[0]), float(k))
+
+    @classmethod
+    def assemble_galerkin(cls, V, F, k, opts=None, stream=None):
+        return cls(nat_bem_assemble_galerkin(V, F, k, opts, stream), int(V.shape[0]), float(k))
 
     @classmethod
     def assemble_mc(cls, Y, N, area, k, opts=None, stream=None):

@@ -127,6 +127,12 @@ static nat_bem_status check_opts(const nat_bem_opts& o) {
 
 using namespace natbem;
 
+namespace {
+// Galerkin assembly keeps element-pair blocks of min(nt, 4096) test triangles x nt trial
+// triangles (96 bytes each) as scratch: 25 GB at this size.
+constexpr int64_t kGalerkinMaxTriangles = 65536;
+}  // namespace
+
 extern "C" {
 
 void nat_bem_opts_default(nat_bem_opts* o) {
@@ -223,6 +229,8 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
     cudaGetDevice(&op->device);
     op->geo.n = nt;
     op->geo.ld = round_up(nt, 32);
+    op->nn = nt;
+    op->ldr = op->geo.ld;
     auto fail = [&](nat_bem_status st) {
       nat_bem_destroy(op);
       return st;
@@ -252,6 +260,101 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
     return NAT_BEM_ECUDA;
   }
 }
+
+nat_bem_status nat_bem_assemble_galerkin(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                                         double k, const nat_bem_opts* opts, void* cuda_stream,
+                                         nat_bem_op** out) {
+  try {
+    clear_error();
+    if (!out) {
+      set_error("out is NULL");
+      return NAT_BEM_EINVAL;
+    }
+    *out = nullptr;
+    if (!verts || !tris) {
+      set_error("verts and tris must not be NULL");
+      return NAT_BEM_EINVAL;
+    }
+    if (!(k > 0.0) || !std::isfinite(k)) {
+      set_error("k must be positive and finite");
+      return NAT_BEM_EINVAL;
+    }
+    if (nv <= 0 || nt <= 0 || nt > kGalerkinMaxTriangles) {
+      set_error("nat_bem_assemble_galerkin: need nv > 0 and 0 < nt <= 65536");
+      return NAT_BEM_EINVAL;
+    }
+    nat_bem_opts o;
+    nat_bem_opts_default(&o);
+    if (opts) o = *opts;
+    NB_TRY(check_opts(o));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    std::vector<double> hV(3 * nv);
+    std::vector<int32_t> hT(3 * nt);
+    NB_TRY_CUDA(cudaMemcpyAsync(hV.data(), verts, 3 * nv * sizeof(double), cudaMemcpyDefault, s));
+    NB_TRY_CUDA(cudaMemcpyAsync(hT.data(), tris, 3 * nt * sizeof(int32_t), cudaMemcpyDefault, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    NB_TRY(validate_mesh_host(hV.data(), nv, hT.data(), nt));
+    {
+      // every vertex must carry a P1 unknown: each one belongs to some triangle
+      std::vector<char> used(nv, 0);
+      for (int64_t i = 0; i < 3 * nt; ++i) used[hT[i]] = 1;
+      for (int64_t v = 0; v < nv; ++v)
+        if (!used[v]) {
+          set_error("nat_bem_assemble_galerkin: vertex " + std::to_string(v) + " belongs to no triangle");
+          return NAT_BEM_EINVAL;
+        }
+    }
+    std::vector<int2> near;
+    build_near_pairs(hT.data(), nv, nt, near);
+    NB_TRY(ensure_rules(o.adj_subdiv_levels, o.self_theta_pts));
+    nat_bem_op* op = new (std::nothrow) nat_bem_op();
+    if (!op) {
+      set_error("host allocation failed");
+      return NAT_BEM_ENOMEM;
+    }
+    op->n = nv;
+    op->k = k;
+    op->opts = o;
+    op->stream = s;
+    op->galerkin = true;
+    cudaGetDevice(&op->device);
+    op->geo.n = nt;
+    op->geo.ld = round_up(nv, 32);
+    op->nn = nt;
+    op->ldr = round_up(nt, 32);
+    auto fail = [&](nat_bem_status st) {
+      nat_bem_destroy(op);
+      return st;
+    };
+    double* dV = nullptr;
+    int32_t* dT = nullptr;
+    nat_bem_status st = dev_alloc_n(&dV, (size_t)(3 * nv), s);
+    if (st == NAT_BEM_OK) st = dev_alloc_n(&dT, (size_t)(3 * nt), s);
+    if (st == NAT_BEM_OK &&
+        (cudaMemcpyAsync(dV, hV.data(), 3 * nv * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+         cudaMemcpyAsync(dT, hT.data(), 3 * nt * sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)) {
+      set_error("nat_bem_assemble_galerkin: mesh copy failed");
+      st = NAT_BEM_ECUDA;
+    }
+    if (st == NAT_BEM_OK) st = geometry_build(op, dV, dT, nv, near, s);
+    if (st == NAT_BEM_OK) st = galerkin_geometry_build(op, hT.data(), nv, s);
+    dev_free(dV, s);
+    dev_free(dT, s);
+    if (st != NAT_BEM_OK) return fail(st);
+    if ((st = dev_alloc_n(&op->L, (size_t)nv * op->geo.ld, s)) != NAT_BEM_OK) return fail(st);
+    if ((st = dev_alloc_n(&op->R, (size_t)nv * op->ldr, s)) != NAT_BEM_OK) return fail(st);
+    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, (size_t)nv * op->geo.ld, s)) != NAT_BEM_OK)
+      return fail(st);
+    if ((st = galerkin_assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
+    *out = op;
+    return NAT_BEM_OK;
+  } catch (...) {
+    set_error("internal error in nat_bem_assemble_galerkin");
+    return NAT_BEM_ECUDA;
+  }
+}
+
+int64_t nat_bem_op_neumann_size(const nat_bem_op* op) { return op ? op->nn : 0; }
 
 nat_bem_status nat_bem_assemble_mc(const double* pts, const double* normals, int64_t m, double area,
                                    double k, const nat_bem_opts* opts, void* cuda_stream,
@@ -316,6 +419,8 @@ nat_bem_status nat_bem_assemble_mc(const double* pts, const double* normals, int
     cudaGetDevice(&op->device);
     op->geo.n = m;
     op->geo.ld = round_up(m, 32);
+    op->nn = m;
+    op->ldr = op->geo.ld;
     auto fail = [&](nat_bem_status st) {
       nat_bem_destroy(op);
       return st;
@@ -366,7 +471,7 @@ nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, int32_t nrhs,
     const size_t cnt = (size_t)op->n * nrhs;
     const float2* dg = nullptr;
     float2* tg = nullptr;
-    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), (size_t)op->nn * nrhs, s, &dg, &tg));
     const bool pdev = is_device_pointer(p_out);
     float2* dp = reinterpret_cast<float2*>(p_out);
     float2* tp = nullptr;
@@ -414,7 +519,7 @@ nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts, int64_t m, 
     float2 *tp = nullptr, *tg = nullptr;
     NB_TRY(to_device(pts, (size_t)(3 * m), s, &dpts, &tpts));
     NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
-    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), (size_t)op->nn * nrhs, s, &dg, &tg));
     const bool odev = is_device_pointer(field_out);
     float2* dout = reinterpret_cast<float2*>(field_out);
     float2* tout = nullptr;
@@ -464,7 +569,7 @@ nat_bem_status nat_bem_far_field(const nat_bem_op* op, const double* dirs, int64
     float2 *tp = nullptr, *tg = nullptr;
     NB_TRY(to_device(dirs, (size_t)(3 * nd), s, &dd, &td));
     NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
-    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), (size_t)op->nn * nrhs, s, &dg, &tg));
     const bool odev = is_device_pointer(out);
     float2* dout = reinterpret_cast<float2*>(out);
     float2* tout = nullptr;
@@ -520,7 +625,7 @@ nat_bem_status nat_bem_sample_field(const nat_bem_op* op, const double* u, int64
     float2 *tp = nullptr, *tg = nullptr;
     NB_TRY(to_device(u, (size_t)(3 * n), s, &du, &tu));
     NB_TRY(to_device(reinterpret_cast<const float2*>(p), cnt, s, &dp, &tp));
-    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), cnt, s, &dg, &tg));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(neumann), (size_t)op->nn * nrhs, s, &dg, &tg));
     const bool cdev = is_device_pointer(coords_out), adev = is_device_pointer(amp_out);
     double* dco = coords_out;
     float* dam = amp_out;
@@ -576,7 +681,7 @@ nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t eng
     const size_t cnt = (size_t)op->n * nrhs;
     const float2* dx = nullptr;
     float2* tx = nullptr;
-    NB_TRY(to_device(reinterpret_cast<const float2*>(X), cnt, s, &dx, &tx));
+    NB_TRY(to_device(reinterpret_cast<const float2*>(X), (size_t)(which == 1 ? op->nn : op->n) * nrhs, s, &dx, &tx));
     const bool ydev = is_device_pointer(Y);
     float2* dy = reinterpret_cast<float2*>(Y);
     float2* ty = nullptr;
@@ -615,9 +720,9 @@ nat_bem_status nat_bem_op_rows(const nat_bem_op* op, int32_t which, int64_t row0
     return NAT_BEM_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int64_t n = op->n, ld = op->geo.ld;
-  NB_TRY_CUDA(cudaMemcpy2DAsync(out, n * sizeof(float2), M + row0 * ld, ld * sizeof(float2),
-                                n * sizeof(float2), nrows, cudaMemcpyDefault, s));
+  const int64_t cols = which == 1 ? op->nn : op->n, ld = which == 1 ? op->ldr : op->geo.ld;
+  NB_TRY_CUDA(cudaMemcpy2DAsync(out, cols * sizeof(float2), M + row0 * ld, ld * sizeof(float2),
+                                cols * sizeof(float2), nrows, cudaMemcpyDefault, s));
   NB_TRY_CUDA(cudaStreamSynchronize(s));
   return NAT_BEM_OK;
 }
@@ -629,6 +734,7 @@ void nat_bem_destroy(nat_bem_op* op) {
   void* ptrs[] = {g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, g.tri, g.cen, g.nrm64, g.area,
                   g.near_pairs, op->L, op->R, op->Lb};
   for (void* p : ptrs) dev_free(p, s);
+  galerkin_free(op, s);
   workspace_free(op->ws, s);
   delete op;
 }
@@ -646,6 +752,7 @@ nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cuda_stream) {
     }
     op->k = k;
     if (op->mc) return mc_assemble_operators(op, (cudaStream_t)cuda_stream);
+    if (op->galerkin) return galerkin_assemble_operators(op, (cudaStream_t)cuda_stream);
     NB_TRY(ensure_rules(op->opts.adj_subdiv_levels, op->opts.self_theta_pts));
     return assemble_operators(op, (cudaStream_t)cuda_stream);
   } catch (...) {

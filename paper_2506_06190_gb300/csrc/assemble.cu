@@ -680,7 +680,7 @@ k_assemble_self(int n, const double* __restrict__ tri, const double* __restrict_
 nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
                               const std::vector<int2>& near_pairs, cudaStream_t s) {
   Geometry& g = op->geo;
-  const int64_t n = op->n;
+  const int64_t n = g.n;  // elements
   (void)nv;
   NB_TRY(dev_alloc_n(&g.c_hi, n, s));
   NB_TRY(dev_alloc_n(&g.c_lo, n, s));

@@ -249,20 +249,50 @@ static void eval_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g,
   }
 }
 
-static void eval_launch(const nat_bem_op* op, int nr, dim3 grid, cudaStream_t s, const double* d_pts,
+// The element records a field kernel sums over: seven points per element, or one point per
+// record (Monte-Carlo samples; the quadrature points of a Galerkin op's elements, with the P1
+// pressure and the P0 Neumann data expanded to them).
+struct EvalSource {
+  const Geometry* g;
+  int n;
+  bool one_point;
+};
+
+static void eval_launch(const EvalSource& src, float k, int nr, dim3 grid, cudaStream_t s, const double* d_pts,
                         int m, const float2* d_p, const float2* d_g, int r0, int per, double2* part) {
-  if (op->mc)
-    eval_launch_nq<1>(nr, grid, s, op->geo, (int)op->n, d_pts, m, (float)op->k, d_p, d_g, r0, per, part);
+  if (src.one_point)
+    eval_launch_nq<1>(nr, grid, s, *src.g, src.n, d_pts, m, k, d_p, d_g, r0, per, part);
   else
-    eval_launch_nq<7>(nr, grid, s, op->geo, (int)op->n, d_pts, m, (float)op->k, d_p, d_g, r0, per, part);
+    eval_launch_nq<7>(nr, grid, s, *src.g, src.n, d_pts, m, k, d_p, d_g, r0, per, part);
 }
+
+static EvalSource eval_source(const nat_bem_op* op) {
+  if (op->galerkin) return EvalSource{&op->gal.pts, (int)op->gal.pts.n, true};
+  return EvalSource{&op->geo, (int)op->n, op->mc};
+}
+
+static nat_bem_status eval_core(const nat_bem_op* op, const double* d_pts, int64_t m,
+                                const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                                cudaStream_t s);
 
 nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
                          const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
                          cudaStream_t s) {
   if (m == 0) return NAT_BEM_OK;
-  const Geometry& g = op->geo;
-  const int n = (int)op->n;
+  if (!op->galerkin) return eval_core(op, d_pts, m, d_p, d_g, nrhs, d_out, s);
+  float2 *pq = nullptr, *gq = nullptr;
+  NB_TRY(galerkin_expand(op, d_p, d_g, nrhs, &pq, &gq, s));
+  nat_bem_status st = eval_core(op, d_pts, m, pq, gq, nrhs, d_out, s);
+  dev_free(pq, s);
+  dev_free(gq, s);
+  return st;
+}
+
+static nat_bem_status eval_core(const nat_bem_op* op, const double* d_pts, int64_t m,
+                                const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                                cudaStream_t s) {
+  const EvalSource src = eval_source(op);
+  const int n = src.n;
   const int pblocks = (int)((m + kEvalThreads - 1) / kEvalThreads);
   // split the elements so that the grid holds about four blocks per SM
   int dev = 0, sms = 148;
@@ -278,7 +308,7 @@ nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    NB_LAUNCH("eval", s, eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
+    NB_LAUNCH("eval", s, eval_launch(src, (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
     NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
@@ -301,11 +331,28 @@ static void far_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, 
   }
 }
 
+static nat_bem_status far_field_core(const nat_bem_op* op, const double* d_dirs, int64_t nd,
+                                     const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                                     cudaStream_t s);
+
 nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_t nd,
                               const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
                               cudaStream_t s) {
   if (nd == 0) return NAT_BEM_OK;
-  const int n = (int)op->n;
+  if (!op->galerkin) return far_field_core(op, d_dirs, nd, d_p, d_g, nrhs, d_out, s);
+  float2 *pq = nullptr, *gq = nullptr;
+  NB_TRY(galerkin_expand(op, d_p, d_g, nrhs, &pq, &gq, s));
+  nat_bem_status st = far_field_core(op, d_dirs, nd, pq, gq, nrhs, d_out, s);
+  dev_free(pq, s);
+  dev_free(gq, s);
+  return st;
+}
+
+static nat_bem_status far_field_core(const nat_bem_op* op, const double* d_dirs, int64_t nd,
+                                     const float2* d_p, const float2* d_g, int nrhs, float2* d_out,
+                                     cudaStream_t s) {
+  const EvalSource src = eval_source(op);
+  const int n = src.n;
   const int pblocks = (int)((nd + kEvalThreads - 1) / kEvalThreads);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -320,10 +367,10 @@ nat_bem_status far_field_impl(const nat_bem_op* op, const double* d_dirs, int64_
   for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
     const int nr = min(kMaxRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    if (op->mc)
-      NB_LAUNCH("far_field", s, far_launch_nq<1>(nr, grid, s, op->geo, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
+    if (src.one_point)
+      NB_LAUNCH("far_field", s, far_launch_nq<1>(nr, grid, s, *src.g, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
     else
-      NB_LAUNCH("far_field", s, far_launch_nq<7>(nr, grid, s, op->geo, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
+      NB_LAUNCH("far_field", s, far_launch_nq<7>(nr, grid, s, *src.g, n, d_dirs, (int)nd, (float)op->k, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = nd * nr;
     NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)nd, splits, nr, pass_width(nr), r0, d_out));
@@ -405,7 +452,6 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
                                         float2* d_out, cudaStream_t s) {
   double2* part = nullptr;
   NB_TRY(scratch_address(&part));
-  const Geometry& g = op->geo;
   const int n = (int)op->n;
   const int pblocks = (int)((m + kEvalThreads - 1) / kEvalThreads);
   int dev = 0, sms = 148;
@@ -422,7 +468,7 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
   for (int r0 = 0; r0 < nrhs; r0 += kNoAllocRhsPass) {
     const int nr = min(kNoAllocRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    eval_launch(op, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part);
+    eval_launch(eval_source(op), (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part);
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
     k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out);
@@ -446,6 +492,10 @@ extern "C" nat_bem_status nat_bem_eval_noalloc(const nat_bem_op* op, const doubl
     if (m > kNoAllocMaxPoints) {
       set_error("nat_bem_eval_noalloc: m = " + std::to_string(m) + " exceeds the maximum of " +
                 std::to_string(kNoAllocMaxPoints) + " points per call (split the points)");
+      return NAT_BEM_EINVAL;
+    }
+    if (op->galerkin) {
+      set_error("nat_bem_eval_noalloc: Galerkin ops need scratch for the P1 expansion: use nat_bem_eval");
       return NAT_BEM_EINVAL;
     }
     if (m == 0) return NAT_BEM_OK;

@@ -1460,7 +1460,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->hnorm, nr, s));
   NB_TRY(dev_alloc_n(&ws->res_true, nr, s));
   NB_TRY(dev_alloc_n(&ws->xf, ld * nr, s));
-  NB_TRY(dev_alloc_n(&ws->gin, ld * nr, s));
+  NB_TRY(dev_alloc_n(&ws->gin, std::max<int64_t>(ld, op->ldr) * nr, s));
   NB_TRY(dev_alloc_n(&ws->pout, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->done, nr, s));
   NB_TRY(dev_alloc_n(&ws->iters, nr, s));
@@ -1858,7 +1858,9 @@ __global__ void k_to_c64(const double2* __restrict__ y, int64_t count, float2* _
 
 nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d_x, int nrhs,
                           float2* d_y, cudaStream_t s) {
-  const int n = (int)op->n, ld = (int)op->geo.ld;
+  // columns: n (L) or the Neumann count (R), padded to the matrix's leading dimension
+  const int n = (int)op->n, ld = which == 1 ? (int)op->ldr : (int)op->geo.ld;
+  const int cols = which == 1 ? (int)op->nn : n;
   float2* xpad = nullptr;
   double2* y64 = nullptr;
   void* scratch = nullptr;
@@ -1879,7 +1881,7 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
   }
   cudaMemsetAsync(err, 0, sizeof(int), s);
   const int64_t tot = (int64_t)ld * nrhs;
-  NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_x, n, ld, nrhs, xpad));
+  NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_x, cols, ld, nrhs, xpad));
   const float2* M = which == 0 ? op->L : op->R;
   if (engine >= NAT_BEM_ENGINE_GEMV0) {
     st = gemv_launch(engine - NAT_BEM_ENGINE_GEMV0, "gemv_apply", M, n, ld, xpad, y64, nrhs, nullptr,
@@ -1925,15 +1927,17 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
-  const int n = (int)op->n, ld = (int)op->geo.ld;
+  const int n = (int)op->n;
   const dim3 vec_grid((n + kChunk - 1) / kChunk, nrhs);
   // b = R g
   {
-    const int64_t tot = (int64_t)ld * nrhs;
-    NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, n, ld, nrhs, ws->gin));
+    // g has op->nn values per RHS (triangles), padded to R's leading dimension
+    const int nn = (int)op->nn, ldr = (int)op->ldr;
+    const int64_t tot = (int64_t)ldr * nrhs;
+    NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, nn, ldr, nrhs, ws->gin));
     NB_CHECK_LAUNCH();
     if (nrhs == 1)
-      NB_TRY(gemv("gemv_rhs", op->R, n, ld, ws->gin, ws->b, nrhs, nullptr, nullptr, s, ws->tc_err));
+      NB_TRY(gemv("gemv_rhs", op->R, n, ldr, ws->gin, ws->b, nrhs, nullptr, nullptr, s, ws->tc_err));
     else
       NB_TRY(product(op, 1, kEngineFp32, ws->gin, nrhs, ws->b, nullptr, nullptr, ws->tc_scratch,
                      ws->tc_bytes, ws->tc_err, s));

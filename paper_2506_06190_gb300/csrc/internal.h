@@ -114,6 +114,15 @@ struct Geometry {
   int64_t n_near = 0;
 };
 
+// Galerkin op (galerkin.cu): vertex -> triangle lists, P1 curls, and the 7 quadrature points
+// of every element as one-point records for the field kernels.
+struct Galerkin {
+  int* adj_ptr = nullptr;  // nv + 1 offsets into adj
+  int2* adj = nullptr;     // per vertex: (triangle, local index), increasing triangle order
+  float4* curl = nullptr;  // 3 per element: curl of the P1 hat of local vertex a
+  Geometry pts;            // 7 nt point records (position hi/lo, normal, weight w A / (4 pi))
+};
+
 // Host-side mesh check and near-pair list (mesh.cpp). Returns NAT_BEM_EINVAL with a message
 // for an invalid mesh.
 nat_bem_status validate_mesh_host(const double* V, int64_t nv, const int32_t* T, int64_t nt);
@@ -140,6 +149,10 @@ struct nat_bem_op {
   natbem::Workspace* ws = nullptr;     // solver workspace, grown on demand
   bool mc = false;                     // Monte-Carlo op (nat_bem_assemble_mc): n samples
   double mc_area = 0.0;                // Monte-Carlo op: total surface area
+  bool galerkin = false;               // Galerkin op: n = vertices, geo.n = triangles
+  int64_t nn = 0;                      // Neumann values per RHS (triangles; n except Galerkin)
+  int64_t ldr = 0;                     // leading dimension of R (geo.ld except Galerkin)
+  natbem::Galerkin gal;                // Galerkin op only
 };
 
 namespace natbem {
@@ -152,6 +165,14 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s);
 // mc.cu
 nat_bem_status mc_geometry_build(nat_bem_op* op, const double* dY, const double* dN, cudaStream_t s);
 nat_bem_status mc_assemble_operators(nat_bem_op* op, cudaStream_t s);
+
+// galerkin.cu
+nat_bem_status galerkin_geometry_build(nat_bem_op* op, const int32_t* T, int64_t nv, cudaStream_t s);
+nat_bem_status galerkin_assemble_operators(nat_bem_op* op, cudaStream_t s);
+// P1 p (nv per RHS) and P0 g (nt per RHS) at the 7 points of every triangle (7 nt per RHS)
+nat_bem_status galerkin_expand(const nat_bem_op* op, const float2* d_p, const float2* d_g, int nrhs,
+                               float2** pq, float2** gq, cudaStream_t s);
+void galerkin_free(nat_bem_op* op, cudaStream_t s);
 
 // gmres.cu
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,

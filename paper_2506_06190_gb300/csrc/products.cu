@@ -458,7 +458,7 @@ size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
 nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
                        double2* Y, const int* done, const int* scal, void* scratch,
                        size_t scratch_bytes, int* err, cudaStream_t s) {
-  const int n = (int)op->n, ld = (int)op->geo.ld;
+  const int n = (int)op->n, ld = which == 1 ? (int)op->ldr : (int)op->geo.ld;
   const float2* M = which == 0 ? op->L : op->R;
   if (engine == kEngineFp32) {
     dim3 grid((n + kGmRows - 1) / kGmRows, (nrhs + kGmRhs - 1) / kGmRhs);

@@ -246,3 +246,23 @@ def _sphere_checks():
     g = S.cos_theta_neumann(V, F)
     p = np.linalg.solve(L, R @ g)
     assert _rel(p, V[:, 2] / np.linalg.norm(V, axis=1) * _h1(k) / (k * _h1p(k))) < 0.06
+
+
+def test_far_field_of_the_pulsating_sphere(spheres):
+    """F(d) = lim r e^{-ikr} p(r d) = p(1) e^{-ik} for the pulsating unit sphere."""
+    k = 2.0
+    V, F, L, R = spheres[2]
+    p = np.linalg.solve(L, R @ np.ones(len(F)))
+    dirs = S.fibonacci_points(40, 1.0)
+    ff = Gk.far_field(V, F, k, dirs, p, np.ones(len(F)))
+    exact = np.exp(-1j * k) / (1j * k - 1.0)
+    assert _rel(ff, np.full(len(dirs), exact)) < 0.025       # the discretisation error (h^2)
+    far = Gk.evaluate(V, F, k, 50.0 * dirs, p, np.ones(len(F))) * 50.0 * np.exp(-50j * k)
+    assert _rel(ff, far) < 1e-3                                # the field's 1/r limit
+
+
+def test_assemble_rows_matches_full(spheres):
+    V, F, L, R = spheres[1]
+    rows = [0, 7, 23, 41]
+    Lr, Rr = Gk.assemble_rows(V, F, 2.0, rows)
+    assert np.max(np.abs(Lr - L[rows])) < 1e-14 and np.max(np.abs(Rr - R[rows])) < 1e-14
