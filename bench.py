@@ -489,8 +489,8 @@ def run_galerkin(args):
     nb.nat_bem_trace_reset()
     step()
     torch.cuda.synchronize()
-    names = ["gal_regular", "gal_singular", "gal_gather_L", "gal_gather_R", "gemv_bf16", "gemv_rhs",
-             "gemv_resid", "gmres_arnoldi", "eval", "gal_expand"]
+    names = ["gal_regular", "gal_singular", "gal_rowsum_L", "gal_gather_L", "gal_gather_R", "gemv_bf16",
+             "gemv_rhs", "gemv_resid", "gmres_arnoldi", "eval", "gal_expand"]
     kern = {nm: nb.nat_bem_trace_kernel(nm) for nm in names}
     nb.nat_bem_trace_enable(False)
     launches0 = nb.nat_bem_trace_launches()
@@ -511,8 +511,9 @@ def run_galerkin(args):
     t, c = kern["gal_regular"]
     peaks, peak_kind = _peaks()
     fp32_peak = FP32_LANES_PER_SM * SMS * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    flops = float(nt) * nt * GAL_FLOPS_PER_PAIR
-    tf = flops / (t / c * 1e-3) / 1e12 if c else None
+    # every launch of the traced step together covers the nt x nt pairs of each of its solves
+    flops = float(len(prob.ks)) * nt * nt * GAL_FLOPS_PER_PAIR
+    tf = flops / (t * 1e-3) / 1e12 if c else None
     op.close()
     return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -121,8 +121,9 @@ NAT_BEM_API nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, con
  * nt x nrhs; the 7-point rule on every element with p interpolated), nat_bem_reassemble, mixed
  * precision, nat_bem_op_apply (R takes nt x nrhs) and nat_bem_op_rows (R rows have nt
  * columns); not with nat_bem_eval_noalloc, nat_bem_run_batch or the server.
- * Arguments as for nat_bem_assemble. Device scratch during assembly: min(nt, 4096) x nt x 96
- * bytes of element-pair blocks, released before returning.
+ * Arguments as for nat_bem_assemble. Device scratch during assembly: element-pair blocks of
+ * rounds of test triangles (about 4 GB, at least 512 triangles x nt x 96 bytes), released
+ * before returning.
  * NAT_BEM_EINVAL: as for nat_bem_assemble, a vertex that belongs to no triangle, nt > 65536.
  * NAT_BEM_ENOMEM / NAT_BEM_ECUDA as for nat_bem_assemble.
  */

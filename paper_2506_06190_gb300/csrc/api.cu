@@ -128,8 +128,8 @@ static nat_bem_status check_opts(const nat_bem_opts& o) {
 using namespace natbem;
 
 namespace {
-// Galerkin assembly keeps element-pair blocks of min(nt, 4096) test triangles x nt trial
-// triangles (96 bytes each) as scratch: 25 GB at this size.
+// Galerkin assembly keeps element-pair blocks of at least 512 test triangles x nt trial
+// triangles (96 bytes each) as scratch: 3.2 GB at this size.
 constexpr int64_t kGalerkinMaxTriangles = 65536;
 }  // namespace
 

@@ -8,10 +8,12 @@
 // Every entry is a sum over element pairs (tau test, sigma trial). The kernels compute, per
 // pair, the 3 x 3 block of L and the 3 entries of R that the pair contributes (k_gal_regular for
 // pairs sharing no vertex, 7 x 7 points; k_gal_singular for pairs sharing a vertex, an edge, or
-// identical, a warp each over 4^4 Gauss points per region of the transformed 4-cube), into a
-// scratch array of pair blocks. k_gal_gather_L / k_gal_gather_R then sum, for every vertex i and
-// column (vertex j, or triangle s), the blocks of the triangles around i (and around j) in a
-// fixed order: the result does not depend on scheduling. FP32 arithmetic throughout: near the
+// identical, a warp each over 4^4 Gauss points per region of the transformed 4-cube), into
+// scratch arrays of pair blocks. The gathers then sum, for every vertex i and column (vertex j,
+// or triangle s), the blocks of the triangles around i (and around j) in a fixed order, so the
+// result does not depend on scheduling: k_gal_rowsum_L first sums each test triangle's row over
+// the triangles around every column vertex (reading each pair block once), k_gal_gather_L and
+// k_gal_gather_R then sum over the triangles around each row vertex. FP32 arithmetic throughout: near the
 // singularity x - y is formed from the transformed coordinates (a radius times a bounded
 // vector), and for regular pairs from the centroid difference (hi/lo pairs) plus the points'
 // offsets, so no cancellation occurs.
@@ -30,7 +32,7 @@ namespace natbem {
 namespace {
 constexpr int kGalSing = 4;          // Gauss-Legendre points per dimension on singular pairs
 constexpr int kGalVals = 12;         // per pair: L block (a, b) at 3a + b, then R entries (a)
-constexpr int kGalChunk = 4096;      // test triangles per round (scratch: chunk x nt pair blocks)
+constexpr double kGalScratch = 4e9;  // bytes of pair blocks per round of test triangles
 constexpr float kTwoPiHi = 6.28318548202514648f;
 constexpr float kTwoPiLo = -1.7484555314695172e-7f;
 constexpr float kInvTwoPi = 0.159154943091895336f;
@@ -132,10 +134,15 @@ __device__ __forceinline__ void gal_finish(const GalAcc& A, float k, float nn, c
   }
 }
 
-__device__ __forceinline__ void gal_store(float2* part, size_t slot, const float2 (&v)[kGalVals]) {
-  float4* p = reinterpret_cast<float4*>(part + slot * kGalVals);
+// Pair (t, s) of the round starting at t0: the L block at partL[((t - t0) nt + s) 9 + 3a + b],
+// the R entries at partR[((t - t0) 3 + a) nt + s] (contiguous over s for the R gather).
+__device__ __forceinline__ void gal_store(float2* partL, float2* partR, int nt, int tr, int s,
+                                          const float2 (&v)[kGalVals]) {
+  float2* pl = partL + ((size_t)tr * nt + s) * 9;
 #pragma unroll
-  for (int i = 0; i < kGalVals / 2; ++i) p[i] = make_float4(v[2 * i].x, v[2 * i].y, v[2 * i + 1].x, v[2 * i + 1].y);
+  for (int i = 0; i < 9; ++i) pl[i] = v[i];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) partR[((size_t)tr * 3 + a) * nt + s] = v[9 + a];
 }
 }  // namespace
 
@@ -174,7 +181,7 @@ __global__ void k_gal_geometry(const double* __restrict__ tri, const double* __r
 __global__ void __launch_bounds__(256)
 k_gal_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo, const float4* __restrict__ nrm,
               const float4* __restrict__ qp, const int4* __restrict__ vid, const float4* __restrict__ curl,
-              int nt, int t0, float k, float2* __restrict__ part) {
+              int nt, int t0, float k, float2* __restrict__ partL, float2* __restrict__ partR) {
   const int t = t0 + blockIdx.y;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nt) return;
@@ -243,7 +250,7 @@ k_gal_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo, 
   }
   float2 out[kGalVals];
   gal_finish(A, k, nx.x * ny.x + nx.y * ny.y + nx.z * ny.z, cc, out);
-  gal_store(part, (size_t)blockIdx.y * nt + s, out);
+  gal_store(partL, partR, nt, blockIdx.y, s, out);
 }
 
 namespace {
@@ -263,7 +270,8 @@ __device__ __forceinline__ float3 f3sub(const double* a, const double* b) {
 __global__ void __launch_bounds__(256)
 k_gal_singular(const int2* __restrict__ near_pairs, int64_t n_near, const double* __restrict__ tri,
                const double* __restrict__ nrm64, const double* __restrict__ area, const int4* __restrict__ vid,
-               const float4* __restrict__ curl, int nt, int t0, int t1, float k, float2* __restrict__ part) {
+               const float4* __restrict__ curl, int nt, int t0, int t1, float k, float2* __restrict__ partL,
+               float2* __restrict__ partR) {
   const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= n_near + nt) return;
@@ -418,14 +426,40 @@ k_gal_singular(const int2* __restrict__ near_pairs, int64_t n_near, const double
       for (int b = 0; b < 3; ++b) out[3 * a + b].x += a == b ? 2.f * m : m;
     for (int a = 0; a < 3; ++a) out[9 + a].y -= (float)(At / 6.0) / k;
   }
-  gal_store(part, (size_t)(t - t0) * nt + s, out);
+  gal_store(partL, partR, nt, t - t0, s, out);
 }
 
-// L[i][j] (+)= sum over the triangles tau around i (local index a) and sigma around j (local
-// index b) of the pair blocks; adjacency lists in increasing triangle order. Columns past nv
-// are zero. With Lb, the BF16 copy is written too (on the last chunk).
+// First stage of the L gather, one block row per test triangle tau of the round: for every
+// column vertex j and local test index a, P2[(tau - t0) 3 + a][j] = sum over the triangles sigma
+// around j (local index b) of the pair blocks (tau, sigma)[a][b]. Each block reads its own row
+// of pair blocks, so every pair block is read from memory once.
 __global__ void __launch_bounds__(256)
-k_gal_gather_L(const float2* __restrict__ part, int nt, int t0, int t1, const int* __restrict__ adj_ptr,
+k_gal_rowsum_L(const float2* __restrict__ partL, int nt, const int* __restrict__ adj_ptr,
+               const int2* __restrict__ adj, int nv, int ldv, float2* __restrict__ P2) {
+  const int tr = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nv) return;
+  const float2* row = partL + (size_t)tr * nt * 9;
+  float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int v = adj_ptr[j]; v < adj_ptr[j + 1]; ++v) {
+    const int2 sb = adj[v];
+    const float2* blk = row + (size_t)sb.x * 9 + sb.y;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float2 x = blk[3 * a];
+      acc[a].x += x.x;
+      acc[a].y += x.y;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) P2[((size_t)tr * 3 + a) * ldv + j] = acc[a];
+}
+
+// L[i][j] (+)= sum over the triangles tau around i (local index a) in the round of
+// P2[(tau - t0) 3 + a][j]; adjacency lists in increasing triangle order. Columns past nv are
+// zero. With Lb, the BF16 copy is written too (on the last round).
+__global__ void __launch_bounds__(256)
+k_gal_gather_L(const float2* __restrict__ P2, int t0, int t1, const int* __restrict__ adj_ptr,
                const int2* __restrict__ adj, int nv, int ldv, int accumulate, float2* __restrict__ L,
                uint32_t* __restrict__ Lb) {
   const int i = blockIdx.y;
@@ -437,22 +471,18 @@ k_gal_gather_L(const float2* __restrict__ part, int nt, int t0, int t1, const in
     for (int u = adj_ptr[i]; u < adj_ptr[i + 1]; ++u) {
       const int2 ta = adj[u];
       if (ta.x < t0 || ta.x >= t1) continue;
-      const float2* row = part + (size_t)(ta.x - t0) * nt * kGalVals + 3 * ta.y;
-      for (int v = adj_ptr[j]; v < adj_ptr[j + 1]; ++v) {
-        const int2 sb = adj[v];
-        const float2 x = row[(size_t)sb.x * kGalVals + sb.y];
-        acc.x += x.x;
-        acc.y += x.y;
-      }
+      const float2 x = P2[((size_t)(ta.x - t0) * 3 + ta.y) * ldv + j];
+      acc.x += x.x;
+      acc.y += x.y;
     }
   }
   L[off] = acc;
   if (Lb) Lb[off] = gal_pack_bf16(acc.x, acc.y);
 }
 
-// R[i][s] (+)= sum over the triangles tau around i of the pair entries (tau, s, a).
+// R[i][s] (+)= sum over the triangles tau around i in the round of partR[(tau - t0) 3 + a][s].
 __global__ void __launch_bounds__(256)
-k_gal_gather_R(const float2* __restrict__ part, int nt, int t0, int t1, const int* __restrict__ adj_ptr,
+k_gal_gather_R(const float2* __restrict__ partR, int nt, int t0, int t1, const int* __restrict__ adj_ptr,
                const int2* __restrict__ adj, int ldr, int accumulate, float2* __restrict__ R) {
   const int i = blockIdx.y;
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,7 +493,7 @@ k_gal_gather_R(const float2* __restrict__ part, int nt, int t0, int t1, const in
     for (int u = adj_ptr[i]; u < adj_ptr[i + 1]; ++u) {
       const int2 ta = adj[u];
       if (ta.x < t0 || ta.x >= t1) continue;
-      const float2 x = part[((size_t)(ta.x - t0) * nt + s) * kGalVals + 9 + ta.y];
+      const float2 x = partR[((size_t)(ta.x - t0) * 3 + ta.y) * nt + s];
       acc.x += x.x;
       acc.y += x.y;
     }
@@ -559,28 +589,35 @@ nat_bem_status galerkin_assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const Galerkin& G = op->gal;
   const int nt = (int)g.n, nv = (int)op->n, ldv = (int)g.ld, ldr = (int)op->ldr;
   const float k = (float)op->k;
-  const int chunk = std::min(nt, kGalChunk);
-  float2* part = nullptr;
-  NB_TRY(dev_alloc_n(&part, (size_t)chunk * nt * kGalVals, s));
-  nat_bem_status st = NAT_BEM_OK;
+  // rounds of test triangles: pair blocks (9 + 3 values) and first-stage row sums (3 ldv)
+  const double per_row = (double)nt * kGalVals * sizeof(float2) + 3.0 * ldv * sizeof(float2);
+  const int chunk = std::max(1, std::min(nt, std::max(512, (int)(kGalScratch / per_row))));
+  float2 *partL = nullptr, *partR = nullptr, *P2 = nullptr;
+  nat_bem_status st = dev_alloc_n(&partL, (size_t)chunk * nt * 9, s);
+  if (st == NAT_BEM_OK) st = dev_alloc_n(&partR, (size_t)chunk * nt * 3, s);
+  if (st == NAT_BEM_OK) st = dev_alloc_n(&P2, (size_t)chunk * 3 * ldv, s);
   for (int t0 = 0; t0 < nt && st == NAT_BEM_OK; t0 += chunk) {
     const int t1 = std::min(nt, t0 + chunk);
     const bool last = t1 == nt;
     NB_LAUNCH("gal_regular", s, k_gal_regular<<<dim3((unsigned)((nt + 255) / 256), (unsigned)(t1 - t0)), 256, 0, s>>>(
-        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, G.curl, nt, t0, k, part));
+        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, G.curl, nt, t0, k, partL, partR));
     const int64_t warps = g.n_near + nt;
     NB_LAUNCH("gal_singular", s, k_gal_singular<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(
-        g.near_pairs, g.n_near, g.tri, g.nrm64, g.area, g.vid, G.curl, nt, t0, t1, k, part));
+        g.near_pairs, g.n_near, g.tri, g.nrm64, g.area, g.vid, G.curl, nt, t0, t1, k, partL, partR));
+    NB_LAUNCH("gal_rowsum_L", s, k_gal_rowsum_L<<<dim3((unsigned)((nv + 255) / 256), (unsigned)(t1 - t0)), 256, 0, s>>>(
+        partL, nt, G.adj_ptr, G.adj, nv, ldv, P2));
     NB_LAUNCH("gal_gather_L", s, k_gal_gather_L<<<dim3((unsigned)((ldv + 255) / 256), (unsigned)nv), 256, 0, s>>>(
-        part, nt, t0, t1, G.adj_ptr, G.adj, nv, ldv, t0 > 0 ? 1 : 0, op->L, last ? op->Lb : nullptr));
+        P2, t0, t1, G.adj_ptr, G.adj, nv, ldv, t0 > 0 ? 1 : 0, op->L, last ? op->Lb : nullptr));
     NB_LAUNCH("gal_gather_R", s, k_gal_gather_R<<<dim3((unsigned)((ldr + 255) / 256), (unsigned)nv), 256, 0, s>>>(
-        part, nt, t0, t1, G.adj_ptr, G.adj, ldr, t0 > 0 ? 1 : 0, op->R));
+        partR, nt, t0, t1, G.adj_ptr, G.adj, ldr, t0 > 0 ? 1 : 0, op->R));
     if (cudaGetLastError() != cudaSuccess) {
       set_error("Galerkin assembly: launch failed");
       st = NAT_BEM_ECUDA;
     }
   }
-  dev_free(part, s);
+  dev_free(partL, s);
+  dev_free(partR, s);
+  dev_free(P2, s);
   return st;
 }
 

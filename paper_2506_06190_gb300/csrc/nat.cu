@@ -164,13 +164,16 @@ __device__ __forceinline__ int64_t nat_index(int i, int j, int k, int N, int log
 // Encode query q into row t of A: the K steps layer 0 reads (2 K0 chunks of 16 bytes).
 // dense_mask bit l: level l is stored densely.
 template <int D>
-__device__ __forceinline__ void nat_encode(const float* __restrict__ x, int64_t q, int64_t n,
+__device__ __forceinline__ void nat_load_x(const float* __restrict__ x, int64_t q, int64_t n, float (&xv)[D]) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) xv[d] = q < n ? __ldg(x + q * D + d) : 0.f;
+}
+
+template <int D>
+__device__ __forceinline__ void nat_encode(const float (&xv)[D], int64_t q, int64_t n,
                                            const float4* __restrict__ tables, const int (&offs)[4],
                                            uint32_t hmask, int dense_mask, uint8_t* sA, int t) {
   constexpr int K0 = nat_k0(D);
-  float xv[D];
-#pragma unroll
-  for (int d = 0; d < D; ++d) xv[d] = q < n ? __ldg(x + q * D + d) : 0.f;
   uint32_t pk[8 * K0];
 #pragma unroll
   for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;
@@ -292,11 +295,19 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const float4* __restrict__
   uint32_t phase = 0;
   bool ok_all = true;
 
-  for (int64_t tile = (int64_t)blockIdx.x * G + g;; tile += (int64_t)gridDim.x * G) {
+  // the next tile's inputs are requested before this tile's layers run
+  const int64_t tstride = (int64_t)gridDim.x * G;
+  float xnext[D];
+  nat_load_x<D>(x, ((int64_t)blockIdx.x * G + g) * 128 + t, n, xnext);
+  for (int64_t tile = (int64_t)blockIdx.x * G + g;; tile += tstride) {
     const int64_t q0 = tile * 128;
     if (q0 >= n) break;  // uniform over the group
     const int64_t q = q0 + t;
-    nat_encode<D>(x, q, n, tables, offs, hmask, dense_mask, sA, t);
+    float xv[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) xv[d] = xnext[d];
+    nat_encode<D>(xv, q, n, tables, offs, hmask, dense_mask, sA, t);
+    nat_load_x<D>(x, q + tstride * 128, n, xnext);
 #pragma unroll
     for (int l = 0; l <= kNatHidden; ++l) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A visible to the tensor cores
