@@ -387,6 +387,12 @@ NAT_BEM_API void nat_bem_trace_reset(void);
 NAT_BEM_API int64_t nat_bem_trace_launches(void);
 NAT_BEM_API nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms,
                                                 int64_t* launches);
+/* Per-launch device times (ms, in launch order) of the traced kernels named exactly `name`:
+ * the first min(cap, count) go to out_ms, *count receives how many there are. Lets a caller
+ * tell launches that did work from those that exited at once (a GMRES iteration of a captured
+ * chunk after convergence). NAT_BEM_EINVAL: name NULL, cap < 0, out_ms NULL with cap > 0. */
+NAT_BEM_API nat_bem_status nat_bem_trace_durations(const char* name, float* out_ms, int64_t cap,
+                                                   int64_t* count);
 
 /*
  * Neural acoustic transfer field (Sec. 3.3, Eq. 3 and 4; Sec. 3.4): the learned map from the

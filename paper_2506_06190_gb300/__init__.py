@@ -38,7 +38,7 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
             "nat_bem_far_field", "nat_bem_sample_field", "nat_bem_gemv_variant", "nat_field_create",
             "nat_field_forward", "nat_field_destroy", "nat_bem_assemble_galerkin",
-            "nat_bem_op_neumann_size"]
+            "nat_bem_op_neumann_size", "nat_bem_trace_durations"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -139,6 +139,8 @@ def lib():
         L.nat_bem_assemble_galerkin.restype = ctypes.c_int
         L.nat_bem_op_neumann_size.argtypes = [vp]
         L.nat_bem_op_neumann_size.restype = i64
+        L.nat_bem_trace_durations.argtypes = [ctypes.c_char_p, vp, i64, ctypes.POINTER(i64)]
+        L.nat_bem_trace_durations.restype = ctypes.c_int
         L.nat_bem_gemv_variant.argtypes = [i64]
         L.nat_bem_gemv_variant.restype = i32
         L.nat_field_create.argtypes = [i32, i32, i32, vp, vp, vp, vp, ctypes.POINTER(vp)]
@@ -529,6 +531,17 @@ def nat_bem_trace_reset():
 
 def nat_bem_trace_launches() -> int:
     return int(lib().nat_bem_trace_launches())
+
+
+def nat_bem_trace_durations(name: str) -> np.ndarray:
+    """Per-launch device times (ms) of the traced kernels named exactly `name`."""
+    c = ctypes.c_int64(0)
+    _check(lib().nat_bem_trace_durations(name.encode(), None, 0, ctypes.byref(c)))
+    out = np.zeros(c.value, dtype=np.float32)
+    if c.value:
+        _check(lib().nat_bem_trace_durations(name.encode(), ctypes.c_void_p(out.ctypes.data), c.value,
+                                             ctypes.byref(c)))
+    return out
 
 
 def nat_bem_trace_kernel(name: str = ""):

@@ -124,4 +124,28 @@ nat_bem_status nat_bem_trace_kernel(const char* name, double* total_ms, int64_t*
   return NAT_BEM_OK;
 }
 
+nat_bem_status nat_bem_trace_durations(const char* name, float* out_ms, int64_t cap, int64_t* count) {
+  clear_error();
+  if (!name || (cap > 0 && !out_ms) || cap < 0) {
+    set_error("nat_bem_trace_durations: bad arguments");
+    return NAT_BEM_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  int64_t c = 0;
+  for (auto& r : g_recs) {
+    if (std::string(r.name) != name) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) {
+      set_error(std::string("trace: ") + cudaGetErrorString(e));
+      return NAT_BEM_ECUDA;
+    }
+    if (c < cap) out_ms[c] = ms;
+    ++c;
+  }
+  if (count) *count = c;
+  return NAT_BEM_OK;
+}
+
 }  // extern "C"
