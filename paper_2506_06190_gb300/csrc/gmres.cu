@@ -1731,14 +1731,89 @@ static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, con
   return gemv_launch(variant, name, A, n, ld, x, y, nrhs, done, scal, e, s);
 }
 
+// BF16-copy GEMV variants (rows per block, 16-byte loads per row in flight per thread) and
+// their autotuner, which the solver runs before the first mixed sweep of a size class (outside
+// any graph capture); until then, and when no tuning ran, the first variant is used.
+enum Bf16Variant { kBf16R2U2 = 0, kBf16R2U4, kBf16R4U2, kBf16R4U1, kBf16Variants };
+
+static nat_bem_status gemv_bf16_launch(int variant, const char* name, const uint32_t* A, int n, int ld,
+                                       const float2* x, double2* y, int nrhs, const int* done,
+                                       const int* scal, cudaStream_t s) {
+  const int rows = (variant == kBf16R4U2 || variant == kBf16R4U1) ? 4 : 2;
+  dim3 grid((n + rows - 1) / rows, nrhs);
+  switch (variant) {
+    case kBf16R2U4:
+      NB_LAUNCH(name, s, k_gemv_bf16<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      break;
+    case kBf16R4U2:
+      NB_LAUNCH(name, s, k_gemv_bf16<4, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      break;
+    case kBf16R4U1:
+      NB_LAUNCH(name, s, k_gemv_bf16<4, 1><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      break;
+    default:
+      NB_LAUNCH(name, s, k_gemv_bf16<2, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+  }
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+namespace {
+std::map<std::pair<int, int64_t>, int> g_tuned_bf16;  // (device, n rounded to 1024) -> variant
+}  // namespace
+
+static int gemv_bf16_lookup(int n) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned_bf16.find(std::make_pair(dev, (int64_t)((n + 1023) / 1024)));
+  return it == g_tuned_bf16.end() ? kBf16R2U2 : it->second;
+}
+
+// Times every BF16 variant on the operator copy (x and y are scratch of the solve), like
+// gemv_variant: a warm-up round, four interleaved rounds, each variant's minimum; the first
+// variant wins ties within 2%. NATBEM_GEMV_BF16_VARIANT=v bypasses it.
+static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, double2* y, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_pair(dev, (int64_t)((n + 1023) / 1024));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tuned_bf16.count(key)) return;
+  }
+  int best = kBf16R2U2;
+  if (const char* env = std::getenv("NATBEM_GEMV_BF16_VARIANT")) {
+    const int v = std::atoi(env);
+    if (v >= 0 && v < kBf16Variants) best = v;
+  } else {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float vmin[kBf16Variants];
+    for (int v = 0; v < kBf16Variants; ++v) vmin[v] = 1e30f;
+    for (int round = 0; round < 5; ++round)
+      for (int v = 0; v < kBf16Variants; ++v) {
+        float ms = 1e30f;
+        cudaEventRecord(e0, s);
+        gemv_bf16_launch(v, "gemv_bf16_tune", A, n, ld, x, y, 1, nullptr, nullptr, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (round > 0) vmin[v] = std::min(vmin[v], ms);
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int v = 1; v < kBf16Variants; ++v)
+      if (vmin[v] < vmin[best] && vmin[v] < 0.98f * vmin[kBf16R2U2]) best = v;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned_bf16[key] = best;
+}
+
 static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int ld,
                                 const float2* x, double2* y, int nrhs, const int* done,
                                 const int* scal, cudaStream_t s) {
-  constexpr int kRows = 2;
-  dim3 grid((n + kRows - 1) / kRows, nrhs);
-  NB_LAUNCH(name, s, k_gemv_bf16<kRows, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
-  NB_CHECK_LAUNCH();
-  return NAT_BEM_OK;
+  return gemv_bf16_launch(gemv_bf16_lookup(n), name, A, n, ld, x, y, nrhs, done, scal, s);
 }
 
 // One GMRES run on the right-hand sides in a.b (x0 = 0): init, iterations until every RHS
@@ -1954,6 +2029,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = nrhs == 1 ? kEngineGemvBf16 : kEngineBf16;
   if (o.prec == NAT_BEM_PREC_MIXED_TF32 && nrhs > 1) inner = kEngineTf32;
   const bool mixed = inner != accurate;
+  if (inner == kEngineGemvBf16) gemv_bf16_tune(op->Lb, n, (int)op->geo.ld, ws->gin, ws->w, s);
   if (!mixed) {
     GArgs a = make_args(op, ws, op->L);
     a.maxit = o.max_iter;
