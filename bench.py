@@ -628,7 +628,7 @@ def run_nat(args):
             "roofline": {"kernel": "nat_forward", "bound": "tensor", "achieved": achieved,
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": achieved / peaks["bf16_tflops"],
-                         "traffic": NCU_TRAFFIC_NAT_PER_MQUERY * n / (1 << 20),
+                         "traffic": (NCU_TRAFFIC_NAT_PER_MQUERY * n / (1 << 20)) if NCU_TRAFFIC_NAT_PER_MQUERY else None,
                          "flops_per_query": flops_q, "peak_source": f"{peak_kind} (bf16_tflops)"},
             "clocks": clk.summary()}
     if args.cpu:
@@ -655,7 +655,7 @@ def _numpy_threads():
 
 # DRAM bytes (read + write) of one k_nat_forward launch per 2^20 queries, from the committed ncu
 # capture (profiles/k_nat_forward_nat_inference_1Mqueries.md); traffic grows with the queries.
-NCU_TRAFFIC_NAT_PER_MQUERY = 29.014016e6 + 25.856e6
+NCU_TRAFFIC_NAT_PER_MQUERY = 28.127232e6 + 52.992e6
 
 
 def run_uneven(args):

@@ -412,7 +412,8 @@ NAT_BEM_API nat_bem_status nat_bem_trace_durations(const char* name, float* out_
  * nat_field_create copies the parameters to the device of the current context (host or device
  * pointers; the caller keeps ownership of its arrays):
  *   tables  float32, the four levels' rows one level after the other, 4 features per row;
- *           level l has min((N_l + 1)^3, 2^table_log2) rows;
+ *           level l has min((N_l + 1)^3, 2^table_log2) rows. The field keeps them in half
+ *           precision (rounded to nearest, as tiny-cuda-nn stores grid parameters);
  *   weights BF16 bit patterns (uint16), row-major [out][in]: four 128 x 128 hidden layers, then
  *           the n_out x 128 output layer;
  *   biases  float32: 4 x 128, then n_out.

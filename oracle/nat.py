@@ -15,7 +15,9 @@ The network, as this build reads the paper (Sec. 3.3, Eq. 3 and 4; Sec. 3.4):
     sin(2^l pi x_d), cos(2^l pi x_d), l = 0..5;
   * MLP on [G, P(v), P(f)] (zero-padded to 128): four 128-wide layers with ReLU, then a linear
     layer to the outputs (Sec. 3.4).
-The GPU kernel feeds the tensor cores BF16 activations and weights with FP32 accumulation; this
+The grid tables are held in half precision, as tiny-cuda-nn (the paper's implementation, Sec. 3.4)
+stores its grid parameters: `encode` rounds them to FP16 first, like the library does when a
+field is created. The GPU kernel feeds the tensor cores BF16 activations and weights with FP32 accumulation; this
 reference takes the same BF16 weights and rounds every layer's input to BF16 the same way, and
 computes everything else in FP64.
 """
@@ -87,9 +89,16 @@ def positional(x):
     return np.stack(cols, axis=1)
 
 
+def to_half(a):
+    """Round to the nearest FP16 value (ties to even) through FP32, returned as float64: the
+    grid tables' storage precision."""
+    return np.asarray(a, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
 def encode(x, tables, table_log2):
-    """The 128-wide MLP input: 16 grid features of (x_0, x_1, x_2), the positional encoding of
-    x_3 onwards (v, then f), zeros."""
+    """The 128-wide MLP input: 16 grid features of (x_0, x_1, x_2) from the half-precision
+    tables, the positional encoding of x_3 onwards (v, then f), zeros."""
+    tables = [to_half(t) for t in tables]
     e = np.concatenate([grid_features(x[:, :3], tables, table_log2), positional(x[:, 3:])], axis=1)
     if e.shape[1] > WIDTH:
         raise ValueError("too many inputs for a 128-wide first layer")
@@ -108,8 +117,7 @@ def forward(x, tables, weights, biases, table_log2):
 def random_model(n_cond=2, n_out=8, table_log2=18, seed=0):
     """Seeded random parameters of the shapes above (BF16 weights, FP32 tables and biases)."""
     rng = np.random.default_rng(seed)
-    tables = [rng.uniform(-1.0, 1.0, size=(level_size(N, table_log2), FEATURES)).astype(np.float32).astype(np.float64)
-              for N in LEVELS]
+    tables = [to_half(rng.uniform(-1.0, 1.0, size=(level_size(N, table_log2), FEATURES))) for N in LEVELS]
     weights, biases = [], []
     for l in range(HIDDEN + 1):
         n_o = n_out if l == HIDDEN else WIDTH

@@ -18,8 +18,11 @@
 //   output   the last layer (N = n_out rounded up to 16) plus bias goes to global memory (FP32).
 // The weights stay in shared memory for the kernel's lifetime (at most 160 KB) and the biases
 // live in the kernel's parameter space (uniform reads through the constant cache), so HBM only
-// carries the queries, the grid tables (through L2) and the outputs.
+// carries the queries, the grid tables (through L2) and the outputs. The tables are half
+// precision (as tiny-cuda-nn stores its grid parameters); a dense level is laid out so that the
+// four vertices of a cell face at one z share a 32-byte sector.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -56,8 +59,11 @@ struct NatBias {
 
 struct nat_field {
   int32_t n_cond = 0, n_out = 0, n16 = 0, table_log2 = 0;
-  float4* tables = nullptr;     // the four levels' rows, level after level (4 features each)
-  int64_t level_off[4] = {0, 0, 0, 0};
+  uint2* tables = nullptr;      // the four levels in half precision (4 features = 8 bytes per
+                                // vertex): a dense level as quads of the (i, j), (i+1, j), (i, j+1),
+                                // (i+1, j+1) vertices at each z (32 bytes, one sector); a hashed
+                                // level as its rows
+  int64_t level_off[4] = {0, 0, 0, 0};  // in 8-byte units, multiples of 4
   uint16_t* weights = nullptr;  // BF16 [out][in]: 4 x 128 x 128, then n16 x 128 (rows >= n_out zero)
   natbem::NatBias bias{};       // host copy, passed by value to the kernel
   int device = 0;
@@ -152,14 +158,6 @@ __device__ __forceinline__ void nat_tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Table row of vertex (i, j, k) of a level with N cells per axis: dense when all (N+1)^3
-// vertices fit the table, else the spatial hash (i * 1) xor (j * p1) xor (k * p2) mod T.
-__device__ __forceinline__ int64_t nat_index(int i, int j, int k, int N, int log2) {
-  const int64_t V = (int64_t)(N + 1) * (N + 1) * (N + 1);
-  if (V <= ((int64_t)1 << log2)) return (int64_t)i + (int64_t)(N + 1) * (j + (int64_t)(N + 1) * k);
-  const uint32_t h = (uint32_t)i ^ ((uint32_t)j * kPrime1) ^ ((uint32_t)k * kPrime2);
-  return (int64_t)(h & ((1u << log2) - 1u));
-}
 
 // Encode query q into row t of A: the K steps layer 0 reads (2 K0 chunks of 16 bytes).
 // dense_mask bit l: level l is stored densely.
@@ -169,9 +167,16 @@ __device__ __forceinline__ void nat_load_x(const float* __restrict__ x, int64_t 
   for (int d = 0; d < D; ++d) xv[d] = q < n ? __ldg(x + q * D + d) : 0.f;
 }
 
+// The four features of a vertex: two half2 in 8 bytes.
+__device__ __forceinline__ float4 nat_h4(uint32_t lo, uint32_t hi) {
+  const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&hi));
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <int D>
 __device__ __forceinline__ void nat_encode(const float (&xv)[D], int64_t q, int64_t n,
-                                           const float4* __restrict__ tables, const int (&offs)[4],
+                                           const uint2* __restrict__ tables, const int (&offs)[4],
                                            uint32_t hmask, int dense_mask, uint8_t* sA, int t) {
   constexpr int K0 = nat_k0(D);
   uint32_t pk[8 * K0];
@@ -190,29 +195,41 @@ __device__ __forceinline__ void nat_encode(const float (&xv)[D], int64_t q, int6
       w0[a] = 1.f - w1[a];
     }
     const float wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
-    uint32_t idx[8];
+    float4 v[8];  // corner c = di + 2 dj + 4 dk
     if (dense_mask & (1 << lvl)) {
-      const uint32_t S1 = (uint32_t)(N + 1), S2 = S1 * S1;
-      const uint32_t b = (uint32_t)i0[0] + S1 * ((uint32_t)i0[1] + S1 * (uint32_t)i0[2]);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) idx[c] = b + (c & 1) + ((c >> 1) & 1) * S1 + (c >> 2) * S2;
+      // the quads at z = k and z = k + 1: four 16-byte loads from two 32-byte sectors
+      const uint4* tq = reinterpret_cast<const uint4*>(tables + offs[lvl]);
+      const uint32_t q0 = (uint32_t)i0[0] + (uint32_t)N * ((uint32_t)i0[1] + (uint32_t)N * (uint32_t)i0[2]);
+      const uint32_t q1 = q0 + (uint32_t)(N * N);
+      const uint4 a = __ldg(tq + 2 * q0), b = __ldg(tq + 2 * q0 + 1);
+      const uint4 c = __ldg(tq + 2 * q1), d = __ldg(tq + 2 * q1 + 1);
+      v[0] = nat_h4(a.x, a.y);
+      v[1] = nat_h4(a.z, a.w);
+      v[2] = nat_h4(b.x, b.y);
+      v[3] = nat_h4(b.z, b.w);
+      v[4] = nat_h4(c.x, c.y);
+      v[5] = nat_h4(c.z, c.w);
+      v[6] = nat_h4(d.x, d.y);
+      v[7] = nat_h4(d.z, d.w);
     } else {
+      const uint2* tl = tables + offs[lvl];
       const uint32_t hx[2] = {(uint32_t)i0[0], (uint32_t)i0[0] + 1u};
       const uint32_t hy[2] = {(uint32_t)i0[1] * kPrime1, ((uint32_t)i0[1] + 1u) * kPrime1};
       const uint32_t hz[2] = {(uint32_t)i0[2] * kPrime2, ((uint32_t)i0[2] + 1u) * kPrime2};
+      uint2 u[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) idx[c] = (hx[c & 1] ^ hy[(c >> 1) & 1] ^ hz[c >> 2]) & hmask;
+      for (int c = 0; c < 8; ++c) u[c] = __ldg(tl + ((hx[c & 1] ^ hy[(c >> 1) & 1] ^ hz[c >> 2]) & hmask));
+#pragma unroll
+      for (int c = 0; c < 8; ++c) v[c] = nat_h4(u[c].x, u[c].y);
     }
-    const float4* tl = tables + offs[lvl];
     float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       const float wt = wxy[c & 3] * (c >> 2 ? w1[2] : w0[2]);
-      const float4 v = __ldg(tl + idx[c]);
-      f0 = fmaf(wt, v.x, f0);
-      f1 = fmaf(wt, v.y, f1);
-      f2 = fmaf(wt, v.z, f2);
-      f3 = fmaf(wt, v.w, f3);
+      f0 = fmaf(wt, v[c].x, f0);
+      f1 = fmaf(wt, v[c].y, f1);
+      f2 = fmaf(wt, v[c].z, f2);
+      f3 = fmaf(wt, v[c].w, f3);
     }
     pk[2 * lvl] = pack2(f0, f1);
     pk[2 * lvl + 1] = pack2(f2, f3);
@@ -239,7 +256,7 @@ __device__ __forceinline__ void nat_encode(const float (&xv)[D], int64_t q, int6
 // G groups of four warps per block, each with its own 128-query tile.
 template <int D, int G>
 __global__ void __launch_bounds__(G * 128, 1)
-k_nat_forward(const float* __restrict__ x, int64_t n, const float4* __restrict__ tables, int off1, int off2,
+k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ tables, int off1, int off2,
               int off3, int log2, int dense_mask, const uint16_t* __restrict__ weights, int n_out, int n16,
               float* __restrict__ out, int* __restrict__ err, const __grid_constant__ NatBias P) {
   constexpr int K0 = nat_k0(D);
@@ -395,6 +412,30 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const float4* __restrict__
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tmem_slot), "r"(kCols));
 }
 
+// The caller's FP32 table rows (level after level, min((N+1)^3, 2^log2) rows each) to the
+// half-precision device layout (round to nearest): a dense level as quads, one thread per quad
+// (i, j, k), i, j < N, k <= N; a hashed level row by row.
+__global__ void k_nat_pack(const float4* __restrict__ in, int N, int dense, int64_t rows, uint2* __restrict__ out) {
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  auto h4 = [](float4 v) {
+    __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+    return make_uint2(*reinterpret_cast<uint32_t*>(&a), *reinterpret_cast<uint32_t*>(&b));
+  };
+  if (!dense) {
+    if (u < rows) out[u] = h4(in[u]);
+    return;
+  }
+  const int64_t quads = (int64_t)N * N * (N + 1);
+  if (u >= quads) return;
+  const int i = (int)(u % N), j = (int)((u / N) % N), k = (int)(u / ((int64_t)N * N));
+  const int64_t S1 = N + 1;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int64_t r = (i + (c & 1)) + S1 * ((j + (c >> 1)) + S1 * k);
+    out[4 * u + c] = h4(in[r]);
+  }
+}
+
 template <int D>
 static nat_bem_status nat_launch_d(const nat_field* f, const float* dx, int64_t n, float* dout, cudaStream_t s,
                                    int sms, bool& attr_done) {
@@ -490,11 +531,20 @@ nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log
     f->table_log2 = table_log2;
     f->stream = s;
     cudaGetDevice(&f->device);
-    int64_t rows = 0;
+    // input rows per level, and the device layout's size per level (8-byte units)
+    int64_t rows = 0, units = 0;
+    int64_t in_off[4], in_rows[4];
+    bool dense[4];
     for (int l = 0; l < 4; ++l) {
-      f->level_off[l] = rows;
-      const int64_t v = (int64_t)(kNatLevels[l] + 1) * (kNatLevels[l] + 1) * (kNatLevels[l] + 1);
-      rows += std::min<int64_t>(v, (int64_t)1 << table_log2);
+      const int64_t N = kNatLevels[l];
+      const int64_t v = (N + 1) * (N + 1) * (N + 1);
+      dense[l] = v <= ((int64_t)1 << table_log2);
+      in_off[l] = rows;
+      in_rows[l] = std::min<int64_t>(v, (int64_t)1 << table_log2);
+      rows += in_rows[l];
+      f->level_off[l] = units;
+      units += dense[l] ? 4 * N * N * (N + 1) : in_rows[l];
+      units = (units + 3) / 4 * 4;
     }
     auto fail = [&](nat_bem_status st) {
       nat_field_destroy(f);
@@ -502,19 +552,32 @@ nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log
     };
     f->n16 = (n_out + 15) / 16 * 16;
     const size_t w_rows = (size_t)4 * 128 + (size_t)f->n16;
-    nat_bem_status st = dev_alloc_n(&f->tables, (size_t)rows, s);
+    const float4* din = nullptr;
+    float4* tin = nullptr;
+    nat_bem_status st = to_device(reinterpret_cast<const float4*>(tables), (size_t)rows, s, &din, &tin);
+    if (st == NAT_BEM_OK) st = dev_alloc_n(&f->tables, (size_t)units, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&f->weights, w_rows * 128, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&f->err, 1, s);
-    if (st != NAT_BEM_OK) return fail(st);
+    if (st != NAT_BEM_OK) {
+      dev_free(tin, s);
+      return fail(st);
+    }
+    for (int l = 0; l < 4; ++l) {
+      const int N = kNatLevels[l];
+      const int64_t work = dense[l] ? (int64_t)N * N * (N + 1) : in_rows[l];
+      k_nat_pack<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(din + in_off[l], N, dense[l] ? 1 : 0, in_rows[l],
+                                                                f->tables + f->level_off[l]);
+    }
     // weights: four 128 x 128 layers, then n_out x 128; the output layer is padded to n16 rows
     const size_t w_in = (size_t)4 * 128 * 128 + (size_t)n_out * 128;
     cudaError_t e = cudaMemsetAsync(f->weights, 0, w_rows * 128 * sizeof(uint16_t), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(f->err, 0, sizeof(int), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(f->tables, tables, (size_t)rows * sizeof(float4), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(f->weights, weights, w_in * sizeof(uint16_t), cudaMemcpyDefault, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(f->bias.b, biases, ((size_t)4 * 128 + n_out) * sizeof(float), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dev_free(tin, s);
     if (e != cudaSuccess) {
       set_error(std::string("nat_field_create: copy failed: ") + cudaGetErrorString(e));
       return fail(NAT_BEM_ECUDA);

@@ -99,3 +99,13 @@ def test_hidden_layers_apply_relu_and_round():
     # after two -I layers: relu(-relu(-e)) = 0 for every e, then relu(0 + 1) = 1, then 1 + 2^-12 -> 1
     assert np.allclose(out[:, 0], 128.0) and np.allclose(out[:, 1], 1.0)
     assert enc.shape == (32, 128)
+
+
+def test_tables_are_rounded_to_half():
+    """Table values are used at FP16 precision: a value between two FP16 numbers moves to the
+    nearest, and the encoding of a query on a vertex returns the rounded value."""
+    assert nat.to_half(1.0 + 2.0 ** -12)[()] == 1.0 and nat.to_half(1.0 + 3 * 2.0 ** -11)[()] == 1.0 + 2.0 ** -9
+    log2 = 12
+    tables = [np.full((nat.level_size(N, log2), 4), 1.0 + 2.0 ** -12) for N in nat.LEVELS]
+    e = nat.encode(np.array([[0.0, 0.0, 0.0, 0.5]]), tables, log2)
+    assert np.all(e[0, :16] == 1.0)
