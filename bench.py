@@ -655,7 +655,7 @@ def _numpy_threads():
 
 # DRAM bytes (read + write) of one k_nat_forward launch per 2^20 queries, from the committed ncu
 # capture (profiles/k_nat_forward_nat_inference_1Mqueries.md); traffic grows with the queries.
-NCU_TRAFFIC_NAT_PER_MQUERY = 28.127232e6 + 52.992e6
+NCU_TRAFFIC_NAT_PER_MQUERY = 28.127488e6 + 32.0e6
 
 
 def run_uneven(args):
