@@ -343,11 +343,15 @@ k_gal_singular(const int2* __restrict__ near_pairs, int64_t n_near, const double
     if (kind == 3) {
       // relative coordinate z on the hexagon T - T, sector `region`, Duffy (rho, w); x in the
       // homothetic triangle of scale 1 - rho by collapsed coordinates (a1, a1 a2)
-      const float hx[6] = {1.f, 1.f, 0.f, -1.f, -1.f, 0.f}, hy[6] = {0.f, 1.f, 1.f, 0.f, -1.f, -1.f};
+      // hexagon vertices (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1), by selects (no local array)
       const int r1 = region == 5 ? 0 : region + 1;
+      const float hx0 = region < 2 ? 1.f : (region == 2 || region == 5) ? 0.f : -1.f;
+      const float hy0 = (region == 0 || region == 3) ? 0.f : region < 3 ? 1.f : -1.f;
+      const float hx1 = r1 < 2 ? 1.f : (r1 == 2 || r1 == 5) ? 0.f : -1.f;
+      const float hy1 = (r1 == 0 || r1 == 3) ? 0.f : r1 < 3 ? 1.f : -1.f;
       const float rho = n0.x, wv = n1.x, a1 = n2.x, a2 = n3.x;
-      const float z1 = rho * fmaf(wv, hx[r1] - hx[region], hx[region]);
-      const float z2 = rho * fmaf(wv, hy[r1] - hy[region], hy[region]);
+      const float z1 = rho * fmaf(wv, hx1 - hx0, hx0);
+      const float z2 = rho * fmaf(wv, hy1 - hy0, hy0);
       const float ca = fmaxf(0.f, -z2), cb = fmaxf(0.f, z2 - z1);
       const float scale = 1.f - rho;
       const float xs = ca + cb + scale * a1, xt = ca + scale * (a1 * a2);

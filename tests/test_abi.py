@@ -156,3 +156,19 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(nb, "_lib", None)
     with pytest.raises(ImportError):
         nb.lib()
+
+
+def test_galerkin_rejects_bad_arguments(nb):
+    """Host-side checks of nat_bem_assemble_galerkin before any device call."""
+    L = nb.lib()
+    op = ctypes.c_void_p()
+    V = np.zeros((4, 3))
+    F = np.zeros((4, 3), np.int32)
+    pv, pf = ctypes.c_void_p(V.ctypes.data), ctypes.c_void_p(F.ctypes.data)
+    assert L.nat_bem_assemble_galerkin(None, 4, pf, 4, 1.0, None, None, ctypes.byref(op)) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_assemble_galerkin(pv, 4, pf, 4, 1.0, None, None, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_assemble_galerkin(pv, 4, pf, 4, -2.0, None, None, ctypes.byref(op)) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_assemble_galerkin(pv, 4, pf, 0, 1.0, None, None, ctypes.byref(op)) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_assemble_galerkin(pv, 4, pf, 65537, 1.0, None, None, ctypes.byref(op)) == nb.NAT_BEM_EINVAL
+    assert not op.value
+    assert L.nat_bem_op_neumann_size(None) == 0
