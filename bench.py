@@ -296,6 +296,18 @@ def run_modal(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # the tensor-core product's launches in one untimed traced step (CUDA events per launch)
+    tc_name = {"bf16": "tc_gemm_bf16", "tf32": "tc_gemm_tf32"}.get(args.prec)
+    tc = None
+    if tc_name:
+        nb.nat_bem_trace_enable(True)
+        nb.nat_bem_trace_select(tc_name)
+        nb.nat_bem_trace_reset()
+        step()
+        torch.cuda.synchronize()
+        tc = _working_launches(nb.nat_bem_trace_durations(tc_name))
+        nb.nat_bem_trace_enable(False)
+        nb.nat_bem_trace_reset()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         t0.record(stream)
@@ -305,6 +317,25 @@ def run_modal(args):
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     n_solves = args.steps * len(prob.ks) * args.nrhs
+    roof = None
+    if tc and tc[1]:
+        n = len(prob.F)
+        ld = (n + 31) // 32 * 32
+        ng = 2 * ((args.nrhs + 15) // 16 * 16)  # real columns of the packed right-hand sides
+        per = tc[0] / tc[1] * 1e-3
+        op_bytes = (4.0 if args.prec == "bf16" else 8.0) * n * ld
+        flops = 2.0 * n * (2 * ld) * ng  # real GEMM n x 2ld times 2ld x ng
+        peaks, peak_kind = _peaks()
+        gbs = op_bytes / per / 1e9
+        tfl = flops / per / 1e12
+        tpeak = peaks["bf16_tflops"] * (1.0 if args.prec == "bf16" else 0.5)
+        roof = {"kernel": tc_name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "launches": tc[1], "launches_exited_early": tc[2],
+                "tensor_tflops": tfl, "tensor_peak": tpeak,
+                "tensor_frac": tfl / tpeak,
+                "note": "operator bytes per launch (the packed right-hand sides are small beside them); "
+                        "64 flop per operator byte at 64 RHS is far below the tensor ridge, so HBM binds",
+                "peak_source": f"{peak_kind} (hbm_gbs; bf16_tflops, TF32 at half the BF16 rate)"}
     # accuracy of the last wavenumber against the FP64 oracle on two right-hand sides
     acc = None
     if args.cpu and len(prob.F) <= 6000:
@@ -327,7 +358,7 @@ def run_modal(args):
             "gmres": {"iterations_max": max(i[0] for i in infos), "refinements_max": max(i[1] for i in infos),
                       "max_rel_residual": max(i[2] for i in infos),
                       "not_converged": sum(1 for i in infos if i[3] != 0)},
-            "accuracy": acc, "clocks": clk.summary()}
+            "roofline": roof, "accuracy": acc, "clocks": clk.summary()}
 
 
 def run_mc(args):
