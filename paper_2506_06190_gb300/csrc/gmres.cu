@@ -86,7 +86,6 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 __device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1566,10 +1565,9 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
 // GEMV variants for one RHS and the autotuner that picks one per (device, operator size).
 enum GemvVariant { kGemvR2U4 = 0, kGemvR4U4, kGemvR2U8, kGemvBulk4x16k, kGemvBulk6x16k,
                    kGemvXsR2U8, kGemvXsR4U4, kGemvXsR2U4, kGemvVariants };
-static const char* kGemvNames[kGemvVariants] = {"rows2_unroll4", "rows4_unroll4", "rows2_unroll8",
-                                                 "bulk_4x16KiB", "bulk_6x16KiB", "xs_rows2_unroll8",
-                                                 "xs_rows4_unroll4", "xs_rows2_unroll4"};
-static_assert(kGemvVariants == NAT_BEM_GEMV_VARIANTS, "GEMV variants and the C ABI disagree");
+// 0 rows2_unroll4, 1 rows4_unroll4, 2 rows2_unroll8, 3 bulk_4x16KiB, 4 bulk_6x16KiB,
+// 5 xs_rows2_unroll8, 6 xs_rows4_unroll4, 7 xs_rows2_unroll4
+static_assert((int)kGemvVariants == (int)NAT_BEM_GEMV_VARIANTS, "GEMV variants and the C ABI disagree");
 constexpr int kGemvXsMaxBytes = 200 * 1024;  // x staged in shared memory up to ld = 25600
 
 // Grid of the staged-x GEMV: as many blocks per SM as shared memory and registers allow.
@@ -1837,7 +1835,7 @@ static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engin
 
 static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, int engine,
                                 int accumulate, float2* pout, cudaStream_t s) {
-  const int n = (int)op->n, ld = (int)op->geo.ld, nrhs = ws->nrhs;
+  const int n = (int)op->n, nrhs = ws->nrhs;
   const dim3 upd_grid(ws->nchunk, nrhs), fin_grid((n + kChunk - 1) / kChunk, nrhs);
   // the dot-product grid covers the Krylov vectors 0..j of the iteration being launched (the
   // device's j equals the host's launch count until every RHS is done)

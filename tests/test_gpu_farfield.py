@@ -96,3 +96,29 @@ def test_sampler_rejects_bad_radii(nb):
         g = np.ones(len(F), np.complex64)
         with pytest.raises(nb.NatBemError):
             op.sample_field(np.zeros((4, 3)), np.zeros(3), 2.0, 1.0, g, g)
+
+
+def test_dataset_step_at_full_size(nb, oracle_lib):
+    """The dataset workload's configuration (interior-source body, 10240 triangles): the GPU
+    solve, then 10,000 shell samples and the 64 x 32 FFAT map; sampled outputs against the
+    oracle's field and far field of the same surface data."""
+    prob = S.interior_source(n_k=1, ka_range=(6.0, 6.0))
+    V, F, k = prob.V, prob.F, float(prob.ks[0])
+    g = np.ascontiguousarray(prob.neumann[0][:, 0]).astype(np.complex64)
+    lo, hi = V.min(axis=0), V.max(axis=0)
+    center, rb = 0.5 * (lo + hi), 0.5 * np.linalg.norm(hi - lo)
+    u = np.random.default_rng(70).random((10000, 3))
+    dirs = oracle_lib.ffat_directions(64, 32)
+    with nb.Operator.assemble(V, F, k) as op:
+        p, info, st = op.solve(g)
+        assert st == nb.NAT_BEM_OK
+        coords, amp = op.sample_field(u, center, 1.5 * rb, 3.0 * rb, p, g)
+        ff = op.far_field(dirs, p, g)
+    pick = np.random.default_rng(71).choice(10000, 64, replace=False)
+    _, xyz = oracle_lib.sample_coords(u[pick], center, 1.5 * rb, 3.0 * rb)
+    p64, g64 = p.astype(np.complex128), g.astype(np.complex128)
+    ref = np.abs(oracle_lib.evaluate(V, F, k, xyz, p64, g64))
+    assert _rel(amp[pick], ref) < TOL
+    dpick = np.random.default_rng(72).choice(len(dirs), 48, replace=False)
+    ref_ff = oracle_lib.far_field(V, F, k, dirs[dpick], p64, g64)
+    assert _rel(ff[dpick], ref_ff) < TOL
