@@ -225,6 +225,7 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
     nb.nat_bem_trace_enable(False)
     kern = _kernel_table(nb)
     working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    summary["gemv_variant"] = nb.nat_bem_gemv_variant(n)
     nb.nat_bem_trace_reset()
     first = results[0][0]
     out = dict(summary, kern=kern, measured=kern, working=working, p0=first[0].cpu().numpy(),
@@ -968,6 +969,7 @@ def main():
         "not_converged": res["n_enoconv"],
         "max_refinements": res["refinements"],
         "concurrency": args.concurrency,
+        "gemv_variant_fp32": res.get("gemv_variant"),
         "gpu_launches": int(res["launches"]),
         "clocks": res["clocks"],
     }
