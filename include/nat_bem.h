@@ -159,6 +159,34 @@ NAT_BEM_API nat_bem_status nat_bem_assemble_mc(const double* pts, const double* 
                                                void* cuda_stream, nat_bem_op** out);
 
 /*
+ * Poisson-disk samples of a triangle mesh for nat_bem_assemble_mc (paper Sec. 4.2: samples at
+ * a minimum distance cover the surface evenly; the paper samples in parallel on the GPU after
+ * Bowers et al. 2010). Dart throwing on a grid, deterministic for given draws:
+ *   1. candidate i from draw u_i = (u0, u1, u2): the first triangle whose cumulative area
+ *      (FP64, in triangle order) exceeds u0 * total area, at barycentric coordinates
+ *      (1 - sqrt(u1), sqrt(u1) (1 - u2), sqrt(u1) u2), with that triangle's unit normal;
+ *   2. cells of size h = radius / sqrt(3) over the vertices' bounding box (at most one
+ *      sample per cell), cell = floor((x - lo) / h) per axis, clamped;
+ *   3. 27 phases (i mod 3, j mod 3, k mod 3) in lexicographic order: each cell of the phase
+ *      accepts its lowest-index candidate with no accepted sample closer than radius in the
+ *      5 x 5 x 5 cells around it (cells of one phase run in parallel).
+ * The accepted candidates come out in increasing index, the same set for any launch order.
+ *   verts: nv x 3 float64, tris: nt x 3 int32 (host or device). u: m x 3 float64 draws in
+ *   [0, 1) (host or device; the caller's random numbers). idx_out: cap int64 (host, may be
+ *   NULL): indices of the accepted candidates. pts_out, normals_out: cap x 3 float64 (host or
+ *   device; may be NULL when cap = 0). *count: the number of accepted samples (host), also set
+ *   when it exceeds cap (then NAT_BEM_EINVAL and only idx_out's first cap entries are written).
+ * Blocks until the outputs are written; m = 0 gives *count = 0.
+ * NAT_BEM_EINVAL: NULL arrays, nv or nt < 1, m < 0 or > 2^31 - 1, radius not positive and
+ * finite, a triangle index out of range, a degenerate triangle, more than 2^28 grid cells,
+ * more samples than cap. NAT_BEM_ENOMEM / NAT_BEM_ECUDA as for nat_bem_assemble.
+ */
+NAT_BEM_API nat_bem_status nat_bem_poisson_sample(const double* verts, int64_t nv, const int32_t* tris,
+                                                  int64_t nt, double radius, const double* u, int64_t m,
+                                                  int64_t cap, int64_t* idx_out, double* pts_out,
+                                                  double* normals_out, int64_t* count, void* cuda_stream);
+
+/*
  * Re-assembles L and R of an existing op at a new wavenumber k (> 0, finite): the mesh checks,
  * the device geometry, the operator memory and the solver workspace are reused, so sweeping
  * the frequencies of one body costs only the element-pair kernels. Work is ordered on

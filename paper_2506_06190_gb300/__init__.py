@@ -38,7 +38,7 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
             "nat_bem_far_field", "nat_bem_sample_field", "nat_bem_gemv_variant", "nat_field_create",
             "nat_field_forward", "nat_field_destroy", "nat_bem_assemble_galerkin",
-            "nat_bem_op_neumann_size", "nat_bem_trace_durations"]
+            "nat_bem_op_neumann_size", "nat_bem_trace_durations", "nat_bem_poisson_sample"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -87,6 +87,9 @@ def lib():
         L.nat_bem_assemble.restype = ctypes.c_int
         L.nat_bem_assemble_mc.argtypes = [vp, vp, i64, d, d, ctypes.POINTER(Opts), vp, ctypes.POINTER(vp)]
         L.nat_bem_assemble_mc.restype = ctypes.c_int
+        L.nat_bem_poisson_sample.argtypes = [vp, i64, vp, i64, d, vp, i64, i64, vp, vp, vp,
+                                             ctypes.POINTER(i64), vp]
+        L.nat_bem_poisson_sample.restype = ctypes.c_int
         L.nat_bem_far_field.argtypes = [vp, vp, i64, vp, vp, ctypes.c_int32, vp, vp]
         L.nat_bem_far_field.restype = ctypes.c_int
         L.nat_bem_sample_field.argtypes = [vp, vp, i64, vp, d, d, vp, vp, ctypes.c_int32, vp, vp, vp]
@@ -258,6 +261,35 @@ def nat_bem_assemble_mc(Y, N, area: float, k: float, opts: Opts | None = None, s
     del ky, kn
     _check(st)
     return op
+
+
+def nat_bem_poisson_sample(V, F, u, radius: float, cap: int | None = None, stream=None):
+    """Poisson-disk samples of the mesh (V, F) from the draws u (m x 3 in [0, 1)) at minimum
+    distance `radius`: (indices of the accepted draws, positions, unit normals), in increasing
+    index. Outputs are numpy arrays, or torch tensors on V's device when V is a torch tensor."""
+    pv, kv = _ptr(V, np.float64)
+    pt, kt = _ptr(F, np.int32)
+    pu, ku = _ptr(u, np.float64)
+    m = int(u.shape[0])
+    cap = m if cap is None else int(cap)
+    idx = np.zeros(max(cap, 1), np.int64)
+    if _is_torch(V):
+        import torch
+        pts = torch.empty((max(cap, 1), 3), dtype=torch.float64, device=V.device)
+        nrm = torch.empty_like(pts)
+        pp, pn = ctypes.c_void_p(pts.data_ptr()), ctypes.c_void_p(nrm.data_ptr())
+    else:
+        pts = np.zeros((max(cap, 1), 3))
+        nrm = np.zeros((max(cap, 1), 3))
+        pp, pn = ctypes.c_void_p(pts.ctypes.data), ctypes.c_void_p(nrm.ctypes.data)
+    count = ctypes.c_int64(0)
+    st = lib().nat_bem_poisson_sample(pv, int(V.shape[0]), pt, int(F.shape[0]), float(radius), pu, m, cap,
+                                      ctypes.c_void_p(idx.ctypes.data), pp, pn, ctypes.byref(count),
+                                      _stream_of(V, stream))
+    del kv, kt, ku
+    _check(st)
+    c = int(count.value)
+    return idx[:c], pts[:c], nrm[:c]
 
 
 def nat_bem_reassemble(op, k: float, stream=None, like=None):

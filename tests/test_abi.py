@@ -172,3 +172,31 @@ def test_galerkin_rejects_bad_arguments(nb):
     assert L.nat_bem_assemble_galerkin(pv, 4, pf, 65537, 1.0, None, None, ctypes.byref(op)) == nb.NAT_BEM_EINVAL
     assert not op.value
     assert L.nat_bem_op_neumann_size(None) == 0
+
+
+def test_poisson_sample_rejects_bad_arguments(nb):
+    L = nb.lib()
+    V, F = S.icosphere(1)
+    u = np.zeros((8, 3))
+    pv, pf, pu = (ctypes.c_void_p(a.ctypes.data) for a in (V, F, u))
+    out = np.zeros((8, 3))
+    po = ctypes.c_void_p(out.ctypes.data)
+    cnt = ctypes.c_int64(-1)
+    ok = dict(nv=len(V), nt=len(F), r=0.1, m=8, cap=8)
+
+    def call(pv=pv, nv=ok["nv"], pf=pf, nt=ok["nt"], r=ok["r"], pu=pu, m=ok["m"], cap=ok["cap"], po=po, cnt=cnt):
+        return L.nat_bem_poisson_sample(pv, nv, pf, nt, r, pu, m, cap, None, po, po,
+                                        ctypes.byref(cnt) if cnt is not None else None, None)
+
+    assert call(pv=None) == nb.NAT_BEM_EINVAL
+    assert call(pf=None) == nb.NAT_BEM_EINVAL
+    assert call(pu=None) == nb.NAT_BEM_EINVAL
+    assert call(cnt=None) == nb.NAT_BEM_EINVAL
+    assert call(nv=0) == nb.NAT_BEM_EINVAL
+    assert call(nt=0) == nb.NAT_BEM_EINVAL
+    assert call(m=-1) == nb.NAT_BEM_EINVAL
+    assert call(m=1 << 31) == nb.NAT_BEM_EINVAL
+    assert call(cap=-1) == nb.NAT_BEM_EINVAL
+    assert call(po=None) == nb.NAT_BEM_EINVAL
+    for r in (0.0, -1.0, float("nan"), float("inf")):
+        assert call(r=r) == nb.NAT_BEM_EINVAL
