@@ -363,19 +363,37 @@ def run_modal(args):
 
 
 def run_mc(args):
-    """Monte-Carlo BEM (paper Sec. 4.1.1, 4.2): the interior-source body sampled with --n-samples
-    Poisson-disk points (uniform random with --random-samples), monopole Neumann data at the
-    samples, --n-k wavenumbers in ka [0.5, 12], 1024 field points at radius 4. One step: for
-    each wavenumber, re-assemble the sample operators, solve, evaluate the field."""
+    """Monte-Carlo BEM (paper Sec. 4.1.1, 4.2): the interior-source body sampled by the GPU
+    Poisson-disk sampler (8 x --n-samples draws at 0.7 of the hexagonal spacing of --n-samples
+    points; about 0.97 x --n-samples accepted) or with --n-samples uniform random points
+    (--random-samples), monopole Neumann data at the samples, --n-k wavenumbers in ka
+    [0.5, 12], 1024 field points at radius 4. One step: for each wavenumber, re-assemble the
+    sample operators, solve, evaluate the field. The sampler runs once per body and is timed on
+    its own."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
     nb_build.build()
-    Y, N, area, ks, gs, pts, exact = S.mc_interior_source(M=args.n_samples, n_k=args.n_k,
-                                                          poisson=not args.random_samples)
+    dev = torch.device("cuda", 0)
+    Y, N, area, ks, gs, pts, exact = S.mc_interior_source(M=args.n_samples, n_k=args.n_k, poisson=False)
+    sampler = None
+    if not args.random_samples:
+        # Poisson-disk samples from the GPU sampler, timed on their own (once per body)
+        V, F = S.mc_interior_body()
+        u, radius = S.poisson_draws(V, F, args.n_samples, 6001)
+        Vd, Fd, ud = torch.from_numpy(V).to(dev), torch.from_numpy(F).to(dev), torch.from_numpy(u).to(dev)
+        times = []
+        for rep in range(13):
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, Yd, Nd = nb.nat_bem_poisson_sample(Vd, Fd, ud, radius)
+            times.append(time.perf_counter() - t)
+        Y, N = Yd.cpu().numpy(), Nd.cpu().numpy()
+        gs = [S.monopole_neumann_at(Y, N, k) for k in ks]
+        sampler = {"ms_median": 1e3 * float(np.median(times[3:])), "candidates": len(u), "radius": radius,
+                   "samples": len(Y), "per": "one call, host wall clock, outputs on the device"}
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
-    dev = torch.device("cuda", 0)
     Yd, Nd, Pd = (torch.from_numpy(a).to(dev) for a in (Y, N, pts))
     Gd = [torch.from_numpy(g.astype(np.complex64)).to(dev) for g in gs]
     stream = torch.cuda.current_stream(dev)
@@ -429,7 +447,7 @@ def run_mc(args):
             "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
             "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
                       "not_converged": sum(1 for i in infos if i[2] != 0)},
-            "accuracy": acc, "clocks": clk.summary()}
+            "accuracy": acc, "sampler": sampler, "clocks": clk.summary()}
 
 
 def run_dataset(args):

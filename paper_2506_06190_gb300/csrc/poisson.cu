@@ -40,7 +40,8 @@ __device__ __forceinline__ int ps_clamp(int v, int n) { return v < 0 ? 0 : v >= 
 __global__ void k_ps_candidates(const double* __restrict__ V, const int32_t* __restrict__ T,
                                 const double* __restrict__ cum, int nt, const double* __restrict__ u, int m,
                                 PsGrid g, double* __restrict__ x, double* __restrict__ nrm,
-                                int* __restrict__ head, int* __restrict__ next) {
+                                int* __restrict__ head, int* __restrict__ next, int64_t* __restrict__ occ,
+                                int* __restrict__ n_occ) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= m) return;
   const double u0 = u[3 * (size_t)i], u1 = u[3 * (size_t)i + 1], u2 = u[3 * (size_t)i + 2];
@@ -76,48 +77,86 @@ __global__ void k_ps_candidates(const double* __restrict__ V, const int32_t* __r
   const int cj = ps_clamp((int)floor(__ddiv_rn(ds(p[1], g.loy), g.h)), g.ny);
   const int ck = ps_clamp((int)floor(__ddiv_rn(ds(p[2], g.loz), g.h)), g.nz);
   const int64_t cell = ((int64_t)ci * g.ny + cj) * g.nz + ck;
-  next[i] = atomicExch(&head[cell], i);
+  const int prev = atomicExch(&head[cell], i);
+  next[i] = prev;
+  if (prev < 0) occ[atomicAdd(n_occ, 1)] = cell;  // first candidate of the cell: list the cell once
 }
 
-// One phase: one thread per cell of the phase.
-__global__ void k_ps_phase(PsGrid g, int px, int py, int pz, double r2, const double* __restrict__ x,
-                           const int* __restrict__ head, const int* __restrict__ next, int* __restrict__ taken) {
-  const int qx = (g.nx - px + 2) / 3, qy = (g.ny - py + 2) / 3, qz = (g.nz - pz + 2) / 3;
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= (int64_t)qx * qy * qz) return;
-  const int ci = px + 3 * (int)(w / ((int64_t)qy * qz));
-  const int cj = py + 3 * (int)((w / qz) % qy);
-  const int ck = pz + 3 * (int)(w % qz);
-  const int64_t cell = ((int64_t)ci * g.ny + cj) * g.nz + ck;
-  int best = -1;
-  for (int i = head[cell]; i >= 0; i = next[i]) {
-    if (best >= 0 && i > best) continue;
-    const double xi = x[3 * (size_t)i], yi = x[3 * (size_t)i + 1], zi = x[3 * (size_t)i + 2];
-    bool ok = true;
-    for (int di = -2; di <= 2 && ok; ++di) {
-      const int a = ci + di;
-      if (a < 0 || a >= g.nx) continue;
-      for (int dj = -2; dj <= 2 && ok; ++dj) {
-        const int b = cj + dj;
-        if (b < 0 || b >= g.ny) continue;
-        for (int dk = -2; dk <= 2 && ok; ++dk) {
-          const int c = ck + dk;
-          if (c < 0 || c >= g.nz) continue;
-          const int s = taken[((int64_t)a * g.ny + b) * g.nz + c];
-          if (s < 0) continue;
-          const double dx = ds(xi, x[3 * (size_t)s]), dy = ds(yi, x[3 * (size_t)s + 1]), dz = ds(zi, x[3 * (size_t)s + 2]);
-          if (da(da(dm(dx, dx), dm(dy, dy)), dm(dz, dz)) < r2) ok = false;
+// One phase: a warp per occupied cell of the phase. Lane l holds the accepted samples of the
+// neighbour cells l, l + 32, l + 64, l + 96 of the 5 x 5 x 5 block (none of them changes during
+// the phase: same-phase cells are three or more cells apart); the warp walks the cell's list
+// and keeps the lowest index that every lane finds at distance >= r from its samples.
+__global__ void __launch_bounds__(256) k_ps_phase(PsGrid g, int phase, double r2, const double* __restrict__ x,
+                                                  const int* __restrict__ head, const int* __restrict__ next,
+                                                  const int64_t* __restrict__ occ, const int* __restrict__ n_occ,
+                                                  int* __restrict__ taken) {
+  const int lane = threadIdx.x & 31;
+  const int n = *n_occ;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  for (int64_t base = (int64_t)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n;
+       base += (int64_t)warps * 32) {
+    int64_t mine = -1;
+    int ci = 0, cj = 0, ck = 0;
+    if (base + lane < n) {
+      const int64_t c = occ[base + lane];
+      ck = (int)(c % g.nz);
+      cj = (int)((c / g.nz) % g.ny);
+      ci = (int)(c / ((int64_t)g.ny * g.nz));
+      if ((ci % 3) * 9 + (cj % 3) * 3 + (ck % 3) == phase) mine = c;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, mine >= 0);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int64_t cell = __shfl_sync(0xffffffffu, mine, src);
+      const int cx = __shfl_sync(0xffffffffu, ci, src), cy = __shfl_sync(0xffffffffu, cj, src),
+                cz = __shfl_sync(0xffffffffu, ck, src);
+      double nx[4], ny[4], nz[4];
+      bool has[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = lane + 32 * q;
+        has[q] = false;
+        nx[q] = ny[q] = nz[q] = 0.0;
+        if (t < 125) {
+          const int a = cx + t / 25 - 2, b = cy + (t / 5) % 5 - 2, c = cz + t % 5 - 2;
+          if (a >= 0 && a < g.nx && b >= 0 && b < g.ny && c >= 0 && c < g.nz) {
+            const int sidx = taken[((int64_t)a * g.ny + b) * g.nz + c];
+            if (sidx >= 0) {
+              has[q] = true;
+              nx[q] = x[3 * (size_t)sidx];
+              ny[q] = x[3 * (size_t)sidx + 1];
+              nz[q] = x[3 * (size_t)sidx + 2];
+            }
+          }
         }
       }
+      int best = -1;
+      for (int i = head[cell]; i >= 0; i = next[i]) {
+        if (best >= 0 && i > best) continue;
+        const double xi = x[3 * (size_t)i], yi = x[3 * (size_t)i + 1], zi = x[3 * (size_t)i + 2];
+        bool ok = true;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (has[q]) {
+            const double dx = ds(xi, nx[q]), dy = ds(yi, ny[q]), dz = ds(zi, nz[q]);
+            if (da(da(dm(dx, dx), dm(dy, dy)), dm(dz, dz)) < r2) ok = false;
+          }
+        }
+        if (__all_sync(0xffffffffu, ok)) best = i;
+      }
+      if (lane == 0 && best >= 0) taken[cell] = best;
     }
-    if (ok) best = i;
   }
-  if (best >= 0) taken[cell] = best;
 }
 
-__global__ void k_ps_flags(const int* __restrict__ taken, int64_t cells, unsigned char* __restrict__ flag) {
-  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < cells && taken[c] >= 0) flag[taken[c]] = 1;
+__global__ void k_ps_flags(const int* __restrict__ taken, const int64_t* __restrict__ occ,
+                           const int* __restrict__ n_occ, unsigned char* __restrict__ flag) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < *n_occ) {
+    const int s = taken[occ[j]];
+    if (s >= 0) flag[s] = 1;
+  }
 }
 
 __global__ void k_ps_gather(const int* __restrict__ idx, int count, const double* __restrict__ x,
@@ -208,11 +247,12 @@ extern "C" nat_bem_status nat_bem_poisson_sample(const double* verts, int64_t nv
     int32_t* dT = nullptr;
     const double* du = nullptr;
     double* tu = nullptr;
-    int *head = nullptr, *next = nullptr, *taken = nullptr, *didx = nullptr;
+    int *head = nullptr, *next = nullptr, *taken = nullptr, *didx = nullptr, *n_occ = nullptr;
+    int64_t* occ = nullptr;
     unsigned char* flag = nullptr;
     double *tp = nullptr, *tn = nullptr;
     auto cleanup = [&]() {
-      void* ptrs[] = {dV, dcum, dx, dn, dT, tu, head, next, taken, didx, flag, tp, tn};
+      void* ptrs[] = {dV, dcum, dx, dn, dT, tu, head, next, taken, didx, flag, tp, tn, occ, n_occ};
       for (void* p : ptrs) dev_free(p, s);
     };
     nat_bem_status st = NAT_BEM_OK;
@@ -225,6 +265,8 @@ extern "C" nat_bem_status nat_bem_poisson_sample(const double* verts, int64_t nv
     if (st == NAT_BEM_OK) st = dev_alloc_n(&taken, (size_t)cells, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&next, (size_t)m, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&flag, (size_t)m, s);
+    if (st == NAT_BEM_OK) st = dev_alloc_n(&occ, (size_t)m, s);
+    if (st == NAT_BEM_OK) st = dev_alloc_n(&n_occ, 1, s);
     if (st == NAT_BEM_OK) st = to_device(u, (size_t)(3 * m), s, &du, &tu);
     if (st != NAT_BEM_OK) {
       cleanup();
@@ -236,22 +278,20 @@ extern "C" nat_bem_status nat_bem_poisson_sample(const double* verts, int64_t nv
     if (e == cudaSuccess) e = cudaMemsetAsync(head, 0xff, (size_t)cells * sizeof(int), s);   // -1
     if (e == cudaSuccess) e = cudaMemsetAsync(taken, 0xff, (size_t)cells * sizeof(int), s);  // -1
     if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, (size_t)m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(n_occ, 0, sizeof(int), s);
     if (e != cudaSuccess) {
       set_error(std::string("nat_bem_poisson_sample: ") + cudaGetErrorString(e));
       cleanup();
       return NAT_BEM_ECUDA;
     }
     NB_LAUNCH("ps_candidates", s, k_ps_candidates<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(
-        dV, dT, dcum, (int)nt, du, (int)m, g, dx, dn, head, next));
+        dV, dT, dcum, (int)nt, du, (int)m, g, dx, dn, head, next, occ, n_occ));
     const double r2 = radius * radius;
-    for (int ph = 0; ph < 27; ++ph) {
-      const int px = ph / 9, py = (ph / 3) % 3, pz = ph % 3;
-      const int64_t work = (int64_t)((g.nx - px + 2) / 3) * ((g.ny - py + 2) / 3) * ((g.nz - pz + 2) / 3);
-      if (work <= 0) continue;
-      NB_LAUNCH("ps_phase", s, k_ps_phase<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(g, px, py, pz, r2, dx, head,
-                                                                                        next, taken));
-    }
-    NB_LAUNCH("ps_flags", s, k_ps_flags<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(taken, cells, flag));
+    // the occupied cells number at most m: 8 warps of 32 cells per block, at most 8 blocks per SM
+    const unsigned pblocks = (unsigned)std::min<int64_t>((m + 255) / 256, 152 * 8);
+    for (int ph = 0; ph < 27; ++ph)
+      NB_LAUNCH("ps_phase", s, k_ps_phase<<<pblocks, 256, 0, s>>>(g, ph, r2, dx, head, next, occ, n_occ, taken));
+    NB_LAUNCH("ps_flags", s, k_ps_flags<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(taken, occ, n_occ, flag));
     std::vector<unsigned char> hflag(m);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hflag.data(), flag, (size_t)m, cudaMemcpyDeviceToHost, s);

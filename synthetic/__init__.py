@@ -448,14 +448,29 @@ def serving_stream(seed: int = 5000, n_req: int = 2000, rate: float = 200.0,
     return [(float(t[i]), int(f[i]), float(ka[i]), int(nrhs[i]), seed + 7 + i) for i in range(n_req)]
 
 
+def mc_interior_body(seed: int = 6000, n_tri: int = 10240):
+    """The Monte-Carlo workload's body: a ring sphere of n_tri triangles deformed into the
+    perturbed ellipsoid of `seed`. Returns (V, F)."""
+    Vs, F = ring_sphere(n_tri)
+    return perturbed_ellipsoid(Vs, seed), F
+
+
+def poisson_draws(V: np.ndarray, F: np.ndarray, M: int, seed: int, oversample: int = 8, frac: float = 0.7):
+    """Draws for a Poisson-disk sampler aiming at about M samples: oversample * M uniform
+    triples in [0, 1)^3 and the radius frac times the spacing of a hexagonal packing of M
+    points over the mesh's area. Returns (u, radius)."""
+    a, b, c, n, area = _triangle_table(V, F)
+    d_hex = math.sqrt(2.0 * float(area.sum()) / (math.sqrt(3.0) * M))
+    return np.random.default_rng(seed).random((oversample * M, 3)), frac * d_hex
+
+
 def mc_interior_source(seed: int = 6000, n_tri: int = 10240, M: int = 4096, n_k: int = 64,
                        ka_range=(0.5, 12.0), n_points: int = 1024, R: float = 4.0, poisson: bool = True):
     """Monte-Carlo workload: the interior-source body (perturbed ellipsoid, l <= 6) sampled with
     M Poisson-disk (or uniform random) points, monopole Neumann data at the samples, n_k
     wavenumbers log-uniform in ka_range, field points at radius R. Returns
     (Y, N, area, ks, [g per k], points, [exact field per k])."""
-    Vs, F = ring_sphere(n_tri)
-    V = perturbed_ellipsoid(Vs, seed)
+    V, F = mc_interior_body(seed, n_tri)
     Y, N, area = (mesh_poisson_samples if poisson else mesh_random_samples)(V, F, M, seed + 1)
     ks = log_uniform(n_k, ka_range[0], ka_range[1], seed + 2)
     pts = fibonacci_points(n_points, R)
