@@ -705,7 +705,9 @@ def _numpy_threads():
 
 # DRAM bytes (read + write) of one k_nat_forward launch per 2^20 queries, from the committed ncu
 # capture (profiles/k_nat_forward_nat_inference_1Mqueries.md); traffic grows with the queries.
-NCU_TRAFFIC_NAT_PER_MQUERY = 28.127488e6 + 32.0e6
+# The write figure is what reached DRAM during the launch: most of the 33.6 MB of outputs were
+# still in L2 when it ended.
+NCU_TRAFFIC_NAT_PER_MQUERY = 28.146176e6 + 0.048896e6
 
 
 def run_uneven(args):

@@ -3,9 +3,9 @@
 // and the frequency, and a 4 x 128 MLP with ReLU and a linear output layer, fused in one
 // persistent kernel on the tensor cores.
 //
-// A block runs two independent groups of four warps; each group owns a tile of 128 queries
-// (one thread per query), an activation tile A in shared memory and 128 TMEM columns, so one
-// group's encoding and epilogues overlap the other group's MMAs. Per tile:
+// A block runs two or three independent groups of four warps; each group owns a tile of 128
+// queries (one thread per query), an activation tile A in shared memory and 128 TMEM columns,
+// so one group's epilogues overlap the other groups' MMAs. Per tile:
 //   encode   each thread forms its query's input row (16 trilinear grid features, then sin and
 //            cos of 2^l pi x_d, l = 0..5, for the condition variables and the frequency, zero
 //            padding), rounds it to BF16 and writes it as row t of A in the 128-byte-swizzled
@@ -16,6 +16,10 @@
 //            (tcgen05.ld), adds the bias, applies ReLU while rounding to BF16 and writes the next
 //            layer's input back into A;
 //   output   the last layer (N = n_out rounded up to 16) plus bias goes to global memory (FP32).
+// The encoding of the next tile runs in pieces while each layer's MMAs are in flight (grid level
+// l during layer l from rows requested one layer earlier, the positional encoding spread over
+// three layers), so the table gathers' latency hides behind the tensor cores instead of adding
+// to the tile's critical path.
 // The weights stay in shared memory for the kernel's lifetime (at most 160 KB) and the biases
 // live in the kernel's parameter space (uniform reads through the constant cache), so HBM only
 // carries the queries, the grid tables (through L2) and the outputs. The tables are half
@@ -178,8 +182,7 @@ __device__ __forceinline__ void nat_tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
 }
 
 
-// Encode query q into row t of A: the K steps layer 0 reads (2 K0 chunks of 16 bytes).
-// dense_mask bit l: level l is stored densely.
+// The D inputs of query q (zeros past the end).
 template <int D>
 __device__ __forceinline__ void nat_load_x(const float* __restrict__ x, int64_t q, int64_t n, float (&xv)[D]) {
 #pragma unroll
@@ -193,81 +196,109 @@ __device__ __forceinline__ float4 nat_h4(uint32_t lo, uint32_t hi) {
   return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// The table rows of one grid level for one query: the eight corners' features (FP16, 8 bytes
+// each), requested by nat_fetch and used by nat_finish a pipeline stage later.
+struct NatRows {
+  uint4 r[4];  // corners 2c and 2c + 1 in r[c]
+};
+
+// Grid level lvl (8 << lvl cells per axis) of the query at xv: the cell and the trilinear
+// weights along each axis.
 template <int D>
-__device__ __forceinline__ void nat_encode(const float (&xv)[D], int64_t q, int64_t n,
-                                           const uint2* __restrict__ tables, const int (&offs)[4],
-                                           uint32_t hmask, int dense_mask, uint8_t* sA, int t) {
-  constexpr int K0 = nat_k0(D);
-  uint32_t pk[8 * K0];
+__device__ __forceinline__ void nat_cell(int lvl, const float (&xv)[D], int (&i0)[3], float (&w1)[3]) {
+  const int N = 8 << lvl;
 #pragma unroll
-  for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;
-#pragma unroll
-  for (int lvl = 0; lvl < 4; ++lvl) {
-    const int N = 8 << lvl;  // 8, 16, 32, 64 cells per axis
-    int i0[3];
-    float w1[3], w0[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const float p = fminf(fmaxf(xv[a], 0.f), 1.f) * (float)N;
-      i0[a] = min((int)p, N - 1);  // p >= 0: truncation is the floor
-      w1[a] = p - (float)i0[a];
-      w0[a] = 1.f - w1[a];
-    }
-    const float wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
-    float4 v[8];  // corner c = di + 2 dj + 4 dk
-    if (dense_mask & (1 << lvl)) {
-      // the quads at z = k and z = k + 1: four 16-byte loads from two 32-byte sectors
-      const uint4* tq = reinterpret_cast<const uint4*>(tables + offs[lvl]);
-      const uint32_t q0 = (uint32_t)i0[0] + (uint32_t)N * ((uint32_t)i0[1] + (uint32_t)N * (uint32_t)i0[2]);
-      const uint32_t q1 = q0 + (uint32_t)(N * N);
-      const uint4 a = __ldg(tq + 2 * q0), b = __ldg(tq + 2 * q0 + 1);
-      const uint4 c = __ldg(tq + 2 * q1), d = __ldg(tq + 2 * q1 + 1);
-      v[0] = nat_h4(a.x, a.y);
-      v[1] = nat_h4(a.z, a.w);
-      v[2] = nat_h4(b.x, b.y);
-      v[3] = nat_h4(b.z, b.w);
-      v[4] = nat_h4(c.x, c.y);
-      v[5] = nat_h4(c.z, c.w);
-      v[6] = nat_h4(d.x, d.y);
-      v[7] = nat_h4(d.z, d.w);
-    } else {
-      const uint2* tl = tables + offs[lvl];
-      const uint32_t hx[2] = {(uint32_t)i0[0], (uint32_t)i0[0] + 1u};
-      const uint32_t hy[2] = {(uint32_t)i0[1] * kPrime1, ((uint32_t)i0[1] + 1u) * kPrime1};
-      const uint32_t hz[2] = {(uint32_t)i0[2] * kPrime2, ((uint32_t)i0[2] + 1u) * kPrime2};
-      uint2 u[8];
-#pragma unroll
-      for (int c = 0; c < 8; ++c) u[c] = __ldg(tl + ((hx[c & 1] ^ hy[(c >> 1) & 1] ^ hz[c >> 2]) & hmask));
-#pragma unroll
-      for (int c = 0; c < 8; ++c) v[c] = nat_h4(u[c].x, u[c].y);
-    }
-    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const float wt = wxy[c & 3] * (c >> 2 ? w1[2] : w0[2]);
-      f0 = fmaf(wt, v[c].x, f0);
-      f1 = fmaf(wt, v[c].y, f1);
-      f2 = fmaf(wt, v[c].z, f2);
-      f3 = fmaf(wt, v[c].w, f3);
-    }
-    pk[2 * lvl] = pack2(f0, f1);
-    pk[2 * lvl + 1] = pack2(f2, f3);
+  for (int a = 0; a < 3; ++a) {
+    const float p = fminf(fmaxf(xv[a], 0.f), 1.f) * (float)N;
+    i0[a] = min((int)p, N - 1);  // p >= 0: truncation is the floor
+    w1[a] = p - (float)i0[a];
   }
+}
+
+// Requests the eight corner rows of level lvl. dense_mask bit lvl: the level is stored densely
+// (the quads at z = k and z = k + 1: four 16-byte loads from two 32-byte sectors), else hashed.
+template <int D>
+__device__ __forceinline__ void nat_fetch(int lvl, const float (&xv)[D], const uint2* __restrict__ tables,
+                                          const int (&offs)[4], uint32_t hmask, int dense_mask, NatRows& rows) {
+  const int N = 8 << lvl;
+  int i0[3];
+  float w1[3];
+  nat_cell<D>(lvl, xv, i0, w1);
+  if (dense_mask & (1 << lvl)) {
+    const uint4* tq = reinterpret_cast<const uint4*>(tables + offs[lvl]);
+    const uint32_t q0 = (uint32_t)i0[0] + (uint32_t)N * ((uint32_t)i0[1] + (uint32_t)N * (uint32_t)i0[2]);
+    const uint32_t q1 = q0 + (uint32_t)(N * N);
+    rows.r[0] = __ldg(tq + 2 * q0);
+    rows.r[1] = __ldg(tq + 2 * q0 + 1);
+    rows.r[2] = __ldg(tq + 2 * q1);
+    rows.r[3] = __ldg(tq + 2 * q1 + 1);
+  } else {
+    const uint2* tl = tables + offs[lvl];
+    const uint32_t hx[2] = {(uint32_t)i0[0], (uint32_t)i0[0] + 1u};
+    const uint32_t hy[2] = {(uint32_t)i0[1] * kPrime1, ((uint32_t)i0[1] + 1u) * kPrime1};
+    const uint32_t hz[2] = {(uint32_t)i0[2] * kPrime2, ((uint32_t)i0[2] + 1u) * kPrime2};
+    uint2 u[8];
 #pragma unroll
-  for (int d = 3; d < D; ++d)  // the condition variables and the frequency
+    for (int c = 0; c < 8; ++c) u[c] = __ldg(tl + ((hx[c & 1] ^ hy[(c >> 1) & 1] ^ hz[c >> 2]) & hmask));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) rows.r[c] = make_uint4(u[2 * c].x, u[2 * c].y, u[2 * c + 1].x, u[2 * c + 1].y);
+  }
+}
+
+// The four trilinear features of level lvl from its fetched rows, as BF16 pairs in pk[2 lvl],
+// pk[2 lvl + 1].
+template <int D, int P>
+__device__ __forceinline__ void nat_finish(int lvl, const float (&xv)[D], const NatRows& rows, uint32_t (&pk)[P]) {
+  int i0[3];
+  float w1[3], w0[3];
+  nat_cell<D>(lvl, xv, i0, w1);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) w0[a] = 1.f - w1[a];
+  const float wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
+  float4 v[8];  // corner c = di + 2 dj + 4 dk
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    v[2 * c] = nat_h4(rows.r[c].x, rows.r[c].y);
+    v[2 * c + 1] = nat_h4(rows.r[c].z, rows.r[c].w);
+  }
+  float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const float wt = wxy[c & 3] * (c >> 2 ? w1[2] : w0[2]);
+    f0 = fmaf(wt, v[c].x, f0);
+    f1 = fmaf(wt, v[c].y, f1);
+    f2 = fmaf(wt, v[c].z, f2);
+    f3 = fmaf(wt, v[c].w, f3);
+  }
+  pk[2 * lvl] = pack2(f0, f1);
+  pk[2 * lvl + 1] = pack2(f2, f3);
+}
+
+// The positional encoding of the condition variables and the frequency (inputs 3..D-1):
+// sin and cos of 2^l pi x_d, l = 0..5, as BF16 pairs after the 16 grid features.
+// part < 0: all inputs; else the inputs d with (d - 3) mod 3 = part.
+template <int D, int P>
+__device__ __forceinline__ void nat_encode_pe(const float (&xv)[D], uint32_t (&pk)[P], int part = -1) {
+#pragma unroll
+  for (int d = 3; d < D; ++d)
 #pragma unroll
     for (int l = 0; l < 6; ++l) {
+      if (part >= 0 && (d - 3) % 3 != part) continue;
       float s, c;
       sincospif(ldexpf(xv[d], l), &s, &c);  // sin, cos of 2^l pi x_d
       pk[8 + (d - 3) * 6 + l] = pack2(s, c);
     }
-  if (q >= n) {
-#pragma unroll
-    for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;
-  }
+}
+
+// The encoded row of query q as row t of A: the K steps layer 0 reads (2 K0 chunks of 16
+// bytes), zero past the end of the queries and in the padding.
+template <int K0>
+__device__ __forceinline__ void nat_store_row(const uint32_t (&pk)[8 * K0], int64_t q, int64_t n, uint8_t* sA, int t) {
+  const bool live = q < n;
 #pragma unroll
   for (int c = 0; c < 2 * K0; ++c)
-    *reinterpret_cast<uint4*>(sA + swz(t, c, 128)) = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+    *reinterpret_cast<uint4*>(sA + swz(t, c, 128)) =
+        live ? make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]) : make_uint4(0u, 0u, 0u, 0u);
 }
 }  // namespace
 
@@ -331,19 +362,34 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
   uint32_t phase = 0;
   bool ok_all = true;
 
-  // the next tile's inputs are requested before this tile's layers run
+  // Software pipeline over the group's tiles: while the MMAs of layer l of tile i run, the
+  // group encodes one piece of tile i + 1 into registers (grid level l for l < 4, the positional
+  // encoding at the output layer); the row goes into A once the output layer's MMA has read it.
   const int64_t tstride = (int64_t)gridDim.x * G;
-  float xnext[D];
-  nat_load_x<D>(x, ((int64_t)blockIdx.x * G + g) * 128 + t, n, xnext);
-  for (int64_t tile = (int64_t)blockIdx.x * G + g;; tile += tstride) {
+  int64_t tile = (int64_t)blockIdx.x * G + g;
+  uint32_t pk[8 * K0];
+#pragma unroll
+  for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;  // the padding stays zero
+  float xn[D], xnn[D];                            // inputs of tiles i + 1 and i + 2
+  NatRows rows;                                   // the rows of the level nat_finish uses next
+  {
+    float xv[D];
+    nat_load_x<D>(x, tile * 128 + t, n, xv);
+#pragma unroll
+    for (int lvl = 0; lvl < 4; ++lvl) {
+      nat_fetch<D>(lvl, xv, tables, offs, hmask, dense_mask, rows);
+      nat_finish<D>(lvl, xv, rows, pk);
+    }
+    nat_encode_pe<D>(xv, pk);
+    nat_store_row<K0>(pk, tile * 128 + t, n, sA, t);
+  }
+  nat_load_x<D>(x, (tile + tstride) * 128 + t, n, xn);
+  nat_fetch<D>(0, xn, tables, offs, hmask, dense_mask, rows);
+  for (;; tile += tstride) {
     const int64_t q0 = tile * 128;
     if (q0 >= n) break;  // uniform over the group
     const int64_t q = q0 + t;
-    float xv[D];
-#pragma unroll
-    for (int d = 0; d < D; ++d) xv[d] = xnext[d];
-    nat_encode<D>(xv, q, n, tables, offs, hmask, dense_mask, sA, t);
-    nat_load_x<D>(x, q + tstride * 128, n, xnext);
+    nat_load_x<D>(x, q + 2 * tstride * 128, n, xnn);
 #pragma unroll
     for (int l = 0; l <= kNatHidden; ++l) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A visible to the tensor cores
@@ -368,6 +414,19 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                      : "memory");
+      }
+      // the next tile's piece while the MMAs run: level l from the rows requested a stage
+      // earlier, then the request of level l + 1 (level 0 of the tile after it at the output
+      // layer); a third of the positional encoding during layers 0, 3 and the output layer
+      // (layer 2 carries the hashed level's eight gathers)
+      if (l < 4) {
+        nat_finish<D>(l, xn, rows, pk);
+        if (l < 3) nat_fetch<D>(l + 1, xn, tables, offs, hmask, dense_mask, rows);
+        if (l == 0) nat_encode_pe<D>(xn, pk, 1);
+        if (l == 3) nat_encode_pe<D>(xn, pk, 2);
+      } else {
+        nat_fetch<D>(0, xnn, tables, offs, hmask, dense_mask, rows);
+        nat_encode_pe<D>(xn, pk, 0);
       }
       // one warp polls the mbarrier; the others wait at the group barrier without issuing
       bool ok = true;
@@ -421,9 +480,13 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
             }
           }
         }
+        // the output layer's MMAs have read A: the next tile's row goes in
+        nat_store_row<K0>(pk, q + tstride * 128, n, sA, t);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
+#pragma unroll
+    for (int d = 0; d < D; ++d) xn[d] = xnn[d];
     if (!ok_all) break;
   }
   if (!ok_all && t < 32) nat_bar_wait(bar, phase ^ 1u);  // MMAs still in flight: bounded wait
