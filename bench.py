@@ -309,6 +309,7 @@ def run_modal(args):
         tc = _working_launches(nb.nat_bem_trace_durations(tc_name))
         nb.nat_bem_trace_enable(False)
         nb.nat_bem_trace_reset()
+    launches0 = nb.nat_bem_trace_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         t0.record(stream)
@@ -317,6 +318,7 @@ def run_modal(args):
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(prob.ks) * args.nrhs
     roof = None
     if tc and tc[1]:
@@ -359,7 +361,7 @@ def run_modal(args):
             "gmres": {"iterations_max": max(i[0] for i in infos), "refinements_max": max(i[1] for i in infos),
                       "max_rel_residual": max(i[2] for i in infos),
                       "not_converged": sum(1 for i in infos if i[3] != 0)},
-            "roofline": roof, "accuracy": acc, "clocks": clk.summary()}
+            "gpu_launches": int(launches), "roofline": roof, "accuracy": acc, "clocks": clk.summary()}
 
 
 def run_mc(args):
@@ -414,6 +416,21 @@ def run_mc(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # per-kernel device times from one untimed step
+    nb.nat_bem_trace_enable(True)
+    nb.nat_bem_trace_select("")
+    nb.nat_bem_trace_reset()
+    step()
+    torch.cuda.synchronize()
+    names = ["assemble_mc", "gemv", "gemv_bf16", "gemv_rhs", "gemv_resid", "ir_residual", "gmres_arnoldi",
+             "gmres_lsq", "eval", "eval_reduce"]
+    kern = {nm: nb.nat_bem_trace_kernel(nm) for nm in names}
+    g = kern["gemv"]
+    kern["gemv"] = tuple(a - b - c - d for a, b, c, d in zip(g, kern["gemv_rhs"], kern["gemv_resid"], kern["gemv_bf16"]))
+    ev = kern["eval"]
+    kern["eval"] = (ev[0] - kern["eval_reduce"][0], ev[1] - kern["eval_reduce"][1])
+    nb.nat_bem_trace_enable(False)
+    launches0 = nb.nat_bem_trace_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         t0.record(stream)
@@ -422,7 +439,32 @@ def run_mc(args):
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(ks)
+    # the matvecs (as for the mesh workloads) and the assembly, which writes L and R (and L's BF16
+    # copy in mixed precision) for every sample pair; the roofline is the dominant one's
+    m = len(Y)
+    peaks, peak_kind = _peaks()
+    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    _, table = roofline({"n": m, "measured": dict(kern, assemble_regular=(0.0, 0)), "working": working},
+                        peaks, peak_kind)
+    bytes_pair = 16 + (4 if args.prec == "bf16" else 0)
+    ta, ca = kern["assemble_mc"]
+    if ca:
+        gbs = (m * m * bytes_pair) / (ta / ca * 1e-3) / 1e9
+        table["assemble_mc"] = {"bound": "hbm", "launches": ca, "avg_ms": ta / ca, "achieved": gbs,
+                                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+                                "algorithmic_bytes_per_launch": m * m * bytes_pair}
+    dom = max(kern, key=lambda nm: kern[nm][0])
+    roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "note": "no roofline: the dominant kernel is latency-bound"}
+    if dom in table:
+        d = table[dom]
+        roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": None, "peak_source": f"{peak_kind} (hbm_gbs)"}
+        if dom in ("gemv", "gemv_bf16"):
+            roof["note"] = ("the operator (8 or 4 x m x ld bytes: 125 or 63 MB at 3956 samples) is about the "
+                            "size of L2 or smaller, so part of each matvec is served from L2")
     p0 = res[0][0].cpu().numpy()
     f0 = res[0][1].cpu().numpy()
     acc = {"surface_rel_err_vs_exact": float(np.linalg.norm(p0 - S.monopole_field(Y, float(ks[0])))
@@ -447,6 +489,9 @@ def run_mc(args):
             "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
             "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
                       "not_converged": sum(1 for i in infos if i[2] != 0)},
+            "gpu_launches": int(launches),
+            "kernels_ms_per_step": {nm: {"ms_total": v[0], "launches": v[1]} for nm, v in kern.items()},
+            "roofline": roof, "rooflines": table,
             "accuracy": acc, "sampler": sampler, "clocks": clk.summary()}
 
 
@@ -487,6 +532,21 @@ def run_dataset(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    # per-kernel device times from one untimed step, and the dominant kernel's roofline
+    nb.nat_bem_trace_reset()
+    nb.nat_bem_trace_select("")
+    nb.nat_bem_trace_enable(True)
+    step()
+    torch.cuda.synchronize()
+    nb.nat_bem_trace_enable(False)
+    kern = _kernel_table(nb)
+    for nm in ("sample_points", "sample_abs", "far_field"):
+        kern[nm] = nb.nat_bem_trace_kernel(nm)
+    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    peaks, peak_kind = _peaks()
+    dom, table = roofline({"n": len(prob.F), "measured": kern, "working": working}, peaks, peak_kind)
+    nb.nat_bem_trace_reset()
+    launches0 = nb.nat_bem_trace_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         t0.record(stream)
@@ -495,8 +555,15 @@ def run_dataset(args):
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
+    launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(prob.ks)
     op.close()
+    roof = None
+    if dom:
+        d = table[dom]
+        roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+                "frac": d["frac"], "traffic": NCU_TRAFFIC_10240.get(dom) if len(prob.F) == 10240 else None,
+                "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else 'derived FP32'})"}
     return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
@@ -504,6 +571,9 @@ def run_dataset(args):
             "config": {"workload": f"dataset_{len(prob.F)}tri_{len(prob.ks)}k_{n_samples}samples_ffat64x32",
                        "samples_per_solve": n_samples, "ffat": [64, 32], "shell": [1.5, 3.0]},
             "training_samples_per_s": n_solves * n_samples / (ms * 1e-3),
+            "gpu_launches": int(launches),
+            "kernels_ms_per_step": {nm: {"ms_total": v[0], "launches": v[1]} for nm, v in kern.items() if v[1]},
+            "roofline": roof,
             "clocks": clk.summary()}
 
 
@@ -881,8 +951,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="natbem", choices=["natbem", "reference"])
-    ap.add_argument("--prec", default="bf16", choices=["fp32", "bf16", "tf32"],
-                    help="interior workload: bf16 = mixed (BF16 inner GMRES, FP32 refinement)")
+    ap.add_argument("--prec", default=None, choices=["fp32", "bf16", "tf32"],
+                    help="bf16 = mixed (BF16 inner GMRES, FP32 refinement); default bf16, fp32 for the "
+                         "Monte-Carlo and Galerkin workloads (their operators stay in or near L2, where the "
+                         "BF16 copy saves little bandwidth and refinement costs iterations)")
     ap.add_argument("--no-compare", dest="compare", action="store_false",
                     help="skip the plain FP32 comparison run of the interior workload")
     ap.add_argument("--n-k", type=int, default=64)
@@ -900,6 +972,8 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()
+    if args.prec is None:
+        args.prec = "fp32" if args.workload in ("mc", "galerkin") else "bf16"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
