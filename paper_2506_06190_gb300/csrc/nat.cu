@@ -17,9 +17,9 @@
 //            layer's input back into A;
 //   output   the last layer (N = n_out rounded up to 16) plus bias goes to global memory (FP32).
 // The encoding of the next tile runs in pieces while each layer's MMAs are in flight (grid level
-// l during layer l from rows requested one layer earlier, the positional encoding spread over
-// three layers), so the table gathers' latency hides behind the tensor cores instead of adding
-// to the tile's critical path.
+// l during layer l from rows requested two layers earlier, the positional encoding spread over
+// the later layers) and collects in TMEM columns next to the accumulators, so the table gathers'
+// latency hides behind the tensor cores instead of adding to the tile's critical path.
 // The weights stay in shared memory for the kernel's lifetime (at most 160 KB) and the biases
 // live in the kernel's parameter space (uniform reads through the constant cache), so HBM only
 // carries the queries, the grid tables (through L2) and the outputs. The tables are half
@@ -181,6 +181,17 @@ __device__ __forceinline__ void nat_tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
   nat_tmem_wait(r);
 }
 
+// Two or four 32-bit values of this thread into its TMEM lane at consecutive columns (the
+// warp's 32 lanes together); complete at the thread's next tcgen05.wait::st.
+__device__ __forceinline__ void nat_tmem_st2(uint32_t taddr, uint32_t a, uint32_t b) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(a), "r"(b) : "memory");
+}
+__device__ __forceinline__ void nat_tmem_st4(uint32_t taddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(a), "r"(b),
+               "r"(c), "r"(d)
+               : "memory");
+}
+
 
 // The D inputs of query q (zeros past the end).
 template <int D>
@@ -245,10 +256,10 @@ __device__ __forceinline__ void nat_fetch(int lvl, const float (&xv)[D], const u
   }
 }
 
-// The four trilinear features of level lvl from its fetched rows, as BF16 pairs in pk[2 lvl],
-// pk[2 lvl + 1].
-template <int D, int P>
-__device__ __forceinline__ void nat_finish(int lvl, const float (&xv)[D], const NatRows& rows, uint32_t (&pk)[P]) {
+// The four trilinear features of level lvl from its fetched rows, as two BF16 pairs.
+template <int D>
+__device__ __forceinline__ void nat_finish(int lvl, const float (&xv)[D], const NatRows& rows, uint32_t& lo,
+                                           uint32_t& hi) {
   int i0[3];
   float w1[3], w0[3];
   nat_cell<D>(lvl, xv, i0, w1);
@@ -270,24 +281,20 @@ __device__ __forceinline__ void nat_finish(int lvl, const float (&xv)[D], const 
     f2 = fmaf(wt, v[c].z, f2);
     f3 = fmaf(wt, v[c].w, f3);
   }
-  pk[2 * lvl] = pack2(f0, f1);
-  pk[2 * lvl + 1] = pack2(f2, f3);
+  lo = pack2(f0, f1);
+  hi = pack2(f2, f3);
 }
 
 // The positional encoding of the condition variables and the frequency (inputs 3..D-1):
 // sin and cos of 2^l pi x_d, l = 0..5, as BF16 pairs after the 16 grid features.
-// part < 0: all inputs; else the inputs d with (d - 3) mod 3 = part.
-template <int D, int P>
-__device__ __forceinline__ void nat_encode_pe(const float (&xv)[D], uint32_t (&pk)[P], int part = -1) {
+// Input d's six pairs, as BF16 pairs.
+__device__ __forceinline__ void nat_pe_input(float xd, uint32_t (&o)[6]) {
 #pragma unroll
-  for (int d = 3; d < D; ++d)
-#pragma unroll
-    for (int l = 0; l < 6; ++l) {
-      if (part >= 0 && (d - 3) % 3 != part) continue;
-      float s, c;
-      sincospif(ldexpf(xv[d], l), &s, &c);  // sin, cos of 2^l pi x_d
-      pk[8 + (d - 3) * 6 + l] = pack2(s, c);
-    }
+  for (int l = 0; l < 6; ++l) {
+    float s, c;
+    sincospif(ldexpf(xd, l), &s, &c);  // sin, cos of 2^l pi x_d
+    o[l] = pack2(s, c);
+  }
 }
 
 // The encoded row of query q as row t of A: the K steps layer 0 reads (2 K0 chunks of 16
@@ -344,7 +351,10 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(nat_smem_u32(&bars[i])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  constexpr uint32_t kCols = G <= 2 ? 256u : 512u;
+  // G groups x 128 accumulator columns, then each group's staging columns for the next
+  // tile's encoded row (8 K0 <= 64 each; G K0 <= 16 since three groups only run with K0 <= 4)
+  constexpr uint32_t kCols = 512u;
+  static_assert(G * 128 + G * 8 * K0 <= 512, "TMEM columns");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(nat_smem_u32(tmem_slot)),
                  "r"(kCols));
@@ -355,6 +365,7 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot + (uint32_t)(g * 128);                 // the group's columns
   const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16);      // this warp's lanes
+  const uint32_t stage = *tmem_slot + (uint32_t)(G * 128 + g * 8 * K0) + ((uint32_t)((warp & 3) * 32) << 16);
   const uint32_t bar = nat_smem_u32(&bars[g]);
   const int offs[4] = {0, off1, off2, off3};
   const uint32_t hmask = (1u << log2) - 1u;
@@ -363,28 +374,38 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
   bool ok_all = true;
 
   // Software pipeline over the group's tiles: while the MMAs of layer l of tile i run, the
-  // group encodes one piece of tile i + 1 into registers (grid level l for l < 4, the positional
-  // encoding at the output layer); the row goes into A once the output layer's MMA has read it.
+  // group encodes one piece of tile i + 1 into its TMEM staging columns (grid level l for l < 4
+  // from rows requested two layers earlier; a share of the positional encoding from layer 1
+  // on); the row goes into A once the output layer's MMA has read it.
   const int64_t tstride = (int64_t)gridDim.x * G;
   int64_t tile = (int64_t)blockIdx.x * G + g;
-  uint32_t pk[8 * K0];
-#pragma unroll
-  for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;  // the padding stays zero
-  float xn[D], xnn[D];                            // inputs of tiles i + 1 and i + 2
-  NatRows rows;                                   // the rows of the level nat_finish uses next
+  float xn[D], xnn[D];  // inputs of tiles i + 1 and i + 2
+  NatRows rb[2];        // requested rows of the levels nat_finish uses next (level l in rb[l & 1])
   {
+    uint32_t pk[8 * K0];
+#pragma unroll
+    for (int i = 0; i < 8 * K0; ++i) pk[i] = 0u;
     float xv[D];
     nat_load_x<D>(x, tile * 128 + t, n, xv);
 #pragma unroll
     for (int lvl = 0; lvl < 4; ++lvl) {
-      nat_fetch<D>(lvl, xv, tables, offs, hmask, dense_mask, rows);
-      nat_finish<D>(lvl, xv, rows, pk);
+      nat_fetch<D>(lvl, xv, tables, offs, hmask, dense_mask, rb[0]);
+      nat_finish<D>(lvl, xv, rb[0], pk[2 * lvl], pk[2 * lvl + 1]);
     }
-    nat_encode_pe<D>(xv, pk);
+#pragma unroll
+    for (int d = 3; d < D; ++d) {
+      uint32_t o[6];
+      nat_pe_input(xv[d], o);
+#pragma unroll
+      for (int l = 0; l < 6; ++l) pk[8 + (d - 3) * 6 + l] = o[l];
+    }
     nat_store_row<K0>(pk, tile * 128 + t, n, sA, t);
+#pragma unroll
+    for (int c = 0; c < 8 * K0; c += 2) nat_tmem_st2(stage + (uint32_t)c, 0u, 0u);  // the padding stays zero
   }
   nat_load_x<D>(x, (tile + tstride) * 128 + t, n, xn);
-  nat_fetch<D>(0, xn, tables, offs, hmask, dense_mask, rows);
+  nat_fetch<D>(0, xn, tables, offs, hmask, dense_mask, rb[0]);
+  nat_fetch<D>(1, xn, tables, offs, hmask, dense_mask, rb[1]);
   for (;; tile += tstride) {
     const int64_t q0 = tile * 128;
     if (q0 >= n) break;  // uniform over the group
@@ -415,18 +436,27 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                      : "memory");
       }
-      // the next tile's piece while the MMAs run: level l from the rows requested a stage
-      // earlier, then the request of level l + 1 (level 0 of the tile after it at the output
-      // layer); a third of the positional encoding during layers 0, 3 and the output layer
-      // (layer 2 carries the hashed level's eight gathers)
+      // the next tile's piece while the MMAs run: level l from the rows requested two layers
+      // earlier into the staging columns, then the request of level l + 2 (of levels 0 and 1 of
+      // the tile after it during layers 2 and 3); input d's positional encoding during layer
+      // 1 + (d - 3) mod 4
       if (l < 4) {
-        nat_finish<D>(l, xn, rows, pk);
-        if (l < 3) nat_fetch<D>(l + 1, xn, tables, offs, hmask, dense_mask, rows);
-        if (l == 0) nat_encode_pe<D>(xn, pk, 1);
-        if (l == 3) nat_encode_pe<D>(xn, pk, 2);
-      } else {
-        nat_fetch<D>(0, xnn, tables, offs, hmask, dense_mask, rows);
-        nat_encode_pe<D>(xn, pk, 0);
+        uint32_t lo, hi;
+        nat_finish<D>(l, xn, rb[l & 1], lo, hi);
+        nat_tmem_st2(stage + (uint32_t)(2 * l), lo, hi);
+        if (l < 2) nat_fetch<D>(l + 2, xn, tables, offs, hmask, dense_mask, rb[l & 1]);
+        else nat_fetch<D>(l - 2, xnn, tables, offs, hmask, dense_mask, rb[l & 1]);
+      }
+      if (l >= 1) {
+#pragma unroll
+        for (int d = 3; d < D; ++d)
+          if ((d - 3) % 4 == l - 1) {  // input d during layer 1 + (d - 3) mod 4
+            uint32_t o[6];
+            nat_pe_input(xn[d], o);
+            const uint32_t c = stage + (uint32_t)(8 + (d - 3) * 6);
+            nat_tmem_st4(c, o[0], o[1], o[2], o[3]);
+            nat_tmem_st2(c + 4u, o[4], o[5]);
+          }
       }
       // one warp polls the mbarrier; the others wait at the group barrier without issuing
       bool ok = true;
@@ -481,6 +511,16 @@ k_nat_forward(const float* __restrict__ x, int64_t n, const uint2* __restrict__ 
           }
         }
         // the output layer's MMAs have read A: the next tile's row goes in
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        uint32_t pk[8 * K0];
+#pragma unroll
+        for (int c = 0; c < 8 * K0; c += 32) {
+          uint32_t v[32];
+          nat_tmem_ld32(stage + (uint32_t)c, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (c + i < 8 * K0) pk[c + i] = v[i];
+        }
         nat_store_row<K0>(pk, q + tstride * 128, n, sA, t);
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
