@@ -777,7 +777,7 @@ def _numpy_threads():
 # capture (profiles/k_nat_forward_nat_inference_1Mqueries.md); traffic grows with the queries.
 # The write figure is what reached DRAM during the launch: most of the 33.6 MB of outputs were
 # still in L2 when it ended.
-NCU_TRAFFIC_NAT_PER_MQUERY = 28.146176e6 + 0.048896e6
+NCU_TRAFFIC_NAT_PER_MQUERY = 28.146944e6 + 0.048128e6
 
 
 def run_uneven(args):
