@@ -52,6 +52,30 @@ struct GalK {
   float gr, gi, yr, yi, xr, xi;
 };
 
+// dny = d . n_y and dnx = d . n_x, given by the caller.
+__device__ __forceinline__ GalK gal_kernels_dn(float dx, float dy, float dz, float k, float w, float dny,
+                                               float dnx) {
+  const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  const float rinv = rsqrtf(r2);
+  const float rho = k * (r2 * rinv);
+  const float nq = rintf(rho * kInvTwoPi);
+  float th = fmaf(-nq, kTwoPiHi, rho);
+  th = fmaf(-nq, kTwoPiLo, th);
+  float sn, cs;
+  __sincosf(th, &sn, &cs);
+  const float gw = rinv * w;
+  GalK o;
+  o.gr = cs * gw;
+  o.gi = sn * gw;
+  const float r2inv = rinv * rinv;
+  const float fr = fmaf(rho, o.gi, o.gr) * r2inv, fi = fmaf(-rho, o.gr, o.gi) * r2inv;
+  o.yr = fr * dny;
+  o.yi = fi * dny;
+  o.xr = -fr * dnx;
+  o.xi = -fi * dnx;
+  return o;
+}
+
 __device__ __forceinline__ GalK gal_kernels(float dx, float dy, float dz, float k, float w, float3 nx,
                                             float3 ny) {
   const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -178,7 +202,7 @@ __global__ void k_gal_geometry(const double* __restrict__ tri, const double* __r
 }
 
 // Pairs sharing no vertex: block row tau = t0 + blockIdx.y, one thread per trial triangle.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 k_gal_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo, const float4* __restrict__ nrm,
               const float4* __restrict__ qp, const int4* __restrict__ vid, const float4* __restrict__ curl,
               int nt, int t0, float k, float2* __restrict__ partL, float2* __restrict__ partR) {
@@ -200,29 +224,63 @@ k_gal_regular(const float4* __restrict__ c_hi, const float4* __restrict__ c_lo, 
   const float4 nt4 = nrm[t], ns4 = nrm[s];
   const float3 nx = make_float3(nt4.x, nt4.y, nt4.z), ny = make_float3(ns4.x, ns4.y, ns4.z);
   float4 qs[7];
+  float qny[7], qnx[7];  // y_q . n_y and y_q . n_x of the trial points' offsets
 #pragma unroll
-  for (int q = 0; q < 7; ++q) qs[q] = qp[7 * (size_t)s + q];
+  for (int q = 0; q < 7; ++q) {
+    qs[q] = qp[7 * (size_t)s + q];
+    qny[q] = fmaf(qs[q].x, ny.x, fmaf(qs[q].y, ny.y, qs[q].z * ny.z));
+    qnx[q] = fmaf(qs[q].x, nx.x, fmaf(qs[q].y, nx.y, qs[q].z * nx.z));
+  }
   GalAcc A;
   gal_acc_zero(A);
 #pragma unroll 1
   for (int p = 0; p < 7; ++p) {
     const float4 qt = qp[7 * (size_t)t + p];
     const float wx = qt.w * kFourPi;  // w_p A_tau (the 1 / (4 pi) is in the trial weights)
-    // inner sums over the trial points, then the test basis functions
-    float sg[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sy[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, sx[2] = {0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      const GalK v = gal_kernels(Dx + (qt.x - qs[q].x), Dy + (qt.y - qs[q].y), Dz + (qt.z - qs[q].z), k, qs[q].w, nx, ny);
+    // x_p - y_q = (D + x_p offset) - y_q offset; its projections likewise
+    const float px = Dx + qt.x, py = Dy + qt.y, pz = Dz + qt.z;
+    const float pny = fmaf(px, ny.x, fmaf(py, ny.y, pz * ny.z)), pnx = fmaf(px, nx.x, fmaf(py, nx.y, pz * nx.z));
+    // inner sums over the trial points, then the test basis functions. The rule's points are
+    // the centroid (weights 1/3 on every basis function) and two orbits whose barycentric
+    // coordinates permute (e, e, 1 - 2e): on an orbit, sum_q mu_b(q) v_q = e S + (1 - 3e) v_q*,
+    // S the orbit's sum and q* its point with 1 - 2e on vertex b.
+    float sg[6], sy[6], sx[2];
+    {
+      const GalK v = gal_kernels_dn(px - qs[0].x, py - qs[0].y, pz - qs[0].z, k, qs[0].w, pny - qny[0], pnx - qnx[0]);
+      const float third = c_gal_b7[0][0];
 #pragma unroll
       for (int b = 0; b < 3; ++b) {
-        const float mb = c_gal_b7[q][b];
-        sg[2 * b] = fmaf(mb, v.gr, sg[2 * b]);
-        sg[2 * b + 1] = fmaf(mb, v.gi, sg[2 * b + 1]);
-        sy[2 * b] = fmaf(mb, v.yr, sy[2 * b]);
-        sy[2 * b + 1] = fmaf(mb, v.yi, sy[2 * b + 1]);
+        sg[2 * b] = third * v.gr;
+        sg[2 * b + 1] = third * v.gi;
+        sy[2 * b] = third * v.yr;
+        sy[2 * b + 1] = third * v.yi;
       }
-      sx[0] += v.xr;
-      sx[1] += v.xi;
+      sx[0] = v.xr;
+      sx[1] = v.xi;
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const int q0 = 1 + 3 * o;  // points q0, q0 + 1, q0 + 2 carry 1 - 2e on vertex 2, 1, 0
+      float vg[3][4];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int q = q0 + i;
+        const GalK v = gal_kernels_dn(px - qs[q].x, py - qs[q].y, pz - qs[q].z, k, qs[q].w, pny - qny[q], pnx - qnx[q]);
+        vg[i][0] = v.gr;
+        vg[i][1] = v.gi;
+        vg[i][2] = v.yr;
+        vg[i][3] = v.yi;
+        sx[0] += v.xr;
+        sx[1] += v.xi;
+      }
+      const float e = c_gal_b7[q0][0], f = c_gal_b7[q0][2] - e;  // e and 1 - 3e
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float S = e * ((vg[0][c] + vg[1][c]) + vg[2][c]);
+        float* acc = c < 2 ? sg : sy;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) acc[2 * b + (c & 1)] += fmaf(f, vg[2 - b][c], S);
+      }
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
