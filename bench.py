@@ -716,18 +716,18 @@ def run_nat(args):
     k_ms, k_launches = nb.nat_bem_trace_kernel("nat_forward")
     launches = nb.nat_bem_trace_launches() - launches0
     nb.nat_bem_trace_enable(False)
-    # end to end: host inputs in, host outputs back, every step
+    # end to end through the public call with pinned host buffers (inputs in, outputs back,
+    # every call; the library overlaps the copies with the kernels chunk by chunk); the call
+    # blocks, so the host clock times it
     xh = torch.from_numpy(x).pin_memory()
     oh = torch.empty((n, 8), dtype=torch.float32).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps * batches):
-        xd.copy_(xh, non_blocking=True)
-        f.forward(xd, out)
-        oh.copy_(out, non_blocking=True)
-    e1.record(stream)
+    f.forward(xh, oh, stream=stream.cuda_stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    t_a = time.perf_counter()
+    for _ in range(args.steps * batches):
+        f.forward(xh, oh, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t_a) * 1e3
     width0 = 16 + 12 * 3  # grid features + P(v_1, v_2) + P(f)
     flops_q = 2 * (width0 * 128 + 3 * 128 * 128 + 128 * 8)  # the MLP's multiply-adds, unpadded
     kernel_ms = k_ms / max(k_launches, 1)

@@ -448,9 +448,12 @@ NAT_BEM_API nat_bem_status nat_bem_trace_durations(const char* name, float* out_
  *   NAT_BEM_EINVAL: NULL argument, n_cond not in 0..8, n_out not in 1..128, table_log2 not in
  *   12..24. NAT_BEM_ENOMEM / NAT_BEM_ECUDA: device allocation or copy failed.
  * nat_field_forward: x n x D float32 row-major, out n x n_out float32 row-major, host or device
- *   pointers, on cuda_stream; blocks until out is written; n = 0 does nothing. NAT_BEM_EINVAL
- *   for NULL or n < 0; NAT_BEM_ETIMEOUT if a bounded wait on the tensor cores gave up (the
- *   output is then incomplete).
+ *   pointers, on cuda_stream; blocks until out is written; n = 0 does nothing. With a host x or
+ *   out and n > 2^20, the queries go in chunks of 2^20 whose uploads and downloads (on two copy
+ *   streams the field keeps) overlap the other chunks' kernels; pinned host memory makes the
+ *   copies asynchronous. Calls on one field must not run concurrently. NAT_BEM_EINVAL for NULL
+ *   or n < 0; NAT_BEM_ETIMEOUT if a bounded wait on the tensor cores gave up (the output is
+ *   then incomplete).
  * nat_field_destroy frees the device copies (NULL is a no-op).
  */
 typedef struct nat_field nat_field;

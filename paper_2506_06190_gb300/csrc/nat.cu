@@ -73,6 +73,8 @@ struct nat_field {
   int device = 0;
   cudaStream_t stream = nullptr;
   int* err = nullptr;           // bounded-wait failures
+  // host buffers: upload and download streams, created on first use
+  cudaStream_t up = nullptr, down = nullptr;
 };
 
 namespace natbem {
@@ -630,6 +632,106 @@ static nat_bem_status nat_launch(const nat_field* f, const float* dx, int64_t n,
 
 using namespace natbem;
 
+namespace natbem {
+namespace {
+constexpr int64_t kNatChunk = int64_t(1) << 20;  // queries per chunk on the host-buffer path
+
+// Host inputs or outputs: chunks of kNatChunk queries in two device buffers each, uploads on
+// one stream, the kernels on the caller's, downloads on another, so that chunk c + 1's upload
+// and chunk c - 1's download run during chunk c's kernel. Queries are independent: the results
+// are the same as one call on device buffers.
+nat_bem_status nat_forward_pipelined(nat_field* f, const float* x, bool xdev, int64_t n, float* out, bool odev,
+                                     cudaStream_t s) {
+  const int D = 4 + f->n_cond;
+  if (!f->up) {
+    if (cudaStreamCreateWithFlags(&f->up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&f->down, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("nat_field_forward: could not create copy streams");
+      return NAT_BEM_ECUDA;
+    }
+  }
+  float *bx[2] = {nullptr, nullptr}, *bo[2] = {nullptr, nullptr};
+  cudaEvent_t ev[7] = {};  // start, uploaded x2, computed x2, downloaded x2
+  auto cleanup = [&]() {
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+      dev_free(bx[b], s);
+      dev_free(bo[b], s);
+    }
+  };
+  nat_bem_status st = NAT_BEM_OK;
+  for (int b = 0; b < 2 && st == NAT_BEM_OK; ++b) {
+    if (!xdev) st = dev_alloc_n(&bx[b], (size_t)kNatChunk * D, s);
+    if (st == NAT_BEM_OK && !odev) st = dev_alloc_n(&bo[b], (size_t)kNatChunk * f->n_out, s);
+  }
+  if (st != NAT_BEM_OK) {
+    cleanup();
+    return st;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+  // the buffers were allocated on s; the copy streams start after that
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(f->up, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(f->down, ev[0], 0);
+  cudaEvent_t *uploaded = ev + 1, *computed = ev + 3, *downloaded = ev + 5;
+  const int64_t chunks = (n + kNatChunk - 1) / kNatChunk;
+  for (int64_t c = 0; c < chunks && e == cudaSuccess && st == NAT_BEM_OK; ++c) {
+    const int b = (int)(c & 1);
+    const int64_t q0 = c * kNatChunk, cnt = std::min(kNatChunk, n - q0);
+    const float* cx = x + q0 * D;
+    float* co = out + q0 * f->n_out;
+    if (!xdev) {
+      if (c >= 2) e = cudaStreamWaitEvent(f->up, computed[b], 0);  // chunk c - 2 has read bx[b]
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bx[b], cx, (size_t)cnt * D * sizeof(float), cudaMemcpyHostToDevice, f->up);
+      if (e == cudaSuccess) e = cudaEventRecord(uploaded[b], f->up);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, uploaded[b], 0);
+      cx = bx[b];
+    }
+    if (!odev) {
+      if (c >= 2 && e == cudaSuccess) e = cudaStreamWaitEvent(s, downloaded[b], 0);  // bo[b] is free
+      co = bo[b];
+    }
+    if (e != cudaSuccess) break;
+    st = nat_launch(f, cx, cnt, co, s);
+    if (st != NAT_BEM_OK) break;
+    e = cudaEventRecord(computed[b], s);
+    if (!odev) {
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(f->down, computed[b], 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + q0 * f->n_out, bo[b], (size_t)cnt * f->n_out * sizeof(float),
+                            cudaMemcpyDeviceToHost, f->down);
+      if (e == cudaSuccess) e = cudaEventRecord(downloaded[b], f->down);
+    }
+  }
+  int err = 0;
+  if (e == cudaSuccess && st == NAT_BEM_OK) {
+    // the caller's stream ends after the last download; the buffers are freed on it
+    e = cudaEventRecord(ev[0], f->down);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[0], 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, f->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  } else {
+    cudaStreamSynchronize(f->up);
+    cudaStreamSynchronize(f->down);
+    cudaStreamSynchronize(s);
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("nat_field_forward: ") + cudaGetErrorString(e));
+    st = NAT_BEM_ECUDA;
+  } else if (st == NAT_BEM_OK && err) {
+    set_error("nat_field_forward: a bounded wait on the tensor cores gave up");
+    st = NAT_BEM_ETIMEOUT;
+  }
+  cleanup();
+  return st;
+}
+}  // namespace
+}  // namespace natbem
+
 extern "C" {
 
 nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log2, const float* tables,
@@ -722,6 +824,9 @@ nat_bem_status nat_field_forward(const nat_field* f, const float* x, int64_t n, 
     if (n == 0) return NAT_BEM_OK;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     const int D = 4 + f->n_cond;
+    const bool xdev = is_device_pointer(x), odev_ = is_device_pointer(out);
+    if ((!xdev || !odev_) && n > kNatChunk)
+      return nat_forward_pipelined(const_cast<nat_field*>(f), x, xdev, n, out, odev_, s);
     const float* dx = nullptr;
     float* tx = nullptr;
     NB_TRY(to_device(x, (size_t)n * D, s, &dx, &tx));
@@ -759,6 +864,8 @@ nat_bem_status nat_field_forward(const nat_field* f, const float* x, int64_t n, 
 
 void nat_field_destroy(nat_field* f) {
   if (!f) return;
+  if (f->up) cudaStreamDestroy(f->up);
+  if (f->down) cudaStreamDestroy(f->down);
   dev_free(f->tables, f->stream);
   dev_free(f->weights, f->stream);
   dev_free(f->err, f->stream);

@@ -10,6 +10,8 @@ few such steps through the later layers; with a single output, whose RMS is not 
 than one hidden activation's contribution, the largest deviation reaches about 1% of the RMS:
 bound 3e-2.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -113,3 +115,37 @@ def test_full_size_sampled(nb):
     rows = np.concatenate([rows, [0, n - 1]])
     ref = O.forward(x[rows].astype(np.float64), m["tables"], m["weights"], m["biases"], m["table_log2"])
     _check(out[rows], ref)
+
+
+def test_host_buffers_pipelined_match_device(nb):
+    """Host inputs or outputs beyond 2^20 queries run in overlapped chunks; every query is
+    independent, so the results equal one call on device buffers bit for bit (2^21 + 777
+    queries: three chunks, the last ragged)."""
+    torch = pytest.importorskip("torch")
+    m = O.random_model(seed=8)
+    n = (1 << 21) + 777
+    x = _inputs(n, 6, 33)
+    with _field(nb, m) as f:
+        xt = torch.from_numpy(x).cuda()
+        ref = f.forward(xt)
+        torch.cuda.synchronize()
+        ref = ref.cpu().numpy()
+        host = f.forward(x)                                   # host in, host out
+        assert np.array_equal(host, ref)
+        xp = torch.from_numpy(x).pin_memory()
+        op = torch.empty((n, 8), dtype=torch.float32).pin_memory()
+        st = nb.lib().nat_field_forward(f.handle, ctypes.c_void_p(xp.data_ptr()), n,
+                                        ctypes.c_void_p(op.data_ptr()), None)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        assert np.array_equal(op.numpy(), ref)                # pinned host in and out
+        od = torch.empty((n, 8), dtype=torch.float32, device="cuda")
+        st = nb.lib().nat_field_forward(f.handle, ctypes.c_void_p(xp.data_ptr()), n,
+                                        ctypes.c_void_p(od.data_ptr()), None)
+        assert st == nb.NAT_BEM_OK
+        torch.cuda.synchronize()
+        assert np.array_equal(od.cpu().numpy(), ref)          # host in, device out
+        oh = np.zeros((n, 8), np.float32)
+        st = nb.lib().nat_field_forward(f.handle, ctypes.c_void_p(xt.data_ptr()), n,
+                                        ctypes.c_void_p(oh.ctypes.data), None)
+        assert st == nb.NAT_BEM_OK
+        assert np.array_equal(oh, ref)                        # device in, host out
