@@ -106,3 +106,31 @@ def test_mc_rejects_non_unit_normals(nb):
     with pytest.raises(nb.NatBemError) as e:
         nb.Operator.assemble_mc(Y, N, A, 2.0)
     assert "EINVAL" in str(e.value)
+
+
+def test_gpu_poisson_samples_through_the_mc_solve(nb, oracle_lib):
+    """The Monte-Carlo path end to end on the device: Poisson-disk samples from the GPU sampler
+    (identical to the sampler's reference), Monte-Carlo operators on them, solve and field,
+    against the FP64 oracle on the same samples; and against the exact interior-source field
+    (the Monte-Carlo discretisation error)."""
+    from oracle import poisson as PS
+    Vs, F = S.ring_sphere(3000)
+    V = S.perturbed_ellipsoid(Vs, 17)
+    u, radius = S.poisson_draws(V, F, 1500, 21)
+    idx, Y, N = nb.nat_bem_poisson_sample(V, F, u, radius)
+    ai, ay, an = PS.sample(V, F, u, radius)
+    assert np.array_equal(idx, ai) and np.array_equal(Y, ay) and np.array_equal(N, an)
+    P0, P1, P2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    A = 0.5 * float(np.linalg.norm(np.cross(P1 - P0, P2 - P0), axis=1).sum())
+    k = 3.0
+    g = S.monopole_neumann_at(Y, N, k)
+    pts = S.fibonacci_points(64, 4.0)
+    p_ref, info = oracle_lib.mc_solve(Y, N, A, k, g, tol=1e-10)
+    f_ref = oracle_lib.mc_evaluate(Y, N, A, k, pts, p_ref, g)
+    with nb.Operator.assemble_mc(Y, N, A, k) as op:
+        p, sinfo, st = op.solve(g.astype(np.complex64))
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        f = op.evaluate(pts, p, g.astype(np.complex64))
+    assert _rel(p, p_ref) < SOL_TOL
+    assert _rel(f, f_ref) < SOL_TOL
+    assert _rel(f, S.monopole_field(pts, k)) < 0.08
