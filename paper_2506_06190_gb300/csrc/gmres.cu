@@ -2009,6 +2009,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));  // this solve's bounded-wait flags
   const int n = (int)op->n;
   const dim3 vec_grid((n + kChunk - 1) / kChunk, nrhs);
   // b = R g

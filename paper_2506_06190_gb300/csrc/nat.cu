@@ -670,7 +670,7 @@ nat_bem_status nat_forward_pipelined(nat_field* f, const float* x, bool xdev, in
     cleanup();
     return st;
   }
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(f->err, 0, sizeof(int), s);  // this call's bounded-wait flag
   for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
   // the buffers were allocated on s; the copy streams start after that
   if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
@@ -837,6 +837,10 @@ nat_bem_status nat_field_forward(const nat_field* f, const float* x, int64_t n, 
     if (!odev) {
       st = dev_alloc_n(&tout, (size_t)n * f->n_out, s);
       dout = tout;
+    }
+    if (st == NAT_BEM_OK && cudaMemsetAsync(f->err, 0, sizeof(int), s) != cudaSuccess) {  // this call's flag
+      set_error("nat_field_forward: could not reset the wait flag");
+      st = NAT_BEM_ECUDA;
     }
     if (st == NAT_BEM_OK) st = nat_launch(f, dx, n, dout, s);
     int err = 0;
