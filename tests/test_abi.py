@@ -99,7 +99,7 @@ def test_assemble_rejects_bad_input(nb, case):
 
 @pytest.mark.parametrize("case", ["one_sample", "area_zero", "area_nan", "k_zero", "null"])
 def test_assemble_mc_rejects_bad_input(nb, case):
-    """Argument checks that need no device (normals and positions are checked on the GPU machine)."""
+    """Argument checks that need no device (normals and positions are checked on the device)."""
     Y, N, A = S.sphere_samples(64)
     m, area, k = 64, A, 2.0
     if case == "one_sample":
