@@ -41,6 +41,14 @@ def main():
         json.dump({"mesh": "icosphere level 2 (320 triangles)", "k": 2.0, "neumann": 1.0,
                    "points": "16 Fibonacci points at radius 3",
                    "p": cplx(p), "field": cplx(fld)}, f, indent=0)
+    # the Poisson-disk sampler (Sec. 4.2, in this build's grid form): accepted draws and
+    # positions on a small case
+    from oracle import poisson as PS
+    u = np.random.default_rng(11).random((400, 3))
+    idx, x, _ = PS.sample(V, F, u, 0.25)
+    with open(os.path.join(HERE, "poisson_icosphere2_r0.25.json"), "w") as f:
+        json.dump({"mesh": "icosphere level 2 (320 triangles)", "draws": "numpy default_rng(11).random((400, 3))",
+                   "radius": 0.25, "accepted": [int(i) for i in idx], "positions": x.tolist()}, f, indent=0)
 
 
 if __name__ == "__main__":

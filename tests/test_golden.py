@@ -36,3 +36,13 @@ def test_pulsating_icosphere(oracle_lib):
     assert np.allclose(p, _c(d["p"]), rtol=1e-11)
     fld = oracle_lib.evaluate(V, F, d["k"], S.fibonacci_points(16, 3.0), p, g)
     assert np.allclose(fld, _c(d["field"]), rtol=1e-11)
+
+
+def test_poisson_sampler():
+    from oracle import poisson as PS
+    d = _load("poisson_icosphere2_r0.25.json")
+    V, F = S.icosphere(2)
+    u = np.random.default_rng(11).random((400, 3))
+    idx, x, _ = PS.sample(V, F, u, d["radius"])
+    assert idx.tolist() == d["accepted"]
+    assert np.array_equal(x, np.asarray(d["positions"]))
