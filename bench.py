@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 
 import synthetic as S  # noqa: E402
 
-METRIC = "BEM solves/s at <=1e-4 rel err vs FP64 oracle (plain FP32 and mixed), p50/p99 ms"
+METRIC = "BEM solves/s at \u22641e-4 rel err vs FP64 oracle, mixed vs plain FP32; p50/p99 ms"
 UNIT = "solves/s"
 
 
