@@ -169,6 +169,8 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
     n = prob.F.shape[0]
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[prec_name]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     Vd = torch.from_numpy(prob.V).to(dev)
     Fd = torch.from_numpy(prob.F).to(dev)
     Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
@@ -277,6 +279,8 @@ def run_modal(args):
                          [S.sh_neumann(V, F, args.nrhs, 3002)] * args.n_k, S.shell_points(4096, 2.0, 5.0, 3003))
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     dev = torch.device("cuda", 0)
     Vd, Fd = torch.from_numpy(prob.V).to(dev), torch.from_numpy(prob.F).to(dev)
     G = torch.from_numpy(np.ascontiguousarray(prob.neumann[0].T).astype(np.complex64)).to(dev)
@@ -396,6 +400,8 @@ def run_mc(args):
                    "samples": len(Y), "per": "one call, host wall clock, outputs on the device"}
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     Yd, Nd, Pd = (torch.from_numpy(a).to(dev) for a in (Y, N, pts))
     Gd = [torch.from_numpy(g.astype(np.complex64)).to(dev) for g in gs]
     stream = torch.cuda.current_stream(dev)
@@ -507,6 +513,8 @@ def run_dataset(args):
     prob = workload(args.n_k, args.n_tri)
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     dev = torch.device("cuda", 0)
     Vd, Fd = torch.from_numpy(prob.V).to(dev), torch.from_numpy(prob.F).to(dev)
     Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
@@ -596,6 +604,8 @@ def run_galerkin(args):
     prob = S.interior_source(n_tri=args.n_tri, n_k=args.n_k, ka_range=(0.5, 10.0))
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     dev = torch.device("cuda", 0)
     Vd, Fd, Pd = (torch.from_numpy(a).to(dev) for a in (prob.V, prob.F, prob.points))
     Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
@@ -791,6 +801,8 @@ def run_uneven(args):
     probs = S.uneven_batch(n_mesh=args.n_mesh)
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     dev = torch.device("cuda", 0)
     jobs = []
     for pr in probs:
@@ -839,6 +851,8 @@ def run_serving(args):
         pool[int(nt)] = (S.perturbed_ellipsoid(Vs, 5000 + int(nt)), F)
     prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
+    if args.inner_tol is not None:
+        opts.inner_tol = args.inner_tol
     dev = torch.device("cuda", 0)
     reqs = []
     pts = torch.from_numpy(S.fibonacci_points(256, 4.0)).to(dev)
@@ -969,6 +983,8 @@ def main():
     ap.add_argument("--n-req", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--inner-tol", type=float, default=None,
+                    help="mixed precision: tolerance of each inner solve (default: the library's)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()

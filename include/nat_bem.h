@@ -70,7 +70,7 @@ typedef struct {
   int32_t max_iter;          /* GMRES iterations (plain), total inner iterations (mixed) (200) */
   nat_bem_precision prec;    /* arithmetic of the solve (NAT_BEM_PREC_FP32)                      */
   int32_t inner_max_iter;    /* mixed: iterations per inner solve (60)                            */
-  double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-3)              */
+  double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-2)              */
   int32_t max_refinements;   /* mixed: outer refinement sweeps (10)                               */
 } nat_bem_opts;
 

@@ -144,7 +144,7 @@ void nat_bem_opts_default(nat_bem_opts* o) {
   o->max_iter = 200;
   o->prec = NAT_BEM_PREC_FP32;
   o->inner_max_iter = 60;
-  o->inner_tol = 1e-3;
+  o->inner_tol = 1e-2;
   o->max_refinements = 10;
 }
 

@@ -42,7 +42,7 @@ def test_opts_defaults(nb):
     o = nb.nat_bem_opts_default()
     assert o.adj_subdiv_levels == 2 and o.self_theta_pts == 16
     assert o.tol == 1e-6 and o.max_iter == 200 and o.prec == nb.PREC_FP32
-    assert o.inner_max_iter == 60 and o.inner_tol == 1e-3 and o.max_refinements == 10
+    assert o.inner_max_iter == 60 and o.inner_tol == 1e-2 and o.max_refinements == 10
 
 
 def test_required_bytes(nb):
