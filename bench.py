@@ -683,25 +683,23 @@ def run_nat(args):
     """Neural acoustic transfer field inference (paper Sec. 3.3, 3.4): --n-queries listening
     points (theta/pi, phi/2pi, r_norm, v_1, v_2, f) uniform in [0, 1]^6 through the grid +
     positional encoding and the 4 x 128 MLP to 8 outputs (e.g. 8 modes), one fused tensor-core
-    kernel per call. Random BF16 weights and hash tables of 2^18 rows (the trained model is not
-    available). Reports queries/s; the roofline counts the MLP's algorithmic FLOPs (first layer
-    52 wide, no padding) against the measured BF16 peak."""
+    kernel per call. Random FP32 parameters from synthetic.nat_params with hash tables of 2^18
+    rows (the trained model is not available); the library stores them in FP16 / BF16. Reports
+    queries/s; the roofline counts the MLP's algorithmic FLOPs (first layer 52 wide, no padding)
+    against the measured BF16 peak."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
-    from oracle import nat as O  # parameter generator and, for the CPU leg, the reference
+    import synthetic as S
     nb_build.build()
     n = args.n_queries
-    m = O.random_model(n_cond=2, n_out=8, table_log2=18, seed=0)
-    tables = np.concatenate(m["tables"], axis=0).astype(np.float32)
-    w = np.concatenate([O.bf16_bits(W).ravel() for W in m["weights"]])
-    b = np.concatenate(m["biases"]).astype(np.float32)
+    m = S.nat_params(n_cond=2, n_out=8, table_log2=18, seed=0)
     dev = torch.device("cuda", 0)
-    x = np.random.default_rng(11).random((n, 6)).astype(np.float32)
+    x = S.nat_queries(n, 6, 11)
     xd = torch.from_numpy(x).to(dev)
     out = torch.empty((n, 8), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    f = nb.NatField(2, 8, 18, tables, w, b)
+    f = nb.NatField.from_params(m)
     batches = 64  # one step: 64 calls of n queries
 
     def step():
@@ -762,15 +760,19 @@ def run_nat(args):
                          "flops_per_query": flops_q, "peak_source": f"{peak_kind} (bf16_tflops)"},
             "clocks": clk.summary()}
     if args.cpu:
+        from oracle import nat as O  # the CPU leg: the FP64 network and its rounding bound
         ns = 1 << 16
         xs = x[:ns].astype(np.float64)
         t = time.perf_counter()
         ref = O.forward(xs, m["tables"], m["weights"], m["biases"], 18)
         dt = time.perf_counter() - t
         got = out[:ns].cpu().numpy().astype(np.float64)
+        sig = O.rounding_sigma(xs[:4096], m["tables"], m["weights"], m["biases"], 18)
         line["cpu_baseline"] = {"value": ns / dt, "unit": "queries/s", "cores": _numpy_threads(),
                                 "kind": "oracle", "sample": f"first {ns} queries"}
-        line["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+        line["accuracy"] = {"rel_l2_vs_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                            "max_dev_in_sigma": float(np.max(np.abs(got[:4096] - ref[:4096]) / sig)),
+                            "bound_sigma": 12.0}
     f.close()
     return line
 

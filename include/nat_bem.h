@@ -442,8 +442,8 @@ NAT_BEM_API nat_bem_status nat_bem_trace_durations(const char* name, float* out_
  *   tables  float32, the four levels' rows one level after the other, 4 features per row;
  *           level l has min((N_l + 1)^3, 2^table_log2) rows. The field keeps them in half
  *           precision (rounded to nearest, as tiny-cuda-nn stores grid parameters);
- *   weights BF16 bit patterns (uint16), row-major [out][in]: four 128 x 128 hidden layers, then
- *           the n_out x 128 output layer;
+ *   weights float32, row-major [out][in]: four 128 x 128 hidden layers, then the n_out x 128
+ *           output layer. The field keeps them in BF16 (rounded to nearest-even on creation);
  *   biases  float32: 4 x 128, then n_out.
  *   NAT_BEM_EINVAL: NULL argument, n_cond not in 0..8, n_out not in 1..128, table_log2 not in
  *   12..24. NAT_BEM_ENOMEM / NAT_BEM_ECUDA: device allocation or copy failed.
@@ -458,7 +458,7 @@ NAT_BEM_API nat_bem_status nat_bem_trace_durations(const char* name, float* out_
  */
 typedef struct nat_field nat_field;
 NAT_BEM_API nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log2,
-                                            const float* tables, const uint16_t* weights,
+                                            const float* tables, const float* weights,
                                             const float* biases, void* cuda_stream, nat_field** out);
 NAT_BEM_API nat_bem_status nat_field_forward(const nat_field* f, const float* x, int64_t n,
                                              float* out, void* cuda_stream);

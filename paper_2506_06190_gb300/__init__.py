@@ -658,17 +658,17 @@ def _f32_ptr(x, width=None):
     return ctypes.c_void_p(a.ctypes.data), a
 
 
-def nat_field_create(n_cond: int, n_out: int, table_log2: int, tables, weights_bf16, biases,
+def nat_field_create(n_cond: int, n_out: int, table_log2: int, tables, weights, biases,
                      stream=None) -> ctypes.c_void_p:
-    """tables: float32 rows of the four levels back to back (rows x 4); weights_bf16: uint16
-    BF16 bit patterns, four 128 x 128 layers then n_out x 128, concatenated; biases: float32."""
+    """tables: float32 rows of the four levels back to back (rows x 4); weights: float32, four
+    128 x 128 layers then n_out x 128, concatenated (row-major [out][in]); biases: float32.
+    The library rounds the tables to FP16 and the weights to BF16 itself."""
     pt, kt = _f32_ptr(tables)
-    w = np.ascontiguousarray(weights_bf16, dtype=np.uint16)
+    pw, kw = _f32_ptr(weights)
     pb, kb = _f32_ptr(biases)
     h = ctypes.c_void_p()
-    _check(lib().nat_field_create(int(n_cond), int(n_out), int(table_log2), pt,
-                                  ctypes.c_void_p(w.ctypes.data), pb, _stream_of(None, stream),
-                                  ctypes.byref(h)))
+    _check(lib().nat_field_create(int(n_cond), int(n_out), int(table_log2), pt, pw, pb,
+                                  _stream_of(None, stream), ctypes.byref(h)))
     return h
 
 
@@ -699,11 +699,19 @@ def nat_field_destroy(field):
 
 
 class NatField:
-    """Owning wrapper of a nat_field handle (parameters as the oracle's random_model returns)."""
+    """Owning wrapper of a nat_field handle: float32 tables (rows x 4, levels back to back),
+    weights (concatenated row-major layers) and biases."""
 
-    def __init__(self, n_cond, n_out, table_log2, tables, weights_bf16, biases, stream=None):
+    def __init__(self, n_cond, n_out, table_log2, tables, weights, biases, stream=None):
         self.n_cond, self.n_out = int(n_cond), int(n_out)
-        self.handle = nat_field_create(n_cond, n_out, table_log2, tables, weights_bf16, biases, stream)
+        self.handle = nat_field_create(n_cond, n_out, table_log2, tables, weights, biases, stream)
+
+    @classmethod
+    def from_params(cls, params, stream=None):
+        """From a dict with n_cond, n_out, table_log2 and lists of tables, weights, biases."""
+        cat = lambda xs: np.concatenate([np.asarray(a, dtype=np.float32).ravel() for a in xs])
+        return cls(params["n_cond"], params["n_out"], params["table_log2"], cat(params["tables"]),
+                   cat(params["weights"]), cat(params["biases"]), stream)
 
     def forward(self, x, out=None, stream=None):
         if int(x.shape[1]) != 4 + self.n_cond:

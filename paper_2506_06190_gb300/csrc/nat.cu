@@ -560,6 +560,16 @@ __global__ void k_nat_pack(const float4* __restrict__ in, int N, int dense, int6
   }
 }
 
+// The caller's FP32 weights (w_in values: four 128 x 128 layers, then n_out x 128) to BF16
+// rounded to nearest-even, with the output layer's padding rows (up to n16) zero.
+__global__ void k_nat_weights_bf16(const float* __restrict__ in, int64_t w_in, int64_t w_out,
+                                   uint16_t* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= w_out) return;
+  const __nv_bfloat16 v = __float2bfloat16_rn(i < w_in ? in[i] : 0.0f);
+  out[i] = *reinterpret_cast<const uint16_t*>(&v);
+}
+
 template <int D>
 static nat_bem_status nat_launch_d(const nat_field* f, const float* dx, int64_t n, float* dout, cudaStream_t s,
                                    int sms, bool& attr_done) {
@@ -735,7 +745,7 @@ nat_bem_status nat_forward_pipelined(nat_field* f, const float* x, bool xdev, in
 extern "C" {
 
 nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log2, const float* tables,
-                                const uint16_t* weights, const float* biases, void* cuda_stream,
+                                const float* weights, const float* biases, void* cuda_stream,
                                 nat_field** out) {
   try {
     clear_error();
@@ -776,14 +786,20 @@ nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log
     };
     f->n16 = (n_out + 15) / 16 * 16;
     const size_t w_rows = (size_t)4 * 128 + (size_t)f->n16;
+    // weights: four 128 x 128 layers, then n_out x 128; the output layer is padded to n16 rows
+    const size_t w_in = (size_t)4 * 128 * 128 + (size_t)n_out * 128;
     const float4* din = nullptr;
     float4* tin = nullptr;
+    const float* dw = nullptr;
+    float* tw = nullptr;
     nat_bem_status st = to_device(reinterpret_cast<const float4*>(tables), (size_t)rows, s, &din, &tin);
+    if (st == NAT_BEM_OK) st = to_device(weights, w_in, s, &dw, &tw);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&f->tables, (size_t)units, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&f->weights, w_rows * 128, s);
     if (st == NAT_BEM_OK) st = dev_alloc_n(&f->err, 1, s);
     if (st != NAT_BEM_OK) {
       dev_free(tin, s);
+      dev_free(tw, s);
       return fail(st);
     }
     for (int l = 0; l < 4; ++l) {
@@ -792,16 +808,15 @@ nat_bem_status nat_field_create(int32_t n_cond, int32_t n_out, int32_t table_log
       k_nat_pack<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(din + in_off[l], N, dense[l] ? 1 : 0, in_rows[l],
                                                                 f->tables + f->level_off[l]);
     }
-    // weights: four 128 x 128 layers, then n_out x 128; the output layer is padded to n16 rows
-    const size_t w_in = (size_t)4 * 128 * 128 + (size_t)n_out * 128;
-    cudaError_t e = cudaMemsetAsync(f->weights, 0, w_rows * 128 * sizeof(uint16_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(f->err, 0, sizeof(int), s);
+    const int64_t w_out = (int64_t)w_rows * 128;
+    k_nat_weights_bf16<<<(unsigned)((w_out + 255) / 256), 256, 0, s>>>(dw, (int64_t)w_in, w_out, f->weights);
+    cudaError_t e = cudaMemsetAsync(f->err, 0, sizeof(int), s);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(f->weights, weights, w_in * sizeof(uint16_t), cudaMemcpyDefault, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(f->bias.b, biases, ((size_t)4 * 128 + n_out) * sizeof(float), cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     dev_free(tin, s);
+    dev_free(tw, s);
     if (e != cudaSuccess) {
       set_error(std::string("nat_field_create: copy failed: ") + cudaGetErrorString(e));
       return fail(NAT_BEM_ECUDA);

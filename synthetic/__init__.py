@@ -27,7 +27,7 @@ __all__ = [
     "fibonacci_points", "shell_points", "log_uniform", "real_sph_harm", "sh_neumann",
     "monopole_neumann", "monopole_field", "uniform_neumann", "cos_theta_neumann", "Problem",
     "pulsating_sphere", "interior_source", "modal_multirhs", "uneven_batch", "serving_stream",
-    "tetrahedron", "octahedron",
+    "tetrahedron", "octahedron", "nat_params", "nat_queries",
 ]
 
 
@@ -476,3 +476,33 @@ def mc_interior_source(seed: int = 6000, n_tri: int = 10240, M: int = 4096, n_k:
     pts = fibonacci_points(n_points, R)
     return (Y, N, area, ks, [monopole_neumann_at(Y, N, k) for k in ks], pts,
             [monopole_field(pts, k) for k in ks])
+
+
+# ------------------------------------------------------- neural acoustic transfer field
+NAT_LEVELS = (8, 16, 32, 64)  # grid cells per axis of the four levels (paper Sec. 3.4)
+NAT_WIDTH = 128               # hidden width; four hidden layers (paper Sec. 3.4)
+
+
+def nat_params(n_cond: int = 2, n_out: int = 8, table_log2: int = 18, seed: int = 0):
+    """Seeded random parameters of the neural transfer field (the trained networks are not
+    available): plain float32 draws, with no rounding to any storage precision.
+
+    tables: one (rows, 4) array per level, rows = min((N + 1)^3, 2^table_log2), U(-1, 1);
+    weights: four (128, 128) arrays, then (n_out, 128), N(0, 2/128) (He initialisation, so the
+    ReLU layers keep the activations' scale); biases: four of 128, then n_out, N(0, 0.05^2).
+    Returns a dict with those lists and the shape arguments."""
+    rng = np.random.default_rng(seed)
+    tables = [rng.uniform(-1.0, 1.0, size=(min((N + 1) ** 3, 1 << table_log2), 4)).astype(np.float32)
+              for N in NAT_LEVELS]
+    weights, biases = [], []
+    for l in range(5):
+        n_o = n_out if l == 4 else NAT_WIDTH
+        weights.append(rng.normal(0.0, math.sqrt(2.0 / NAT_WIDTH), size=(n_o, NAT_WIDTH)).astype(np.float32))
+        biases.append(rng.normal(0.0, 0.05, size=n_o).astype(np.float32))
+    return dict(n_cond=n_cond, n_out=n_out, table_log2=table_log2, tables=tables, weights=weights,
+                biases=biases)
+
+
+def nat_queries(n: int, D: int, seed: int) -> np.ndarray:
+    """n query rows of D normalised inputs in [0, 1) (float32), uniform."""
+    return np.random.default_rng(seed).random((n, D)).astype(np.float32)

@@ -137,7 +137,7 @@ def test_nat_field_rejects_bad_arguments(nb):
     L = nb.lib()
     h = ctypes.c_void_p()
     t = np.zeros(16, np.float32)
-    w = np.zeros(16, np.uint16)
+    w = np.zeros(16, np.float32)
     b = np.zeros(16, np.float32)
     ok = (ctypes.c_void_p(t.ctypes.data), ctypes.c_void_p(w.ctypes.data), ctypes.c_void_p(b.ctypes.data))
     assert L.nat_field_create(2, 8, 18, None, ok[1], ok[2], None, ctypes.byref(h)) == nb.NAT_BEM_EINVAL
