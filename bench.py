@@ -151,9 +151,17 @@ def _kernel_table(nb):
     return kern
 
 
+def check_indices(ks):
+    """The wavenumbers whose results the bench checks against the oracle: the lowest, the
+    median and the highest of the workload."""
+    order = np.argsort(np.asarray(ks))
+    return sorted({int(order[0]), int(order[len(order) // 2]), int(order[-1])})
+
+
 def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
     """One timed measurement of the interior workload at precision `prec_name`; with `full`
-    also the traced per-kernel step and the end-to-end pass."""
+    also the traced per-kernel step and the end-to-end pass. The surface pressure and field of
+    the wavenumbers of check_indices (first timed step) come back for the oracle check."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -214,6 +222,8 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
                    max_rel_res=max(r[2].rel_residual for res in results for r in res),
                    n_enoconv=sum(1 for s_ in statuses if s_ != nb.NAT_BEM_OK),
                    refinements=max(r[2].refinements for res in results for r in res), prob=prob)
+    summary["checks"] = {i: (results[0][i][0].cpu().numpy(), results[0][i][1].cpu().numpy())
+                         for i in check_indices(prob.ks)}
     if not full:
         return summary
     # One more (untimed) step, one solve at a time, with every kernel bracketed by CUDA events
@@ -654,7 +664,7 @@ def run_galerkin(args):
     nt = len(prob.F)
     t, c = kern["gal_regular"]
     peaks, peak_kind = _peaks()
-    fp32_peak = FP32_LANES_PER_SM * SMS * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fp32_peak = FP32_LANES_PER_SM * sm_count() * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     # every launch of the traced step together covers the nt x nt pairs of each of its solves
     flops = float(len(prob.ks)) * nt * nt * GAL_FLOPS_PER_PAIR
     tf = flops / (t * 1e-3) / 1e12 if c else None
@@ -914,7 +924,7 @@ def roofline(res, peaks, peak_kind):
         pairs = float(n) * n
         flops = pairs * FLOPS_PER_PAIR
         tf = flops / (t / c * 1e-3) / 1e12
-        fp32_peak = FP32_LANES_PER_SM * SMS * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        fp32_peak = FP32_LANES_PER_SM * sm_count() * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         table["assemble_regular"] = {"bound": "alu", "launches": c, "avg_ms": t / c, "achieved": tf,
                                      "peak": fp32_peak, "unit": "TFLOP/s", "frac": tf / fp32_peak,
                                      "algorithmic_flops_per_launch": flops}
@@ -932,7 +942,17 @@ NCU_TRAFFIC_10240 = {"gemv": 838.986e6 + 3.255e6, "gemv_bf16": 419.534e6 + 3.466
 # counted; per pair 6 + 15 operations for the centroid difference and the three dot products.
 FLOPS_PER_PAIR = 7 * 77 + 21
 FP32_LANES_PER_SM = 128
-SMS = 152
+
+
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300 when no GPU is seen)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    return 152
 
 
 def aggregate_ranks(n_solves_local: float, ms_local: float, world: int, device=None):
@@ -1046,9 +1066,11 @@ def main():
     value, my_rate_time = aggregate_ranks(n_solves, res["ms_total"], world, device="cuda" if world > 1 else None)
     # the plain FP32 form on the same workload, same launch configuration, for comparison
     cmp = None
+    cmp_checks = None
     if args.compare and args.prec != "fp32":
         cres = run_gpu(args, rank, world, "fp32", full=False)
         cres.pop("prob")
+        cmp_checks = cres.pop("checks")
         cvalue, cms = aggregate_ranks(n_solves, cres["ms_total"], world, device="cuda" if world > 1 else None)
         cmp = {"value": cvalue, "unit": UNIT, "ms_per_step": cms / args.steps,
                "latency_ms": {"p50": float(np.percentile(cres["lat"], 50)),
@@ -1091,7 +1113,7 @@ def main():
                             "unit": d["unit"], "frac": d["frac"],
                             "traffic": NCU_TRAFFIC_10240.get(dom) if res["n"] == 10240 else None,
                             "measured_on": "one untimed step of the workload, one solve at a time, CUDA events per launch",
-                            "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else 'derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock'})"}
+                            "peak_source": f"{peak_kind} ({'hbm_gbs' if d['bound'] == 'hbm' else f'derived: 128 FP32 lanes x {sm_count()} SMs x 2 x max SM clock'})"}
     if cmp:
         line["plain_fp32"] = cmp
     line["kernels"] = {k: {"ms_total": v[0], "launches": v[1]} for k, v in res["kern"].items()}
@@ -1108,7 +1130,29 @@ def main():
         line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
                                 "sample": f"one solve (k={prob.ks[0]:.4f}) of the 64; stage seconds "
                                           f"{[round(x, 2) for x in info['times']]}"}
-        line["rel_err_vs_oracle"] = {"surface": ep, "field": ef, "k": float(prob.ks[0])}
+        # accuracy: the lowest, median and highest wavenumber, both precisions, against oracle
+        # solves to 1e-10 (untimed)
+        per_k = []
+        for i in sorted(res["checks"]):
+            k = float(prob.ks[i])
+            g = prob.neumann[i][:, 0]
+            pr, fr, _ = oracle.bem_solve(prob.V, prob.F, k, g, prob.points, tol=1e-10, maxit=400,
+                                         nthreads=nth)
+            row = {"k": k}
+            main_name = "plain_fp32" if args.prec == "fp32" else f"mixed_{args.prec}"
+            for name, chk in ((main_name, res["checks"]), ("plain_fp32", cmp_checks)):
+                if chk is None:
+                    continue
+                pg, fg = chk[i]
+                row[name] = {"surface": float(np.linalg.norm(pg - pr) / np.linalg.norm(pr)),
+                             "field": float(np.linalg.norm(fg - fr) / np.linalg.norm(fr))}
+            per_k.append(row)
+        errs = [v for row in per_k for nm, e in row.items() if nm != "k" for v in e.values()]
+        line["rel_err_vs_oracle"] = {"max": max(errs), "meets_1e-4": bool(max(errs) <= 1e-4),
+                                     "checked": "lowest, median and highest wavenumber; mixed and plain FP32; "
+                                                "surface and field; oracle GMRES to 1e-10",
+                                     "per_k": per_k,
+                                     "first_k": {"surface": ep, "field": ef, "k": float(prob.ks[0])}}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -63,22 +63,33 @@ typedef enum {
   NAT_BEM_PREC_MIXED_BF16 = 2  /* inner GMRES on a BF16 operator copy, FP64-refined residual   */
 } nat_bem_precision;
 
+/*
+ * Solver and quadrature options (paper Sec. 6.1 gives the solver settings: tolerance 1e-6, at
+ * most 200 iterations; Sec. 4.1 says only "Gaussian quadrature", so the rules are this
+ * library's choice, stated here).
+ */
 typedef struct {
   int32_t adj_subdiv_levels; /* vertex-sharing pairs: 7-point rule on 4^levels sub-triangles (2) */
   int32_t self_theta_pts;    /* self pair: Gauss-Legendre points per edge in the angle (16)      */
   double tol;                /* relative residual ||b - L p|| / ||b|| to stop at (1e-6)         */
-  int32_t max_iter;          /* GMRES iterations (plain), total inner iterations (mixed) (200) */
+  int32_t max_iter;          /* GMRES iterations (plain), total inner iterations (mixed) (200); */
+                             /* at most 255 unrestarted, 100000 with restart > 0                */
   nat_bem_precision prec;    /* arithmetic of the solve (NAT_BEM_PREC_FP32)                      */
   int32_t inner_max_iter;    /* mixed: iterations per inner solve (60)                            */
   double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-2)              */
   int32_t max_refinements;   /* mixed: outer refinement sweeps (10)                               */
+  int32_t restart;           /* GMRES(m): Krylov vectors kept, m in 1..255; 0 = unrestarted (0).  */
+                             /* The basis takes 16 nt nrhs (m + 1) bytes instead of             */
+                             /* 16 nt nrhs (max_iter + 1): the lever for serving memory          */
+  int32_t quad_regular;      /* points of the rule on pairs sharing no vertex: 7 (Radon's degree- */
+                             /* 5 rule) is the only value (7)                                      */
 } nat_bem_opts;
 
 typedef struct nat_bem_op nat_bem_op; /* opaque */
 
 typedef struct {
   int32_t iterations;   /* GMRES iterations (mixed: summed over inner solves), max over RHS   */
-  int32_t refinements;  /* mixed: outer sweeps done; plain: 0                                   */
+  int32_t refinements;  /* mixed: outer sweeps done; restarted: GMRES cycles; else 0            */
   double rel_residual;  /* largest ||b - L p|| / ||b|| over the RHS (FP64 accumulation)        */
 } nat_bem_solve_info;
 
@@ -199,7 +210,10 @@ NAT_BEM_API nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cu
  *   neumann: nt x nrhs complex64, column-major.  p_out: same layout, receives p.
  *   info: may be NULL.  Blocks until the solve is done.
  * Convergence: plain FP32, GMRES's residual estimate reaches tol (the true residual with the
- * FP32 operator, reported in info->rel_residual, can sit above tol at high k). Mixed: the true
+ * FP32 operator, reported in info->rel_residual, can sit above tol at high k). Restarted
+ * (opts.restart = m > 0): cycles of at most m iterations, each on the true residual with the
+ * FP32 operator, until a cycle's estimate or the true residual reaches tol relative to
+ * ||R g||, within max_iter iterations in all. Mixed: the true
  * residual reaches tol after a refinement sweep; when a sweep shrinks a residual by less than
  * 10x, or the sweeps or max_iter inner iterations are spent, one final solve of the correction
  * equation on the FP32 operator (its own max_iter) finishes by the plain criterion.
@@ -211,7 +225,10 @@ NAT_BEM_API nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, i
                              nat_bem_solve_info* info, void* cuda_stream);
 
 /*
- * Field pressure at m points: field[q, s] = sum_j int_j [p_js dG/dn_y - g_js G](x_q, y) dS_y
+ * Field pressure at m points (paper Sec. 3.4: the pressure anywhere follows from the Neumann and
+ * the solved Dirichlet data; this is the exterior representation formula with the Green's
+ * function of Sec. 4.2, whose limit on the surface is the first line of Sec. 4, Eq. 6):
+ *   field[q, s] = sum_j int_j [p_js dG/dn_y - g_js G](x_q, y) dS_y
  * with the 7-point rule on every element (points should lie off the surface by at least an
  * element size). pts: m x 3 float64.  p, neumann: nt x nrhs complex64 column-major.
  * field_out: m x nrhs complex64 column-major. m = 0 is allowed and does nothing.
@@ -232,7 +249,8 @@ NAT_BEM_API nat_bem_status nat_bem_eval(const nat_bem_op* op, const double* pts,
  *   message beyond that; split larger point sets over several calls).
  *   Partial sums go to a fixed 4 MiB array compiled into the library, which every GPU that
  *   loads the library holds until the process exits. The first call on each device looks up
- *   that array's device address (make that first call before any stream capture). All calls
+ *   that array's device address (make that first call before any stream capture) and keeps
+ *   it, so the library must not be used across a cudaDeviceReset. All calls
  *   share the array and it keeps the last call's partial sums, which the next call overwrites
  *   before reading (nothing needs to start at zero); calls that overlap on the GPU (different
  *   streams, or different host threads) race on it and must be serialised by the caller.

@@ -53,7 +53,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("adj_subdiv_levels", ctypes.c_int32), ("self_theta_pts", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("inner_max_iter", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("max_refinements", ctypes.c_int32)]
+                ("max_refinements", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("quad_regular", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -387,10 +388,25 @@ def nat_bem_sample_field(op, u, center, r_lo, r_hi, p, neumann, stream=None):
 
 def nat_bem_eval_noalloc(op, points, p, neumann, out, stream=None) -> int:
     """nat_bem_eval without device allocation: all arrays must be CUDA torch tensors and
-    `out` is written in place ((nrhs, m) or (m,) complex64). Returns the status code."""
+    `out` is written in place ((nrhs, m) or (m,) complex64). Returns the status code.
+    The C call cannot see array sizes, so the shapes and devices are checked here first
+    (ValueError), before anything is launched."""
+    for name, t in (("points", points), ("p", p), ("neumann", neumann), ("out", out)):
+        if not _is_torch(t) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA torch tensor")
+    if len({t.device for t in (points, p, neumann, out)}) != 1:
+        raise ValueError("points, p, neumann and out must be on one CUDA device")
     m = int(points.shape[0])
     n = int(lib().nat_bem_op_size(op))
+    if points.dim() != 2 or int(points.shape[1]) != 3:
+        raise ValueError("points must be (m, 3)")
     nrhs = _nrhs_of(p, n)
+    if p.dim() == 2 and int(p.shape[1]) != n or p.dim() == 1 and int(p.shape[0]) != n:
+        raise ValueError(f"p must be ({n},) or (nrhs, {n})")
+    if tuple(neumann.shape) != tuple(p.shape):
+        raise ValueError("neumann must have the shape of p")
+    if int(out.numel()) != nrhs * m:
+        raise ValueError(f"out must hold nrhs * m = {nrhs * m} values, has {int(out.numel())}")
     pp, _ = _ptr(points, np.float64)
     pd, _ = _ptr(p, np.complex64)
     pg, _ = _ptr(neumann, np.complex64)

@@ -106,8 +106,16 @@ static nat_bem_status check_opts(const nat_bem_opts& o) {
     set_error("opts.tol must be positive and finite");
     return NAT_BEM_EINVAL;
   }
-  if (o.max_iter < 1 || o.max_iter > 255) {
-    set_error("opts.max_iter must be in [1, 255]");
+  if (o.restart < 0 || o.restart > 255) {
+    set_error("opts.restart must be in [0, 255] (0 = unrestarted GMRES)");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.max_iter < 1 || o.max_iter > (o.restart > 0 ? 100000 : 255)) {
+    set_error("opts.max_iter must be in [1, 255] (unrestarted) or [1, 100000] (restart > 0)");
+    return NAT_BEM_EINVAL;
+  }
+  if (o.quad_regular != 7) {
+    set_error("opts.quad_regular must be 7 (the 7-point degree-5 rule is the only regular rule)");
     return NAT_BEM_EINVAL;
   }
   if (o.prec != NAT_BEM_PREC_FP32 && o.prec != NAT_BEM_PREC_MIXED_TF32 &&
@@ -146,6 +154,8 @@ void nat_bem_opts_default(nat_bem_opts* o) {
   o->inner_max_iter = 60;
   o->inner_tol = 1e-2;
   o->max_refinements = 10;
+  o->restart = 0;
+  o->quad_regular = 7;
 }
 
 const char* nat_bem_last_error(void) { return g_last_error.c_str(); }

@@ -425,7 +425,9 @@ void* g_scratch_ptr[64] = {};
 }  // namespace
 
 // Device address of g_eval_scratch on the current device, looked up once per device (host
-// code cannot use the symbol itself: on the host it names a stand-in, not device memory).
+// code cannot use the symbol itself: on the host it names a stand-in, not device memory). The
+// address is kept for the life of the process, so the library must not be used across a
+// cudaDeviceReset (which would also invalidate every op).
 static nat_bem_status scratch_address(double2** out) {
   int dev = 0;
   NB_TRY_CUDA(cudaGetDevice(&dev));
@@ -468,10 +470,10 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
   for (int r0 = 0; r0 < nrhs; r0 += kNoAllocRhsPass) {
     const int nr = min(kNoAllocRhsPass, nrhs - r0);
     dim3 grid(pblocks, splits);
-    eval_launch(eval_source(op), (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part);
+    NB_LAUNCH("eval", s, eval_launch(eval_source(op), (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
-    k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out);
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
   }
   return NAT_BEM_OK;

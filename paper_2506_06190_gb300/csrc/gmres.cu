@@ -6,13 +6,17 @@
 // one re-orthogonalisation pass (CGS2), the Hessenberg matrix, the complex Givens rotations
 // and the small least-squares solve are FP64.
 //
-// One iteration (all right-hand sides in lockstep, each with its own Krylov space) is five
-// kernels: normalise v_j = w / h_{j,j-1}; w = L v_j; h = V^H w; w -= V h and h' = V^H w;
-// w -= V h' with ||w||, Givens update and convergence test. The iteration index, the per-RHS
+// One iteration (all right-hand sides in lockstep, each with its own Krylov space) is two
+// launches: the matvec w = L v_j, then one cooperative kernel (k_arnoldi, or k_arnoldi_units
+// for many right-hand sides) that does the Gram-Schmidt passes, ||w||, v_{j+1} and the Givens
+// update with grid barriers. Where a cooperative launch cannot hold every block, the same step
+// runs as five kernels (dots, update, dots, update, finish). The iteration index, the per-RHS
 // convergence flags and the "all done" flag live in device memory, so the launch sequence is
-// the same every iteration and finished iterations cost only empty launches. Reductions are
-// deterministic: per-chunk partial sums, summed in a fixed order by the last block to finish
-// (counted with an atomic ticket).
+// the same every iteration and finished iterations cost only empty launches; chunks of
+// iterations are captured as CUDA graphs. Reductions are deterministic: per-chunk partial
+// sums, summed in a fixed order by the last block to finish (counted with an atomic ticket).
+// Restarted GMRES(m) and mixed-precision refinement run sweeps of this loop on the current
+// residual, accumulating the solution in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +48,7 @@ struct Workspace {
   double *cs = nullptr, *partn = nullptr, *bnorm = nullptr, *res = nullptr, *hnorm = nullptr;
   double* res_true = nullptr;
   double2 *b0 = nullptr, *xacc = nullptr;  // refinement: R g and the accumulated solution
+  double* b0norm = nullptr;                 // refinement / restart: ||R g|| per RHS
   float2 *xf = nullptr, *gin = nullptr, *pout = nullptr;
   int *done = nullptr, *iters = nullptr, *scal = nullptr;  // scal: j, all_done, rhs ticket
   int* outer_done = nullptr;                               // refinement: converged RHS
@@ -52,7 +57,8 @@ struct Workspace {
   double2 *pblk = nullptr, *hred = nullptr;                // fused kernel: block partials, totals
   int arn_smem = 0;                                        // fused kernel: dynamic shared bytes
   double2* pbu = nullptr;                                  // multi-RHS fused kernel: unit partials
-  // captured iteration chunks: key (engine, first iteration, count, cap, tol, refinement mode)
+  // captured iteration chunks: key (engine, first iteration, count, cap, tol, mode bits:
+  // 1 skip flags, 2 accumulate, 4 tolerance relative to ||R g||)
   std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
   void* tc_scratch = nullptr;                              // packed B + split-K partials
@@ -66,6 +72,8 @@ struct GArgs {
   int n, ld, nrhs, m, nchunk;
   int maxit;           // iteration cap of this GMRES run (<= m)
   const int* skip;     // RHS to leave alone in this run (refinement), or null
+  const double* bscale;  // stop at res <= tol * bscale[s] (||R g||: restart cycles and the
+                         // FP32 finish of refinement), or null: res <= tol * ||b|| of this run
   const float2* L;
   double2 *b, *V, *w, *x, *H, *hcol, *htmp, *sn, *gv, *y, *part;
   double *cs, *partn, *bnorm, *res, *hnorm, *res_true;
@@ -627,7 +635,8 @@ __global__ void __launch_bounds__(256) k_update(GArgs a, int pass) {
     const double res_ = sqrt(cabs2(gv_[(j) + 1]));                                            \
     (a).res[s] = res_;                                                                        \
     (a).iters[s] = (j) + 1;                                                                   \
-    if (res_ <= (a).tol * (a).bnorm[s] || (hn) == 0.0) (a).done[s] = 1;                       \
+    if (res_ <= (a).tol * ((a).bscale ? (a).bscale[s] : (a).bnorm[s]) || (hn) == 0.0)      \
+      (a).done[s] = 1;                                                                        \
   } while (0)
 
 // ||w|| from the block partials and v = w / ||w|| into V[jt] and the FP32 copy xf.
@@ -835,7 +844,7 @@ __device__ void givens_warp(const GArgs& a, int s, int j, double hn, double2* hc
     a.res[s] = res;
     a.hnorm[s] = hn;
     a.iters[s] = j + 1;
-    if (res <= a.tol * a.bnorm[s] || hn == 0.0) a.done[s] = 1;
+    if (res <= a.tol * (a.bscale ? a.bscale[s] : a.bnorm[s]) || hn == 0.0) a.done[s] = 1;
   }
 }
 
@@ -1394,12 +1403,18 @@ __global__ void k_pad_copy(const float2* __restrict__ src, int n, int ld, int nr
 }
 
 // ---------------------------------------------------------------------------- host side
+// Krylov dimension: the restart length of GMRES(m), or the iteration cap when unrestarted.
+static int krylov_dim(const nat_bem_opts& o) {
+  const int cap = std::max(1, o.max_iter);
+  return o.restart > 0 ? std::min(o.restart, cap) : cap;
+}
+
 int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
-  const int64_t m = std::max(1, o.max_iter);
+  const int64_t m = krylov_dim(o);
   const int64_t ld = round_up(n, 32);
   const int64_t nchunk = (n + kUpdRows - 1) / kUpdRows;
   int64_t b = 0;
-  b += 16 * n * nrhs * 5;                 // b, w, x, b0, xacc
+  b += 16 * n * nrhs * 5 + 8 * nrhs;      // b, w, x, b0, xacc, ||b0||
   b += 16 * n * nrhs * (m + 1);           // V
   b += 8 * ld * nrhs * 3;                 // xf, gin, pout
   b += 16 * nrhs * (m + 1) * (m + 4);     // H, hcol, htmp, gv, sn, y
@@ -1415,7 +1430,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   void* ptrs[] = {ws->b, ws->V, ws->w, ws->x, ws->H, ws->hcol, ws->htmp, ws->sn, ws->gv, ws->y,
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
-                  ws->b0, ws->xacc, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar,
+                  ws->b0, ws->xacc, ws->b0norm, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar,
                   ws->pblk, ws->hred, ws->pbu};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
@@ -1425,7 +1440,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
 }
 
 static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s) {
-  const int m = std::max(1, op->opts.max_iter);
+  const int m = krylov_dim(op->opts);
   Workspace* ws = op->ws;
   if (ws && ws->cap >= nrhs && ws->m == m) {
     ws->nrhs = nrhs;  // reuse: every array is sized for `cap` right-hand sides
@@ -1467,6 +1482,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->cnt, nr * kCounters, s));
   NB_TRY(dev_alloc_n(&ws->b0, n * nr, s));
   NB_TRY(dev_alloc_n(&ws->xacc, n * nr, s));
+  NB_TRY(dev_alloc_n(&ws->b0norm, nr, s));
   NB_TRY(dev_alloc_n(&ws->outer_done, nr, s));
   NB_TRY(dev_alloc_n(&ws->tc_err, 1, s));
   NB_TRY(dev_alloc_n(&ws->gbar, 2, s));
@@ -1559,6 +1575,7 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
   a.tol = op->opts.tol;
   a.maxit = ws->m;
   a.skip = nullptr;
+  a.bscale = nullptr;
   return a;
 }
 
@@ -1892,7 +1909,8 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
     const int c = std::min(chunk, a.maxit - it);
     bool done_direct = true;
     if (use_graphs) {
-      const auto key = std::make_tuple(engine, it, c, a.maxit, a.tol, (a.skip ? 1 : 0) + (accumulate ? 2 : 0));
+      const auto key = std::make_tuple(engine, it, c, a.maxit, a.tol,
+                                       (a.skip ? 1 : 0) + (accumulate ? 2 : 0) + (a.bscale ? 4 : 0));
       auto f = ws->graphs.find(key);
       if (f == ws->graphs.end()) {
         const int64_t l0 = launch_count();
@@ -2037,8 +2055,11 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = nrhs == 1 ? kEngineGemvBf16 : kEngineBf16;
   if (o.prec == NAT_BEM_PREC_MIXED_TF32 && nrhs > 1) inner = kEngineTf32;
   const bool mixed = inner != accurate;
+  // GMRES(m): the Krylov basis holds m = restart vectors and the solve runs cycles of at most
+  // m iterations, each on the current residual
+  const bool restarted = ws->m < std::max(1, o.max_iter);
   if (inner == kEngineGemvBf16) gemv_bf16_tune(op->Lb, n, (int)op->geo.ld, ws->gin, ws->w, s);
-  if (!mixed) {
+  if (!mixed && !restarted) {
     GArgs a = make_args(op, ws, op->L);
     a.maxit = o.max_iter;
     NB_TRY(gmres_run(op, ws, a, accurate, 0, d_p, s));
@@ -2055,29 +2076,34 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       converged = converged && done[q];
     }
   } else {
-    // Mixed precision iterative refinement: inner GMRES on the BF16 copy of L to inner_tol,
-    // x += d in FP64, residual b0 - L x with the FP32 operator and FP64 sums.
+    // Refinement form, shared by mixed precision and restarted GMRES: x accumulates in FP64
+    // (xacc), b holds the current residual b0 - L x with the FP32 operator and FP64 sums, and
+    // each sweep solves the correction equation L d = b with GMRES from d = 0, x += d.
     NB_TRY_CUDA(cudaMemcpyAsync(ws->b0, ws->b, (size_t)n * nrhs * sizeof(double2), cudaMemcpyDeviceToDevice, s));
     NB_TRY_CUDA(cudaMemsetAsync(ws->xacc, 0, (size_t)n * nrhs * sizeof(double2), s));
     NB_TRY_CUDA(cudaMemsetAsync(ws->outer_done, 0, nrhs * sizeof(int), s));
     GArgs a = make_args(op, ws, op->L);
     a.x = ws->xacc;
     a.skip = ws->outer_done;
-    a.tol = o.inner_tol;
     int budget = o.max_iter;
     converged = false;
-    bool fallback = false;
-    std::vector<int> od(nrhs);
+    bool first = true;
+    std::vector<int> od(nrhs), inner_done(nrhs);
     std::vector<double> prev(nrhs, 1.0);
-    // one refinement sweep: inner GMRES on the correction equation, x += d, true residual
-    auto sweep_once = [&]() -> nat_bem_status {
-      a.maxit = fallback ? budget : std::min(o.inner_max_iter, budget);
-      NB_TRY(gmres_run(op, ws, a, inner, 1, d_p, s));
+    // one sweep with the given engine: GMRES on the correction equation (at most a.maxit
+    // iterations), x += d, the true residual and the outer convergence flags
+    auto sweep_once = [&](int eng) -> nat_bem_status {
+      NB_TRY(gmres_run(op, ws, a, eng, 1, d_p, s));
+      if (first) {  // the first run started from b = b0: its ||b|| is ||R g||
+        NB_TRY_CUDA(cudaMemcpyAsync(ws->b0norm, ws->bnorm, nrhs * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        first = false;
+      }
       NB_TRY(matvec(op, ws, 0, accurate, ws->w, nullptr, nullptr, "gemv_resid", s));
       NB_LAUNCH("ir_residual", s, k_ir_residual<<<vec_grid, kChunk, 0, s>>>(a, ws->b0, ws->outer_done, o.tol));
       NB_CHECK_LAUNCH();
       NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
       NB_TRY_CUDA(cudaMemcpyAsync(od.data(), ws->outer_done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
+      NB_TRY_CUDA(cudaMemcpyAsync(inner_done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
       NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
       NB_TRY_CUDA(cudaStreamSynchronize(s));
       int used = 0;
@@ -2091,37 +2117,44 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       for (int q = 0; q < nrhs; ++q) converged = converged && od[q];
       return NAT_BEM_OK;
     };
-    for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
-      NB_TRY(sweep_once());
-      if (converged || fallback) break;
-      // A sweep that shrank some residual by less than 10x (the low-precision operator's error
-      // is comparable to the inner tolerance: high k, ill-conditioned L) or that used up the
-      // budget: the rest is one solve of the correction equation with the FP32 operator, to
-      // the full tolerance relative to b0, with a fresh iteration budget. It runs even when
-      // the refinement count is spent.
-      double worst = 0.0, maxrt = 0.0;
-      for (int q = 0; q < nrhs; ++q)
-        if (!od[q]) {
-          worst = std::max(worst, rt[q] / prev[q]);
-          maxrt = std::max(maxrt, rt[q]);
+    bool finish = !mixed;
+    if (mixed) {
+      // Mixed precision iterative refinement: inner GMRES on the BF16 copy of L (or the
+      // tensor-core products) to inner_tol relative to the current residual.
+      a.tol = o.inner_tol;
+      for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
+        a.maxit = std::min(std::min(o.inner_max_iter, budget), ws->m);
+        NB_TRY(sweep_once(inner));
+        if (converged) break;
+        // A sweep that shrank some residual by less than 10x (the low-precision operator's
+        // error is comparable to the inner tolerance: high k, ill-conditioned L) or that used
+        // up the budget: the rest is solved with the FP32 operator below, with a fresh
+        // iteration budget. It runs even when the refinement count is spent.
+        double worst = 0.0;
+        for (int q = 0; q < nrhs; ++q)
+          if (!od[q]) worst = std::max(worst, rt[q] / prev[q]);
+        if (worst > 0.1 || budget <= 0 || sweep + 1 >= o.max_refinements) {
+          finish = true;
+          break;
         }
-      if (worst > 0.1 || budget <= 0 || sweep + 1 >= o.max_refinements) {
-        fallback = true;
-        inner = accurate;
-        a.tol = std::max(0.5 * o.tol / std::max(maxrt, o.tol), 1e-14);
-        budget = o.max_iter;
-        NB_TRY(sweep_once());
-        // The FP32 solve meets the tolerance by GMRES's own residual, the criterion of the
-        // plain FP32 path; the true residual (info.rel_residual) then sits at the FP32
-        // operator's floor, which at high k can lie above the tolerance.
-        std::vector<int> inner_done(nrhs);
-        NB_TRY_CUDA(cudaMemcpyAsync(inner_done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
-        NB_TRY_CUDA(cudaStreamSynchronize(s));
+        prev = rt;
+      }
+    }
+    if (finish && !converged) {
+      // GMRES with the FP32 operator on the correction equation, in cycles of at most m
+      // iterations (one cycle when unrestarted), until GMRES's residual estimate meets the
+      // tolerance relative to ||R g|| (the plain path's criterion; after mixed sweeps, half
+      // of it) or the true residual does.
+      if (mixed) budget = o.max_iter;
+      a.tol = mixed ? 0.5 * o.tol : o.tol;
+      while (budget > 0) {
+        a.bscale = first ? nullptr : ws->b0norm;
+        a.maxit = std::min(budget, ws->m);
+        NB_TRY(sweep_once(accurate));
         converged = true;
         for (int q = 0; q < nrhs; ++q) converged = converged && (od[q] || inner_done[q]);
-        break;
+        if (converged) break;
       }
-      prev = rt;
     }
   }
   int tc_err = 0;

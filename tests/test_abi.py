@@ -43,6 +43,7 @@ def test_opts_defaults(nb):
     assert o.adj_subdiv_levels == 2 and o.self_theta_pts == 16
     assert o.tol == 1e-6 and o.max_iter == 200 and o.prec == nb.PREC_FP32
     assert o.inner_max_iter == 60 and o.inner_tol == 1e-2 and o.max_refinements == 10
+    assert o.restart == 0 and o.quad_regular == 7
 
 
 def test_required_bytes(nb):
@@ -53,6 +54,19 @@ def test_required_bytes(nb):
     assert b < 16 * n * ld * 1.2
     assert nb.nat_bem_required_bytes(n, 64) > b
     assert nb.nat_bem_required_bytes(0, 1) == 0
+
+
+def test_required_bytes_restart(nb):
+    """GMRES(m) keeps m + 1 Krylov vectors instead of max_iter + 1: admission sees the saving.
+    A 40k-triangle request with 32 right-hand sides at max_iter = 200 needs 16 n 32 (m + 1)
+    bytes of basis: about 4.1 GB unrestarted, about 0.63 GB at m = 30."""
+    n, nrhs = 40000, 32
+    full = nb.nat_bem_required_bytes(n, nrhs)
+    r30 = nb.nat_bem_required_bytes(n, nrhs, nb.nat_bem_opts_default(restart=30))
+    assert full - r30 >= 16 * n * nrhs * (200 - 30)
+    assert nb.nat_bem_required_bytes(n, nrhs, nb.nat_bem_opts_default(restart=200)) == full
+    # restart beyond max_iter is the unrestarted solve
+    assert nb.nat_bem_required_bytes(n, nrhs, nb.nat_bem_opts_default(restart=255)) == full
 
 
 def _assemble_status(nb, V, F, k=2.0, opts=None):
@@ -66,7 +80,8 @@ def _assemble_status(nb, V, F, k=2.0, opts=None):
 
 
 @pytest.mark.parametrize("case", ["inward", "open", "flipped_one", "index", "nan", "degenerate",
-                                  "k_zero", "k_nan", "empty", "bad_levels", "bad_maxit"])
+                                  "k_zero", "k_nan", "empty", "bad_levels", "bad_maxit",
+                                  "maxit_unrestarted", "bad_restart", "bad_quad"])
 def test_assemble_rejects_bad_input(nb, case):
     V, F = S.icosphere(1)
     k, opts = 2.0, None
@@ -92,6 +107,12 @@ def test_assemble_rejects_bad_input(nb, case):
         opts = nb.nat_bem_opts_default(adj_subdiv_levels=7)
     elif case == "bad_maxit":
         opts = nb.nat_bem_opts_default(max_iter=0)
+    elif case == "maxit_unrestarted":  # more than 255 iterations need restarts
+        opts = nb.nat_bem_opts_default(max_iter=300)
+    elif case == "bad_restart":
+        opts = nb.nat_bem_opts_default(restart=256)
+    elif case == "bad_quad":
+        opts = nb.nat_bem_opts_default(quad_regular=6)
     st, op = _assemble_status(nb, V, F, k, opts)
     assert st == nb.NAT_BEM_EINVAL and not op.value
     assert len(nb.nat_bem_last_error()) > 0

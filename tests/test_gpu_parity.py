@@ -159,30 +159,79 @@ def test_empty_field_and_errors(nb):
             nb.nat_bem_op_rows(op.handle, 0, op.n - 1, 5)
 
 
-@pytest.mark.parametrize("ka", [0.5, 20.0])
-def test_full_size_interior_source(nb, oracle_lib, ka):
-    """The 10240-triangle interior-source mesh as the bench runs it: sampled operator rows
-    against the oracle, the GPU solution against the oracle's full solve, the field at all
-    1024 points, and the discretisation error against the exact monopole field."""
+@pytest.fixture(scope="module")
+def full_size_ref(oracle_lib):
+    """Oracle results on the 10240-triangle interior-source mesh (the bench's), per ka: sampled
+    operator rows, the FP64 solution (GMRES to 1e-10) and the field at the 1024 points."""
     prob = S.interior_source(n_k=1)
-    V, F = prob.V, prob.F
-    k = ka
-    g = S.monopole_neumann(V, F, k)
-    rows = np.unique(np.concatenate([np.arange(0, len(F), 331), [len(F) - 1]]))
-    Lr, Rr = oracle_lib.assemble_rows(V, F, k, rows)
-    with nb.Operator.assemble(V, F, k) as op:
-        Lg = np.concatenate([op.rows(0, int(r), 1) for r in rows]).astype(np.complex128)
-        Rg = np.concatenate([op.rows(1, int(r), 1) for r in rows]).astype(np.complex128)
+    cache = {}
+
+    def get(ka):
+        if ka not in cache:
+            V, F = prob.V, prob.F
+            g = S.monopole_neumann(V, F, ka)
+            rows = np.unique(np.concatenate([np.arange(0, len(F), 331), [len(F) - 1]]))
+            Lr, Rr = oracle_lib.assemble_rows(V, F, ka, rows)
+            p_ref, _ = oracle_lib.solve(V, F, ka, g, tol=1e-10)
+            f_ref = oracle_lib.evaluate(V, F, ka, prob.points, p_ref, g)
+            cache[ka] = dict(g=g, rows=rows, Lr=Lr, Rr=Rr, p=p_ref, f=f_ref)
+        return cache[ka]
+
+    return prob, get
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("ka", [0.5, 5.0, 20.0])
+def test_full_size_interior_source(nb, oracle_lib, full_size_ref, ka, prec):
+    """The 10240-triangle interior-source mesh as the bench runs it, in plain FP32 and in the
+    mixed BF16 form the bench's headline uses, at the low, middle and high end of its ka range:
+    sampled operator rows against the oracle, the GPU solution against the oracle's full solve,
+    the field at all 1024 points, and the discretisation error against the exact monopole
+    field."""
+    prob, get = full_size_ref
+    ref = get(ka)
+    V, F, g = prob.V, prob.F, ref["g"]
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16)
+    with nb.Operator.assemble(V, F, ka, opts) as op:
+        if prec == "fp32":
+            Lg = np.concatenate([op.rows(0, int(r), 1) for r in ref["rows"]]).astype(np.complex128)
+            Rg = np.concatenate([op.rows(1, int(r), 1) for r in ref["rows"]]).astype(np.complex128)
+            assert np.max(_rowwise(Lg, ref["Lr"])) < OP_TOL and np.max(_rowwise(Rg, ref["Rr"])) < OP_TOL
         p, info, st = op.solve(g)
-        assert st == nb.NAT_BEM_OK
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        if prec == "bf16":
+            assert info.refinements >= 1
         fld = op.evaluate(prob.points, p, g)
-    assert np.max(_rowwise(Lg, Lr)) < OP_TOL and np.max(_rowwise(Rg, Rr)) < OP_TOL
-    p_ref, info_ref = oracle_lib.solve(V, F, k, g, tol=1e-10)
-    assert _rel(p, p_ref) < SOL_TOL
-    f_ref = oracle_lib.evaluate(V, F, k, prob.points, p_ref, g)
-    assert _rel(fld, f_ref) < SOL_TOL
+    assert _rel(p, ref["p"]) < SOL_TOL
+    assert _rel(fld, ref["f"]) < SOL_TOL
     c, _, _ = oracle_lib.geometry(V, F)
-    assert _rel(p, S.monopole_field(c, k)) < 0.1
+    assert _rel(p, S.monopole_field(c, ka)) < 0.1
+
+
+def test_modal_multi_rhs_full_size_bf16(nb, oracle_lib):
+    """The multi-RHS modal workload's shape: a 20480-triangle perturbed icosphere, 64 smooth
+    right-hand sides solved in one block with BF16 tensor-core inner products and FP32
+    refinement. Sampled operator rows against the oracle, and two right-hand sides against the
+    oracle's FP64 solve (GMRES to 1e-10 on the full operator), surface and field."""
+    prob = S.modal_multirhs(nrhs=64)
+    V, F, k = prob.V, prob.F, float(np.max(prob.ks))  # the workload's highest wavenumber
+    G = prob.neumann[0]
+    pts = prob.points[::8]
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16)
+    rows = np.unique(np.concatenate([np.arange(0, len(F), 997), [len(F) - 1]]))
+    with nb.Operator.assemble(V, F, k, opts) as op:
+        Lg = np.concatenate([op.rows(0, int(r), 1) for r in rows]).astype(np.complex128)
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        assert info.refinements >= 1
+        fld = op.evaluate(pts, P, G)
+    L, R = oracle_lib.assemble(V, F, k)
+    assert np.max(_rowwise(Lg, L[rows])) < OP_TOL
+    for s in (0, 63):
+        p_ref, _, _, ok = oracle_lib.gmres(L, R @ G[:, s], tol=1e-10, maxit=400)
+        assert ok
+        assert _rel(P[:, s], p_ref) < SOL_TOL
+        assert _rel(fld[:, s], oracle_lib.evaluate(V, F, k, pts, p_ref, G[:, s])) < SOL_TOL
 
 
 @pytest.mark.parametrize("ka", [1.0, 12.0])
@@ -227,6 +276,50 @@ def test_mixed_bf16_high_wavenumber_converges(nb, oracle_lib, nrhs):
         assert _rel(P[:, s], np.linalg.solve(L, R @ G[:, s])) < SOL_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_restarted_gmres_matches_oracle(nb, oracle_lib, prec):
+    """GMRES(m) with m = 30 Krylov vectors (the unrestarted solve needs more at ka = 9): several
+    cycles, each on the true residual, and the result within 1e-4 of the oracle on the surface
+    and in the field, for two right-hand sides, plain and mixed."""
+    Vs, F = S.ring_sphere(2306)
+    V = S.perturbed_ellipsoid(Vs, 15)
+    ka = 9.0
+    G = np.stack([S.monopole_neumann(V, F, ka), S.sh_neumann(V, F, 1, 16)[:, 0]], axis=1)
+    pts = S.fibonacci_points(64, 4.0)
+    L, R = oracle_lib.assemble(V, F, ka)
+    pc = nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16
+    with nb.Operator.assemble(V, F, ka, nb.nat_bem_opts_default(prec=pc)) as op:
+        _, info_full, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK
+    opts = nb.nat_bem_opts_default(prec=pc, restart=30, max_iter=3000)
+    with nb.Operator.assemble(V, F, ka, opts) as op:
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
+        assert info.refinements >= 2 and info.iterations > 30
+        fld = op.evaluate(pts, P, G)
+    if prec == "fp32":
+        assert info_full.iterations > 30  # so restarts really happened
+    for s in range(2):
+        p_ref = np.linalg.solve(L, R @ G[:, s])
+        assert _rel(P[:, s], p_ref) < SOL_TOL
+        assert _rel(fld[:, s], oracle_lib.evaluate(V, F, ka, pts, p_ref, G[:, s])) < SOL_TOL
+
+
+def test_restart_at_or_beyond_max_iter_is_the_unrestarted_solve(nb):
+    """restart >= max_iter keeps every Krylov vector: the same path and the same bits as the
+    default (restart = 0)."""
+    Vs, F = S.ring_sphere(1000)
+    V = S.perturbed_ellipsoid(Vs, 17)
+    g = S.monopole_neumann(V, F, 6.0)
+    out = []
+    for r in (0, 200, 255):
+        with nb.Operator.assemble(V, F, 6.0, nb.nat_bem_opts_default(restart=r)) as op:
+            p, info, st = op.solve(g)
+            assert st == nb.NAT_BEM_OK and info.refinements == 0
+            out.append(p)
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
 def test_reassemble_matches_fresh_assembly(nb):
     """A new wavenumber on an existing op gives the same operator bits as a fresh assembly."""
     Vs, F = S.ring_sphere(700)
@@ -246,9 +339,12 @@ def test_reassemble_matches_fresh_assembly(nb):
         nb.nat_bem_reassemble(None, 1.0)
 
 
-def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib):
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib, prec):
     """Batched solves over meshes of uneven size (two jobs share a mesh) give the same bits as
-    one solve at a time, with any number of workers; one job is checked against the oracle."""
+    one solve at a time, with any number of workers, in plain FP32 and in mixed precision;
+    every job is checked against the oracle, surface and field."""
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16)
     import torch
     jobs = []
     for i, n_tri in enumerate([520, 1300, 760, 2010]):
@@ -260,18 +356,20 @@ def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib):
     jobs.append(dict(jobs[1], k=7.7, neumann=S.sh_neumann(jobs[1]["V"], jobs[1]["F"], 1, 77)[:, 0]))
     singles = []
     for jd in jobs:
-        with nb.Operator.assemble(jd["V"], jd["F"], jd["k"]) as op:
+        with nb.Operator.assemble(jd["V"], jd["F"], jd["k"], opts) as op:
             p, info, st = op.solve(jd["neumann"])
             singles.append((p, op.evaluate(jd["points"], p, jd["neumann"])))
     for conc in (1, 3):
-        st, res = nb.nat_bem_run_batch(jobs, concurrency=conc)
+        st, res = nb.nat_bem_run_batch(jobs, opts, concurrency=conc)
         assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
         for (p, f, info, s_, ms), (p1, f1) in zip(res, singles):
             assert s_ == nb.NAT_BEM_OK and info.iterations > 0 and ms > 0
             assert np.array_equal(p, p1) and np.array_equal(f, f1)
-    jd = jobs[4]
-    p_ref, _ = oracle_lib.solve(jd["V"], jd["F"], jd["k"], jd["neumann"])
-    assert _rel(res[4][0], p_ref) < SOL_TOL
+    for jd, r in zip(jobs, res):
+        L, R = oracle_lib.assemble(jd["V"], jd["F"], jd["k"])
+        p_ref = np.linalg.solve(L, R @ jd["neumann"])
+        assert _rel(r[0], p_ref) < SOL_TOL
+        assert _rel(r[1], oracle_lib.evaluate(jd["V"], jd["F"], jd["k"], jd["points"], p_ref, jd["neumann"])) < SOL_TOL
 
 
 @pytest.fixture(scope="module")

@@ -32,21 +32,43 @@ def _jobs():
     return out
 
 
-def test_results_same_alone_and_in_the_mix(nb):
+def _oracle_check(oracle_lib, jd, p, f):
+    """Every right-hand side of a served request against the FP64 oracle (dense solve of the
+    oracle's operators), surface and field, at the solver's 1e-4 bar."""
+    L, R = oracle_lib.assemble(jd["V"], jd["F"], jd["k"])
+    G = np.asarray(jd["neumann"]).reshape(len(jd["F"]), -1)
+    P = np.asarray(p).reshape(len(jd["F"]), -1, order="F")
+    Fd = np.asarray(f).reshape(len(jd["points"]), -1, order="F")
+    for s in range(G.shape[1]):
+        p_ref = np.linalg.solve(L, R @ G[:, s])
+        f_ref = oracle_lib.evaluate(jd["V"], jd["F"], jd["k"], jd["points"], p_ref, G[:, s])
+        assert np.linalg.norm(P[:, s] - p_ref) / np.linalg.norm(p_ref) < 1e-4
+        assert np.linalg.norm(Fd[:, s] - f_ref) / np.linalg.norm(f_ref) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_results_same_alone_and_in_the_mix(nb, oracle_lib, prec):
+    """Six requests of 640-2400 triangles and 1-3 right-hand sides through three slots: each
+    result is bit-identical to the same request solved alone, and within 1e-4 of the FP64
+    oracle, in plain FP32 and in mixed precision (BF16 inner solves, FP32 refinement)."""
+    opts = nb.nat_bem_opts_default(prec=nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16)
     jobs = _jobs()
     alone = []
     for jd in jobs:
-        with nb.Operator.assemble(jd["V"], jd["F"], jd["k"]) as op:
+        with nb.Operator.assemble(jd["V"], jd["F"], jd["k"], opts) as op:
             p, info, st = op.solve(jd["neumann"])
             assert st == nb.NAT_BEM_OK
             alone.append((p, op.evaluate(jd["points"], p, jd["neumann"])))
-    with nb.Server(64 << 30, slots=3) as srv:
+    with nb.Server(64 << 30, opts, slots=3) as srv:
         tickets = [srv.submit(jd) for jd in jobs]
         res = [srv.wait(t, 120000) for t in tickets]
         assert srv.reserved() == 0
-    for (st, p, f, info, dev_ms, q_ms, tot_ms), (p1, f1) in zip(res, alone):
+    for (st, p, f, info, dev_ms, q_ms, tot_ms), (p1, f1), jd in zip(res, alone, jobs):
         assert st == nb.NAT_BEM_OK and info.iterations > 0 and dev_ms > 0 and tot_ms >= q_ms >= 0
+        if prec == "bf16":
+            assert info.refinements >= 1
         assert np.array_equal(p, p1) and np.array_equal(f, f1)
+        _oracle_check(oracle_lib, jd, p, f)
 
 
 def test_budget_admits_one_at_a_time(nb):
