@@ -2001,7 +2001,8 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
         return st;
       }
     }
-    st = product(op, which, eng, xpad, nrhs, y64, nullptr, nullptr, scratch, sbytes, err, s);
+    if (eng != kEngineFp32 && which == 0) st = tc_tune(op, eng, nrhs, xpad, y64, scratch, sbytes, err, s);
+    if (st == NAT_BEM_OK) st = product(op, which, eng, xpad, nrhs, y64, nullptr, nullptr, scratch, sbytes, err, s);
   }
   if (st == NAT_BEM_OK) {
     const int64_t cnt = (int64_t)n * nrhs;
@@ -2059,6 +2060,8 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   // m iterations, each on the current residual
   const bool restarted = ws->m < std::max(1, o.max_iter);
   if (inner == kEngineGemvBf16) gemv_bf16_tune(op->Lb, n, (int)op->geo.ld, ws->gin, ws->w, s);
+  if (inner == kEngineTf32 || inner == kEngineBf16)  // the tensor-core shape, outside any capture
+    NB_TRY(tc_tune(op, inner, nrhs, ws->xf, ws->w, ws->tc_scratch, ws->tc_bytes, ws->tc_err, s));
   if (!mixed && !restarted) {
     GArgs a = make_args(op, ws, op->L);
     a.maxit = o.max_iter;

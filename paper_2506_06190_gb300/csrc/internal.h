@@ -191,6 +191,10 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
                        double2* Y, const int* done, const int* scal, void* scratch,
                        size_t scratch_bytes, int* err, cudaStream_t s);
 size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms);
+// Picks the tensor-core product's launch shape for this operator size and RHS count by timing
+// the candidates once per size class (outside graph capture); X, Y and scratch are the caller's.
+nat_bem_status tc_tune(nat_bem_op* op, int engine, int nrhs, const float2* X, double2* Y,
+                       void* scratch, size_t scratch_bytes, int* err, cudaStream_t s);
 
 // eval.cu
 nat_bem_status eval_impl(const nat_bem_op* op, const double* d_pts, int64_t m,

@@ -6,12 +6,17 @@
 //    product is a real GEMM: row i of the complex64 operator read as 2*ld reals
 //    [Re M_i0, Im M_i0, Re M_i1, ...] times the real matrix B whose column c < P is
 //    (Re x_c0, -Im x_c0, Re x_c1, ...) and column P + c is (Im x_c0, Re x_c0, ...); then
-//    Y[i][c] = Re (M x_c)_i and Y[i][P + c] = Im (M x_c)_i. A 128-row tile of the operator and
-//    the whole of B (N = 2P <= 256 columns) are staged by TMA with 128-byte swizzling through
-//    a ring of shared-memory stages guarded by mbarriers; one thread issues the TMA copies,
-//    one thread issues the MMAs into a TMEM accumulator (128 lanes x N columns, FP32), and all
-//    four warps read TMEM back (tcgen05.ld) for the epilogue. K is split over blocks; the FP32
-//    partials are summed in a fixed order into FP64.
+//    Y[i][c] = Re (M x_c)_i and Y[i][P + c] = Im (M x_c)_i. At tens of right-hand sides this is
+//    far below the tensor ridge, so the kernel is built to stream the operator at HBM speed:
+//    a persistent grid (one CTA per SM) splits the (128-row tile, K block) iteration space into
+//    equal contiguous ranges (stream-K), so every SM streams the same number of operator bytes
+//    whatever the tile count. One thread issues TMA copies (128-byte swizzle) of the A tile and
+//    of B into a ring of up to eight shared-memory stages guarded by mbarriers; one thread
+//    issues the MMAs into one of two TMEM accumulators (128 lanes x N columns, FP32), switching
+//    at each new row tile, so four epilogue warps drain the previous tile's accumulator
+//    (tcgen05.ld) while the next one fills. Each CTA writes one partial tile per row tile it
+//    touched; k_tc_reduce adds a tile's partials in K order in FP64 (a fixed order, so results
+//    do not depend on timing).
 //  * k_cgemm_fp32: FP32 CUDA-core complex GEMM (64 rows x 32 RHS per block, FP32 products
 //    summed in FP32 over 128 terms, then FP64) for the products that must carry full FP32
 //    accuracy: the right-hand side R G, the refinement residuals and the plain FP32 solve.
@@ -23,7 +28,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 #include <string>
 
 #include "internal.h"
@@ -34,8 +43,10 @@ namespace natbem {
 namespace {
 
 constexpr int kTcRows = 128;         // M of the MMA (rows of the operator per tile)
-constexpr int kTcStages = 3;         // shared-memory ring
-constexpr int kTcThreads = 128;
+constexpr int kTcMaxStages = 8;      // shared-memory ring (as many as fit, at most this)
+constexpr int kTcThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kTcMinBlocks = 4;      // K blocks per CTA at least (small products use fewer CTAs)
+constexpr uint32_t kTcSmemMax = 227 * 1024 - 256;  // dynamic shared memory (static needs a little)
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -79,6 +90,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
     if ((i & 1023u) == 1023u && globaltimer_ns() - t0 > timeout_ns) return false;
   }
   return false;
+}
+
+// The same wait, giving up early once *abort is set by another role of the block.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity, const volatile int* abort,
+                                                   uint64_t timeout_ns = 2000000000ull) {
+  const uint64_t t0 = globaltimer_ns();
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && (*abort || globaltimer_ns() - t0 > timeout_ns)) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
@@ -154,50 +180,66 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 
 }  // namespace
 
-// Y_part[ks][row][c] = sum over this block's K range of A[row][k] B[c][k]. A: n x Kt (tensor map
-// ta, box BK x 128), B: Ng x Kt (tensor map tb, box BK x Ng). kKind 0: TF32 (FP32 storage,
-// BK = 32), 1: BF16 (BK = 64); either way a stage row is 128 bytes and one MMA covers 32
-// bytes of K, four per stage.
-template <int kKind>
+// Partial products of the stream-K partition: the iteration space is the m_tiles x nkb grid of
+// (row tile, K block) pairs in row-major order, T = m_tiles * nkb, a row tile being kTiles x 128
+// rows; CTA c takes the pairs [c per, min((c + 1) per, T)). Each contiguous run of one row tile
+// is a segment; segment j of CTA c goes to partial slot c * msp + j (msp: most segments a CTA
+// can have), stored column by column: part[slot][col][row in tile]. With kTiles = 2 one B stage
+// feeds two M = 128 MMAs (two accumulators), halving B's share of the shared-memory traffic.
+// A: n x Kt (tensor map ta, box BK x 128 kTiles), B: Ng x Kt
+// (tensor map tb, box BK x Ng). kKind 0: TF32 (FP32 storage, BK = 32), 1: BF16 (BK = 64);
+// either way a stage row is 128 bytes and one MMA covers 32 bytes of K, four per stage.
+template <int kKind, int kTiles>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int n,
-          int Kt, int kps, int Ng, float* __restrict__ part, int* __restrict__ err,
-          const int* __restrict__ scal) {
+          int nkb, int per, int msp, int Ng, int stages, float* __restrict__ part,
+          int* __restrict__ err, const int* __restrict__ scal) {
   constexpr int BK = kKind == 0 ? 32 : 64;
+  constexpr int TM = kTcRows * kTiles;
   if (scal && scal[1]) return;  // every right-hand side has converged
+  const int m_tiles = (n + TM - 1) / TM;
+  const int64_t T = (int64_t)m_tiles * nkb;
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t t1 = min(T, t0 + per);
+  if (t0 >= T) return;
+  const int mt_first = (int)(t0 / nkb);
+  const int nseg = (int)((t1 - 1) / nkb) - mt_first + 1;
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte alignment of the shared-memory address itself (the 128-byte swizzle atom)
   const uint32_t raw = smem_u32(smem_raw);
   uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  const uint32_t a_bytes = kTcRows * 128, b_bytes = (uint32_t)Ng * 128;
+  const uint32_t a_bytes = TM * 128, b_bytes = (uint32_t)Ng * 128;
   const uint32_t stage_bytes = a_bytes + b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + kTcStages * stage_bytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kTcStages;
-  uint64_t* accum = bars + 2 * kTcStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
-  __shared__ int s_abort;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + stages * stage_bytes);
+  uint64_t* full = bars;                     // [stages] TMA -> MMA
+  uint64_t* empty = bars + kTcMaxStages;     // [stages] MMA -> TMA
+  uint64_t* tfull = bars + 2 * kTcMaxStages; // [2] MMA -> epilogue: accumulators ready
+  uint64_t* tempty = tfull + 2;              // [2] epilogue -> MMA: accumulators drained
+  uint64_t* fin = tempty + 2;                // every MMA of the block complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kTcRows, ks = blockIdx.y;
-  const int k_begin = ks * kps;
-  const int k_end = min(Kt, k_begin + kps);
-  const int nk = k_end > k_begin ? (k_end - k_begin + BK - 1) / BK : 0;
-  uint32_t ncols = 32;
+  uint32_t ncols = 32;  // TMEM columns per accumulator (a power of two >= Ng)
   while ((int)ncols < Ng) ncols <<= 1;
+  const uint32_t alloc_cols = 2 * kTiles * ncols;  // two buffers of kTiles accumulators
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < kTcStages; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
+    for (int q = 0; q < stages; ++q) {
+      mbar_init(smem_u32(&full[q]), 1);
+      mbar_init(smem_u32(&empty[q]), 1);
     }
-    mbar_init(smem_u32(accum), 1);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&tfull[q]), 1);
+      mbar_init(smem_u32(&tempty[q]), 4);
+    }
+    mbar_init(smem_u32(fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"(ncols));
+                 "r"(alloc_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -206,77 +248,113 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // producer: TMA copies of the A tile and of B into the ring
+    // producer: TMA copies of A tile (mt, kb) and of B's K block kb into the ring
     int issued = 0;
-    for (int it = 0; it < nk && !s_abort; ++it) {
-      const int s = it % kTcStages;
-      const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
-      if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1u)) {
+    for (int64_t t = t0; t < t1 && !s_abort; ++t) {
+      const int it = (int)(t - t0);
+      const int q = it % stages;
+      const uint32_t ph = (uint32_t)(it / stages) & 1u;
+      if (!mbar_wait_or_abort(smem_u32(&empty[q]), ph ^ 1u, &s_abort)) {
         atomicOr(err, 1);
         s_abort = 1;
         break;
       }
-      const uint32_t sa = smem_u32(base + s * stage_bytes);
-      const uint32_t fb = smem_u32(&full[s]);
+      const uint32_t sa = smem_u32(base + q * stage_bytes);
+      const uint32_t fb = smem_u32(&full[q]);
       mbar_expect_tx(fb, stage_bytes);
-      const int k0 = k_begin + it * BK;
-      tma_load_2d(sa, &ta, k0, m0, fb);
-      tma_load_2d(sa + a_bytes, &tb, k0, 0, fb);
+      const int mt = (int)(t / nkb), kb = (int)(t % nkb);
+      tma_load_2d(sa, &ta, kb * BK, mt * TM, fb);
+      tma_load_2d(sa + a_bytes, &tb, kb * BK, 0, fb);
       issued = it + 1;
     }
     if (s_abort) {
       // let the copies already issued land before the block exits
-      for (int it = max(0, issued - kTcStages); it < issued; ++it)
-        mbar_wait(smem_u32(&full[it % kTcStages]), (uint32_t)(it / kTcStages) & 1u);
+      for (int it = max(0, issued - stages); it < issued; ++it)
+        mbar_wait(smem_u32(&full[it % stages]), (uint32_t)(it / stages) & 1u);
     }
   } else if (warp == 1 && lane == 0) {
-    // MMA issuer
+    // MMA issuer: kTiles accumulators per segment, alternating between the two TMEM buffers
     const uint32_t idesc = instr_desc(kKind == 0 ? 2u : 1u, (uint32_t)Ng, (uint32_t)kTcRows);
-    for (int it = 0; it < nk && !s_abort; ++it) {
-      const int s = it % kTcStages;
-      const uint32_t ph = (uint32_t)(it / kTcStages) & 1u;
-      if (!mbar_wait(smem_u32(&full[s]), ph)) {
+    int seg = -1, mt_cur = -1;
+    uint32_t acc = tmem;
+    bool first = true;
+    for (int64_t t = t0; t < t1 && !s_abort; ++t) {
+      const int it = (int)(t - t0);
+      const int mt = (int)(t / nkb);
+      if (mt != mt_cur) {
+        if (seg >= 0) mma_commit(smem_u32(&tfull[seg & 1]));
+        ++seg;
+        mt_cur = mt;
+        if (!mbar_wait_or_abort(smem_u32(&tempty[seg & 1]), ((uint32_t)(seg >> 1) & 1u) ^ 1u, &s_abort)) {
+          atomicOr(err, 8);
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        acc = tmem + (uint32_t)(seg & 1) * kTiles * ncols;
+        first = true;
+      }
+      const int q = it % stages;
+      const uint32_t ph = (uint32_t)(it / stages) & 1u;
+      if (!mbar_wait_or_abort(smem_u32(&full[q]), ph, &s_abort)) {
         atomicOr(err, 2);
         s_abort = 1;
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(base + s * stage_bytes);
-      const uint64_t da = smem_desc(sa), db = smem_desc(sa + a_bytes);
+      const uint32_t sa = smem_u32(base + q * stage_bytes);
+      const uint64_t db = smem_desc(sa + a_bytes);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per MMA: +2 in the 16-byte address field
-        mma<kKind>(tmem, da + 2 * kk, db + 2 * kk, idesc, (it > 0 || kk > 0) ? 1u : 0u);
-      mma_commit(smem_u32(&empty[s]));
-    }
-    mma_commit(smem_u32(accum));
-  }
-  __syncwarp();
-  // epilogue: TMEM lanes 32w..32w+31 hold rows m0 + 32w + lane, 32 columns per load
-  const bool ok = mbar_wait(smem_u32(accum), 0);
-  if (!ok && lane == 0) atomicOr(err, 4);
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  __syncwarp();
-  if (ok && !s_abort) {
-    const int row = m0 + warp * 32 + lane;
-    float* out = part + ((size_t)ks * n + (size_t)row) * Ng;
-    for (int c0 = 0; c0 < Ng; c0 += 32) {  // Ng is a multiple of 32
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < n && nk > 0) {
+      for (int u = 0; u < kTiles; ++u) {
+        const uint64_t da = smem_desc(sa + u * kTcRows * 128);
 #pragma unroll
-        for (int q = 0; q < 32; q += 4)
-          *reinterpret_cast<float4*>(out + c0 + q) =
-              make_float4(__uint_as_float(r[q]), __uint_as_float(r[q + 1]),
-                          __uint_as_float(r[q + 2]), __uint_as_float(r[q + 3]));
-      } else if (row < n) {
-#pragma unroll
-        for (int q = 0; q < 32; q += 4) *reinterpret_cast<float4*>(out + c0 + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int kk = 0; kk < 4; ++kk)  // 32 bytes of K per MMA: +2 in the 16-byte address field
+          mma<kKind>(acc + u * ncols, da + 2 * kk, db + 2 * kk, idesc, (!first || kk > 0) ? 1u : 0u);
       }
+      first = false;
+      mma_commit(smem_u32(&empty[q]));
+    }
+    if (seg >= 0) mma_commit(smem_u32(&tfull[seg & 1]));
+    mma_commit(smem_u32(fin));
+  } else if (warp >= 2) {
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of each accumulator, i.e. rows
+    // u 128 + 32 (w % 4) + lane of the row tile
+    const int quarter = warp & 3;
+    for (int j = 0; j < nseg; ++j) {
+      const int b = j & 1;
+      if (!mbar_wait_or_abort(smem_u32(&tfull[b]), (uint32_t)(j >> 1) & 1u, &s_abort)) {
+        if (lane == 0) atomicOr(err, 4);
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* out = part + ((size_t)blockIdx.x * msp + j) * (size_t)Ng * TM;
+#pragma unroll
+      for (int u = 0; u < kTiles; ++u) {
+        const int r = u * kTcRows + quarter * 32 + lane;
+        for (int c0 = 0; c0 < Ng; c0 += 32) {  // Ng is a multiple of 32
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * kTiles + u) * ncols + (uint32_t)c0, v);
+          if (!s_abort) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) out[(size_t)(c0 + q) * TM + r] = __uint_as_float(v[q]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+  if (warp == 0) {
+    // every MMA of the block has completed before the accumulators are released (bounded)
+    if (!mbar_wait(smem_u32(fin), 0) && lane == 0) atomicOr(err, 16);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(alloc_cols));
+  }
 }
 
 // B for the tensor-core product from nrhs complex64 vectors (x_c at X + c * ld), P = nrhs
@@ -307,20 +385,25 @@ __global__ void k_pack_b(const float2* __restrict__ X, int ld, int nrhs, int P, 
   }
 }
 
-// Y[c][row] (complex128, column c at Y + c * n) = sum over splits of the FP32 partials.
-__global__ void k_tc_reduce(const float* __restrict__ part, int n, int Ng, int P, int nrhs,
-                            int splits, double2* __restrict__ Y, const int* __restrict__ done,
-                            const int* __restrict__ scal) {
+// Y[c][row] (complex128, column c at Y + c * n) = the sum of the row tile's partial tiles in K
+// order (the CTAs c_lo..c_hi that covered it, see k_tc_gemm; TM rows per tile), in FP64.
+__global__ void k_tc_reduce(const float* __restrict__ part, int n, int TM, int Ng, int P, int nrhs,
+                            int nkb, int per, int msp, double2* __restrict__ Y,
+                            const int* __restrict__ done, const int* __restrict__ scal) {
   if (scal && scal[1]) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nrhs * n
   if (i >= (int64_t)nrhs * n) return;
   const int c = (int)(i / n), row = (int)(i % n);
   if (done && done[c]) return;
+  const int mt = row / TM, r = row % TM;
+  const int64_t first = (int64_t)mt * nkb, last = first + nkb - 1;
+  const int c_lo = (int)(first / per), c_hi = (int)(last / per);
   double re = 0.0, im = 0.0;
-  for (int s = 0; s < splits; ++s) {
-    const float* p = part + ((size_t)s * n + row) * Ng;
-    re += p[c];
-    im += p[P + c];
+  for (int cta = c_lo; cta <= c_hi; ++cta) {
+    const int j = mt - (int)(((int64_t)cta * per) / nkb);  // the segment of this tile in CTA cta
+    const float* p = part + ((size_t)cta * msp + j) * (size_t)Ng * TM;
+    re += p[(size_t)c * TM + r];
+    im += p[(size_t)(P + c) * TM + r];
   }
   Y[(size_t)c * n + row] = make_double2(re, im);
 }
@@ -453,19 +536,112 @@ nat_bem_status make_map(CUtensorMap* map, CUtensorMapDataType dt, const void* pt
   }
   return NAT_BEM_OK;
 }
+
+}  // namespace
+
+namespace {
+// The stream-K partition of k_tc_gemm for n rows in tiles of tm and nkb K blocks on `ctas`
+// CTAs at most: the CTA count, the K blocks per CTA and the most row-tile segments one CTA can
+// touch.
+struct TcPlan {
+  int grid, per, msp;
+};
+TcPlan tc_plan(int64_t n, int64_t tm, int64_t nkb, int ctas) {
+  const int64_t m_tiles = (n + tm - 1) / tm;
+  const int64_t T = m_tiles * nkb;
+  int64_t g = std::max<int64_t>(1, std::min<int64_t>(ctas, (T + kTcMinBlocks - 1) / kTcMinBlocks));
+  const int64_t per = (T + g - 1) / g;
+  g = (T + per - 1) / per;
+  return TcPlan{(int)g, (int)per, (int)((per + nkb - 1) / nkb + 1)};
+}
+
+// Launch shape of k_tc_gemm: row tiles per stage (1 or 2 x 128 rows), ring stages, CTAs per SM.
+struct TcShape {
+  int tiles, stages, cps;
+};
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : dflt;
+}
+
+uint32_t tc_fixed_bytes() { return 1024 + 8 * (2 * kTcMaxStages + 5) + 16; }
+
+uint32_t tc_ncols(int Ng) {
+  uint32_t c = 32;
+  while ((int)c < Ng) c <<= 1;
+  return c;
+}
+
+// A shape with as many stages as fit beside `cps` - 1 other CTAs on the SM, or stages = 0 if the
+// two TMEM buffers of every CTA on the SM do not fit in its 512 columns or the operator is
+// shorter than one row tile.
+TcShape tc_fit(int Ng, int64_t n, int tiles, int cps, int max_stages = kTcMaxStages) {
+  TcShape sh{tiles, 0, cps};
+  if (2u * tiles * tc_ncols(Ng) * cps > 512u || (tiles > 1 && n < (int64_t)tiles * kTcRows)) return sh;
+  const uint32_t budget = cps == 1 ? kTcSmemMax : (228u * 1024u / 2u - 1024u - 256u);
+  const uint32_t stage_bytes = (uint32_t)(kTcRows * tiles * 128 + Ng * 128);
+  const int fit = (int)((budget - tc_fixed_bytes()) / stage_bytes);
+  sh.stages = std::min(std::min(kTcMaxStages, max_stages), fit);
+  if (sh.stages < 2) sh.stages = 0;
+  return sh;
+}
+
+// Candidate shapes in order of preference: two CTAs per SM (two independent TMA / MMA streams),
+// two row tiles per stage (B read once for 256 rows), one of each.
+std::vector<TcShape> tc_candidates(int Ng, int64_t n) {
+  std::vector<TcShape> out;
+  for (auto tc : {std::make_pair(1, 2), std::make_pair(2, 1), std::make_pair(1, 1)}) {
+    const TcShape sh = tc_fit(Ng, n, tc.first, tc.second);
+    if (sh.stages) out.push_back(sh);
+  }
+  return out;
+}
+
+// Shapes the autotuner chose, per (device, operator rows rounded up to 1024, Ng, engine).
+std::mutex g_tc_mu;
+std::map<std::tuple<int, int64_t, int, int>, TcShape> g_tc_tuned;
+
+// The shape for this product: NATBEM_TC_TILES / _CPS / _STAGES when set (diagnostics), else the
+// tuned one, else the first candidate.
+TcShape tc_shape(int dev, int64_t n, int Ng, int engine) {
+  const char* et = std::getenv("NATBEM_TC_TILES");
+  const char* ec = std::getenv("NATBEM_TC_CPS");
+  if (et || ec) {
+    TcShape sh = tc_fit(Ng, n, std::max(1, std::min(2, env_int("NATBEM_TC_TILES", 1))),
+                        std::max(1, std::min(2, env_int("NATBEM_TC_CPS", 1))),
+                        std::max(2, env_int("NATBEM_TC_STAGES", kTcMaxStages)));
+    if (sh.stages) return sh;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    auto f = g_tc_tuned.find(std::make_tuple(dev, round_up(n, 1024), Ng, engine));
+    if (f != g_tc_tuned.end()) return f->second;
+  }
+  return tc_candidates(Ng, n).front();
+}
 }  // namespace
 
 size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
   const int P = (int)round_up(nrhs, 16);  // N = 2P is a multiple of 32: whole TMEM loads
   const int Ng = 2 * P;
-  const int64_t m_tiles = (n + kTcRows - 1) / kTcRows;
-  const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(16, (4 * sms + m_tiles - 1) / m_tiles));
-  return (size_t)Ng * 2 * ld * 4 + (size_t)splits * n * Ng * 4 + 64;
+  const int64_t Kt = 2 * ld;
+  // partial tiles: the largest plan over K blocks of 32 (TF32) or 64 (BF16), row tiles of 128
+  // or 256 and one or two CTAs per SM
+  size_t floats = 0;
+  for (int64_t bk : {32, 64})
+    for (int64_t tm : {128, 256})
+      for (int cps : {1, 2}) {
+        const TcPlan pl = tc_plan(n, tm, (Kt + bk - 1) / bk, cps * sms);
+        floats = std::max(floats, (size_t)pl.grid * pl.msp * (size_t)tm);
+      }
+  return round_up((size_t)Ng * Kt * 4, 256) + floats * Ng * 4 + 64;
 }
 
-nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
-                       double2* Y, const int* done, const int* scal, void* scratch,
-                       size_t scratch_bytes, int* err, cudaStream_t s) {
+static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
+                                     double2* Y, const int* done, const int* scal, void* scratch,
+                                     size_t scratch_bytes, int* err, cudaStream_t s,
+                                     const TcShape* force) {
   const int n = (int)op->n, ld = which == 1 ? (int)op->ldr : (int)op->geo.ld;
   const float2* M = which == 0 ? op->L : op->R;
   if (engine == kEngineFp32) {
@@ -489,15 +665,14 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
     return NAT_BEM_EINVAL;
   }
   const int64_t Kt = 2 * (int64_t)ld;
-  const int m_tiles = (n + kTcRows - 1) / kTcRows;
-  const int splits = std::max(1, std::min(16, (4 * sms + m_tiles - 1) / m_tiles));
   const int BK = engine == kEngineTf32 ? 32 : 64;
-  int kps = (int)((Kt + splits - 1) / splits);
-  kps = (kps + BK - 1) / BK * BK;
-  const int nsplit = (int)((Kt + kps - 1) / kps);
+  const int nkb = (int)((Kt + BK - 1) / BK);
+  const TcShape sh = force ? *force : tc_shape(dev, n, Ng, engine);
+  const int TM = kTcRows * sh.tiles;
+  const TcPlan pl = tc_plan(n, TM, nkb, sh.cps * sms);
   const size_t esz = engine == kEngineTf32 ? 4 : 2;
   const size_t bbytes = (size_t)Ng * Kt * esz;
-  const size_t pbytes = (size_t)nsplit * n * Ng * 4;
+  const size_t pbytes = (size_t)pl.grid * pl.msp * Ng * TM * 4;
   if (round_up(bbytes, 256) + pbytes > scratch_bytes) {
     set_error("tensor-core product: scratch too small");
     return NAT_BEM_ECUDA;
@@ -515,28 +690,98 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
   CUtensorMap ta, tb;
   const CUtensorMapDataType dt = engine == kEngineTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const void* Aptr = engine == kEngineTf32 ? (const void*)op->L : (const void*)op->Lb;
-  NB_TRY(make_map(&ta, dt, Aptr, (uint64_t)Kt, (uint64_t)n, (uint64_t)Kt * esz, (uint32_t)BK, kTcRows));
+  NB_TRY(make_map(&ta, dt, Aptr, (uint64_t)Kt, (uint64_t)n, (uint64_t)Kt * esz, (uint32_t)BK, (uint32_t)TM));
   NB_TRY(make_map(&tb, dt, B, (uint64_t)Kt, (uint64_t)Ng, (uint64_t)Kt * esz, (uint32_t)BK, (uint32_t)Ng));
-  const size_t smem = 1024 + (size_t)kTcStages * (kTcRows * 128 + (size_t)Ng * 128) + 8 * (2 * kTcStages + 2);
-  dim3 grid(m_tiles, nsplit);
-  // opt in to the dynamic shared memory this launch needs (once per size increase)
-  static size_t attr_set[2] = {0, 0};
-  const int ki = engine == kEngineTf32 ? 0 : 1;
-  if (smem > attr_set[ki]) {
-    if (ki == 0)
-      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    else
-      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set[ki] = smem;
+  const uint32_t stage_bytes = (uint32_t)(TM * 128 + Ng * 128);
+  const size_t smem = tc_fixed_bytes() + (size_t)sh.stages * stage_bytes;
+  // opt in to the largest dynamic shared memory any launch uses (per kernel, once)
+  static std::mutex attr_mu;
+  static bool attr_set = false;
+  {
+    std::lock_guard<std::mutex> lk(attr_mu);
+    if (!attr_set) {
+      const int mx = (int)kTcSmemMax;
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      attr_set = true;
+    }
   }
-  if (ki == 0)
-    NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
-  else
-    NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1><<<grid, kTcThreads, smem, s>>>(ta, tb, n, (int)Kt, kps, Ng, part, err, scal));
+  if (engine == kEngineTf32) {
+    if (sh.tiles == 2)
+      NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0, 2><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+    else
+      NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0, 1><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+  } else {
+    if (sh.tiles == 2)
+      NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1, 2><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+    else
+      NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1, 1><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+  }
   NB_CHECK_LAUNCH();
   const int64_t tot = (int64_t)nrhs * n;
-  NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, n, Ng, P, nrhs, nsplit, Y, done, scal));
+  NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, n, TM, Ng, P, nrhs, nkb, pl.per, pl.msp, Y, done, scal));
   NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
+}
+
+nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
+                       double2* Y, const int* done, const int* scal, void* scratch,
+                       size_t scratch_bytes, int* err, cudaStream_t s) {
+  return product_shaped(op, which, engine, X, nrhs, Y, done, scal, scratch, scratch_bytes, err, s, nullptr);
+}
+
+// The tensor-core product's autotuner, run once per (device, size class, Ng, engine) before the
+// first product of a solve (outside any graph capture): each candidate shape is timed on the
+// operator itself with CUDA events on the solve's stream, one warm-up round and three
+// interleaved rounds, keeping each shape's minimum (other streams' kernels only slow a run
+// down); the first candidate wins ties within 2%. X and Y are scratch of the caller.
+nat_bem_status tc_tune(nat_bem_op* op, int engine, int nrhs, const float2* X, double2* Y,
+                       void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
+  if (engine != kEngineTf32 && engine != kEngineBf16) return NAT_BEM_OK;
+  if (std::getenv("NATBEM_TC_TILES") || std::getenv("NATBEM_TC_CPS")) return NAT_BEM_OK;
+  int dev = 0;
+  NB_TRY_CUDA(cudaGetDevice(&dev));
+  const int Ng = 2 * (int)round_up(nrhs, 16);
+  const auto key = std::make_tuple(dev, round_up(op->n, 1024), Ng, engine);
+  {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    if (g_tc_tuned.count(key)) return NAT_BEM_OK;
+  }
+  const std::vector<TcShape> cand = tc_candidates(Ng, op->n);
+  if (cand.size() < 2) {
+    std::lock_guard<std::mutex> lk(g_tc_mu);
+    g_tc_tuned[key] = cand.front();
+    return NAT_BEM_OK;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  NB_TRY_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    set_error("cudaEventCreate failed");
+    return NAT_BEM_ECUDA;
+  }
+  std::vector<float> best(cand.size(), 1e30f);
+  nat_bem_status st = NAT_BEM_OK;
+  for (int round = 0; round < 4 && st == NAT_BEM_OK; ++round)
+    for (size_t c = 0; c < cand.size() && st == NAT_BEM_OK; ++c) {
+      cudaEventRecord(e0, s);
+      st = product_shaped(op, 0, engine, X, nrhs, Y, nullptr, nullptr, scratch, scratch_bytes, err, s, &cand[c]);
+      cudaEventRecord(e1, s);
+      if (st == NAT_BEM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+        float ms = 0.f;
+        if (round > 0 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) best[c] = std::min(best[c], ms);
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != NAT_BEM_OK) return st;
+  size_t pick = 0;
+  for (size_t c = 1; c < cand.size(); ++c)
+    if (best[c] < 0.98f * best[pick]) pick = c;
+  std::lock_guard<std::mutex> lk(g_tc_mu);
+  g_tc_tuned[key] = cand[pick];
   return NAT_BEM_OK;
 }
 
