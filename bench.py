@@ -346,8 +346,9 @@ def run_modal(args):
         gbs = op_bytes / per / 1e9
         tfl = flops / per / 1e12
         tpeak = peaks["bf16_tflops"] * (1.0 if args.prec == "bf16" else 0.5)
+        traffic = NCU_TRAFFIC_MODAL_20480.get(args.prec) if n == 20480 and args.nrhs == 64 else None
         roof = {"kernel": tc_name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": gbs / peaks["hbm_gbs"], "traffic": None, "launches": tc[1], "launches_exited_early": tc[2],
+                "frac": gbs / peaks["hbm_gbs"], "traffic": traffic, "launches": tc[1], "launches_exited_early": tc[2],
                 "tensor_tflops": tfl, "tensor_peak": tpeak,
                 "tensor_frac": tfl / tpeak,
                 "note": "operator bytes per launch (the packed right-hand sides are small beside them); "
@@ -376,6 +377,12 @@ def run_modal(args):
                       "max_rel_residual": max(i[2] for i in infos),
                       "not_converged": sum(1 for i in infos if i[3] != 0)},
             "gpu_launches": int(launches), "roofline": roof, "accuracy": acc, "clocks": clk.summary()}
+
+
+# DRAM bytes (read + write) per launch of the BF16 tensor-core product on the 20480-triangle,
+# 64-RHS modal operator, from one ncu capture (profiles/k_tc_gemm_modal_20480tri_64rhs.md,
+# the mean of three launches).
+NCU_TRAFFIC_MODAL_20480 = {"bf16": 1.7233e9 + 11.57e6}
 
 
 def run_mc(args):
