@@ -187,7 +187,11 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
     stream = torch.cuda.current_stream(dev)
 
     def step(conc=None):
-        st, res = nb.nat_bem_run_batch(jobs, opts, concurrency=conc or args.concurrency)
+        if args.batch_mode == "fused" and conc is None:
+            st, res = nb.nat_bem_run_batch_fused(jobs, opts, max_batch=args.max_batch,
+                                                 concurrency=args.fused_workers)
+        else:
+            st, res = nb.nat_bem_run_batch(jobs, opts, concurrency=conc or args.concurrency)
         if st not in (nb.NAT_BEM_OK, nb.NAT_BEM_ENOCONV):
             raise RuntimeError(nb.nat_bem_last_error())
         return res
@@ -811,8 +815,11 @@ NCU_TRAFFIC_NAT_PER_MQUERY = 28.146944e6 + 0.048128e6
 
 def run_uneven(args):
     """Uneven batch: --n-mesh perturbed ring spheres of 500-8000 triangles (log-uniform), one
-    wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4, through the
-    batch driver (largest first, --concurrency workers)."""
+    wavenumber (ka in [0.5, 12]) and one smooth field each, 1024 points at radius 4. Two forms of
+    the same batch, each timed over --steps steps: the fused batch (size buckets of meshes solved
+    in lockstep as padded systems of independent operators, --max-batch meshes per bucket; the
+    line's value) and the worker pool (largest first, --concurrency workers, one op and stream
+    each). The lowest, median and largest meshes' results are checked against the oracle."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -829,28 +836,61 @@ def run_uneven(args):
                          neumann=torch.from_numpy(np.ascontiguousarray(pr.neumann[0][:, 0]).astype(np.complex64)).to(dev),
                          points=torch.from_numpy(pr.points).to(dev)))
     stream = torch.cuda.current_stream(dev)
-    for _ in range(args.warmup):
-        nb.nat_bem_run_batch(jobs, opts, concurrency=args.concurrency)
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    lats = []
-    with ClockSampler(0) as clk:
-        t0.record(stream)
-        for _ in range(args.steps):
-            st, res = nb.nat_bem_run_batch(jobs, opts, concurrency=args.concurrency)
-            lats += [r[4] for r in res]
-        t1.record(stream)
+    runners = {"fused": lambda: nb.nat_bem_run_batch_fused(jobs, opts, max_batch=args.max_batch,
+                                                           concurrency=args.fused_workers),
+               "worker_pool": lambda: nb.nat_bem_run_batch(jobs, opts, concurrency=args.concurrency)}
+    out = {}
+    for name, fn in runners.items():
+        for _ in range(args.warmup):
+            fn()
         torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+        nb.nat_bem_trace_enable(False)
+        launches0 = nb.nat_bem_trace_launches()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lats = []
+        with ClockSampler(0) as clk:
+            t0.record(stream)
+            for _ in range(args.steps):
+                st, res = fn()
+                lats += [r[4] for r in res]
+            t1.record(stream)
+            torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        out[name] = dict(value=args.steps * len(jobs) / (ms * 1e-3), ms=ms, lats=lats, res=res, clk=clk.summary(),
+                         launches=nb.nat_bem_trace_launches() - launches0)
     sizes = [int(pr.F.shape[0]) for pr in probs]
-    return {"metric": METRIC, "value": args.steps * len(jobs) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+    f = out["fused"]
+    acc = None
+    if args.cpu:
+        import oracle
+        order = np.argsort(sizes)
+        errs = []
+        for q in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
+            pr = probs[q]
+            g = pr.neumann[0][:, 0]
+            pr_ref, fr_ref, _ = oracle.bem_solve(pr.V, pr.F, float(pr.ks[0]), g, pr.points, tol=1e-10, maxit=400)
+            for name in ("fused", "worker_pool"):
+                p_, f_ = out[name]["res"][q][0].cpu().numpy(), out[name]["res"][q][1].cpu().numpy()
+                errs.append({"n_tri": sizes[q], "form": name,
+                             "surface": float(np.linalg.norm(p_ - pr_ref) / np.linalg.norm(pr_ref)),
+                             "field": float(np.linalg.norm(f_ - fr_ref) / np.linalg.norm(fr_ref))})
+        acc = {"max": max(max(e["surface"], e["field"]) for e in errs), "per_job": errs}
+    return {"metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": f["ms"] / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
             "data": "synthetic",
             "config": {"workload": f"uneven_batch_{len(jobs)}meshes", "n_tri_range": [min(sizes), max(sizes)],
-                       "mean_n_tri": float(np.mean(sizes)), "concurrency": args.concurrency},
-            "latency_ms": dict(_percentiles(lats), per="one solve, device time, in the batch"),
-            "not_converged": sum(1 for r in res if r[3] != 0), "clocks": clk.summary()}
+                       "mean_n_tri": float(np.mean(sizes)), "form": "fused size buckets",
+                       "max_batch": args.max_batch, "fused_workers": args.fused_workers},
+            "latency_ms": dict(_percentiles(f["lats"]), per="one solve, device time of its bucket"),
+            "gpu_launches": int(f["launches"]),
+            "not_converged": sum(1 for r in f["res"] if r[3] != 0), "clocks": f["clk"],
+            "worker_pool": {"value": out["worker_pool"]["value"], "ms_per_step": out["worker_pool"]["ms"] / args.steps,
+                            "concurrency": args.concurrency, "gpu_launches": int(out["worker_pool"]["launches"]),
+                            "latency_ms": dict(_percentiles(out["worker_pool"]["lats"]),
+                                               per="one solve, device time, in the batch"),
+                            "not_converged": sum(1 for r in out["worker_pool"]["res"] if r[3] != 0)},
+            "rel_err_vs_oracle": acc}
 
 
 def run_serving(args):
@@ -1009,6 +1049,10 @@ def main():
     ap.add_argument("--n-queries", type=int, default=1 << 22, help="NAT inference workload: queries per step")
     ap.add_argument("--nrhs", type=int, default=64)
     ap.add_argument("--n-mesh", type=int, default=512)
+    ap.add_argument("--max-batch", type=int, default=64, help="uneven workload: meshes per fused bucket")
+    ap.add_argument("--fused-workers", type=int, default=4, help="fused batch: bucket workers")
+    ap.add_argument("--batch-mode", default="pool", choices=["pool", "fused"],
+                    help="interior workload: worker pool (one op per job) or fused buckets")
     ap.add_argument("--n-req", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--budget-gb", type=float, default=150.0)

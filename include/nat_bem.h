@@ -297,6 +297,33 @@ NAT_BEM_API nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
                                              void* cuda_stream);
 
 /*
+ * Fused batch (no counterpart in the paper; it batches the per-object solves of the data
+ * generation, Sec. 3.4): the jobs' meshes are sorted by size and grouped into buckets of
+ * meshes within a factor 2^(1/4) of the bucket's largest triangle count N (at most max_batch
+ * meshes, and at most 24 GB of operators per bucket). A bucket is solved as one system of
+ * independent operators in lockstep: each mesh's L and R (and BF16 copy) are assembled into
+ * one allocation, padded to N unknowns (identity rows in L, zero rows in R and zero right-hand
+ * side entries past the mesh's own n, which leaves its solution unchanged), and every GMRES
+ * iteration is one matvec launch over all the bucket's operators and one cooperative Arnoldi
+ * launch over all its Krylov spaces (captured in CUDA graphs), each mesh with its own
+ * convergence test. Each job's field is then evaluated on its own mesh. Jobs with nrhs > 1
+ * are solved one after another through the ordinary path. Results match nat_bem_run_batch's to
+ * rounding (summation orders differ with the padded size), within the solver's tolerance.
+ *   jobs, njobs, opts: as for nat_bem_run_batch (opts NULL = defaults; NAT_BEM_PREC_MIXED_TF32
+ *   solves a bucket in plain FP32: its products are matvecs, not GEMMs). max_batch: 1..256.
+ *   concurrency: 1..32 host workers, each with its own stream, take the buckets largest first
+ *   (then the jobs with several right-hand sides), so one bucket's mesh checks and assembly
+ *   overlap another's solve. Work starts after the caller's earlier work on cuda_stream; the
+ *   call returns when every job is done, with the statuses and device_ms (the device time of
+ *   the job's bucket, assembly to field) filled in.
+ * Returns as nat_bem_run_batch does. NAT_BEM_EINVAL: a bad argument (checked for every job
+ * before any work), opts out of range.
+ */
+NAT_BEM_API nat_bem_status nat_bem_run_batch_fused(nat_bem_job* jobs, int32_t njobs,
+                                                   const nat_bem_opts* opts, int32_t max_batch,
+                                                   int32_t concurrency, void* cuda_stream);
+
+/*
  * Far-field pattern, the leading term Phi_1 of the FFAT expansion |p(x)| = sum_i Phi_i(theta,
  * phi) / r^i (paper Sec. 3.1): for unit directions d_q,
  *   F(d) = lim_{r -> inf} r e^{-ikr} p(r d) = (1/4pi) int [ p (-i k d.n_y) - g ] e^{-ik d.y} dS_y,

@@ -38,7 +38,8 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_bem_server_destroy", "nat_bem_selftest_bounded_wait", "nat_bem_assemble_mc",
             "nat_bem_far_field", "nat_bem_sample_field", "nat_bem_gemv_variant", "nat_field_create",
             "nat_field_forward", "nat_field_destroy", "nat_bem_assemble_galerkin",
-            "nat_bem_op_neumann_size", "nat_bem_trace_durations", "nat_bem_poisson_sample"]
+            "nat_bem_op_neumann_size", "nat_bem_trace_durations", "nat_bem_poisson_sample",
+            "nat_bem_run_batch_fused"]
 ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
 GEMV_VARIANTS = 8
 
@@ -105,6 +106,8 @@ def lib():
         L.nat_bem_eval_noalloc.restype = ctypes.c_int
         L.nat_bem_run_batch.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Opts), i32, vp]
         L.nat_bem_run_batch.restype = ctypes.c_int
+        L.nat_bem_run_batch_fused.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Opts), i32, i32, vp]
+        L.nat_bem_run_batch_fused.restype = ctypes.c_int
         L.nat_bem_server_create.argtypes = [i64, ctypes.POINTER(Opts), i32, ctypes.POINTER(vp)]
         L.nat_bem_server_create.restype = ctypes.c_int
         L.nat_bem_submit.argtypes = [vp, ctypes.POINTER(Job), ctypes.POINTER(i64)]
@@ -452,6 +455,25 @@ def nat_bem_run_batch(jobs, opts: Opts | None = None, concurrency: int = 3, stre
                                  int(concurrency), _stream_of(jobs[0]["V"] if jobs else None, stream))
     res = [(outs[i][0], outs[i][1], arr[i].info, arr[i].status, arr[i].device_ms)
            for i in range(len(jobs))]
+    del keep
+    return st, res
+
+
+def nat_bem_run_batch_fused(jobs, opts: Opts | None = None, max_batch: int = 64, concurrency: int = 4,
+                            stream=None):
+    """Fused batch: meshes bucketed by size, each bucket solved in lockstep as one padded system
+    of independent operators (see include/nat_bem.h). Job dicts and results as for
+    nat_bem_run_batch."""
+    keep, outs = [], []
+    arr = (Job * len(jobs))()
+    for i, jd in enumerate(jobs):
+        job, p, f, k = _make_job(jd)
+        arr[i] = job
+        outs.append((p, f))
+        keep.append(k)
+    st = lib().nat_bem_run_batch_fused(arr, len(jobs), ctypes.byref(opts) if opts else None, int(max_batch),
+                                       int(concurrency), _stream_of(jobs[0]["V"] if jobs else None, stream))
+    res = [(outs[i][0], outs[i][1], arr[i].info, arr[i].status, arr[i].device_ms) for i in range(len(jobs))]
     del keep
     return st, res
 

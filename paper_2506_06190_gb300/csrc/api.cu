@@ -93,7 +93,7 @@ static nat_bem_status ensure_rules(int levels, int self_pts) {
   return NAT_BEM_OK;
 }
 
-static nat_bem_status check_opts(const nat_bem_opts& o) {
+nat_bem_status check_opts(const nat_bem_opts& o) {
   if (o.adj_subdiv_levels < 0 || o.adj_subdiv_levels > 3) {
     set_error("opts.adj_subdiv_levels must be in [0, 3]");
     return NAT_BEM_EINVAL;
@@ -177,6 +177,88 @@ int64_t nat_bem_required_bytes(int64_t nt, int32_t nrhs, const nat_bem_opts* opt
   return b;
 }
 
+}  // extern "C"
+
+namespace natbem {
+
+nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double k,
+                             const nat_bem_opts& o, cudaStream_t s, int64_t ld, float2* L, float2* R,
+                             uint32_t* Lb, nat_bem_op** out) {
+  *out = nullptr;
+  // host copies for the mesh checks and the near-pair list
+  const bool vdev = is_device_pointer(verts), tdev = is_device_pointer(tris);
+  std::vector<double> hV;
+  std::vector<int32_t> hT;
+  const double* V = verts;
+  const int32_t* T = tris;
+  if (vdev) {
+    hV.resize(3 * nv);
+    NB_TRY_CUDA(cudaMemcpyAsync(hV.data(), verts, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    V = hV.data();
+  }
+  if (tdev) {
+    hT.resize(3 * nt);
+    NB_TRY_CUDA(cudaMemcpyAsync(hT.data(), tris, 3 * nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    T = hT.data();
+  }
+  NB_TRY(validate_mesh_host(V, nv, T, nt));
+  std::vector<int2> near;
+  build_near_pairs(T, nv, nt, near);
+  NB_TRY(ensure_rules(o.adj_subdiv_levels, o.self_theta_pts));
+
+  nat_bem_op* op = new (std::nothrow) nat_bem_op();
+  if (!op) {
+    set_error("host allocation failed");
+    return NAT_BEM_ENOMEM;
+  }
+  op->n = nt;
+  op->k = k;
+  op->opts = o;
+  op->stream = s;
+  cudaGetDevice(&op->device);
+  op->geo.n = nt;
+  op->geo.ld = std::max<int64_t>(ld, round_up(nt, 32));
+  op->nn = nt;
+  op->ldr = op->geo.ld;
+  auto fail = [&](nat_bem_status st) {
+    nat_bem_destroy(op);
+    return st;
+  };
+  const double* dV = nullptr;
+  const int32_t* dT = nullptr;
+  double* tV = nullptr;
+  int32_t* tT = nullptr;
+  nat_bem_status st = to_device(verts, (size_t)(3 * nv), s, &dV, &tV);
+  if (st != NAT_BEM_OK) return fail(st);
+  st = to_device(tris, (size_t)(3 * nt), s, &dT, &tT);
+  if (st != NAT_BEM_OK) return fail(st);
+  st = geometry_build(op, dV, dT, nv, near, s);
+  dev_free(tV, s);
+  dev_free(tT, s);
+  if (st != NAT_BEM_OK) return fail(st);
+  if (L) {  // the caller's memory
+    op->views = true;
+    op->L = L;
+    op->R = R;
+    op->Lb = o.prec == NAT_BEM_PREC_MIXED_BF16 ? Lb : nullptr;
+  } else {
+    const size_t mat = (size_t)nt * (size_t)op->geo.ld;
+    if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
+    if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
+    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
+      return fail(st);
+  }
+  if ((st = assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
+  *out = op;
+  return NAT_BEM_OK;
+}
+
+}  // namespace natbem
+
+extern "C" {
+
 nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                                 double k, const nat_bem_opts* opts, void* cuda_stream,
                                 nat_bem_op** out) {
@@ -203,68 +285,8 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
     nat_bem_opts_default(&o);
     if (opts) o = *opts;
     NB_TRY(check_opts(o));
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    // host copies for the mesh checks and the near-pair list
-    const bool vdev = is_device_pointer(verts), tdev = is_device_pointer(tris);
-    std::vector<double> hV;
-    std::vector<int32_t> hT;
-    const double* V = verts;
-    const int32_t* T = tris;
-    if (vdev) {
-      hV.resize(3 * nv);
-      NB_TRY_CUDA(cudaMemcpyAsync(hV.data(), verts, 3 * nv * sizeof(double), cudaMemcpyDeviceToHost, s));
-      NB_TRY_CUDA(cudaStreamSynchronize(s));
-      V = hV.data();
-    }
-    if (tdev) {
-      hT.resize(3 * nt);
-      NB_TRY_CUDA(cudaMemcpyAsync(hT.data(), tris, 3 * nt * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-      NB_TRY_CUDA(cudaStreamSynchronize(s));
-      T = hT.data();
-    }
-    NB_TRY(validate_mesh_host(V, nv, T, nt));
-    std::vector<int2> near;
-    build_near_pairs(T, nv, nt, near);
-    NB_TRY(ensure_rules(o.adj_subdiv_levels, o.self_theta_pts));
-
-    nat_bem_op* op = new (std::nothrow) nat_bem_op();
-    if (!op) {
-      set_error("host allocation failed");
-      return NAT_BEM_ENOMEM;
-    }
-    op->n = nt;
-    op->k = k;
-    op->opts = o;
-    op->stream = s;
-    cudaGetDevice(&op->device);
-    op->geo.n = nt;
-    op->geo.ld = round_up(nt, 32);
-    op->nn = nt;
-    op->ldr = op->geo.ld;
-    auto fail = [&](nat_bem_status st) {
-      nat_bem_destroy(op);
-      return st;
-    };
-    const double* dV = nullptr;
-    const int32_t* dT = nullptr;
-    double* tV = nullptr;
-    int32_t* tT = nullptr;
-    nat_bem_status st = to_device(verts, (size_t)(3 * nv), s, &dV, &tV);
-    if (st != NAT_BEM_OK) return fail(st);
-    st = to_device(tris, (size_t)(3 * nt), s, &dT, &tT);
-    if (st != NAT_BEM_OK) return fail(st);
-    st = geometry_build(op, dV, dT, nv, near, s);
-    dev_free(tV, s);
-    dev_free(tT, s);
-    if (st != NAT_BEM_OK) return fail(st);
-    const size_t mat = (size_t)nt * (size_t)op->geo.ld;
-    if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
-    if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
-    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
-      return fail(st);
-    if ((st = assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
-    *out = op;
-    return NAT_BEM_OK;
+    return build_mesh_op(verts, nv, tris, nt, k, o, (cudaStream_t)cuda_stream, 0, nullptr, nullptr,
+                         nullptr, out);
   } catch (...) {
     set_error("internal error in nat_bem_assemble");
     return NAT_BEM_ECUDA;
@@ -741,9 +763,14 @@ void nat_bem_destroy(nat_bem_op* op) {
   if (!op) return;
   cudaStream_t s = op->stream;
   Geometry& g = op->geo;
-  void* ptrs[] = {g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, g.tri, g.cen, g.nrm64, g.area,
-                  g.near_pairs, op->L, op->R, op->Lb};
-  for (void* p : ptrs) dev_free(p, s);
+  if (!op->geo_view) {
+    void* gp[] = {g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, g.tri, g.cen, g.nrm64, g.area, g.near_pairs};
+    for (void* p : gp) dev_free(p, s);
+  }
+  if (!op->views) {
+    void* mp[] = {op->L, op->R, op->Lb};
+    for (void* p : mp) dev_free(p, s);
+  }
   galerkin_free(op, s);
   workspace_free(op->ws, s);
   delete op;

@@ -216,10 +216,11 @@ template <int kRows, int kUnroll>
 __global__ void __launch_bounds__(256)
 k_gemv(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x, int64_t xstride,
        double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
-       const int* __restrict__ scal) {
+       const int* __restrict__ scal, int64_t astride) {
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
+  A += (size_t)s * astride;  // a batch of operators: one per right-hand side
   const int row0 = blockIdx.x * kRows;
   const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
   const float4* a[kRows];
@@ -263,11 +264,12 @@ template <int kRows, int kUnroll>
 __global__ void __launch_bounds__(256)
 k_gemv_xs(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x, int64_t xstride,
           double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
-          const int* __restrict__ scal) {
+          const int* __restrict__ scal, int64_t astride) {
   extern __shared__ float4 s_x[];
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
+  A += (size_t)s * astride;
   const int n4 = ld >> 1;
   const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
   for (int i = threadIdx.x; i < n4; i += 256) s_x[i] = __ldg(xv + i);
@@ -314,10 +316,11 @@ template <int kRows, int kUnroll>
 __global__ void __launch_bounds__(256)
 k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
             int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
-            const int* __restrict__ scal) {
+            const int* __restrict__ scal, int64_t astride) {
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
+  A += (size_t)s * astride;
   const int row0 = blockIdx.x * kRows;
   const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
   const uint4* a[kRows];
@@ -398,7 +401,7 @@ template <int kStages, int kSeg>
 __global__ void __launch_bounds__(288)
 k_gemv_bulk(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ x,
             int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
-            const int* __restrict__ scal, int rows_per_block, int* __restrict__ err) {
+            const int* __restrict__ scal, int rows_per_block, int* __restrict__ err, int64_t astride) {
   extern __shared__ __align__(128) float4 ring_raw[];  // kStages x kSeg bytes (dynamic)
   float4 (*ring)[kSeg / 16] = reinterpret_cast<float4 (*)[kSeg / 16]>(ring_raw);
   __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
@@ -407,6 +410,7 @@ k_gemv_bulk(const float2* __restrict__ A, int n, int ld, const float2* __restric
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
+  A += (size_t)s * astride;
   const int row_begin = blockIdx.x * rows_per_block;
   const int row_end = min(n, row_begin + rows_per_block);
   if (row_begin >= row_end) return;
@@ -1613,19 +1617,19 @@ static int gemv_xs_blocks(int ld, int sms) {
 
 static nat_bem_status gemv_launch(int variant, const char* name, const float2* A, int n, int ld,
                                   const float2* x, double2* y, int nrhs, const int* done,
-                                  const int* scal, int* err, cudaStream_t s) {
+                                  const int* scal, int* err, cudaStream_t s, int64_t astride = 0) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   switch (variant) {
     case kGemvR4U4: {
       dim3 grid((n + 3) / 4, nrhs);
-      NB_LAUNCH(name, s, k_gemv<4, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv<4, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     }
     case kGemvR2U8: {
       dim3 grid((n + 1) / 2, nrhs);
-      NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     }
     case kGemvBulk4x16k:
@@ -1640,9 +1644,9 @@ static nat_bem_status gemv_launch(int variant, const char* name, const float2* A
         attr = true;
       }
       if (variant == kGemvBulk4x16k)
-        NB_LAUNCH(name, s, k_gemv_bulk<4, 16384><<<grid, 288, 4 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
+        NB_LAUNCH(name, s, k_gemv_bulk<4, 16384><<<grid, 288, 4 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err, astride));
       else
-        NB_LAUNCH(name, s, k_gemv_bulk<6, 16384><<<grid, 288, 6 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err));
+        NB_LAUNCH(name, s, k_gemv_bulk<6, 16384><<<grid, 288, 6 * 16384, s>>>(A, n, ld, x, ld, y, n, done, scal, rpb, err, astride));
       break;
     }
     case kGemvXsR2U8:
@@ -1654,22 +1658,22 @@ static nat_bem_status gemv_launch(int variant, const char* name, const float2* A
                  : variant == kGemvXsR4U4 ? gemv_xs_blocks<4, 4>(ld, sms) : gemv_xs_blocks<2, 4>(ld, sms);
       if (smem > (size_t)kGemvXsMaxBytes || blocks <= 0) {  // x does not fit: plain variant
         dim3 grid((n + 1) / 2, nrhs);
-        NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+        NB_LAUNCH(name, s, k_gemv<2, 8><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
         break;
       }
       blocks = std::min(blocks, (n + rows - 1) / rows);
       dim3 grid(blocks, nrhs);
       if (variant == kGemvXsR2U8)
-        NB_LAUNCH(name, s, k_gemv_xs<2, 8><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
+        NB_LAUNCH(name, s, k_gemv_xs<2, 8><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       else if (variant == kGemvXsR4U4)
-        NB_LAUNCH(name, s, k_gemv_xs<4, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
+        NB_LAUNCH(name, s, k_gemv_xs<4, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       else
-        NB_LAUNCH(name, s, k_gemv_xs<2, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal));
+        NB_LAUNCH(name, s, k_gemv_xs<2, 4><<<grid, 256, smem, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     }
     default: {
       dim3 grid((n + 1) / 2, nrhs);
-      NB_LAUNCH(name, s, k_gemv<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
     }
   }
   NB_CHECK_LAUNCH();
@@ -1747,12 +1751,12 @@ int gemv_tuned_variant(int64_t n) {
 // y_s = A x_s for all RHS (x padded to ld), skipping RHS flagged done when `done` is given.
 static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, const float2* x,
                            double2* y, int nrhs, const int* done, const int* scal, cudaStream_t s,
-                           int* err = nullptr) {
+                           int* err = nullptr, int64_t astride = 0) {
   int* e = err ? err : nullptr;
   int variant = kGemvR2U4;
   if (e) variant = gemv_variant(A, n, ld, x, y, e, s);
   if (!e && (variant == kGemvBulk4x16k || variant == kGemvBulk6x16k)) variant = kGemvR2U4;
-  return gemv_launch(variant, name, A, n, ld, x, y, nrhs, done, scal, e, s);
+  return gemv_launch(variant, name, A, n, ld, x, y, nrhs, done, scal, e, s, astride);
 }
 
 // BF16-copy GEMV variants (rows per block, 16-byte loads per row in flight per thread) and
@@ -1762,21 +1766,21 @@ enum Bf16Variant { kBf16R2U2 = 0, kBf16R2U4, kBf16R4U2, kBf16R4U1, kBf16Variants
 
 static nat_bem_status gemv_bf16_launch(int variant, const char* name, const uint32_t* A, int n, int ld,
                                        const float2* x, double2* y, int nrhs, const int* done,
-                                       const int* scal, cudaStream_t s) {
+                                       const int* scal, cudaStream_t s, int64_t astride = 0) {
   const int rows = (variant == kBf16R4U2 || variant == kBf16R4U1) ? 4 : 2;
   dim3 grid((n + rows - 1) / rows, nrhs);
   switch (variant) {
     case kBf16R2U4:
-      NB_LAUNCH(name, s, k_gemv_bf16<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv_bf16<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     case kBf16R4U2:
-      NB_LAUNCH(name, s, k_gemv_bf16<4, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv_bf16<4, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     case kBf16R4U1:
-      NB_LAUNCH(name, s, k_gemv_bf16<4, 1><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv_bf16<4, 1><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
       break;
     default:
-      NB_LAUNCH(name, s, k_gemv_bf16<2, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal));
+      NB_LAUNCH(name, s, k_gemv_bf16<2, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
   }
   NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
@@ -1836,8 +1840,8 @@ static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, do
 
 static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int ld,
                                 const float2* x, double2* y, int nrhs, const int* done,
-                                const int* scal, cudaStream_t s) {
-  return gemv_bf16_launch(gemv_bf16_lookup(n), name, A, n, ld, x, y, nrhs, done, scal, s);
+                                const int* scal, cudaStream_t s, int64_t astride = 0) {
+  return gemv_bf16_launch(gemv_bf16_lookup(n), name, A, n, ld, x, y, nrhs, done, scal, s, astride);
 }
 
 // One GMRES run on the right-hand sides in a.b (x0 = 0): init, iterations until every RHS
@@ -1850,9 +1854,9 @@ static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engin
   const float2* M = which == 0 ? op->L : op->R;
   switch (engine) {
     case kEngineGemv:
-      return gemv(name, M, n, ld, ws->xf, y, nrhs, done, scal, s, ws->tc_err);
+      return gemv(name, M, n, ld, ws->xf, y, nrhs, done, scal, s, ws->tc_err, op->bstride);
     case kEngineGemvBf16:
-      return gemv_bf16(name, op->Lb, n, ld, ws->xf, y, nrhs, done, scal, s);
+      return gemv_bf16(name, op->Lb, n, ld, ws->xf, y, nrhs, done, scal, s, op->bstride);
     default:
       return product(op, which, engine, ws->xf, nrhs, y, done, scal, ws->tc_scratch, ws->tc_bytes,
                      ws->tc_err, s);
@@ -1913,7 +1917,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
                                        (a.skip ? 1 : 0) + (accumulate ? 2 : 0) + (a.bscale ? 4 : 0));
       auto f = ws->graphs.find(key);
       if (f == ws->graphs.end()) {
-        const int64_t l0 = launch_count();
+        const int64_t l0 = thread_launch_count();  // other threads' launches are not captured
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
@@ -1921,7 +1925,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
         ok = (cudaStreamEndCapture(s, &g) == cudaSuccess) && ok && cs == NAT_BEM_OK;
         if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
-        const int64_t captured = launch_count() - l0;
+        const int64_t captured = thread_launch_count() - l0;
         add_launches(-captured);  // capturing launches nothing
         if (ok) {
           f = ws->graphs.emplace(key, std::make_pair(ge, captured)).first;
@@ -2023,7 +2027,8 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
 }
 
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
-                          nat_bem_solve_info* info, cudaStream_t s) {
+                          nat_bem_solve_info* info, cudaStream_t s, std::vector<nat_bem_solve_info>* per_rhs,
+                          std::vector<int>* per_conv) {
   NB_TRY(workspace_ensure(op, nrhs, s));
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
@@ -2038,23 +2043,26 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     const int64_t tot = (int64_t)ldr * nrhs;
     NB_LAUNCH("pad_copy", s, k_pad_copy<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d_neumann, nn, ldr, nrhs, ws->gin));
     NB_CHECK_LAUNCH();
-    if (nrhs == 1)
-      NB_TRY(gemv("gemv_rhs", op->R, n, ldr, ws->gin, ws->b, nrhs, nullptr, nullptr, s, ws->tc_err));
+    if (nrhs == 1 || op->bstride > 0)  // one RHS, or a batch of operators (one per RHS)
+      NB_TRY(gemv("gemv_rhs", op->R, n, ldr, ws->gin, ws->b, nrhs, nullptr, nullptr, s, ws->tc_err, op->bstride));
     else
       NB_TRY(product(op, 1, kEngineFp32, ws->gin, nrhs, ws->b, nullptr, nullptr, ws->tc_scratch,
                      ws->tc_bytes, ws->tc_err, s));
   }
-  std::vector<int> iters(nrhs), done(nrhs), total(nrhs, 0);
+  std::vector<int> iters(nrhs), done(nrhs), total(nrhs, 0), conv(nrhs, 0);
   std::vector<double> rt(nrhs);
   int refinements = 0;
   bool converged = true;
   // engines: the accurate product (FP32 GEMV for one RHS, FP32 CUDA-core GEMM for several) and
   // the inner product of mixed refinement (BF16 GEMV for one RHS; tensor cores for several:
   // TF32 on L or BF16 on its copy). TF32 with one RHS would save no bytes: it runs plain.
-  const int accurate = nrhs == 1 ? kEngineGemv : kEngineFp32;
+  // A batch of operators (one per RHS, bstride > 0) runs GEMVs throughout: the products of
+  // different operators are not one GEMM.
+  const bool gemv_path = nrhs == 1 || op->bstride > 0;
+  const int accurate = gemv_path ? kEngineGemv : kEngineFp32;
   int inner = accurate;
-  if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = nrhs == 1 ? kEngineGemvBf16 : kEngineBf16;
-  if (o.prec == NAT_BEM_PREC_MIXED_TF32 && nrhs > 1) inner = kEngineTf32;
+  if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = gemv_path ? kEngineGemvBf16 : kEngineBf16;
+  if (o.prec == NAT_BEM_PREC_MIXED_TF32 && !gemv_path) inner = kEngineTf32;
   const bool mixed = inner != accurate;
   // GMRES(m): the Krylov basis holds m = restart vectors and the solve runs cycles of at most
   // m iterations, each on the current residual
@@ -2076,6 +2084,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     NB_TRY_CUDA(cudaStreamSynchronize(s));
     for (int q = 0; q < nrhs; ++q) {
       total[q] = iters[q];
+      conv[q] = done[q];
       converged = converged && done[q];
     }
   } else {
@@ -2117,7 +2126,10 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       budget -= std::max(used, 1);
       ++refinements;
       converged = true;
-      for (int q = 0; q < nrhs; ++q) converged = converged && od[q];
+      for (int q = 0; q < nrhs; ++q) {
+        conv[q] = od[q];
+        converged = converged && od[q];
+      }
       return NAT_BEM_OK;
     };
     bool finish = !mixed;
@@ -2155,7 +2167,10 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
         a.maxit = std::min(budget, ws->m);
         NB_TRY(sweep_once(accurate));
         converged = true;
-        for (int q = 0; q < nrhs; ++q) converged = converged && (od[q] || inner_done[q]);
+        for (int q = 0; q < nrhs; ++q) {
+          conv[q] = od[q] || inner_done[q];
+          converged = converged && conv[q];
+        }
         if (converged) break;
       }
     }
@@ -2178,6 +2193,11 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     info->refinements = refinements;
     info->rel_residual = maxres;
   }
+  if (per_rhs) {
+    per_rhs->resize(nrhs);
+    for (int q = 0; q < nrhs; ++q) (*per_rhs)[q] = nat_bem_solve_info{total[q], refinements, rt[q]};
+  }
+  if (per_conv) *per_conv = conv;
   if (!converged) {
     set_error("GMRES did not reach the tolerance within the iteration limits");
     return NAT_BEM_ENOCONV;

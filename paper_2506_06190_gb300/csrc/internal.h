@@ -53,6 +53,7 @@ class TraceScope {
 
 bool tracing_enabled();
 int64_t launch_count();
+int64_t thread_launch_count();  // launches from the calling thread only
 void add_launches(int64_t n);  // kernels launched through a replayed CUDA graph
 
 #define NB_LAUNCH(name, stream, ...)            \
@@ -146,6 +147,10 @@ struct nat_bem_op {
   float2* L = nullptr;                 // n x ld complex64, row-major
   float2* R = nullptr;                 // n x ld complex64, row-major (store_r)
   uint32_t* Lb = nullptr;              // n x ld complex as packed bf16 pairs (mixed BF16)
+  bool views = false;                  // L, R and Lb belong to someone else (not freed here)
+  bool geo_view = false;               // geo belongs to another op of the same mesh
+  int64_t bstride = 0;                 // > 0: a batch of operators, RHS s uses L + s bstride
+                                       // (and R, Lb likewise); 0: one operator for every RHS
   natbem::Workspace* ws = nullptr;     // solver workspace, grown on demand
   bool mc = false;                     // Monte-Carlo op (nat_bem_assemble_mc): n samples
   double mc_area = 0.0;                // Monte-Carlo op: total surface area
@@ -156,6 +161,14 @@ struct nat_bem_op {
 };
 
 namespace natbem {
+
+// api.cu: a mesh op as nat_bem_assemble builds it, with leading dimension ld (>= nt rounded up
+// to 32) and, when L is given, its operators written into the caller's memory (views: L, R and,
+// for mixed BF16, Lb of nt x ld each) instead of owned allocations.
+nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double k,
+                             const nat_bem_opts& o, cudaStream_t s, int64_t ld, float2* L, float2* R,
+                             uint32_t* Lb, nat_bem_op** out);
+nat_bem_status check_opts(const nat_bem_opts& o);
 
 // assemble.cu
 nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
@@ -175,8 +188,12 @@ nat_bem_status galerkin_expand(const nat_bem_op* op, const float2* d_p, const fl
 void galerkin_free(nat_bem_op* op, cudaStream_t s);
 
 // gmres.cu
+// per_rhs / per_conv (may be null): each RHS's iterations and true residual, and whether it
+// met the tolerance.
 nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, float2* d_p,
-                          nat_bem_solve_info* info, cudaStream_t s);
+                          nat_bem_solve_info* info, cudaStream_t s,
+                          std::vector<nat_bem_solve_info>* per_rhs = nullptr,
+                          std::vector<int>* per_conv = nullptr);
 void workspace_free(Workspace* ws, cudaStream_t s);
 nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d_x, int nrhs,
                           float2* d_y, cudaStream_t s);

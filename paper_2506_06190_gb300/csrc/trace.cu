@@ -12,6 +12,7 @@ namespace natbem {
 
 namespace {
 std::atomic<int64_t> g_launches{0};
+thread_local int64_t t_launches = 0;  // this thread's launches (graph capture is per thread)
 std::atomic<int> g_trace{0};
 std::mutex g_mu;
 struct Rec {
@@ -43,6 +44,7 @@ cudaEvent_t get_event() {
 
 TraceScope::TraceScope(const char* name, cudaStream_t s) : name_(name), s_(s) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
   if (g_trace.load(std::memory_order_relaxed)) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!selected(name)) return;
@@ -62,7 +64,11 @@ TraceScope::~TraceScope() {
 
 bool tracing_enabled() { return g_trace.load(std::memory_order_relaxed) != 0; }
 int64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
-void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t thread_launch_count() { return t_launches; }
+void add_launches(int64_t n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 
 }  // namespace natbem
 

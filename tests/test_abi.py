@@ -153,6 +153,31 @@ def test_solve_and_eval_reject_null(nb):
     L.nat_bem_destroy(None)
 
 
+def test_run_batch_fused_rejects_bad_arguments(nb):
+    """Argument checks of the fused batch happen for every job before any device work."""
+    L = nb.lib()
+    V, F = S.icosphere(1)
+    g = S.uniform_neumann(F).astype(np.complex64)
+    p = np.zeros(len(F), np.complex64)
+    job = nb.Job(ctypes.c_void_p(V.ctypes.data), len(V), ctypes.c_void_p(F.ctypes.data), len(F), 2.0,
+                 ctypes.c_void_p(g.ctypes.data), 1, None, 0, ctypes.c_void_p(p.ctypes.data), None,
+                 nb.SolveInfo(), 0, 0.0)
+    arr = (nb.Job * 2)(job, job)
+    assert L.nat_bem_run_batch_fused(arr, 2, None, 0, 2, None) == nb.NAT_BEM_EINVAL      # max_batch
+    assert L.nat_bem_run_batch_fused(arr, 2, None, 257, 2, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_run_batch_fused(arr, 2, None, 4, 0, None) == nb.NAT_BEM_EINVAL     # concurrency
+    assert L.nat_bem_run_batch_fused(None, 1, None, 4, 2, None) == nb.NAT_BEM_EINVAL
+    arr[1].k = 0.0                                                                     # a bad job
+    assert L.nat_bem_run_batch_fused(arr, 2, None, 4, 2, None) == nb.NAT_BEM_EINVAL
+    assert "job 1" in nb.nat_bem_last_error()
+    arr[1].k = 2.0
+    arr[1].m = 5                                                                       # points missing
+    assert L.nat_bem_run_batch_fused(arr, 2, None, 4, 2, None) == nb.NAT_BEM_EINVAL
+    bad = nb.nat_bem_opts_default(restart=-1)
+    assert L.nat_bem_run_batch_fused(arr, 1, ctypes.byref(bad), 4, 2, None) == nb.NAT_BEM_EINVAL
+    assert L.nat_bem_run_batch_fused(arr, 0, None, 4, 2, None) == nb.NAT_BEM_OK
+
+
 def test_nat_field_rejects_bad_arguments(nb):
     """Host-side checks of the neural-field entry points (before any device call)."""
     L = nb.lib()
