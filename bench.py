@@ -924,26 +924,39 @@ def run_serving(args):
                                  points=pts), nrhs))
     torch.cuda.synchronize()
     budget = int(args.budget_gb * (1 << 30))
-    with nb.Server(budget, opts, slots=args.concurrency) as srv:
-        t_start = time.perf_counter()
-        tickets = []
-        for t_arr, jd, nrhs in reqs:
-            while time.perf_counter() - t_start < t_arr:
-                time.sleep(0.0005)
-            tickets.append((srv.submit(jd), nrhs))
-        res = [(srv.wait(t, -1), nrhs) for t, nrhs in tickets]
-        t_end = time.perf_counter()
+
+    def serve(opts_):
+        with nb.Server(budget, opts_, slots=args.concurrency) as srv:
+            tickets = []
+            t_start = time.perf_counter()
+            for t_arr, jd, nrhs in reqs:
+                while time.perf_counter() - t_start < t_arr:
+                    time.sleep(0.0005)
+                tickets.append((srv.submit(jd), nrhs))
+            res = [(srv.wait(t, -1), nrhs) for t, nrhs in tickets]
+            t_end = time.perf_counter()
+        return res, t_end - t_start
+
+    res, dt = serve(opts)
     lat = [r[0][6] for r in res]
     solves = sum(nrhs for r, nrhs in res if r[0] == 0)
-    return {"metric": METRIC, "value": solves / (t_end - t_start), "unit": UNIT, "n_gpus": 1,
-            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * (t_end - t_start), "higher_is_better": True,
+    line = {"metric": METRIC, "value": solves / dt, "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": 1e3 * dt, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": f"serving_poisson_{args.rate}per_s_{args.n_req}req", "budget_gb": args.budget_gb,
                        "slots": args.concurrency, "offered_rate_req_s": args.rate},
-            "requests_per_s": len(res) / (t_end - t_start),
+            "requests_per_s": len(res) / dt,
             "latency_ms": dict(_percentiles(lat), per="request, submit to completion (queueing included)"),
             "queue_ms": _percentiles([r[0][5] for r in res]),
             "statuses": {str(k): int(v) for k, v in zip(*np.unique([r[0][0] for r in res], return_counts=True))}}
+    if args.prec != "fp32":
+        res_p, dt_p = serve(nb.nat_bem_opts_default(prec=nb.PREC_FP32))
+        lat_p = [r[0][6] for r in res_p]
+        line["plain_fp32"] = {"value": sum(nrhs for r, nrhs in res_p if r[0] == 0) / dt_p, "unit": UNIT,
+                              "requests_per_s": len(res_p) / dt_p, "latency_ms": _percentiles(lat_p),
+                              "statuses": {str(k): int(v) for k, v in
+                                           zip(*np.unique([r[0][0] for r in res_p], return_counts=True))}}
+    return line
 
 
 def roofline(res, peaks, peak_kind):
@@ -1028,6 +1041,30 @@ def cpu_baseline(prob, nthreads: int):
     return p, fld, dt, info
 
 
+def run_extras(args):
+    """The other workloads in short form (one warm-up and one timed step each), summarised under
+    "workloads" in the headline's line: the multi-RHS modal products, the uneven batch (fused
+    buckets beside the worker pool) and the serving stream (mixed beside plain FP32)."""
+    out = {}
+    base = dict(vars(args), steps=1, warmup=1, n_k=16, n_tri=20480, nrhs=64, prec="bf16", cpu=False,
+                inner_tol=args.inner_tol)
+    keep = ("value", "unit", "ms_per_step", "config", "latency_ms", "gpu_launches", "not_converged",
+            "worker_pool", "plain_fp32", "requests_per_s", "statuses", "gmres", "rel_err_vs_oracle")
+    for name, fn, over in (("modal", run_modal, {}),
+                           ("uneven", run_uneven, dict(n_k=64, n_tri=10240, cpu=args.cpu)),
+                           ("serve", run_serving, dict(concurrency=4))):
+        try:
+            r = fn(argparse.Namespace(**dict(base, **over)))
+            d = {k: r[k] for k in keep if k in r}
+            if r.get("roofline"):
+                d["roofline"] = {k: r["roofline"][k] for k in ("kernel", "achieved", "peak", "unit", "frac", "traffic")
+                                 if k in r["roofline"]}
+            out[name] = d
+        except Exception as e:  # report, do not lose the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1059,6 +1096,8 @@ def main():
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: tolerance of each inner solve (default: the library's)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="interior workload: skip the short modal, uneven-batch and serving runs")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args()
     if args.prec is None:
@@ -1204,6 +1243,8 @@ def main():
                                                 "surface and field; oracle GMRES to 1e-10",
                                      "per_k": per_k,
                                      "first_k": {"surface": ep, "field": ef, "k": float(prob.ks[0])}}
+    if args.extras and world == 1:
+        line["workloads"] = run_extras(args)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -83,6 +83,11 @@ typedef struct {
                              /* 16 nt nrhs (max_iter + 1): the lever for serving memory          */
   int32_t quad_regular;      /* points of the rule on pairs sharing no vertex: 7 (Radon's degree- */
                              /* 5 rule) is the only value (7)                                      */
+  int32_t device_loop;       /* 1: each GMRES run goes to convergence on the device (a CUDA graph */
+                             /* whose conditional loop repeats captured iterations), so a plain  */
+                             /* solve makes one host sync; 0: chunks of iterations with a host    */
+                             /* check after each (1). The batch driver and the server use 0 when  */
+                             /* they run several workers (other streams fill those gaps)          */
 } nat_bem_opts;
 
 typedef struct nat_bem_op nat_bem_op; /* opaque */

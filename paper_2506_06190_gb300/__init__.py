@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("inner_max_iter", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("max_refinements", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("quad_regular", ctypes.c_int32)]
+                ("quad_regular", ctypes.c_int32), ("device_loop", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

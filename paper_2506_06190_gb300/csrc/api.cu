@@ -114,6 +114,10 @@ nat_bem_status check_opts(const nat_bem_opts& o) {
     set_error("opts.max_iter must be in [1, 255] (unrestarted) or [1, 100000] (restart > 0)");
     return NAT_BEM_EINVAL;
   }
+  if (o.device_loop != 0 && o.device_loop != 1) {
+    set_error("opts.device_loop must be 0 or 1");
+    return NAT_BEM_EINVAL;
+  }
   if (o.quad_regular != 7) {
     set_error("opts.quad_regular must be 7 (the 7-point degree-5 rule is the only regular rule)");
     return NAT_BEM_EINVAL;
@@ -156,6 +160,7 @@ void nat_bem_opts_default(nat_bem_opts* o) {
   o->max_refinements = 10;
   o->restart = 0;
   o->quad_regular = 7;
+  o->device_loop = 1;
 }
 
 const char* nat_bem_last_error(void) { return g_last_error.c_str(); }

@@ -720,19 +720,26 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
         n, g.tri, g.cen, ld, op->k, op->L, op->R, op->Lb));
     NB_CHECK_LAUNCH();
   }
-  // regular pairs: columns in blocks of 256, rows split so the grid holds a few waves
+  // regular pairs: columns in blocks of 256 (two columns a thread in the paired form), rows
+  // split in blocks of rows_per_block. Every entry is computed the same way whatever the split,
+  // so the autotuner (rows per block 64, 32, 128 or 16, per size class) changes no result.
   const int col_blocks = (ld + kRegThreads - 1) / kRegThreads;
-  const int rows_per_block = 64;
-  const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
-  dim3 grid(col_blocks, row_blocks);
   static const bool scalar = std::getenv("NATBEM_ASSEMBLY_SCALAR") != nullptr;
-  if (scalar)
-    NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
-        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
-  else
-    NB_LAUNCH("assemble_regular", s, k_assemble_regular_x2<<<grid, kX2Threads, 0, s>>>(
-        g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
-  NB_CHECK_LAUNCH();
+  auto launch = [&](int rows_per_block) -> nat_bem_status {
+    const int row_blocks = (n + rows_per_block - 1) / rows_per_block;
+    dim3 grid(col_blocks, row_blocks);
+    if (scalar)
+      NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
+          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+    else
+      NB_LAUNCH("assemble_regular", s, k_assemble_regular_x2<<<grid, kX2Threads, 0, s>>>(
+          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+    NB_CHECK_LAUNCH();
+    return NAT_BEM_OK;
+  };
+  static const int kRows[4] = {64, 32, 128, 16};
+  const int pick = autotune("assemble_rows", (n + 1023) / 1024, 4, [&](int c) { return launch(kRows[c]); }, s);
+  NB_TRY(launch(kRows[pick]));
   return NAT_BEM_OK;
 }
 

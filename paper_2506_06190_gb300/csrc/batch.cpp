@@ -70,6 +70,12 @@ extern "C" nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
         return NAT_BEM_ECUDA;
       }
     }
+    // with several workers, other streams fill the host round trips between GMRES chunks, and
+    // the device-side loop measured slower there: host-polled chunks
+    nat_bem_opts wo;
+    nat_bem_opts_default(&wo);
+    if (opts) wo = *opts;
+    if (nw > 1) wo.device_loop = 0;
     std::atomic<int32_t> next{0};
     std::mutex err_mu;
     std::string first_error;
@@ -87,7 +93,7 @@ extern "C" nat_bem_status nat_bem_run_batch(nat_bem_job* jobs, int32_t njobs,
         } else {
           nat_bem_destroy(w.op);
           w.op = nullptr;
-          st = nat_bem_assemble(j.verts, j.nv, j.tris, j.nt, j.k, opts, w.stream, &w.op);
+          st = nat_bem_assemble(j.verts, j.nv, j.tris, j.nt, j.k, &wo, w.stream, &w.op);
           if (st == NAT_BEM_OK) {
             w.verts = j.verts;
             w.tris = j.tris;

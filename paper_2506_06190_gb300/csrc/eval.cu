@@ -294,28 +294,44 @@ static nat_bem_status eval_core(const nat_bem_op* op, const double* d_pts, int64
   const EvalSource src = eval_source(op);
   const int n = src.n;
   const int pblocks = (int)((m + kEvalThreads - 1) / kEvalThreads);
-  // split the elements so that the grid holds about four blocks per SM
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int splits = (4 * sms + pblocks - 1) / pblocks;
-  splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
-  int per = (n + splits - 1) / splits;
-  per = (per + kElemStage - 1) / kElemStage * kElemStage;
-  splits = (n + per - 1) / per;
+  // split the elements so that the grid holds about `bps` blocks per SM; the autotuner picks
+  // bps among 4 (the default), 2, 8 and 16 per size class (elements, points, RHS pass)
+  auto split_of = [&](int bps, int* per_out) {
+    int splits = (bps * sms + pblocks - 1) / pblocks;
+    splits = max(1, min(splits, (n + kElemStage - 1) / kElemStage));
+    int per = (n + splits - 1) / splits;
+    per = (per + kElemStage - 1) / kElemStage * kElemStage;
+    *per_out = per;
+    return (n + per - 1) / per;
+  };
+  static const int kBps[4] = {4, 2, 8, 16};
+  int max_splits = 1, per = 0;
+  for (int c = 0; c < 4; ++c) max_splits = max(max_splits, split_of(kBps[c], &per));
   double2* part = nullptr;
-  NB_TRY(dev_alloc_n(&part, (size_t)splits * m * pass_width(min(kMaxRhsPass, nrhs)), s));
-  for (int r0 = 0; r0 < nrhs; r0 += kMaxRhsPass) {
-    const int nr = min(kMaxRhsPass, nrhs - r0);
+  NB_TRY(dev_alloc_n(&part, (size_t)max_splits * m * pass_width(min(kMaxRhsPass, nrhs)), s));
+  auto run = [&](int bps, int r0, int nr) -> nat_bem_status {
+    int per_c = 0;
+    const int splits = split_of(bps, &per_c);
     dim3 grid(pblocks, splits);
-    NB_LAUNCH("eval", s, eval_launch(src, (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
+    NB_LAUNCH("eval", s, eval_launch(src, (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per_c, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
     NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
-  }
+    return NAT_BEM_OK;
+  };
+  const int nr0 = min(kMaxRhsPass, nrhs);
+  const int64_t cls = ((int64_t)((n + 1023) / 1024) << 32) | ((int64_t)((m + 255) / 256) << 8) |
+                      (int64_t)pass_width(nr0) | (src.one_point ? 128 : 0);
+  const int pick = autotune("eval_bps", cls, 4, [&](int c) { return run(kBps[c], 0, nr0); }, s);
+  nat_bem_status st = NAT_BEM_OK;
+  for (int r0 = 0; r0 < nrhs && st == NAT_BEM_OK; r0 += kMaxRhsPass)
+    st = run(kBps[pick], r0, min(kMaxRhsPass, nrhs - r0));
   dev_free(part, s);
-  return NAT_BEM_OK;
+  return st;
 }
 
 template <int NQ>

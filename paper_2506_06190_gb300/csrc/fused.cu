@@ -235,6 +235,7 @@ extern "C" nat_bem_status nat_bem_run_batch_fused(nat_bem_job* jobs, int32_t njo
     nat_bem_opts_default(&o);
     if (opts) o = *opts;
     NB_TRY(check_opts(o));
+    if (concurrency > 1) o.device_loop = 0;  // other workers' streams fill the host round trips
     for (int32_t i = 0; i < njobs; ++i) {
       const nat_bem_job& j = jobs[i];
       if (!j.verts || !j.tris || j.nv <= 0 || j.nt <= 0 || j.nt > (1 << 30) || j.nrhs < 1 || !j.neumann ||

@@ -61,6 +61,12 @@ struct Workspace {
   // 1 skip flags, 2 accumulate, 4 tolerance relative to ||R g||)
   std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
+  // whole GMRES runs on the device: a graph whose conditional while node repeats a captured
+  // chunk of iterations until every RHS is done; key (engine, cap, tol, mode bits)
+  std::map<std::tuple<int, int, double, int>, cudaGraphExec_t> loops;
+  bool loops_off = false;
+  unsigned long long* loop_launches = nullptr;  // kernels the loop bodies ran (device counter)
+  unsigned long long* host_loop = nullptr;      // pinned mirror, read at host sync points
   void* tc_scratch = nullptr;                              // packed B + split-K partials
   size_t tc_bytes = 0;
   int* tc_err = nullptr;                                   // bounded-wait failures
@@ -1440,6 +1446,9 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
   for (auto& kv : ws->graphs) cudaGraphExecDestroy(kv.second.first);
+  for (auto& kv : ws->loops) cudaGraphExecDestroy(kv.second);
+  if (ws->loop_launches) dev_free(ws->loop_launches, s);
+  if (ws->host_loop) cudaFreeHost(ws->host_loop);
   delete ws;
 }
 
@@ -1490,6 +1499,8 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->outer_done, nr, s));
   NB_TRY(dev_alloc_n(&ws->tc_err, 1, s));
   NB_TRY(dev_alloc_n(&ws->gbar, 2, s));
+  NB_TRY(dev_alloc_n(&ws->loop_launches, 1, s));
+  NB_TRY_CUDA(cudaMemsetAsync(ws->loop_launches, 0, sizeof(unsigned long long), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
   {
     // the fused Arnoldi kernel runs one block per SM when every block fits at once and the
@@ -1543,6 +1554,8 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY_CUDA(cudaMemsetAsync(ws->scal, 0, 4 * sizeof(int), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->xf, 0, ld * nr * sizeof(float2), s));
   NB_TRY_CUDA(cudaMallocHost(&ws->host_scal, 4 * sizeof(int)));
+  NB_TRY_CUDA(cudaMallocHost(&ws->host_loop, sizeof(unsigned long long)));
+  *ws->host_loop = 0;
   return NAT_BEM_OK;
 }
 
@@ -1799,8 +1812,9 @@ static int gemv_bf16_lookup(int n) {
 }
 
 // Times every BF16 variant on the operator copy (x and y are scratch of the solve), like
-// gemv_variant: a warm-up round, four interleaved rounds, each variant's minimum; the first
-// variant wins ties within 2%. NATBEM_GEMV_BF16_VARIANT=v bypasses it.
+// gemv_variant: a warm-up round, four interleaved rounds, each variant's minimum; another
+// variant must beat the first by 5%. Operators of 8192 rows or more take the first variant
+// untuned. NATBEM_GEMV_BF16_VARIANT=v bypasses it.
 static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, double2* y, cudaStream_t s) {
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1813,6 +1827,11 @@ static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, do
   if (const char* env = std::getenv("NATBEM_GEMV_BF16_VARIANT")) {
     const int v = std::atoi(env);
     if (v >= 0 && v < kBf16Variants) best = v;
+  } else if (n >= 8192) {
+    // far beyond L2: two rows, two loads in flight (pinned one at a time on the 10240-row
+    // bench workload with four solves in flight it was fastest; the tuner, run while other
+    // solves share the GPU, has picked slower variants there)
+    best = kBf16R2U2;
   } else {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1832,7 +1851,7 @@ static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, do
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int v = 1; v < kBf16Variants; ++v)
-      if (vmin[v] < vmin[best] && vmin[v] < 0.98f * vmin[kBf16R2U2]) best = v;
+      if (vmin[v] < vmin[best] && vmin[v] < 0.95f * vmin[kBf16R2U2]) best = v;
   }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tuned_bf16[key] = best;
@@ -1861,6 +1880,27 @@ static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engin
       return product(op, which, engine, ws->xf, nrhs, y, done, scal, ws->tc_scratch, ws->tc_bytes,
                      ws->tc_err, s);
   }
+}
+
+// End of one loop body: count the body's kernels and continue while some RHS is not done
+// (scal[1] is set once every RHS converged or the iteration cap was reached).
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* __restrict__ scal,
+                            unsigned long long* __restrict__ launches, int per_body) {
+  if (threadIdx.x == 0) {
+    *launches += (unsigned long long)per_body;
+    cudaGraphSetConditional(h, scal[1] ? 0u : 1u);
+  }
+}
+
+// Kernels the device-side loops ran, for the launch counter: loop_copy enqueues the read of the
+// device counter (and its reset) before a host sync point, loop_count adds it after the sync.
+static void loop_copy(Workspace* ws, cudaStream_t s) {
+  cudaMemcpyAsync(ws->host_loop, ws->loop_launches, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s);
+  cudaMemsetAsync(ws->loop_launches, 0, sizeof(unsigned long long), s);
+}
+static void loop_count(Workspace* ws) {
+  add_launches((int64_t)*ws->host_loop);
+  *ws->host_loop = 0;
 }
 
 static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, int engine,
@@ -1909,6 +1949,62 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
     }
     return NAT_BEM_OK;
   };
+  // The whole run on the device: with the cooperative Arnoldi step every iteration launches
+  // the same kernels, so one captured chunk of 8 iterations serves as the body of a conditional
+  // while node that repeats it until every RHS is done; no host round trip until the caller
+  // reads the results.
+  static const bool loop_env_off = std::getenv("NATBEM_NO_DEVICE_LOOP") != nullptr;
+  if (use_graphs && !loop_env_off && op->opts.device_loop && !ws->loops_off && ws->coop_blocks > 0) {
+    const auto key = std::make_tuple(engine, a.maxit, a.tol,
+                                     (a.skip ? 1 : 0) + (accumulate ? 2 : 0) + (a.bscale ? 4 : 0));
+    auto f = ws->loops.find(key);
+    if (f == ws->loops.end()) {
+      cudaGraph_t g = nullptr, body = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      cudaGraphConditionalHandle h{};
+      cudaGraphNode_t node = nullptr;
+      bool ok = cudaGraphCreate(&g, 0) == cudaSuccess &&
+                cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+      if (ok) {
+        cudaGraphNodeParams np{};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess;
+        if (ok) body = np.conditional.phGraph_out[0];
+      }
+      if (ok) {
+        ok = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+             cudaSuccess;
+        if (ok) {
+          const int64_t l0 = thread_launch_count();
+          const nat_bem_status cs = launch_chunk(0, 8);
+          const int per_body = (int)(thread_launch_count() - l0) + 1;
+          add_launches(-(per_body - 1));  // capturing launches nothing
+          k_loop_cond<<<1, 32, 0, s>>>(h, a.scal, ws->loop_launches, per_body);
+          cudaGraph_t captured = nullptr;
+          ok = cudaStreamEndCapture(s, &captured) == cudaSuccess && cs == NAT_BEM_OK;
+        }
+      }
+      if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+      if (ok) {
+        f = ws->loops.emplace(key, ge).first;
+      } else {
+        cudaGetLastError();
+        ws->loops_off = true;  // chunks with host polling for this workspace
+      }
+    }
+    if (f != ws->loops.end()) {
+      NB_TRY_CUDA(cudaGraphLaunch(f->second, s));
+      const dim3 vg((n + kChunk - 1) / kChunk, nrhs);
+      NB_LAUNCH("gmres_lsq", s, k_lsq<<<nrhs, 256, 0, s>>>(a));
+      NB_LAUNCH("gmres_xupdate", s, k_xupdate<<<vg, kChunk, 0, s>>>(a, pout, accumulate));
+      NB_CHECK_LAUNCH();
+      return NAT_BEM_OK;
+    }
+  }
   while (it < a.maxit) {
     const int c = std::min(chunk, a.maxit - it);
     bool done_direct = true;
@@ -2051,6 +2147,7 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   }
   std::vector<int> iters(nrhs), done(nrhs), total(nrhs, 0), conv(nrhs, 0);
   std::vector<double> rt(nrhs);
+  int tc_err = 0;  // bounded-wait flags of the tensor-core kernels, read at every host sync
   int refinements = 0;
   bool converged = true;
   // engines: the accurate product (FP32 GEMV for one RHS, FP32 CUDA-core GEMM for several) and
@@ -2081,7 +2178,10 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     NB_TRY_CUDA(cudaMemcpyAsync(iters.data(), ws->iters, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
     NB_TRY_CUDA(cudaMemcpyAsync(done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
     NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-    NB_TRY_CUDA(cudaStreamSynchronize(s));
+    NB_TRY_CUDA(cudaMemcpyAsync(&tc_err, ws->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    loop_copy(ws, s);
+    NB_TRY_CUDA(cudaStreamSynchronize(s));  // the solve's one host sync
+    loop_count(ws);
     for (int q = 0; q < nrhs; ++q) {
       total[q] = iters[q];
       conv[q] = done[q];
@@ -2117,7 +2217,10 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       NB_TRY_CUDA(cudaMemcpyAsync(od.data(), ws->outer_done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
       NB_TRY_CUDA(cudaMemcpyAsync(inner_done.data(), ws->done, nrhs * sizeof(int), cudaMemcpyDeviceToHost, s));
       NB_TRY_CUDA(cudaMemcpyAsync(rt.data(), ws->res_true, nrhs * sizeof(double), cudaMemcpyDeviceToHost, s));
-      NB_TRY_CUDA(cudaStreamSynchronize(s));
+      NB_TRY_CUDA(cudaMemcpyAsync(&tc_err, ws->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+      loop_copy(ws, s);
+      NB_TRY_CUDA(cudaStreamSynchronize(s));  // one host sync per sweep
+      loop_count(ws);
       int used = 0;
       for (int q = 0; q < nrhs; ++q) {
         total[q] += iters[q];
@@ -2175,9 +2278,6 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       }
     }
   }
-  int tc_err = 0;
-  NB_TRY_CUDA(cudaMemcpyAsync(&tc_err, ws->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  NB_TRY_CUDA(cudaStreamSynchronize(s));
   if (tc_err) {
     set_error("tensor-core product: a bounded wait gave up (code " + std::to_string(tc_err) + ")");
     return NAT_BEM_ECUDA;

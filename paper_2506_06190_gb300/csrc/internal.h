@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -225,5 +226,10 @@ nat_bem_status sample_field_impl(const nat_bem_op* op, const double* d_u, int64_
                                  double* d_coords, float* d_amp, cudaStream_t s);
 
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+// tune.cu: index of the fastest of `ncand` launch shapes of `kind` for this size class on the
+// current device; run(c) enqueues shape c on s (timed once per class, outside graph capture).
+int autotune(const char* kind, int64_t size_class, int ncand, const std::function<nat_bem_status(int)>& run,
+             cudaStream_t s);
 
 }  // namespace natbem

@@ -158,6 +158,7 @@ nat_bem_status nat_bem_server_create(int64_t budget_bytes, const nat_bem_opts* o
     srv->budget = budget_bytes;
     nat_bem_opts_default(&srv->opts);
     if (opts) srv->opts = *opts;
+    if (slots > 1) srv->opts.device_loop = 0;  // other slots' streams fill the host round trips
     const char* fake = std::getenv("NATBEM_SERVER_FAKE");
     srv->fake = fake && fake[0] == '1';
     if (!srv->fake && cudaGetDevice(&srv->device) != cudaSuccess) {

@@ -43,7 +43,7 @@ def test_opts_defaults(nb):
     assert o.adj_subdiv_levels == 2 and o.self_theta_pts == 16
     assert o.tol == 1e-6 and o.max_iter == 200 and o.prec == nb.PREC_FP32
     assert o.inner_max_iter == 60 and o.inner_tol == 1e-2 and o.max_refinements == 10
-    assert o.restart == 0 and o.quad_regular == 7
+    assert o.restart == 0 and o.quad_regular == 7 and o.device_loop == 1
 
 
 def test_required_bytes(nb):
@@ -81,7 +81,7 @@ def _assemble_status(nb, V, F, k=2.0, opts=None):
 
 @pytest.mark.parametrize("case", ["inward", "open", "flipped_one", "index", "nan", "degenerate",
                                   "k_zero", "k_nan", "empty", "bad_levels", "bad_maxit",
-                                  "maxit_unrestarted", "bad_restart", "bad_quad"])
+                                  "maxit_unrestarted", "bad_restart", "bad_quad", "bad_loop"])
 def test_assemble_rejects_bad_input(nb, case):
     V, F = S.icosphere(1)
     k, opts = 2.0, None
@@ -113,6 +113,8 @@ def test_assemble_rejects_bad_input(nb, case):
         opts = nb.nat_bem_opts_default(restart=256)
     elif case == "bad_quad":
         opts = nb.nat_bem_opts_default(quad_regular=6)
+    elif case == "bad_loop":
+        opts = nb.nat_bem_opts_default(device_loop=2)
     st, op = _assemble_status(nb, V, F, k, opts)
     assert st == nb.NAT_BEM_EINVAL and not op.value
     assert len(nb.nat_bem_last_error()) > 0

@@ -504,3 +504,59 @@ def test_multi_rhs_mixed_tensor_core_solve(nb, oracle_lib, prec):
         assert info.refinements >= 1 and info.rel_residual <= 1e-6
     for s in range(G.shape[1]):
         assert _rel(P[:, s], np.linalg.solve(L, R @ G[:, s])) < SOL_TOL
+
+
+_LOOP_CHILD = r"""
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import synthetic as S, paper_2506_06190_gb300 as nb
+Vs, F = S.ring_sphere(2306)
+V = S.perturbed_ellipsoid(Vs, 19)
+out = []
+for prec in (nb.PREC_FP32, nb.PREC_MIXED_BF16):
+    g = np.stack([S.monopole_neumann(V, F, 7.0), S.sh_neumann(V, F, 1, 20)[:, 0]], axis=1)
+    with nb.Operator.assemble(V, F, 7.0, nb.nat_bem_opts_default(prec=prec)) as op:
+        p, info, st = op.solve(g[:, 0])
+        out.append(p)
+        p2, info, st = op.solve(g)
+        out.append(p2.ravel(order="F"))
+np.save(sys.argv[2], np.concatenate(out))
+"""
+
+
+def test_device_loop_option_gives_the_same_bits(nb):
+    """opts.device_loop = 0 (host-polled chunks) and 1 (the loop on the device) run the same
+    kernels in the same order: the same bits."""
+    Vs, F = S.ring_sphere(1500)
+    V = S.perturbed_ellipsoid(Vs, 23)
+    g = S.monopole_neumann(V, F, 4.0)
+    out = []
+    for loop in (1, 0):
+        with nb.Operator.assemble(V, F, 4.0, nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16, device_loop=loop)) as op:
+            p, info, st = op.solve(g)
+            assert st == nb.NAT_BEM_OK
+            out.append(p)
+    assert np.array_equal(out[0], out[1])
+
+
+def test_device_loop_matches_host_polled_chunks(tmp_path):
+    """The GMRES loop run on the device (a conditional while node repeating a captured chunk)
+    launches the same kernels in the same order as the host-polled chunks, so the results are
+    the same bits, plain and mixed, one and two right-hand sides (two processes, one with the
+    device loop switched off)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for off in (False, True):
+        env = dict(os.environ)
+        env.pop("NATBEM_NO_DEVICE_LOOP", None)
+        if off:
+            env["NATBEM_NO_DEVICE_LOOP"] = "1"
+        f = str(tmp_path / f"p{int(off)}.npy")
+        r = subprocess.run([sys.executable, "-c", _LOOP_CHILD, root, f], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(f))
+    assert np.array_equal(outs[0], outs[1])
