@@ -66,6 +66,7 @@ struct Workspace {
   std::map<std::tuple<int, int, double, int>, cudaGraphExec_t> loops;
   bool loops_off = false;
   unsigned long long* loop_launches = nullptr;  // kernels the loop bodies ran (device counter)
+  int* loop_bodies = nullptr;                    // bodies the current loop ran (reset per run)
   unsigned long long* host_loop = nullptr;      // pinned mirror, read at host sync points
   void* tc_scratch = nullptr;                              // packed B + split-K partials
   size_t tc_bytes = 0;
@@ -1448,6 +1449,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
   for (auto& kv : ws->graphs) cudaGraphExecDestroy(kv.second.first);
   for (auto& kv : ws->loops) cudaGraphExecDestroy(kv.second);
   if (ws->loop_launches) dev_free(ws->loop_launches, s);
+  if (ws->loop_bodies) dev_free(ws->loop_bodies, s);
   if (ws->host_loop) cudaFreeHost(ws->host_loop);
   delete ws;
 }
@@ -1500,6 +1502,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
   NB_TRY(dev_alloc_n(&ws->tc_err, 1, s));
   NB_TRY(dev_alloc_n(&ws->gbar, 2, s));
   NB_TRY(dev_alloc_n(&ws->loop_launches, 1, s));
+  NB_TRY(dev_alloc_n(&ws->loop_bodies, 1, s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->loop_launches, 0, sizeof(unsigned long long), s));
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));
   {
@@ -1883,12 +1886,16 @@ static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engin
 }
 
 // End of one loop body: count the body's kernels and continue while some RHS is not done
-// (scal[1] is set once every RHS converged or the iteration cap was reached).
+// (scal[1] is set once every RHS converged or the iteration cap was reached). The loop also
+// ends after max_bodies bodies (the cap's worth of iterations and one more body) or once a
+// kernel has raised a bounded-wait error, so it ends whatever the kernels did.
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* __restrict__ scal,
-                            unsigned long long* __restrict__ launches, int per_body) {
+                            unsigned long long* __restrict__ launches, int per_body,
+                            int* __restrict__ bodies, int max_bodies, const int* __restrict__ err) {
   if (threadIdx.x == 0) {
     *launches += (unsigned long long)per_body;
-    cudaGraphSetConditional(h, scal[1] ? 0u : 1u);
+    const int b = ++*bodies;
+    cudaGraphSetConditional(h, (scal[1] || b >= max_bodies || *err) ? 0u : 1u);
   }
 }
 
@@ -1982,7 +1989,9 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
           const nat_bem_status cs = launch_chunk(0, 8);
           const int per_body = (int)(thread_launch_count() - l0) + 1;
           add_launches(-(per_body - 1));  // capturing launches nothing
-          k_loop_cond<<<1, 32, 0, s>>>(h, a.scal, ws->loop_launches, per_body);
+          const int max_bodies = (a.maxit + 7) / 8 + 1;
+          k_loop_cond<<<1, 32, 0, s>>>(h, a.scal, ws->loop_launches, per_body, ws->loop_bodies, max_bodies,
+                                       ws->tc_err);
           cudaGraph_t captured = nullptr;
           ok = cudaStreamEndCapture(s, &captured) == cudaSuccess && cs == NAT_BEM_OK;
         }
@@ -1997,6 +2006,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
       }
     }
     if (f != ws->loops.end()) {
+      NB_TRY_CUDA(cudaMemsetAsync(ws->loop_bodies, 0, sizeof(int), s));
       NB_TRY_CUDA(cudaGraphLaunch(f->second, s));
       const dim3 vg((n + kChunk - 1) / kChunk, nrhs);
       NB_LAUNCH("gmres_lsq", s, k_lsq<<<nrhs, 256, 0, s>>>(a));
