@@ -125,6 +125,7 @@ def workload(n_k: int, n_tri: int = 10240):
 
 # ------------------------------------------------------------------------------ GPU arm
 KERNELS = ("assemble_regular", "assemble_near", "assemble_self", "geometry", "gemv_rhs", "gemv_resid", "gemv_bf16",
+           "gemv_fp16", "copy_fp16",
            "gmres_start", "gmres_arnoldi", "gmres_dots", "gmres_update", "gmres_finish", "gmres_lsq",
            "gmres_xupdate", "eval_reduce", "ir_residual", "pad_copy", "cgemm_fp32", "tc_gemm", "tc_pack",
            "tc_reduce")
@@ -145,7 +146,8 @@ def _working_launches(d):
 def _kernel_table(nb):
     kern = {name: nb.nat_bem_trace_kernel(name) for name in KERNELS}
     g = nb.nat_bem_trace_kernel("gemv")
-    kern["gemv"] = tuple(a - b - c - d for a, b, c, d in zip(g, kern["gemv_rhs"], kern["gemv_resid"], kern["gemv_bf16"]))
+    kern["gemv"] = tuple(a - b - c - d - e for a, b, c, d, e in
+                         zip(g, kern["gemv_rhs"], kern["gemv_resid"], kern["gemv_bf16"], kern["gemv_fp16"]))
     ev = nb.nat_bem_trace_kernel("eval")
     kern["eval"] = (ev[0] - kern["eval_reduce"][0], ev[1] - kern["eval_reduce"][1])
     return kern
@@ -175,7 +177,7 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
         torch.distributed.barrier()
     prob = workload(args.n_k, args.n_tri)
     n = prob.F.shape[0]
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[prec_name]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[prec_name]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -240,7 +242,7 @@ def run_gpu(args, rank: int, world: int, prec_name: str, full: bool = True):
     torch.cuda.synchronize()
     nb.nat_bem_trace_enable(False)
     kern = _kernel_table(nb)
-    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16", "gemv_fp16")}
     summary["gemv_variant"] = nb.nat_bem_gemv_variant(n)
     nb.nat_bem_trace_reset()
     first = results[0][0]
@@ -291,7 +293,7 @@ def run_modal(args):
         V = S.perturbed_ellipsoid(Vs, 3000)
         prob = S.Problem("modal_multirhs", V, F, S.log_uniform(args.n_k, 1.0, 15.0, 3001),
                          [S.sh_neumann(V, F, args.nrhs, 3002)] * args.n_k, S.shell_points(4096, 2.0, 5.0, 3003))
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -316,7 +318,7 @@ def run_modal(args):
         step()
     torch.cuda.synchronize()
     # the tensor-core product's launches in one untimed traced step (CUDA events per launch)
-    tc_name = {"bf16": "tc_gemm_bf16", "tf32": "tc_gemm_tf32"}.get(args.prec)
+    tc_name = {"bf16": "tc_gemm_bf16", "tf32": "tc_gemm_tf32", "fp16": "tc_gemm_fp16"}.get(args.prec)
     tc = None
     if tc_name:
         nb.nat_bem_trace_enable(True)
@@ -344,12 +346,12 @@ def run_modal(args):
         ld = (n + 31) // 32 * 32
         ng = 2 * ((args.nrhs + 15) // 16 * 16)  # real columns of the packed right-hand sides
         per = tc[0] / tc[1] * 1e-3
-        op_bytes = (4.0 if args.prec == "bf16" else 8.0) * n * ld
+        op_bytes = (8.0 if args.prec == "tf32" else 4.0) * n * ld
         flops = 2.0 * n * (2 * ld) * ng  # real GEMM n x 2ld times 2ld x ng
         peaks, peak_kind = _peaks()
         gbs = op_bytes / per / 1e9
         tfl = flops / per / 1e12
-        tpeak = peaks["bf16_tflops"] * (1.0 if args.prec == "bf16" else 0.5)
+        tpeak = peaks["bf16_tflops"] * (0.5 if args.prec == "tf32" else 1.0)
         traffic = NCU_TRAFFIC_MODAL_20480.get(args.prec) if n == 20480 and args.nrhs == 64 else None
         roof = {"kernel": tc_name, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": gbs / peaks["hbm_gbs"], "traffic": traffic, "launches": tc[1], "launches_exited_early": tc[2],
@@ -373,7 +375,8 @@ def run_modal(args):
     return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "tf32": "tf32 tensor cores + f32 refinement", "bf16": "bf16 tensor cores + f32 refinement"}[args.prec],
+            "dtype": {"fp32": "f32", "tf32": "tf32 tensor cores + f32 refinement", "bf16": "bf16 tensor cores + f32 refinement",
+                      "fp16": "fp16 (row-scaled) tensor cores + f32 refinement"}[args.prec],
             "data": "synthetic",
             "config": {"workload": f"modal_multirhs_{len(prob.F)}tri_{args.nrhs}rhs_{len(prob.ks)}k",
                        "precision": args.prec, "field_points": 4096},
@@ -419,7 +422,7 @@ def run_mc(args):
         gs = [S.monopole_neumann_at(Y, N, k) for k in ks]
         sampler = {"ms_median": 1e3 * float(np.median(times[3:])), "candidates": len(u), "radius": radius,
                    "samples": len(Y), "per": "one call, host wall clock, outputs on the device"}
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -472,7 +475,7 @@ def run_mc(args):
     # copy in mixed precision) for every sample pair; the roofline is the dominant one's
     m = len(Y)
     peaks, peak_kind = _peaks()
-    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16", "gemv_fp16")}
     _, table = roofline({"n": m, "measured": dict(kern, assemble_regular=(0.0, 0)), "working": working},
                         peaks, peak_kind)
     bytes_pair = 16 + (4 if args.prec == "bf16" else 0)
@@ -532,7 +535,7 @@ def run_dataset(args):
     from paper_2506_06190_gb300 import build as nb_build
     nb_build.build()
     prob = workload(args.n_k, args.n_tri)
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -571,7 +574,7 @@ def run_dataset(args):
     kern = _kernel_table(nb)
     for nm in ("sample_points", "sample_abs", "far_field"):
         kern[nm] = nb.nat_bem_trace_kernel(nm)
-    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16")}
+    working = {nm: _working_launches(nb.nat_bem_trace_durations(nm)) for nm in ("gemv", "gemv_bf16", "gemv_fp16")}
     peaks, peak_kind = _peaks()
     dom, table = roofline({"n": len(prob.F), "measured": kern, "working": working}, peaks, peak_kind)
     nb.nat_bem_trace_reset()
@@ -623,7 +626,7 @@ def run_galerkin(args):
     from paper_2506_06190_gb300 import build as nb_build
     nb_build.build()
     prob = S.interior_source(n_tri=args.n_tri, n_k=args.n_k, ka_range=(0.5, 10.0))
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -825,7 +828,7 @@ def run_uneven(args):
     from paper_2506_06190_gb300 import build as nb_build
     nb_build.build()
     probs = S.uneven_batch(n_mesh=args.n_mesh)
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -908,7 +911,7 @@ def run_serving(args):
     for nt in pool_sizes:
         Vs, F = S.ring_sphere(int(nt))
         pool[int(nt)] = (S.perturbed_ellipsoid(Vs, 5000 + int(nt)), F)
-    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32}[args.prec]
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32, "fp16": nb.PREC_MIXED_FP16}[args.prec]
     opts = nb.nat_bem_opts_default(prec=prec)
     if args.inner_tol is not None:
         opts.inner_tol = args.inner_tol
@@ -969,10 +972,12 @@ def roofline(res, peaks, peak_kind):
     # gemv: 8 n ld bytes of operator + 8 ld of x + 16 n of y per launch (one RHS); BF16 copy:
     # 4 n ld + 8 ld + 16 n. Averages over the launches that streamed the operator (the
     # iterations a captured chunk ran after convergence exit at once and are counted apart).
-    for name, elem in (("gemv", 8.0), ("gemv_bf16", 4.0)):
+    for name, elem in (("gemv", 8.0), ("gemv_bf16", 4.0), ("gemv_fp16", 4.0)):
+        if name not in kern:
+            continue
         t, c, skipped = working.get(name, (kern[name][0], kern[name][1], 0))
         if c:
-            bytes_per = elem * n * ld + 8.0 * ld + 16.0 * n
+            bytes_per = elem * n * ld + 8.0 * ld + 16.0 * n + (4.0 * n if name == "gemv_fp16" else 0.0)
             gbs = bytes_per / (t / c * 1e-3) / 1e9
             table[name] = {"bound": "hbm", "launches": c, "launches_exited_early": skipped,
                            "avg_ms": t / c, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -1071,7 +1076,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="natbem", choices=["natbem", "reference"])
-    ap.add_argument("--prec", default=None, choices=["fp32", "bf16", "tf32"],
+    ap.add_argument("--prec", default=None, choices=["fp32", "bf16", "tf32", "fp16"],
                     help="bf16 = mixed (BF16 inner GMRES, FP32 refinement); default bf16, fp32 for the "
                          "Monte-Carlo and Galerkin workloads (their operators stay in or near L2, where the "
                          "BF16 copy saves little bandwidth and refinement costs iterations)")
@@ -1178,6 +1183,7 @@ def main():
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32 (+f64 near pairs and Krylov)",
                   "bf16": "bf16 inner GMRES + f32 refinement (+f64 near pairs and Krylov)",
+                  "fp16": "fp16 (row-scaled) inner GMRES + f32 refinement (+f64 near pairs and Krylov)",
                   "tf32": "f32 (one RHS: TF32 saves no bytes)"}[args.prec],
         "data": "synthetic",
         "config": {"workload": f"interior_source_{res['n']}tri_{len(prob.ks)}k", "n_tri": res["n"],

@@ -60,7 +60,10 @@ typedef enum {
 typedef enum {
   NAT_BEM_PREC_FP32 = 0,       /* FP32 operator and matvec, FP64 Gram-Schmidt / least squares */
   NAT_BEM_PREC_MIXED_TF32 = 1, /* inner GMRES products in TF32, FP64-refined FP32 residual    */
-  NAT_BEM_PREC_MIXED_BF16 = 2  /* inner GMRES on a BF16 operator copy, FP64-refined residual   */
+  NAT_BEM_PREC_MIXED_BF16 = 2, /* inner GMRES on a BF16 operator copy, FP64-refined residual   */
+  NAT_BEM_PREC_MIXED_FP16 = 3  /* inner GMRES on an FP16 operator copy, each row scaled by a     */
+                               /* power of two into FP16's range (the same bytes as BF16, 3 more */
+                               /* significant bits, so refinement sweeps contract further)      */
 } nat_bem_precision;
 
 /*
@@ -107,7 +110,8 @@ NAT_BEM_API void nat_bem_opts_default(nat_bem_opts* opts);
  *   k: wavenumber (> 0, finite).  opts: NULL for defaults.  *out: receives the new op.
  * Work: geometry on the device, FP32 regular element pairs, FP64 self and vertex-sharing
  * pairs. The op keeps L and R (8 nt^2 bytes each, complex64, leading dimension nt rounded up
- * to 32) plus a BF16 copy of L for NAT_BEM_PREC_MIXED_BF16 (4 nt^2 bytes). Returns when the
+ * to 32) plus a BF16 copy of L for NAT_BEM_PREC_MIXED_BF16 (4 nt^2 bytes), or an FP16 copy with
+ * one power-of-two scale per row for NAT_BEM_PREC_MIXED_FP16 (4 nt^2 + 4 nt bytes). Returns when the
  * work is enqueued (the mesh checks run on the host before).
  * NAT_BEM_EINVAL: nv or nt <= 0, an index out of range, a non-finite coordinate, a zero-area
  * triangle, a mesh that is not closed with every edge used once in each direction, negative
@@ -363,8 +367,9 @@ NAT_BEM_API nat_bem_status nat_bem_sample_field(const nat_bem_op* op, const doub
  * (X, Y: nt x nrhs, column-major; host or device), by the chosen product engine:
  *   NAT_BEM_ENGINE_AUTO: the solver's accurate product (GEMV for one vector, FP32 GEMM else);
  *   NAT_BEM_ENGINE_FP32: FP32 CUDA-core complex GEMM;
- *   NAT_BEM_ENGINE_TF32 / NAT_BEM_ENGINE_BF16: tcgen05 tensor cores on L (TF32) or on its BF16
- *     copy (op built with NAT_BEM_PREC_MIXED_BF16), FP32 accumulation, nrhs <= 128, L only;
+ *   NAT_BEM_ENGINE_TF32 / NAT_BEM_ENGINE_BF16 / NAT_BEM_ENGINE_FP16: tcgen05 tensor cores on L
+ *     (TF32) or on its BF16 copy (op built with NAT_BEM_PREC_MIXED_BF16) or its row-scaled FP16
+ *     copy (NAT_BEM_PREC_MIXED_FP16), FP32 accumulation, nrhs <= 128, L only;
  *   NAT_BEM_ENGINE_GEMV0 + v: GEMV variant v (0 <= v < NAT_BEM_GEMV_VARIANTS; one vector):
  *     0-2 register-tiled (2 or 4 rows per block), 3-4 bulk-copy staged, 5-7 persistent blocks
  *     with x staged in shared memory (plain variant when 8 * ld bytes exceed 200 KiB).
@@ -377,6 +382,7 @@ enum {
   NAT_BEM_ENGINE_FP32 = 1,
   NAT_BEM_ENGINE_TF32 = 2,
   NAT_BEM_ENGINE_BF16 = 3,
+  NAT_BEM_ENGINE_FP16 = 4,
   NAT_BEM_ENGINE_GEMV0 = 10,
   NAT_BEM_GEMV_VARIANTS = 8
 };

@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "libnatbem.so")
 
 NAT_BEM_OK, NAT_BEM_EINVAL, NAT_BEM_ENOMEM, NAT_BEM_ENOCONV = 0, 1, 2, 3
 NAT_BEM_ECUDA, NAT_BEM_ETIMEOUT, NAT_BEM_EBUSY = 4, 5, 6
-PREC_FP32, PREC_MIXED_TF32, PREC_MIXED_BF16 = 0, 1, 2
+PREC_FP32, PREC_MIXED_TF32, PREC_MIXED_BF16, PREC_MIXED_FP16 = 0, 1, 2, 3
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ENOCONV", 4: "ECUDA", 5: "ETIMEOUT", 6: "EBUSY"}
 
 # every symbol include/nat_bem.h declares
@@ -40,7 +40,7 @@ EXPORTED = ["nat_bem_opts_default", "nat_bem_assemble", "nat_bem_reassemble", "n
             "nat_field_forward", "nat_field_destroy", "nat_bem_assemble_galerkin",
             "nat_bem_op_neumann_size", "nat_bem_trace_durations", "nat_bem_poisson_sample",
             "nat_bem_run_batch_fused"]
-ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_GEMV0 = 0, 1, 2, 3, 10
+ENGINE_AUTO, ENGINE_FP32, ENGINE_TF32, ENGINE_BF16, ENGINE_FP16, ENGINE_GEMV0 = 0, 1, 2, 3, 4, 10
 GEMV_VARIANTS = 8
 
 

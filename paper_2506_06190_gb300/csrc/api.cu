@@ -123,7 +123,7 @@ nat_bem_status check_opts(const nat_bem_opts& o) {
     return NAT_BEM_EINVAL;
   }
   if (o.prec != NAT_BEM_PREC_FP32 && o.prec != NAT_BEM_PREC_MIXED_TF32 &&
-      o.prec != NAT_BEM_PREC_MIXED_BF16) {
+      o.prec != NAT_BEM_PREC_MIXED_BF16 && o.prec != NAT_BEM_PREC_MIXED_FP16) {
     set_error("opts.prec is not a nat_bem_precision value");
     return NAT_BEM_EINVAL;
   }
@@ -176,7 +176,8 @@ int64_t nat_bem_required_bytes(int64_t nt, int32_t nrhs, const nat_bem_opts* opt
   if (nt <= 0 || nrhs < 1) return 0;
   const int64_t ld = round_up(nt, 32);
   int64_t b = 2 * 8 * nt * ld;                                     // L and R
-  if (o.prec == NAT_BEM_PREC_MIXED_BF16) b += 4 * nt * ld;         // BF16 copy of L
+  if (low_copy(o)) b += 4 * nt * ld;                               // BF16 or FP16 copy of L
+  if (o.prec == NAT_BEM_PREC_MIXED_FP16) b += 4 * nt;               // its row scales
   b += nt * (7 * 16 + 5 * 16 + 9 * 8 + 7 * 8 + 8 * 14);             // geometry + near pairs
   b += workspace_bytes(nt, nrhs, o);
   return b;
@@ -188,7 +189,7 @@ namespace natbem {
 
 nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double k,
                              const nat_bem_opts& o, cudaStream_t s, int64_t ld, float2* L, float2* R,
-                             uint32_t* Lb, nat_bem_op** out) {
+                             uint32_t* Lb, float* row_scale, nat_bem_op** out) {
   *out = nullptr;
   // host copies for the mesh checks and the near-pair list
   const bool vdev = is_device_pointer(verts), tdev = is_device_pointer(tris);
@@ -221,6 +222,7 @@ nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tri
   op->n = nt;
   op->k = k;
   op->opts = o;
+  op->copy_fp16 = o.prec == NAT_BEM_PREC_MIXED_FP16;
   op->stream = s;
   cudaGetDevice(&op->device);
   op->geo.n = nt;
@@ -247,13 +249,14 @@ nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tri
     op->views = true;
     op->L = L;
     op->R = R;
-    op->Lb = o.prec == NAT_BEM_PREC_MIXED_BF16 ? Lb : nullptr;
+    op->Lb = low_copy(o) ? Lb : nullptr;
+    op->row_scale = op->copy_fp16 ? row_scale : nullptr;
   } else {
     const size_t mat = (size_t)nt * (size_t)op->geo.ld;
     if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
     if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
-    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
-      return fail(st);
+    if (low_copy(o) && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK) return fail(st);
+    if (op->copy_fp16 && (st = dev_alloc_n(&op->row_scale, (size_t)nt, s)) != NAT_BEM_OK) return fail(st);
   }
   if ((st = assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
   *out = op;
@@ -291,7 +294,7 @@ nat_bem_status nat_bem_assemble(const double* verts, int64_t nv, const int32_t* 
     if (opts) o = *opts;
     NB_TRY(check_opts(o));
     return build_mesh_op(verts, nv, tris, nt, k, o, (cudaStream_t)cuda_stream, 0, nullptr, nullptr,
-                         nullptr, out);
+                         nullptr, nullptr, out);
   } catch (...) {
     set_error("internal error in nat_bem_assemble");
     return NAT_BEM_ECUDA;
@@ -380,7 +383,9 @@ nat_bem_status nat_bem_assemble_galerkin(const double* verts, int64_t nv, const 
     if (st != NAT_BEM_OK) return fail(st);
     if ((st = dev_alloc_n(&op->L, (size_t)nv * op->geo.ld, s)) != NAT_BEM_OK) return fail(st);
     if ((st = dev_alloc_n(&op->R, (size_t)nv * op->ldr, s)) != NAT_BEM_OK) return fail(st);
-    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, (size_t)nv * op->geo.ld, s)) != NAT_BEM_OK)
+    op->copy_fp16 = o.prec == NAT_BEM_PREC_MIXED_FP16;
+    if (op->copy_fp16 && (st = dev_alloc_n(&op->row_scale, (size_t)nv, s)) != NAT_BEM_OK) return fail(st);
+    if (low_copy(o) && (st = dev_alloc_n(&op->Lb, (size_t)nv * op->geo.ld, s)) != NAT_BEM_OK)
       return fail(st);
     if ((st = galerkin_assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
     *out = op;
@@ -485,7 +490,9 @@ nat_bem_status nat_bem_assemble_mc(const double* pts, const double* normals, int
     const size_t mat = (size_t)m * (size_t)op->geo.ld;
     if ((st = dev_alloc_n(&op->L, mat, s)) != NAT_BEM_OK) return fail(st);
     if ((st = dev_alloc_n(&op->R, mat, s)) != NAT_BEM_OK) return fail(st);
-    if (o.prec == NAT_BEM_PREC_MIXED_BF16 && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
+    op->copy_fp16 = o.prec == NAT_BEM_PREC_MIXED_FP16;
+    if (op->copy_fp16 && (st = dev_alloc_n(&op->row_scale, (size_t)m, s)) != NAT_BEM_OK) return fail(st);
+    if (low_copy(o) && (st = dev_alloc_n(&op->Lb, mat, s)) != NAT_BEM_OK)
       return fail(st);
     if ((st = mc_assemble_operators(op, s)) != NAT_BEM_OK) return fail(st);
     *out = op;
@@ -707,10 +714,13 @@ nat_bem_status nat_bem_op_apply(const nat_bem_op* op, int32_t which, int32_t eng
     const bool gemv_engine = engine >= NAT_BEM_ENGINE_GEMV0 && engine < NAT_BEM_ENGINE_GEMV0 + NAT_BEM_GEMV_VARIANTS;
     if (!op || !X || !Y || nrhs < 1 || which < 0 || which > 1 ||
         !(engine == NAT_BEM_ENGINE_AUTO || engine == NAT_BEM_ENGINE_FP32 ||
-          engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16 || gemv_engine) ||
+          engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16 || engine == NAT_BEM_ENGINE_FP16 ||
+          gemv_engine) ||
         (gemv_engine && nrhs != 1) ||
-        ((engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16) && (which != 0 || nrhs > 128)) ||
-        (engine == NAT_BEM_ENGINE_BF16 && !op->Lb)) {
+        ((engine == NAT_BEM_ENGINE_TF32 || engine == NAT_BEM_ENGINE_BF16 || engine == NAT_BEM_ENGINE_FP16) &&
+         (which != 0 || nrhs > 128)) ||
+        (engine == NAT_BEM_ENGINE_BF16 && (!op->Lb || op->copy_fp16)) ||
+        (engine == NAT_BEM_ENGINE_FP16 && (!op->Lb || !op->copy_fp16))) {
       set_error("nat_bem_op_apply: bad arguments or engine not usable for this op");
       return NAT_BEM_EINVAL;
     }
@@ -773,7 +783,7 @@ void nat_bem_destroy(nat_bem_op* op) {
     for (void* p : gp) dev_free(p, s);
   }
   if (!op->views) {
-    void* mp[] = {op->L, op->R, op->Lb};
+    void* mp[] = {op->L, op->R, op->Lb, op->row_scale};
     for (void* p : mp) dev_free(p, s);
   }
   galerkin_free(op, s);

@@ -22,6 +22,7 @@
 //       a = (rho^2 - 3) q + n_x.n_y,   b = rho (3 q - n_x.n_y),
 //   G + beta dG/dn_x = G [ 1 - d.n_x / r - i d.n_x / (k r^2) ].
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <array>
@@ -714,10 +715,10 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
     const int64_t adj_blocks = (g.n_near * 16 + threads - 1) / threads;
     if (adj_blocks > 0)
       NB_LAUNCH("assemble_near", s, k_assemble_adjacent<<<(unsigned)adj_blocks, (unsigned)threads, 0, s>>>(
-          g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, op->Lb));
+          g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, bf16_target(op)));
     const int64_t self_blocks = ((int64_t)n * 32 + threads - 1) / threads;
     NB_LAUNCH("assemble_self", s, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, s>>>(
-        n, g.tri, g.cen, ld, op->k, op->L, op->R, op->Lb));
+        n, g.tri, g.cen, ld, op->k, op->L, op->R, bf16_target(op)));
     NB_CHECK_LAUNCH();
   }
   // regular pairs: columns in blocks of 256 (two columns a thread in the paired form), rows
@@ -730,16 +731,56 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
     dim3 grid(col_blocks, row_blocks);
     if (scalar)
       NB_LAUNCH("assemble_regular", s, k_assemble_regular<<<grid, kRegThreads, 0, s>>>(
-          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, bf16_target(op)));
     else
       NB_LAUNCH("assemble_regular", s, k_assemble_regular_x2<<<grid, kX2Threads, 0, s>>>(
-          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, op->Lb));
+          g.c_hi, g.c_lo, g.nrm, g.qp, g.vid, n, ld, rows_per_block, (float)op->k, op->L, op->R, bf16_target(op)));
     NB_CHECK_LAUNCH();
     return NAT_BEM_OK;
   };
   static const int kRows[4] = {64, 32, 128, 16};
   const int pick = autotune("assemble_rows", (n + 1023) / 1024, 4, [&](int c) { return launch(kRows[c]); }, s);
   NB_TRY(launch(kRows[pick]));
+  return finish_low_copy(op, s);
+}
+
+// The row-scaled FP16 copy of L: one block per row finds the row's largest real or imaginary
+// magnitude m = f 2^E (f in [0.5, 1)), takes s = 2^(15 - E) so that the scaled entries stay
+// below 2^15 (FP16's largest finite value is 65504) and keep FP16's full 11 significant bits
+// down to 2^-29 of m, writes half2(L_ij s) rounded to nearest, and 1/s (exact) as the row scale.
+__global__ void __launch_bounds__(256) k_copy_fp16_rows(const float2* __restrict__ L, int ld,
+                                                        uint32_t* __restrict__ Lh, float* __restrict__ row_scale) {
+  __shared__ float red[8];
+  const size_t row = blockIdx.x;
+  const float2* src = L + row * ld;
+  float m = 0.f;
+  for (int j = threadIdx.x; j < ld; j += 256) {
+    const float2 v = src[j];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) m = fmaxf(m, red[w]);
+  int e = 0;
+  if (m > 0.f) frexpf(m, &e);
+  const float scale = m > 0.f ? ldexpf(1.0f, 15 - e) : 1.0f;
+  for (int j = threadIdx.x; j < ld; j += 256) {
+    const float2 v = src[j];
+    __half2 h = __floats2half2_rn(v.x * scale, v.y * scale);
+    Lh[row * ld + j] = *reinterpret_cast<uint32_t*>(&h);
+  }
+  if (threadIdx.x == 0) row_scale[row] = m > 0.f ? ldexpf(1.0f, e - 15) : 1.0f;
+}
+
+nat_bem_status finish_low_copy(nat_bem_op* op, cudaStream_t s) {
+  if (!op->copy_fp16 || !op->Lb) return NAT_BEM_OK;
+  NB_LAUNCH("copy_fp16", s, k_copy_fp16_rows<<<(unsigned)op->n, 256, 0, s>>>(op->L, (int)op->geo.ld, op->Lb,
+                                                                              op->row_scale));
+  NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
 }
 

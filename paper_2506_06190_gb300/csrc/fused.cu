@@ -32,10 +32,11 @@ namespace {
 constexpr double kBucketRatio = 1.189207115002721;       // 2^(1/4)
 constexpr int64_t kBucketBytes = (int64_t)24 << 30;     // operators of one bucket (L, R, BF16 copy)
 
-// Rows n..N-1 of one padded operator: L the identity, R zero (BF16 copy: identity). One thread
+// Rows n..N-1 of one padded operator: L the identity, R zero (the low-precision copy: the
+// identity too, bf16(1) = 0x3F80 or fp16(1) = 0x3C00 in the low half, row scale 1). One thread
 // per (row, column).
 __global__ void k_pad_rows(float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb,
-                           int n, int N, int ld) {
+                           uint32_t one, float* __restrict__ row_scale, int n, int N, int ld) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)(N - n) * ld;
   if (i >= total) return;
@@ -44,7 +45,8 @@ __global__ void k_pad_rows(float2* __restrict__ L, float2* __restrict__ R, uint3
   const bool diag = row == col;
   L[off] = make_float2(diag ? 1.f : 0.f, 0.f);
   R[off] = make_float2(0.f, 0.f);
-  if (Lb) Lb[off] = diag ? 0x3F80u : 0u;  // bf16(1) in the low half, imaginary part 0
+  if (Lb) Lb[off] = diag ? one : 0u;
+  if (row_scale && col == 0) row_scale[row] = 1.0f;
 }
 
 // Column s of the bucket's right-hand sides: the mesh's n Neumann values, zeros up to N.
@@ -68,10 +70,12 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
                           std::string& first_error) {
   const int B = (int)bk.jobs.size();
   const int64_t N = bk.N, ld = round_up(N, 32);
-  const bool bf16 = o.prec == NAT_BEM_PREC_MIXED_BF16;
+  const bool bf16 = low_copy(o);  // a low-precision copy (BF16, or FP16 with row scales)
+  const bool fp16 = o.prec == NAT_BEM_PREC_MIXED_FP16;
   const size_t slice = (size_t)N * (size_t)ld;
   float2 *L = nullptr, *R = nullptr, *G = nullptr, *P = nullptr;
   uint32_t* Lb = nullptr;
+  float* RS = nullptr;
   std::vector<nat_bem_op*> ops(B, nullptr);
   nat_bem_op* batch = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;
@@ -81,6 +85,7 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
     dev_free(L, s);
     dev_free(R, s);
     dev_free(Lb, s);
+    dev_free(RS, s);
     dev_free(G, s);
     dev_free(P, s);
     if (t0) cudaEventDestroy(t0);
@@ -95,6 +100,7 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
   nat_bem_status st = NAT_BEM_OK;
   if ((st = dev_alloc_n(&L, slice * B, s)) != NAT_BEM_OK || (st = dev_alloc_n(&R, slice * B, s)) != NAT_BEM_OK ||
       (bf16 && (st = dev_alloc_n(&Lb, slice * B, s)) != NAT_BEM_OK) ||
+      (fp16 && (st = dev_alloc_n(&RS, (size_t)N * B, s)) != NAT_BEM_OK) ||
       (st = dev_alloc_n(&G, (size_t)N * B, s)) != NAT_BEM_OK || (st = dev_alloc_n(&P, (size_t)N * B, s)) != NAT_BEM_OK)
     return fail_all(st);
   if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
@@ -129,11 +135,12 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
       op->L = L + off;
       op->R = R + off;
       op->Lb = bf16 ? Lb + off : nullptr;
+      op->row_scale = fp16 ? RS + (size_t)b * N : nullptr;
       ops[b] = op;
       st = assemble_operators(op, s);
     } else {
       st = build_mesh_op(j.verts, j.nv, j.tris, j.nt, j.k, o, s, ld, L + off, R + off, bf16 ? Lb + off : nullptr,
-                         &ops[b]);
+                         fp16 ? RS + (size_t)b * N : nullptr, &ops[b]);
     }
     int n_b = (int)j.nt;
     if (st != NAT_BEM_OK) {
@@ -146,7 +153,8 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
     if (n_b < N) {
       const int64_t tot = (int64_t)(N - n_b) * ld;
       NB_LAUNCH("pad_rows", s, k_pad_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
-          L + off, R + off, bf16 ? Lb + off : nullptr, n_b, (int)N, (int)ld));
+          L + off, R + off, bf16 ? Lb + off : nullptr, fp16 ? 0x3C00u : 0x3F80u,
+          fp16 ? RS + (size_t)b * N : nullptr, n_b, (int)N, (int)ld));
     }
     // right-hand side column b (zero for a mesh that left the bucket)
     const float2* dg = nullptr;
@@ -178,6 +186,8 @@ nat_bem_status run_bucket(nat_bem_job* jobs, const Bucket& bk, const nat_bem_opt
   batch->L = L;
   batch->R = R;
   batch->Lb = Lb;
+  batch->copy_fp16 = fp16;
+  batch->row_scale = RS;
   batch->bstride = (int64_t)slice;
   std::vector<nat_bem_solve_info> per;
   std::vector<int> conv;
@@ -251,7 +261,7 @@ extern "C" nat_bem_status nat_bem_run_batch_fused(nat_bem_job* jobs, int32_t njo
     std::vector<int32_t> fused, single;
     for (int32_t i = 0; i < njobs; ++i) (jobs[i].nrhs == 1 ? fused : single).push_back(i);
     std::stable_sort(fused.begin(), fused.end(), [&](int32_t a, int32_t b) { return jobs[a].nt > jobs[b].nt; });
-    const bool bf16 = o.prec == NAT_BEM_PREC_MIXED_BF16;
+    const bool bf16 = low_copy(o);
     std::vector<Bucket> buckets;
     for (int32_t q : fused) {
       const int64_t nt = jobs[q].nt;
@@ -301,7 +311,8 @@ extern "C" nat_bem_status nat_bem_run_batch_fused(nat_bem_job* jobs, int32_t njo
           cudaEventCreate(&e0);
           cudaEventCreate(&e1);
           cudaEventRecord(e0, s);
-          nat_bem_status st = build_mesh_op(j.verts, j.nv, j.tris, j.nt, j.k, o, s, 0, nullptr, nullptr, nullptr, &op);
+          nat_bem_status st =
+              build_mesh_op(j.verts, j.nv, j.tris, j.nt, j.k, o, s, 0, nullptr, nullptr, nullptr, nullptr, &op);
           if (st == NAT_BEM_OK) st = nat_bem_solve(op, j.neumann, j.nrhs, j.p_out, &j.info, s);
           if ((st == NAT_BEM_OK || st == NAT_BEM_ENOCONV) && j.m > 0) {
             const nat_bem_status se = nat_bem_eval(op, j.pts, j.m, j.p_out, j.neumann, j.nrhs, j.field_out, s);

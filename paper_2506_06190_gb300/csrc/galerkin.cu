@@ -669,7 +669,7 @@ nat_bem_status galerkin_assemble_operators(nat_bem_op* op, cudaStream_t s) {
     NB_LAUNCH("gal_rowsum_L", s, k_gal_rowsum_L<<<dim3((unsigned)((nv + 255) / 256), (unsigned)(t1 - t0)), 256, 0, s>>>(
         partL, nt, G.adj_ptr, G.adj, nv, ldv, P2));
     NB_LAUNCH("gal_gather_L", s, k_gal_gather_L<<<dim3((unsigned)((ldv + 255) / 256), (unsigned)nv), 256, 0, s>>>(
-        P2, t0, t1, G.adj_ptr, G.adj, nv, ldv, t0 > 0 ? 1 : 0, op->L, last ? op->Lb : nullptr));
+        P2, t0, t1, G.adj_ptr, G.adj, nv, ldv, t0 > 0 ? 1 : 0, op->L, last ? bf16_target(op) : nullptr));
     NB_LAUNCH("gal_gather_R", s, k_gal_gather_R<<<dim3((unsigned)((ldr + 255) / 256), (unsigned)nv), 256, 0, s>>>(
         partR, nt, t0, t1, G.adj_ptr, G.adj, ldr, t0 > 0 ? 1 : 0, op->R));
     if (cudaGetLastError() != cudaSuccess) {
@@ -680,6 +680,7 @@ nat_bem_status galerkin_assemble_operators(nat_bem_op* op, cudaStream_t s) {
   dev_free(partL, s);
   dev_free(partR, s);
   dev_free(P2, s);
+  if (st == NAT_BEM_OK) st = finish_low_copy(op, s);
   return st;
 }
 

@@ -17,6 +17,7 @@
 // sums, summed in a fixed order by the last block to finish (counted with an atomic ticket).
 // Restarted GMRES(m) and mixed-precision refinement run sweeps of this loop on the current
 // residual, accumulating the solution in FP64.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -189,7 +190,8 @@ __device__ __forceinline__ void warp_sum_df(float s, float c, float& hi, float& 
 template <int kRows>
 __device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], const float (&cr)[kRows],
                                                   const float (&si)[kRows], const float (&ci)[kRows],
-                                                  int n, int row0, double2* __restrict__ y) {
+                                                  int n, int row0, double2* __restrict__ y,
+                                                  const float* __restrict__ rs = nullptr) {
   __shared__ float2 sh[kRows][8];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
@@ -211,7 +213,8 @@ __device__ __forceinline__ void gemv_block_reduce(const float (&sr)[kRows], cons
       tr += sh[r][q].x;
       ti += sh[r][q].y;
     }
-    y[row0 + r] = make_double2(tr, ti);
+    const double sc = rs ? (double)rs[row0 + r] : 1.0;  // a power of two: exact
+    y[row0 + r] = make_double2(tr * sc, ti * sc);
   }
 }
 
@@ -317,17 +320,21 @@ k_gemv_xs(const float2* __restrict__ A, int n, int ld, const float2* __restrict_
   }
 }
 
-// The same product with A stored as packed bf16 complex pairs (real in the low half): half
-// the bytes of the FP32 operator; 16-byte loads hold four complex entries.
-template <int kRows, int kUnroll>
-__global__ void __launch_bounds__(256)
-k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
-            int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
-            const int* __restrict__ scal, int64_t astride) {
+// The same product with A stored as a 16-bit copy: packed bf16 complex pairs (kFmt 0, real in
+// the low half), or half2 pairs of the row-scaled entries L_ij s_i (kFmt 1; the row's sum is
+// multiplied by rs[row] = 1/s_i, a power of two). Half the bytes of the FP32 operator; 16-byte
+// loads hold four complex entries.
+template <int kRows, int kUnroll, int kFmt>
+__device__ __forceinline__ void gemv_copy_body(const uint32_t* __restrict__ A, int n, int ld,
+                                               const float2* __restrict__ x, int64_t xstride,
+                                               double2* __restrict__ y, int64_t ystride,
+                                               const int* __restrict__ done, const int* __restrict__ scal,
+                                               int64_t astride, const float* __restrict__ rs, int64_t sstride) {
   if (scal && scal[1]) return;
   const int s = blockIdx.y;
   if (done && done[s]) return;
   A += (size_t)s * astride;
+  if (rs) rs += (size_t)s * sstride;
   const int row0 = blockIdx.x * kRows;
   const float4* xv = reinterpret_cast<const float4*>(x + (size_t)s * xstride);
   const uint4* a[kRows];
@@ -360,7 +367,15 @@ k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restr
         float pr = 0.f, pi = 0.f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float ar = __uint_as_float(w[e] << 16), ai = __uint_as_float(w[e] & 0xffff0000u);
+          float ar, ai;
+          if (kFmt == 0) {
+            ar = __uint_as_float(w[e] << 16);
+            ai = __uint_as_float(w[e] & 0xffff0000u);
+          } else {
+            const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+            ar = v.x;
+            ai = v.y;
+          }
           pr = fmaf(ar, xr[e], fmaf(-ai, xi[e], pr));
           pi = fmaf(ar, xi[e], fmaf(ai, xr[e], pi));
         }
@@ -369,7 +384,23 @@ k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restr
       }
     }
   }
-  gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride);
+  gemv_block_reduce<kRows>(sr, cr, si, ci, n, row0, y + (size_t)s * ystride, rs);
+}
+
+template <int kRows, int kUnroll>
+__global__ void __launch_bounds__(256)
+k_gemv_bf16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
+            int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+            const int* __restrict__ scal, int64_t astride) {
+  gemv_copy_body<kRows, kUnroll, 0>(A, n, ld, x, xstride, y, ystride, done, scal, astride, nullptr, 0);
+}
+
+template <int kRows, int kUnroll>
+__global__ void __launch_bounds__(256)
+k_gemv_fp16(const uint32_t* __restrict__ A, int n, int ld, const float2* __restrict__ x,
+            int64_t xstride, double2* __restrict__ y, int64_t ystride, const int* __restrict__ done,
+            const int* __restrict__ scal, int64_t astride, const float* __restrict__ rs, int64_t sstride) {
+  gemv_copy_body<kRows, kUnroll, 1>(A, n, ld, x, xstride, y, ystride, done, scal, astride, rs, sstride);
 }
 
 // Bulk-copy GEMV for one RHS per blockIdx.y: each block streams a contiguous range of rows
@@ -1780,37 +1811,42 @@ static nat_bem_status gemv(const char* name, const float2* A, int n, int ld, con
 // any graph capture); until then, and when no tuning ran, the first variant is used.
 enum Bf16Variant { kBf16R2U2 = 0, kBf16R2U4, kBf16R4U2, kBf16R4U1, kBf16Variants };
 
+// rs (row scales) null: the BF16 copy; else the row-scaled FP16 copy.
 static nat_bem_status gemv_bf16_launch(int variant, const char* name, const uint32_t* A, int n, int ld,
                                        const float2* x, double2* y, int nrhs, const int* done,
-                                       const int* scal, cudaStream_t s, int64_t astride = 0) {
+                                       const int* scal, cudaStream_t s, int64_t astride = 0,
+                                       const float* rs = nullptr, int64_t sstride = 0) {
   const int rows = (variant == kBf16R4U2 || variant == kBf16R4U1) ? 4 : 2;
   dim3 grid((n + rows - 1) / rows, nrhs);
+#define NB_COPY_GEMV(R, U)                                                                              \
+  do {                                                                                                   \
+    if (rs)                                                                                              \
+      NB_LAUNCH(name, s, k_gemv_fp16<R, U><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride, rs, \
+                                                                    sstride));                          \
+    else                                                                                                 \
+      NB_LAUNCH(name, s, k_gemv_bf16<R, U><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride)); \
+  } while (0)
   switch (variant) {
-    case kBf16R2U4:
-      NB_LAUNCH(name, s, k_gemv_bf16<2, 4><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
-      break;
-    case kBf16R4U2:
-      NB_LAUNCH(name, s, k_gemv_bf16<4, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
-      break;
-    case kBf16R4U1:
-      NB_LAUNCH(name, s, k_gemv_bf16<4, 1><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
-      break;
-    default:
-      NB_LAUNCH(name, s, k_gemv_bf16<2, 2><<<grid, 256, 0, s>>>(A, n, ld, x, ld, y, n, done, scal, astride));
+    case kBf16R2U4: NB_COPY_GEMV(2, 4); break;
+    case kBf16R4U2: NB_COPY_GEMV(4, 2); break;
+    case kBf16R4U1: NB_COPY_GEMV(4, 1); break;
+    default: NB_COPY_GEMV(2, 2);
   }
+#undef NB_COPY_GEMV
   NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
 }
 
 namespace {
-std::map<std::pair<int, int64_t>, int> g_tuned_bf16;  // (device, n rounded to 1024) -> variant
+// (device, 2 x (n rounded to 1024) + copy format) -> variant
+std::map<std::pair<int, int64_t>, int> g_tuned_bf16;
 }  // namespace
 
-static int gemv_bf16_lookup(int n) {
+static int gemv_bf16_lookup(int n, bool fp16) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned_bf16.find(std::make_pair(dev, (int64_t)((n + 1023) / 1024)));
+  auto it = g_tuned_bf16.find(std::make_pair(dev, (int64_t)((n + 1023) / 1024) * 2 + (fp16 ? 1 : 0)));
   return it == g_tuned_bf16.end() ? kBf16R2U2 : it->second;
 }
 
@@ -1818,10 +1854,11 @@ static int gemv_bf16_lookup(int n) {
 // gemv_variant: a warm-up round, four interleaved rounds, each variant's minimum; another
 // variant must beat the first by 5%. Operators of 8192 rows or more take the first variant
 // untuned. NATBEM_GEMV_BF16_VARIANT=v bypasses it.
-static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, double2* y, cudaStream_t s) {
+static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, double2* y, cudaStream_t s,
+                           const float* rs = nullptr) {
   int dev = 0;
   cudaGetDevice(&dev);
-  const auto key = std::make_pair(dev, (int64_t)((n + 1023) / 1024));
+  const auto key = std::make_pair(dev, (int64_t)((n + 1023) / 1024) * 2 + (rs ? 1 : 0));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_tuned_bf16.count(key)) return;
@@ -1845,7 +1882,7 @@ static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, do
       for (int v = 0; v < kBf16Variants; ++v) {
         float ms = 1e30f;
         cudaEventRecord(e0, s);
-        gemv_bf16_launch(v, "gemv_bf16_tune", A, n, ld, x, y, 1, nullptr, nullptr, s);
+        gemv_bf16_launch(v, "gemv_bf16_tune", A, n, ld, x, y, 1, nullptr, nullptr, s, 0, rs);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -1862,8 +1899,10 @@ static void gemv_bf16_tune(const uint32_t* A, int n, int ld, const float2* x, do
 
 static nat_bem_status gemv_bf16(const char* name, const uint32_t* A, int n, int ld,
                                 const float2* x, double2* y, int nrhs, const int* done,
-                                const int* scal, cudaStream_t s, int64_t astride = 0) {
-  return gemv_bf16_launch(gemv_bf16_lookup(n), name, A, n, ld, x, y, nrhs, done, scal, s, astride);
+                                const int* scal, cudaStream_t s, int64_t astride = 0,
+                                const float* rs = nullptr, int64_t sstride = 0) {
+  return gemv_bf16_launch(gemv_bf16_lookup(n, rs != nullptr), name, A, n, ld, x, y, nrhs, done, scal, s,
+                          astride, rs, sstride);
 }
 
 // One GMRES run on the right-hand sides in a.b (x0 = 0): init, iterations until every RHS
@@ -1877,8 +1916,9 @@ static nat_bem_status matvec(nat_bem_op* op, Workspace* ws, int which, int engin
   switch (engine) {
     case kEngineGemv:
       return gemv(name, M, n, ld, ws->xf, y, nrhs, done, scal, s, ws->tc_err, op->bstride);
-    case kEngineGemvBf16:
-      return gemv_bf16(name, op->Lb, n, ld, ws->xf, y, nrhs, done, scal, s, op->bstride);
+    case kEngineGemvCopy:  // the BF16 copy, or the FP16 copy with its row scales
+      return gemv_bf16(name, op->Lb, n, ld, ws->xf, y, nrhs, done, scal, s, op->bstride,
+                       op->copy_fp16 ? op->row_scale : nullptr, op->bstride > 0 ? n : 0);
     default:
       return product(op, which, engine, ws->xf, nrhs, y, done, scal, ws->tc_scratch, ws->tc_bytes,
                      ws->tc_err, s);
@@ -1927,7 +1967,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
   auto launch_chunk = [&](int it0, int c) -> nat_bem_status {
     for (int q = 0; q < c; ++q) {
       NB_TRY(matvec(op, ws, 0, engine, ws->w, ws->done, ws->scal,
-                    engine == kEngineGemvBf16 ? "gemv_bf16" : "gemv", s));
+                    engine == kEngineGemvCopy ? (op->copy_fp16 ? "gemv_fp16" : "gemv_bf16") : "gemv", s));
       if (ws->coop_blocks > 0) {
         GArgs ac = a;
         double2* pb = ws->pblk;
@@ -2100,7 +2140,8 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
     st = gemv("gemv_apply", M, n, ld, xpad, y64, 1, nullptr, nullptr, s, err);
   } else {
     const int eng = engine == NAT_BEM_ENGINE_TF32 ? kEngineTf32
-                    : engine == NAT_BEM_ENGINE_BF16 ? kEngineBf16 : kEngineFp32;
+                    : engine == NAT_BEM_ENGINE_BF16 ? kEngineBf16
+                    : engine == NAT_BEM_ENGINE_FP16 ? kEngineFp16 : kEngineFp32;
     if (eng != kEngineFp32) {
       int dev = 0, sms = 148;
       cudaGetDevice(&dev);
@@ -2168,14 +2209,16 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
   const bool gemv_path = nrhs == 1 || op->bstride > 0;
   const int accurate = gemv_path ? kEngineGemv : kEngineFp32;
   int inner = accurate;
-  if (o.prec == NAT_BEM_PREC_MIXED_BF16 && op->Lb) inner = gemv_path ? kEngineGemvBf16 : kEngineBf16;
+  if (low_copy(o) && op->Lb)
+    inner = gemv_path ? kEngineGemvCopy : (op->copy_fp16 ? kEngineFp16 : kEngineBf16);
   if (o.prec == NAT_BEM_PREC_MIXED_TF32 && !gemv_path) inner = kEngineTf32;
   const bool mixed = inner != accurate;
   // GMRES(m): the Krylov basis holds m = restart vectors and the solve runs cycles of at most
   // m iterations, each on the current residual
   const bool restarted = ws->m < std::max(1, o.max_iter);
-  if (inner == kEngineGemvBf16) gemv_bf16_tune(op->Lb, n, (int)op->geo.ld, ws->gin, ws->w, s);
-  if (inner == kEngineTf32 || inner == kEngineBf16)  // the tensor-core shape, outside any capture
+  if (inner == kEngineGemvCopy)
+    gemv_bf16_tune(op->Lb, n, (int)op->geo.ld, ws->gin, ws->w, s, op->copy_fp16 ? op->row_scale : nullptr);
+  if (inner == kEngineTf32 || inner == kEngineBf16 || inner == kEngineFp16)  // tensor-core shape, outside capture
     NB_TRY(tc_tune(op, inner, nrhs, ws->xf, ws->w, ws->tc_scratch, ws->tc_bytes, ws->tc_err, s));
   if (!mixed && !restarted) {
     GArgs a = make_args(op, ws, op->L);

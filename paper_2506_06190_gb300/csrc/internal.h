@@ -147,7 +147,10 @@ struct nat_bem_op {
   natbem::Geometry geo;
   float2* L = nullptr;                 // n x ld complex64, row-major
   float2* R = nullptr;                 // n x ld complex64, row-major (store_r)
-  uint32_t* Lb = nullptr;              // n x ld complex as packed bf16 pairs (mixed BF16)
+  uint32_t* Lb = nullptr;              // n x ld complex as packed bf16 pairs (mixed BF16) or, with
+                                       // copy_fp16, packed half2 of the row-scaled entries
+  bool copy_fp16 = false;              // mixed FP16: Lb holds L_ij s_i in half precision
+  float* row_scale = nullptr;          // mixed FP16: 1 / s_i per row (a power of two)
   bool views = false;                  // L, R and Lb belong to someone else (not freed here)
   bool geo_view = false;               // geo belongs to another op of the same mesh
   int64_t bstride = 0;                 // > 0: a batch of operators, RHS s uses L + s bstride
@@ -168,13 +171,21 @@ namespace natbem {
 // for mixed BF16, Lb of nt x ld each) instead of owned allocations.
 nat_bem_status build_mesh_op(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, double k,
                              const nat_bem_opts& o, cudaStream_t s, int64_t ld, float2* L, float2* R,
-                             uint32_t* Lb, nat_bem_op** out);
+                             uint32_t* Lb, float* row_scale, nat_bem_op** out);
+inline bool low_copy(const nat_bem_opts& o) {
+  return o.prec == NAT_BEM_PREC_MIXED_BF16 || o.prec == NAT_BEM_PREC_MIXED_FP16;
+}
 nat_bem_status check_opts(const nat_bem_opts& o);
 
 // assemble.cu
 nat_bem_status geometry_build(nat_bem_op* op, const double* dV, const int32_t* dT, int64_t nv,
                               const std::vector<int2>& near_pairs, cudaStream_t s);
 nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s);
+// The BF16 copy is written by the assembly kernels; this writes the row-scaled FP16 copy from
+// the assembled L (mixed FP16; nothing otherwise). Every assembly ends with it.
+nat_bem_status finish_low_copy(nat_bem_op* op, cudaStream_t s);
+// The pointer the assembly kernels write the BF16 copy to (null for an FP16 or no copy).
+inline uint32_t* bf16_target(const nat_bem_op* op) { return op->copy_fp16 ? nullptr : op->Lb; }
 
 // mc.cu
 nat_bem_status mc_geometry_build(nat_bem_op* op, const double* dY, const double* dN, cudaStream_t s);
@@ -204,7 +215,9 @@ int gemv_tuned_variant(int64_t n);  // -1 before the autotuner met this size
 // products.cu: Y = M X for nrhs right-hand sides (M = L for which == 0, R for 1).
 // kEngineFp32: FP32 CUDA-core complex GEMM; kEngineTf32 / kEngineBf16: tcgen05 tensor cores
 // on L (TF32) or its BF16 copy, using `scratch` for the packed B and the split-K partials.
-enum Engine { kEngineGemv = 0, kEngineGemvBf16 = 1, kEngineFp32 = 2, kEngineTf32 = 3, kEngineBf16 = 4 };
+// kEngineGemvCopy: the GEMV on the low-precision copy (BF16 or row-scaled FP16, by the op).
+enum Engine { kEngineGemv = 0, kEngineGemvCopy = 1, kEngineFp32 = 2, kEngineTf32 = 3, kEngineBf16 = 4,
+              kEngineFp16 = 5 };
 nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
                        double2* Y, const int* done, const int* scal, void* scratch,
                        size_t scratch_bytes, int* err, cudaStream_t s);

@@ -148,9 +148,9 @@ nat_bem_status mc_assemble_operators(nat_bem_op* op, cudaStream_t s) {
   const int rows_per_block = 64;
   dim3 grid((ld + kMcThreads - 1) / kMcThreads, (m + rows_per_block - 1) / rows_per_block);
   NB_LAUNCH("assemble_mc", s, k_mc_assemble<<<grid, kMcThreads, 0, s>>>(
-      g.c_hi, g.c_lo, g.nrm, m, ld, rows_per_block, (float)op->k, (float)w, (float)eps, op->L, op->R, op->Lb));
+      g.c_hi, g.c_lo, g.nrm, m, ld, rows_per_block, (float)op->k, (float)w, (float)eps, op->L, op->R, bf16_target(op)));
   NB_CHECK_LAUNCH();
-  return NAT_BEM_OK;
+  return finish_low_copy(op, s);
 }
 
 }  // namespace natbem

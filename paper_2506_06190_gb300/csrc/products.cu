@@ -25,6 +25,7 @@
 // skips its remaining work, waits (bounded) for its own copies, frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -187,8 +188,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 // can have), stored column by column: part[slot][col][row in tile]. With kTiles = 2 one B stage
 // feeds two M = 128 MMAs (two accumulators), halving B's share of the shared-memory traffic.
 // A: n x Kt (tensor map ta, box BK x 128 kTiles), B: Ng x Kt
-// (tensor map tb, box BK x Ng). kKind 0: TF32 (FP32 storage, BK = 32), 1: BF16 (BK = 64);
-// either way a stage row is 128 bytes and one MMA covers 32 bytes of K, four per stage.
+// (tensor map tb, box BK x Ng). kKind 0: TF32 (FP32 storage, BK = 32), 1: BF16, 2: FP16 (the
+// row-scaled copy; BK = 64); either way a stage row is 128 bytes and one MMA covers 32 bytes
+// of K, four per stage.
 template <int kKind, int kTiles>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int n,
@@ -274,7 +276,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: kTiles accumulators per segment, alternating between the two TMEM buffers
-    const uint32_t idesc = instr_desc(kKind == 0 ? 2u : 1u, (uint32_t)Ng, (uint32_t)kTcRows);
+    // operand formats: TF32 = 2 (kind::tf32); BF16 = 1, F16 = 0 (kind::f16)
+    const uint32_t idesc = instr_desc(kKind == 0 ? 2u : kKind == 1 ? 1u : 0u, (uint32_t)Ng, (uint32_t)kTcRows);
     int seg = -1, mt_cur = -1;
     uint32_t acc = tmem;
     bool first = true;
@@ -360,7 +363,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
 // B for the tensor-core product from nrhs complex64 vectors (x_c at X + c * ld), P = nrhs
 // rounded up to 16 (so the epilogue reads whole 32-column TMEM chunks): rows c < P
 // (Re, -Im) pairs, rows P + c (Im, Re) pairs; rows of absent RHS are zero. TF32: FP32 storage;
-// BF16: round to nearest.
+// BF16 / FP16: round to nearest (the Krylov vectors have unit norm, inside FP16's range).
 template <int kKind>
 __global__ void k_pack_b(const float2* __restrict__ X, int ld, int nrhs, int P, void* __restrict__ B,
                          const int* __restrict__ scal) {
@@ -376,12 +379,18 @@ __global__ void k_pack_b(const float2* __restrict__ X, int ld, int nrhs, int P, 
     b[(size_t)c * Kt + 2 * j + 1] = -x.y;
     b[(size_t)(P + c) * Kt + 2 * j] = x.y;
     b[(size_t)(P + c) * Kt + 2 * j + 1] = x.x;
-  } else {
+  } else if (kKind == 1) {
     __nv_bfloat16* b = static_cast<__nv_bfloat16*>(B);
     b[(size_t)c * Kt + 2 * j] = __float2bfloat16_rn(x.x);
     b[(size_t)c * Kt + 2 * j + 1] = __float2bfloat16_rn(-x.y);
     b[(size_t)(P + c) * Kt + 2 * j] = __float2bfloat16_rn(x.y);
     b[(size_t)(P + c) * Kt + 2 * j + 1] = __float2bfloat16_rn(x.x);
+  } else {
+    __half* b = static_cast<__half*>(B);
+    b[(size_t)c * Kt + 2 * j] = __float2half_rn(x.x);
+    b[(size_t)c * Kt + 2 * j + 1] = __float2half_rn(-x.y);
+    b[(size_t)(P + c) * Kt + 2 * j] = __float2half_rn(x.y);
+    b[(size_t)(P + c) * Kt + 2 * j + 1] = __float2half_rn(x.x);
   }
 }
 
@@ -389,7 +398,8 @@ __global__ void k_pack_b(const float2* __restrict__ X, int ld, int nrhs, int P, 
 // order (the CTAs c_lo..c_hi that covered it, see k_tc_gemm; TM rows per tile), in FP64.
 __global__ void k_tc_reduce(const float* __restrict__ part, int n, int TM, int Ng, int P, int nrhs,
                             int nkb, int per, int msp, double2* __restrict__ Y,
-                            const int* __restrict__ done, const int* __restrict__ scal) {
+                            const int* __restrict__ done, const int* __restrict__ scal,
+                            const float* __restrict__ rs) {
   if (scal && scal[1]) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nrhs * n
   if (i >= (int64_t)nrhs * n) return;
@@ -405,7 +415,8 @@ __global__ void k_tc_reduce(const float* __restrict__ part, int n, int TM, int N
     re += p[(size_t)c * TM + r];
     im += p[(size_t)(P + c) * TM + r];
   }
-  Y[(size_t)c * n + row] = make_double2(re, im);
+  const double sc = rs ? (double)rs[row] : 1.0;  // the FP16 copy's row scale (a power of two)
+  Y[(size_t)c * n + row] = make_double2(re * sc, im * sc);
 }
 
 // ------------------------------------------------------------- FP32 CUDA-core complex GEMM
@@ -651,8 +662,9 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
     NB_CHECK_LAUNCH();
     return NAT_BEM_OK;
   }
-  if (which != 0 || (engine == kEngineBf16 && !op->Lb)) {
-    set_error("tensor-core product needs L (and its BF16 copy for the BF16 engine)");
+  if (which != 0 || ((engine == kEngineBf16 || engine == kEngineFp16) && !op->Lb) ||
+      (engine == kEngineBf16 && op->copy_fp16) || (engine == kEngineFp16 && !op->copy_fp16)) {
+    set_error("tensor-core product needs L (and its BF16 or FP16 copy for those engines)");
     return NAT_BEM_EINVAL;
   }
   int dev = 0, sms = 148;
@@ -683,12 +695,16 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
     const int64_t tot = (int64_t)P * ld;
     if (engine == kEngineTf32)
       NB_LAUNCH("tc_pack", s, k_pack_b<0><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, nrhs, P, B, scal));
-    else
+    else if (engine == kEngineBf16)
       NB_LAUNCH("tc_pack", s, k_pack_b<1><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, nrhs, P, B, scal));
+    else
+      NB_LAUNCH("tc_pack", s, k_pack_b<2><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, nrhs, P, B, scal));
     NB_CHECK_LAUNCH();
   }
   CUtensorMap ta, tb;
-  const CUtensorMapDataType dt = engine == kEngineTf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapDataType dt = engine == kEngineTf32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : engine == kEngineBf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   const void* Aptr = engine == kEngineTf32 ? (const void*)op->L : (const void*)op->Lb;
   NB_TRY(make_map(&ta, dt, Aptr, (uint64_t)Kt, (uint64_t)n, (uint64_t)Kt * esz, (uint32_t)BK, (uint32_t)TM));
   NB_TRY(make_map(&tb, dt, B, (uint64_t)Kt, (uint64_t)Ng, (uint64_t)Kt * esz, (uint32_t)BK, (uint32_t)Ng));
@@ -705,6 +721,8 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
       NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+      NB_TRY_CUDA(cudaFuncSetAttribute(k_tc_gemm<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
       attr_set = true;
     }
   }
@@ -713,15 +731,21 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
       NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0, 2><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
     else
       NB_LAUNCH("tc_gemm_tf32", s, k_tc_gemm<0, 1><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
-  } else {
+  } else if (engine == kEngineBf16) {
     if (sh.tiles == 2)
       NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1, 2><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
     else
       NB_LAUNCH("tc_gemm_bf16", s, k_tc_gemm<1, 1><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+  } else {
+    if (sh.tiles == 2)
+      NB_LAUNCH("tc_gemm_fp16", s, k_tc_gemm<2, 2><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
+    else
+      NB_LAUNCH("tc_gemm_fp16", s, k_tc_gemm<2, 1><<<pl.grid, kTcThreads, smem, s>>>(ta, tb, n, nkb, pl.per, pl.msp, Ng, sh.stages, part, err, scal));
   }
   NB_CHECK_LAUNCH();
   const int64_t tot = (int64_t)nrhs * n;
-  NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, n, TM, Ng, P, nrhs, nkb, pl.per, pl.msp, Y, done, scal));
+  NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      part, n, TM, Ng, P, nrhs, nkb, pl.per, pl.msp, Y, done, scal, engine == kEngineFp16 ? op->row_scale : nullptr));
   NB_CHECK_LAUNCH();
   return NAT_BEM_OK;
 }
@@ -739,7 +763,7 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
 // down); the first candidate wins ties within 2%. X and Y are scratch of the caller.
 nat_bem_status tc_tune(nat_bem_op* op, int engine, int nrhs, const float2* X, double2* Y,
                        void* scratch, size_t scratch_bytes, int* err, cudaStream_t s) {
-  if (engine != kEngineTf32 && engine != kEngineBf16) return NAT_BEM_OK;
+  if (engine != kEngineTf32 && engine != kEngineBf16 && engine != kEngineFp16) return NAT_BEM_OK;
   if (std::getenv("NATBEM_TC_TILES") || std::getenv("NATBEM_TC_CPS")) return NAT_BEM_OK;
   int dev = 0;
   NB_TRY_CUDA(cudaGetDevice(&dev));

@@ -56,6 +56,14 @@ def test_required_bytes(nb):
     assert nb.nat_bem_required_bytes(0, 1) == 0
 
 
+def test_required_bytes_fp16_copy(nb):
+    """The FP16 copy takes the bytes of the BF16 one plus one scale per row."""
+    n = 10240
+    b16 = nb.nat_bem_required_bytes(n, 1, nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16))
+    f16 = nb.nat_bem_required_bytes(n, 1, nb.nat_bem_opts_default(prec=nb.PREC_MIXED_FP16))
+    assert f16 - b16 == 4 * n
+
+
 def test_required_bytes_restart(nb):
     """GMRES(m) keeps m + 1 Krylov vectors instead of max_iter + 1: admission sees the saving.
     A 40k-triangle request with 32 right-hand sides at max_iter = 200 needs 16 n 32 (m + 1)

@@ -180,7 +180,10 @@ def full_size_ref(oracle_lib):
     return prob, get
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "fp16": 3}
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 @pytest.mark.parametrize("ka", [0.5, 5.0, 20.0])
 def test_full_size_interior_source(nb, oracle_lib, full_size_ref, ka, prec):
     """The 10240-triangle interior-source mesh as the bench runs it, in plain FP32 and in the
@@ -191,7 +194,7 @@ def test_full_size_interior_source(nb, oracle_lib, full_size_ref, ka, prec):
     prob, get = full_size_ref
     ref = get(ka)
     V, F, g = prob.V, prob.F, ref["g"]
-    opts = nb.nat_bem_opts_default(prec=nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16)
+    opts = nb.nat_bem_opts_default(prec=PRECS[prec])
     with nb.Operator.assemble(V, F, ka, opts) as op:
         if prec == "fp32":
             Lg = np.concatenate([op.rows(0, int(r), 1) for r in ref["rows"]]).astype(np.complex128)
@@ -199,7 +202,7 @@ def test_full_size_interior_source(nb, oracle_lib, full_size_ref, ka, prec):
             assert np.max(_rowwise(Lg, ref["Lr"])) < OP_TOL and np.max(_rowwise(Rg, ref["Rr"])) < OP_TOL
         p, info, st = op.solve(g)
         assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
-        if prec == "bf16":
+        if prec != "fp32":
             assert info.refinements >= 1
         fld = op.evaluate(prob.points, p, g)
     assert _rel(p, ref["p"]) < SOL_TOL
@@ -234,22 +237,26 @@ def test_modal_multi_rhs_full_size_bf16(nb, oracle_lib):
         assert _rel(fld[:, s], oracle_lib.evaluate(V, F, k, pts, p_ref, G[:, s])) < SOL_TOL
 
 
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
 @pytest.mark.parametrize("ka", [1.0, 12.0])
-def test_mixed_bf16_refinement_matches_oracle(nb, oracle_lib, ka):
-    """Inner GMRES on the BF16 operator copy, refined against the FP32 operator: the same
-    1e-4 bar against the FP64 oracle as the plain path."""
+def test_mixed_bf16_refinement_matches_oracle(nb, oracle_lib, ka, prec):
+    """Inner GMRES on the BF16 (or row-scaled FP16) operator copy, refined against the FP32
+    operator: the same 1e-4 bar against the FP64 oracle as the plain path."""
     Vs, F = S.ring_sphere(2306)
     V = S.perturbed_ellipsoid(Vs, 5)
     g = S.monopole_neumann(V, F, ka)
     G = np.stack([g, S.sh_neumann(V, F, 1, 3)[:, 0]], axis=1)
     pts = S.fibonacci_points(64, 4.0)
     L, R = oracle_lib.assemble(V, F, ka)
-    opts = nb.nat_bem_opts_default(prec=nb.PREC_MIXED_BF16)
+    opts = nb.nat_bem_opts_default(prec=PRECS[prec])
     with nb.Operator.assemble(V, F, ka, opts) as op:
         P, info, st = op.solve(G)
         assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
         assert info.refinements >= 1 and info.rel_residual <= 1e-6
         fld = op.evaluate(pts, P, G)
+        if prec == "fp16":  # one RHS alone takes the FP16 GEMV (two take the tensor cores)
+            p1, info1, st1 = op.solve(G[:, 0])
+            assert st1 == nb.NAT_BEM_OK and _rel(p1, np.linalg.solve(L, R @ G[:, 0])) < SOL_TOL
     for s in range(2):
         p_ref = np.linalg.solve(L, R @ G[:, s])
         assert _rel(P[:, s], p_ref) < SOL_TOL
@@ -372,14 +379,14 @@ def test_run_batch_uneven_meshes_matches_single_solves(nb, oracle_lib, prec):
         assert _rel(r[1], oracle_lib.evaluate(jd["V"], jd["F"], jd["k"], jd["points"], p_ref, jd["neumann"])) < SOL_TOL
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp16"])
 def test_run_batch_fused_uneven_meshes_match_oracle(nb, oracle_lib, prec):
     """The fused batch (size buckets solved in lockstep as padded systems of independent
     operators) on nine meshes of 520-2300 triangles, two sharing a mesh, plus one job with two
     right-hand sides (solved on its own): every job within 1e-4 of the oracle on the surface
     and in the field, and within 1e-5 of the one-at-a-time batch driver. max_batch 3 forces
     several buckets of each size class."""
-    opts = nb.nat_bem_opts_default(prec=nb.PREC_FP32 if prec == "fp32" else nb.PREC_MIXED_BF16)
+    opts = nb.nat_bem_opts_default(prec=PRECS[prec])
     jobs = []
     for i, n_tri in enumerate([520, 560, 610, 1300, 760, 2300, 1100, 990]):
         Vs, F = S.ring_sphere(n_tri)
@@ -480,14 +487,22 @@ def test_tensor_core_products_match_oracle(nb, product_case, nrhs):
     with nb.Operator.assemble(V, F, k, opts) as op:
         Yt = op.apply(0, nb.ENGINE_TF32, Xs)
         Yb = op.apply(0, nb.ENGINE_BF16, Xs)
-    for Y, tol in ((Yt, 2e-3), (Yb, 8e-3)):
+        with pytest.raises(nb.NatBemError):  # no FP16 copy on a BF16 op
+            op.apply(0, nb.ENGINE_FP16, Xs)
+    with nb.Operator.assemble(V, F, k, nb.nat_bem_opts_default(prec=nb.PREC_MIXED_FP16)) as op:
+        Yh = op.apply(0, nb.ENGINE_FP16, Xs)
+        with pytest.raises(nb.NatBemError):
+            op.apply(0, nb.ENGINE_BF16, Xs)
+    # FP16 keeps 11 significant bits (operator rows scaled into its range, x of unit scale):
+    # 2^-11 per factor
+    for Y, tol in ((Yt, 2e-3), (Yb, 8e-3), (Yh, 1.5e-3)):
         err = np.linalg.norm(Y.reshape(len(F), -1) - ref.reshape(len(F), -1), axis=0) / \
             np.linalg.norm(ref.reshape(len(F), -1), axis=0)
         assert np.all(err < tol), (err.max(), tol)
         assert np.all(err > 1e-7)  # really the reduced-precision path
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
 def test_multi_rhs_mixed_tensor_core_solve(nb, oracle_lib, prec):
     """Inner GMRES products on tensor cores, refinement against the FP32 operator: each RHS
     within 1e-4 of the FP64 oracle."""
@@ -496,8 +511,7 @@ def test_multi_rhs_mixed_tensor_core_solve(nb, oracle_lib, prec):
     k = 3.3
     G = S.sh_neumann(V, F, 8, 12)
     L, R = oracle_lib.assemble(V, F, k)
-    p_const = nb.PREC_MIXED_TF32 if prec == "tf32" else nb.PREC_MIXED_BF16
-    opts = nb.nat_bem_opts_default(prec=p_const)
+    opts = nb.nat_bem_opts_default(prec=PRECS[prec])
     with nb.Operator.assemble(V, F, k, opts) as op:
         P, info, st = op.solve(G)
         assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
