@@ -748,21 +748,26 @@ __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
 
 // ------------------------------------------------- fused Krylov step (cooperative launch)
 // Grid barrier for a cooperative launch (every block co-resident): arrival count plus a
-// generation number. Bounded: a wait longer than about two seconds sets err bit 64 and goes on.
+// generation number, with release/acquire atomics at GPU scope instead of full fences: the
+// arrival (acq_rel) publishes the block's writes, which __syncthreads has ordered before it,
+// and the waiters' acquire loads of the new generation make every block's writes visible.
+// Bounded: a wait longer than about two seconds sets err bit 64 and goes on.
 __device__ __forceinline__ void grid_sync(unsigned* count, unsigned* gen, unsigned nblocks, int* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vg = gen;
-    const unsigned g = *vg;
-    __threadfence();
-    if (atomicAdd(count, 1u) == nblocks - 1u) {
-      *count = 0u;
-      __threadfence();
-      atomicAdd(gen, 1u);
+    unsigned g, old;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+    if (old == nblocks - 1u) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(count) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
     } else {
       uint64_t t0, t;
       asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
-      for (unsigned it = 1; *vg == g; ++it) {
+      for (unsigned it = 1;; ++it) {
+        unsigned cur;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+        if (cur != g) break;
         if ((it & 255u) == 0u) {
           asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
           if (t - t0 > 2000000000ull) {
@@ -772,7 +777,6 @@ __device__ __forceinline__ void grid_sync(unsigned* count, unsigned* gen, unsign
         }
       }
     }
-    __threadfence();
   }
   __syncthreads();
 }
