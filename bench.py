@@ -997,9 +997,10 @@ def roofline(res, peaks, peak_kind):
     return dom, table
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of each matvec kernel on the
-# 10240-triangle workload (profiles/k_gemv_interior_source_10240tri.md); None elsewhere.
-NCU_TRAFFIC_10240 = {"gemv": 838.986e6 + 3.255e6, "gemv_bf16": 419.534e6 + 3.466e6}
+# DRAM bytes (read + write) per launch from ncu captures of the BF16 matvec on the current
+# code, mean of six launches, 10240-triangle workload (profiles/k_gemv_interior_source_10240tri.md);
+# None for kernels whose source changed since their capture.
+NCU_TRAFFIC_10240 = {"gemv_bf16": 419.543e6 + 0.66e6}
 
 
 # FP32 operations of k_assemble_regular per (i, j) pair: per quadrature point 29 FMA + 19
