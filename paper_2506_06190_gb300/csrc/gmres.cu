@@ -1468,6 +1468,15 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 8 * nchunk * nrhs;                                            // partial norms
   b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
   if (nrhs > kArnUnitsMinRhs) b += 16 * (m + 2) * (4 * 256 + nrhs);  // multi-RHS unit partials
+  if (nrhs > 1) {  // operand and partial tiles of the multi-RHS products
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      sms = 160;  // no device: an upper bound for current parts
+    }
+    b += (int64_t)tc_workspace_bytes(n, ld, nrhs, sms);
+  }
   return b;
 }
 
@@ -1585,7 +1594,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    ws->tc_bytes = tc_workspace_bytes(n, ld, nrhs, sms);
+    ws->tc_bytes = tc_workspace_bytes(n, std::max<int64_t>(ld, op->ldr), nrhs, sms);  // L and R products
     NB_TRY(dev_alloc(&ws->tc_scratch, ws->tc_bytes, s));
   }
   NB_TRY_CUDA(cudaMemsetAsync(ws->cnt, 0, nr * kCounters * sizeof(unsigned), s));
@@ -2146,7 +2155,7 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
     const int eng = engine == NAT_BEM_ENGINE_TF32 ? kEngineTf32
                     : engine == NAT_BEM_ENGINE_BF16 ? kEngineBf16
                     : engine == NAT_BEM_ENGINE_FP16 ? kEngineFp16 : kEngineFp32;
-    if (eng != kEngineFp32) {
+    {  // tensor-core operand and partial tiles, or the FP32 GEMM's partial tiles
       int dev = 0, sms = 148;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

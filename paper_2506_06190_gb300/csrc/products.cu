@@ -17,9 +17,11 @@
 //    (tcgen05.ld) while the next one fills. Each CTA writes one partial tile per row tile it
 //    touched; k_tc_reduce adds a tile's partials in K order in FP64 (a fixed order, so results
 //    do not depend on timing).
-//  * k_cgemm_fp32: FP32 CUDA-core complex GEMM (64 rows x 32 RHS per block, FP32 products
-//    summed in FP32 over 128 terms, then FP64) for the products that must carry full FP32
-//    accuracy: the right-hand side R G, the refinement residuals and the plain FP32 solve.
+//  * k_cgemm_sk: FP32 CUDA-core complex GEMM (persistent stream-K, 64 rows x up to 64 RHS per
+//    tile, FP32 products summed in FP32 over 128 terms, then carried as float-float pairs) for
+//    the products that must carry full FP32 accuracy: the right-hand side R G, the refinement
+//    residuals and the plain FP32 solve. k_cgemm_fp32 (fixed tiles, FP64 carries) computes the
+//    same product for operators whose leading dimension is not a multiple of 16.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error flag, the kernel
 // skips its remaining work, waits (bounded) for its own copies, frees its TMEM and returns.
@@ -492,6 +494,212 @@ k_cgemm_fp32(const float2* __restrict__ A, int n, int ld, const float2* __restri
     }
 }
 
+// ------------------------------------------- FP32 CUDA-core complex GEMM, stream-K form
+// The same product Y = M X with FP32 products, organised for the FP32 pipe and for GB300's
+// narrow FP64 pipe:
+//  * 256 threads as RG = 256 / CG row groups x CG RHS groups; thread (rg, cg) holds rows
+//    rg + RG i (i < 4) and RHS cg + CG q (q < TN): a block tile of BM = 4 RG rows x BN = CG TN
+//    right-hand sides. A warp spans 32 / CG row groups and CG RHS groups, so its 16-byte
+//    shared loads of A and of X each touch few distinct addresses (broadcasts); CG is chosen
+//    from nrhs so that few columns of a tile are padding;
+//  * K blocks of BK complex terms stream through a ring of shared-memory stages by 16-byte
+//    cp.async copies (rows past n and RHS past nrhs are zero-filled);
+//  * the FP32 sums are folded every 128 terms into a float-float pair by TwoSum (Knuth), so no
+//    FP64 instruction runs inside the loop; a partial is hi + lo in FP64;
+//  * persistent stream-K: the (row tile, RHS tile, K block) space is split into equal
+//    contiguous ranges, one per CTA, so every SM does the same work whatever the tile count;
+//    each CTA writes one FP64 partial tile per tile it touched, and k_cgemm_sk_reduce adds a
+//    tile's partials in CTA order (fixed, so results do not depend on timing).
+// K blocks past the leading dimension ld are zero-filled. ld must be even and A, X 16-byte
+// aligned (every operator this library builds is); otherwise k_cgemm_fp32 runs.
+namespace {
+constexpr int kCgTerms = 128;   // FP32 terms summed before each float-float fold
+constexpr int kCgMinBlocks = 8;  // K blocks per CTA at least
+
+__host__ __device__ constexpr int cg_stage_bytes(int CG, int TN, int BK) {
+  return (4 * (256 / CG) + CG * TN) * (BK + 2) * 8;
+}
+// ring depth: as many stages as fit (at most 4) beside MINB - 1 other CTAs on the SM
+__host__ __device__ constexpr int cg_stages(int CG, int TN, int BK, int MINB) {
+  return (MINB == 2 ? 113 * 1024 : 225 * 1024) / cg_stage_bytes(CG, TN, BK) < 4
+             ? (MINB == 2 ? 113 * 1024 : 225 * 1024) / cg_stage_bytes(CG, TN, BK)
+             : 4;
+}
+
+__device__ __forceinline__ void cg_copy16(float2* dst, const float2* src, bool valid) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cg_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cg_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+// hi + lo += c, exactly up to the rounding of lo (TwoSum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float c) {
+  const float s = __fadd_rn(hi, c);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(c, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+}  // namespace
+
+template <int CG, int TN, int BK, int MINB>
+__global__ void __launch_bounds__(256, MINB)
+k_cgemm_sk(const float2* __restrict__ A, int n, int ld, const float2* __restrict__ X, int nrhs, int ntn,
+           int nkb, int per, int msp, double2* __restrict__ part, const int* __restrict__ scal) {
+  constexpr int RG = 256 / CG, BM = 4 * RG, BN = CG * TN;
+  constexpr int kPitch = BK + 2;  // float2 per shared row: 16-byte loads of 8 rows hit 8 bank groups
+  constexpr int kFlush = kCgTerms / BK;
+  constexpr int S = cg_stages(CG, TN, BK, MINB);
+  constexpr int kStage = (BM + BN) * kPitch;  // float2 per stage
+  static_assert(S >= 2, "shared-memory ring too shallow");
+  extern __shared__ float4 cg_smem[];
+  float2* sm = reinterpret_cast<float2*>(cg_smem);
+  if (scal && scal[1]) return;
+  const int tid = threadIdx.x, cg = tid % CG, rg = tid / CG;
+  const int64_t mt = (n + BM - 1) / BM;
+  const int64_t T = mt * ntn * nkb;
+  const int64_t u0 = (int64_t)blockIdx.x * per, u1 = min(T, u0 + per);
+  if (u0 >= u1) return;
+  const int64_t tile0 = u0 / nkb;
+
+  auto load = [&](int st, int64_t u) {
+    const int64_t tile = u / nkb;
+    const int kb = (int)(u - tile * nkb);
+    const int row0 = (int)(tile / ntn) * BM, rhs0 = (int)(tile % ntn) * BN, k0 = kb * BK;
+    float2* sA = sm + st * kStage;
+    float2* sX = sA + BM * kPitch;
+    constexpr int kPieces = BK / 2;  // 16-byte pieces per row
+#pragma unroll
+    for (int e = tid; e < BM * kPieces; e += 256) {
+      const int r = e / kPieces, c = (e % kPieces) * 2;
+      const bool ok = row0 + r < n && k0 + c < ld;
+      cg_copy16(sA + r * kPitch + c, ok ? A + (size_t)(row0 + r) * ld + k0 + c : A, ok);
+    }
+#pragma unroll
+    for (int e = tid; e < BN * kPieces; e += 256) {
+      const int r = e / kPieces, c = (e % kPieces) * 2;
+      const bool ok = rhs0 + r < nrhs && k0 + c < ld;
+      cg_copy16(sX + r * kPitch + c, ok ? X + (size_t)(rhs0 + r) * ld + k0 + c : X, ok);
+    }
+  };
+
+  float ar[4][TN], ai[4][TN], hr[4][TN], hi_[4][TN], lr[4][TN], li[4][TN];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int q = 0; q < TN; ++q) ar[i][q] = ai[i][q] = hr[i][q] = hi_[i][q] = lr[i][q] = li[i][q] = 0.f;
+
+#pragma unroll
+  for (int p = 0; p < S - 1; ++p) {
+    if (u0 + p < u1) load(p, u0 + p);
+    cg_commit();
+  }
+  int since = 0;  // K blocks summed in FP32 since the last fold
+  for (int64_t u = u0; u < u1; ++u) {
+    const int it = (int)(u - u0);
+    cg_wait<S - 2>();
+    __syncthreads();  // stage it is in; every thread is done with the stage the next copy overwrites
+    if (u + S - 1 < u1) load((it + S - 1) % S, u + S - 1);
+    cg_commit();
+    const float2* sA = sm + (it % S) * kStage;
+    const float2* sX = sA + BM * kPitch;
+#pragma unroll
+    for (int k = 0; k < BK; k += 2) {
+      float4 a[4], x[TN];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(sA + (rg + RG * i) * kPitch + k);
+#pragma unroll
+      for (int q = 0; q < TN; ++q) x[q] = *reinterpret_cast<const float4*>(sX + (cg + CG * q) * kPitch + k);
+      // per accumulator: re -= Im a Im x, re += Re a Re x, im += Im a Re x, im += Re a Im x for
+      // term k, then term k + 1; written pass by pass so dependent FMAs sit far apart
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ar[i][q] = fmaf(-a[i].y, x[q].y, ar[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ai[i][q] = fmaf(a[i].y, x[q].x, ai[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ar[i][q] = fmaf(a[i].x, x[q].x, ar[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ai[i][q] = fmaf(a[i].x, x[q].y, ai[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ar[i][q] = fmaf(-a[i].w, x[q].w, ar[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ai[i][q] = fmaf(a[i].w, x[q].z, ai[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ar[i][q] = fmaf(a[i].z, x[q].z, ar[i][q]);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) ai[i][q] = fmaf(a[i].z, x[q].w, ai[i][q]);
+    }
+    const int64_t tile = u / nkb;
+    const bool seg_end = u + 1 == u1 || (u + 1) % nkb == 0;
+    if (++since == kFlush || seg_end) {
+      since = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) {
+          two_sum_acc(hr[i][q], lr[i][q], ar[i][q]);
+          two_sum_acc(hi_[i][q], li[i][q], ai[i][q]);
+          ar[i][q] = ai[i][q] = 0.f;
+        }
+    }
+    if (seg_end) {
+      double2* p = part + ((size_t)blockIdx.x * msp + (size_t)(tile - tile0)) * BN * BM;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) {
+          p[(size_t)(cg + CG * q) * BM + rg + RG * i] =
+              make_double2((double)hr[i][q] + (double)lr[i][q], (double)hi_[i][q] + (double)li[i][q]);
+          hr[i][q] = hi_[i][q] = lr[i][q] = li[i][q] = 0.f;
+        }
+    }
+  }
+  cg_wait<0>();
+}
+
+// Y[c][row] = the sum, in CTA order, of the partials of the tile holding (row, c)
+__global__ void k_cgemm_sk_reduce(const double2* __restrict__ part, int n, int nrhs, int BM, int BN, int ntn,
+                                  int nkb, int per, int msp, double2* __restrict__ Y,
+                                  const int* __restrict__ done, const int* __restrict__ scal) {
+  if (scal && scal[1]) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over nrhs * n
+  if (i >= (int64_t)nrhs * n) return;
+  const int c = (int)(i / n), row = (int)(i % n);
+  if (done && done[c]) return;
+  const int64_t tile = (int64_t)(row / BM) * ntn + c / BN;
+  const int r = row % BM, cl = c % BN;
+  const int64_t first = tile * nkb, last = first + nkb - 1;
+  const int c_lo = (int)(first / per), c_hi = (int)(last / per);
+  double re = 0.0, im = 0.0;
+  for (int cta = c_lo; cta <= c_hi; ++cta) {
+    const int64_t j = tile - ((int64_t)cta * per) / nkb;
+    const double2 v = part[((size_t)cta * msp + (size_t)j) * BN * BM + (size_t)cl * BM + r];
+    re += v.x;
+    im += v.y;
+  }
+  Y[(size_t)c * n + row] = make_double2(re, im);
+}
+
 // An mbarrier that nothing completes: the bounded wait must give up (result 2) and return.
 __global__ void k_selftest_wait(uint64_t timeout_ns, int* __restrict__ result) {
   __shared__ __align__(8) uint64_t bar;
@@ -633,6 +841,72 @@ TcShape tc_shape(int dev, int64_t n, int Ng, int engine) {
 }
 }  // namespace
 
+namespace {
+// Shapes of k_cgemm_sk: RHS groups, RHS per thread, K block, CTAs per SM. Picked by nrhs so that
+// at most half of a tile's columns are padding; measured on GB300 at 20480 rows (FP32 operator
+// 3.36 GB): 0.60 ms at 1-2 RHS (5.6 TB/s), 0.69 at 3-4, 0.98 at 5-8, 1.62 at 9-16, 2.52 at
+// 17-32, 4.80 at 33-64 (45 TFLOP/s); deeper K blocks paid at every width (fewer barriers and
+// longer runs of each operator row per visit).
+struct CgCfg {
+  int cg, tn, bk, minb;
+};
+constexpr CgCfg kCgCfgs[] = {{16, 4, 64, 1}, {16, 2, 32, 2}, {16, 1, 32, 2},
+                             {8, 1, 64, 1},  {4, 1, 32, 1},  {2, 1, 16, 1}};
+constexpr int kCgNumCfgs = (int)(sizeof(kCgCfgs) / sizeof(kCgCfgs[0]));
+
+int cg_pick(int nrhs) { return nrhs > 32 ? 0 : nrhs > 16 ? 1 : nrhs > 8 ? 2 : nrhs > 4 ? 3 : nrhs > 2 ? 4 : 5; }
+
+// The stream-K partition of k_cgemm_sk: its shape, tile sizes, RHS tile count, K blocks, CTAs,
+// K blocks per CTA, the most tiles one CTA can touch.
+struct CgPlan {
+  int cfg, bm, bn, ntn, nkb, grid, per, msp;
+};
+CgPlan cg_plan(int64_t n, int64_t ld, int nrhs, int sms) {
+  CgPlan p;
+  p.cfg = cg_pick(nrhs);
+  const CgCfg& c = kCgCfgs[p.cfg];
+  p.bm = 4 * (256 / c.cg);
+  p.bn = c.cg * c.tn;
+  p.ntn = (nrhs + p.bn - 1) / p.bn;
+  p.nkb = (int)((ld + c.bk - 1) / c.bk);  // the last K block may run past ld: zero-filled
+  const int64_t T = (n + p.bm - 1) / p.bm * p.ntn * p.nkb;
+  int64_t g = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * c.minb, (T + kCgMinBlocks - 1) / kCgMinBlocks));
+  const int64_t per = (T + g - 1) / g;
+  p.grid = (int)((T + per - 1) / per);
+  p.per = (int)per;
+  p.msp = (int)((per + p.nkb - 1) / p.nkb + 1);
+  return p;
+}
+size_t cg_partial_bytes(const CgPlan& p) { return (size_t)p.grid * p.msp * p.bn * p.bm * sizeof(double2); }
+
+template <int CFG>
+nat_bem_status cg_launch(const char* nm, const float2* M, int n, int ld, const float2* X, int nrhs,
+                         const CgPlan& cp, double2* part, const int* scal, cudaStream_t s) {
+  constexpr CgCfg c = kCgCfgs[CFG];
+  constexpr int smem = cg_stages(c.cg, c.tn, c.bk, c.minb) * cg_stage_bytes(c.cg, c.tn, c.bk);
+  static const cudaError_t ae =
+      cudaFuncSetAttribute(k_cgemm_sk<c.cg, c.tn, c.bk, c.minb>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (ae != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ae));
+    return NAT_BEM_ECUDA;
+  }
+  NB_LAUNCH(nm, s, k_cgemm_sk<c.cg, c.tn, c.bk, c.minb><<<cp.grid, 256, smem, s>>>(
+                       M, n, ld, X, nrhs, cp.ntn, cp.nkb, cp.per, cp.msp, part, scal));
+  return NAT_BEM_OK;
+}
+
+template <int CFG = 0>
+nat_bem_status cg_dispatch(int cfg, const char* nm, const float2* M, int n, int ld, const float2* X, int nrhs,
+                           const CgPlan& cp, double2* part, const int* scal, cudaStream_t s) {
+  if constexpr (CFG < kCgNumCfgs) {
+    if (cfg == CFG) return cg_launch<CFG>(nm, M, n, ld, X, nrhs, cp, part, scal, s);
+    return cg_dispatch<CFG + 1>(cfg, nm, M, n, ld, X, nrhs, cp, part, scal, s);
+  }
+  set_error("no such FP32 GEMM shape");
+  return NAT_BEM_EINVAL;
+}
+}  // namespace
+
 size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
   const int P = (int)round_up(nrhs, 16);  // N = 2P is a multiple of 32: whole TMEM loads
   const int Ng = 2 * P;
@@ -646,7 +920,8 @@ size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
         const TcPlan pl = tc_plan(n, tm, (Kt + bk - 1) / bk, cps * sms);
         floats = std::max(floats, (size_t)pl.grid * pl.msp * (size_t)tm);
       }
-  return round_up((size_t)Ng * Kt * 4, 256) + floats * Ng * 4 + 64;
+  const size_t tc = round_up((size_t)Ng * Kt * 4, 256) + floats * Ng * 4 + 64;
+  return std::max(tc, cg_partial_bytes(cg_plan(n, ld, nrhs, sms)) + 64);
 }
 
 static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
@@ -655,7 +930,23 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
                                      const TcShape* force) {
   const int n = (int)op->n, ld = which == 1 ? (int)op->ldr : (int)op->geo.ld;
   const float2* M = which == 0 ? op->L : op->R;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (engine == kEngineFp32) {
+    const CgPlan cp = cg_plan(n, ld, nrhs, sms);
+    const bool aligned = ld % 2 == 0 && ((uintptr_t)M & 15u) == 0 && ((uintptr_t)X & 15u) == 0 &&
+                         ((uintptr_t)scratch & 15u) == 0;
+    if (aligned && scratch && cg_partial_bytes(cp) <= scratch_bytes && !std::getenv("NATBEM_CGEMM_TILED")) {
+      double2* part = static_cast<double2*>(scratch);
+      NB_TRY(cg_dispatch(cp.cfg, which == 0 ? "cgemm_fp32_L" : "cgemm_fp32_R", M, n, ld, X, nrhs, cp, part, scal, s));
+      NB_CHECK_LAUNCH();
+      const int64_t tot = (int64_t)nrhs * n;
+      NB_LAUNCH("cgemm_reduce", s, k_cgemm_sk_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+          part, n, nrhs, cp.bm, cp.bn, cp.ntn, cp.nkb, cp.per, cp.msp, Y, done, scal));
+      NB_CHECK_LAUNCH();
+      return NAT_BEM_OK;
+    }
     dim3 grid((n + kGmRows - 1) / kGmRows, (nrhs + kGmRhs - 1) / kGmRhs);
     NB_LAUNCH(which == 0 ? "cgemm_fp32_L" : "cgemm_fp32_R", s,
               k_cgemm_fp32<<<grid, 256, 0, s>>>(M, n, ld, X, nrhs, Y, done, scal));
@@ -667,9 +958,6 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
     set_error("tensor-core product needs L (and its BF16 or FP16 copy for those engines)");
     return NAT_BEM_EINVAL;
   }
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int P = (int)round_up(nrhs, 16);  // N = 2P is a multiple of 32: whole TMEM loads
   const int Ng = 2 * P;
   if (Ng > 256) {

@@ -463,7 +463,7 @@ def test_gemv_variants_match_oracle(nb, product_case, variant):
             assert _rel(y, M @ x.astype(np.complex128)) < 1e-5
 
 
-@pytest.mark.parametrize("nrhs", [1, 6, 40])
+@pytest.mark.parametrize("nrhs", [1, 6, 17, 40, 64, 100])
 def test_fp32_gemm_matches_oracle(nb, product_case, nrhs):
     V, F, k, L, R, X = product_case
     Xs = np.asfortranarray(X[:, :nrhs])
@@ -473,6 +473,32 @@ def test_fp32_gemm_matches_oracle(nb, product_case, nrhs):
             ref = M @ Xs.astype(np.complex128)
             assert _rel(Y, ref) < 1e-5
             assert np.max(np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)) < 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [2, 17, 64, 100])
+def test_fp32_gemm_carries_fp32_accuracy(nb, product_case, nrhs, monkeypatch):
+    """Both FP32 GEMM kernels (stream-K with float-float carries, and the fixed-tile one with
+    FP64 carries, NATBEM_CGEMM_TILED=1) against an FP64 product of the same FP32 operator
+    entries: every column within 1e-6 (FP32 products summed in FP32 over 128 terms: about
+    2e-7 on this case), and the two kernels within 1e-6 of each other."""
+    V, F, k, L, R, X = product_case
+    Xs = np.asfortranarray(X[:, :nrhs])
+    with nb.Operator.assemble(V, F, k) as op:
+        for which in (0, 1):
+            M = op.rows(which, 0, op.n).astype(np.complex128)
+            ref = M @ Xs.astype(np.complex128)
+            ys = []
+            for tiled in (False, True):
+                if tiled:
+                    monkeypatch.setenv("NATBEM_CGEMM_TILED", "1")
+                else:
+                    monkeypatch.delenv("NATBEM_CGEMM_TILED", raising=False)
+                Y = op.apply(which, nb.ENGINE_FP32, Xs)
+                err = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
+                assert err.max() < 1e-6, (tiled, err.max())
+                ys.append(Y)
+            monkeypatch.delenv("NATBEM_CGEMM_TILED", raising=False)
+            assert _rel(ys[0], ys[1]) < 1e-6
 
 
 @pytest.mark.parametrize("nrhs", [1, 6, 40, 64, 100])
