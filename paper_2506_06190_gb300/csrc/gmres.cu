@@ -58,13 +58,16 @@ struct Workspace {
   double2 *pblk = nullptr, *hred = nullptr;                // fused kernel: block partials, totals
   int arn_smem = 0;                                        // fused kernel: dynamic shared bytes
   double2* pbu = nullptr;                                  // multi-RHS fused kernel: unit partials
-  // captured iteration chunks: key (engine, first iteration, count, cap, tol, mode bits:
-  // 1 skip flags, 2 accumulate, 4 tolerance relative to ||R g||)
-  std::map<std::tuple<int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
+  float2* wf = nullptr;                                    // multi-RHS fused kernel: FP32 w
+  // captured iteration chunks: key (engine, RHS count, first iteration, count, cap, tol, mode
+  // bits: 1 skip flags, 2 accumulate, 4 tolerance relative to ||R g||). The RHS count is part
+  // of the key: a workspace serves later solves with fewer columns, and a graph holds the
+  // launch shapes and arguments of the count it was captured with.
+  std::map<std::tuple<int, int, int, int, int, double, int>, std::pair<cudaGraphExec_t, int64_t>> graphs;
   bool graphs_off = false;
   // whole GMRES runs on the device: a graph whose conditional while node repeats a captured
-  // chunk of iterations until every RHS is done; key (engine, cap, tol, mode bits)
-  std::map<std::tuple<int, int, double, int>, cudaGraphExec_t> loops;
+  // chunk of iterations until every RHS is done; key (engine, RHS count, cap, tol, mode bits)
+  std::map<std::tuple<int, int, int, double, int>, cudaGraphExec_t> loops;
   bool loops_off = false;
   unsigned long long* loop_launches = nullptr;  // kernels the loop bodies ran (device counter)
   int* loop_bodies = nullptr;                    // bodies the current loop ran (reset per run)
@@ -86,6 +89,9 @@ struct GArgs {
   double2 *b, *V, *w, *x, *H, *hcol, *htmp, *sn, *gv, *y, *part;
   double *cs, *partn, *bnorm, *res, *hnorm, *res_true;
   float2* xf;
+  // FP32 Krylov basis (same layout as V, in V's memory) and FP32 copy of w, used by inner
+  // solves of refinement on the multi-RHS fused kernel; Vf null: the FP64 basis V
+  float2 *Vf, *wf;
   int *done, *iters, *scal;
   unsigned* cnt;
   double tol;
@@ -704,8 +710,12 @@ __global__ void __launch_bounds__(256) k_finish(GArgs a, int mode) {
     const double inv = 1.0 / hn;
     const double2 ww = a.w[(size_t)s * a.n + r];
     const double2 v = make_double2(ww.x * inv, ww.y * inv);
-    a.V[vidx(a, jt, s) + r] = v;
-    a.xf[(size_t)s * a.ld + r] = make_float2((float)v.x, (float)v.y);
+    const float2 vf = make_float2((float)v.x, (float)v.y);
+    if (a.Vf)
+      a.Vf[vidx(a, jt, s) + r] = vf;
+    else
+      a.V[vidx(a, jt, s) + r] = v;
+    a.xf[(size_t)s * a.ld + r] = vf;
   }
   if (!last_block(a.cnt + s * kCounters + 0, gridDim.x)) return;
   if (mode == 1 && active) {
@@ -1164,9 +1174,15 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
 // every block takes the decisions for every RHS from the totals (so all blocks agree on the
 // barrier count), then updates its units' rows, and the owner of chunk 0 of an RHS applies
 // its Givens rotation. Same arithmetic and second-pass test as k_arnoldi.
+// kF32: the FP32 basis of inner refinement solves (a.Vf, a.wf): the dots and the row updates
+// run in FP32 (lane sums in FP32, unit and chunk totals, Hessenberg column and rotations in
+// FP64), so the loop over the basis uses no FP64 instruction and reads half the bytes. An inner
+// solve stops at a relative residual of 1e-2, far above the FP32 basis' loss of orthogonality.
+template <bool kF32>
 __global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restrict__ pbu, double2* __restrict__ hr,
                                                        unsigned* __restrict__ bar, int* __restrict__ err,
                                                        int unit, int cps) {
+  __shared__ float2 s_hf[256];
   __shared__ double2 s_h[256];
   __shared__ double2 s_acc[256];
   __shared__ double2 s_sn[256];
@@ -1188,6 +1204,66 @@ __global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restr
     bool any = false;
     for (int q = 0; q < a.nrhs; ++q) any |= (s_act[q] >= want);
     if (!any) break;
+    if constexpr (kF32) {
+      // FP32 copy of this block's rows of w = L v_j (the second pass reads the w - V h that
+      // the first pass left there)
+      if (pass == 0) {
+        for (int u = b; u < nunits; u += G) {
+          const int s = u / cps, chunk = u % cps;
+          if (s_act[s] < want) continue;
+          const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
+          for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
+            const double2 ww = a.w[(size_t)s * a.n + r];
+            a.wf[(size_t)s * a.n + r] = make_float2((float)ww.x, (float)ww.y);
+          }
+        }
+      }
+      __syncthreads();
+      for (int u = b; u < nunits; u += G) {
+        const int s = u / cps, chunk = u % cps;
+        if (s_act[s] < want) continue;
+        const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
+        const float2* w = a.wf + (size_t)s * a.n;
+        for (int c = warp; c < np; c += 8) {
+          float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+          if (c <= j) {
+            const float2* v = a.Vf + vidx(a, c, s);
+            for (int r = q0 + lane; r < q1; r += 128) {
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const int rr = r + 32 * t;
+                if (rr < q1) {
+                  const float2 vv = v[rr], ww = w[rr];
+                  re[t] = fmaf(vv.x, ww.x, re[t]);
+                  re[t] = fmaf(vv.y, ww.y, re[t]);
+                  im[t] = fmaf(vv.x, ww.y, im[t]);
+                  im[t] = fmaf(-vv.y, ww.x, im[t]);
+                }
+              }
+            }
+          } else {
+            for (int r = q0 + lane; r < q1; r += 128) {
+#pragma unroll
+              for (int t = 0; t < 4; ++t) {
+                const int rr = r + 32 * t;
+                if (rr < q1) {
+                  const float2 ww = w[rr];
+                  re[t] = fmaf(ww.x, ww.x, re[t]);
+                  re[t] = fmaf(ww.y, ww.y, re[t]);
+                }
+              }
+            }
+          }
+          float sr = (re[0] + re[1]) + (re[2] + re[3]), si = (im[0] + im[1]) + (im[2] + im[3]);
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+          }
+          if (lane == 0) pbu[((size_t)s * ps + c) * cps + chunk] = make_double2((double)sr, (double)si);
+        }
+      }
+    } else {
     // (A) partial sums over each unit's rows
     for (int u = b; u < nunits; u += G) {
       const int s = u / cps, chunk = u % cps;
@@ -1229,6 +1305,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restr
         si = warp_sum(si);
         if (lane == 0) pbu[((size_t)s * ps + c) * cps + chunk] = make_double2(sr, si);
       }
+    }
     }
     grid_sync(bar, bar + 1, G, err);
     // (R) totals over the chunks, one thread per (RHS, column)
@@ -1272,9 +1349,47 @@ __global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restr
       const bool last = hn >= 0.0;
       const double2* hs = hr + (size_t)s * ps;
       __syncthreads();
-      for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = hs[c];
+      for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+        s_h[c] = hs[c];
+        if constexpr (kF32) s_hf[c] = make_float2((float)hs[c].x, (float)hs[c].y);
+      }
       __syncthreads();
       const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
+      if constexpr (kF32) {
+        const float finv = (float)inv;
+        for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
+          float2 acc[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                           make_float2(0.f, 0.f)};
+          int c = 0;
+          for (; c + 4 <= j + 1; c += 4) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              const float2 vv = a.Vf[vidx(a, c + t, s) + r], h = s_hf[c + t];
+              acc[t].x = fmaf(vv.x, h.x, acc[t].x);
+              acc[t].x = fmaf(-vv.y, h.y, acc[t].x);
+              acc[t].y = fmaf(vv.x, h.y, acc[t].y);
+              acc[t].y = fmaf(vv.y, h.x, acc[t].y);
+            }
+          }
+          for (; c <= j; ++c) {
+            const float2 vv = a.Vf[vidx(a, c, s) + r], h = s_hf[c];
+            acc[0].x = fmaf(vv.x, h.x, acc[0].x);
+            acc[0].x = fmaf(-vv.y, h.y, acc[0].x);
+            acc[0].y = fmaf(vv.x, h.y, acc[0].y);
+            acc[0].y = fmaf(vv.y, h.x, acc[0].y);
+          }
+          const float2 ww = a.wf[(size_t)s * a.n + r];
+          const float2 wv = make_float2(ww.x - ((acc[0].x + acc[1].x) + (acc[2].x + acc[3].x)),
+                                        ww.y - ((acc[0].y + acc[1].y) + (acc[2].y + acc[3].y)));
+          if (!last) {
+            a.wf[(size_t)s * a.n + r] = wv;
+          } else if (hn > 0.0) {
+            const float2 v = make_float2(wv.x * finv, wv.y * finv);
+            a.Vf[vidx(a, j + 1, s) + r] = v;
+            a.xf[(size_t)s * a.ld + r] = v;
+          }
+        }
+      } else
       for (int r = q0 + threadIdx.x; r < q1; r += blockDim.x) {
         double2 acc[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
                           make_double2(0.0, 0.0)};
@@ -1374,14 +1489,30 @@ __global__ void __launch_bounds__(256) k_lsq(GArgs a) {
 
 // x = V y (FP64), or x += V y when `accumulate` (refinement), with the complex64 output and
 // the FP32 copy of x for the residual matvec.
+// With the FP32 basis the correction V y is formed in FP32 (y staged once per block as FP32)
+// and added to x in FP64: an inner solve's correction needs far less than FP32 accuracy.
 __global__ void __launch_bounds__(kChunk) k_xupdate(GArgs a, float2* __restrict__ pout, int accumulate) {
+  __shared__ float2 s_y[256];
   const int s = blockIdx.y;
   const int r = blockIdx.x * kChunk + threadIdx.x;
-  if (r >= a.n) return;
   const int kdim = (a.skip && a.skip[s]) ? 0 : a.iters[s];
   const double2* y = a.y + (size_t)s * a.m;
+  if (a.Vf) {
+    for (int c = threadIdx.x; c < kdim; c += blockDim.x) s_y[c] = make_float2((float)y[c].x, (float)y[c].y);
+    __syncthreads();
+  }
+  if (r >= a.n) return;
   double2 acc = accumulate ? a.x[(size_t)s * a.n + r] : make_double2(0.0, 0.0);
-  for (int c = 0; c < kdim; ++c) acc = cadd(acc, cmul(a.V[vidx(a, c, s) + r], y[c]));
+  if (a.Vf) {
+    float dr = 0.f, di = 0.f;
+    for (int c = 0; c < kdim; ++c) {
+      const float2 v = a.Vf[vidx(a, c, s) + r], h = s_y[c];
+      dr = fmaf(v.x, h.x, fmaf(-v.y, h.y, dr));
+      di = fmaf(v.x, h.y, fmaf(v.y, h.x, di));
+    }
+    acc = make_double2(acc.x + (double)dr, acc.y + (double)di);
+  }
+  for (int c = 0; c < (a.Vf ? 0 : kdim); ++c) acc = cadd(acc, cmul(a.V[vidx(a, c, s) + r], y[c]));
   a.x[(size_t)s * a.n + r] = acc;
   pout[(size_t)s * a.n + r] = make_float2((float)acc.x, (float)acc.y);
   a.xf[(size_t)s * a.ld + r] = make_float2((float)acc.x, (float)acc.y);
@@ -1467,7 +1598,7 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
   b += 8 * nchunk * nrhs;                                            // partial norms
   b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
-  if (nrhs > kArnUnitsMinRhs) b += 16 * (m + 2) * (4 * 256 + nrhs);  // multi-RHS unit partials
+  if (nrhs > kArnUnitsMinRhs) b += 16 * (m + 2) * (4 * 256 + nrhs) + 8 * n * nrhs;  // unit partials, FP32 w
   if (nrhs > 1) {  // operand and partial tiles of the multi-RHS products
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1486,7 +1617,7 @@ void workspace_free(Workspace* ws, cudaStream_t s) {
                   ws->part, ws->cs, ws->partn, ws->bnorm, ws->res, ws->hnorm, ws->res_true,
                   ws->xf, ws->gin, ws->pout, ws->done, ws->iters, ws->scal, ws->cnt,
                   ws->b0, ws->xacc, ws->b0norm, ws->outer_done, ws->tc_scratch, ws->tc_err, ws->gbar,
-                  ws->pblk, ws->hred, ws->pbu};
+                  ws->pblk, ws->hred, ws->pbu, ws->wf};
   for (void* p : ptrs)
     if (p) dev_free(p, s);
   if (ws->host_scal) cudaFreeHost(ws->host_scal);
@@ -1586,6 +1717,7 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
           most = std::max(most, (size_t)q * (size_t)((n + u - 1) / u));
         }
         NB_TRY(dev_alloc_n(&ws->pbu, most * (mm + 2), s));
+        NB_TRY(dev_alloc_n(&ws->wf, (size_t)n * nr, s));
       }
     }
   }
@@ -1640,6 +1772,8 @@ static GArgs make_args(nat_bem_op* op, Workspace* ws, const float2* Lop) {
   a.maxit = ws->m;
   a.skip = nullptr;
   a.bscale = nullptr;
+  a.Vf = nullptr;
+  a.wf = ws->wf;
   return a;
 }
 
@@ -1992,7 +2126,8 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
           int unit = arnoldi_unit(n, nrhs, ws->coop_blocks);
           int cps = (n + unit - 1) / unit;
           void* args[] = {&ac, &pu, &hr, &bar, &errp, &unit, &cps};
-          NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_units, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
+          const void* kern = ac.Vf ? (const void*)k_arnoldi_units<true> : (const void*)k_arnoldi_units<false>;
+          NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
           continue;
         }
         int pcap = ws->arn_smem / (int)sizeof(double2);
@@ -2015,7 +2150,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
   // reads the results.
   static const bool loop_env_off = std::getenv("NATBEM_NO_DEVICE_LOOP") != nullptr;
   if (use_graphs && !loop_env_off && op->opts.device_loop && !ws->loops_off && ws->coop_blocks > 0) {
-    const auto key = std::make_tuple(engine, a.maxit, a.tol,
+    const auto key = std::make_tuple(engine, a.nrhs, a.maxit, a.tol,
                                      (a.skip ? 1 : 0) + (accumulate ? 2 : 0) + (a.bscale ? 4 : 0));
     auto f = ws->loops.find(key);
     if (f == ws->loops.end()) {
@@ -2072,7 +2207,7 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
     const int c = std::min(chunk, a.maxit - it);
     bool done_direct = true;
     if (use_graphs) {
-      const auto key = std::make_tuple(engine, it, c, a.maxit, a.tol,
+      const auto key = std::make_tuple(engine, a.nrhs, it, c, a.maxit, a.tol,
                                        (a.skip ? 1 : 0) + (accumulate ? 2 : 0) + (a.bscale ? 4 : 0));
       auto f = ws->graphs.find(key);
       if (f == ws->graphs.end()) {
@@ -2305,10 +2440,17 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     if (mixed) {
       // Mixed precision iterative refinement: inner GMRES on the BF16 copy of L (or the
       // tensor-core products) to inner_tol relative to the current residual.
+      // Inner solves on the multi-RHS fused Arnoldi kernel keep an FP32 Krylov basis (in V's
+      // memory) and an FP32 copy of w: GB300's FP64 pipe made the FP64 Gram-Schmidt the
+      // largest cost of these solves, and they stop at 1e-2.
+      static const bool fp64_basis = std::getenv("NATBEM_FP64_BASIS") != nullptr;
+      const bool fp32_basis = !fp64_basis && nrhs > kArnUnitsMinRhs && ws->coop_blocks > 0 && ws->pbu && ws->wf;
       a.tol = o.inner_tol;
       for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
         a.maxit = std::min(std::min(o.inner_max_iter, budget), ws->m);
+        a.Vf = fp32_basis ? reinterpret_cast<float2*>(ws->V) : nullptr;
         NB_TRY(sweep_once(inner));
+        a.Vf = nullptr;
         if (converged) break;
         // A sweep that shrank some residual by less than 10x (the low-precision operator's
         // error is comparable to the inner tolerance: high k, ill-conditioned L) or that used

@@ -119,6 +119,25 @@ def test_multi_rhs_matches_oracle_and_single(nb, oracle_lib):
             assert _rel(p1, P[:, s]) < 1e-5
 
 
+@pytest.mark.parametrize("device_loop", [1, 0])
+def test_fewer_columns_on_a_reused_workspace(nb, device_loop):
+    """A solve with 6 RHS, then one with 5 and one with 3 of them on the same operator (its
+    workspace and captured graphs are reused): each result has the bits of the same columns
+    solved on a fresh operator, with the device-side loop and with host-polled chunks."""
+    Vs, F = S.ring_sphere(900)
+    V = S.perturbed_ellipsoid(Vs, 11)
+    G = S.sh_neumann(V, F, 6, 12)
+    opts = nb.nat_bem_opts_default(device_loop=device_loop)
+    with nb.Operator.assemble(V, F, 2.7, opts) as op:
+        for cols in (6, 5, 3):
+            p, info, st = op.solve(np.asfortranarray(G[:, :cols]))
+            assert st == nb.NAT_BEM_OK
+            with nb.Operator.assemble(V, F, 2.7, opts) as fresh:
+                p1, info1, st1 = fresh.solve(np.asfortranarray(G[:, :cols]))
+            assert st1 == nb.NAT_BEM_OK and info.iterations == info1.iterations
+            assert np.array_equal(p, p1), cols
+
+
 def test_device_pointers_match_host(nb):
     import torch
     V, F = S.icosphere(2)
@@ -600,3 +619,59 @@ def test_device_loop_matches_host_polled_chunks(tmp_path):
         assert r.returncode == 0, r.stderr[-2000:]
         outs.append(np.load(f))
     assert np.array_equal(outs[0], outs[1])
+
+
+_BASIS_CHILD = r"""
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+import synthetic as S, paper_2506_06190_gb300 as nb
+Vs, F = S.ring_sphere(1200)
+V = S.perturbed_ellipsoid(Vs, 8)
+out, its = [], []
+for k, prec in ((3.3, nb.PREC_MIXED_BF16), (3.3, nb.PREC_MIXED_TF32), (14.0, nb.PREC_MIXED_BF16)):
+    G = S.sh_neumann(V, F, 8, 12)
+    with nb.Operator.assemble(V, F, k, nb.nat_bem_opts_default(prec=prec)) as op:
+        P, info, st = op.solve(G)
+        assert st == nb.NAT_BEM_OK and info.rel_residual <= 1e-6, (st, info.rel_residual)
+        out.append(P.ravel(order="F"))
+        its.append(info.iterations)
+np.save(sys.argv[2], np.concatenate(out))
+np.save(sys.argv[2] + ".its.npy", np.array(its))
+"""
+
+
+def test_fp32_krylov_basis_matches_fp64_basis_and_oracle(tmp_path, oracle_lib):
+    """Inner refinement solves with 8 RHS run the fused Arnoldi kernel on an FP32 basis; with
+    NATBEM_FP64_BASIS=1 they keep the FP64 one. Both reach the 1e-6 true residual, every RHS
+    within 1e-4 of the FP64 oracle, the two within 1e-5 of each other, at ka 3.3 (BF16 and TF32
+    products) and 14 (BF16 sweeps that hand over to FP32)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs, its = [], []
+    for fp64 in (False, True):
+        env = dict(os.environ)
+        env.pop("NATBEM_FP64_BASIS", None)
+        if fp64:
+            env["NATBEM_FP64_BASIS"] = "1"
+        f = str(tmp_path / f"b{int(fp64)}.npy")
+        r = subprocess.run([sys.executable, "-c", _BASIS_CHILD, root, f], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        outs.append(np.load(f))
+        its.append(np.load(f + ".its.npy"))
+    Vs, F = S.ring_sphere(1200)
+    V = S.perturbed_ellipsoid(Vs, 8)
+    G = S.sh_neumann(V, F, 8, 12)
+    n = len(F)
+    for case, k in enumerate((3.3, 3.3, 14.0)):
+        L, R = oracle_lib.assemble(V, F, k)
+        Pref = np.linalg.solve(L, R @ G)
+        for o in outs:
+            P = o[case * 8 * n:(case + 1) * 8 * n].reshape(n, 8, order="F")
+            for s in range(8):
+                assert _rel(P[:, s], Pref[:, s]) < SOL_TOL
+        assert _rel(outs[0][case * 8 * n:(case + 1) * 8 * n], outs[1][case * 8 * n:(case + 1) * 8 * n]) < 1e-5
+    assert np.all(its[0] <= its[1] + 8), (its[0], its[1])
+
