@@ -392,6 +392,50 @@ def run_modal(args):
 NCU_TRAFFIC_MODAL_20480 = {"bf16": 1.7233e9 + 11.57e6}
 
 
+def run_products(args):
+    """The multi-RHS operator products alone (profiling and launch-shape sweeps): Y = L X for
+    --nrhs seeded complex64 columns on a ring-sphere mesh of --n-tri triangles (default 20480),
+    with the FP32 CUDA-core GEMM (--prec fp32) or the tensor-core product (bf16, tf32, fp16).
+    --warmup products, then --steps products timed from the library's launch trace."""
+    import torch
+    import paper_2506_06190_gb300 as nb
+    from paper_2506_06190_gb300 import build as nb_build
+    nb_build.build()
+    Vs, F = S.ring_sphere(args.n_tri)
+    V = S.perturbed_ellipsoid(Vs, 3000)
+    prec = {"fp32": nb.PREC_FP32, "bf16": nb.PREC_MIXED_BF16, "tf32": nb.PREC_MIXED_TF32,
+            "fp16": nb.PREC_MIXED_FP16}[args.prec]
+    engine = {"fp32": nb.ENGINE_FP32, "bf16": nb.ENGINE_BF16, "tf32": nb.ENGINE_TF32, "fp16": nb.ENGINE_FP16}[args.prec]
+    rng = np.random.default_rng(3004)
+    with nb.Operator.assemble(V, F, 4.0, nb.nat_bem_opts_default(prec=prec)) as op:
+        n = op.n
+        ld = (n + 31) // 32 * 32
+        X = np.asfortranarray((rng.normal(size=(n, args.nrhs)) + 1j * rng.normal(size=(n, args.nrhs)))
+                              .astype(np.complex64))
+        for _ in range(args.warmup):
+            op.apply(0, engine, X)
+        torch.cuda.synchronize()
+        nb.nat_bem_trace_enable(True)
+        nb.nat_bem_trace_select("")
+        nb.nat_bem_trace_reset()
+        for _ in range(args.steps):
+            op.apply(0, engine, X)
+        torch.cuda.synchronize()
+        name = "cgemm_fp32" if args.prec == "fp32" else "tc_gemm"
+        t, c = nb.nat_bem_trace_kernel(name)
+        tr, cr = nb.nat_bem_trace_kernel("cgemm_reduce" if args.prec == "fp32" else "tc_reduce")
+        nb.nat_bem_trace_enable(False)
+    ms = t / max(c, 1)
+    op_bytes = (8 if args.prec in ("fp32", "tf32") else 4) * n * ld
+    peaks, _ = _peaks()
+    return {"metric": "multi-RHS operator products per second", "value": 1e3 / ms, "unit": "products/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": f"products_{n}tri_{args.nrhs}rhs", "engine": args.prec},
+            "ms_per_product": ms, "reduce_ms": tr / max(cr, 1), "tflops": 8.0 * n * ld * args.nrhs / ms / 1e9,
+            "operator_gbs": op_bytes / ms / 1e6, "hbm_frac": op_bytes / ms / 1e6 / peaks["hbm_gbs"]}
+
+
 def run_mc(args):
     """Monte-Carlo BEM (paper Sec. 4.1.1, 4.2): the interior-source body sampled by the GPU
     Poisson-disk sampler (8 x --n-samples draws at 0.7 of the hexagonal spacing of --n-samples
@@ -1086,7 +1130,8 @@ def main():
     ap.add_argument("--n-k", type=int, default=64)
     ap.add_argument("--n-tri", type=int, default=10240, help="smaller meshes only for profiling")
     ap.add_argument("--concurrency", type=int, default=4, help="solves in flight (batch workers)")
-    ap.add_argument("--workload", default="interior", choices=["interior", "modal", "uneven", "serve", "mc", "dataset", "nat", "galerkin"])
+    ap.add_argument("--workload", default="interior",
+                    choices=["interior", "modal", "uneven", "serve", "mc", "dataset", "nat", "galerkin", "products"])
     ap.add_argument("--n-samples", type=int, default=4096, help="Monte-Carlo workload: surface samples")
     ap.add_argument("--random-samples", action="store_true", help="Monte-Carlo workload: uniform random samples")
     ap.add_argument("--n-queries", type=int, default=1 << 22, help="NAT inference workload: queries per step")
@@ -1143,7 +1188,10 @@ def main():
     if args.workload != "interior":
         if rank == 0:
             fn = {"modal": run_modal, "uneven": run_uneven, "serve": run_serving, "mc": run_mc,
-                  "dataset": run_dataset, "nat": run_nat, "galerkin": run_galerkin}[args.workload]
+                  "dataset": run_dataset, "nat": run_nat, "galerkin": run_galerkin,
+                  "products": run_products}[args.workload]
+            if args.workload == "products" and args.n_tri == 10240:
+                args.n_tri = 20480
             if args.workload == "modal" and args.n_k == 64:
                 args.n_k = 16
             if args.workload == "modal" and args.n_tri == 10240:
