@@ -225,7 +225,10 @@ NAT_BEM_API nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cu
  * ||R g||, within max_iter iterations in all. Mixed: the true
  * residual reaches tol after a refinement sweep; when a sweep shrinks a residual by less than
  * 10x, or the sweeps or max_iter inner iterations are spent, one final solve of the correction
- * equation on the FP32 operator (its own max_iter) finishes by the plain criterion.
+ * equation on the FP32 operator (its own max_iter) finishes by the plain criterion. A sweep
+ * that shrinks a residual by less than 10x with every unconverged true residual within 4 tol
+ * ends the solve (the rounding floor of the FP32 residual product; info->rel_residual then
+ * reports a value in (tol, 4 tol]).
  * NAT_BEM_EINVAL: op NULL, nrhs < 1, NULL arrays.
  * NAT_BEM_ENOCONV: the tolerance was not met within the iteration limit; p_out holds the
  * best iterate and info is filled.
