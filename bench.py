@@ -421,18 +421,29 @@ def run_products(args):
         for _ in range(args.steps):
             op.apply(0, engine, X)
         torch.cuda.synchronize()
-        name = "cgemm_fp32" if args.prec == "fp32" else "tc_gemm"
-        t, c = nb.nat_bem_trace_kernel(name)
-        tr, cr = nb.nat_bem_trace_kernel("cgemm_reduce" if args.prec == "fp32" else "tc_reduce")
+        # the FP32-accurate product runs on the split tensor-core kernel from 8 RHS (L only),
+        # else on the CUDA-core GEMM
+        names = ["tc_gemm_x6", "cgemm_fp32"] if args.prec == "fp32" else ["tc_gemm"]
+        for name in names:
+            t, c = nb.nat_bem_trace_kernel(name)
+            if c > 0:
+                break
+        tr, cr = nb.nat_bem_trace_kernel("cgemm_reduce" if name == "cgemm_fp32" else "tc_reduce")
+        tp, cp_ = nb.nat_bem_trace_kernel("tc_pack")
         nb.nat_bem_trace_enable(False)
-    ms = t / max(c, 1)
-    op_bytes = (8 if args.prec in ("fp32", "tf32") else 4) * n * ld
+    if c == 0:
+        raise RuntimeError("no product kernel ran")
+    ms = t / c
+    # operator bytes one product streams: FP32 L (8 per complex), the three BF16 pieces (12),
+    # or the BF16 / FP16 copy (4)
+    op_bytes = (12 if name == "tc_gemm_x6" else 8 if args.prec in ("fp32", "tf32") else 4) * n * ld
     peaks, _ = _peaks()
     return {"metric": "multi-RHS operator products per second", "value": 1e3 / ms, "unit": "products/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": f"products_{n}tri_{args.nrhs}rhs", "engine": args.prec},
-            "ms_per_product": ms, "reduce_ms": tr / max(cr, 1), "tflops": 8.0 * n * ld * args.nrhs / ms / 1e9,
+            "config": {"workload": f"products_{n}tri_{args.nrhs}rhs", "engine": args.prec, "kernel": name},
+            "ms_per_product": ms, "reduce_ms": tr / max(cr, 1), "pack_ms": tp / max(cp_, 1),
+            "tflops": 8.0 * n * ld * args.nrhs / ms / 1e9,
             "operator_gbs": op_bytes / ms / 1e6, "hbm_frac": op_bytes / ms / 1e6 / peaks["hbm_gbs"]}
 
 
@@ -972,17 +983,37 @@ def run_serving(args):
     torch.cuda.synchronize()
     budget = int(args.budget_gb * (1 << 30))
 
-    def serve(opts_):
+    def serve(opts_, scale=1.0):
+        # scale stretches the arrival times: the same requests offered at rate / scale
         with nb.Server(budget, opts_, slots=args.concurrency) as srv:
             tickets = []
             t_start = time.perf_counter()
             for t_arr, jd, nrhs in reqs:
-                while time.perf_counter() - t_start < t_arr:
+                while time.perf_counter() - t_start < t_arr * scale:
                     time.sleep(0.0005)
                 tickets.append((srv.submit(jd), nrhs))
             res = [(srv.wait(t, -1), nrhs) for t, nrhs in tickets]
             t_end = time.perf_counter()
         return res, t_end - t_start
+
+    sweep = []
+    for rate in [float(r) for r in args.rates.split(",") if r.strip()]:
+        # the same stream offered at a lower rate (the arrival draws scale with 1 / rate). A rate
+        # counts as sustained when the server keeps up (completions >= 0.95 x offered) and the
+        # queue does not grow along the stream (p99 latency of the last third of the requests
+        # <= 1.5 x that of the first third)
+        r_res, r_dt = serve(opts, args.rate / rate)
+        r_lat = [r[0][6] for r in r_res]
+        third = len(r_lat) // 3
+        p_first = float(np.percentile(r_lat[:third], 99))
+        p_last = float(np.percentile(r_lat[-third:], 99))
+        rps = len(r_res) / r_dt
+        sweep.append({"offered_req_s": rate, "requests_per_s": rps,
+                      "solves_per_s": sum(nrhs for r, nrhs in r_res if r[0] == 0) / r_dt,
+                      "latency_ms": _percentiles(r_lat), "queue_ms": _percentiles([r[0][5] for r in r_res]),
+                      "p99_first_third_ms": p_first, "p99_last_third_ms": p_last,
+                      "sustained": bool(rps >= 0.95 * rate and p_last <= 1.5 * p_first),
+                      "all_ok": all(r[0][0] == 0 for r in r_res)})
 
     res, dt = serve(opts)
     lat = [r[0][6] for r in res]
@@ -996,6 +1027,10 @@ def run_serving(args):
             "latency_ms": dict(_percentiles(lat), per="request, submit to completion (queueing included)"),
             "queue_ms": _percentiles([r[0][5] for r in res]),
             "statuses": {str(k): int(v) for k, v in zip(*np.unique([r[0][0] for r in res], return_counts=True))}}
+    if sweep:
+        line["rate_sweep"] = sweep
+        ok = [r["offered_req_s"] for r in sweep if r["sustained"] and r["all_ok"]]
+        line["largest_sustained_rate_req_s"] = max(ok) if ok else None
     if args.prec != "fp32":
         res_p, dt_p = serve(nb.nat_bem_opts_default(prec=nb.PREC_FP32))
         lat_p = [r[0][6] for r in res_p]
@@ -1143,6 +1178,8 @@ def main():
                     help="interior workload: worker pool (one op per job) or fused buckets")
     ap.add_argument("--n-req", type=int, default=300)
     ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--rates", default="", help="serve workload: also offer the same stream at these rates "
+                                                "(comma-separated req/s) and report the largest sustained one")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     ap.add_argument("--inner-tol", type=float, default=None,
                     help="mixed precision: tolerance of each inner solve (default: the library's)")

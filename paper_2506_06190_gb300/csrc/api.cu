@@ -180,6 +180,7 @@ int64_t nat_bem_required_bytes(int64_t nt, int32_t nrhs, const nat_bem_opts* opt
   if (o.prec == NAT_BEM_PREC_MIXED_FP16) b += 4 * nt;               // its row scales
   b += nt * (7 * 16 + 5 * 16 + 9 * 8 + 7 * 8 + 8 * 14);             // geometry + near pairs
   b += workspace_bytes(nt, nrhs, o);
+  if (nrhs >= kX6MinRhs) b += 12 * nt * ld;  // three BF16 planes of L for the accurate products
   return b;
 }
 
@@ -786,6 +787,7 @@ void nat_bem_destroy(nat_bem_op* op) {
     void* mp[] = {op->L, op->R, op->Lb, op->row_scale};
     for (void* p : mp) dev_free(p, s);
   }
+  if (op->Ls) dev_free(op->Ls, s);
   galerkin_free(op, s);
   workspace_free(op->ws, s);
   delete op;
@@ -803,6 +805,7 @@ nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cuda_stream) {
       return NAT_BEM_EINVAL;
     }
     op->k = k;
+    op->split_ok = false;
     if (op->mc) return mc_assemble_operators(op, (cudaStream_t)cuda_stream);
     if (op->galerkin) return galerkin_assemble_operators(op, (cudaStream_t)cuda_stream);
     NB_TRY(ensure_rules(op->opts.adj_subdiv_levels, op->opts.self_theta_pts));

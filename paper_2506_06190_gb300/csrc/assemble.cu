@@ -777,6 +777,7 @@ __global__ void __launch_bounds__(256) k_copy_fp16_rows(const float2* __restrict
 }
 
 nat_bem_status finish_low_copy(nat_bem_op* op, cudaStream_t s) {
+  op->split_ok = false;  // L changed: its three-way split is rebuilt before the next use
   if (!op->copy_fp16 || !op->Lb) return NAT_BEM_OK;
   NB_LAUNCH("copy_fp16", s, k_copy_fp16_rows<<<(unsigned)op->n, 256, 0, s>>>(op->L, (int)op->geo.ld, op->Lb,
                                                                               op->row_scale));

@@ -2303,6 +2303,7 @@ nat_bem_status apply_impl(nat_bem_op* op, int which, int engine, const float2* d
         return st;
       }
     }
+    if (eng == kEngineFp32 && which == 0 && nrhs >= kX6MinRhs && x6_enabled()) st = ensure_split(op, s);
     if (eng != kEngineFp32 && which == 0) st = tc_tune(op, eng, nrhs, xpad, y64, scratch, sbytes, err, s);
     if (st == NAT_BEM_OK) st = product(op, which, eng, xpad, nrhs, y64, nullptr, nullptr, scratch, sbytes, err, s);
   }
@@ -2328,6 +2329,8 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
                           nat_bem_solve_info* info, cudaStream_t s, std::vector<nat_bem_solve_info>* per_rhs,
                           std::vector<int>* per_conv) {
   NB_TRY(workspace_ensure(op, nrhs, s));
+  // the split of L for the FP32-accurate tensor-core products (built outside any capture)
+  if (nrhs >= kX6MinRhs && op->bstride == 0 && x6_enabled()) NB_TRY(ensure_split(op, s));
   Workspace* ws = op->ws;
   const nat_bem_opts& o = op->opts;
   NB_TRY_CUDA(cudaMemsetAsync(ws->gbar, 0, 2 * sizeof(unsigned), s));

@@ -151,6 +151,9 @@ struct nat_bem_op {
                                        // copy_fp16, packed half2 of the row-scaled entries
   bool copy_fp16 = false;              // mixed FP16: Lb holds L_ij s_i in half precision
   float* row_scale = nullptr;          // mixed FP16: 1 / s_i per row (a power of two)
+  uint16_t* Ls = nullptr;              // FP32-accurate multi-RHS products: L split into three
+                                       // BF16 planes (n x 2 ld each), built on first use
+  bool split_ok = false;               // Ls holds the split of the current L
   bool views = false;                  // L, R and Lb belong to someone else (not freed here)
   bool geo_view = false;               // geo belongs to another op of the same mesh
   int64_t bstride = 0;                 // > 0: a batch of operators, RHS s uses L + s bstride
@@ -222,6 +225,11 @@ nat_bem_status product(nat_bem_op* op, int which, int engine, const float2* X, i
                        double2* Y, const int* done, const int* scal, void* scratch,
                        size_t scratch_bytes, int* err, cudaStream_t s);
 size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms);
+// The FP32-accurate multi-RHS product on tensor cores (three-way BF16 split of L and X) runs for
+// products with L and at least kX6MinRhs RHS once ensure_split has built the split of L.
+constexpr int kX6MinRhs = 8;
+bool x6_enabled();
+nat_bem_status ensure_split(nat_bem_op* op, cudaStream_t s);
 // Picks the tensor-core product's launch shape for this operator size and RHS count by timing
 // the candidates once per size class (outside graph capture); X, Y and scratch are the caller's.
 nat_bem_status tc_tune(nat_bem_op* op, int engine, int nrhs, const float2* X, double2* Y,

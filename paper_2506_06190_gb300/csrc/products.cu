@@ -362,6 +362,256 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   }
 }
 
+// ------------------------------------------ FP32-accurate product on tensor cores (x6)
+// The operator and the right-hand sides are split exactly into three BF16 pieces each:
+// a1 = bf16(a), a2 = bf16(a - a1), a3 = bf16(a - a1 - a2), every difference exact in FP32, so
+// a = a1 + a2 + a3 to within 2^-24 |a| or so. The product sums the six piece products with
+// i + j <= 4 (the three omitted ones lie below 2^-24 of a x); a BF16 x BF16 product is exact
+// in the FP32 accumulator. The accumulator is drained every kX6Drain K blocks (256 real terms)
+// into FP32 registers, so each long sum is short FP32 runs plus one add per run, as in the
+// CUDA-core GEMM's folds. Six MMAs per operand pair, three A and three B tiles per stage.
+constexpr int kX6Drain = 4;
+
+__device__ __forceinline__ void split3(float a, __nv_bfloat16& p1, __nv_bfloat16& p2, __nv_bfloat16& p3) {
+  p1 = __float2bfloat16_rn(a);
+  const float r1 = __fsub_rn(a, __bfloat162float(p1));   // exact
+  p2 = __float2bfloat16_rn(r1);
+  const float r2 = __fsub_rn(r1, __bfloat162float(p2));  // exact
+  p3 = __float2bfloat16_rn(r2);
+}
+
+// The three pieces of `count` floats (a multiple of 4) into planes `plane` elements apart.
+__global__ void k_split3(const float4* __restrict__ a, int64_t count4, __nv_bfloat16* __restrict__ out,
+                         int64_t plane) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count4; i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 v = a[i];
+    __nv_bfloat16 p[3][4];
+    split3(v.x, p[0][0], p[1][0], p[2][0]);
+    split3(v.y, p[0][1], p[1][1], p[2][1]);
+    split3(v.z, p[0][2], p[1][2], p[2][2]);
+    split3(v.w, p[0][3], p[1][3], p[2][3]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      uint2 w;
+      w.x = (uint32_t)__bfloat16_as_ushort(p[q][0]) | ((uint32_t)__bfloat16_as_ushort(p[q][1]) << 16);
+      w.y = (uint32_t)__bfloat16_as_ushort(p[q][2]) | ((uint32_t)__bfloat16_as_ushort(p[q][3]) << 16);
+      *reinterpret_cast<uint2*>(out + q * plane + 4 * i) = w;
+    }
+  }
+}
+
+// B of the x6 product: the layout of k_pack_b's BF16 form, one plane per piece.
+__global__ void k_pack_b3(const float2* __restrict__ X, int ld, int nrhs, int P, __nv_bfloat16* __restrict__ B,
+                          int64_t plane, const int* __restrict__ scal) {
+  if (scal && scal[1]) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over P * ld
+  if (i >= (int64_t)P * ld) return;
+  const int c = (int)(i / ld), j = (int)(i % ld);
+  const float2 x = c < nrhs ? X[(size_t)c * ld + j] : make_float2(0.f, 0.f);
+  const size_t Kt = 2 * (size_t)ld;
+  const float v[4] = {x.x, -x.y, x.y, x.x};
+  const size_t at[4] = {(size_t)c * Kt + 2 * j, (size_t)c * Kt + 2 * j + 1, (size_t)(P + c) * Kt + 2 * j,
+                        (size_t)(P + c) * Kt + 2 * j + 1};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    __nv_bfloat16 p1, p2, p3;
+    split3(v[e], p1, p2, p3);
+    B[at[e]] = p1;
+    B[plane + at[e]] = p2;
+    B[2 * plane + at[e]] = p3;
+  }
+}
+
+// The stream-K partition of k_tc_gemm with one 128-row tile per stage and K blocks of 64;
+// each stage holds the three A pieces then the three B pieces. The MMA thread switches TMEM
+// buffer at every drain chunk (kX6Drain K blocks, or the end of a segment); the epilogue adds
+// each chunk into FP32 registers (Ng <= 128 columns per row) and writes the segment's partial
+// tile at its end.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CUtensorMap ta2,
+             const __grid_constant__ CUtensorMap ta3, const __grid_constant__ CUtensorMap tb1,
+             const __grid_constant__ CUtensorMap tb2, const __grid_constant__ CUtensorMap tb3, int n,
+             int nkb, int per, int msp, int Ng, int stages, float* __restrict__ part,
+             int* __restrict__ err, const int* __restrict__ scal) {
+  constexpr int BK = 64, TM = kTcRows;
+  if (scal && scal[1]) return;
+  const int m_tiles = (n + TM - 1) / TM;
+  const int64_t T = (int64_t)m_tiles * nkb;
+  const int64_t t0 = (int64_t)blockIdx.x * per;
+  const int64_t t1 = min(T, t0 + per);
+  if (t0 >= T) return;
+  const int mt_first = (int)(t0 / nkb);
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t a_bytes = TM * 128, b_bytes = (uint32_t)Ng * 128;
+  const uint32_t stage_bytes = 3 * (a_bytes + b_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + stages * stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kTcMaxStages;
+  uint64_t* tfull = bars + 2 * kTcMaxStages;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* fin = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t ncols = 32;
+  while ((int)ncols < Ng) ncols <<= 1;
+  const uint32_t alloc_cols = 2 * ncols;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int q = 0; q < stages; ++q) {
+      mbar_init(smem_u32(&full[q]), 1);
+      mbar_init(smem_u32(&empty[q]), 1);
+    }
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(smem_u32(&tfull[q]), 1);
+      mbar_init(smem_u32(&tempty[q]), 4);
+    }
+    mbar_init(smem_u32(fin), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(alloc_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: the three A pieces of tile (mt, kb) and the three B pieces of K block kb
+    int issued = 0;
+    for (int64_t t = t0; t < t1 && !s_abort; ++t) {
+      const int it = (int)(t - t0);
+      const int q = it % stages;
+      const uint32_t ph = (uint32_t)(it / stages) & 1u;
+      if (!mbar_wait_or_abort(smem_u32(&empty[q]), ph ^ 1u, &s_abort)) {
+        atomicOr(err, 1);
+        s_abort = 1;
+        break;
+      }
+      const uint32_t sa = smem_u32(base + q * stage_bytes);
+      const uint32_t fb = smem_u32(&full[q]);
+      mbar_expect_tx(fb, stage_bytes);
+      const int mt = (int)(t / nkb), kb = (int)(t % nkb);
+      tma_load_2d(sa, &ta1, kb * BK, mt * TM, fb);
+      tma_load_2d(sa + a_bytes, &ta2, kb * BK, mt * TM, fb);
+      tma_load_2d(sa + 2 * a_bytes, &ta3, kb * BK, mt * TM, fb);
+      tma_load_2d(sa + 3 * a_bytes, &tb1, kb * BK, 0, fb);
+      tma_load_2d(sa + 3 * a_bytes + b_bytes, &tb2, kb * BK, 0, fb);
+      tma_load_2d(sa + 3 * a_bytes + 2 * b_bytes, &tb3, kb * BK, 0, fb);
+      issued = it + 1;
+    }
+    if (s_abort) {
+      for (int it = max(0, issued - stages); it < issued; ++it)
+        mbar_wait(smem_u32(&full[it % stages]), (uint32_t)(it / stages) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: piece pairs (A i, B j), smallest first
+    const uint32_t idesc = instr_desc(1u, (uint32_t)Ng, (uint32_t)kTcRows);
+    constexpr int kPa[6] = {0, 1, 2, 0, 1, 0}, kPb[6] = {2, 1, 0, 1, 0, 0};
+    int chunk = -1;
+    uint32_t acc = tmem;
+    bool first = true;
+    for (int64_t t = t0; t < t1 && !s_abort; ++t) {
+      const int it = (int)(t - t0);
+      const int kb = (int)(t % nkb);
+      if (t == t0 || kb % kX6Drain == 0) {  // a new drain chunk (a new segment starts at kb = 0)
+        if (chunk >= 0) mma_commit(smem_u32(&tfull[chunk & 1]));
+        ++chunk;
+        if (!mbar_wait_or_abort(smem_u32(&tempty[chunk & 1]), ((uint32_t)(chunk >> 1) & 1u) ^ 1u, &s_abort)) {
+          atomicOr(err, 8);
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        acc = tmem + (uint32_t)(chunk & 1) * ncols;
+        first = true;
+      }
+      const int q = it % stages;
+      const uint32_t ph = (uint32_t)(it / stages) & 1u;
+      if (!mbar_wait_or_abort(smem_u32(&full[q]), ph, &s_abort)) {
+        atomicOr(err, 2);
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t sa = smem_u32(base + q * stage_bytes);
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr) {
+        const uint64_t da = smem_desc(sa + kPa[pr] * a_bytes);
+        const uint64_t db = smem_desc(sa + 3 * a_bytes + kPb[pr] * b_bytes);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma<1>(acc, da + 2 * kk, db + 2 * kk, idesc, (first && pr == 0 && kk == 0) ? 0u : 1u);
+      }
+      first = false;
+      mma_commit(smem_u32(&empty[q]));
+    }
+    if (chunk >= 0) mma_commit(smem_u32(&tfull[chunk & 1]));
+    mma_commit(smem_u32(fin));
+  } else if (warp >= 2) {
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
+    const int quarter = warp & 3;
+    const int r = quarter * 32 + lane;
+    float accr[128];
+#pragma unroll
+    for (int c = 0; c < 128; ++c) accr[c] = 0.f;
+    int chunk = -1;
+    for (int64_t t = t0; t < t1; ++t) {
+      const int kb = (int)(t % nkb);
+      const bool seg_end = t + 1 == t1 || kb + 1 == nkb;
+      if (!seg_end && (kb + 1) % kX6Drain != 0) continue;  // not the last K block of a chunk
+      ++chunk;
+      const int b = chunk & 1;
+      if (!mbar_wait_or_abort(smem_u32(&tfull[b]), (uint32_t)(chunk >> 1) & 1u, &s_abort)) {
+        if (lane == 0) atomicOr(err, 4);
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < 128; c0 += 32) {
+        if (c0 < Ng) {
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * ncols + (uint32_t)c0, v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) accr[c0 + q] += __uint_as_float(v[q]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+      if (seg_end) {
+        const int j = (int)(t / nkb) - mt_first;
+        float* out = part + ((size_t)blockIdx.x * msp + j) * (size_t)Ng * TM;
+#pragma unroll
+        for (int c0 = 0; c0 < 128; c0 += 32) {
+          if (c0 < Ng && !s_abort) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) out[(size_t)(c0 + q) * TM + r] = accr[c0 + q];
+          }
+#pragma unroll
+          for (int q = 0; q < 32; ++q) accr[c0 + q] = 0.f;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  __syncthreads();
+  if (warp == 0) {
+    if (!mbar_wait(smem_u32(fin), 0) && lane == 0) atomicOr(err, 16);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(alloc_cols));
+  }
+}
+
 // B for the tensor-core product from nrhs complex64 vectors (x_c at X + c * ld), P = nrhs
 // rounded up to 16 (so the epilogue reads whole 32-column TMEM chunks): rows c < P
 // (Re, -Im) pairs, rows P + c (Im, Re) pairs; rows of absent RHS are zero. TF32: FP32 storage;
@@ -921,7 +1171,93 @@ size_t tc_workspace_bytes(int64_t n, int64_t ld, int nrhs, int sms) {
         floats = std::max(floats, (size_t)pl.grid * pl.msp * (size_t)tm);
       }
   const size_t tc = round_up((size_t)Ng * Kt * 4, 256) + floats * Ng * 4 + 64;
-  return std::max(tc, cg_partial_bytes(cg_plan(n, ld, nrhs, sms)) + 64);
+  // x6: three BF16 planes of B for at most 64 RHS per call, one-tile plan on one CTA per SM
+  const int Ng6 = std::min(Ng, 128);
+  const TcPlan p6 = tc_plan(n, kTcRows, (Kt + 63) / 64, sms);
+  const size_t x6 = round_up((size_t)3 * Ng6 * Kt * 2, 256) + (size_t)p6.grid * p6.msp * kTcRows * Ng6 * 4 + 64;
+  return std::max(std::max(tc, x6), cg_partial_bytes(cg_plan(n, ld, nrhs, sms)) + 64);
+}
+
+bool x6_enabled() { return std::getenv("NATBEM_NO_X6") == nullptr; }
+
+// The x6 kernel's shared-memory opt-in, set once (first from ensure_split, outside any capture).
+static cudaError_t x6_attr() {
+  static const cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm_x6, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax);
+  return e;
+}
+
+nat_bem_status ensure_split(nat_bem_op* op, cudaStream_t s) {
+  if (op->views || op->bstride > 0 || !op->L) return NAT_BEM_OK;  // batches run GEMVs
+  const int64_t Kt = 2 * op->geo.ld;
+  const int64_t count = op->n * Kt;  // floats of L (a multiple of 64)
+  if (!op->Ls) NB_TRY(dev_alloc_n(&op->Ls, 3 * (size_t)count, s));
+  if (!op->split_ok) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    NB_LAUNCH("split3", s, k_split3<<<sms * 8, 256, 0, s>>>(reinterpret_cast<const float4*>(op->L), count / 4,
+                                                           reinterpret_cast<__nv_bfloat16*>(op->Ls), count));
+    NB_CHECK_LAUNCH();
+    op->split_ok = true;
+  }
+  if (x6_attr() != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(x6_attr()));
+    return NAT_BEM_ECUDA;
+  }
+  return NAT_BEM_OK;
+}
+
+// Y = L X for nrhs <= 64 with the x6 kernel (the caller checked op->split_ok).
+static nat_bem_status product_x6(nat_bem_op* op, const float2* X, int nrhs, double2* Y, const int* done,
+                                 const int* scal, void* scratch, size_t scratch_bytes, int* err, cudaStream_t s,
+                                 int sms) {
+  const int n = (int)op->n, ld = (int)op->geo.ld;
+  const int P = (int)round_up(nrhs, 16);
+  const int Ng = 2 * P;
+  const int64_t Kt = 2 * (int64_t)ld;
+  const int nkb = (int)((Kt + 63) / 64);
+  const TcPlan pl = tc_plan(n, kTcRows, nkb, sms);
+  const size_t bplane = (size_t)Ng * Kt;
+  const size_t bbytes = round_up(3 * bplane * 2, 256);
+  const size_t pbytes = (size_t)pl.grid * pl.msp * Ng * kTcRows * 4;
+  if (Ng > 128 || bbytes + pbytes > scratch_bytes) {
+    set_error("x6 product: more than 64 RHS or scratch too small");
+    return NAT_BEM_ECUDA;
+  }
+  __nv_bfloat16* B = static_cast<__nv_bfloat16*>(scratch);
+  float* part = reinterpret_cast<float*>(static_cast<uint8_t*>(scratch) + bbytes);
+  {
+    const int64_t tot = (int64_t)P * ld;
+    NB_LAUNCH("tc_pack", s, k_pack_b3<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, nrhs, P, B, (int64_t)bplane, scal));
+    NB_CHECK_LAUNCH();
+  }
+  CUtensorMap ta[3], tb[3];
+  for (int q = 0; q < 3; ++q) {
+    NB_TRY(make_map(&ta[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, op->Ls + (size_t)q * n * Kt, (uint64_t)Kt, (uint64_t)n,
+                    (uint64_t)Kt * 2, 64u, (uint32_t)kTcRows));
+    NB_TRY(make_map(&tb[q], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, B + (size_t)q * bplane, (uint64_t)Kt, (uint64_t)Ng,
+                    (uint64_t)Kt * 2, 64u, (uint32_t)Ng));
+  }
+  const uint32_t stage_bytes = 3u * (uint32_t)(kTcRows * 128 + Ng * 128);
+  const int stages = std::min(kTcMaxStages, (int)((kTcSmemMax - tc_fixed_bytes()) / stage_bytes));
+  if (stages < 2) {
+    set_error("x6 product: shared memory too small");
+    return NAT_BEM_ECUDA;
+  }
+  const size_t smem = tc_fixed_bytes() + (size_t)stages * stage_bytes;
+  if (x6_attr() != cudaSuccess) {
+    set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(x6_attr()));
+    return NAT_BEM_ECUDA;
+  }
+  NB_LAUNCH("tc_gemm_x6", s, k_tc_gemm_x6<<<pl.grid, kTcThreads, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], n, nkb,
+                                                                          pl.per, pl.msp, Ng, stages, part, err, scal));
+  NB_CHECK_LAUNCH();
+  const int64_t tot = (int64_t)nrhs * n;
+  NB_LAUNCH("tc_reduce", s, k_tc_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+      part, n, kTcRows, Ng, P, nrhs, nkb, pl.per, pl.msp, Y, done, scal, nullptr));
+  NB_CHECK_LAUNCH();
+  return NAT_BEM_OK;
 }
 
 static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, const float2* X, int nrhs,
@@ -933,6 +1269,13 @@ static nat_bem_status product_shaped(nat_bem_op* op, int which, int engine, cons
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (engine == kEngineFp32 && which == 0 && nrhs >= kX6MinRhs && op->Ls && op->split_ok && x6_enabled() &&
+      ((uintptr_t)scratch & 255u) == 0) {
+    for (int c0 = 0; c0 < nrhs; c0 += 64)  // at most 64 RHS per launch (Ng <= 128 TMEM columns)
+      NB_TRY(product_x6(op, X + (size_t)c0 * ld, std::min(64, nrhs - c0), Y + (size_t)c0 * n, done ? done + c0 : nullptr,
+                        scal, scratch, scratch_bytes, err, s, sms));
+    return NAT_BEM_OK;
+  }
   if (engine == kEngineFp32) {
     const CgPlan cp = cg_plan(n, ld, nrhs, sms);
     const bool aligned = ld % 2 == 0 && ((uintptr_t)M & 15u) == 0 && ((uintptr_t)X & 15u) == 0 &&

@@ -497,12 +497,13 @@ def test_fp32_gemm_matches_oracle(nb, product_case, nrhs):
             assert np.max(np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)) < 1e-5
 
 
-@pytest.mark.parametrize("nrhs", [2, 17, 64, 100])
+@pytest.mark.parametrize("nrhs", [2, 8, 17, 64, 100])
 def test_fp32_gemm_carries_fp32_accuracy(nb, product_case, nrhs, monkeypatch):
-    """Both FP32 GEMM kernels (stream-K with float-float carries, and the fixed-tile one with
-    FP64 carries, NATBEM_CGEMM_TILED=1) against an FP64 product of the same FP32 operator
-    entries: every column within 1e-6 (FP32 products summed in FP32 over 128 terms: about
-    2e-7 on this case), and the two kernels within 1e-6 of each other."""
+    """The FP32-accurate products against an FP64 product of the same FP32 operator entries,
+    every column within 1e-6 (about 2e-7 on this case), and within 1e-6 of each other: the
+    tensor-core form (L and X split into three BF16 pieces, six exact piece products, used for
+    L with 8 RHS or more), the stream-K CUDA-core GEMM (NATBEM_NO_X6=1; float-float carries)
+    and the fixed-tile one (NATBEM_CGEMM_TILED=1; FP64 carries)."""
     V, F, k, L, R, X = product_case
     Xs = np.asfortranarray(X[:, :nrhs])
     with nb.Operator.assemble(V, F, k) as op:
@@ -510,17 +511,50 @@ def test_fp32_gemm_carries_fp32_accuracy(nb, product_case, nrhs, monkeypatch):
             M = op.rows(which, 0, op.n).astype(np.complex128)
             ref = M @ Xs.astype(np.complex128)
             ys = []
-            for tiled in (False, True):
-                if tiled:
-                    monkeypatch.setenv("NATBEM_CGEMM_TILED", "1")
-                else:
-                    monkeypatch.delenv("NATBEM_CGEMM_TILED", raising=False)
+            for env in ({}, {"NATBEM_NO_X6": "1"}, {"NATBEM_NO_X6": "1", "NATBEM_CGEMM_TILED": "1"}):
+                for v in ("NATBEM_NO_X6", "NATBEM_CGEMM_TILED"):
+                    monkeypatch.delenv(v, raising=False)
+                for kv in env.items():
+                    monkeypatch.setenv(*kv)
                 Y = op.apply(which, nb.ENGINE_FP32, Xs)
                 err = np.linalg.norm(Y - ref, axis=0) / np.linalg.norm(ref, axis=0)
-                assert err.max() < 1e-6, (tiled, err.max())
+                assert err.max() < 1e-6, (env, err.max())
                 ys.append(Y)
-            monkeypatch.delenv("NATBEM_CGEMM_TILED", raising=False)
-            assert _rel(ys[0], ys[1]) < 1e-6
+            for v in ("NATBEM_NO_X6", "NATBEM_CGEMM_TILED"):
+                monkeypatch.delenv(v, raising=False)
+            assert _rel(ys[0], ys[1]) < 1e-6 and _rel(ys[1], ys[2]) < 1e-6
+
+
+def test_plain_multi_rhs_solve_on_split_products(nb, oracle_lib, monkeypatch):
+    """A plain FP32 solve with 12 RHS runs every matvec on the split tensor-core product: each
+    RHS within 1e-4 of the FP64 oracle, within 1e-5 of the same solve on the CUDA-core GEMM,
+    and a reassembly at another k rebuilds the split (the second solve matches a fresh op)."""
+    Vs, F = S.ring_sphere(1500)
+    V = S.perturbed_ellipsoid(Vs, 31)
+    G = S.sh_neumann(V, F, 12, 32)
+    out = {}
+    for tag, env in (("x6", None), ("cuda_core", "1")):
+        if env:
+            monkeypatch.setenv("NATBEM_NO_X6", env)
+        else:
+            monkeypatch.delenv("NATBEM_NO_X6", raising=False)
+        with nb.Operator.assemble(V, F, 2.0) as op:
+            P, info, st = op.solve(G)
+            assert st == nb.NAT_BEM_OK
+            op.reassemble(4.5)
+            P2, info2, st2 = op.solve(G)
+            assert st2 == nb.NAT_BEM_OK
+        out[tag] = (P, P2)
+    monkeypatch.delenv("NATBEM_NO_X6", raising=False)
+    for k, i in ((2.0, 0), (4.5, 1)):
+        L, R = oracle_lib.assemble(V, F, k)
+        Pref = np.linalg.solve(L, R @ G)
+        for s in range(12):
+            assert _rel(out["x6"][i][:, s], Pref[:, s]) < SOL_TOL
+        assert _rel(out["x6"][i], out["cuda_core"][i]) < 1e-5
+    with nb.Operator.assemble(V, F, 4.5) as fresh:
+        P3, _, _ = fresh.solve(G)
+    assert np.array_equal(P3, out["x6"][1])
 
 
 @pytest.mark.parametrize("nrhs", [1, 6, 40, 64, 100])
