@@ -23,7 +23,8 @@ constexpr float kTwoPiLo = -1.7484555314695172e-7f;
 constexpr float kInvTwoPi = 0.159154943091895336f;
 constexpr int kEvalThreads = 128;  // field points per block
 constexpr int kElemStage = 32;     // elements staged per shared-memory round
-constexpr int kMaxRhsPass = 16;    // right-hand sides accumulated per pass (kernel values reused)
+constexpr int kMaxRhsPass = 16;    // far field: right-hand sides per pass (kernel values reused)
+constexpr int kEvalRhsPass = 32;   // field: right-hand sides per pass
 constexpr int kNoAllocRhsPass = 4; // the allocation-free path: passes of four (scratch sizing)
 }  // namespace
 
@@ -232,6 +233,9 @@ __global__ void k_eval_reduce(const double2* __restrict__ part, int m, int split
 // Pass width for nr right-hand sides: the smallest of 1, 2, 4, 8, 16 that holds them. Each
 // (point, element) kernel value is computed once per pass and applied to every RHS of it.
 static int pass_width(int nr) { return nr <= 1 ? 1 : nr <= 2 ? 2 : nr <= 4 ? 4 : nr <= 8 ? 8 : 16; }
+// The field kernel also takes passes of 32 RHS (64 accumulators a thread, 168 registers): each
+// kernel value is then evaluated twice at 64 RHS instead of four times. A pass of 64 spills.
+static int eval_pass_width(int nr) { return nr <= 16 ? pass_width(nr) : 32; }
 
 // One k_eval launch for nr right-hand sides: seven quadrature points per element, or one
 // sample point per Monte-Carlo sample (weight w / (4 pi) at offset 0). Partials are strided by
@@ -240,12 +244,13 @@ template <int NQ>
 static void eval_launch_nq(int nr, dim3 grid, cudaStream_t s, const Geometry& g, int n,
                            const double* d_pts, int m, float k, const float2* d_p,
                            const float2* d_g, int r0, int per, double2* part) {
-  switch (pass_width(nr)) {
+  switch (eval_pass_width(nr)) {
     case 1: k_eval<1, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
     case 2: k_eval<2, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
     case 4: k_eval<4, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
     case 8: k_eval<8, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
-    default: k_eval<16, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    case 16: k_eval<16, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
+    default: k_eval<32, NQ><<<grid, kEvalThreads, 0, s>>>(g.c_hi, g.c_lo, g.nrm, g.qp, n, d_pts, m, k, d_p, d_g, r0, nr, per, part); break;
   }
 }
 
@@ -311,7 +316,7 @@ static nat_bem_status eval_core(const nat_bem_op* op, const double* d_pts, int64
   int max_splits = 1, per = 0;
   for (int c = 0; c < 4; ++c) max_splits = max(max_splits, split_of(kBps[c], &per));
   double2* part = nullptr;
-  NB_TRY(dev_alloc_n(&part, (size_t)max_splits * m * pass_width(min(kMaxRhsPass, nrhs)), s));
+  NB_TRY(dev_alloc_n(&part, (size_t)max_splits * m * eval_pass_width(min(kEvalRhsPass, nrhs)), s));
   auto run = [&](int bps, int r0, int nr) -> nat_bem_status {
     int per_c = 0;
     const int splits = split_of(bps, &per_c);
@@ -319,17 +324,17 @@ static nat_bem_status eval_core(const nat_bem_op* op, const double* d_pts, int64
     NB_LAUNCH("eval", s, eval_launch(src, (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per_c, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
-    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, eval_pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
     return NAT_BEM_OK;
   };
-  const int nr0 = min(kMaxRhsPass, nrhs);
+  const int nr0 = min(kEvalRhsPass, nrhs);
   const int64_t cls = ((int64_t)((n + 1023) / 1024) << 32) | ((int64_t)((m + 255) / 256) << 8) |
-                      (int64_t)pass_width(nr0) | (src.one_point ? 128 : 0);
+                      ((int64_t)eval_pass_width(nr0) << 1) | (src.one_point ? 1 : 0);
   const int pick = autotune("eval_bps", cls, 4, [&](int c) { return run(kBps[c], 0, nr0); }, s);
   nat_bem_status st = NAT_BEM_OK;
-  for (int r0 = 0; r0 < nrhs && st == NAT_BEM_OK; r0 += kMaxRhsPass)
-    st = run(kBps[pick], r0, min(kMaxRhsPass, nrhs - r0));
+  for (int r0 = 0; r0 < nrhs && st == NAT_BEM_OK; r0 += kEvalRhsPass)
+    st = run(kBps[pick], r0, min(kEvalRhsPass, nrhs - r0));
   dev_free(part, s);
   return st;
 }
@@ -489,7 +494,7 @@ static nat_bem_status eval_noalloc_impl(const nat_bem_op* op, const double* d_pt
     NB_LAUNCH("eval", s, eval_launch(eval_source(op), (float)op->k, nr, grid, s, d_pts, (int)m, d_p, d_g, r0, per, part));
     NB_CHECK_LAUNCH();
     const int64_t tot = m * nr;
-    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, pass_width(nr), r0, d_out));
+    NB_LAUNCH("eval_reduce", s, k_eval_reduce<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, (int)m, splits, nr, eval_pass_width(nr), r0, d_out));
     NB_CHECK_LAUNCH();
   }
   return NAT_BEM_OK;

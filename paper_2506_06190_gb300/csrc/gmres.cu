@@ -55,6 +55,7 @@ struct Workspace {
   int* outer_done = nullptr;                               // refinement: converged RHS
   unsigned* gbar = nullptr;                                // grid barrier state (count, gen)
   int coop_blocks = 0;                                     // 0: fused kernel not usable
+  int units_blocks = 0;                                    // grid of the multi-RHS fused kernel
   double2 *pblk = nullptr, *hred = nullptr;                // fused kernel: block partials, totals
   int arn_smem = 0;                                        // fused kernel: dynamic shared bytes
   double2* pbu = nullptr;                                  // multi-RHS fused kernel: unit partials
@@ -912,6 +913,7 @@ constexpr int kArnMaxRows = 512;           // rows per block (n <= 151 * 512 wit
 constexpr int kArnPanelBytes = 96 * 1024;
 constexpr int kArnMaxRhs = 256;
 constexpr int kArnUnitsMinRhs = 4;  // more right-hand sides than this: k_arnoldi_units
+constexpr int kArnUnitsPerSm = 2;   // k_arnoldi_units: blocks per SM (at most)
 // mixed refinement: a stalled sweep with every open true residual within this factor of the
 // tolerance ends the solve (the FP32 residual product's rounding floor)
 constexpr double kResidualFloor = 4.0;
@@ -1228,36 +1230,45 @@ __global__ void __launch_bounds__(256) k_arnoldi_units(GArgs a, double2* __restr
         const int q0 = chunk * unit, q1 = min(a.n, q0 + unit);
         const float2* w = a.wf + (size_t)s * a.n;
         for (int c = warp; c < np; c += 8) {
-          float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+          // eight rows per lane in flight (16 loads of 8 bytes)
+          float re[8], im[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) re[t] = im[t] = 0.f;
           if (c <= j) {
             const float2* v = a.Vf + vidx(a, c, s);
-            for (int r = q0 + lane; r < q1; r += 128) {
+            for (int r = q0 + lane; r < q1; r += 256) {
+              float2 vv[8], ww[8];
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
+              for (int t = 0; t < 8; ++t) {
                 const int rr = r + 32 * t;
-                if (rr < q1) {
-                  const float2 vv = v[rr], ww = w[rr];
-                  re[t] = fmaf(vv.x, ww.x, re[t]);
-                  re[t] = fmaf(vv.y, ww.y, re[t]);
-                  im[t] = fmaf(vv.x, ww.y, im[t]);
-                  im[t] = fmaf(-vv.y, ww.x, im[t]);
-                }
+                vv[t] = rr < q1 ? v[rr] : make_float2(0.f, 0.f);
+                ww[t] = rr < q1 ? w[rr] : make_float2(0.f, 0.f);
+              }
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                re[t] = fmaf(vv[t].x, ww[t].x, re[t]);
+                re[t] = fmaf(vv[t].y, ww[t].y, re[t]);
+                im[t] = fmaf(vv[t].x, ww[t].y, im[t]);
+                im[t] = fmaf(-vv[t].y, ww[t].x, im[t]);
               }
             }
           } else {
-            for (int r = q0 + lane; r < q1; r += 128) {
+            for (int r = q0 + lane; r < q1; r += 256) {
+              float2 ww[8];
 #pragma unroll
-              for (int t = 0; t < 4; ++t) {
+              for (int t = 0; t < 8; ++t) {
                 const int rr = r + 32 * t;
-                if (rr < q1) {
-                  const float2 ww = w[rr];
-                  re[t] = fmaf(ww.x, ww.x, re[t]);
-                  re[t] = fmaf(ww.y, ww.y, re[t]);
-                }
+                ww[t] = rr < q1 ? w[rr] : make_float2(0.f, 0.f);
+              }
+#pragma unroll
+              for (int t = 0; t < 8; ++t) {
+                re[t] = fmaf(ww[t].x, ww[t].x, re[t]);
+                re[t] = fmaf(ww[t].y, ww[t].y, re[t]);
               }
             }
           }
-          float sr = (re[0] + re[1]) + (re[2] + re[3]), si = (im[0] + im[1]) + (im[2] + im[3]);
+          float sr = ((re[0] + re[1]) + (re[2] + re[3])) + ((re[4] + re[5]) + (re[6] + re[7]));
+          float si = ((im[0] + im[1]) + (im[2] + im[3])) + ((im[4] + im[5]) + (im[6] + im[7]));
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -1601,7 +1612,8 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
   b += 8 * nchunk * nrhs;                                            // partial norms
   b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
-  if (nrhs > kArnUnitsMinRhs) b += 16 * (m + 2) * (4 * 256 + nrhs) + 8 * n * nrhs;  // unit partials, FP32 w
+  if (nrhs > kArnUnitsMinRhs)  // unit partials (about four units per block, <= 160 SMs), FP32 w
+    b += 16 * (m + 2) * (4 * kArnUnitsPerSm * 160 + nrhs) + 8 * n * nrhs;
   if (nrhs > 1) {  // operand and partial tiles of the multi-RHS products
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1714,9 +1726,17 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
       NB_TRY(dev_alloc_n(&ws->pblk, nr * (mm + 2) * (size_t)ws->coop_blocks, s));
       NB_TRY(dev_alloc_n(&ws->hred, nr * (mm + 2), s));
       if (nrhs > kArnUnitsMinRhs) {  // the multi-RHS kernel: partials for the largest unit count
+        // its own grid: up to kArnUnitsPerSm blocks per SM (more loads in flight for the
+        // streaming dots and row updates; one block per SM kept about a third of the HBM rate)
+        int pu32 = 0, pu64 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pu32, k_arnoldi_units<true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pu64, k_arnoldi_units<false>, 256, 0);
+        static const int env_per_sm = std::getenv("NATBEM_UNITS_PER_SM") ? std::atoi(std::getenv("NATBEM_UNITS_PER_SM")) : 0;
+        const int want = env_per_sm > 0 ? std::min(env_per_sm, kArnUnitsPerSm) : kArnUnitsPerSm;
+        ws->units_blocks = sms * std::max(1, std::min(want, std::min(pu32, pu64)));
         size_t most = 0;
         for (int q = kArnUnitsMinRhs + 1; q <= nrhs; ++q) {
-          const int u = arnoldi_unit((int)n, q, ws->coop_blocks);
+          const int u = arnoldi_unit((int)n, q, ws->units_blocks);
           most = std::max(most, (size_t)q * (size_t)((n + u - 1) / u));
         }
         NB_TRY(dev_alloc_n(&ws->pbu, most * (mm + 2), s));
@@ -2126,11 +2146,11 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
         int* errp = ws->tc_err;
         if (nrhs > kArnUnitsMinRhs && ws->pbu) {
           double2* pu = ws->pbu;
-          int unit = arnoldi_unit(n, nrhs, ws->coop_blocks);
+          int unit = arnoldi_unit(n, nrhs, ws->units_blocks);
           int cps = (n + unit - 1) / unit;
           void* args[] = {&ac, &pu, &hr, &bar, &errp, &unit, &cps};
           const void* kern = ac.Vf ? (const void*)k_arnoldi_units<true> : (const void*)k_arnoldi_units<false>;
-          NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->coop_blocks), dim3(256), args, 0, s)));
+          NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->units_blocks), dim3(256), args, 0, s)));
           continue;
         }
         int pcap = ws->arn_smem / (int)sizeof(double2);
