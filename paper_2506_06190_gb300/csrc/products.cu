@@ -181,6 +181,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
       : "memory");
 }
 
+// 16 columns of this warp's 32 TMEM lanes (32x32b.x16), waited for before use
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+      :
+      : "memory");
+}
+
 }  // namespace
 
 // Partial products of the stream-K partition: the iteration space is the m_tiles x nkb grid of
@@ -362,15 +379,31 @@ k_tc_gemm(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtens
   }
 }
 
+// hi + lo += c, exactly up to the rounding of lo (TwoSum)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float c) {
+  const float s = __fadd_rn(hi, c);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(c, bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
 // ------------------------------------------ FP32-accurate product on tensor cores (x6)
 // The operator and the right-hand sides are split exactly into three BF16 pieces each:
 // a1 = bf16(a), a2 = bf16(a - a1), a3 = bf16(a - a1 - a2), every difference exact in FP32, so
 // a = a1 + a2 + a3 to within 2^-24 |a| or so. The product sums the six piece products with
 // i + j <= 4 (the three omitted ones lie below 2^-24 of a x); a BF16 x BF16 product is exact
-// in the FP32 accumulator. The accumulator is drained every kX6Drain K blocks (256 real terms)
-// into FP32 registers, so each long sum is short FP32 runs plus one add per run, as in the
-// CUDA-core GEMM's folds. Six MMAs per operand pair, three A and three B tiles per stage.
-constexpr int kX6Drain = 4;
+// in the FP32 accumulator. The accumulator is drained after every K block (64 real terms,
+// 24 MMAs) into FP32 registers: the tensor core's FP32 accumulation error grows linearly with
+// the run length (measured at 20480 rows, 64 RHS, per column against an FP64 product: 1.1e-7,
+// 4.3e-7, 9.2e-7, 1.8e-6 for runs of 1, 2, 4, 8 K blocks, the mark of a biased, truncating
+// accumulation, where round-to-nearest errors would grow as the square root). With one-block
+// runs the product is more accurate than the CUDA-core GEMM (3.3e-7) for 10% more time than
+// four-block runs. Each run is added to a float-float pair per (row, column) by TwoSum, so
+// the register sums add no rounding of their own. Eight epilogue warps, two per TMEM lane
+// quarter, each hold half of the columns.
+constexpr int kX6Drain = 1;  // K blocks per accumulator run
+constexpr int kX6Threads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 
 __device__ __forceinline__ void split3(float a, __nv_bfloat16& p1, __nv_bfloat16& p2, __nv_bfloat16& p3) {
   p1 = __float2bfloat16_rn(a);
@@ -424,10 +457,10 @@ __global__ void k_pack_b3(const float2* __restrict__ X, int ld, int nrhs, int P,
 
 // The stream-K partition of k_tc_gemm with one 128-row tile per stage and K blocks of 64;
 // each stage holds the three A pieces then the three B pieces. The MMA thread switches TMEM
-// buffer at every drain chunk (kX6Drain K blocks, or the end of a segment); the epilogue adds
-// each chunk into FP32 registers (Ng <= 128 columns per row) and writes the segment's partial
-// tile at its end.
-__global__ void __launch_bounds__(kTcThreads, 1)
+// buffer at every accumulator run (kX6Drain K blocks, or the end of a segment); the epilogue adds
+// each run into float-float register sums (Ng <= 128 columns per row, half of them per warp)
+// and writes the segment's partial tile (hi + lo in FP32) at its end.
+__global__ void __launch_bounds__(kX6Threads, 1)
 k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CUtensorMap ta2,
              const __grid_constant__ CUtensorMap ta3, const __grid_constant__ CUtensorMap tb1,
              const __grid_constant__ CUtensorMap tb2, const __grid_constant__ CUtensorMap tb3, int n,
@@ -468,7 +501,7 @@ k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CU
     }
     for (int q = 0; q < 2; ++q) {
       mbar_init(smem_u32(&tfull[q]), 1);
-      mbar_init(smem_u32(&tempty[q]), 4);
+      mbar_init(smem_u32(&tempty[q]), 8);
     }
     mbar_init(smem_u32(fin), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -556,12 +589,14 @@ k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CU
     if (chunk >= 0) mma_commit(smem_u32(&tfull[chunk & 1]));
     mma_commit(smem_u32(fin));
   } else if (warp >= 2) {
-    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (rows of the tile), columns
+    // 64 h .. 64 h + 63 with h = (w - 2) / 4, into float-float sums (hi, lo)
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
     const int r = quarter * 32 + lane;
-    float accr[128];
+    float hi[64], lo[64];
 #pragma unroll
-    for (int c = 0; c < 128; ++c) accr[c] = 0.f;
+    for (int c = 0; c < 64; ++c) hi[c] = lo[c] = 0.f;
     int chunk = -1;
     for (int64_t t = t0; t < t1; ++t) {
       const int kb = (int)(t % nkb);
@@ -576,12 +611,13 @@ k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CU
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-      for (int c0 = 0; c0 < 128; c0 += 32) {
-        if (c0 < Ng) {
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * ncols + (uint32_t)c0, v);
+      for (int c0 = 0; c0 < 64; c0 += 16) {
+        const int col = 64 * half + c0;
+        if (col < Ng) {  // Ng is a multiple of 32: whole 16-column loads
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)b * ncols + (uint32_t)col, v);
 #pragma unroll
-          for (int q = 0; q < 32; ++q) accr[c0 + q] += __uint_as_float(v[q]);
+          for (int q = 0; q < 16; ++q) two_sum_acc(hi[c0 + q], lo[c0 + q], __uint_as_float(v[q]));
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -591,13 +627,14 @@ k_tc_gemm_x6(const __grid_constant__ CUtensorMap ta1, const __grid_constant__ CU
         const int j = (int)(t / nkb) - mt_first;
         float* out = part + ((size_t)blockIdx.x * msp + j) * (size_t)Ng * TM;
 #pragma unroll
-        for (int c0 = 0; c0 < 128; c0 += 32) {
-          if (c0 < Ng && !s_abort) {
+        for (int c0 = 0; c0 < 64; c0 += 32) {
+          const int col = 64 * half + c0;
+          if (col < Ng && !s_abort) {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) out[(size_t)(c0 + q) * TM + r] = accr[c0 + q];
+            for (int q = 0; q < 32; ++q) out[(size_t)(col + q) * TM + r] = __fadd_rn(hi[c0 + q], lo[c0 + q]);
           }
 #pragma unroll
-          for (int q = 0; q < 32; ++q) accr[c0 + q] = 0.f;
+          for (int q = 0; q < 32; ++q) hi[c0 + q] = lo[c0 + q] = 0.f;
         }
       }
     }
@@ -785,14 +822,6 @@ __device__ __forceinline__ void cg_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cg_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// hi + lo += c, exactly up to the rounding of lo (TwoSum)
-__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float c) {
-  const float s = __fadd_rn(hi, c);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(c, bb));
-  hi = s;
-  lo = __fadd_rn(lo, e);
 }
 }  // namespace
 
@@ -1250,7 +1279,7 @@ static nat_bem_status product_x6(nat_bem_op* op, const float2* X, int nrhs, doub
     set_error(std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(x6_attr()));
     return NAT_BEM_ECUDA;
   }
-  NB_LAUNCH("tc_gemm_x6", s, k_tc_gemm_x6<<<pl.grid, kTcThreads, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], n, nkb,
+  NB_LAUNCH("tc_gemm_x6", s, k_tc_gemm_x6<<<pl.grid, kX6Threads, smem, s>>>(ta[0], ta[1], ta[2], tb[0], tb[1], tb[2], n, nkb,
                                                                           pl.per, pl.msp, Ng, stages, part, err, scal));
   NB_CHECK_LAUNCH();
   const int64_t tot = (int64_t)nrhs * n;
