@@ -1170,6 +1170,244 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
   }
 }
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// k_arnoldi on the FP32 basis of inner refinement solves (a.Vf, a.wf): the block's panel of
+// V is staged as FP32 (twice the columns fit), the dots and the row updates run in FP32 with
+// FP32 lane and warp sums, the block partials, totals, Hessenberg column and rotations stay
+// FP64. Same blocks, barriers, decisions and second-pass test as k_arnoldi. pcap counts float2.
+__global__ void __launch_bounds__(256, 2) k_arnoldi_f32(GArgs a, double2* __restrict__ pb, double2* __restrict__ hr,
+                                                     unsigned* __restrict__ bar, int* __restrict__ err,
+                                                     int pcap) {
+  extern __shared__ float2 s_pf[];  // Vf_0..Vf_j on this block's rows (one RHS), when it fits
+  __shared__ float2 s_wf[kArnMaxRows];
+  __shared__ double2 s_h[256];
+  __shared__ float2 s_hf[256];
+  __shared__ double2 s_acc[256];
+  __shared__ float2 s_accf[256];
+  __shared__ double2 s_sn[256];
+  __shared__ double s_cs[256];
+  __shared__ unsigned char s_act[kArnMaxRhs];
+  __shared__ double s_hn[kArnMaxRhs], s_inv[kArnMaxRhs];
+  if (a.scal[1]) return;
+  const int j = a.scal[0];
+  const int G = (int)gridDim.x, b = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = (a.n + G - 2) / (G - 1);
+  const int r0 = b == 0 ? 0 : min(a.n, (b - 1) * R), r1 = b == 0 ? 0 : min(a.n, r0 + R);
+  const int rows = r1 - r0;
+  const int np = j + 2;
+  const size_t ps = (size_t)(a.m + 2);
+  const bool panel = (j + 1) * rows <= pcap;
+  for (int s = threadIdx.x; s < a.nrhs; s += blockDim.x) s_act[s] = a.done[s] ? 0 : 1;
+  __syncthreads();
+
+  for (int pass = 0; pass < 2; ++pass) {
+    const unsigned char want = pass == 0 ? 1 : 2;
+    bool any = false;
+    for (int s = 0; s < a.nrhs; ++s) any |= (s_act[s] >= want);
+    if (!any) break;
+    // (A) partial sums over this block's rows; w is L v_j (FP64) in the first pass and the
+    // FP32 w - V h that the first pass left in wf in the second
+    if (b > 0) {
+      const int l8 = lane & 7;
+      for (int s = 0; s < a.nrhs; ++s) {
+        if (s_act[s] < want) continue;
+        if (panel) {
+          for (int e = threadIdx.x; e < (j + 1) * rows; e += blockDim.x) {
+            const int c = e / rows, r = e - c * rows;
+            cp_async8(&s_pf[e], a.Vf + vidx(a, c, s) + r0 + r);
+          }
+        }
+        for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+          if (pass == 0) {
+            const double2 ww = a.w[(size_t)s * a.n + r0 + r];
+            s_wf[r] = make_float2((float)ww.x, (float)ww.y);
+          } else {
+            s_wf[r] = a.wf[(size_t)s * a.n + r0 + r];
+          }
+        }
+        if (panel) cp_async_wait_all();
+        __syncthreads();
+        for (int c0 = warp * 4; c0 < np; c0 += 32) {
+          const int c = c0 + (lane >> 3);
+          float re0 = 0.f, im0 = 0.f, re1 = 0.f, im1 = 0.f;
+          if (c <= j) {
+            const float2* v = panel ? s_pf + c * rows : a.Vf + vidx(a, c, s) + r0;
+            for (int r = l8; r < rows; r += 16) {
+              const float2 v0 = v[r], w0 = s_wf[r];
+              re0 = fmaf(v0.x, w0.x, re0);
+              re0 = fmaf(v0.y, w0.y, re0);
+              im0 = fmaf(v0.x, w0.y, im0);
+              im0 = fmaf(-v0.y, w0.x, im0);
+              if (r + 8 < rows) {
+                const float2 v1 = v[r + 8], w1 = s_wf[r + 8];
+                re1 = fmaf(v1.x, w1.x, re1);
+                re1 = fmaf(v1.y, w1.y, re1);
+                im1 = fmaf(v1.x, w1.y, im1);
+                im1 = fmaf(-v1.y, w1.x, im1);
+              }
+            }
+          } else if (c == j + 1) {
+            for (int r = l8; r < rows; r += 16) {
+              const float2 w0 = s_wf[r];
+              re0 = fmaf(w0.x, w0.x, re0);
+              re0 = fmaf(w0.y, w0.y, re0);
+              if (r + 8 < rows) {
+                const float2 w1 = s_wf[r + 8];
+                re1 = fmaf(w1.x, w1.x, re1);
+                re1 = fmaf(w1.y, w1.y, re1);
+              }
+            }
+          }
+          float re = re0 + re1, im = im0 + im1;
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+          }
+          if (l8 == 0 && c < np) pb[((size_t)s * ps + c) * G + b] = make_double2((double)re, (double)im);
+        }
+        __syncthreads();
+      }
+    }
+    grid_sync(bar, bar + 1, G, err);
+    // (R) totals over blocks 1..G-1, one warp per (RHS, column), fixed order
+    {
+      const int items = a.nrhs * np;
+      for (int it = b * 8 + warp; it < items; it += G * 8) {
+        const int s = it / np, c = it % np;
+        if (s_act[s] < want) continue;
+        const double2* src = pb + ((size_t)s * ps + c) * G;
+        double re = 0.0, im = 0.0;
+        for (int qb = 1 + lane; qb < G; qb += 256) {
+          double2 t[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) t[u] = qb + 32 * u < G ? src[qb + 32 * u] : make_double2(0.0, 0.0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            re += t[u].x;
+            im += t[u].y;
+          }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          re += __shfl_xor_sync(0xffffffffu, re, o);
+          im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        if (lane == 0) hr[(size_t)s * ps + c] = make_double2(re, im);
+      }
+    }
+    grid_sync(bar, bar + 1, G, err);
+    // (B) decisions, row updates, v_{j+1}; block s mod G: Hessenberg column and Givens of RHS s
+    for (int s = 0; s < a.nrhs; ++s) {
+      if (s_act[s] < want) continue;
+      const double2* hs = hr + (size_t)s * ps;
+      for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+        s_h[c] = hs[c];
+        s_hf[c] = make_float2((float)hs[c].x, (float)hs[c].y);
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double t = 0.0;
+        for (int c = lane; c <= j; c += 32) t += cabs2(s_h[c]);
+        t = warp_sum(t);
+        if (lane == 0) {
+          const double wn2 = hs[j + 1].x;
+          const double hn2 = fmax(wn2 - t, 0.0);
+          const bool again = pass == 0 && !(hn2 > 1e-4 * wn2);
+          const double inv = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
+          s_hn[s] = again ? -1.0 : hn2 * inv;
+          s_inv[s] = inv;
+          if (again) s_act[s] = 2;
+        }
+      }
+      __syncthreads();
+      const double hn = s_hn[s];
+      const bool last = hn >= 0.0;
+      if (b == s % G) {
+        const size_t ho = (size_t)s * (a.m + 1);
+        for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+          const double2 t = pass == 0 ? s_h[c] : cadd(a.hcol[ho + c], s_h[c]);
+          if (!last) a.hcol[ho + c] = t;
+          s_acc[c] = t;
+          if (c < j) {
+            s_cs[c] = a.cs[(size_t)s * a.m + c];
+            s_sn[c] = a.sn[(size_t)s * a.m + c];
+          }
+        }
+        __syncthreads();
+        if (last && warp == 0) givens_warp(a, s, j, hn, s_acc, s_cs, s_sn, lane);
+        __syncthreads();
+      }
+      if (b > 0 && rows > 0) {
+        const float finv = (float)s_inv[s];
+        for (int rc = 0; rc < rows; rc += 256) {
+          const int nr = min(256, rows - rc);
+          const int ng = 256 / nr;
+          const int lr = threadIdx.x % nr, g = threadIdx.x / nr;
+          const int r = r0 + rc + lr;
+          float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+          if (g < ng) {
+            const bool from_panel = panel && a.nrhs == 1;
+            for (int cb = g; cb <= j; cb += 8 * ng) {
+              float2 vv[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int c = cb + u * ng;
+                vv[u] = c > j ? make_float2(0.f, 0.f)
+                              : (from_panel ? s_pf[c * rows + rc + lr] : a.Vf[vidx(a, c, s) + r]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const int c = cb + u * ng;
+                const float2 h = c <= j ? s_hf[c] : make_float2(0.f, 0.f);
+                float2& acc = (u & 1) ? acc1 : acc0;
+                acc.x = fmaf(vv[u].x, h.x, acc.x);
+                acc.x = fmaf(-vv[u].y, h.y, acc.x);
+                acc.y = fmaf(vv[u].x, h.y, acc.y);
+                acc.y = fmaf(vv[u].y, h.x, acc.y);
+              }
+            }
+          }
+          s_accf[threadIdx.x] = make_float2(acc0.x + acc1.x, acc0.y + acc1.y);
+          __syncthreads();
+          if (threadIdx.x < nr) {
+            float2 t = s_accf[threadIdx.x];
+            for (int q = 1; q < ng; ++q) t = make_float2(t.x + s_accf[q * nr + threadIdx.x].x, t.y + s_accf[q * nr + threadIdx.x].y);
+            float2 w;
+            if (pass == 0) {
+              const double2 ww = a.w[(size_t)s * a.n + r];
+              w = make_float2((float)ww.x, (float)ww.y);
+            } else {
+              w = a.wf[(size_t)s * a.n + r];
+            }
+            w = make_float2(w.x - t.x, w.y - t.y);
+            if (!last) {
+              a.wf[(size_t)s * a.n + r] = w;
+            } else if (hn > 0.0) {
+              const float2 v = make_float2(w.x * finv, w.y * finv);
+              a.Vf[vidx(a, j + 1, s) + r] = v;
+              a.xf[(size_t)s * a.ld + r] = v;
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+  if (a.nrhs > 1) grid_sync(bar, bar + 1, G, err);
+  if (b == 0 && threadIdx.x == 0) {
+    int all = 1;
+    for (int q = 0; q < a.nrhs; ++q) all &= a.done[q];
+    a.scal[0] = j + 1;
+    a.scal[1] = all || j + 1 >= a.maxit;
+  }
+}
+
 // The same iteration for several right-hand sides, one cooperative launch. The work is dealt
 // in units of (RHS s, row range of `unit` rows): block b takes units b, b + G, ..., so every
 // block streams long coalesced row ranges of V with no per-RHS barrier, and the FP64 pipe stays
@@ -1612,8 +1850,9 @@ int64_t workspace_bytes(int64_t n, int nrhs, const nat_bem_opts& o) {
   b += 16 * std::max<int64_t>(nchunk, kDotChunks) * nrhs * (m + 1);  // partial dots
   b += 8 * nchunk * nrhs;                                            // partial norms
   b += 16 * nrhs * (m + 2) * (256 + 1);   // fused Arnoldi partials (<= 256 blocks) and totals
-  if (nrhs > kArnUnitsMinRhs)  // unit partials (about four units per block, <= 160 SMs), FP32 w
-    b += 16 * (m + 2) * (4 * kArnUnitsPerSm * 160 + nrhs) + 8 * n * nrhs;
+  if (nrhs > kArnUnitsMinRhs)  // unit partials (about four units per block, <= 160 SMs)
+    b += 16 * (m + 2) * (4 * kArnUnitsPerSm * 160 + nrhs);
+  b += 8 * n * nrhs;  // FP32 w of inner solves
   if (nrhs > 1) {  // operand and partial tiles of the multi-RHS products
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1714,12 +1953,21 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
       std::lock_guard<std::mutex> lk(attr_mu);
       if (dev >= 0 && dev < 64 && attr_set[dev] == 0) {
         attr_set[dev] = cudaFuncSetAttribute(k_arnoldi, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kArnPanelBytes) == cudaSuccess ? 1 : -1;
+                                             kArnPanelBytes) == cudaSuccess &&
+                                cudaFuncSetAttribute(k_arnoldi_f32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     kArnPanelBytes) == cudaSuccess
+                            ? 1
+                            : -1;
         if (attr_set[dev] < 0) cudaGetLastError();
       }
       ws->arn_smem = (dev >= 0 && dev < 64 && attr_set[dev] == 1) ? (int)want : 0;
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi, 256, ws->arn_smem);
+    {
+      int per_sm32 = 0;  // the FP32-basis form must fit as well
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm32, k_arnoldi_f32, 256, ws->arn_smem);
+      per_sm = std::min(per_sm, per_sm32);
+    }
     const bool fits = sms >= 2 && n <= (int64_t)(sms - 1) * kArnMaxRows && nrhs <= kArnMaxRhs;
     ws->coop_blocks = (coop && per_sm >= 1 && fits && !std::getenv("NATBEM_NO_FUSED_KRYLOV")) ? sms : 0;
     if (ws->coop_blocks > 0) {
@@ -1731,17 +1979,15 @@ static nat_bem_status workspace_ensure(nat_bem_op* op, int nrhs, cudaStream_t s)
         int pu32 = 0, pu64 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pu32, k_arnoldi_units<true>, 256, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pu64, k_arnoldi_units<false>, 256, 0);
-        static const int env_per_sm = std::getenv("NATBEM_UNITS_PER_SM") ? std::atoi(std::getenv("NATBEM_UNITS_PER_SM")) : 0;
-        const int want = env_per_sm > 0 ? std::min(env_per_sm, kArnUnitsPerSm) : kArnUnitsPerSm;
-        ws->units_blocks = sms * std::max(1, std::min(want, std::min(pu32, pu64)));
+        ws->units_blocks = sms * std::max(1, std::min(kArnUnitsPerSm, std::min(pu32, pu64)));
         size_t most = 0;
         for (int q = kArnUnitsMinRhs + 1; q <= nrhs; ++q) {
           const int u = arnoldi_unit((int)n, q, ws->units_blocks);
           most = std::max(most, (size_t)q * (size_t)((n + u - 1) / u));
         }
         NB_TRY(dev_alloc_n(&ws->pbu, most * (mm + 2), s));
-        NB_TRY(dev_alloc_n(&ws->wf, (size_t)n * nr, s));
       }
+      NB_TRY(dev_alloc_n(&ws->wf, (size_t)n * nr, s));  // FP32 w of inner solves on the FP32 basis
     }
   }
   NB_TRY_CUDA(cudaMemsetAsync(ws->tc_err, 0, sizeof(int), s));
@@ -2153,9 +2399,10 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
           NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->units_blocks), dim3(256), args, 0, s)));
           continue;
         }
-        int pcap = ws->arn_smem / (int)sizeof(double2);
+        int pcap = ws->arn_smem / (int)(ac.Vf ? sizeof(float2) : sizeof(double2));
         void* args[] = {&ac, &pb, &hr, &bar, &errp, &pcap};
-        NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi, dim3(ws->coop_blocks), dim3(256), args, (size_t)ws->arn_smem, s)));
+        const void* kern = ac.Vf ? (const void*)k_arnoldi_f32 : (const void*)k_arnoldi;
+        NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->coop_blocks), dim3(256), args, (size_t)ws->arn_smem, s)));
         continue;
       }
       const dim3 dot_grid(std::min(it0 + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
@@ -2466,11 +2713,12 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
     if (mixed) {
       // Mixed precision iterative refinement: inner GMRES on the BF16 copy of L (or the
       // tensor-core products) to inner_tol relative to the current residual.
-      // Inner solves on the multi-RHS fused Arnoldi kernel keep an FP32 Krylov basis (in V's
-      // memory) and an FP32 copy of w: GB300's FP64 pipe made the FP64 Gram-Schmidt the
-      // largest cost of these solves, and they stop at 1e-2.
+      // Inner solves on the fused Arnoldi kernels keep an FP32 Krylov basis (in V's memory)
+      // and an FP32 copy of w: GB300's FP64 pipe made the FP64 Gram-Schmidt the largest cost
+      // of multi-RHS inner solves, and they stop at 1e-2.
       static const bool fp64_basis = std::getenv("NATBEM_FP64_BASIS") != nullptr;
-      const bool fp32_basis = !fp64_basis && nrhs > kArnUnitsMinRhs && ws->coop_blocks > 0 && ws->pbu && ws->wf;
+      const bool fp32_basis =
+          !fp64_basis && ws->coop_blocks > 0 && ws->wf && (nrhs <= kArnUnitsMinRhs || ws->pbu != nullptr);
       a.tol = o.inner_tol;
       for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
         a.maxit = std::min(std::min(o.inner_max_iter, budget), ws->m);
