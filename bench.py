@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -584,7 +585,7 @@ def run_dataset(args):
     """Training-data generation (paper Sec. 3.4): for each of --n-k wavenumbers of the
     interior-source body, re-assemble, solve, draw 10,000 samples at (theta, phi, r) with r in
     [1.5, 3] bounding radii and take |p| there, and compute the 64 x 32 FFAT map of the far
-    field. Reports solves/s and training samples/s."""
+    field; --concurrency wavenumbers in flight. Reports solves/s and training samples/s."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -607,23 +608,42 @@ def run_dataset(args):
     T, P = np.meshgrid(th, ph, indexing="ij")
     dirs = torch.from_numpy(np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    op = nb.Operator.assemble(Vd, Fd, float(prob.ks[0]), opts)
+    # --concurrency workers, each with its own operator and stream, take the wavenumbers in turn
+    # (the library's calls release the GIL and block only their own thread)
+    conc = max(1, min(args.concurrency, len(prob.ks)))
+    if conc > 1:
+        opts.device_loop = 0  # host-polled chunks with several solves in flight (as the batch driver does)
+    streams = [torch.cuda.Stream(dev) for _ in range(conc)]
+    ops = [nb.Operator.assemble(Vd, Fd, float(prob.ks[0]), opts, stream=st.cuda_stream) for st in streams]
+    torch.cuda.synchronize()
 
-    def step():
-        for i, k in enumerate(prob.ks):
-            op.reassemble(float(k), like=Vd)
-            p, info, st = op.solve(Gd[i])
-            op.sample_field(U[i], center, 1.5 * rb, 3.0 * rb, p, Gd[i])
-            op.far_field(dirs, p, Gd[i])
+    def work(w, nw):
+        st, op = streams[w], ops[w]
+        with torch.cuda.stream(st):
+            for i in range(w, len(prob.ks), nw):
+                op.reassemble(float(prob.ks[i]), stream=st.cuda_stream)
+                p, info, s_ = op.solve(Gd[i], stream=st.cuda_stream)
+                op.sample_field(U[i], center, 1.5 * rb, 3.0 * rb, p, Gd[i], stream=st.cuda_stream)
+                op.far_field(dirs, p, Gd[i], stream=st.cuda_stream)
+
+    def step(nw=conc):
+        if nw == 1:
+            work(0, 1)
+            return
+        ths = [threading.Thread(target=work, args=(w, nw)) for w in range(nw)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # per-kernel device times from one untimed step, and the dominant kernel's roofline
+    # per-kernel device times from one untimed step (one worker), and the dominant kernel's roofline
     nb.nat_bem_trace_reset()
     nb.nat_bem_trace_select("")
     nb.nat_bem_trace_enable(True)
-    step()
+    step(1)
     torch.cuda.synchronize()
     nb.nat_bem_trace_enable(False)
     kern = _kernel_table(nb)
@@ -636,15 +656,23 @@ def run_dataset(args):
     launches0 = nb.nat_bem_trace_launches()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
         t0.record(stream)
+        for st in streams:  # the workers' streams start after t0 ...
+            st.wait_event(t0)
         for _ in range(args.steps):
             step()
+        for st in streams:  # ... and t1 follows all of them
+            e = torch.cuda.Event()
+            e.record(st)
+            stream.wait_event(e)
         t1.record(stream)
         torch.cuda.synchronize()
     ms = t0.elapsed_time(t1)
     launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(prob.ks)
-    op.close()
+    for op in ops:
+        op.close()
     roof = None
     if dom:
         d = table[dom]
@@ -656,7 +684,8 @@ def run_dataset(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.prec,
             "data": "synthetic",
             "config": {"workload": f"dataset_{len(prob.F)}tri_{len(prob.ks)}k_{n_samples}samples_ffat64x32",
-                       "samples_per_solve": n_samples, "ffat": [64, 32], "shell": [1.5, 3.0]},
+                       "samples_per_solve": n_samples, "ffat": [64, 32], "shell": [1.5, 3.0],
+                       "in_flight": conc},
             "training_samples_per_s": n_solves * n_samples / (ms * 1e-3),
             "gpu_launches": int(launches),
             "kernels_ms_per_step": {nm: {"ms_total": v[0], "launches": v[1]} for nm, v in kern.items() if v[1]},
