@@ -393,6 +393,55 @@ def run_modal(args):
 NCU_TRAFFIC_MODAL_20480 = {"bf16": 1.7233e9 + 11.57e6}
 
 
+def _pool(torch, dev, conc, make_op):
+    """--concurrency workers over a list of wavenumbers: worker w owns an operator and a stream
+    and takes wavenumbers w, w + nw, ... (the library's calls release the GIL and block only
+    their own thread). Returns (streams, ops)."""
+    streams = [torch.cuda.Stream(dev) for _ in range(conc)]
+    ops = [make_op(st.cuda_stream) for st in streams]
+    torch.cuda.synchronize()
+    return streams, ops
+
+
+def _pool_run(torch, streams, ops, n, body, nw=None):
+    """body(op, stream handle, i) for i < n over the first nw workers; its results by i."""
+    nw = len(ops) if nw is None else nw
+    out = [None] * n
+
+    def work(w):
+        st = streams[w]
+        with torch.cuda.stream(st):
+            for i in range(w, n, nw):
+                out[i] = body(ops[w], st.cuda_stream, i)
+
+    if nw == 1:
+        work(0)
+    else:
+        ths = [threading.Thread(target=work, args=(w,)) for w in range(nw)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+    return out
+
+
+def _pool_time(torch, stream, streams, fn):
+    """Device milliseconds of fn() with the workers' streams bracketed by events on `stream`."""
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for st in streams:
+        st.wait_event(t0)
+    res = fn()
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        stream.wait_event(e)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), res
+
+
 def run_products(args):
     """The multi-RHS operator products alone (profiling and launch-shape sweeps): Y = L X for
     --nrhs seeded complex64 columns on a ring-sphere mesh of --n-tri triangles (default 20480),
@@ -454,8 +503,8 @@ def run_mc(args):
     points; about 0.97 x --n-samples accepted) or with --n-samples uniform random points
     (--random-samples), monopole Neumann data at the samples, --n-k wavenumbers in ka
     [0.5, 12], 1024 field points at radius 4. One step: for each wavenumber, re-assemble the
-    sample operators, solve, evaluate the field. The sampler runs once per body and is timed on
-    its own."""
+    sample operators, solve, evaluate the field; --concurrency wavenumbers in flight. The
+    sampler runs once per body and is timed on its own."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -485,28 +534,32 @@ def run_mc(args):
     Yd, Nd, Pd = (torch.from_numpy(a).to(dev) for a in (Y, N, pts))
     Gd = [torch.from_numpy(g.astype(np.complex64)).to(dev) for g in gs]
     stream = torch.cuda.current_stream(dev)
-    op = nb.Operator.assemble_mc(Yd, Nd, area, float(ks[0]), opts)
+    conc = max(1, min(args.concurrency, len(ks)))
+    if conc > 1:
+        opts.device_loop = 0  # host-polled chunks with several solves in flight
+    streams, ops = _pool(torch, dev, conc, lambda sh: nb.Operator.assemble_mc(Yd, Nd, area, float(ks[0]), opts, stream=sh))
     infos = []
 
-    def step(record=None):
-        out = []
-        for i, k in enumerate(ks):
-            op.reassemble(float(k), like=Yd)
-            p, info, st = op.solve(Gd[i])
-            f = op.evaluate(Pd, p, Gd[i])
-            out.append((p, f))
-            if record is not None:
-                record.append((info.iterations, info.rel_residual, st))
+    def body(op, sh, i):
+        op.reassemble(float(ks[i]), stream=sh)
+        p, info, st = op.solve(Gd[i], stream=sh)
+        f = op.evaluate(Pd, p, Gd[i], stream=sh)
+        return p, f, (info.iterations, info.rel_residual, st)
+
+    def step(record=None, nw=None):
+        out = _pool_run(torch, streams, ops, len(ks), body, nw)
+        if record is not None:
+            record.extend(o[2] for o in out)
         return out
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # per-kernel device times from one untimed step
+    # per-kernel device times from one untimed step (one worker)
     nb.nat_bem_trace_enable(True)
     nb.nat_bem_trace_select("")
     nb.nat_bem_trace_reset()
-    step()
+    step(nw=1)
     torch.cuda.synchronize()
     names = ["assemble_mc", "gemv", "gemv_bf16", "gemv_rhs", "gemv_resid", "ir_residual", "gmres_arnoldi",
              "gmres_lsq", "eval", "eval_reduce"]
@@ -517,14 +570,8 @@ def run_mc(args):
     kern["eval"] = (ev[0] - kern["eval_reduce"][0], ev[1] - kern["eval_reduce"][1])
     nb.nat_bem_trace_enable(False)
     launches0 = nb.nat_bem_trace_launches()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
-        t0.record(stream)
-        for _ in range(args.steps):
-            res = step(infos)
-        t1.record(stream)
-        torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+        ms, res = _pool_time(torch, stream, streams, lambda: [step(infos) for _ in range(args.steps)][-1])
     launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(ks)
     # the matvecs (as for the mesh workloads) and the assembly, which writes L and R (and L's BF16
@@ -564,15 +611,18 @@ def run_mc(args):
         fref = oracle.mc_evaluate(Y, N, area, float(ks[0]), pts, pref, gs[0])
         acc["surface_rel_err_vs_oracle"] = float(np.linalg.norm(p0 - pref) / np.linalg.norm(pref))
         acc["field_rel_err_vs_oracle"] = float(np.linalg.norm(f0 - fref) / np.linalg.norm(fref))
-    op.close()
+    for op in ops:
+        op.close()
     return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16 inner GMRES + f32 refinement", "tf32": "f32"}[args.prec],
             "data": "synthetic",
             "config": {"workload": f"bem_mc_{'random' if args.random_samples else 'poisson'}_{len(Y)}samples_{len(ks)}k",
-                       "samples": len(Y), "ka_range": [0.5, 12.0], "field_points": len(pts), "precision": args.prec},
-            "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
+                       "samples": len(Y), "ka_range": [0.5, 12.0], "field_points": len(pts), "precision": args.prec,
+                       "in_flight": conc},
+            "latency_ms": {"mean": ms / n_solves * conc,
+                           "per": f"one solve (re-assembly + GMRES + field), {conc} in flight"},
             "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
                       "not_converged": sum(1 for i in infos if i[2] != 0)},
             "gpu_launches": int(launches),
@@ -704,7 +754,7 @@ def run_galerkin(args):
     the interior-source body on --n-tri triangles (default 5120, 2562 vertices; P1 pressure, P0
     Neumann data), monopole Neumann data, --n-k wavenumbers log-uniform in ka [0.5, 10], 1024
     field points at radius 4. One step: for each wavenumber, re-assemble (element-pair blocks
-    and their gathers), solve, evaluate the field."""
+    and their gathers), solve, evaluate the field; --concurrency wavenumbers in flight."""
     import torch
     import paper_2506_06190_gb300 as nb
     from paper_2506_06190_gb300 import build as nb_build
@@ -718,42 +768,41 @@ def run_galerkin(args):
     Vd, Fd, Pd = (torch.from_numpy(a).to(dev) for a in (prob.V, prob.F, prob.points))
     Gd = [torch.from_numpy(np.ascontiguousarray(g[:, 0]).astype(np.complex64)).to(dev) for g in prob.neumann]
     stream = torch.cuda.current_stream(dev)
-    op = nb.Operator.assemble_galerkin(Vd, Fd, float(prob.ks[0]), opts)
+    conc = max(1, min(args.concurrency, len(prob.ks)))
+    if conc > 1:
+        opts.device_loop = 0  # host-polled chunks with several solves in flight
+    streams, ops = _pool(torch, dev, conc,
+                         lambda sh: nb.Operator.assemble_galerkin(Vd, Fd, float(prob.ks[0]), opts, stream=sh))
     infos = []
 
-    def step(record=None):
-        out = []
-        for i, k in enumerate(prob.ks):
-            op.reassemble(float(k), like=Vd)
-            p, info, st = op.solve(Gd[i])
-            f = op.evaluate(Pd, p, Gd[i])
-            out.append((p, f))
-            if record is not None:
-                record.append((info.iterations, info.rel_residual, st))
+    def body(op, sh, i):
+        op.reassemble(float(prob.ks[i]), stream=sh)
+        p, info, st = op.solve(Gd[i], stream=sh)
+        f = op.evaluate(Pd, p, Gd[i], stream=sh)
+        return p, f, (info.iterations, info.rel_residual, st)
+
+    def step(record=None, nw=None):
+        out = _pool_run(torch, streams, ops, len(prob.ks), body, nw)
+        if record is not None:
+            record.extend(o[2] for o in out)
         return out
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # per-kernel device times from one untimed step
+    # per-kernel device times from one untimed step (one worker)
     nb.nat_bem_trace_enable(True)
     nb.nat_bem_trace_select("")
     nb.nat_bem_trace_reset()
-    step()
+    step(nw=1)
     torch.cuda.synchronize()
     names = ["gal_regular", "gal_singular", "gal_rowsum_L", "gal_gather_L", "gal_gather_R", "gemv_bf16",
              "gemv_rhs", "gemv_resid", "gmres_arnoldi", "eval", "gal_expand"]
     kern = {nm: nb.nat_bem_trace_kernel(nm) for nm in names}
     nb.nat_bem_trace_enable(False)
     launches0 = nb.nat_bem_trace_launches()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
-        t0.record(stream)
-        for _ in range(args.steps):
-            res = step(infos)
-        t1.record(stream)
-        torch.cuda.synchronize()
-    ms = t0.elapsed_time(t1)
+        ms, res = _pool_time(torch, stream, streams, lambda: [step(infos) for _ in range(args.steps)][-1])
     launches = nb.nat_bem_trace_launches() - launches0
     n_solves = args.steps * len(prob.ks)
     f0 = res[0][1].cpu().numpy()
@@ -766,7 +815,8 @@ def run_galerkin(args):
     # every launch of the traced step together covers the nt x nt pairs of each of its solves
     flops = float(len(prob.ks)) * nt * nt * GAL_FLOPS_PER_PAIR
     tf = flops / (t * 1e-3) / 1e12 if c else None
-    op.close()
+    for op in ops:
+        op.close()
     return {"metric": METRIC, "value": n_solves / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -774,8 +824,9 @@ def run_galerkin(args):
             "data": "synthetic",
             "config": {"workload": f"galerkin_interior_source_{nt}tri_{len(prob.V)}vert_{len(prob.ks)}k",
                        "n_tri": nt, "n_vert": len(prob.V), "ka_range": [0.5, 10.0],
-                       "field_points": len(prob.points), "precision": args.prec},
-            "latency_ms": {"mean": ms / n_solves, "per": "one solve (re-assembly + GMRES + field), sequential"},
+                       "field_points": len(prob.points), "precision": args.prec, "in_flight": conc},
+            "latency_ms": {"mean": ms / n_solves * conc,
+                           "per": f"one solve (re-assembly + GMRES + field), {conc} in flight"},
             "gmres": {"iterations_max": max(i[0] for i in infos), "max_rel_residual": max(i[1] for i in infos),
                       "not_converged": sum(1 for i in infos if i[2] != 0)},
             "gpu_launches": int(launches),
