@@ -218,6 +218,9 @@ NAT_BEM_API nat_bem_status nat_bem_reassemble(nat_bem_op* op, double k, void* cu
  * Solves L p = R g for nrhs right-hand sides (GMRES from p = 0, Sec. 6.1 settings by default).
  *   neumann: nt x nrhs complex64, column-major.  p_out: same layout, receives p.
  *   info: may be NULL.  Blocks until the solve is done.
+ *   cuda_stream: NULL (the legacy default stream) runs the solve on a stream the op owns,
+ *   after the work already queued on the legacy stream (the legacy stream cannot be captured
+ *   into the CUDA graphs the solver replays).
  * Convergence: plain FP32, GMRES's residual estimate reaches tol (the true residual with the
  * FP32 operator, reported in info->rel_residual, can sit above tol at high k). Restarted
  * (opts.restart = m > 0): cycles of at most m iterations, each on the true residual with the

@@ -513,6 +513,18 @@ nat_bem_status nat_bem_solve(nat_bem_op* op, const float* neumann, int32_t nrhs,
       return NAT_BEM_EINVAL;
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
+    if (s == nullptr || s == cudaStreamLegacy) {
+      // the legacy default stream cannot be captured: run on the op's own stream, after the
+      // caller's earlier work on the legacy stream (the solve ends with a host sync, so later
+      // work there sees its results)
+      if (!op->solve_stream) {
+        NB_TRY_CUDA(cudaStreamCreateWithFlags(&op->solve_stream, cudaStreamNonBlocking));
+        NB_TRY_CUDA(cudaEventCreateWithFlags(&op->solve_event, cudaEventDisableTiming));
+      }
+      NB_TRY_CUDA(cudaEventRecord(op->solve_event, cudaStreamLegacy));
+      NB_TRY_CUDA(cudaStreamWaitEvent(op->solve_stream, op->solve_event, 0));
+      s = op->solve_stream;
+    }
     const size_t cnt = (size_t)op->n * nrhs;
     const float2* dg = nullptr;
     float2* tg = nullptr;
@@ -790,6 +802,11 @@ void nat_bem_destroy(nat_bem_op* op) {
   if (op->Ls) dev_free(op->Ls, s);
   galerkin_free(op, s);
   workspace_free(op->ws, s);
+  if (op->solve_stream) {
+    cudaStreamSynchronize(op->solve_stream);
+    cudaStreamDestroy(op->solve_stream);
+  }
+  if (op->solve_event) cudaEventDestroy(op->solve_event);
   delete op;
 }
 

@@ -144,6 +144,8 @@ struct nat_bem_op {
   nat_bem_opts opts{};
   int device = 0;
   cudaStream_t stream = nullptr;       // stream the op was built on (frees are ordered there)
+  cudaStream_t solve_stream = nullptr; // solves called on the legacy default stream run here
+  cudaEvent_t solve_event = nullptr;   // (captured graphs need a non-legacy stream)
   natbem::Geometry geo;
   float2* L = nullptr;                 // n x ld complex64, row-major
   float2* R = nullptr;                 // n x ld complex64, row-major (store_r)

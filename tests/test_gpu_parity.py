@@ -141,6 +141,31 @@ def test_fewer_columns_on_a_reused_workspace(nb, device_loop):
             assert np.array_equal(p, p1), cols
 
 
+def test_default_stream_solve_is_ordered_and_matches_explicit_stream(nb):
+    """A solve called on the legacy default stream runs on the op's own stream (so its GMRES
+    chunks can be captured as graphs): it must still see the Neumann data that a kernel queued
+    just before it on the default stream wrote, and give the bits of the same solve on an
+    explicit stream."""
+    import torch
+    Vs, F = S.ring_sphere(1200)
+    V = S.perturbed_ellipsoid(Vs, 21)
+    g = S.monopole_neumann(V, F, 2.5).astype(np.complex64)
+    with nb.Operator.assemble(V, F, 2.5) as op:
+        torch.cuda.synchronize()
+        gd = torch.zeros(len(F), dtype=torch.complex64, device="cuda")
+        big = torch.randn(4096, 4096, device="cuda")
+        _ = big @ big  # keeps the default stream busy for a while
+        gd.copy_(torch.from_numpy(g).cuda())  # queued behind it, not yet done when solve starts
+        p0, info0, st0 = op.solve(gd)
+        assert st0 == nb.NAT_BEM_OK
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            p1, info1, st1 = op.solve(torch.from_numpy(g).cuda(), stream=st.cuda_stream)
+        torch.cuda.synchronize()
+        assert st1 == nb.NAT_BEM_OK
+    assert np.array_equal(p0.cpu().numpy(), p1.cpu().numpy())
+
+
 def test_device_pointers_match_host(nb):
     import torch
     V, F = S.icosphere(2)
