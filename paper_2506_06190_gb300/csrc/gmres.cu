@@ -911,6 +911,11 @@ constexpr int kArnMaxRows = 512;           // rows per block (n <= 151 * 512 wit
 // in flight) than 72 KiB with 64 registers a thread, which lets two fused kernels and more
 // matvec blocks share an SM (75 solves/s).
 constexpr int kArnPanelBytes = 96 * 1024;
+// The FP32 panel of inner solves: half the bytes per vector, and 48 KiB (about 90 vectors of a
+// block's rows at n = 10240, more than an inner solve reaches) let the kernels of two solves in
+// flight share an SM: 125.3 against 123.6 solves/s with 96 KiB on the four-in-flight bench
+// (64 KiB: 122.9; 32 KiB: 125.4).
+constexpr int kArnPanelBytesF32 = 48 * 1024;
 constexpr int kArnMaxRhs = 256;
 constexpr int kArnUnitsMinRhs = 4;  // more right-hand sides than this: k_arnoldi_units
 constexpr int kArnUnitsPerSm = 2;   // k_arnoldi_units: blocks per SM (at most)
@@ -2399,10 +2404,11 @@ static nat_bem_status gmres_run(nat_bem_op* op, Workspace* ws, const GArgs& a, i
           NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->units_blocks), dim3(256), args, 0, s)));
           continue;
         }
-        int pcap = ws->arn_smem / (int)(ac.Vf ? sizeof(float2) : sizeof(double2));
+        const int smem = ac.Vf ? std::min(ws->arn_smem, kArnPanelBytesF32) : ws->arn_smem;
+        int pcap = smem / (int)(ac.Vf ? sizeof(float2) : sizeof(double2));
         void* args[] = {&ac, &pb, &hr, &bar, &errp, &pcap};
         const void* kern = ac.Vf ? (const void*)k_arnoldi_f32 : (const void*)k_arnoldi;
-        NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->coop_blocks), dim3(256), args, (size_t)ws->arn_smem, s)));
+        NB_LAUNCH("gmres_arnoldi", s, NB_TRY_CUDA(cudaLaunchCooperativeKernel(kern, dim3(ws->coop_blocks), dim3(256), args, (size_t)smem, s)));
         continue;
       }
       const dim3 dot_grid(std::min(it0 + q + 1, std::max(1, a.maxit)), kDotChunks, nrhs);
