@@ -1,6 +1,6 @@
 // Multi-right-hand-side operator products Y = M X (M = L or R, X = nrhs complex vectors).
 //
-// Two engines:
+// Three engines:
 //  * k_tc_gemm: tensor cores (tcgen05.mma, kind::tf32 on the FP32 operator or kind::f16 on its
 //    BF16 copy) for the inner Krylov products of mixed-precision refinement. The complex
 //    product is a real GEMM: row i of the complex64 operator read as 2*ld reals
@@ -17,11 +17,15 @@
 //    (tcgen05.ld) while the next one fills. Each CTA writes one partial tile per row tile it
 //    touched; k_tc_reduce adds a tile's partials in K order in FP64 (a fixed order, so results
 //    do not depend on timing).
-//  * k_cgemm_sk: FP32 CUDA-core complex GEMM (persistent stream-K, 64 rows x up to 64 RHS per
-//    tile, FP32 products summed in FP32 over 128 terms, then carried as float-float pairs) for
-//    the products that must carry full FP32 accuracy: the right-hand side R G, the refinement
-//    residuals and the plain FP32 solve. k_cgemm_fp32 (fixed tiles, FP64 carries) computes the
-//    same product for operators whose leading dimension is not a multiple of 16.
+//  * k_tc_gemm_x6: the products that must carry FP32 accuracy (refinement residuals, the plain
+//    multi-RHS solve) with L from 8 RHS up, on tensor cores: L and X split exactly into three
+//    BF16 pieces, the six piece products with i + j <= 4, the accumulator drained after every
+//    K block into float-float sums.
+//  * k_cgemm_sk: FP32 CUDA-core complex GEMM (persistent stream-K, up to 64 RHS per tile, FP32
+//    products summed in FP32 over 128 terms, then carried as float-float pairs) for the other
+//    FP32-accurate products: the right-hand side R G and products with fewer than 8 RHS.
+//    k_cgemm_fp32 (fixed tiles, FP64 carries) computes the same product for operators whose
+//    leading dimension is odd.
 //
 // Every wait on an mbarrier is bounded; a wait that gives up sets an error flag, the kernel
 // skips its remaining work, waits (bounded) for its own copies, frees its TMEM and returns.
