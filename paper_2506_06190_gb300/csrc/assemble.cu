@@ -41,6 +41,8 @@ __constant__ double c_rule7[7][4];          // barycentric l0, l1, l2 and weight
 constexpr int kMaxAdjPts = 7 * 64;          // 4^3 sub-triangles
 constexpr int kMaxSelfPts = 64;
 __device__ double4 g_adj_rule[kMaxAdjPts];  // parent barycentrics and weight (sum 1)
+__device__ float4 g_adj_ab[kMaxAdjPts];     // barycentrics l1, l2 as FP32 (hi, lo) pairs
+__device__ float g_adj_w[kMaxAdjPts];       // the weight in FP32
 __device__ double2 g_gl[kMaxSelfPts];       // Gauss-Legendre nodes / weights on [-1, 1]
 __constant__ int c_adj_npts;
 __constant__ int c_self_pts;
@@ -131,6 +133,15 @@ nat_bem_status upload_rules(int adj_levels, int self_pts) {
     }
   int np = (int)pts.size();
   NB_TRY_CUDA(cudaMemcpyToSymbol(g_adj_rule, pts.data(), np * sizeof(double4)));
+  std::vector<float4> ab(np);
+  std::vector<float> wf(np);
+  for (int i = 0; i < np; ++i) {
+    const float ah = (float)pts[i].y, bh = (float)pts[i].z;
+    ab[i] = make_float4(ah, (float)(pts[i].y - (double)ah), bh, (float)(pts[i].z - (double)bh));
+    wf[i] = (float)pts[i].w;
+  }
+  NB_TRY_CUDA(cudaMemcpyToSymbol(g_adj_ab, ab.data(), np * sizeof(float4)));
+  NB_TRY_CUDA(cudaMemcpyToSymbol(g_adj_w, wf.data(), np * sizeof(float)));
   NB_TRY_CUDA(cudaMemcpyToSymbol(c_adj_npts, &np, sizeof(int)));
   std::vector<double> gx, gw;
   gauss_legendre_host(self_pts, gx, gw);
@@ -527,13 +538,31 @@ __device__ __forceinline__ void half_warp_sum_df(float s, float c, float& hi, fl
 
 }  // namespace
 
+// D - (a e + b f) for float-float D, e, f and barycentrics a = (ab.x, ab.y), b = (ab.z, ab.w):
+// error-free products and sums (Dekker, Knuth) in round-to-nearest FP32 intrinsics (never
+// contracted), rounded to FP32 once at the end.
+__device__ __forceinline__ float ff_offset(float Dh, float Dl, float4 ab, float eh, float el, float fh, float fl) {
+  const float p = __fmul_rn(ab.x, eh);
+  const float pe = __fmaf_rn(ab.x, el, __fmaf_rn(ab.y, eh, __fmaf_rn(ab.x, eh, -p)));
+  const float q = __fmul_rn(ab.z, fh);
+  const float qe = __fmaf_rn(ab.z, fl, __fmaf_rn(ab.w, fh, __fmaf_rn(ab.z, fh, -q)));
+  const float s = __fadd_rn(p, q);
+  const float sb = __fsub_rn(s, p);
+  const float se = __fadd_rn(__fadd_rn(__fsub_rn(p, __fsub_rn(s, sb)), __fsub_rn(q, sb)), __fadd_rn(pe, qe));
+  const float d = __fsub_rn(Dh, s);
+  const float db = __fsub_rn(d, Dh);
+  const float de = __fadd_rn(__fsub_rn(Dh, __fsub_rn(d, db)), __fsub_rn(-s, db));
+  return __fadd_rn(d, __fadd_rn(de, __fsub_rn(Dl, se)));
+}
+
 // Vertex-sharing pairs (i, j != i): the 7-point rule on the 4^levels sub-triangles of element j,
 // 16 lanes per pair (two pairs per warp; 112 points at levels = 2 is seven per lane). The
-// quadrature point and x_i are close compared with their distance from the origin, so the
-// offset of the point from vertex a of j and d = x_i - y are formed in FP64 from the FP64
-// vertices; d is then exact to FP32 rounding and every factor after it (r, d.n, the phase,
-// G and the hypersingular combination) runs on the FP32 pipe, which GB300 issues ~60x faster
-// than FP64. Per-lane sums are compensated (Kahan) and the 16 lanes are added as double-float.
+// quadrature point and x_i are close compared with their distance from the origin, so
+// d = x_i - y is formed from x_i - v0 and the edges of j (taken in FP64 from the FP64 vertices,
+// once per pair) in float-float arithmetic (ff_offset, about 48 bits); d is then exact to FP32
+// rounding and every factor after it (r, d.n, the phase, G and the hypersingular combination)
+// runs on the FP32 pipe, which GB300 issues ~60x faster than FP64. Per-lane sums are
+// compensated (Kahan) and the 16 lanes are added as double-float.
 __global__ void __launch_bounds__(256)
 k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
                     const double* __restrict__ cen, const double* __restrict__ nrm64,
@@ -549,9 +578,20 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
     j = pr.y;
   }
   const double* t = tri + 9 * j;
-  const double D0 = cen[3 * i] - t[0], D1 = cen[3 * i + 1] - t[1], D2 = cen[3 * i + 2] - t[2];
-  const double e10 = t[3] - t[0], e11 = t[4] - t[1], e12 = t[5] - t[2];
-  const double e20 = t[6] - t[0], e21 = t[7] - t[1], e22 = t[8] - t[2];
+  // D = x_i - v0 and the edges e1 = v1 - v0, e2 = v2 - v0 of triangle j as float-float pairs:
+  // d = D - (l1 e1 + l2 e2) then keeps about 48 bits on the FP32 pipe (GB300's FP64 rate is
+  // about 1/76 of its FP32 rate; this kernel was FP64-pipe-bound)
+  float Dh[3], Dl[3], e1h[3], e1l[3], e2h[3], e2l[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double Dc = cen[3 * i + c] - t[c], e1c = t[3 + c] - t[c], e2c = t[6 + c] - t[c];
+    Dh[c] = (float)Dc;
+    Dl[c] = (float)(Dc - (double)Dh[c]);
+    e1h[c] = (float)e1c;
+    e1l[c] = (float)(e1c - (double)e1h[c]);
+    e2h[c] = (float)e2c;
+    e2l[c] = (float)(e2c - (double)e2h[c]);
+  }
   const float ni0 = (float)nrm64[3 * i], ni1 = (float)nrm64[3 * i + 1], ni2 = (float)nrm64[3 * i + 2];
   const float nj0 = (float)nrm64[3 * j], nj1 = (float)nrm64[3 * j + 1], nj2 = (float)nrm64[3 * j + 2];
   const float nxny = ni0 * nj0 + ni1 * nj1 + ni2 * nj2;
@@ -560,10 +600,10 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
   float Lr = 0.f, Li = 0.f, Rr = 0.f, Ri = 0.f, cLr = 0.f, cLi = 0.f, cRr = 0.f, cRi = 0.f;
   const int np = valid ? c_adj_npts : 0;
   for (int p = l16; p < np; p += 16) {
-    const double4 rl = g_adj_rule[p];
-    const float d0 = (float)(D0 - fma(rl.z, e20, rl.y * e10));
-    const float d1 = (float)(D1 - fma(rl.z, e21, rl.y * e11));
-    const float d2 = (float)(D2 - fma(rl.z, e22, rl.y * e12));
+    const float4 ab = g_adj_ab[p];
+    const float d0 = ff_offset(Dh[0], Dl[0], ab, e1h[0], e1l[0], e2h[0], e2l[0]);
+    const float d1 = ff_offset(Dh[1], Dl[1], ab, e1h[1], e1l[1], e2h[1], e2l[1]);
+    const float d2 = ff_offset(Dh[2], Dl[2], ab, e1h[2], e1l[2], e2h[2], e2l[2]);
     const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
@@ -574,7 +614,7 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
     const float th = fmaf(-nq, kTwoPiLo, fmaf(-nq, kTwoPiHi, rho));
     float sn, cs;
     sincosf(th, &sn, &cs);
-    const float gw = (float)rl.w * scale * rinv;
+    const float gw = g_adj_w[p] * scale * rinv;
     const float Gr = cs * gw, Gi = sn * gw;
     const float rinv2 = rinv * rinv;
     const float qq = dnx * dny * rinv2;
