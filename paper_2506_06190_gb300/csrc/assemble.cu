@@ -566,7 +566,7 @@ __device__ __forceinline__ float ff_offset(float Dh, float Dl, float4 ab, float 
 __global__ void __launch_bounds__(256)
 k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
                     const double* __restrict__ cen, const double* __restrict__ nrm64,
-                    const double* __restrict__ area, int ld, double k, float2* __restrict__ L,
+                    const double* __restrict__ area, int ld, float kf, float kinvf, float2* __restrict__ L,
                     float2* __restrict__ R, uint32_t* __restrict__ Lb) {
   const int64_t pr_idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 4;
   const int l16 = threadIdx.x & 15;
@@ -580,23 +580,38 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
   const double* t = tri + 9 * j;
   // D = x_i - v0 and the edges e1 = v1 - v0, e2 = v2 - v0 of triangle j as float-float pairs:
   // d = D - (l1 e1 + l2 e2) then keeps about 48 bits on the FP32 pipe (GB300's FP64 rate is
-  // about 1/76 of its FP32 rate; this kernel was FP64-pipe-bound)
+  // about 1/76 of its FP32 rate; this kernel was FP64-pipe-bound). The FP64 prologue is dealt
+  // over the pair's 16 lanes (lane c < 9: component c % 3 of D, e1 or e2; lanes 9-14: the two
+  // normals; lane 15: the area factor) and broadcast by shuffles.
+  float vh = 0.f, vl = 0.f;
+  if (l16 < 9) {
+    const int w = l16 / 3, c = l16 % 3;
+    const double v = (w == 0 ? cen[3 * i + c] : t[3 * w + c]) - t[c];
+    vh = (float)v;
+    vl = (float)(v - (double)vh);
+  } else if (l16 < 12) {
+    vh = (float)nrm64[3 * i + (l16 - 9)];
+  } else if (l16 < 15) {
+    vh = (float)nrm64[3 * j + (l16 - 12)];
+  } else {
+    vh = (float)(area[j] * (0.25 / 3.14159265358979323846));
+  }
   float Dh[3], Dl[3], e1h[3], e1l[3], e2h[3], e2l[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const double Dc = cen[3 * i + c] - t[c], e1c = t[3 + c] - t[c], e2c = t[6 + c] - t[c];
-    Dh[c] = (float)Dc;
-    Dl[c] = (float)(Dc - (double)Dh[c]);
-    e1h[c] = (float)e1c;
-    e1l[c] = (float)(e1c - (double)e1h[c]);
-    e2h[c] = (float)e2c;
-    e2l[c] = (float)(e2c - (double)e2h[c]);
+    Dh[c] = __shfl_sync(0xffffffffu, vh, c, 16);
+    Dl[c] = __shfl_sync(0xffffffffu, vl, c, 16);
+    e1h[c] = __shfl_sync(0xffffffffu, vh, 3 + c, 16);
+    e1l[c] = __shfl_sync(0xffffffffu, vl, 3 + c, 16);
+    e2h[c] = __shfl_sync(0xffffffffu, vh, 6 + c, 16);
+    e2l[c] = __shfl_sync(0xffffffffu, vl, 6 + c, 16);
   }
-  const float ni0 = (float)nrm64[3 * i], ni1 = (float)nrm64[3 * i + 1], ni2 = (float)nrm64[3 * i + 2];
-  const float nj0 = (float)nrm64[3 * j], nj1 = (float)nrm64[3 * j + 1], nj2 = (float)nrm64[3 * j + 2];
+  const float ni0 = __shfl_sync(0xffffffffu, vh, 9, 16), ni1 = __shfl_sync(0xffffffffu, vh, 10, 16),
+              ni2 = __shfl_sync(0xffffffffu, vh, 11, 16);
+  const float nj0 = __shfl_sync(0xffffffffu, vh, 12, 16), nj1 = __shfl_sync(0xffffffffu, vh, 13, 16),
+              nj2 = __shfl_sync(0xffffffffu, vh, 14, 16);
+  const float scale = __shfl_sync(0xffffffffu, vh, 15, 16);
   const float nxny = ni0 * nj0 + ni1 * nj1 + ni2 * nj2;
-  const float scale = (float)(area[j] * (0.25 / 3.14159265358979323846));
-  const float kf = (float)k, kinvf = (float)(1.0 / k);
   float Lr = 0.f, Li = 0.f, Rr = 0.f, Ri = 0.f, cLr = 0.f, cLi = 0.f, cRr = 0.f, cRi = 0.f;
   const int np = valid ? c_adj_npts : 0;
   for (int p = l16; p < np; p += 16) {
@@ -755,7 +770,8 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
     const int64_t adj_blocks = (g.n_near * 16 + threads - 1) / threads;
     if (adj_blocks > 0)
       NB_LAUNCH("assemble_near", s, k_assemble_adjacent<<<(unsigned)adj_blocks, (unsigned)threads, 0, s>>>(
-          g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, op->k, op->L, op->R, bf16_target(op)));
+          g.near_pairs, g.n_near, g.tri, g.cen, g.nrm64, g.area, ld, (float)op->k, (float)(1.0 / op->k), op->L,
+          op->R, bf16_target(op)));
     const int64_t self_blocks = ((int64_t)n * 32 + threads - 1) / threads;
     NB_LAUNCH("assemble_self", s, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, s>>>(
         n, g.tri, g.cen, ld, op->k, op->L, op->R, bf16_target(op)));
