@@ -13,9 +13,12 @@
 //                        staged through shared memory and read as broadcasts, coalesced row
 //                        stores of L and R. Pairs that share a vertex are skipped.
 //   k_assemble_adjacent  vertex-sharing pairs (j != i), 16 lanes per pair over the subdivided
-//                        rule: d = x - y formed in FP64 (where it cancels), everything after it
-//                        in FP32 with compensated sums.
-//   k_assemble_self      the self pair, one warp per element: the angular integrals in FP64.
+//                        rule: d = x - y formed in float-float arithmetic (where it cancels)
+//                        from per-pair FP64 differences, everything after it in FP32 with
+//                        compensated sums.
+//   k_assemble_self      the self pair, one warp per element: the vertices relative to the
+//                        centroid in FP64, the edge geometry and the angular integrals in FP32
+//                        with cancellation-free forms.
 //
 // With d = x - y, r = |d|, rho = k r, q = (d.n_x)(d.n_y)/r^2 the integrands reduce to
 //   dG/dn_y + beta H = G/r^2 [ (d.n_y - b/k) + i (a/k - rho d.n_y) ],
@@ -43,7 +46,7 @@ constexpr int kMaxSelfPts = 64;
 __device__ double4 g_adj_rule[kMaxAdjPts];  // parent barycentrics and weight (sum 1)
 __device__ float4 g_adj_ab[kMaxAdjPts];     // barycentrics l1, l2 as FP32 (hi, lo) pairs
 __device__ float g_adj_w[kMaxAdjPts];       // the weight in FP32
-__device__ double2 g_gl[kMaxSelfPts];       // Gauss-Legendre nodes / weights on [-1, 1]
+__device__ float2 g_glf[kMaxSelfPts];       // Gauss-Legendre nodes / weights on [-1, 1]
 __constant__ int c_adj_npts;
 __constant__ int c_self_pts;
 
@@ -145,9 +148,9 @@ nat_bem_status upload_rules(int adj_levels, int self_pts) {
   NB_TRY_CUDA(cudaMemcpyToSymbol(c_adj_npts, &np, sizeof(int)));
   std::vector<double> gx, gw;
   gauss_legendre_host(self_pts, gx, gw);
-  std::vector<double2> gl(self_pts);
-  for (int i = 0; i < self_pts; ++i) gl[i] = make_double2(gx[i], gw[i]);
-  NB_TRY_CUDA(cudaMemcpyToSymbol(g_gl, gl.data(), self_pts * sizeof(double2)));
+  std::vector<float2> glf(self_pts);
+  for (int i = 0; i < self_pts; ++i) glf[i] = make_float2((float)gx[i], (float)gw[i]);
+  NB_TRY_CUDA(cudaMemcpyToSymbol(g_glf, glf.data(), self_pts * sizeof(float2)));
   NB_TRY_CUDA(cudaMemcpyToSymbol(c_self_pts, &self_pts, sizeof(int)));
   return NAT_BEM_OK;
 }
@@ -496,14 +499,8 @@ k_assemble_regular_x2(const float4* __restrict__ c_hi, const float4* __restrict_
   }
 }
 
-// ------------------------------------------------------------------ near pairs (FP64)
+// ------------------------------------------------------------- near pairs and self terms
 namespace {
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Compensated FP32 running sum (Kahan 1965): s - c is the exact sum to about twice FP32 precision.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
@@ -657,77 +654,108 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
   }
 }
 
-// Self terms (flat element, collocation at the centroid), one warp per element, FP64:
+// Self terms (flat element, collocation at the centroid), one warp per element (the vertices
+// relative to the centroid in FP64, everything after them in FP32):
 //   S = (1/4pi) sum_e int (e^{ikR} - 1)/(ik) dpsi,   FP = (1/4pi) sum_e int (ik - e^{ikR}/R) dpsi,
 // with R = d_e / cos(psi) the distance from the centroid to edge e along the ray (radial part
 // analytic, Hadamard finite part of the hypersingular term); L_ii = 1/2 - beta FP and
 // R_ii = -S - beta/2 with beta = i/k.
 __global__ void __launch_bounds__(256)
 k_assemble_self(int n, const double* __restrict__ tri, const double* __restrict__ cen, int ld,
-                double k, float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb) {
+                float kf, float kinvf, float2* __restrict__ L, float2* __restrict__ R, uint32_t* __restrict__ Lb) {
   const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (i >= n) return;  // whole warps
-  const double kinv = 1.0 / k;
-  const double inv4pi = 0.25 / 3.14159265358979323846;
-  const double x0 = cen[3 * i], x1 = cen[3 * i + 1], x2 = cen[3 * i + 2];
+  const float inv4pi = (float)(0.25 / 3.14159265358979323846);
   const double* t = tri + 9 * i;
   const int ns = c_self_pts;
   // per edge e (lanes 0..2): the distance d_e from the centroid to the edge line and the
-  // angles of the edge's end points seen from the centroid, measured from the perpendicular
-  double de = 0.0, mid = 0.0, half = 0.0;
+  // angles of the edge's end points seen from the centroid, measured from the perpendicular.
+  // The end points relative to the centroid are formed in FP64 (the coordinates are far larger
+  // than the element) and the rest in FP32 on those element-sized vectors.
+  float de = 0.f, mid = 0.f, half = 0.f;
   if (lane < 3) {
     const double* P = t + 3 * lane;
     const double* Q = t + 3 * ((lane + 1) % 3);
-    double u0 = Q[0] - P[0], u1 = Q[1] - P[1], u2 = Q[2] - P[2];
-    const double ul = rsqrt(u0 * u0 + u1 * u1 + u2 * u2);
+    float p[3], q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double xc = cen[3 * i + c];
+      p[c] = (float)(P[c] - xc);
+      q[c] = (float)(Q[c] - xc);
+    }
+    float u0 = q[0] - p[0], u1 = q[1] - p[1], u2 = q[2] - p[2];
+    const float ul = rsqrtf(fmaf(u0, u0, fmaf(u1, u1, u2 * u2)));
     u0 *= ul;
     u1 *= ul;
     u2 *= ul;
     // positions of P and Q along the edge line, relative to the foot of the perpendicular
-    const double sP = (P[0] - x0) * u0 + (P[1] - x1) * u1 + (P[2] - x2) * u2;
-    const double sQ = (Q[0] - x0) * u0 + (Q[1] - x1) * u1 + (Q[2] - x2) * u2;
-    const double f0 = P[0] - x0 - sP * u0, f1 = P[1] - x1 - sP * u1, f2 = P[2] - x2 - sP * u2;
-    de = sqrt(f0 * f0 + f1 * f1 + f2 * f2);
-    const double psiP = atan2(sP, de), psiQ = atan2(sQ, de);
-    half = 0.5 * (psiQ - psiP);
-    mid = 0.5 * (psiQ + psiP);
+    const float sP = fmaf(p[0], u0, fmaf(p[1], u1, p[2] * u2));
+    const float sQ = fmaf(q[0], u0, fmaf(q[1], u1, q[2] * u2));
+    const float f0 = fmaf(-sP, u0, p[0]), f1 = fmaf(-sP, u1, p[1]), f2 = fmaf(-sP, u2, p[2]);
+    de = sqrtf(fmaf(f0, f0, fmaf(f1, f1, f2 * f2)));
+    const float psiP = atan2f(sP, de), psiQ = atan2f(sQ, de);
+    half = 0.5f * (psiQ - psiP);
+    mid = 0.5f * (psiQ + psiP);
   }
-  double de_e[3], mid_e[3], half_e[3];
+  float dEf[3], mEf[3], hEf[3];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
-    de_e[e] = __shfl_sync(0xffffffffu, de, e);
-    mid_e[e] = __shfl_sync(0xffffffffu, mid, e);
-    half_e[e] = __shfl_sync(0xffffffffu, half, e);
+    dEf[e] = __shfl_sync(0xffffffffu, de, e);
+    mEf[e] = __shfl_sync(0xffffffffu, mid, e);
+    hEf[e] = __shfl_sync(0xffffffffu, half, e);
   }
-  double Sre = 0, Sim = 0, Fre = 0, Fim = 0;
+  // The angular points in FP32 (GB300's FP64 rate is about 1/76 of its FP32 rate), with
+  // cancellation-free forms: with x = kR and h = x/2, (e^{ikR} - 1)/(ik) = (sin x + 2i sin^2 h)/k,
+  // cos x = cos^2 h - sin^2 h, and k - sin(kR)/R = k (1 - sinc x) from its Taylor series
+  // sum_{n>=1} (-1)^(n+1) x^(2n) / (2n+1)! below x = 1.5 (six terms: below 2e-8 of the value)
+  // and 1 - sin(x)/x above (where 1 - sinc x >= 0.33).
+  float Sre = 0.f, Sim = 0.f, Fre = 0.f, Fim = 0.f;
   for (int p = lane; p < 3 * ns; p += 32) {
     const int e = p / ns, g = p - e * ns;
-    const double dE = e == 0 ? de_e[0] : (e == 1 ? de_e[1] : de_e[2]);
-    const double mE = e == 0 ? mid_e[0] : (e == 1 ? mid_e[1] : mid_e[2]);
-    const double hE = e == 0 ? half_e[0] : (e == 1 ? half_e[1] : half_e[2]);
-    const double2 gl = g_gl[g];
-    const double psi = mE + hE * gl.x;
-    const double cpsi = cos(psi);
-    const double Rr = dE / cpsi;
-    const double invR = cpsi / dE;
-    const double wq = hE * gl.y;
-    double sn, cs;
-    sincos(k * Rr, &sn, &cs);
-    // (e^{ikR} - 1)/(ik) = sin(kR)/k + i (1 - cos(kR))/k
-    Sre += wq * sn * kinv;
-    Sim += wq * (1.0 - cs) * kinv;
-    Fre -= wq * cs * invR;
-    Fim += wq * (k - sn * invR);
+    const float dE = e == 0 ? dEf[0] : (e == 1 ? dEf[1] : dEf[2]);
+    const float mE = e == 0 ? mEf[0] : (e == 1 ? mEf[1] : mEf[2]);
+    const float hE = e == 0 ? hEf[0] : (e == 1 ? hEf[1] : hEf[2]);
+    const float2 gl = g_glf[g];
+    const float psi = fmaf(hE, gl.x, mE);
+    const float cpsi = cosf(psi);
+    const float Rr = dE / cpsi;
+    const float invR = cpsi / dE;
+    const float wq = hE * gl.y;
+    const float x = kf * Rr;
+    float s2, c2;
+    sincosf(0.5f * x, &s2, &c2);
+    const float sn = 2.0f * s2 * c2, omc = 2.0f * s2 * s2, cs = (c2 - s2) * (c2 + s2);
+    float omsinc;  // 1 - sin(x)/x
+    if (x < 1.5f) {
+      const float x2 = x * x;
+      omsinc = x2 * (1.0f / 6.0f -
+                     x2 * (1.0f / 120.0f -
+                           x2 * (1.0f / 5040.0f -
+                                 x2 * (1.0f / 362880.0f - x2 * (1.0f / 39916800.0f - x2 * (1.0f / 6227020800.0f))))));
+    } else {
+      omsinc = 1.0f - sn / x;
+    }
+    Sre = fmaf(wq, sn * kinvf, Sre);
+    Sim = fmaf(wq, omc * kinvf, Sim);
+    Fre = fmaf(-wq, cs * invR, Fre);
+    Fim = fmaf(wq, kf * omsinc, Fim);
   }
-  Sre = warp_sum(Sre) * inv4pi;
-  Sim = warp_sum(Sim) * inv4pi;
-  Fre = warp_sum(Fre) * inv4pi;
-  Fim = warp_sum(Fim) * inv4pi;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Sre += __shfl_xor_sync(0xffffffffu, Sre, o);
+    Sim += __shfl_xor_sync(0xffffffffu, Sim, o);
+    Fre += __shfl_xor_sync(0xffffffffu, Fre, o);
+    Fim += __shfl_xor_sync(0xffffffffu, Fim, o);
+  }
+  Sre *= inv4pi;
+  Sim *= inv4pi;
+  Fre *= inv4pi;
+  Fim *= inv4pi;
   if (lane == 0) {
-    const float2 lv = make_float2((float)(0.5 + Fim * kinv), (float)(-Fre * kinv));
+    const float2 lv = make_float2(fmaf(Fim, kinvf, 0.5f), -Fre * kinvf);
     L[(size_t)i * ld + i] = lv;
-    R[(size_t)i * ld + i] = make_float2((float)(-Sre), (float)(-Sim - 0.5 * kinv));
+    R[(size_t)i * ld + i] = make_float2(-Sre, fmaf(-0.5f, kinvf, -Sim));
     if (Lb) Lb[(size_t)i * ld + i] = pack_bf16(lv.x, lv.y);
   }
 }
@@ -774,7 +802,7 @@ nat_bem_status assemble_operators(nat_bem_op* op, cudaStream_t s) {
           op->R, bf16_target(op)));
     const int64_t self_blocks = ((int64_t)n * 32 + threads - 1) / threads;
     NB_LAUNCH("assemble_self", s, k_assemble_self<<<(unsigned)self_blocks, (unsigned)threads, 0, s>>>(
-        n, g.tri, g.cen, ld, op->k, op->L, op->R, bf16_target(op)));
+        n, g.tri, g.cen, ld, (float)op->k, (float)(1.0 / op->k), op->L, op->R, bf16_target(op)));
     NB_CHECK_LAUNCH();
   }
   // regular pairs: columns in blocks of 256 (two columns a thread in the paired form), rows
