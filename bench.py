@@ -1347,9 +1347,9 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": my_rate_time / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp32": "f32 (+f64 near pairs and Krylov)",
-                  "bf16": "bf16 inner GMRES + f32 refinement (+f64 near pairs and Krylov)",
-                  "fp16": "fp16 (row-scaled) inner GMRES + f32 refinement (+f64 near pairs and Krylov)",
+        "dtype": {"fp32": "f32 (+f64 Krylov)",
+                  "bf16": "bf16 inner GMRES + f32 refinement (+f64 Hessenberg and refinement sums)",
+                  "fp16": "fp16 (row-scaled) inner GMRES + f32 refinement (+f64 Hessenberg and refinement sums)",
                   "tf32": "f32 (one RHS: TF32 saves no bytes)"}[args.prec],
         "data": "synthetic",
         "config": {"workload": f"interior_source_{res['n']}tri_{len(prob.ks)}k", "n_tri": res["n"],
