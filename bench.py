@@ -834,7 +834,7 @@ def run_galerkin(args):
             "roofline": {"kernel": "gal_regular", "bound": "alu", "achieved": tf, "peak": fp32_peak,
                          "unit": "TFLOP/s", "frac": (tf / fp32_peak) if tf else None, "traffic": None,
                          "flops_per_pair": GAL_FLOPS_PER_PAIR,
-                         "peak_source": "derived: 128 FP32 lanes x 152 SMs x 2 x max SM clock"},
+                         "peak_source": f"derived: 128 FP32 lanes x {sm_count()} SMs x 2 x max SM clock"},
             "accuracy": acc, "clocks": clk.summary()}
 
 

@@ -557,9 +557,10 @@ __device__ __forceinline__ float ff_offset(float Dh, float Dl, float4 ab, float 
 // quadrature point and x_i are close compared with their distance from the origin, so
 // d = x_i - y is formed from x_i - v0 and the edges of j (taken in FP64 from the FP64 vertices,
 // once per pair) in float-float arithmetic (ff_offset, about 48 bits); d is then exact to FP32
-// rounding and every factor after it (r, d.n, the phase, G and the hypersingular combination)
-// runs on the FP32 pipe, which GB300 issues ~60x faster than FP64. Per-lane sums are
-// compensated (Kahan) and the 16 lanes are added as double-float.
+// rounding. The normal components d.n_i and d.n_j come from per-pair FP64 dot products (they
+// cancel for nearly coplanar neighbours). Everything after that (r, the phase, G and the
+// hypersingular combination) runs on the FP32 pipe, which GB300 issues ~60x faster than FP64.
+// Per-lane sums are compensated (Kahan) and the 16 lanes are added as double-float.
 __global__ void __launch_bounds__(256)
 k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const double* __restrict__ tri,
                     const double* __restrict__ cen, const double* __restrict__ nrm64,
@@ -581,11 +582,14 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
   // over the pair's 16 lanes (lane c < 9: component c % 3 of D, e1 or e2; lanes 9-14: the two
   // normals; lane 15: the area factor) and broadcast by shuffles.
   float vh = 0.f, vl = 0.f;
+  double pi = 0.0, pj = 0.0;  // lanes 0..8: component c of D, e1 or e2 times n_i,c and n_j,c
   if (l16 < 9) {
     const int w = l16 / 3, c = l16 % 3;
     const double v = (w == 0 ? cen[3 * i + c] : t[3 * w + c]) - t[c];
     vh = (float)v;
     vl = (float)(v - (double)vh);
+    pi = v * nrm64[3 * i + c];
+    pj = v * nrm64[3 * j + c];
   } else if (l16 < 12) {
     vh = (float)nrm64[3 * i + (l16 - 9)];
   } else if (l16 < 15) {
@@ -608,6 +612,21 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
   const float nj0 = __shfl_sync(0xffffffffu, vh, 12, 16), nj1 = __shfl_sync(0xffffffffu, vh, 13, 16),
               nj2 = __shfl_sync(0xffffffffu, vh, 14, 16);
   const float scale = __shfl_sync(0xffffffffu, vh, 15, 16);
+  // d.n_i and d.n_j are O(theta |d|) for nearly coplanar neighbours (theta the angle between
+  // them): as FP32 dot products with FP32-rounded normals they carry an absolute error of about
+  // 6e-8 |d|, which at low k (beta = i/k weights d.n_i in R) reached 2e-6 of an entry. So the
+  // pair's D.n_i, e1.n_i, e2.n_i and D.n_j are FP64 dot products with the FP64 normals (summed
+  // over the three lanes of each vector), and per point d.n_i = D.n_i - a e1.n_i - b e2.n_i has
+  // no cancellation; d.n_j = D.n_j on the whole flat element j (its edges are normal to n_j).
+  const int g3 = (l16 / 3) * 3;  // first lane of this lane's vector (lanes 9..15: unused values)
+  const double si = __shfl_sync(0xffffffffu, pi, g3, 16) + __shfl_sync(0xffffffffu, pi, g3 + 1, 16) +
+                    __shfl_sync(0xffffffffu, pi, g3 + 2, 16);
+  const double sj = __shfl_sync(0xffffffffu, pj, g3, 16) + __shfl_sync(0xffffffffu, pj, g3 + 1, 16) +
+                    __shfl_sync(0xffffffffu, pj, g3 + 2, 16);
+  const float fi = (float)si, fj = (float)sj;
+  const float Dni = __shfl_sync(0xffffffffu, fi, 0, 16), E1i = __shfl_sync(0xffffffffu, fi, 3, 16),
+              E2i = __shfl_sync(0xffffffffu, fi, 6, 16);
+  const float dny = __shfl_sync(0xffffffffu, fj, 0, 16);
   const float nxny = ni0 * nj0 + ni1 * nj1 + ni2 * nj2;
   float Lr = 0.f, Li = 0.f, Rr = 0.f, Ri = 0.f, cLr = 0.f, cLi = 0.f, cRr = 0.f, cRi = 0.f;
   const int np = valid ? c_adj_npts : 0;
@@ -619,8 +638,7 @@ k_assemble_adjacent(const int2* __restrict__ pairs, int64_t n_pairs, const doubl
     const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    const float dnx = fmaf(d0, ni0, fmaf(d1, ni1, d2 * ni2));
-    const float dny = fmaf(d0, nj0, fmaf(d1, nj1, d2 * nj2));
+    const float dnx = fmaf(-ab.x, E1i, fmaf(-ab.z, E2i, Dni));
     const float rho = kf * r;
     const float nq = rintf(rho * kInvTwoPi);
     const float th = fmaf(-nq, kTwoPiLo, fmaf(-nq, kTwoPiHi, rho));

@@ -4,7 +4,9 @@ Tolerances (from the arithmetic, stated where used):
   * operator rows: relative L2 per row <= 1e-5. The regular entries are FP32 kernel values
     summed over 7 points (about 40 FP32 operations each, relative rounding ~1e-6) with the
     phase reduced to [-pi, pi] and taken from the hardware sine/cosine (absolute error ~4e-7);
-    the self and vertex-sharing entries are FP64 rounded once to complex64 (~6e-8).
+    the self and vertex-sharing entries take d = x - y in float-float arithmetic (or, for the
+    self term, the vertices relative to the centroid in FP64) and FP32 after that, with no
+    cancelling forms: each term ~1e-7 relative, checked elementwise at 1e-6.
   * surface and field pressure: relative L2 <= 1e-4, the accuracy target of the solver. The
     GPU solve stops at a relative residual of 1e-6 against an FP32 operator; the oracle solves
     to 1e-12 in FP64.
@@ -54,7 +56,7 @@ def test_operator_entries(nb, oracle_lib, mesh, k):
         Rg = op.rows(1, 0, op.n).astype(np.complex128)
     assert np.max(_rowwise(Lg, L)) < OP_TOL
     assert np.max(_rowwise(Rg, R)) < OP_TOL
-    # the self and vertex-sharing entries (FP64 on the GPU) are accurate to complex64 rounding
+    # the self and vertex-sharing entries (float-float d, FP32 after it) are accurate elementwise
     near = np.array([[len(set(F[i]) & set(F[j])) > 0 for j in range(len(F))] for i in range(len(F))])
     assert np.max(np.abs(Lg - L)[near] / np.abs(L)[near]) < 1e-6
     assert np.max(np.abs(Rg - R)[near] / np.abs(R)[near]) < 1e-6
@@ -247,6 +249,11 @@ def test_full_size_interior_source(nb, oracle_lib, full_size_ref, ka, prec):
             Lg = np.concatenate([op.rows(0, int(r), 1) for r in ref["rows"]]).astype(np.complex128)
             Rg = np.concatenate([op.rows(1, int(r), 1) for r in ref["rows"]]).astype(np.complex128)
             assert np.max(_rowwise(Lg, ref["Lr"])) < OP_TOL and np.max(_rowwise(Rg, ref["Rr"])) < OP_TOL
+            # each sampled row's self and vertex-sharing entries, elementwise as on small meshes
+            for t, r in enumerate(ref["rows"]):
+                near = np.isin(F, F[int(r)]).any(axis=1)
+                for gpu, orc in ((Lg[t], ref["Lr"][t]), (Rg[t], ref["Rr"][t])):
+                    assert np.max(np.abs(gpu - orc)[near] / np.abs(orc)[near]) < 1e-6, (ka, int(r))
         p, info, st = op.solve(g)
         assert st == nb.NAT_BEM_OK, nb.nat_bem_last_error()
         if prec != "fp32":
