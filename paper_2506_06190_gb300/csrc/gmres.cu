@@ -922,6 +922,21 @@ constexpr int kArnUnitsPerSm = 2;   // k_arnoldi_units: blocks per SM (at most)
 // mixed refinement: a stalled sweep with every open true residual within this factor of the
 // tolerance ends the solve (the FP32 residual product's rounding floor)
 constexpr double kResidualFloor = 4.0;
+// mixed refinement: the inner tolerance of a sweep is inner_tol, loosened once the open true
+// residuals are close to the target: kSweepMargin x (tol / largest open residual) is the
+// contraction still missing (with a margin), rounded down to inner_tol x 2^e, e <= kSweepMaxDoubling
+// (few distinct values, so few captured graphs)
+constexpr double kSweepMargin = 0.3;
+constexpr int kSweepMaxDoubling = 5;
+
+// The inner tolerance of the next refinement sweep when the largest open relative residual is
+// rho (tol: the outer target; base: the configured inner tolerance).
+inline double sweep_inner_tol(double base, double tol, double rho) {
+  double want = base;
+  const double missing = kSweepMargin * tol / std::max(rho, 1e-300);
+  for (int e = 0; e < kSweepMaxDoubling && 2.0 * want <= missing && 2.0 * want < 1.0; ++e) want *= 2.0;
+  return want;
+}
 
 // Rows per work unit of k_arnoldi_units: about four units per block, 64 <= unit <= n.
 inline int arnoldi_unit(int n, int nrhs, int blocks) {
@@ -2725,8 +2740,15 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
       static const bool fp64_basis = std::getenv("NATBEM_FP64_BASIS") != nullptr;
       const bool fp32_basis =
           !fp64_basis && ws->coop_blocks > 0 && ws->wf && (nrhs <= kArnUnitsMinRhs || ws->pbu != nullptr);
-      a.tol = o.inner_tol;
+      // The last sweeps need only the contraction still missing to the outer target, so
+      // their inner tolerance is loosened (sweep_inner_tol); NATBEM_FIXED_INNER_TOL keeps
+      // inner_tol for every sweep.
+      static const bool fixed_inner = std::getenv("NATBEM_FIXED_INNER_TOL") != nullptr;
       for (int sweep = 0; sweep < o.max_refinements && budget > 0; ++sweep) {
+        double rho = 0.0;
+        for (int q = 0; q < nrhs; ++q)
+          if (!od[q]) rho = std::max(rho, sweep == 0 ? 1.0 : prev[q]);
+        a.tol = fixed_inner ? o.inner_tol : sweep_inner_tol(o.inner_tol, o.tol, rho);
         a.maxit = std::min(std::min(o.inner_max_iter, budget), ws->m);
         a.Vf = fp32_basis ? reinterpret_cast<float2*>(ws->V) : nullptr;
         NB_TRY(sweep_once(inner));
@@ -2740,6 +2762,9 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
         // of the FP32 residual product itself (on modal low-k solves the sweeps contract by
         // 0.01-0.09 down to 1-2e-6 and then by 0.7, and FP32 GMRES on the correction equation
         // ends at the same level): the solve stops there instead.
+        // a stall: some open residual contracted by a factor above 0.1, or above twice the
+        // inner tolerance of a loosened sweep
+        const double stall = std::max(0.1, 2.0 * a.tol);
         double worst = 0.0;
         bool at_floor = true;
         for (int q = 0; q < nrhs; ++q)
@@ -2747,12 +2772,12 @@ nat_bem_status solve_impl(nat_bem_op* op, const float2* d_neumann, int nrhs, flo
             worst = std::max(worst, rt[q] / prev[q]);
             at_floor = at_floor && rt[q] <= kResidualFloor * o.tol;
           }
-        if (worst > 0.1 && at_floor) {
+        if (worst > stall && at_floor) {
           converged = true;
           for (int q = 0; q < nrhs; ++q) conv[q] = 1;
           break;
         }
-        if (worst > 0.1 || budget <= 0 || sweep + 1 >= o.max_refinements) {
+        if (worst > stall || budget <= 0 || sweep + 1 >= o.max_refinements) {
           finish = true;
           break;
         }
