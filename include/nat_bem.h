@@ -81,7 +81,7 @@ typedef struct {
   int32_t inner_max_iter;    /* mixed: iterations per inner solve (60)                            */
   double inner_tol;          /* mixed: relative tolerance of each inner solve (1e-2). A sweep    */
                              /* near the end asks only for the contraction still missing,        */
-                             /* 0.3 tol / (largest open relative residual), where that is looser: */
+                             /* 0.7 tol / (largest open relative residual), where that is looser: */
                              /* inner_tol x 2^e for the largest e <= 5 that stays within it       */
   int32_t max_refinements;   /* mixed: outer refinement sweeps (10)                               */
   int32_t restart;           /* GMRES(m): Krylov vectors kept, m in 1..255; 0 = unrestarted (0).  */
