@@ -56,3 +56,15 @@ def test_peaks_fall_back_when_unmeasured(bench, tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     peaks, kind = bench._peaks()
     assert kind == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
+
+
+def test_sustained_rate_uses_the_streams_own_rate(bench):
+    """A seeded Poisson stream's mean rate differs from the nominal one: the server is judged
+    against the rate the stream actually offered, and a growing queue fails it."""
+    # 300 requests whose last arrival is at 6.92 s offer 43.4 req/s; 42.7 served/s keeps up
+    offered, served, ok = bench._sustained(300, 6.915, 300 / 42.7, 339.0, 283.0)
+    assert abs(offered - 300 / 6.915) < 1e-12 and abs(served - 42.7) < 1e-9 and ok
+    # the same completions against a stream that really offered 50 req/s do not
+    assert not bench._sustained(300, 6.0, 300 / 42.7, 339.0, 283.0)[2]
+    # keeping up on average while the last third waits twice as long as the first: a growing queue
+    assert not bench._sustained(300, 6.915, 300 / 43.0, 300.0, 600.0)[2]
