@@ -1062,6 +1062,13 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
         }
         __syncthreads();
       }
+    } else if (a.nrhs == 1 && pass == 0) {
+      // block 0 owns no rows: while the others form their partial sums it fetches the earlier
+      // rotations its Givens update needs after the second barrier
+      for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        s_cs[c] = a.cs[c];
+        s_sn[c] = a.sn[c];
+      }
     }
     grid_sync(bar, bar + 1, G, err);
     // (R) totals over blocks 1..G-1, one warp per (RHS, column), fixed order
@@ -1095,14 +1102,14 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
     for (int s = 0; s < a.nrhs; ++s) {
       if (s_act[s] < want) continue;
       const double2* hs = hr + (size_t)s * ps;
-      for (int c = threadIdx.x; c <= j; c += blockDim.x) s_h[c] = hs[c];
+      for (int c = threadIdx.x; c <= j + 1; c += blockDim.x) s_h[c] = hs[c];  // with ||w||^2
       __syncthreads();
       if (warp == 0) {
         double t = 0.0;
         for (int c = lane; c <= j; c += 32) t += cabs2(s_h[c]);
         t = warp_sum(t);
         if (lane == 0) {
-          const double wn2 = hs[j + 1].x;
+          const double wn2 = s_h[j + 1].x;
           const double hn2 = fmax(wn2 - t, 0.0);
           // second pass only after cancellation by more than 100x in ||w - V h||: one FP64
           // pass then leaves components ~1e-14 along V, far below what GMRES notices
@@ -1123,7 +1130,7 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi(GArgs a, double2* __restrict
           const double2 t = pass == 0 ? s_h[c] : cadd(a.hcol[ho + c], s_h[c]);
           if (!last) a.hcol[ho + c] = t;
           s_acc[c] = t;
-          if (c < j) {
+          if (c < j && a.nrhs > 1) {  // one RHS: block 0 fetched them during the partial sums
             s_cs[c] = a.cs[(size_t)s * a.m + c];
             s_sn[c] = a.sn[(size_t)s * a.m + c];
           }
@@ -1295,6 +1302,13 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi_f32(GArgs a, double2* __rest
         }
         __syncthreads();
       }
+    } else if (a.nrhs == 1 && pass == 0) {
+      // block 0 owns no rows: while the others form their partial sums it fetches the earlier
+      // rotations its Givens update needs after the second barrier
+      for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        s_cs[c] = a.cs[c];
+        s_sn[c] = a.sn[c];
+      }
     }
     grid_sync(bar, bar + 1, G, err);
     // (R) totals over blocks 1..G-1, one warp per (RHS, column), fixed order
@@ -1328,9 +1342,9 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi_f32(GArgs a, double2* __rest
     for (int s = 0; s < a.nrhs; ++s) {
       if (s_act[s] < want) continue;
       const double2* hs = hr + (size_t)s * ps;
-      for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+      for (int c = threadIdx.x; c <= j + 1; c += blockDim.x) {  // with ||w||^2
         s_h[c] = hs[c];
-        s_hf[c] = make_float2((float)hs[c].x, (float)hs[c].y);
+        if (c <= j) s_hf[c] = make_float2((float)hs[c].x, (float)hs[c].y);
       }
       __syncthreads();
       if (warp == 0) {
@@ -1338,7 +1352,7 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi_f32(GArgs a, double2* __rest
         for (int c = lane; c <= j; c += 32) t += cabs2(s_h[c]);
         t = warp_sum(t);
         if (lane == 0) {
-          const double wn2 = hs[j + 1].x;
+          const double wn2 = s_h[j + 1].x;
           const double hn2 = fmax(wn2 - t, 0.0);
           const bool again = pass == 0 && !(hn2 > 1e-4 * wn2);
           const double inv = hn2 > 0.0 ? rsqrt_nr(hn2) : 0.0;
@@ -1356,7 +1370,7 @@ __global__ void __launch_bounds__(256, 2) k_arnoldi_f32(GArgs a, double2* __rest
           const double2 t = pass == 0 ? s_h[c] : cadd(a.hcol[ho + c], s_h[c]);
           if (!last) a.hcol[ho + c] = t;
           s_acc[c] = t;
-          if (c < j) {
+          if (c < j && a.nrhs > 1) {  // one RHS: block 0 fetched them during the partial sums
             s_cs[c] = a.cs[(size_t)s * a.m + c];
             s_sn[c] = a.sn[(size_t)s * a.m + c];
           }
